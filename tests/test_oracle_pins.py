@@ -1,0 +1,716 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test ties one oracle step to what the paper or the mathematics fixes:
+exact rational arithmetic, closed forms, a library routine used as an
+independent evaluation, brute force on tiny inputs, or an invariant.  A
+plausible slip (dropped term, wrong sign or index, transposed operand) in the
+oracle fails at least one of these.  CPU only.
+"""
+import math
+import os
+from fractions import Fraction as Fr
+
+import numpy as np
+import pytest
+import torch
+from scipy.interpolate import CubicHermiteSpline
+from scipy.ndimage import correlate
+
+import oracle
+from oracle import value64 as v64
+from paper_2607_04230_b300 import synth
+
+F32_EPS = float(np.finfo(np.float32).eps)
+
+
+def _groom_from_layers(layers, bary, segs, faces=None):
+    """A hand-built groom: layers float [L][V][3], strands with given bary
+    (all on face 0)."""
+    layers = np.asarray(layers, np.float32)
+    L, V, _ = layers.shape
+    faces = np.asarray(faces if faces is not None else [[0, 1, 2]], np.int32)
+    bary = np.asarray(bary, np.float32).reshape(-1, 2)
+    S = bary.shape[0]
+    return synth.Groom(layer_verts=np.ascontiguousarray(layers), faces=faces,
+                       strand_face=np.zeros(S, np.uint32), strand_bary=np.ascontiguousarray(bary),
+                       strand_albedo=np.full((S, 3), 0.4, np.float32),
+                       bundle_delta=np.full(faces.shape[0], 0.5, np.float32), segments_per_strand=segs)
+
+
+# ---------------------------------------------------------------------------
+# strand generation (Sec. 2, Sec. 3.1.1)
+# ---------------------------------------------------------------------------
+
+def test_layer_point_unit_barycentrics_exact():
+    rng = np.random.default_rng(1)
+    layers = rng.normal(size=(5, 3, 3)).astype(np.float32)
+    g = _groom_from_layers(layers, [[0, 0], [1, 0], [0, 1]], 8)
+    for s, vi in enumerate([0, 1, 2]):
+        cp = oracle.strand_control_points(g, s, 5)   # C == L: control points are the layer points
+        np.testing.assert_array_equal(cp, layers[:, vi])
+
+
+def test_layer_point_matches_exact_rational():
+    rng = np.random.default_rng(2)
+    layers = rng.uniform(-0.3, 0.3, size=(4, 3, 3)).astype(np.float32)
+    r1, r2 = rng.random(200), rng.random(200)
+    bary = np.stack([np.sqrt(r1) * (1 - r2), np.sqrt(r1) * r2], 1).astype(np.float32)
+    g = _groom_from_layers(layers, bary, 3)
+    for s in range(200):
+        cp = oracle.strand_control_points(g, s, 4)
+        b1, b2 = Fr(float(bary[s, 0])), Fr(float(bary[s, 1]))
+        b0 = 1 - b1 - b2
+        for k in range(4):
+            for c in range(3):
+                terms = [b0 * Fr(float(layers[k, 0, c])), b1 * Fr(float(layers[k, 1, c])),
+                         b2 * Fr(float(layers[k, 2, c]))]
+                exact = float(sum(terms))
+                bound = 6 * F32_EPS * sum(abs(float(t)) for t in terms) + 1e-30
+                assert abs(float(cp[k, c]) - exact) <= bound
+
+
+def test_hermite_straight_line_is_uniform():
+    """Collinear, equally spaced layers: with chord-length tangents the
+    Hermite spline is the straight line traversed uniformly."""
+    A = np.array([0.01, -0.02, 0.03])
+    d = np.array([0.011, 0.017, -0.007])
+    L = 6
+    layers = np.stack([np.stack([A + k * d + off for off in (np.zeros(3), [1e-3, 0, 0], [0, 1e-3, 0])])
+                       for k in range(L)]).astype(np.float32)
+    g = _groom_from_layers(layers, [[0, 0]], 16)
+    for C in (2, 3, 9, 17, 33, 6, 11):
+        cp = oracle.strand_control_points(g, 0, C).astype(np.float64)
+        P0 = layers[0, 0].astype(np.float64)
+        PL = layers[-1, 0].astype(np.float64)
+        exp = P0[None] + (np.arange(C)[:, None] / (C - 1)) * (PL - P0)[None]
+        np.testing.assert_allclose(cp, exp, atol=2e-8)
+
+
+def test_hermite_matches_scipy_per_interval():
+    """Independent evaluation: scipy's cubic Hermite on each layer interval
+    with the finite-difference tangents scaled by the chord length."""
+    rng = np.random.default_rng(3)
+    L = 7
+    base = np.cumsum(rng.normal(scale=0.02, size=(L, 3)), 0)
+    layers = np.stack([base, base + [0.002, 0, 0], base + [0, 0.002, 0]], 1).astype(np.float32)
+    g = _groom_from_layers(layers, [[0.2, 0.3]], 20)
+    P = oracle.strand_control_points(g, 0, L).astype(np.float64)   # layer points
+    nrm = lambda v: v / np.linalg.norm(v)
+    mh = [nrm(P[1] - P[0])] + [nrm(P[k + 1] - P[k - 1]) for k in range(1, L - 1)] + [nrm(P[-1] - P[-2])]
+    for C in (13, 17, 21, 9):
+        cp = oracle.strand_control_points(g, 0, C).astype(np.float64)
+        for j in range(C):
+            u = j * (L - 1) / (C - 1)
+            k = min(int(math.floor(u)), L - 2)
+            ell = np.linalg.norm(P[k + 1] - P[k])
+            spl = CubicHermiteSpline([0.0, 1.0], np.stack([P[k], P[k + 1]]),
+                                     np.stack([mh[k] * ell, mh[k + 1] * ell]))
+            np.testing.assert_allclose(cp[j], spl(u - k), atol=5e-8)
+
+
+def test_styled_tangent_rules():
+    """Code 1 calcTangent: forward at the root, backward at the tip, central
+    otherwise, unit length."""
+    sc = synth.tiny_scene(5, num_strands=50)
+    g = sc.grooms[0]
+    for s in (0, 17, 49):
+        C = 9
+        p = oracle.strand_control_points(g, s, C).astype(np.float64)
+        t = oracle.strand_tangents(g, s, C).astype(np.float64)
+        nrm = lambda v: v / np.linalg.norm(v)
+        exp = [nrm(p[1] - p[0])] + [nrm(p[j + 1] - p[j - 1]) for j in range(1, C - 1)] + [nrm(p[-1] - p[-2])]
+        np.testing.assert_allclose(t, np.stack(exp), atol=3e-6)
+
+
+def test_value_layer_control_points_agree_with_decision_layer():
+    sc = synth.tiny_scene(6, num_strands=64)
+    g = sc.grooms[0]
+    gt = v64.GroomT(g, np.full(g.num_faces, 9), 0)
+    s = torch.arange(64)
+    P = v64.layer_points(gt, s)
+    mh = v64.layer_tangents(P)
+    for C in (9, 5, 4):
+        for j in range(C):
+            c64 = v64.control_points(P, mh, torch.full((64,), C), torch.full((64,), j)).numpy()
+            c32 = np.stack([oracle.strand_control_points(g, i, C)[j] for i in range(64)])
+            np.testing.assert_allclose(c64, c32, atol=2e-7)
+
+
+# ---------------------------------------------------------------------------
+# projection and snap (Sec. 3.1.2)
+# ---------------------------------------------------------------------------
+
+def test_projection_matches_float64_viewport_map():
+    sc = synth.tiny_scene(0, width=320, height=200)
+    cam = sc.camera
+    rng = np.random.default_rng(4)
+    M = cam.view_proj.astype(np.float64)
+    for _ in range(400):
+        p = (sc.grooms[0].layer_verts.reshape(-1, 3)[rng.integers(0, 100)].astype(np.float64)
+             + rng.normal(scale=0.05, size=3)).astype(np.float32)
+        valid, X, Y, wz = oracle.project_point(cam, p)
+        c = M @ np.r_[p.astype(np.float64), 1.0]
+        assert valid == (c[3] >= cam.near)
+        if not valid:
+            continue
+        xs = (c[0] / c[3] + 1) * 0.5 * cam.width
+        ys = (1 - c[1] / c[3]) * 0.5 * cam.height
+        assert abs(X - xs * 256) <= 1.0 and abs(Y - ys * 256) <= 1.0
+        assert abs(wz[1] - (c[3] - cam.near) / (cam.far - cam.near)) < 1e-6
+
+
+def test_projection_target_is_screen_centre_and_behind_is_invalid():
+    sc = synth.tiny_scene(0, width=256, height=128)
+    cam = sc.camera
+    c, _, _ = synth._aabb_center(sc.grooms)
+    valid, X, Y, _ = oracle.project_point(cam, c.astype(np.float32))
+    assert valid and abs(X - 128 * 256) <= 2 and abs(Y - 64 * 256) <= 2
+    behind = (cam.cam_pos.astype(np.float64) + (cam.cam_pos - c) * 0.5).astype(np.float32)
+    assert not oracle.project_point(cam, behind)[0]
+
+
+# ---------------------------------------------------------------------------
+# coverage predicate and depth (Sec. 3.1.2, Sec. 3.3)
+# ---------------------------------------------------------------------------
+
+def _lb_intersects(A, B, cx, cy, h):
+    """Exact Liang-Barsky clip of segment AB against the closed box."""
+    t0, t1 = Fr(0), Fr(1)
+    dX, dY = B[0] - A[0], B[1] - A[1]
+    for p, q in ((-dX, A[0] - (cx - h)), (dX, (cx + h) - A[0]), (-dY, A[1] - (cy - h)), (dY, (cy + h) - A[1])):
+        if p == 0:
+            if q < 0:
+                return False
+            continue
+        r = Fr(q, p)
+        if p < 0:
+            t0 = max(t0, r)
+        else:
+            t1 = min(t1, r)
+        if t0 > t1:
+            return False
+    return True
+
+
+def test_coverage_predicate_exact_rational_bruteforce():
+    rng = np.random.default_rng(5)
+    n = 0
+    for _ in range(6000):
+        A = [int(v) for v in rng.integers(-700, 700, 2)]
+        mode = rng.integers(0, 5)
+        if mode == 0:
+            B = list(A)                      # degenerate: a point
+        elif mode == 1:
+            B = [A[0] + int(rng.integers(-900, 900)), A[1]]   # horizontal
+        elif mode == 2:
+            B = [A[0], A[1] + int(rng.integers(-900, 900))]   # vertical
+        else:
+            B = [int(v) for v in rng.integers(-700, 700, 2)]
+        if rng.random() < 0.5:
+            cx, cy = [int(v) * 256 + 128 for v in rng.integers(-3, 3, 2)]
+        else:   # a box near a point of the segment
+            u = rng.random()
+            px, py = A[0] + u * (B[0] - A[0]), A[1] + u * (B[1] - A[1])
+            cx = int(np.floor(px / 256 + rng.normal(scale=0.6))) * 256 + 128
+            cy = int(np.floor(py / 256 + rng.normal(scale=0.6))) * 256 + 128
+        h = int(rng.choice([128, 1, 9, 32, 64, 127]))
+        got = oracle.segment_covers(A[0], A[1], B[0], B[1], cx, cy, h)
+        assert got == _lb_intersects(A, B, cx, cy, h), (A, B, cx, cy, h)
+        n += got
+    assert n > 600
+
+
+def test_coverage_boundary_touches_are_closed():
+    # a segment ending exactly on the box edge, and one grazing a corner
+    assert oracle.segment_covers(0, 0, 256, 0, 256 + 128, 0, 128)        # ends at x = 256 = cx - h
+    assert not oracle.segment_covers(0, 0, 255, 0, 256 + 128, 0, 128)
+    assert oracle.segment_covers(0, 512, 512, 0, 384, 384, 128)          # passes through corner (256, 256)
+    assert not oracle.segment_covers(0, 511, 511, 0, 384, 384, 128)
+
+
+def test_coverage_horizontal_segment_analytic():
+    """From x0 <= x1 at height Y: conservative rows j satisfy
+    |Y - (256 j + 128)| <= 128, columns ceil(x0/256)-1 .. floor(x1/256);
+    centre rows |Y - cy| <= hc and x0 - hc <= cx <= x1 + hc."""
+    rng = np.random.default_rng(6)
+    for _ in range(60):
+        x0 = int(rng.integers(-300, 2000))
+        x1 = x0 + int(rng.integers(0, 1500))
+        Y = int(rng.integers(0, 2000))
+        hc = int(rng.choice([1, 9, 32, 128]))
+        for j in range(-1, 10):
+            cy = 256 * j + 128
+            for i in range(-2, 12):
+                cx = 256 * i + 128
+                cons = abs(Y - cy) <= 128 and math.ceil(x0 / 256) - 1 <= i <= math.floor(x1 / 256)
+                cen = abs(Y - cy) <= hc and x0 - hc <= cx <= x1 + hc
+                assert oracle.segment_covers(x0, Y, x1, Y, cx, cy, 128) == cons
+                assert oracle.segment_covers(x1, Y, x0, Y, cx, cy, hc) == cen
+
+
+def test_depth24_endpoints_and_quantization():
+    # pixel centre at A -> zA; at B -> zB; beyond B clamps to zB
+    zA, zB = np.float32(0.25), np.float32(0.75)
+    assert oracle.depth24(128, 128, 128 + 2560, 128, zA, zB, 128, 128) == int(0.25 * 2 ** 24)
+    assert oracle.depth24(128, 128, 128 + 2560, 128, zA, zB, 128 + 2560, 128) == int(0.75 * 2 ** 24)
+    assert oracle.depth24(128, 128, 128 + 2560, 128, zA, zB, 128 + 9000, 128) == int(0.75 * 2 ** 24)
+    assert oracle.depth24(0, 0, 0, 0, np.float32(1.5), zB, 100, 100) == 2 ** 24 - 1   # clamp, degenerate
+    # halfway, exactly representable
+    assert oracle.depth24(0, 0, 512, 0, zA, zB, 256, 0) == int(0.5 * 2 ** 24)
+
+
+def _brute_force_keys(g, cam, C, base=0):
+    """Per-pixel nearest-segment search over every segment of every strand
+    (exact rational coverage), recomputing d24 in float32 numpy."""
+    W, H = cam.width, cam.height
+    segs = []
+    f32 = np.float32
+    focal = f32(f32(0.5) * f32(H)) / f32(cam.tan_half_fovy)
+    for s in range(g.num_strands):
+        cp = oracle.strand_control_points(g, s, C)
+        pr = [oracle.project_point(cam, p) for p in cp]
+        for j in range(C - 1):
+            (va, XA, YA, wa), (vb, XB, YB, wb) = pr[j], pr[j + 1]
+            if not (va and vb):
+                continue
+            wm = f32(f32(wa[0] + wb[0]) * f32(0.5))
+            r = f32(f32(f32(128.0) * f32(g.strand_width_m)) * focal) / wm
+            hc = int(min(max(np.rint(r), 1), 128))
+            segs.append((XA, YA, XB, YB, f32(wa[1]), f32(wb[1]), hc, ((base + s) << 7) | j))
+    vc = np.full(W * H, oracle.EMPTY, np.uint64)
+    va = vc.copy()
+    for (XA, YA, XB, YB, zA, zB, hc, sid) in segs:
+        for m in range(H):
+            cy = 256 * m + 128
+            if min(YA, YB) > cy + 256 or max(YA, YB) < cy - 256:
+                continue
+            for i in range(W):
+                cx = 256 * i + 128
+                if min(XA, XB) > cx + 256 or max(XA, XB) < cx - 256:
+                    continue
+                ca = _lb_intersects((XA, YA), (XB, YB), cx, cy, 128)
+                cc = _lb_intersects((XA, YA), (XB, YB), cx, cy, hc)
+                if not (ca or cc):
+                    continue
+                dX, dY = XB - XA, YB - YA
+                num, den = (cx - XA) * dX + (cy - YA) * dY, dX * dX + dY * dY
+                t = f32(0) if den == 0 else min(max(f32(num) / f32(den), f32(0)), f32(1))
+                z = min(max(f32(zA + f32(f32(zB - zA) * t)), f32(0)), f32(1))
+                d = min(int(np.floor(f32(z * f32(16777216.0)))), 2 ** 24 - 1)
+                key = np.uint64((d << 40) | sid)
+                px = m * W + i
+                if ca:
+                    va[px] = min(va[px], key)
+                if cc:
+                    vc[px] = min(vc[px], key)
+    return vc, va
+
+
+@pytest.mark.parametrize("seed,W,H,C", [(11, 37, 29, 5), (12, 24, 40, 4)])
+def test_raster_equals_bruteforce_nearest_segment(seed, W, H, C):
+    sc = synth.tiny_scene(seed, width=W, height=H, num_strands=40, segments=C - 1,
+                          dist_m=0.35, jitter_m=0.004)
+    g = sc.grooms[0]
+    lods = [oracle.lod(g, sc.camera, synth.LodParams(0))]
+    vc, va, cnt = oracle.raster([g], sc.camera, lods)
+    bc, ba = _brute_force_keys(g, sc.camera, C)
+    assert (va != oracle.EMPTY).sum() > 50
+    np.testing.assert_array_equal(va, ba)
+    np.testing.assert_array_equal(vc, bc)
+
+
+def test_raster_invariants_and_thread_independence():
+    sc = synth.scene_tiny_256()
+    lods = oracle.lods_for(sc)
+    vc1, va1, c1 = oracle.raster(sc.grooms, sc.camera, lods, nthreads=1)
+    vc4, va4, c4 = oracle.raster(sc.grooms, sc.camera, lods, nthreads=4)
+    np.testing.assert_array_equal(vc1, vc4)
+    np.testing.assert_array_equal(va1, va4)
+    assert tuple(c1) == tuple(c4)
+    # centre sample subset of conservative: A <= G everywhere, G set implies A set
+    assert np.all(va1 <= vc1)
+    eG, dG, sg, seg = v64.key_fields(vc1)
+    eA, _, sgA, segA = v64.key_fields(va1)
+    assert np.all(~eA[~eG])
+    # decoded IDs round-trip into valid strands and segments
+    g = sc.grooms[0]
+    for e, s_, j_ in ((eG, sg, seg), (eA, sgA, segA)):
+        s_ = s_[~e]
+        j_ = j_[~e]
+        assert np.all(s_ < g.num_strands)
+        assert np.all(j_ < lods[0][1][g.strand_face[s_]] - 1)
+    # counts are the number of covered (pixel, layer) pairs >= distinct pixels
+    assert c1[1] >= (~eA).sum() and c1[0] >= (~eG).sum()
+
+
+def test_key_packing_round_trip():
+    rng = np.random.default_rng(7)
+    d = rng.integers(0, 2 ** 24, 1000).astype(np.uint64)
+    s = rng.integers(0, 2 ** 33 - 1, 1000).astype(np.uint64)
+    j = rng.integers(0, 127, 1000).astype(np.uint64)
+    key = (d << np.uint64(40)) | (s << np.uint64(7)) | j
+    e, d2, s2, j2 = v64.key_fields(key)
+    assert not e.any()
+    np.testing.assert_array_equal(d2, d.astype(np.int64))
+    np.testing.assert_array_equal(s2, s.astype(np.int64))
+    np.testing.assert_array_equal(j2, j.astype(np.int64))
+    # smaller depth always wins over any payload
+    assert ((np.uint64(5) << np.uint64(40)) | np.uint64(0xFFFFFFFFFE)) < (np.uint64(6) << np.uint64(40))
+
+
+# ---------------------------------------------------------------------------
+# LOD (Sec. 3.2, Eqs. 1-5)
+# ---------------------------------------------------------------------------
+
+def test_lod_control_point_snap_table_cmax127():
+    """Eqs. 4-5 with C_max = 127: C is a power of two plus one and never
+    exceeds 65; the layer count is the lower bound."""
+    seen = set()
+    for Lf in np.linspace(0.0, 1.0, 2001).astype(np.float32):
+        raw64 = math.sqrt(float(Lf)) * 127
+        if abs(raw64 - round(raw64)) < 1e-3:
+            continue
+        craw = max(int(math.floor(raw64)), 4)
+        exp = min(2 ** int(math.floor(math.log2(craw - 1))) + 1, 127)
+        exp = max(exp, 4)
+        _, c = oracle.lod_counts(Lf, 100, 0.5, 4, 127)
+        assert c == exp
+        seen.add(c)
+    assert seen == {5, 9, 17, 33, 65, 4}
+    assert oracle.lod_counts(1.0, 10, 0.0, 4, 127)[1] == 65
+
+
+def test_lod_full_detail_reaches_cmax_only_for_power_of_two_segments():
+    assert oracle.lod_counts(1.0, 10, 0.1, 8, 17) == (10, 17)
+    assert oracle.lod_counts(1.0, 10, 0.1, 6, 13) == (10, 9)      # 12 segments snap to 8
+    assert oracle.lod_counts(0.0, 10, 0.1, 6, 13) == (1, 6)       # floor: layers, at least one strand
+
+
+def test_lod_strand_count_eq1():
+    rng = np.random.default_rng(8)
+    for _ in range(3000):
+        Lf = np.float32(rng.random())
+        N = int(rng.integers(0, 400))
+        dl = np.float32(rng.random() * 0.999)
+        v = float(Lf) * (N + float(dl))
+        if abs(v - round(v)) < 1e-3:
+            continue
+        exp = 0 if N == 0 else min(max(math.ceil(v), 1), N)
+        assert oracle.lod_counts(Lf, N, dl, 4, 9)[0] == exp
+
+
+def test_lod_disabled_is_full_detail_and_culling():
+    sc = synth.tiny_scene(0, num_strands=500)
+    g = sc.grooms[0]
+    n, c = oracle.lod(g, sc.camera, synth.LodParams(0))
+    counts = np.bincount(g.strand_face, minlength=g.num_faces)
+    np.testing.assert_array_equal(n, counts)
+    assert np.all(c == g.segments_per_strand + 1)
+    # camera turned away: every bundle is culled
+    ctr, _, _ = synth._aabb_center([g])
+    away = synth.make_camera(ctr + np.array([0, 0, 0.5]), ctr + np.array([0, 0, 1.5]), 40, 256, 256)
+    n2, _ = oracle.lod(g, away, synth.LodParams(1, 3.0))
+    assert n2.sum() == 0
+    # groom entirely to the right of the frustum
+    right = synth.make_camera(ctr + np.array([-2.0, 0, 0.5]), ctr + np.array([-2.0, 0, 0]), 40, 256, 256)
+    assert oracle.lod(g, right, synth.LodParams(1, 3.0))[0].sum() == 0
+
+
+def test_lod_bundle_aabb_eq2_eq3():
+    sc = synth.tiny_scene(9, num_strands=800, width=400, height=300, dist_m=1.2)
+    g, cam = sc.grooms[0], sc.camera
+    n, c = oracle.lod(g, cam, synth.LodParams(1, 3.0))
+    counts = np.bincount(g.strand_face, minlength=g.num_faces)
+    M = cam.view_proj.astype(np.float64)
+    checked = 0
+    for f in range(g.num_faces):
+        pts = g.layer_verts[:, g.faces[f]].reshape(-1, 3).astype(np.float64)
+        clip = np.c_[pts, np.ones(len(pts))] @ M.T
+        xs = (clip[:, 0] / clip[:, 3] + 1) * 0.5 * cam.width
+        ys = (1 - clip[:, 1] / clip[:, 3]) * 0.5 * cam.height
+        diag = math.hypot(xs.max() - xs.min(), ys.max() - ys.min())
+        Lf = min(max(diag / cam.height * 3.0, 0.0), 1.0)
+        v = Lf * (counts[f] + float(g.bundle_delta[f]))
+        raw = math.sqrt(Lf) * (g.segments_per_strand + 1)
+        if abs(v - round(v)) < 1e-3 or abs(raw - round(raw)) < 1e-3:
+            continue
+        expn = 0 if counts[f] == 0 else min(max(math.ceil(v), 1), counts[f])
+        craw = max(int(math.floor(raw)), g.num_layers)
+        expc = max(min(2 ** int(math.floor(math.log2(craw - 1))) + 1, g.segments_per_strand + 1), g.num_layers)
+        assert n[f] == expn and c[f] == expc
+        checked += 1
+    assert checked > 20
+
+
+def test_lod_total_strands_monotone_in_distance():
+    g = synth.make_groom(1, 8, 2, 5, 0.2, 6000, 16, curl_amp_m=0.01)
+    tot = []
+    for i in range(8):
+        sc = synth.scene_lod_sweep(i, g)
+        tot.append(int(oracle.lod(g, sc.camera, sc.lod)[0].sum()))
+    # farthest first: counts grow as the groom gets bigger on screen
+    assert all(a <= b for a, b in zip(tot, tot[1:])), tot
+    assert tot[0] < tot[-1] <= g.num_strands
+
+
+# ---------------------------------------------------------------------------
+# shading (Sec. 3.4) and screen tangent (Code 2)
+# ---------------------------------------------------------------------------
+
+def _shade_one(T, X, albedo, cam_pos, dirs, rad, rough=0.15, tilt=-0.05, amb=0.05):
+    cam = synth.Camera(np.eye(4, dtype=np.float32), np.asarray(cam_pos, np.float32), 0.05, 256, 0.5, 8, 8)
+    lights = synth.make_lights(dirs, rad, ambient=amb)
+    out = v64.shade(torch.tensor(np.array([X], np.float64)), torch.tensor(np.array([T], np.float64)),
+                    torch.tensor(np.array([albedo], np.float64)), cam, lights, rough, tilt)
+    return out[0].numpy(), lights
+
+
+def test_shading_closed_forms():
+    kd, ks = float(np.float32(1 / math.pi)), float(np.float32(0.25))
+    b = 0.15
+    sa = math.sin(-0.05)
+    alb = np.array([0.3, 0.4, 0.5])
+    # T perpendicular to L and V: diffuse = albedo k_d, lobe at T.L = T.V = 0
+    c, _ = _shade_one([1, 0, 0], [0, 0, 0], alb, [0, 0, 2], [[0, 1, 0]], [1.0])
+    exp = alb * kd + ks * math.exp(-(sa * sa) / (2 * b * b)) + float(np.float32(0.05)) * alb
+    np.testing.assert_allclose(c, exp, rtol=1e-12)
+    # T parallel to L: no diffuse; T.L = 1, T.V = 0
+    c, _ = _shade_one([0, 1, 0], [0, 0, 0], alb, [0, 0, 2], [[0, 1, 0]], [1.0])
+    u = 0.5 + sa
+    exp = ks * math.exp(-(u * u) / (2 * b * b)) + float(np.float32(0.05)) * alb
+    np.testing.assert_allclose(c, exp, rtol=1e-12)
+    # two lights add
+    c1, _ = _shade_one([0.6, 0.8, 0], [0, 0, 0], alb, [0, 0, 2], [[1, 0, 0]], [0.7], amb=0)
+    c2, _ = _shade_one([0.6, 0.8, 0], [0, 0, 0], alb, [0, 0, 2], [[0, 0, 1]], [0.2], amb=0)
+    c12, _ = _shade_one([0.6, 0.8, 0], [0, 0, 0], alb, [0, 0, 2], [[1, 0, 0], [0, 0, 1]], [0.7, 0.2], amb=0)
+    np.testing.assert_allclose(c12, c1 + c2, rtol=1e-12)
+
+
+def test_screen_tangent_against_numerical_jacobian_and_signs():
+    sc = synth.tiny_scene(0, width=300, height=200)
+    cam = sc.camera
+    M = cam.view_proj.astype(np.float64)
+
+    def scr(p):
+        c = M @ np.r_[p, 1.0]
+        return np.array([(c[0] / c[3] + 1) * 0.5 * cam.width, (1 - c[1] / c[3]) * 0.5 * cam.height])
+
+    rng = np.random.default_rng(10)
+    ctr, _, _ = synth._aabb_center(sc.grooms)
+    for _ in range(50):
+        X = ctr + rng.normal(scale=0.03, size=3)
+        T = rng.normal(size=3)
+        T /= np.linalg.norm(T)
+        h = 1e-6
+        J = (scr(X + h * T) - scr(X - h * T)) / (2 * h)
+        exp = J / np.linalg.norm(J)
+        ts64 = v64.screen_tangent(torch.tensor(X[None]), torch.tensor(T[None]), cam)[0].numpy()
+        np.testing.assert_allclose(ts64, exp, atol=1e-6)
+        iso, ts32 = oracle.screen_tangent(cam, X.astype(np.float32), T.astype(np.float32))
+        assert not iso
+        np.testing.assert_allclose(ts32, exp, atol=2e-5)
+    # camera looks along -z: world +x is screen right, world +y is screen up (y down)
+    assert np.allclose(oracle.screen_tangent(cam, ctr.astype(np.float32), np.float32([1, 0, 0]))[1], [1, 0], atol=1e-3)
+    assert np.allclose(oracle.screen_tangent(cam, ctr.astype(np.float32), np.float32([0, 1, 0]))[1], [0, -1], atol=1e-3)
+    # a tangent along the view ray through X is degenerate; so is one within
+    # 0.3 degrees of it, but not one 3 degrees off; a zero tangent is too
+    ray = (ctr - cam.cam_pos).astype(np.float64)
+    ray /= np.linalg.norm(ray)
+    assert oracle.screen_tangent(cam, ctr.astype(np.float32), ray.astype(np.float32))[0]
+    side = np.cross(ray, [0.0, 1.0, 0.0])
+    side /= np.linalg.norm(side)
+    for ang, iso in ((0.005, True), (0.05, False)):
+        t = np.cos(ang) * ray + np.sin(ang) * side
+        assert oracle.screen_tangent(cam, ctr.astype(np.float32), t.astype(np.float32))[0] == iso
+    assert oracle.screen_tangent(cam, ctr.astype(np.float32), np.zeros(3, np.float32))[0]
+
+
+def test_strip_membership_geometry():
+    assert oracle.in_strip(0, 1.0, 0.0, 5, 0, 0.5)
+    assert not oracle.in_strip(0, 1.0, 0.0, 0, 1, 0.5)
+    r = np.float32(math.sqrt(0.5))
+    assert oracle.in_strip(0, r, r, 3, 3, 0.5)
+    assert not oracle.in_strip(0, r, r, 1, 0, 0.5)          # distance 0.707 > 0.5
+    assert oracle.in_strip(1, 0, 0, 0, 0, 0.5) and not oracle.in_strip(1, 0, 0, 1, 0, 0.5)
+
+
+# ---------------------------------------------------------------------------
+# filter, alpha, reconnection (Sec. 3.3)
+# ---------------------------------------------------------------------------
+
+def _resolve_scene(sc, filt=None, lights=None):
+    lods = oracle.lods_for(sc)
+    filt = filt or sc.filt
+    vc, va, _ = oracle.raster(sc.grooms, sc.camera, lods)
+    dec = oracle.resolve_decisions(sc.grooms, sc.camera, lods, filt, vc, va)
+    gts = [v64.GroomT(g, l[1], b) for g, l, b in zip(sc.grooms, lods, oracle.strand_bases(sc.grooms))]
+    rgba, pix = v64.resolve(gts, sc.camera, lights or sc.lights, filt, vc, va, dec)
+    return rgba, pix, vc, va, dec, lods
+
+
+def test_filter_preserves_uniform_colour():
+    """Ambient-only light and one albedo: every centre colour is equal, so
+    every normalized filter output equals it."""
+    sc = synth.tiny_scene(0, num_strands=600)
+    sc.grooms[0].strand_albedo[:] = np.float32(0.37)
+    lights = synth.make_lights(np.zeros((0, 3)) + [[0, 1, 0]], [0.0], ambient=0.5)
+    rgba, pix, vc, va, dec, _ = _resolve_scene(sc, lights=lights)
+    c = float(np.float32(0.5)) * float(np.float32(0.37))
+    nz = rgba[:, 3] > 0
+    assert nz.sum() > 100
+    np.testing.assert_allclose(rgba[nz, :3].numpy(), c, rtol=1e-13)
+    a = rgba[:, 3].numpy()
+    assert np.all((a >= 0) & (a <= 1))
+
+
+def test_filter_isotropic_unit_weights_is_masked_gaussian_convolution():
+    """s_par = s_perp, no colour term, no depth rejection: the filter is a
+    normalized Gaussian convolution of the centre-sample image restricted to
+    centre pixels (scipy correlate, zero outside the screen)."""
+    sc = synth.tiny_scene(1, num_strands=400, width=96, height=80)
+    filt = synth.FilterParams(s_par=0.4, s_perp=0.4, sigma_c=1e9, depth_reject_m=1e9, depth_mismatch_m=1e9)
+    rgba, pix, vc, va, dec, lods = _resolve_scene(sc, filt=filt)
+    W, H = sc.camera.width, sc.camera.height
+    eG = v64.key_fields(vc)[0].reshape(H, W)
+    # centre colours from the same scene with the filter off
+    off = synth.FilterParams(enabled=0)
+    gts = [v64.GroomT(g, l[1], b) for g, l, b in zip(sc.grooms, lods, oracle.strand_bases(sc.grooms))]
+    img0, pix0 = v64.resolve(gts, sc.camera, sc.lights, off, vc, va, dec)
+    C = v64.full_image(img0, pix0, W, H).numpy()[..., :3]
+    r = 5
+    sig = 0.4 * r
+    yy, xx = np.mgrid[-r:r + 1, -r:r + 1]
+    k = np.exp(-(xx ** 2 + yy ** 2) / sig ** 2)
+    mask = (~eG).astype(np.float64)
+    num = np.stack([correlate(C[..., ch] * mask, k, mode="constant") for ch in range(3)], -1)
+    den = correlate(mask, k, mode="constant")
+    out = v64.full_image(rgba, pix, W, H).numpy()
+    sel = ~eG
+    den = np.where(den > 0, den, 1.0)
+    assert sel.sum() > 50
+    np.testing.assert_allclose(out[sel][:, :3], (num / den[..., None])[sel], atol=1e-9)
+
+
+def test_filter_isolated_centre_pixel_keeps_its_colour():
+    """A centre pixel with no other contributing neighbour in its window
+    outputs its own shaded colour."""
+    sc = synth.tiny_scene(2, num_strands=12, width=200, height=200)
+    rgba, pix, vc, va, dec, lods = _resolve_scene(sc)
+    W, H = sc.camera.width, sc.camera.height
+    eG, dG, _, _ = v64.key_fields(vc)
+    gts = [v64.GroomT(g, l[1], b) for g, l, b in zip(sc.grooms, lods, oracle.strand_bases(sc.grooms))]
+    img0, pix0 = v64.resolve(gts, sc.camera, sc.lights, synth.FilterParams(enabled=0), vc, va, dec)
+    C = v64.full_image(img0, pix0, W, H).numpy().reshape(-1, 4)
+    out = v64.full_image(rgba, pix, W, H).numpy().reshape(-1, 4)
+    rej, mis = oracle.depth_thresholds(sc.camera, sc.filt)
+    eA, dA, _, _ = v64.key_fields(va)
+    n = 0
+    for p in np.nonzero(~eG)[0]:
+        x, y = p % W, p // W
+        others = 0
+        for dy in range(-5, 6):
+            for dx in range(-5, 6):
+                qx, qy = x + dx, y + dy
+                if (dx or dy) and 0 <= qx < W and 0 <= qy < H:
+                    q = qy * W + qx
+                    others += (not eG[q]) and abs(dG[q] - dG[p]) <= rej
+        if others == 0 and not (dA[p] + mis <= dG[p]):
+            np.testing.assert_allclose(out[p, :3], C[p, :3], rtol=1e-13)
+            n += 1
+    assert n >= 3
+
+
+def test_strip_counts_equal_window_bruteforce():
+    sc = synth.tiny_scene(3, num_strands=300, width=80, height=72)
+    rgba, pix, vc, va, dec, lods = _resolve_scene(sc)
+    W, H = sc.camera.width, sc.camera.height
+    eG = v64.key_fields(vc)[0]
+    eA = v64.key_fields(va)[0]
+    gts = [v64.GroomT(g, l[1], b) for g, l, b in zip(sc.grooms, lods, oracle.strand_bases(sc.grooms))]
+    rng = np.random.default_rng(11)
+    cand = np.nonzero(~eG)[0]
+    for p in rng.choice(cand, size=min(40, cand.size), replace=False):
+        x, y = p % W, p // W
+        X, T, _ = v64.pixel_geometry(gts[0], v64.key_fields(vc)[2][[p]], v64.key_fields(vc)[3][[p]],
+                                     dec["numG"][[p]], dec["denG"][[p]])
+        iso, ts = oracle.screen_tangent(sc.camera, X[0].numpy().astype(np.float32), T[0].numpy().astype(np.float32))
+        hc = ha = 0
+        for dy in range(-5, 6):
+            for dx in range(-5, 6):
+                qx, qy = x + dx, y + dy
+                if 0 <= qx < W and 0 <= qy < H and oracle.in_strip(iso, ts[0], ts[1], dx, dy, 0.5):
+                    hc += not eG[qy * W + qx]
+                    ha += not eA[qy * W + qx]
+        # the FP64-rounded geometry may sit on a strip boundary; allow that rare case
+        assert abs(dec["HcG"][p] - hc) <= 1 and abs(dec["HaG"][p] - ha) <= 1
+        assert dec["HaG"][p] >= 1 and 0 <= dec["HcG"][p] <= dec["HaG"][p] + 0
+
+
+def test_depth_thresholds_in_d24_units():
+    cam = synth.tiny_scene(0).camera
+    rej, mis = oracle.depth_thresholds(cam, synth.FilterParams())
+    span = float(np.float32(256.0)) - float(np.float32(0.05))
+    assert rej == round(1.45e-3 / span * 2 ** 24) == 95
+    assert mis == round(5e-4 / span * 2 ** 24) == 33
+
+
+def test_paper_constants_golden():
+    here = os.path.dirname(__file__)
+    vals = {}
+    for line in open(os.path.join(here, "golden", "paper_constants.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, val = line.split()[:2]
+        vals[name] = float(val)
+    f = synth.FilterParams()
+    assert f.radius == vals["filter_radius"]
+    assert f.sigma_c == vals["sigma_c"] and f.iso_scale == vals["iso_scale"]
+    assert f.depth_reject_m == vals["depth_reject"] and f.depth_mismatch_m == vals["depth_mismatch"]
+    assert f.strip_halfwidth == vals["strip_halfwidth"]
+    assert synth.LodParams().lam == vals["lambda_groom1"]
+    # with C_max = 127 the full-detail snap of Eq. 5 is 65
+    assert oracle.lod_counts(1.0, 1, 0.0, 2, int(vals["c_max"]))[1] == 65
+
+
+# ---------------------------------------------------------------------------
+# gradient of the FP64 value layer (visibility held fixed)
+# ---------------------------------------------------------------------------
+
+def test_value_layer_gradient_matches_central_differences():
+    sc = synth.tiny_scene(4, num_strands=60, width=64, height=56, dist_m=0.3)
+    g = sc.grooms[0]
+    lods = oracle.lods_for(sc)
+    vc, va, _ = oracle.raster(sc.grooms, sc.camera, lods)
+    dec = oracle.resolve_decisions(sc.grooms, sc.camera, lods, sc.filt, vc, va)
+    rng = np.random.default_rng(12)
+    target = torch.from_numpy(rng.random((64 * 56, 3)) * 0.2)
+
+    def loss(lv, alb):
+        gt = v64.GroomT(g, lods[0][1], 0, layer_verts=lv, albedo=alb)
+        rgba, pix = v64.resolve([gt], sc.camera, sc.lights, sc.filt, vc, va, dec)
+        img = torch.zeros((64 * 56, 3), dtype=torch.float64).index_put((torch.from_numpy(pix),),
+                                                                       rgba[:, :3] * rgba[:, 3:4])
+        return torch.sqrt(((img - target) ** 2).sum())
+
+    lv = torch.from_numpy(g.layer_verts.astype(np.float64)).requires_grad_(True)
+    alb = torch.from_numpy(g.strand_albedo.astype(np.float64)).requires_grad_(True)
+    l0 = loss(lv, alb)
+    l0.backward()
+    glv, galb = lv.grad.numpy(), alb.grad.numpy()
+    assert np.abs(glv).max() > 0
+    h = 1e-5
+    flat = np.argsort(-np.abs(glv).ravel())[:12]
+    for idx in list(flat) + list(rng.integers(0, glv.size, 6)):
+        e = torch.zeros(glv.size, dtype=torch.float64)
+        e[idx] = h
+        e = e.reshape(glv.shape)
+        with torch.no_grad():
+            fd = (loss(lv + e, alb) - loss(lv - e, alb)).item() / (2 * h)
+        assert abs(fd - glv.ravel()[idx]) <= 1e-6 + 1e-4 * abs(fd), (idx, fd, glv.ravel()[idx])
+    for idx in np.argsort(-np.abs(galb).ravel())[:6]:
+        e = torch.zeros(galb.size, dtype=torch.float64)
+        e[idx] = h
+        e = e.reshape(galb.shape)
+        with torch.no_grad():
+            fd = (loss(lv, alb + e) - loss(lv, alb - e)).item() / (2 * h)
+        assert abs(fd - galb.ravel()[idx]) <= 1e-7 + 1e-5 * abs(fd)
