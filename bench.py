@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark of the deferred hair rasterizer on B300.
+
+One step = one frame of the whole hot path on synthetic inputs already
+resident in HBM: clear, LOD pre-pass + work list, strand generation +
+rasterization into both 64-bit visibility layers, deferred resolve (decode,
+shading, strand-connection / bilateral filter, alpha).  The L2 is flushed
+(256 MiB write) between timed steps; each step is timed with CUDA events that
+the library records on the launching stream at phase boundaries.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl native|reference]
+
+Prints one JSON line (rank 0).  N > 1 runs N independent replicas (one frame
+per GPU, no collective on the data path); value = all ranks' segments / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "strand segments rasterized/s (resolved frame, 1 spp)"
+UNIT = "segments/s"
+L2_FLUSH_BYTES = 256 << 20
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+FALLBACK_HBM_GBS = 6400.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", choices=["single_1080p", "crowd_4k", "tiny_256"], default="single_1080p")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_scene(name):
+    from paper_2607_04230_b300 import synth
+    if name == "single_1080p":
+        sc = synth.scene_single_1080p()
+        cfg = {"workload": "single groom, 1920x1080, 1 spp", "strands": 100_000, "segments_per_strand": 16,
+               "scalp_triangles": 2048, "layers": 8, "lod": "off (full detail)", "lights": 2,
+               "filter": "on, r=5"}
+    elif name == "crowd_4k":
+        sc = synth.scene_crowd_4k()
+        cfg = {"workload": "crowd of 64 grooms, 3840x2160, 1 spp, one render call", "grooms": 64,
+               "strands": int(sum(g.num_strands for g in sc.grooms)), "lod": "on, lambda=3", "lights": 2,
+               "filter": "on, r=5"}
+    else:
+        sc = synth.scene_tiny_256()
+        cfg = {"workload": "tiny groom, 256x256, 1 spp", "strands": 1000, "segments_per_strand": 8,
+               "lod": "off", "filter": "on, r=5"}
+    cfg["resolution"] = f"{sc.camera.width}x{sc.camera.height}"
+    cfg["l2"] = "flushed between timed steps (256 MiB write)"
+    cfg["inputs"] = "seeded synthetic hair meshes (no paper grooms in the container)"
+    return sc, cfg
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], 0.0, set()
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax = max(smax, float(p[1]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def kernel_src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2607_04230_b300", "csrc")
+    for n in sorted(os.listdir(d)):
+        if n.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, n), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
+    None when it was taken on other kernel sources or another workload."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = t.get(workload, {}).get(kernel)
+    if not e or e.get("src_hash") != kernel_src_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def probe_atomic_peak(torch, hm, n_elems):
+    """Best 64-bit atomicMin rate (ops/s) of the probe kernel over a buffer of
+    frame size: coalesced distinct addresses and hashed addresses."""
+    buf = torch.empty(n_elems, dtype=torch.int64, device="cuda")
+    best = {}
+    for pattern in (0, 1):
+        rates = []
+        for _ in range(5):
+            buf.fill_(-1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            hm.probe_atomic_min(buf, rounds=8, pattern=pattern)
+            b.record()
+            b.synchronize()
+            rates.append(n_elems * 8 / (a.elapsed_time(b) * 1e-3))
+        best[pattern] = max(rates)
+    del buf
+    return best
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------
+def _subsample_groom(g, every: int, offset: int = 0):
+    from paper_2607_04230_b300 import synth
+    idx = np.arange(offset % every, g.num_strands, every)
+    return synth.Groom(layer_verts=g.layer_verts, faces=g.faces, strand_face=g.strand_face[idx],
+                       strand_bary=g.strand_bary[idx], strand_albedo=g.strand_albedo[idx],
+                       bundle_delta=g.bundle_delta, segments_per_strand=g.segments_per_strand,
+                       strand_width_m=g.strand_width_m, roughness=g.roughness, tilt=g.tilt), idx.size
+
+
+def oracle_frame_sample(scene, every: int, offset: int = 0):
+    """Oracle raster + FP64 resolve of every `every`-th strand of every groom.
+    Returns (segments drawn, seconds)."""
+    import oracle
+    from oracle import value64 as v64
+    from paper_2607_04230_b300 import synth
+    sub = synth.Scene([_subsample_groom(g, every, offset)[0] for g in scene.grooms], scene.camera, scene.lights,
+                      scene.filt, scene.lod)
+    t0 = time.perf_counter()
+    lods = oracle.lods_for(sub)
+    vc, va, _ = oracle.raster(sub.grooms, sub.camera, lods)
+    dec = oracle.resolve_decisions(sub.grooms, sub.camera, lods, sub.filt, vc, va)
+    gts = [v64.GroomT(g, l[1], b) for g, l, b in zip(sub.grooms, lods, oracle.strand_bases(sub.grooms))]
+    v64.resolve(gts, sub.camera, sub.lights, sub.filt, vc, va, dec)
+    dt = time.perf_counter() - t0
+    segs = int(sum(int((n.astype(np.int64) * (c.astype(np.int64) - 1)).sum()) for n, c in lods))
+    return segs, dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(scene, budget_s: float = 20.0):
+    every = 25
+    segs, dt = oracle_frame_sample(scene, every)
+    return {"value": segs / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+            "sample": f"every {every}th strand of every groom ({segs} segments) rasterized by the C oracle "
+                      f"(OpenMP, all host threads) and resolved by the FP64 torch oracle, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    scene, cfg = make_scene(args.workload)
+    every = {"single_1080p": 400, "crowd_4k": 800, "tiny_256": 10}[args.workload]
+    for i in range(args.warmup):
+        oracle_frame_sample(scene, every, offset=i)
+    tot_s, tot_t = 0, 0.0
+    for i in range(args.steps):
+        s, t = oracle_frame_sample(scene, every, offset=args.warmup + i)
+        tot_s += s
+        tot_t += t
+    v = tot_s / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 decisions + f64 values",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                             "sample": f"each step: every {every}th strand (rotating offset) of the workload, "
+                                       f"C oracle raster + FP64 torch resolve"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_native(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2607_04230_b300 import build, hm
+    build.build()
+    torch.cuda.set_device(local_rank)
+    scene, cfg = make_scene(args.workload)
+    grooms = hm.upload_scene(scene)
+    W, H = scene.camera.width, scene.camera.height
+    frame = hm.Frame(W, H)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        hm.render(grooms, scene, frame)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    hm.get_device_status()
+    st = hm.stats_dict(frame.stats)
+    segs = st["segments"]
+    atomics = st["covered_cons"] + st["covered_center"]
+
+    peak_rates = probe_atomic_peak(torch, hm, 2 * W * H)
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    gpu_uuid = str(torch.cuda.get_device_properties(local_rank).uuid)
+    if not gpu_uuid.startswith("GPU-"):
+        gpu_uuid = "GPU-" + gpu_uuid
+    clocks = ClockSampler(gpu_uuid)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k)
+        hm.set_phase_events(ev[k])
+        step()
+    hm.set_phase_events(None)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    frame_ms = [e[0].elapsed_time(e[5]) for e in ev]
+    phase_ms = {name: sum(e[a].elapsed_time(e[b]) for e in ev) / args.steps
+                for name, a, b in (("clear", 0, 1), ("lod", 1, 2), ("raster", 2, 3), ("resolve", 4, 5))}
+    t_total = sum(frame_ms) * 1e-3
+    if world > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    value = segs * args.steps * world / t_total
+    hm.get_device_status()
+
+    # end to end through the public API with host buffers: H2D of the hair
+    # mesh (animated layer vertices) and D2H of the RGBA image every step
+    e2e = None
+    if not args.no_e2e:
+        h_lv = [torch.from_numpy(g.layer_verts).pin_memory() for g in scene.grooms]
+        d_lv = [t.cuda() for t in h_lv]
+        h_rgba = torch.empty(frame.rgba.shape, dtype=torch.float32).pin_memory()
+        h2d = sum(t.numel() * 4 for t in h_lv)
+        d2h = h_rgba.numel() * 4
+        e2e_steps = max(10, args.steps // 4)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+        for k in range(e2e_steps + 3):
+            flush.fill_(k)
+            if k >= 3:
+                evs[k - 3][0].record()
+            for hg, h, d in zip(grooms, h_lv, d_lv):
+                d.copy_(h, non_blocking=True)
+                hg.update_layer_verts(d)
+            step()
+            h_rgba.copy_(frame.rgba, non_blocking=True)
+            if k >= 3:
+                evs[k - 3][1].record()
+        torch.cuda.synchronize()
+        te = sum(a.elapsed_time(b) for a, b in evs) * 1e-3
+        if world > 1:
+            tt = torch.tensor([te], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": segs * e2e_steps * world / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": te / e2e_steps * 1e3}
+
+    if rank != 0:
+        return 0
+    peaks, peaks_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    atom_peak = max(peak_rates.values())
+    t_r = phase_ms["raster"] * 1e-3
+    t_s = phase_ms["resolve"] * 1e-3
+    res_bytes = 32 * W * H            # both keys read once + RGBA written once
+    kernels = {
+        "raster_kernel": {"bound": "l2_atomic", "achieved": atomics / t_r / 1e9, "peak": atom_peak / 1e9,
+                          "unit": "Gatom/s", "ms": phase_ms["raster"],
+                          "work": f"{atomics} covered (pixel, layer) pairs per launch = 64-bit atomicMin ops"},
+        "resolve_kernel": {"bound": "hbm", "achieved": res_bytes / t_s / 1e9, "peak": hbm, "unit": "GB/s",
+                           "ms": phase_ms["resolve"], "work": f"{res_bytes} B per launch (32 B/px)"},
+    }
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    d = kernels[dom]
+    roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+                "frac": d["achieved"] / d["peak"], "traffic": ncu_traffic(dom, args.workload), "kernel": dom,
+                "peak_source": ("live probe: best 64-bit atomicMin rate of hm_probe_atomic_min over a "
+                                f"{2 * W * H}-element buffer (coalesced {peak_rates[0] / 1e9:.1f}, hashed "
+                                f"{peak_rates[1] / 1e9:.1f} Gatom/s)") if d["bound"] == "l2_atomic"
+                else f"{peaks_kind} hbm_gbs of MEASURED_PEAKS.json",
+                "work_per_launch": d["work"]}
+    for k in kernels.values():
+        k["frac"] = k["achieved"] / k["peak"]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
+            "config": dict(cfg, parallelism=f"replicas x{world}"),
+            "frame_ms": {k: round(v, 5) for k, v in phase_ms.items()},
+            "segments_per_frame": segs, "raster_segments_per_s": segs / t_r,
+            "roofline": roofline, "kernels": kernels,
+            "e2e": e2e, "gpu_launches": 4 * args.steps, "clocks": clk, "wall_s": wall}
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(scene)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        return run_native(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

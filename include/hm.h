@@ -1,0 +1,256 @@
+/*
+ * hm.h -- C ABI of libhm: deferred software rasterization of strand hair
+ * generated from hair meshes, on one NVIDIA B300 (sm_103a).
+ *
+ * The method is arXiv 2607.04230 ("Deferred Software Rasterization for
+ * Efficient Real-time Hair Rendering"): strands are generated on the fly from
+ * a hair mesh (Sec. 2 "Background: Hair mesh rendering", Sec. 3.1.1),
+ * rasterized into a 64-bit depth|ID visibility buffer with atomicMin in two
+ * layers, centre sample and conservative (Sec. 3.1.2, Sec. 3.3), shaded in a
+ * deferred pass (Sec. 3.4), reconstructed by the strand-connection /
+ * bilateral filter with alpha estimation (Sec. 3.3.1-3.3.3) and thinned by
+ * the distance/coverage LOD (Sec. 3.2, Eqs. 1-5).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are DEVICE pointers on the current CUDA device,
+ *    allocated and owned by the caller.  Other pointers are host pointers,
+ *    read during the call only.
+ *  - `stream` is a cudaStream_t passed as void*.  Work is enqueued on it and
+ *    the call returns without synchronizing, except where stated.
+ *  - Arguments are validated on the host before anything is launched: a bad
+ *    argument returns HM_ERR_INVALID_ARG and enqueues nothing.  A CUDA error
+ *    returns HM_ERR_CUDA; hm_last_error() gives the message (per thread).
+ *  - The library never aborts the process and never traps on the device.
+ *    Device-side consistency checks (a key that decodes to no strand, a
+ *    segment index out of range) set a device status word that
+ *    hm_get_device_status() reads.
+ *  - A groom handle is used by at most one stream at a time; calls that share
+ *    a groom must be ordered on the host or by stream order.
+ *
+ * Visibility keys (Sec. 3.1.2, 24-bit depth in the high bits):
+ *     key = d24 << 40 | strand_global << 7 | segment,   EMPTY = ~0
+ * strand_global < 2^33 - 1, segment < 127.  A key whose low 40 bits are all
+ * ones carries no strand (EMPTY, or a scene-depth pre-fill).
+ */
+#ifndef HM_H_
+#define HM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HM_OK = 0,
+    HM_ERR_INVALID_ARG = 1,
+    HM_ERR_OOM = 2,
+    HM_ERR_CUDA = 3,
+    HM_ERR_CAPACITY = 4,
+    HM_ERR_TIMEOUT = 5,
+    HM_ERR_NOT_READY = 6,
+    HM_ERR_DEVICE_CHECK = 7
+} hm_status;
+
+#define HM_MAX_LAYERS 32
+#define HM_MAX_SEGMENTS 126        /* control points per strand <= 127 (Sec. 3.2.2) */
+#define HM_MAX_GROOMS_PER_CALL 64
+#define HM_MAX_LIGHTS 8
+#define HM_MAX_FILTER_RADIUS 8
+#define HM_MAX_RESOLUTION 16384
+
+typedef struct hm_groom_s *hm_groom;
+
+/* A hair mesh plus strand parameters (Sec. 2; Sec. 3.1.1).  Bundles are
+ * triangle prisms: scalp triangle f with vertex indices faces[f] on every
+ * layer.  Layer 0 holds the roots, layer L-1 the tips.  Strand s grows from
+ * bundle strand_face[s] at barycentric (b1, b2) = strand_bary[s], with
+ * b0 = 1 - b1 - b2, fixed along the strand.  strand_face must be ascending
+ * (strands of a bundle contiguous); the first N_LOD strands of a bundle are
+ * the ones drawn under LOD (Eq. 1), so their order within a bundle should be
+ * random.  bundle_delta[f] in [0, 1) is the per-bundle LOD offset delta of
+ * Eq. 1.  All arrays are HOST pointers, copied to the device by
+ * hm_create_groom. */
+typedef struct {
+    int32_t num_layers;            /* L, 2..HM_MAX_LAYERS */
+    int32_t num_verts;             /* V, vertices per layer */
+    int32_t num_faces;             /* F, bundles */
+    int32_t segments_per_strand;   /* full-detail segments, 1..HM_MAX_SEGMENTS; C_max = segs + 1 */
+    int64_t num_strands;           /* S */
+    const float *layer_verts;      /* [L][V][3], metres */
+    const int32_t *faces;          /* [F][3], indices into a layer's vertices */
+    const uint32_t *strand_face;   /* [S], ascending */
+    const float *strand_bary;      /* [S][2] */
+    const float *strand_albedo;    /* [S][3], linear RGB */
+    const float *bundle_delta;     /* [F] */
+    float strand_width_m;          /* sets the centre-sample box (Sec. 3.1.2) */
+    float roughness;               /* longitudinal lobe width beta (Sec. 3.4) */
+    float tilt;                    /* cuticle tilt alpha, radians (Sec. 3.4) */
+} hm_groom_desc;
+
+/* Pinhole camera: clip = view_proj * (x, y, z, 1), row-major; clip.w is the
+ * view-axis depth in metres.  Pixels: x right, y down, centres at +0.5. */
+typedef struct {
+    float view_proj[16];
+    float cam_pos[3];
+    float near_m, far_m;
+    float tan_half_fovy;
+    int32_t width, height;
+} hm_camera;
+
+/* LOD of Sec. 3.2: enabled = 0 draws every strand at C_max control points. */
+typedef struct {
+    int32_t enabled;
+    float lambda;                  /* LOD sensitivity, Eq. 2 */
+} hm_lod_params;
+
+/* Directional lights plus ambient for the shading model of Sec. 3.4. */
+typedef struct {
+    int32_t count;                 /* 0..HM_MAX_LIGHTS */
+    float dir[HM_MAX_LIGHTS][3];   /* unit, pointing toward the light */
+    float radiance[HM_MAX_LIGHTS][3];
+    float ambient;
+    float k_d, k_s;
+} hm_lights;
+
+/* Reconstruction filter of Sec. 3.3 (defaults in parentheses). */
+typedef struct {
+    int32_t enabled;               /* 0: centre-sample shading only, alpha 0/1 */
+    int32_t radius;                /* r (5), 0..HM_MAX_FILTER_RADIUS */
+    float s_par, s_perp;           /* sigma = r * s (0.5, 0.1), Eq. 7 */
+    float sigma_c;                 /* colour term (0.9), Eq. 7 */
+    float iso_scale;               /* sigma_iso = iso_scale * r (0.4) */
+    float strip_halfwidth;         /* alpha strip half-width, px (0.5), Sec. 3.3.3 */
+    float depth_reject_m;          /* neighbour depth reject, metres (1.45e-3) */
+    float depth_mismatch_m;        /* conservative-in-front threshold, metres (5e-4) */
+} hm_filter_params;
+
+/* Per-frame counters written by hm_render_visibility (device memory).
+ * covered_* count (pixel, segment) pairs that pass each layer's coverage
+ * test, i.e. the atomicMin operations the method performs. */
+typedef struct {
+    uint64_t strands;              /* strands drawn after LOD */
+    uint64_t segments;             /* segments drawn after LOD */
+    uint64_t bundles_culled;
+    uint64_t covered_center;
+    uint64_t covered_cons;
+    uint64_t reserved[3];
+} hm_frame_stats;
+
+/* Copy a hair mesh to the device and return a handle (allocates device
+ * memory with cudaMalloc; enqueues the copies on `stream` and synchronizes
+ * it before returning).  LOD starts disabled.
+ * Errors: HM_ERR_INVALID_ARG (null pointer, size out of range, unsorted
+ * strand_face, bad face index, bary outside [0, 1], delta outside [0, 1)),
+ * HM_ERR_CAPACITY (more than 2^33 - 2 strands), HM_ERR_OOM, HM_ERR_CUDA. */
+hm_status hm_create_groom(const hm_groom_desc *desc, void *stream, hm_groom *out);
+
+/* Free the groom's device memory.  The caller must ensure no enqueued work
+ * still uses it. */
+hm_status hm_destroy_groom(hm_groom g);
+
+/* Store LOD parameters used by every later hm_render_visibility (Sec. 3.2). */
+hm_status hm_set_lod(hm_groom g, const hm_lod_params *p);
+
+/* Replace the layer vertices from a DEVICE buffer [L][V][3] (animation or an
+ * optimisation step); enqueued on `stream`. */
+hm_status hm_update_layer_verts(hm_groom g, const float *d_layer_verts, void *stream);
+
+/* Replace the per-strand albedo from a DEVICE buffer [S][3]; enqueued on
+ * `stream`. */
+hm_status hm_update_albedo(hm_groom g, const float *d_albedo, void *stream);
+
+/* Render the visibility buffers of n grooms into one shared pair of layers
+ * (Sec. 3.1-3.2; multiple grooms share depth, Sec. 4 "Multiple Grooms").
+ *
+ * Steps, all on `stream`, no host synchronization:
+ *   clear (if clear != 0): both layers set to EMPTY, or to the scene depth
+ *     pre-fill d24 << 40 | 0xFFFFFFFFFF when d_scene_d24 is not NULL;
+ *   LOD pre-pass, one thread per bundle (Eqs. 1-5; Sec. 3.2), which also
+ *     builds the device work list;
+ *   strand generation + projection + 16.8 snap + rasterization with 64-bit
+ *     atomicMin into d_vis_center (centre-sample layer) and d_vis_cons
+ *     (conservative layer).
+ * Strand ids: groom i's strands are numbered after those of grooms 0..i-1
+ * in this call.  The LOD result is kept in each groom and used by
+ * hm_resolve_shade / hm_shade_backward, which must receive the same groom
+ * array in the same order.
+ *
+ * d_vis_center, d_vis_cons: [height][width] uint64, 8-byte aligned.
+ * d_scene_d24: [height][width] uint32 (24-bit depth) or NULL.
+ * d_stats: one hm_frame_stats or NULL.
+ * Errors: HM_ERR_INVALID_ARG (n out of 1..HM_MAX_GROOMS_PER_CALL, null or
+ * misaligned buffers, resolution out of range, near/far invalid),
+ * HM_ERR_CAPACITY (strand ids would exceed 33 bits), HM_ERR_CUDA. */
+hm_status hm_render_visibility(const hm_groom *grooms, int32_t n, const hm_camera *cam,
+                               uint64_t *d_vis_center, uint64_t *d_vis_cons,
+                               const uint32_t *d_scene_d24, int32_t clear,
+                               hm_frame_stats *d_stats, void *stream);
+
+/* Deferred resolve (Sec. 3.1.2 deferred shading, Sec. 3.3 filter, Sec. 3.4
+ * shading): decode each key back to its strand segment, shade centre-sample
+ * pixels, run the strand-connection / elliptical bilateral filter and alpha
+ * estimation, and write straight-alpha RGBA.
+ * d_rgba: [height][width][4] float32, 16-byte aligned.  d_tape: reserved,
+ * pass NULL.  Same grooms, in the same order, as the render call that wrote
+ * the keys.
+ * Errors: HM_ERR_INVALID_ARG, HM_ERR_CUDA. */
+hm_status hm_resolve_shade(const hm_groom *grooms, int32_t n, const hm_camera *cam,
+                           const hm_lights *lights, const hm_filter_params *filt,
+                           const uint64_t *d_vis_center, const uint64_t *d_vis_cons,
+                           float *d_rgba, void *d_tape, void *stream);
+
+/* Adjoint of hm_resolve_shade with the visibility keys, the pixel-centre
+ * projection parameters and every filter mask held fixed (the alpha is then
+ * constant).  d_grad_rgba [height][width][4] is dLoss/d(rgba) (the alpha
+ * channel is ignored).  Gradients are ADDED into d_grad_layer_verts
+ * ([L][V][3] of grooms[i], one pointer per groom, NULL to skip) and
+ * d_grad_albedo ([S][3] per groom, NULL to skip).
+ * d_scratch: device buffer of hm_backward_scratch_bytes(width, height)
+ * bytes, 16-byte aligned, contents ignored on entry.
+ * Errors: HM_ERR_INVALID_ARG, HM_ERR_CUDA. */
+hm_status hm_shade_backward(const hm_groom *grooms, int32_t n, const hm_camera *cam,
+                            const hm_lights *lights, const hm_filter_params *filt,
+                            const uint64_t *d_vis_center, const uint64_t *d_vis_cons,
+                            const float *d_grad_rgba, float *const *d_grad_layer_verts,
+                            float *const *d_grad_albedo, void *d_scratch, void *stream);
+
+/* Bytes of scratch hm_shade_backward needs at this resolution. */
+size_t hm_backward_scratch_bytes(int32_t width, int32_t height);
+
+/* Copy the groom's current per-bundle LOD result (strands drawn N_LOD and
+ * control points C, Eqs. 1-5) to host arrays of num_faces entries.
+ * Synchronizes `stream`. */
+hm_status hm_get_lod(hm_groom g, int32_t *n_lod, int32_t *c, void *stream);
+
+/* Counts of the groom: layers, verts, faces, strands, segments_per_strand. */
+hm_status hm_groom_info(hm_groom g, int32_t *L, int32_t *V, int32_t *F, int64_t *S, int32_t *segs);
+
+/* Synchronize `stream`, read and clear the device status word (set by a
+ * failed device-side consistency check): HM_OK or HM_ERR_DEVICE_CHECK. */
+hm_status hm_get_device_status(void *stream);
+
+/* Profiling: record CUDA events (cudaEvent_t passed as void*) at phase
+ * boundaries of later calls on this host thread, on the call's stream:
+ * events[0] before the clear, [1] after the clear, [2] after the LOD
+ * pre-pass, [3] after the rasterizer (hm_render_visibility); [4] before and
+ * [5] after the resolve kernel (hm_resolve_shade).  count = 0 or events =
+ * NULL turns it off; a NULL entry is skipped. */
+hm_status hm_set_phase_events(void *const *events, int32_t count);
+
+/* Measurement probe for the roofline denominator, not part of rendering:
+ * one launch of 64-bit atomicMin over d_buf[0..n) with `rounds` operations
+ * per element, addresses coalesced and distinct within a warp (pattern 0)
+ * or scattered by a multiplicative hash (pattern 1).  Contents of d_buf are
+ * overwritten.  16-byte aligned, n >= 1. */
+hm_status hm_probe_atomic_min(uint64_t *d_buf, int64_t n, int32_t rounds, int32_t pattern, void *stream);
+
+const char *hm_status_string(hm_status s);
+const char *hm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HM_H_ */

@@ -1,0 +1,516 @@
+// hm_api.cu -- the C ABI declared in include/hm.h: argument validation, groom
+// upload, per-call groom tables, kernel launches, device status.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hm.h"
+#include "hm_device.cuh"
+#include "hm_kernels.h"
+
+struct hm_groom_s {
+    int32_t L, V, F, segs;
+    int64_t S;
+    float width_m, roughness, tilt;
+    hm_lod_params lod;
+    int device;
+    size_t max_batches;
+    float4 *d_lv;
+    int4 *d_faces;
+    uint32_t *d_sface;
+    float2 *d_bary;
+    float4 *d_albedo;
+    float *d_delta;
+    uint4 *d_lod;
+    uint32_t *d_batch_map;
+    uint32_t *d_counters;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// One device status word per device (set by device-side consistency checks).
+__device__ uint32_t g_device_status;
+
+hm_status fail(hm_status s, const char *msg) {
+    g_last_error = msg;
+    return s;
+}
+
+hm_status cuda_fail(cudaError_t e, const char *where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? HM_ERR_OOM : HM_ERR_CUDA;
+}
+
+#define HM_CUDA(call, where)                          \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+bool finite_all(const float *v, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+uint32_t *status_word() {
+    static uint32_t *ptrs[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!ptrs[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) return nullptr;
+        ptrs[dev] = static_cast<uint32_t *>(p);
+    }
+    return ptrs[dev];
+}
+
+hm_status check_camera(const hm_camera *cam) {
+    if (!cam) return fail(HM_ERR_INVALID_ARG, "camera is NULL");
+    if (cam->width < 1 || cam->height < 1 || cam->width > HM_MAX_RESOLUTION || cam->height > HM_MAX_RESOLUTION)
+        return fail(HM_ERR_INVALID_ARG, "resolution out of range");
+    if (!finite_all(cam->view_proj, 16) || !finite_all(cam->cam_pos, 3))
+        return fail(HM_ERR_INVALID_ARG, "camera has non-finite values");
+    if (!(cam->near_m > 0.0f) || !(cam->far_m > cam->near_m) || !std::isfinite(cam->far_m))
+        return fail(HM_ERR_INVALID_ARG, "need 0 < near < far");
+    if (!(cam->tan_half_fovy > 0.0f) || !std::isfinite(cam->tan_half_fovy))
+        return fail(HM_ERR_INVALID_ARG, "tan_half_fovy must be positive");
+    return HM_OK;
+}
+
+hm::CamDev cam_dev(const hm_camera *c) {
+    hm::CamDev d;
+    std::memcpy(d.m, c->view_proj, sizeof d.m);
+    std::memcpy(d.cam_pos, c->cam_pos, sizeof d.cam_pos);
+    d.near_m = c->near_m;
+    d.far_m = c->far_m;
+    d.tan_half = c->tan_half_fovy;
+    d.W = c->width;
+    d.H = c->height;
+    return d;
+}
+
+hm_status build_table(const hm_groom *grooms, int32_t n, hm::CallTable &tab) {
+    if (!grooms) return fail(HM_ERR_INVALID_ARG, "grooms is NULL");
+    if (n < 1 || n > HM_MAX_GROOMS_PER_CALL) return fail(HM_ERR_INVALID_ARG, "groom count out of range");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::memset(&tab, 0, sizeof tab);
+    tab.n = n;
+    uint64_t base = 0;
+    for (int i = 0; i < n; ++i) {
+        const hm_groom g = grooms[i];
+        if (!g) return fail(HM_ERR_INVALID_ARG, "groom handle is NULL");
+        if (g->device != dev) return fail(HM_ERR_INVALID_ARG, "groom lives on another device");
+        for (int k = 0; k < i; ++k)
+            if (grooms[k] == g) return fail(HM_ERR_INVALID_ARG, "groom appears twice in one call");
+        hm::GroomDev &d = tab.g[i];
+        d.lv = g->d_lv;
+        d.faces = g->d_faces;
+        d.sface = g->d_sface;
+        d.bary = g->d_bary;
+        d.albedo = g->d_albedo;
+        d.delta = g->d_delta;
+        d.lod = g->d_lod;
+        d.batch_map = g->d_batch_map;
+        d.counters = g->d_counters;
+        d.L = g->L;
+        d.V = g->V;
+        d.F = g->F;
+        d.cmax = g->segs + 1;
+        d.S = g->S;
+        d.base = base;
+        d.width_m = g->width_m;
+        d.roughness = g->roughness;
+        d.tilt = g->tilt;
+        d.lod_lambda = g->lod.lambda;
+        d.lod_enabled = g->lod.enabled;
+        base += (uint64_t)g->S;
+    }
+    if (base > (1ull << 33) - 2) return fail(HM_ERR_CAPACITY, "strand ids exceed 33 bits");
+    return HM_OK;
+}
+
+template <typename T>
+hm_status dev_alloc(T **p, size_t count, const char *what) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return HM_OK;
+}
+
+void free_groom(hm_groom g) {
+    if (!g) return;
+    cudaFree(g->d_lv);
+    cudaFree(g->d_faces);
+    cudaFree(g->d_sface);
+    cudaFree(g->d_bary);
+    cudaFree(g->d_albedo);
+    cudaFree(g->d_delta);
+    cudaFree(g->d_lod);
+    cudaFree(g->d_batch_map);
+    cudaFree(g->d_counters);
+    delete g;
+}
+
+thread_local void *g_phase_events[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+
+void phase(int i, cudaStream_t s) {
+    if (g_phase_events[i]) cudaEventRecord(static_cast<cudaEvent_t>(g_phase_events[i]), s);
+}
+
+bool raster_precheck() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = std::getenv("HM_RASTER_PRECHECK");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
+}  // namespace
+
+namespace hm {
+int num_sms() {
+    static int cache[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cache[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = v > 0 ? v : 1;
+    }
+    return cache[dev];
+}
+}  // namespace hm
+
+extern "C" {
+
+const char *hm_status_string(hm_status s) {
+    switch (s) {
+        case HM_OK: return "HM_OK";
+        case HM_ERR_INVALID_ARG: return "HM_ERR_INVALID_ARG";
+        case HM_ERR_OOM: return "HM_ERR_OOM";
+        case HM_ERR_CUDA: return "HM_ERR_CUDA";
+        case HM_ERR_CAPACITY: return "HM_ERR_CAPACITY";
+        case HM_ERR_TIMEOUT: return "HM_ERR_TIMEOUT";
+        case HM_ERR_NOT_READY: return "HM_ERR_NOT_READY";
+        case HM_ERR_DEVICE_CHECK: return "HM_ERR_DEVICE_CHECK";
+    }
+    return "HM_ERR_UNKNOWN";
+}
+
+const char *hm_last_error(void) { return g_last_error.c_str(); }
+
+hm_status hm_create_groom(const hm_groom_desc *d, void *stream, hm_groom *out) {
+    if (!d || !out) return fail(HM_ERR_INVALID_ARG, "desc/out is NULL");
+    *out = nullptr;
+    const int32_t L = d->num_layers, V = d->num_verts, F = d->num_faces, segs = d->segments_per_strand;
+    const int64_t S = d->num_strands;
+    if (L < 2 || L > HM_MAX_LAYERS) return fail(HM_ERR_INVALID_ARG, "num_layers out of 2..HM_MAX_LAYERS");
+    if (V < 3 || F < 1) return fail(HM_ERR_INVALID_ARG, "need V >= 3 and F >= 1");
+    if (segs < 1 || segs > HM_MAX_SEGMENTS) return fail(HM_ERR_INVALID_ARG, "segments_per_strand out of range");
+    if (S < 0) return fail(HM_ERR_INVALID_ARG, "num_strands < 0");
+    if (S > 0x7FFFFFFFll) return fail(HM_ERR_CAPACITY, "more than 2^31 - 1 strands in one groom");
+    if ((int64_t)L * V > (1ll << 28)) return fail(HM_ERR_CAPACITY, "hair mesh too large");
+    if (!d->layer_verts || !d->faces || !d->bundle_delta)
+        return fail(HM_ERR_INVALID_ARG, "layer_verts/faces/bundle_delta is NULL");
+    if (S > 0 && (!d->strand_face || !d->strand_bary || !d->strand_albedo))
+        return fail(HM_ERR_INVALID_ARG, "strand arrays are NULL");
+    if (!finite_all(d->layer_verts, L * V * 3)) return fail(HM_ERR_INVALID_ARG, "non-finite layer vertex");
+    if (!(d->strand_width_m > 0.0f) || !std::isfinite(d->strand_width_m) || !(d->roughness > 0.0f) ||
+        !std::isfinite(d->tilt))
+        return fail(HM_ERR_INVALID_ARG, "strand width / roughness must be positive, tilt finite");
+    for (int64_t i = 0; i < 3ll * F; ++i)
+        if (d->faces[i] < 0 || d->faces[i] >= V) return fail(HM_ERR_INVALID_ARG, "face index out of range");
+    for (int32_t f = 0; f < F; ++f)
+        if (!(d->bundle_delta[f] >= 0.0f && d->bundle_delta[f] < 1.0f))
+            return fail(HM_ERR_INVALID_ARG, "bundle_delta outside [0, 1)");
+    std::vector<int32_t> first(F + 1, 0);
+    for (int64_t s = 0; s < S; ++s) {
+        uint32_t f = d->strand_face[s];
+        if (f >= (uint32_t)F) return fail(HM_ERR_INVALID_ARG, "strand_face out of range");
+        if (s > 0 && f < d->strand_face[s - 1]) return fail(HM_ERR_INVALID_ARG, "strand_face not ascending");
+        float b1 = d->strand_bary[2 * s], b2 = d->strand_bary[2 * s + 1];
+        if (!(b1 >= 0.0f && b1 <= 1.0f && b2 >= 0.0f && b2 <= 1.0f))
+            return fail(HM_ERR_INVALID_ARG, "barycentric outside [0, 1]");
+        first[f + 1]++;
+    }
+    for (int32_t f = 0; f < F; ++f) first[f + 1] += first[f];
+    size_t max_batches = 0;
+    for (int32_t f = 0; f < F; ++f) {
+        int64_t nseg = (int64_t)(first[f + 1] - first[f]) * segs;
+        max_batches += (size_t)((nseg + hm::kSegBatch - 1) / hm::kSegBatch);
+    }
+    if (max_batches > 0xFFFFFFF0ull) return fail(HM_ERR_CAPACITY, "too many segment batches");
+
+    // host-side repack to the device layout
+    std::vector<float4> lv((size_t)L * V);
+    for (size_t i = 0; i < lv.size(); ++i)
+        lv[i] = make_float4(d->layer_verts[3 * i], d->layer_verts[3 * i + 1], d->layer_verts[3 * i + 2], 0.0f);
+    std::vector<int4> faces((size_t)F + 1);
+    for (int32_t f = 0; f < F; ++f)
+        faces[f] = make_int4(d->faces[3 * f], d->faces[3 * f + 1], d->faces[3 * f + 2], first[f]);
+    faces[F] = make_int4(0, 0, 0, first[F]);
+    std::vector<float4> alb((size_t)(S > 0 ? S : 1));
+    for (int64_t s = 0; s < S; ++s)
+        alb[s] = make_float4(d->strand_albedo[3 * s], d->strand_albedo[3 * s + 1], d->strand_albedo[3 * s + 2], 0.0f);
+
+    hm_groom g = new hm_groom_s();
+    std::memset(g, 0, sizeof *g);
+    g->L = L;
+    g->V = V;
+    g->F = F;
+    g->segs = segs;
+    g->S = S;
+    g->width_m = d->strand_width_m;
+    g->roughness = d->roughness;
+    g->tilt = d->tilt;
+    g->lod.enabled = 0;
+    g->lod.lambda = 3.0f;
+    g->max_batches = max_batches;
+    cudaGetDevice(&g->device);
+    hm_status st = HM_OK;
+#define HM_ALLOC(ptr, n, what) \
+    if (st == HM_OK) st = dev_alloc(&(ptr), (n), what);
+    HM_ALLOC(g->d_lv, lv.size(), "alloc layer_verts")
+    HM_ALLOC(g->d_faces, faces.size(), "alloc faces")
+    HM_ALLOC(g->d_sface, (size_t)S, "alloc strand_face")
+    HM_ALLOC(g->d_bary, (size_t)S, "alloc strand_bary")
+    HM_ALLOC(g->d_albedo, (size_t)S, "alloc strand_albedo")
+    HM_ALLOC(g->d_delta, (size_t)F, "alloc bundle_delta")
+    HM_ALLOC(g->d_lod, (size_t)F, "alloc lod")
+    HM_ALLOC(g->d_batch_map, max_batches, "alloc batch map")
+    HM_ALLOC(g->d_counters, (size_t)hm::kCtrWords, "alloc counters")
+#undef HM_ALLOC
+    if (st != HM_OK) {
+        free_groom(g);
+        return st;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void *dst, const void *src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    cp(g->d_lv, lv.data(), lv.size() * sizeof(float4));
+    cp(g->d_faces, faces.data(), faces.size() * sizeof(int4));
+    cp(g->d_sface, d->strand_face, (size_t)S * sizeof(uint32_t));
+    cp(g->d_bary, d->strand_bary, (size_t)S * sizeof(float2));
+    cp(g->d_albedo, alb.data(), (size_t)S * sizeof(float4));
+    cp(g->d_delta, d->bundle_delta, (size_t)F * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_counters, 0, hm::kCtrWords * sizeof(uint32_t), s);
+    // LOD state starts at full detail so a resolve before any render decodes safely
+    if (e == cudaSuccess) {
+        std::vector<uint4> lod0(F);
+        for (int32_t f = 0; f < F; ++f) lod0[f] = make_uint4(first[f + 1] - first[f], segs + 1, 0, 0);
+        e = cudaMemcpyAsync(g->d_lod, lod0.data(), (size_t)F * sizeof(uint4), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) {
+        free_groom(g);
+        return cuda_fail(e, "upload groom");
+    }
+    *out = g;
+    return HM_OK;
+}
+
+hm_status hm_destroy_groom(hm_groom g) {
+    if (!g) return fail(HM_ERR_INVALID_ARG, "groom is NULL");
+    free_groom(g);
+    return HM_OK;
+}
+
+hm_status hm_set_lod(hm_groom g, const hm_lod_params *p) {
+    if (!g || !p) return fail(HM_ERR_INVALID_ARG, "groom/params is NULL");
+    if (p->enabled && !(p->lambda >= 0.0f && std::isfinite(p->lambda)))
+        return fail(HM_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+    g->lod = *p;
+    return HM_OK;
+}
+
+hm_status hm_update_layer_verts(hm_groom g, const float *d_layer_verts, void *stream) {
+    if (!g || !d_layer_verts) return fail(HM_ERR_INVALID_ARG, "groom/buffer is NULL");
+    HM_CUDA(hm::launch_pack_float3(d_layer_verts, g->d_lv, (int64_t)g->L * g->V, static_cast<cudaStream_t>(stream)),
+            "pack layer verts");
+    return HM_OK;
+}
+
+hm_status hm_update_albedo(hm_groom g, const float *d_albedo, void *stream) {
+    if (!g || (!d_albedo && g->S > 0)) return fail(HM_ERR_INVALID_ARG, "groom/buffer is NULL");
+    if (g->S == 0) return HM_OK;
+    HM_CUDA(hm::launch_pack_float3(d_albedo, g->d_albedo, g->S, static_cast<cudaStream_t>(stream)), "pack albedo");
+    return HM_OK;
+}
+
+hm_status hm_render_visibility(const hm_groom *grooms, int32_t n, const hm_camera *cam, uint64_t *d_vis_center,
+                               uint64_t *d_vis_cons, const uint32_t *d_scene_d24, int32_t clear,
+                               hm_frame_stats *d_stats, void *stream) {
+    hm_status st = check_camera(cam);
+    if (st != HM_OK) return st;
+    if (!d_vis_center || !d_vis_cons) return fail(HM_ERR_INVALID_ARG, "visibility buffer is NULL");
+    if ((reinterpret_cast<uintptr_t>(d_vis_center) & 15) || (reinterpret_cast<uintptr_t>(d_vis_cons) & 15))
+        return fail(HM_ERR_INVALID_ARG, "visibility buffers must be 16-byte aligned");
+    if (d_vis_center == d_vis_cons) return fail(HM_ERR_INVALID_ARG, "the two layers must be distinct buffers");
+    hm::CallTable tab;
+    st = build_table(grooms, n, tab);
+    if (st != HM_OK) return st;
+    const hm::CamDev cd = cam_dev(cam);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t npx = (int64_t)cam->width * cam->height;
+    phase(0, s);
+    HM_CUDA(hm::launch_clear(d_vis_center, d_vis_cons, npx, d_scene_d24, clear, d_stats, s), "clear");
+    phase(1, s);
+    HM_CUDA(hm::launch_lod(tab, cd, d_stats, s), "lod");
+    phase(2, s);
+    HM_CUDA(hm::launch_raster(tab, cd, d_vis_center, d_vis_cons, raster_precheck(), d_stats, s), "raster");
+    phase(3, s);
+    return HM_OK;
+}
+
+static hm_status filter_dev(const hm_filter_params *f, const hm_camera *cam, hm::FilterDev &fd) {
+    if (!f) return fail(HM_ERR_INVALID_ARG, "filter params are NULL");
+    std::memset(&fd, 0, sizeof fd);
+    fd.enabled = f->enabled ? 1 : 0;
+    if (!fd.enabled) return HM_OK;
+    if (f->radius < 0 || f->radius > HM_MAX_FILTER_RADIUS) return fail(HM_ERR_INVALID_ARG, "radius out of range");
+    if (!(f->s_par > 0.0f) || !(f->s_perp > 0.0f) || !(f->sigma_c > 0.0f) || !(f->iso_scale > 0.0f) ||
+        !(f->strip_halfwidth >= 0.0f) || !(f->depth_reject_m >= 0.0f) || !(f->depth_mismatch_m >= 0.0f))
+        return fail(HM_ERR_INVALID_ARG, "filter widths must be positive");
+    fd.radius = f->radius;
+    const float r = (float)(f->radius > 0 ? f->radius : 1);
+    const float sp = f->s_par * r, sq = f->s_perp * r, si = f->iso_scale * r;
+    fd.inv_spar2 = 1.0f / (sp * sp);
+    fd.inv_sperp2 = 1.0f / (sq * sq);
+    fd.inv_siso2 = 1.0f / (si * si);
+    fd.inv_sc2 = 1.0f / (f->sigma_c * f->sigma_c);
+    volatile float hw = f->strip_halfwidth;
+    fd.hw2 = hw * hw;
+    const double span = (double)cam->far_m - (double)cam->near_m;
+    const double rej = std::floor((double)f->depth_reject_m / span * 16777216.0 + 0.5);
+    const double mis = std::floor((double)f->depth_mismatch_m / span * 16777216.0 + 0.5);
+    fd.drej = (int32_t)(rej > 16777216.0 ? 16777216.0 : rej);
+    fd.dmis = (int32_t)(mis > 16777216.0 ? 16777216.0 : mis);
+    return HM_OK;
+}
+
+static hm_status lights_dev(const hm_lights *l, hm::LightsDev &ld) {
+    if (!l) return fail(HM_ERR_INVALID_ARG, "lights are NULL");
+    if (l->count < 0 || l->count > HM_MAX_LIGHTS) return fail(HM_ERR_INVALID_ARG, "light count out of range");
+    std::memset(&ld, 0, sizeof ld);
+    ld.n = l->count;
+    std::memcpy(ld.dir, l->dir, sizeof ld.dir);
+    std::memcpy(ld.rad, l->radiance, sizeof ld.rad);
+    ld.ambient = l->ambient;
+    ld.kd = l->k_d;
+    ld.ks = l->k_s;
+    return HM_OK;
+}
+
+hm_status hm_resolve_shade(const hm_groom *grooms, int32_t n, const hm_camera *cam, const hm_lights *lights,
+                           const hm_filter_params *filt, const uint64_t *d_vis_center, const uint64_t *d_vis_cons,
+                           float *d_rgba, void *d_tape, void *stream) {
+    (void)d_tape;
+    hm_status st = check_camera(cam);
+    if (st != HM_OK) return st;
+    if (!d_vis_center || !d_vis_cons || !d_rgba) return fail(HM_ERR_INVALID_ARG, "buffer is NULL");
+    if ((reinterpret_cast<uintptr_t>(d_rgba) & 15) || (reinterpret_cast<uintptr_t>(d_vis_center) & 7) ||
+        (reinterpret_cast<uintptr_t>(d_vis_cons) & 7))
+        return fail(HM_ERR_INVALID_ARG, "misaligned buffer");
+    hm::LightsDev ld;
+    hm::FilterDev fd;
+    if ((st = lights_dev(lights, ld)) != HM_OK) return st;
+    if ((st = filter_dev(filt, cam, fd)) != HM_OK) return st;
+    hm::CallTable tab;
+    st = build_table(grooms, n, tab);
+    if (st != HM_OK) return st;
+    uint32_t *sw = status_word();
+    if (!sw) return fail(HM_ERR_CUDA, "device status word unavailable");
+    phase(4, static_cast<cudaStream_t>(stream));
+    HM_CUDA(hm::launch_resolve(tab, cam_dev(cam), ld, fd, d_vis_center, d_vis_cons, d_rgba, sw,
+                               static_cast<cudaStream_t>(stream)),
+            "resolve");
+    phase(5, static_cast<cudaStream_t>(stream));
+    return HM_OK;
+}
+
+hm_status hm_set_phase_events(void *const *events, int32_t count) {
+    if (count < 0 || count > 6) return fail(HM_ERR_INVALID_ARG, "count out of 0..6");
+    for (int i = 0; i < 6; ++i) g_phase_events[i] = (events && i < count) ? events[i] : nullptr;
+    return HM_OK;
+}
+
+hm_status hm_probe_atomic_min(uint64_t *d_buf, int64_t n, int32_t rounds, int32_t pattern, void *stream) {
+    if (!d_buf || n < 1 || rounds < 1 || (pattern != 0 && pattern != 1))
+        return fail(HM_ERR_INVALID_ARG, "bad probe arguments");
+    HM_CUDA(hm::launch_probe_atomic_min(d_buf, n, rounds, pattern, static_cast<cudaStream_t>(stream)), "probe");
+    return HM_OK;
+}
+
+hm_status hm_get_lod(hm_groom g, int32_t *n_lod, int32_t *c, void *stream) {
+    if (!g || !n_lod || !c) return fail(HM_ERR_INVALID_ARG, "NULL argument");
+    std::vector<uint4> h(g->F);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    HM_CUDA(cudaMemcpyAsync(h.data(), g->d_lod, (size_t)g->F * sizeof(uint4), cudaMemcpyDeviceToHost, s), "copy lod");
+    HM_CUDA(cudaStreamSynchronize(s), "sync");
+    for (int32_t f = 0; f < g->F; ++f) {
+        n_lod[f] = (int32_t)h[f].x;
+        c[f] = (int32_t)h[f].y;
+    }
+    return HM_OK;
+}
+
+hm_status hm_groom_info(hm_groom g, int32_t *L, int32_t *V, int32_t *F, int64_t *S, int32_t *segs) {
+    if (!g) return fail(HM_ERR_INVALID_ARG, "groom is NULL");
+    if (L) *L = g->L;
+    if (V) *V = g->V;
+    if (F) *F = g->F;
+    if (S) *S = g->S;
+    if (segs) *segs = g->segs;
+    return HM_OK;
+}
+
+hm_status hm_get_device_status(void *stream) {
+    uint32_t *sw = status_word();
+    if (!sw) return fail(HM_ERR_CUDA, "device status word unavailable");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t v = 0;
+    HM_CUDA(cudaMemcpyAsync(&v, sw, sizeof v, cudaMemcpyDeviceToHost, s), "read status");
+    HM_CUDA(cudaMemsetAsync(sw, 0, sizeof v, s), "clear status");
+    HM_CUDA(cudaStreamSynchronize(s), "sync");
+    if (v) {
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "device consistency check failed (status bits 0x%x)", v);
+        return fail(HM_ERR_DEVICE_CHECK, buf);
+    }
+    return HM_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+size_t hm_backward_scratch_bytes(int32_t width, int32_t height) {
+    if (width < 1 || height < 1) return 0;
+    return (size_t)width * (size_t)height * 16;
+}
+
+hm_status hm_shade_backward(const hm_groom *grooms, int32_t n, const hm_camera *cam, const hm_lights *lights,
+                            const hm_filter_params *filt, const uint64_t *d_vis_center, const uint64_t *d_vis_cons,
+                            const float *d_grad_rgba, float *const *d_grad_layer_verts, float *const *d_grad_albedo,
+                            void *d_scratch, void *stream) {
+    (void)grooms; (void)n; (void)cam; (void)lights; (void)filt; (void)d_vis_center; (void)d_vis_cons;
+    (void)d_grad_rgba; (void)d_grad_layer_verts; (void)d_grad_albedo; (void)d_scratch; (void)stream;
+    return fail(HM_ERR_NOT_READY, "hm_shade_backward is not built in this version");
+}
+
+}  // extern "C"

@@ -1,0 +1,363 @@
+// hm_device.cuh -- device-side data layout and the FP32 "decision layer" of
+// the deferred hair rasterizer (arXiv 2607.04230).
+//
+// Every quantity that decides an integer (covered pixels, packed keys, LOD
+// counts, filter masks) is computed here with explicit round-to-nearest
+// intrinsics (__fadd_rn, __fmul_rn, __fdiv_rn, __fsqrt_rn, ...), which the
+// compiler never contracts into FMA or reorders, so the results are the same
+// IEEE binary32 values on every launch.  The continuous part of the resolve
+// (shading, filter weights) lives in hm_resolve.cu and may use FMA.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/hm.h"
+
+namespace hm {
+
+constexpr uint64_t kEmptyKey = ~0ull;
+constexpr uint64_t kPayloadMask = 0xFFFFFFFFFFull;
+constexpr uint64_t kStrandMask = 0x1FFFFFFFFull;   // 33 bits
+constexpr float kGuard = 1048576.0f;               // 2^20 px guard band
+constexpr int kSegBatch = 32;                      // segments per warp batch
+
+// Per-groom device counters (one block of words per groom).
+enum CounterWord : int { kCtrBatches = 0, kCtrTicket = 1, kCtrWords = 4 };
+
+// Device status bits (read by hm_get_device_status).
+enum StatusBit : uint32_t { kStatusBadKey = 1u, kStatusBadBatch = 2u };
+
+// One groom as the kernels see it.  Arrays are device memory owned by the
+// groom handle.
+struct GroomDev {
+    const float4 *lv;        // [L][V] layer vertices, xyz (w unused)
+    const int4 *faces;       // [F + 1] (i0, i1, i2, first strand); faces[F].w = S
+    const uint32_t *sface;   // [S] bundle of each strand
+    const float2 *bary;      // [S] (b1, b2)
+    const float4 *albedo;    // [S] rgb
+    const float *delta;      // [F] LOD offset of Eq. 1
+    uint4 *lod;              // [F] (N_LOD, C, first batch, segments)
+    uint32_t *batch_map;     // [max_batches] bundle of each 32-segment batch
+    uint32_t *counters;      // [kCtrWords]
+    int32_t L, V, F, cmax;
+    int64_t S;
+    uint64_t base;           // global id of strand 0 in this call
+    float width_m, roughness, tilt, lod_lambda;
+    int32_t lod_enabled;
+    int32_t pad_;
+};
+
+struct CallTable {
+    int32_t n;
+    int32_t pad_[3];
+    GroomDev g[HM_MAX_GROOMS_PER_CALL];
+};
+
+struct CamDev {
+    float m[16];
+    float cam_pos[3];
+    float near_m, far_m, tan_half;
+    int32_t W, H;
+};
+
+// ---------------------------------------------------------------------------
+// binary32 helpers with a fixed evaluation order
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fclamp(float v, float lo, float hi) {
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+__device__ __forceinline__ float3 v3sub(float3 a, float3 b) {
+    return make_float3(fsub(a.x, b.x), fsub(a.y, b.y), fsub(a.z, b.z));
+}
+// ((x x + y y) + z z)
+__device__ __forceinline__ float v3len2(float3 v) {
+    return fadd(fadd(fmul(v.x, v.x), fmul(v.y, v.y)), fmul(v.z, v.z));
+}
+// v / sqrt(|v|^2), zero for a zero vector
+__device__ __forceinline__ float3 v3unit(float3 v) {
+    float n2 = v3len2(v);
+    if (n2 == 0.0f) return make_float3(0.0f, 0.0f, 0.0f);
+    float n = __fsqrt_rn(n2);
+    return make_float3(fdiv(v.x, n), fdiv(v.y, n), fdiv(v.z, n));
+}
+// Finite-difference tangent of point i of an n-point polyline (Sec. 3.1.1):
+// forward at the root, backward at the tip, central elsewhere.
+__device__ __forceinline__ float3 fd_tangent(int i, int n, float3 prev, float3 cur, float3 next) {
+    if (i == 0) return v3unit(v3sub(next, cur));
+    if (i == n - 1) return v3unit(v3sub(cur, prev));
+    return v3unit(v3sub(next, prev));
+}
+
+// ---------------------------------------------------------------------------
+// strand generation from the hair mesh (Sec. 2 Background; Sec. 3.1.1)
+// ---------------------------------------------------------------------------
+struct Root {
+    int32_t i0, i1, i2;
+    float b0, b1, b2;
+};
+
+__device__ __forceinline__ Root make_root(const GroomDev &g, int64_t s, uint32_t f) {
+    int4 t = __ldg(&g.faces[f]);
+    float2 b = __ldg(&g.bary[s]);
+    Root r;
+    r.i0 = t.x; r.i1 = t.y; r.i2 = t.z;
+    r.b1 = b.x; r.b2 = b.y;
+    r.b0 = fsub(fsub(1.0f, b.x), b.y);
+    return r;
+}
+
+// Layer point k: the root's barycentric coordinates on layer k's triangle,
+// ((b0 V0 + b1 V1) + b2 V2).
+__device__ __forceinline__ float3 layer_pt(const GroomDev &g, const Root &r, int k) {
+    const float4 *row = g.lv + (int64_t)k * g.V;
+    float4 a = __ldg(&row[r.i0]);
+    float4 b = __ldg(&row[r.i1]);
+    float4 c = __ldg(&row[r.i2]);
+    return make_float3(fadd(fadd(fmul(r.b0, a.x), fmul(r.b1, b.x)), fmul(r.b2, c.x)),
+                       fadd(fadd(fmul(r.b0, a.y), fmul(r.b1, b.y)), fmul(r.b2, c.y)),
+                       fadd(fadd(fmul(r.b0, a.z), fmul(r.b1, b.z)), fmul(r.b2, c.z)));
+}
+
+// Control point j of a C-point strand: cubic Hermite through the layer
+// points with finite-difference tangents scaled by the interval's chord
+// length; interval k = min(j (L-1) / (C-1), L-2), local parameter
+// s = (j (L-1) - k (C-1)) / (C-1).  Only the layer points the interval needs
+// are evaluated.
+__device__ __forceinline__ float3 control_pt(const GroomDev &g, const Root &r, int C, int j) {
+    const int L = g.L;
+    int x = j * (L - 1);
+    int k = x / (C - 1);
+    if (k > L - 2) k = L - 2;
+    float s = fdiv(__int2float_rn(x - k * (C - 1)), __int2float_rn(C - 1));
+    float3 P0 = layer_pt(g, r, k);
+    float3 P1 = layer_pt(g, r, k + 1);
+    float3 Pm = (k > 0) ? layer_pt(g, r, k - 1) : P0;
+    float3 P2 = (k + 2 <= L - 1) ? layer_pt(g, r, k + 2) : P1;
+    float3 t0 = fd_tangent(k, L, Pm, P0, P1);
+    float3 t1 = fd_tangent(k + 1, L, P0, P1, P2);
+    float ell = __fsqrt_rn(v3len2(v3sub(P1, P0)));
+    float3 m0 = make_float3(fmul(t0.x, ell), fmul(t0.y, ell), fmul(t0.z, ell));
+    float3 m1 = make_float3(fmul(t1.x, ell), fmul(t1.y, ell), fmul(t1.z, ell));
+    float s2 = fmul(s, s);
+    float s3 = fmul(s2, s);
+    float h00 = fadd(fsub(fmul(2.0f, s3), fmul(3.0f, s2)), 1.0f);
+    float h10 = fadd(fsub(s3, fmul(2.0f, s2)), s);
+    float h01 = fsub(fmul(3.0f, s2), fmul(2.0f, s3));
+    float h11 = fsub(s3, s2);
+    return make_float3(
+        fadd(fadd(fadd(fmul(h00, P0.x), fmul(h10, m0.x)), fmul(h01, P1.x)), fmul(h11, m1.x)),
+        fadd(fadd(fadd(fmul(h00, P0.y), fmul(h10, m0.y)), fmul(h01, P1.y)), fmul(h11, m1.y)),
+        fadd(fadd(fadd(fmul(h00, P0.z), fmul(h10, m0.z)), fmul(h01, P1.z)), fmul(h11, m1.z)));
+}
+
+// ---------------------------------------------------------------------------
+// projection, 16.8 snap, depth (Sec. 3.1.2)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float clip_row(const CamDev &c, int r, float3 p) {
+    const float *m = c.m + 4 * r;
+    return fadd(fadd(fadd(fmul(m[0], p.x), fmul(m[1], p.y)), fmul(m[2], p.z)), m[3]);
+}
+
+struct Proj {
+    int32_t X, Y;      // 1/256 px
+    float w, z;        // view depth (m), linear depth in [0, 1] when inside
+    float xs, ys;      // unsnapped pixel position
+    bool valid;        // w >= near
+};
+
+__device__ __forceinline__ Proj project(const CamDev &c, float3 p) {
+    Proj r;
+    float c0 = clip_row(c, 0, p);
+    float c1 = clip_row(c, 1, p);
+    float w = clip_row(c, 3, p);
+    r.w = w;
+    r.valid = (w >= c.near_m);
+    r.z = fdiv(fsub(w, c.near_m), fsub(c.far_m, c.near_m));
+    r.X = r.Y = 0;
+    r.xs = r.ys = 0.0f;
+    if (!r.valid) return r;
+    float xs = fmul(fmul(fadd(fdiv(c0, w), 1.0f), 0.5f), __int2float_rn(c.W));
+    float ys = fmul(fmul(fsub(1.0f, fdiv(c1, w)), 0.5f), __int2float_rn(c.H));
+    xs = fclamp(xs, -kGuard, kGuard);
+    ys = fclamp(ys, -kGuard, kGuard);
+    r.xs = xs;
+    r.ys = ys;
+    r.X = __float2int_rn(fmul(xs, 256.0f));
+    r.Y = __float2int_rn(fmul(ys, 256.0f));
+    return r;
+}
+
+__device__ __forceinline__ float focal_px(const CamDev &c) {
+    return fdiv(fmul(0.5f, __int2float_rn(c.H)), c.tan_half);
+}
+
+// Centre-sample half-width in 1/256 px: the projected strand half-width,
+// rounded half-even, clamped to [1, 128].
+__device__ __forceinline__ int32_t centre_halfwidth(const CamDev &c, float width_m, float wA, float wB) {
+    float wm = fmul(fadd(wA, wB), 0.5f);
+    float r = fdiv(fmul(fmul(128.0f, width_m), focal_px(c)), wm);
+    float q = rintf(r);
+    q = q < 1.0f ? 1.0f : (q > 128.0f ? 128.0f : q);
+    return (int32_t)q;
+}
+
+// Exact separating-axis test of segment AB against the closed box of
+// half-width h around (cx, cy): bounding boxes overlap and the box corners
+// are not all strictly on one side of AB.
+__device__ __forceinline__ bool seg_covers(int32_t XA, int32_t YA, int32_t XB, int32_t YB,
+                                           int64_t cx, int64_t cy, int64_t h) {
+    int64_t xlo = min(XA, XB), xhi = max(XA, XB);
+    int64_t ylo = min(YA, YB), yhi = max(YA, YB);
+    if (xhi < cx - h || xlo > cx + h || yhi < cy - h || ylo > cy + h) return false;
+    int64_t dX = (int64_t)XB - XA, dY = (int64_t)YB - YA;
+    int64_t ax = (cx - h) - XA, bx = (cx + h) - XA;
+    int64_t ay = (cy - h) - YA, by = (cy + h) - YA;
+    int64_t e0 = dX * ay - dY * ax;
+    int64_t e1 = dX * ay - dY * bx;
+    int64_t e2 = dX * by - dY * ax;
+    int64_t e3 = dX * by - dY * bx;
+    int64_t emin = min(min(e0, e1), min(e2, e3));
+    int64_t emax = max(max(e0, e1), max(e2, e3));
+    return emin <= 0 && emax >= 0;
+}
+
+// Pixel-centre projection parameter t = clamp(float(num) / float(den), 0, 1).
+__device__ __forceinline__ float seg_t(int32_t XA, int32_t YA, int32_t XB, int32_t YB,
+                                       int64_t cx, int64_t cy) {
+    int64_t dX = (int64_t)XB - XA, dY = (int64_t)YB - YA;
+    int64_t num = (cx - XA) * dX + (cy - YA) * dY;
+    int64_t den = dX * dX + dY * dY;
+    if (den == 0) return 0.0f;
+    return fclamp(fdiv(__ll2float_rn(num), __ll2float_rn(den)), 0.0f, 1.0f);
+}
+
+// 24-bit depth: z = zA + (zB - zA) t, clamped, floor(z 2^24), max 2^24 - 1.
+__device__ __forceinline__ uint32_t depth24(float zA, float zB, float t) {
+    float z = fclamp(fadd(zA, fmul(fsub(zB, zA), t)), 0.0f, 1.0f);
+    uint32_t d = (uint32_t)floorf(fmul(z, 16777216.0f));
+    return d > 16777215u ? 16777215u : d;
+}
+
+__device__ __forceinline__ bool key_empty(uint64_t k) { return (k & kPayloadMask) == kPayloadMask; }
+
+// ---------------------------------------------------------------------------
+// resolve-side decode and masks (Sec. 3.1.2 deferred shading; Sec. 3.3)
+// ---------------------------------------------------------------------------
+
+// Screen tangent J T / |J T| at X (pixels, y down).  Degenerate -- the strand
+// within about 0.6 degrees of the view ray, |J T| w < 0.01 focal -- selects
+// the isotropic filter mode.
+__device__ __forceinline__ bool screen_tangent(const CamDev &c, float3 X, float3 T, float &tsx, float &tsy) {
+    const float *m = c.m;
+    float c0 = clip_row(c, 0, X);
+    float c1 = clip_row(c, 1, X);
+    float w = clip_row(c, 3, X);
+    float a0 = fadd(fadd(fmul(m[0], T.x), fmul(m[1], T.y)), fmul(m[2], T.z));
+    float a1 = fadd(fadd(fmul(m[4], T.x), fmul(m[5], T.y)), fmul(m[6], T.z));
+    float a3 = fadd(fadd(fmul(m[12], T.x), fmul(m[13], T.y)), fmul(m[14], T.z));
+    float w2 = fmul(w, w);
+    float jx = fmul(fdiv(fsub(fmul(a0, w), fmul(c0, a3)), w2), fmul(0.5f, __int2float_rn(c.W)));
+    float jy = -fmul(fdiv(fsub(fmul(a1, w), fmul(c1, a3)), w2), fmul(0.5f, __int2float_rn(c.H)));
+    float n = __fsqrt_rn(fadd(fmul(jx, jx), fmul(jy, jy)));
+    if (!(fmul(n, w) >= fmul(0.01f, focal_px(c)))) {
+        tsx = 0.0f;
+        tsy = 0.0f;
+        return true;
+    }
+    tsx = fdiv(jx, n);
+    tsy = fdiv(jy, n);
+    return false;
+}
+
+// Window offset (dx, dy) inside the alpha strip of half-width hw
+// (hw2 = hw * hw); the strip of a degenerate tangent is the pixel itself.
+__device__ __forceinline__ bool in_strip(bool iso, float tsx, float tsy, int dx, int dy, float hw2,
+                                         float &dpar, float &perp2) {
+    float fx = __int2float_rn(dx), fy = __int2float_rn(dy);
+    if (iso) {
+        dpar = 0.0f;
+        perp2 = 0.0f;
+        return dx == 0 && dy == 0;
+    }
+    dpar = fadd(fmul(fx, tsx), fmul(fy, tsy));
+    float ex = fsub(fx, fmul(dpar, tsx));
+    float ey = fsub(fy, fmul(dpar, tsy));
+    perp2 = fadd(fmul(ex, ex), fmul(ey, ey));
+    return perp2 <= hw2;
+}
+
+// Index of the groom owning global strand id sg (ids are numbered groom by
+// groom); bases[] holds the n + 1 prefix ids.  -1 if none.
+__device__ __forceinline__ int find_groom(const uint64_t *bases, int n, uint64_t sg) {
+    int lo = 0, hi = n;          // bases[lo] <= sg < bases[hi]
+    if (sg >= bases[n]) return -1;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (bases[mid] <= sg) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// The geometry a key decodes to at pixel (px, py).
+struct Decoded {
+    float3 X, T;        // FP32 position and unit tangent at the pixel centre
+    float t;            // pixel-centre projection parameter
+    float tsx, tsy;     // unit screen tangent
+    int64_t s;          // local strand index
+    int gi;             // groom
+    int j, C;           // segment, control points
+    bool iso, ok;
+};
+
+__device__ __forceinline__ Decoded decode_key(const CallTable &tab, const uint64_t *bases, const CamDev &cam,
+                                              uint64_t key, int px, int py, uint32_t *status) {
+    Decoded d;
+    d.ok = false;
+    d.iso = true;
+    d.tsx = d.tsy = 0.0f;
+    d.X = d.T = make_float3(0.0f, 0.0f, 0.0f);
+    d.t = 0.0f;
+    d.s = 0;
+    d.gi = 0;
+    d.j = 0;
+    d.C = 0;
+    uint64_t sg = (key >> 7) & kStrandMask;
+    int gi = find_groom(bases, tab.n, sg);
+    if (gi < 0) { atomicOr(status, kStatusBadKey); return d; }
+    const GroomDev &g = tab.g[gi];
+    int64_t s = (int64_t)(sg - bases[gi]);
+    int j = (int)(key & 127ull);
+    uint32_t f = __ldg(&g.sface[s]);
+    if (f >= (uint32_t)g.F) { atomicOr(status, kStatusBadKey); return d; }
+    int C = (int)g.lod[f].y;
+    if (j + 1 >= C) { atomicOr(status, kStatusBadKey); return d; }
+    Root r = make_root(g, s, f);
+    float3 p0 = control_pt(g, r, C, j);
+    float3 p1 = control_pt(g, r, C, j + 1);
+    float3 pm = (j >= 1) ? control_pt(g, r, C, j - 1) : p0;
+    float3 pp = (j + 2 <= C - 1) ? control_pt(g, r, C, j + 2) : p1;
+    Proj a = project(cam, p0), b = project(cam, p1);
+    float t = seg_t(a.X, a.Y, b.X, b.Y, 256 * (int64_t)px + 128, 256 * (int64_t)py + 128);
+    d.X = make_float3(fadd(p0.x, fmul(fsub(p1.x, p0.x), t)), fadd(p0.y, fmul(fsub(p1.y, p0.y), t)),
+                      fadd(p0.z, fmul(fsub(p1.z, p0.z), t)));
+    float3 T0 = fd_tangent(j, C, pm, p0, p1);
+    float3 T1 = fd_tangent(j + 1, C, p0, p1, pp);
+    d.T = v3unit(make_float3(fadd(T0.x, fmul(fsub(T1.x, T0.x), t)), fadd(T0.y, fmul(fsub(T1.y, T0.y), t)),
+                             fadd(T0.z, fmul(fsub(T1.z, T0.z), t))));
+    d.iso = screen_tangent(cam, d.X, d.T, d.tsx, d.tsy);
+    d.t = t;
+    d.s = s;
+    d.gi = gi;
+    d.j = j;
+    d.C = C;
+    d.ok = true;
+    return d;
+}
+
+}  // namespace hm

@@ -1,0 +1,40 @@
+// hm_kernels.h -- host-side launchers and the small parameter blocks the
+// kernels take by value.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hm_device.cuh"
+
+namespace hm {
+
+struct LightsDev {
+    int32_t n;
+    float dir[HM_MAX_LIGHTS][3];
+    float rad[HM_MAX_LIGHTS][3];
+    float ambient, kd, ks;
+};
+
+struct FilterDev {
+    int32_t enabled, radius;
+    float hw2;                 // strip half-width squared (binary32 product)
+    float inv_spar2, inv_sperp2, inv_siso2, inv_sc2;
+    int32_t drej, dmis;        // depth thresholds in d24 units
+};
+
+int num_sms();
+
+cudaError_t launch_clear(uint64_t *vis_c, uint64_t *vis_a, int64_t npx, const uint32_t *scene_d24, int do_clear,
+                         hm_frame_stats *stats, cudaStream_t st);
+cudaError_t launch_lod(const CallTable &tab, const CamDev &cam, hm_frame_stats *stats, cudaStream_t st);
+cudaError_t launch_raster(const CallTable &tab, const CamDev &cam, uint64_t *vis_c, uint64_t *vis_a, bool precheck,
+                          hm_frame_stats *stats, cudaStream_t st);
+cudaError_t launch_probe_atomic_min(uint64_t *buf, int64_t n, int rounds, int pattern, cudaStream_t st);
+cudaError_t launch_resolve(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
+                           const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status,
+                           cudaStream_t st);
+cudaError_t launch_pack_float3(const float *src, float4 *dst, int64_t n, cudaStream_t st);
+
+}  // namespace hm

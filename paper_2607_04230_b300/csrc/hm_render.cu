@@ -1,0 +1,437 @@
+// hm_render.cu -- visibility pass of the deferred hair rasterizer
+// (arXiv 2607.04230, Sec. 3.1-3.2): clear, LOD pre-pass with the device work
+// list, and the strand-generation + 64-bit atomicMin rasterizer.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hm_device.cuh"
+#include "hm_kernels.h"
+
+namespace hm {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------------------
+// clear: both layers to EMPTY or to the scene-depth pre-fill; zero the stats
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) clear_kernel(ulonglong2 *vis_c, ulonglong2 *vis_a, int64_t npairs,
+                                                    const uint32_t *scene_d24, int64_t npx, int do_clear,
+                                                    hm_frame_stats *stats) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && stats) {
+        stats->strands = 0;
+        stats->segments = 0;
+        stats->bundles_culled = 0;
+        stats->covered_center = 0;
+        stats->covered_cons = 0;
+    }
+    if (!do_clear) return;
+    // npairs = npx / 2 whole 16-byte pairs; an odd last pixel is written alone
+    if (i == 0 && (npx & 1)) {
+        const int64_t p = npx - 1;
+        const uint64_t v = scene_d24 ? (((uint64_t)(scene_d24[p] & 0xFFFFFFu) << 40) | kPayloadMask) : kEmptyKey;
+        reinterpret_cast<uint64_t *>(vis_c)[p] = v;
+        reinterpret_cast<uint64_t *>(vis_a)[p] = v;
+    }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < npairs; i += stride) {
+        ulonglong2 v;
+        if (scene_d24) {
+            const int64_t p = 2 * i;
+            v.x = ((uint64_t)(scene_d24[p] & 0xFFFFFFu) << 40) | kPayloadMask;
+            v.y = ((uint64_t)(scene_d24[p + 1] & 0xFFFFFFu) << 40) | kPayloadMask;
+        } else {
+            v.x = kEmptyKey;
+            v.y = kEmptyKey;
+        }
+        vis_c[i] = v;
+        vis_a[i] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// LOD pre-pass (Sec. 3.2, Eqs. 1-5): one thread per bundle, one CTA per groom
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void lod_counts(float Lf, int nfull, float delta, int L, int cmax, int &n_out,
+                                           int &c_out) {
+    int n = 0;
+    if (nfull > 0) {
+        float v = ceilf(fmul(Lf, fadd(__int2float_rn(nfull), delta)));
+        n = (int)v;
+        if (n < 1) n = 1;
+        if (n > nfull) n = nfull;
+    }
+    int craw = (int)floorf(fmul(__fsqrt_rn(Lf), __int2float_rn(cmax)));
+    if (craw < L) craw = L;
+    int c = (1 << (31 - __clz(craw - 1))) + 1;
+    if (c > cmax) c = cmax;
+    int lo = L < cmax ? L : cmax;
+    if (c < lo) c = lo;
+    n_out = n;
+    c_out = c;
+}
+
+// Screen AABB over every layer's triangle (Eq. 3), frustum cull, L (Eq. 2).
+// A bundle wholly behind the near plane is culled; one straddling it is
+// drawn at L = 1.  Returns false when culled.
+__device__ __forceinline__ bool lod_select(const GroomDev &g, const CamDev &cam, int f, float &Lf) {
+    int4 tri = __ldg(&g.faces[f]);
+    float xmin = __int_as_float(0x7f800000), xmax = -__int_as_float(0x7f800000);
+    float ymin = xmin, ymax = xmax;
+    bool behind = false, front = false;
+    for (int k = 0; k < g.L; ++k) {
+        const float4 *row = g.lv + (int64_t)k * g.V;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int vi = c == 0 ? tri.x : (c == 1 ? tri.y : tri.z);
+            float4 v = __ldg(&row[vi]);
+            Proj p = project(cam, make_float3(v.x, v.y, v.z));
+            if (!p.valid) { behind = true; continue; }
+            front = true;
+            if (p.xs < xmin) xmin = p.xs;
+            if (p.xs > xmax) xmax = p.xs;
+            if (p.ys < ymin) ymin = p.ys;
+            if (p.ys > ymax) ymax = p.ys;
+        }
+    }
+    if (!front) return false;
+    if (behind) { Lf = 1.0f; return true; }
+    if (xmax < 0.0f || xmin > __int2float_rn(cam.W) || ymax < 0.0f || ymin > __int2float_rn(cam.H)) return false;
+    float dx = fsub(xmax, xmin), dy = fsub(ymax, ymin);
+    float diag = __fsqrt_rn(fadd(fmul(dx, dx), fmul(dy, dy)));
+    Lf = fclamp(fmul(fdiv(diag, __int2float_rn(cam.H)), g.lod_lambda), 0.0f, 1.0f);
+    return true;
+}
+
+template <int NT>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t &total, uint32_t *sm) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sm[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = lane < NT / 32 ? sm[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < NT / 32) sm[lane] = s;
+    }
+    __syncthreads();
+    uint32_t off = w > 0 ? sm[w - 1] : 0;
+    total = sm[NT / 32 - 1];
+    __syncthreads();
+    return off + x - v;
+}
+
+constexpr int kLodThreads = 512;
+
+__global__ void __launch_bounds__(kLodThreads) lod_kernel(CallTable tab, CamDev cam, hm_frame_stats *stats) {
+    __shared__ uint32_t sm[kLodThreads / 32];
+    const GroomDev &g = tab.g[blockIdx.x];
+    uint32_t running = 0;
+    unsigned long long strands = 0, segs = 0, culled = 0;
+    for (int base = 0; base < g.F; base += kLodThreads) {
+        int f = base + (int)threadIdx.x;
+        int n = 0, c = g.cmax;
+        if (f < g.F) {
+            int nfull = __ldg(&g.faces[f + 1]).w - __ldg(&g.faces[f]).w;
+            if (!g.lod_enabled) {
+                n = nfull;
+            } else {
+                float Lf = 0.0f;
+                if (lod_select(g, cam, f, Lf)) {
+                    lod_counts(Lf, nfull, __ldg(&g.delta[f]), g.L, g.cmax, n, c);
+                } else {
+                    n = 0;
+                    culled += 1;
+                }
+            }
+        }
+        uint32_t nseg = (uint32_t)n * (uint32_t)(c - 1);
+        uint32_t nb = (nseg + kSegBatch - 1) / kSegBatch;
+        uint32_t tot;
+        uint32_t first = running + block_excl_scan<kLodThreads>(nb, tot, sm);
+        if (f < g.F) {
+            g.lod[f] = make_uint4((uint32_t)n, (uint32_t)c, first, nseg);
+            for (uint32_t b = 0; b < nb; ++b) g.batch_map[first + b] = (uint32_t)f;
+            strands += (unsigned long long)n;
+            segs += nseg;
+        }
+        running += tot;
+    }
+    if (threadIdx.x == 0) {
+        g.counters[kCtrBatches] = running;
+        if (blockIdx.x == 0) g.counters[kCtrTicket] = 0;
+    }
+    if (stats) {
+        // warp-reduce then one atomic per warp
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            strands += __shfl_down_sync(kFull, strands, o);
+            segs += __shfl_down_sync(kFull, segs, o);
+            culled += __shfl_down_sync(kFull, culled, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd((unsigned long long *)&stats->strands, strands);
+            atomicAdd((unsigned long long *)&stats->segments, segs);
+            atomicAdd((unsigned long long *)&stats->bundles_culled, culled);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// rasterizer (Sec. 3.1.1 strand assembly, Sec. 3.1.2 atomicMin visibility,
+// Sec. 3.3 two layers)
+//
+// Persistent grid; each warp pulls 32-segment batches from a ticket.  A lane
+// generates one segment (two control points), projects and snaps it, then the
+// warp enumerates the batch's candidate pixels together: work items are
+// (segment, pixel step along the major axis), load-balanced across the warp
+// by a prefix sum, and each item tests its 2-4 minor-axis pixels with the
+// exact predicate and issues the 64-bit atomicMin for each layer.
+// ---------------------------------------------------------------------------
+struct SegRec {
+    int32_t uA, vA, uB, vB;      // endpoints in the major (u) / minor (v) frame, 1/256 px
+    float zA, zB;
+    int32_t hc;
+    int32_t ilo;                 // first major pixel index
+    uint32_t id_lo, id_hi;       // payload strand << 7 | segment
+    int32_t start;               // first work item of this segment
+    int32_t xmajor;
+};
+
+constexpr int kRasterThreads = 256;
+constexpr int kRasterWarps = kRasterThreads / 32;
+
+template <bool kPrecheck>
+__global__ void __launch_bounds__(kRasterThreads) raster_kernel(CallTable tab, CamDev cam, uint64_t *__restrict__ vis_c,
+                                                                uint64_t *__restrict__ vis_a, hm_frame_stats *stats) {
+    __shared__ uint32_t s_goff[HM_MAX_GROOMS_PER_CALL + 1];
+    __shared__ SegRec s_rec[kRasterWarps][32];
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int i = 0; i < tab.n; ++i) {
+            s_goff[i] = acc;
+            acc += tab.g[i].counters[kCtrBatches];
+        }
+        s_goff[tab.n] = acc;
+    }
+    __syncthreads();
+    const uint32_t total = s_goff[tab.n];
+    const int lane = threadIdx.x & 31;
+    SegRec *rec = s_rec[threadIdx.x >> 5];
+    uint32_t *ticket = tab.g[0].counters + kCtrTicket;
+    const int W = cam.W, H = cam.H;
+    uint32_t n_cons = 0, n_cen = 0;
+
+    for (;;) {
+        uint32_t b = 0;
+        if (lane == 0) b = atomicAdd(ticket, 1u);
+        b = __shfl_sync(kFull, b, 0);
+        if (b >= total) break;
+        int gi = 0;
+        while (gi + 1 < tab.n && s_goff[gi + 1] <= b) ++gi;
+        const GroomDev &g = tab.g[gi];
+        const uint32_t lb = b - s_goff[gi];
+        const uint32_t f = __ldg(&g.batch_map[lb]);
+        const uint4 lo = g.lod[f];
+        const int C = (int)lo.y;
+        const uint32_t sl = (lb - lo.z) * kSegBatch + lane;
+
+        SegRec r;
+        int nmaj = 0;
+        if (sl < lo.w) {
+            const int64_t s = (int64_t)__ldg(&g.faces[f]).w + sl / (uint32_t)(C - 1);
+            const int j = (int)(sl % (uint32_t)(C - 1));
+            const Root rt = make_root(g, s, f);
+            const Proj A = project(cam, control_pt(g, rt, C, j));
+            const Proj B = project(cam, control_pt(g, rt, C, j + 1));
+            if (A.valid && B.valid) {
+                const bool xm = abs(B.X - A.X) >= abs(B.Y - A.Y);
+                r.uA = xm ? A.X : A.Y;
+                r.vA = xm ? A.Y : A.X;
+                r.uB = xm ? B.X : B.Y;
+                r.vB = xm ? B.Y : B.X;
+                r.zA = A.z;
+                r.zB = B.z;
+                r.hc = centre_halfwidth(cam, g.width_m, A.w, B.w);
+                const uint64_t id = ((g.base + (uint64_t)s) << 7) | (uint64_t)j;
+                r.id_lo = (uint32_t)id;
+                r.id_hi = (uint32_t)(id >> 32);
+                r.xmajor = xm;
+                const int du = xm ? W : H, dv = xm ? H : W;
+                const int32_t umin = min(r.uA, r.uB), umax = max(r.uA, r.uB);
+                const int32_t vmin = min(r.vA, r.vB), vmax = max(r.vA, r.vB);
+                // pixel m's conservative box spans [256 m, 256 m + 256]
+                int ilo = ((umin + 255) >> 8) - 1, ihi = umax >> 8;
+                ilo = max(ilo, 0);
+                ihi = min(ihi, du - 1);
+                const bool vin = vmax >= 0 && vmin <= 256 * dv;
+                r.ilo = ilo;
+                nmaj = (vin && ihi >= ilo) ? ihi - ilo + 1 : 0;
+            }
+        }
+        int incl = nmaj;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        r.start = incl - nmaj;
+        rec[lane] = r;
+        __syncwarp();
+        const int items = __shfl_sync(kFull, incl, 31);
+        for (int base = 0; base < items; base += 32) {
+            const int item = base + lane;
+            int src = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                int v = __shfl_sync(kFull, incl, src + step - 1);
+                if (v <= item) src += step;
+            }
+            if (item >= items) continue;
+            const SegRec &q = rec[src];
+            const int i = q.ilo + (item - q.start);
+            const int32_t du = q.uB - q.uA, dvv = q.vB - q.vA;
+            const int32_t umin = min(q.uA, q.uB), umax = max(q.uA, q.uB);
+            const int32_t ua = max(256 * i, umin), ub = min(256 * i + 256, umax);
+            float flo, fhi;
+            if (du == 0) {
+                flo = 0.0f;
+                fhi = 0.0f;
+            } else {
+                const float slope = (float)dvv / (float)du;
+                const float va = (float)(ua - q.uA) * slope, vb = (float)(ub - q.uA) * slope;
+                flo = floorf(fminf(va, vb));
+                fhi = ceilf(fmaxf(va, vb));
+            }
+            // float error of the minor range is below |dv| 2^-21 + 1 unit
+            const int32_t slack = 8 + (abs(dvv) >> 20);
+            const int64_t vlo = (int64_t)q.vA + (int64_t)flo - slack;
+            const int64_t vhi = (int64_t)q.vA + (int64_t)fhi + slack;
+            const int dimv = q.xmajor ? H : W;
+            const int mlo = (int)max(((vlo + 255) >> 8) - 1, (int64_t)0);
+            const int mhi = (int)min(vhi >> 8, (int64_t)(dimv - 1));
+            const int32_t XA = q.xmajor ? q.uA : q.vA, YA = q.xmajor ? q.vA : q.uA;
+            const int32_t XB = q.xmajor ? q.uB : q.vB, YB = q.xmajor ? q.vB : q.uB;
+            const uint64_t id = ((uint64_t)q.id_hi << 32) | q.id_lo;
+            for (int m = mlo; m <= mhi; ++m) {
+                const int px = q.xmajor ? i : m, py = q.xmajor ? m : i;
+                const int64_t cx = 256 * (int64_t)px + 128, cy = 256 * (int64_t)py + 128;
+                if (!seg_covers(XA, YA, XB, YB, cx, cy, 128)) continue;
+                const bool cen = (q.hc >= 128) || seg_covers(XA, YA, XB, YB, cx, cy, q.hc);
+                const uint64_t key = ((uint64_t)depth24(q.zA, q.zB, seg_t(XA, YA, XB, YB, cx, cy)) << 40) | id;
+                const int64_t p = (int64_t)py * W + px;
+                n_cons += 1;
+                n_cen += cen;
+                if (!kPrecheck || key < __ldcg(reinterpret_cast<const unsigned long long *>(vis_a + p)))
+                    atomicMin(reinterpret_cast<unsigned long long *>(vis_a + p), (unsigned long long)key);
+                if (cen) {
+                    if (!kPrecheck || key < __ldcg(reinterpret_cast<const unsigned long long *>(vis_c + p)))
+                        atomicMin(reinterpret_cast<unsigned long long *>(vis_c + p), (unsigned long long)key);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    if (stats) {
+        unsigned long long a = n_cons, c = n_cen;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(kFull, a, o);
+            c += __shfl_down_sync(kFull, c, o);
+        }
+        if (lane == 0) {
+            atomicAdd((unsigned long long *)&stats->covered_cons, a);
+            atomicAdd((unsigned long long *)&stats->covered_center, c);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// roofline probe: 64-bit atomicMin throughput on a frame-sized buffer
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) probe_atomic_min_kernel(unsigned long long *buf, int64_t n, int rounds,
+                                                               int pattern) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < rounds; ++r) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+            int64_t a = pattern ? (int64_t)(((uint64_t)i * 0x9E3779B97F4A7C15ull) % (uint64_t)n) : i;
+            atomicMin(buf + a, (unsigned long long)((int64_t)rounds - r) << 40 | (unsigned long long)i);
+        }
+    }
+}
+
+cudaError_t launch_probe_atomic_min(uint64_t *buf, int64_t n, int rounds, int pattern, cudaStream_t st) {
+    int grid = num_sms() * 8;
+    probe_atomic_min_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<unsigned long long *>(buf), n, rounds, pattern);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_clear(uint64_t *vis_c, uint64_t *vis_a, int64_t npx, const uint32_t *scene_d24, int do_clear,
+                         hm_frame_stats *stats, cudaStream_t st) {
+    int64_t npairs = npx / 2;
+    int sms = num_sms();
+    int64_t want = (npairs + 255) / 256;
+    int grid = (int)(want < (int64_t)sms * 8 ? (want > 0 ? want : 1) : (int64_t)sms * 8);
+    clear_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<ulonglong2 *>(vis_c), reinterpret_cast<ulonglong2 *>(vis_a),
+                                       npairs, scene_d24, npx, do_clear, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lod(const CallTable &tab, const CamDev &cam, hm_frame_stats *stats, cudaStream_t st) {
+    lod_kernel<<<tab.n, kLodThreads, 0, st>>>(tab, cam, stats);
+    return cudaGetLastError();
+}
+
+int raster_grid(bool precheck) {
+    static int cached[2] = {0, 0};
+    int &c = cached[precheck ? 1 : 0];
+    if (c == 0) {
+        int per_sm = 0;
+        if (precheck)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<true>, kRasterThreads, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<false>, kRasterThreads, 0);
+        if (per_sm < 1) per_sm = 1;
+        c = per_sm * num_sms();
+    }
+    return c;
+}
+
+cudaError_t launch_raster(const CallTable &tab, const CamDev &cam, uint64_t *vis_c, uint64_t *vis_a, bool precheck,
+                          hm_frame_stats *stats, cudaStream_t st) {
+    int grid = raster_grid(precheck);
+    if (precheck)
+        raster_kernel<true><<<grid, kRasterThreads, 0, st>>>(tab, cam, vis_c, vis_a, stats);
+    else
+        raster_kernel<false><<<grid, kRasterThreads, 0, st>>>(tab, cam, vis_c, vis_a, stats);
+    return cudaGetLastError();
+}
+
+}  // namespace hm
+
+namespace hm {
+
+__global__ void pack_float3_kernel(const float *__restrict__ src, float4 *__restrict__ dst, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = make_float4(src[3 * i], src[3 * i + 1], src[3 * i + 2], 0.0f);
+}
+
+cudaError_t launch_pack_float3(const float *src, float4 *dst, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    pack_float3_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace hm

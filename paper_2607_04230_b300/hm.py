@@ -1,0 +1,323 @@
+"""Thin Python binding of libhm (include/hm.h): argument marshalling only.
+
+Every step of the rendering path runs in the CUDA kernels behind the C ABI;
+this module only packs structs, passes device pointers of torch tensors and
+the current CUDA stream, and turns error codes into exceptions.  There is no
+CPU fallback: if libhm.so is missing or cannot load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libhm.so")
+_HEADER = os.path.join(os.path.dirname(_PKG), "include", "hm.h")
+
+HM_OK = 0
+STATUS_NAMES = {0: "HM_OK", 1: "HM_ERR_INVALID_ARG", 2: "HM_ERR_OOM", 3: "HM_ERR_CUDA",
+                4: "HM_ERR_CAPACITY", 5: "HM_ERR_TIMEOUT", 6: "HM_ERR_NOT_READY", 7: "HM_ERR_DEVICE_CHECK"}
+MAX_LIGHTS = 8
+MAX_GROOMS_PER_CALL = 64
+
+
+class HmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GroomDesc(ctypes.Structure):
+    _fields_ = [("num_layers", ctypes.c_int32), ("num_verts", ctypes.c_int32), ("num_faces", ctypes.c_int32),
+                ("segments_per_strand", ctypes.c_int32), ("num_strands", ctypes.c_int64),
+                ("layer_verts", ctypes.c_void_p), ("faces", ctypes.c_void_p), ("strand_face", ctypes.c_void_p),
+                ("strand_bary", ctypes.c_void_p), ("strand_albedo", ctypes.c_void_p),
+                ("bundle_delta", ctypes.c_void_p), ("strand_width_m", ctypes.c_float),
+                ("roughness", ctypes.c_float), ("tilt", ctypes.c_float)]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("view_proj", ctypes.c_float * 16), ("cam_pos", ctypes.c_float * 3), ("near_m", ctypes.c_float),
+                ("far_m", ctypes.c_float), ("tan_half_fovy", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32)]
+
+
+class LodParams(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_int32), ("lambda_", ctypes.c_float)]
+
+
+class Lights(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("dir", (ctypes.c_float * 3) * MAX_LIGHTS),
+                ("radiance", (ctypes.c_float * 3) * MAX_LIGHTS), ("ambient", ctypes.c_float),
+                ("k_d", ctypes.c_float), ("k_s", ctypes.c_float)]
+
+
+class FilterParams(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_int32), ("radius", ctypes.c_int32), ("s_par", ctypes.c_float),
+                ("s_perp", ctypes.c_float), ("sigma_c", ctypes.c_float), ("iso_scale", ctypes.c_float),
+                ("strip_halfwidth", ctypes.c_float), ("depth_reject_m", ctypes.c_float),
+                ("depth_mismatch_m", ctypes.c_float)]
+
+
+STATS_FIELDS = ("strands", "segments", "bundles_culled", "covered_center", "covered_cons")
+
+
+def declared_symbols() -> list:
+    """Function names declared in include/hm.h."""
+    txt = open(_HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:hm_status|size_t|const char \*)\s*(hm_\w+)\s*\(", txt, re.M)))
+
+
+_lib = None
+
+
+def lib():
+    """Load libhm.so (built in-tree by paper_2607_04230_b300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"libhm.so not built ({_LIB_PATH}); run paper_2607_04230_b300.build.build()")
+    L = ctypes.CDLL(_LIB_PATH)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "hm_create_groom": [P, P, P],
+        "hm_destroy_groom": [P],
+        "hm_set_lod": [P, P],
+        "hm_update_layer_verts": [P, P, P],
+        "hm_update_albedo": [P, P, P],
+        "hm_render_visibility": [P, i32, P, P, P, P, i32, P, P],
+        "hm_resolve_shade": [P, i32, P, P, P, P, P, P, P, P],
+        "hm_shade_backward": [P, i32, P, P, P, P, P, P, P, P, P, P],
+        "hm_get_lod": [P, P, P, P],
+        "hm_groom_info": [P, P, P, P, P, P],
+        "hm_get_device_status": [P],
+        "hm_set_phase_events": [P, i32],
+        "hm_probe_atomic_min": [P, i64, i32, i32, P],
+    }
+    for name, args in sig.items():
+        if hasattr(L, name):
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+    if hasattr(L, "hm_backward_scratch_bytes"):
+        L.hm_backward_scratch_bytes.argtypes = [i32, i32]
+        L.hm_backward_scratch_bytes.restype = ctypes.c_size_t
+    L.hm_status_string.argtypes = [ctypes.c_int]
+    L.hm_status_string.restype = ctypes.c_char_p
+    L.hm_last_error.argtypes = []
+    L.hm_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def check(status: int):
+    if status != HM_OK:
+        raise HmError(status, lib().hm_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# struct packing
+# ---------------------------------------------------------------------------
+
+def camera_struct(cam) -> Camera:
+    c = Camera()
+    vp = np.ascontiguousarray(cam.view_proj, np.float32).reshape(16)
+    for i in range(16):
+        c.view_proj[i] = float(vp[i])
+    for i in range(3):
+        c.cam_pos[i] = float(np.float32(cam.cam_pos[i]))
+    c.near_m, c.far_m, c.tan_half_fovy = cam.near, cam.far, cam.tan_half_fovy
+    c.width, c.height = cam.width, cam.height
+    return c
+
+
+def lights_struct(lights) -> Lights:
+    L = Lights()
+    n = lights.dirs.shape[0]
+    if n > MAX_LIGHTS:
+        raise ValueError("too many lights")
+    L.count = n
+    for i in range(n):
+        for k in range(3):
+            L.dir[i][k] = float(lights.dirs[i, k])
+            L.radiance[i][k] = float(lights.radiance[i, k])
+    L.ambient, L.k_d, L.k_s = lights.ambient, lights.k_d, lights.k_s
+    return L
+
+
+def filter_struct(f) -> FilterParams:
+    s = FilterParams()
+    s.enabled, s.radius = int(f.enabled), int(f.radius)
+    s.s_par, s.s_perp, s.sigma_c, s.iso_scale = f.s_par, f.s_perp, f.sigma_c, f.iso_scale
+    s.strip_halfwidth, s.depth_reject_m, s.depth_mismatch_m = f.strip_halfwidth, f.depth_reject_m, f.depth_mismatch_m
+    return s
+
+
+# ---------------------------------------------------------------------------
+# grooms and calls
+# ---------------------------------------------------------------------------
+
+class Groom:
+    """A hair mesh uploaded to the current CUDA device (hm_create_groom)."""
+
+    def __init__(self, g, stream=None):
+        self._keep = dict(
+            lv=np.ascontiguousarray(g.layer_verts, np.float32),
+            faces=np.ascontiguousarray(g.faces, np.int32),
+            sf=np.ascontiguousarray(g.strand_face, np.uint32),
+            bary=np.ascontiguousarray(g.strand_bary, np.float32),
+            alb=np.ascontiguousarray(g.strand_albedo, np.float32),
+            delta=np.ascontiguousarray(g.bundle_delta, np.float32))
+        d = GroomDesc()
+        d.num_layers, d.num_verts, d.num_faces = g.num_layers, g.num_verts, g.num_faces
+        d.segments_per_strand, d.num_strands = g.segments_per_strand, g.num_strands
+        k = self._keep
+        d.layer_verts, d.faces, d.strand_face = k["lv"].ctypes.data, k["faces"].ctypes.data, k["sf"].ctypes.data
+        d.strand_bary, d.strand_albedo, d.bundle_delta = k["bary"].ctypes.data, k["alb"].ctypes.data, k["delta"].ctypes.data
+        d.strand_width_m, d.roughness, d.tilt = g.strand_width_m, g.roughness, g.tilt
+        h = ctypes.c_void_p()
+        check(lib().hm_create_groom(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)))
+        self.handle = h
+        self.num_faces = g.num_faces
+        self.num_strands = g.num_strands
+        self.num_layers = g.num_layers
+        self.num_verts = g.num_verts
+        self._keep = None
+
+    def set_lod(self, enabled: int, lam: float = 3.0):
+        p = LodParams(int(enabled), float(lam))
+        check(lib().hm_set_lod(self.handle, ctypes.byref(p)))
+
+    def update_layer_verts(self, t, stream=None):
+        check(lib().hm_update_layer_verts(self.handle, _dptr(t), _stream_ptr(stream)))
+
+    def update_albedo(self, t, stream=None):
+        check(lib().hm_update_albedo(self.handle, _dptr(t), _stream_ptr(stream)))
+
+    def get_lod(self, stream=None):
+        n = np.zeros(self.num_faces, np.int32)
+        c = np.zeros(self.num_faces, np.int32)
+        check(lib().hm_get_lod(self.handle, n.ctypes.data_as(ctypes.c_void_p), c.ctypes.data_as(ctypes.c_void_p),
+                               _stream_ptr(stream)))
+        return n, c
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().hm_destroy_groom(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _handles(grooms):
+    arr = (ctypes.c_void_p * len(grooms))(*[g.handle.value for g in grooms])
+    return arr, len(grooms)
+
+
+def render_visibility(grooms, cam, vis_center, vis_cons, scene_d24=None, clear=True, stats=None, stream=None):
+    arr, n = _handles(grooms)
+    c = camera_struct(cam)
+    check(lib().hm_render_visibility(arr, n, ctypes.byref(c), _dptr(vis_center), _dptr(vis_cons), _dptr(scene_d24),
+                                     int(bool(clear)), _dptr(stats), _stream_ptr(stream)))
+
+
+def resolve_shade(grooms, cam, lights, filt, vis_center, vis_cons, rgba, stream=None):
+    arr, n = _handles(grooms)
+    c, L, f = camera_struct(cam), lights_struct(lights), filter_struct(filt)
+    check(lib().hm_resolve_shade(arr, n, ctypes.byref(c), ctypes.byref(L), ctypes.byref(f), _dptr(vis_center),
+                                 _dptr(vis_cons), _dptr(rgba), None, _stream_ptr(stream)))
+
+
+def backward_scratch_bytes(width: int, height: int) -> int:
+    return int(lib().hm_backward_scratch_bytes(int(width), int(height)))
+
+
+def shade_backward(grooms, cam, lights, filt, vis_center, vis_cons, grad_rgba, grad_layer_verts, grad_albedo,
+                   scratch, stream=None):
+    arr, n = _handles(grooms)
+    c, L, f = camera_struct(cam), lights_struct(lights), filter_struct(filt)
+    glv = (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in grad_layer_verts])
+    gal = (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in grad_albedo])
+    check(lib().hm_shade_backward(arr, n, ctypes.byref(c), ctypes.byref(L), ctypes.byref(f), _dptr(vis_center),
+                                  _dptr(vis_cons), _dptr(grad_rgba), glv, gal, _dptr(scratch), _stream_ptr(stream)))
+
+
+def set_phase_events(events):
+    """Record torch.cuda.Event objects (enable_timing=True) at the phase
+    boundaries of later calls on this thread; None turns it off."""
+    if not events:
+        check(lib().hm_set_phase_events(None, 0))
+        return
+    arr = (ctypes.c_void_p * len(events))(*[(e.cuda_event if e is not None else None) for e in events])
+    check(lib().hm_set_phase_events(arr, len(events)))
+
+
+def probe_atomic_min(buf, rounds: int = 1, pattern: int = 0, stream=None):
+    check(lib().hm_probe_atomic_min(_dptr(buf), buf.numel(), int(rounds), int(pattern), _stream_ptr(stream)))
+
+
+def stats_dict(stats_tensor):
+    v = stats_tensor.cpu().numpy().view(np.uint64)
+    return {k: int(v[i]) for i, k in enumerate(STATS_FIELDS)}
+
+
+def get_device_status(stream=None):
+    check(lib().hm_get_device_status(_stream_ptr(stream)))
+
+
+class Frame:
+    """Device buffers of one frame: two key layers, RGBA, counters."""
+
+    def __init__(self, width: int, height: int, device="cuda"):
+        import torch
+        npx = width * height
+        self.width, self.height = width, height
+        self.vis_center = torch.empty(npx, dtype=torch.int64, device=device)
+        self.vis_cons = torch.empty(npx, dtype=torch.int64, device=device)
+        self.rgba = torch.empty((height, width, 4), dtype=torch.float32, device=device)
+        self.stats = torch.zeros(8, dtype=torch.int64, device=device)
+
+    def keys_numpy(self):
+        return (self.vis_center.cpu().numpy().view(np.uint64), self.vis_cons.cpu().numpy().view(np.uint64))
+
+
+def render(grooms, scene, frame: Frame, stream=None):
+    """Visibility + resolve of one frame (both on the current stream)."""
+    render_visibility(grooms, scene.camera, frame.vis_center, frame.vis_cons, stats=frame.stats, stream=stream)
+    resolve_shade(grooms, scene.camera, scene.lights, scene.filt, frame.vis_center, frame.vis_cons, frame.rgba,
+                  stream=stream)
+
+
+def upload_scene(scene, stream=None):
+    """hm grooms for every groom of a synthetic scene, LOD set from the scene."""
+    gs = []
+    for g in scene.grooms:
+        h = Groom(g, stream=stream)
+        h.set_lod(scene.lod.enabled, scene.lod.lam)
+        gs.append(h)
+    return gs

@@ -1,0 +1,114 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol
+include/hm.h declares, and rejects bad arguments before touching CUDA."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2607_04230_b300 import build, hm, synth
+
+INVALID = 1
+CAPACITY = 4
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return hm.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    syms = hm.declared_symbols()
+    assert len(syms) >= 14
+    missing = [s for s in syms if not hasattr(L, s)]
+    assert not missing, missing
+
+
+def test_status_strings(L):
+    for code, name in hm.STATUS_NAMES.items():
+        assert L.hm_status_string(code).decode() == name
+
+
+def _desc(g, **over):
+    keep = dict(lv=np.ascontiguousarray(g.layer_verts, np.float32), faces=np.ascontiguousarray(g.faces, np.int32),
+                sf=np.ascontiguousarray(g.strand_face, np.uint32), bary=np.ascontiguousarray(g.strand_bary, np.float32),
+                alb=np.ascontiguousarray(g.strand_albedo, np.float32),
+                delta=np.ascontiguousarray(g.bundle_delta, np.float32))
+    keep.update(over.pop("arrays", {}))
+    d = hm.GroomDesc()
+    d.num_layers, d.num_verts, d.num_faces = g.num_layers, g.num_verts, g.num_faces
+    d.segments_per_strand, d.num_strands = g.segments_per_strand, g.num_strands
+    d.layer_verts, d.faces, d.strand_face = keep["lv"].ctypes.data, keep["faces"].ctypes.data, keep["sf"].ctypes.data
+    d.strand_bary, d.strand_albedo = keep["bary"].ctypes.data, keep["alb"].ctypes.data
+    d.bundle_delta = keep["delta"].ctypes.data
+    d.strand_width_m, d.roughness, d.tilt = 1e-4, 0.15, -0.05
+    for k, v in over.items():
+        setattr(d, k, v)
+    return d, keep
+
+
+def _create(L, d):
+    h = ctypes.c_void_p()
+    return L.hm_create_groom(ctypes.byref(d), None, ctypes.byref(h)), h
+
+
+def test_create_groom_rejects_bad_descriptors(L):
+    g = synth.tiny_scene(0, num_strands=50).grooms[0]
+    assert L.hm_create_groom(None, None, None) == INVALID
+    for over in (dict(num_layers=1), dict(num_layers=33), dict(segments_per_strand=0),
+                 dict(segments_per_strand=127), dict(num_faces=0), dict(strand_width_m=0.0),
+                 dict(layer_verts=None)):
+        d, keep = _desc(g, **over)
+        assert _create(L, d)[0] == INVALID, over
+    d, keep = _desc(g, num_strands=2 ** 31)
+    assert _create(L, d)[0] == CAPACITY
+    bad_faces = g.faces.copy()
+    bad_faces[3, 1] = g.num_verts
+    d, keep = _desc(g, arrays=dict(faces=bad_faces))
+    assert _create(L, d)[0] == INVALID
+    unsorted = g.strand_face.copy()
+    unsorted[[0, -1]] = unsorted[[-1, 0]]
+    d, keep = _desc(g, arrays=dict(sf=unsorted))
+    assert _create(L, d)[0] == INVALID
+    delta = g.bundle_delta.copy()
+    delta[0] = 1.0
+    d, keep = _desc(g, arrays=dict(delta=delta))
+    assert _create(L, d)[0] == INVALID
+    bary = g.strand_bary.copy()
+    bary[5, 0] = -0.1
+    d, keep = _desc(g, arrays=dict(bary=bary))
+    assert _create(L, d)[0] == INVALID
+    assert "barycentric" in L.hm_last_error().decode()
+
+
+def test_render_and_resolve_reject_bad_arguments(L):
+    sc = synth.tiny_scene(0, num_strands=10)
+    cam = hm.camera_struct(sc.camera)
+    fake = ctypes.c_void_p(1 << 20)         # never dereferenced: validation fails first
+    grooms = (ctypes.c_void_p * 1)(1 << 20)
+    assert L.hm_render_visibility(grooms, 1, None, fake, fake, None, 1, None, None) == INVALID
+    bad = hm.camera_struct(sc.camera)
+    bad.width = 0
+    assert L.hm_render_visibility(grooms, 1, ctypes.byref(bad), fake, fake, None, 1, None, None) == INVALID
+    bad = hm.camera_struct(sc.camera)
+    bad.far_m = bad.near_m
+    assert L.hm_render_visibility(grooms, 1, ctypes.byref(bad), fake, fake, None, 1, None, None) == INVALID
+    assert L.hm_render_visibility(grooms, 1, ctypes.byref(cam), None, fake, None, 1, None, None) == INVALID
+    assert L.hm_render_visibility(grooms, 1, ctypes.byref(cam), ctypes.c_void_p((1 << 20) + 8), fake, None, 1,
+                                  None, None) == INVALID
+    assert L.hm_render_visibility(grooms, 1, ctypes.byref(cam), fake, fake, None, 1, None, None) == INVALID
+    assert L.hm_render_visibility(grooms, 0, ctypes.byref(cam), fake, ctypes.c_void_p(2 << 20), None, 1, None,
+                                  None) == INVALID
+    assert L.hm_render_visibility(None, 1, ctypes.byref(cam), fake, ctypes.c_void_p(2 << 20), None, 1, None,
+                                  None) == INVALID
+    lights = hm.lights_struct(sc.lights)
+    f = hm.filter_struct(synth.FilterParams(radius=9))
+    assert L.hm_resolve_shade(grooms, 1, ctypes.byref(cam), ctypes.byref(lights), ctypes.byref(f), fake, fake, fake,
+                              None, None) == INVALID
+    lights.count = 9
+    f = hm.filter_struct(synth.FilterParams())
+    assert L.hm_resolve_shade(grooms, 1, ctypes.byref(cam), ctypes.byref(lights), ctypes.byref(f), fake, fake, fake,
+                              None, None) == INVALID
+    assert L.hm_set_phase_events(None, 7) == INVALID
+    assert L.hm_set_phase_events(None, 0) == 0
+    assert L.hm_probe_atomic_min(None, 10, 1, 0, None) == INVALID

@@ -1,0 +1,116 @@
+"""GPU path vs the CPU oracle, through the C ABI.
+
+Visibility keys and LOD results must be bit-exact; the number of covered
+(pixel, layer) pairs must equal the oracle's count; RGBA must agree with the
+FP64 oracle within 1e-4 (linear RGB and alpha).  Sizes span several raster
+batches and resolve tiles with ragged edges; the full 1080p frame is checked
+key for key and on sampled pixels for colour.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_04230_b300 import synth
+
+from _parity import RGBA_TOL, assert_keys_equal, assert_rgba_close, check_full, gpu_frame, oracle_keys, oracle_rgba
+
+pytestmark = pytest.mark.gpu
+
+
+def test_tiny_256_frame():
+    out, err = check_full(synth.scene_tiny_256())
+    assert (out["vis_a"] != oracle.EMPTY).sum() > 5000
+    assert err <= RGBA_TOL
+
+
+@pytest.mark.parametrize("seed,W,H,lod", [(1, 97, 61, 0), (2, 33, 17, 1), (3, 250, 130, 1), (4, 129, 257, 0)])
+def test_ragged_frames(seed, W, H, lod):
+    sc = synth.tiny_scene(seed, width=W, height=H, num_strands=700, segments=7, num_layers=5,
+                          length_m=0.06, dist_m=0.4, jitter_m=0.004)
+    sc.lod = synth.LodParams(lod, 3.0)
+    check_full(sc)
+
+
+@pytest.mark.parametrize("radius,enabled", [(0, 1), (3, 1), (8, 1), (5, 0)])
+def test_filter_variants(radius, enabled):
+    sc = synth.tiny_scene(5, width=120, height=90, num_strands=800)
+    sc.filt = synth.FilterParams(enabled=enabled, radius=radius)
+    check_full(sc)
+
+
+def test_lod_sweep_small_groom():
+    g = synth.make_groom(7, 8, 3, 6, 0.2, 12_000, 16, curl_amp_m=0.01)
+    for i in range(8):
+        sc = synth.scene_lod_sweep(i, g)
+        check_full(sc, sample=3000)
+
+
+def test_camera_inside_groom_and_behind():
+    sc = synth.tiny_scene(6, width=160, height=120, num_strands=900, dist_m=0.06)
+    for lod in (0, 1):
+        sc.lod = synth.LodParams(lod, 3.0)
+        check_full(sc)
+    # looking away: LOD culls every bundle; without LOD every segment is clipped
+    ctr, _, _ = synth._aabb_center(sc.grooms)
+    sc.camera = synth.make_camera(ctr + np.array([0, 0, 0.5]), ctr + np.array([0, 0, 1.5]), 40, 64, 48)
+    for lod in (0, 1):
+        sc.lod = synth.LodParams(lod, 3.0)
+        out, _ = check_full(sc)
+        assert np.all(out["vis_a"] == oracle.EMPTY)
+
+
+def test_empty_groom_and_many_grooms():
+    g0 = synth.tiny_scene(8, num_strands=0).grooms[0]
+    g0.strand_face = g0.strand_face[:0]
+    sc = synth.tiny_scene(9, width=96, height=96, num_strands=300)
+    sc.grooms = [g0] + sc.grooms + [synth.tiny_scene(10, num_strands=200).grooms[0]]
+    check_full(sc)
+
+
+def test_crowd_small():
+    gs = synth.crowd_grooms(seed=11, n_side=3, strand_scale=0.05)
+    sc = synth.scene_crowd_4k(gs, width=640, height=360)
+    check_full(sc, sample=20000)
+
+
+def test_scene_depth_prefill():
+    import torch
+    from paper_2607_04230_b300 import hm
+    sc = synth.tiny_scene(12, width=128, height=96, num_strands=600)
+    rng = np.random.default_rng(0)
+    lods, vc0, va0, _ = oracle_keys(sc)
+    d = (vc0 >> np.uint64(40)).astype(np.int64)
+    # a wall that hides part of the groom
+    scene = np.where(rng.random(d.size) < 0.5, np.median(d[d < 2 ** 24 - 1]), 2 ** 24 - 1).astype(np.uint32)
+    grooms = hm.upload_scene(sc)
+    frame = hm.Frame(sc.camera.width, sc.camera.height)
+    sd = torch.from_numpy(scene.view(np.int32)).cuda()
+    hm.render_visibility(grooms, sc.camera, frame.vis_center, frame.vis_cons, scene_d24=sd)
+    torch.cuda.synchronize()
+    vc, va = frame.keys_numpy()
+    ovc, ova, _ = oracle.raster(sc.grooms, sc.camera, lods, prefill_d24=scene)
+    assert_keys_equal(vc, ovc, "centre layer with scene depth")
+    assert_keys_equal(va, ova, "conservative layer with scene depth")
+
+
+def test_deterministic_repeat():
+    sc = synth.tiny_scene(13, width=200, height=150, num_strands=2000)
+    a = gpu_frame(sc)
+    b = gpu_frame(sc, grooms=a["grooms"])
+    assert np.array_equal(a["vis_c"], b["vis_c"]) and np.array_equal(a["vis_a"], b["vis_a"])
+    assert np.array_equal(a["rgba"], b["rgba"])
+
+
+def test_single_groom_1080p_full_size():
+    """100k strands x 16 segments at 1920x1080, the benchmark workload:
+    every key of both layers, and colour on sampled pixels."""
+    sc = synth.scene_single_1080p()
+    out, err = check_full(sc, sample=6000)
+    assert out["stats"]["segments"] == 1_600_000
+    assert out["stats"]["strands"] == 100_000
+
+
+def test_crowd_4k_full_size():
+    """64 grooms, 3840x2160, LOD by distance, one render call."""
+    sc = synth.scene_crowd_4k()
+    check_full(sc, sample=6000)
