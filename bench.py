@@ -287,6 +287,10 @@ def run_native(args, rank, world, local_rank):
     peak_rates = probe_atomic_peak(torch, hm, 2 * W * H)
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    for row in ev:              # torch creates the cudaEvent_t on first record
+        for e in row:
+            e.record()
+    torch.cuda.synchronize()
     gpu_uuid = str(torch.cuda.get_device_properties(local_rank).uuid)
     if not gpu_uuid.startswith("GPU-"):
         gpu_uuid = "GPU-" + gpu_uuid

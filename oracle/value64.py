@@ -264,6 +264,7 @@ def resolve(gts, cam, lights, filt, vis_c, vis_a, dec, pixels=None):
     def reconstruct(ref_d24, Ts, iso, use_color):
         S = torch.zeros((pixels.size, 3), dtype=torch.float64)
         Wt = torch.zeros((pixels.size, 1), dtype=torch.float64)
+        cnt = torch.zeros((pixels.size, 1), dtype=torch.int64)
         for dy in range(-r, r + 1):
             for dx in range(-r, r + 1):
                 qx, qy = px + dx, py + dy
@@ -285,15 +286,16 @@ def resolve(gts, cam, lights, filt, vis_c, vis_a, dec, pixels=None):
                 w = torch.where(ok, ws * wc, torch.zeros_like(ws))[:, None]
                 S = S + w * CQ
                 Wt = Wt + w
-        return S, Wt
+                cnt = cnt + ok[:, None].long()
+        return S, Wt, cnt
 
     # centre-referenced reconstruction (colour term on)
     isoG = torch.from_numpy(dec_at(dec, "isoG", pixels, None).astype(bool))
     isoA = torch.from_numpy(dec_at(dec, "isoA", pixels, None).astype(bool))
     refG = torch.from_numpy(dG[pixels])
     refA = torch.from_numpy(dA[pixels])
-    SG, WG = reconstruct(refG, TsG, isoG, CP)
-    SA, WA = reconstruct(refA, TsA, isoA, None)
+    SG, WG, _ = reconstruct(refG, TsG, isoG, CP)
+    SA, WA, nA = reconstruct(refA, TsA, isoA, None)
     safeWG = torch.where(WG > 0, WG, torch.ones_like(WG))
     safeWA = torch.where(WA > 0, WA, torch.ones_like(WA))
     CG = SG / safeWG
@@ -308,7 +310,9 @@ def resolve(gts, cam, lights, filt, vis_c, vis_a, dec, pixels=None):
     isc_t = torch.from_numpy(isc)[:, None]
     mism_t = torch.from_numpy(mism)[:, None]
     isa_t = torch.from_numpy(isa)[:, None]
-    hasA = WA > 0
+    # a promoted reconstruction exists iff some centre-sample neighbour
+    # contributes (every weight exp(-e) is positive), Sec. 3.3.2
+    hasA = nA > 0
     blend = torch.where(hasA, aA * CAh + (1.0 - aA) * CG, CG)
     rgb_c = torch.where(mism_t, blend, CG)
     a_c = torch.where(mism_t, torch.ones_like(aG), aG)

@@ -1,0 +1,43 @@
+"""torch.autograd.Function over the deferred resolve (argument marshalling
+only; forward and backward run in libhm's kernels).
+
+forward(layer_verts, albedo) renders one groom (visibility + resolve) and
+returns straight-alpha RGBA [H][W][4].  backward calls hm_shade_backward with
+the forward's visibility buffers held fixed: gradients reach the hair-mesh
+layer vertices [L][V][3] and the per-strand albedo [S][3]; the alpha channel is
+constant (its strip counts are discrete) and gets no gradient.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import hm
+
+
+class HairRender(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, layer_verts, albedo, groom, scene, frame):
+        groom.update_layer_verts(layer_verts.detach().float().contiguous())
+        groom.update_albedo(albedo.detach().float().contiguous())
+        hm.render([groom], scene, frame)
+        ctx.groom, ctx.scene = groom, scene
+        ctx.vis = (frame.vis_center.clone(), frame.vis_cons.clone())
+        ctx.lv_shape, ctx.alb_shape = layer_verts.shape, albedo.shape
+        return frame.rgba.clone()
+
+    @staticmethod
+    def backward(ctx, grad_rgba):
+        sc = ctx.scene
+        dev = grad_rgba.device
+        glv = torch.zeros(ctx.lv_shape, dtype=torch.float32, device=dev)
+        galb = torch.zeros(ctx.alb_shape, dtype=torch.float32, device=dev)
+        nbytes = hm.backward_scratch_bytes(sc.camera.width, sc.camera.height)
+        scratch = torch.empty(nbytes // 4, dtype=torch.float32, device=dev)
+        hm.shade_backward([ctx.groom], sc.camera, sc.lights, sc.filt, ctx.vis[0], ctx.vis[1],
+                          grad_rgba.float().contiguous(), [glv], [galb], scratch)
+        return glv, galb, None, None, None
+
+
+def render(groom, scene, frame, layer_verts, albedo):
+    """Differentiable RGBA of one groom w.r.t. its layer vertices and albedo."""
+    return HairRender.apply(layer_verts, albedo, groom, scene, frame)

@@ -508,9 +508,26 @@ hm_status hm_shade_backward(const hm_groom *grooms, int32_t n, const hm_camera *
                             const hm_filter_params *filt, const uint64_t *d_vis_center, const uint64_t *d_vis_cons,
                             const float *d_grad_rgba, float *const *d_grad_layer_verts, float *const *d_grad_albedo,
                             void *d_scratch, void *stream) {
-    (void)grooms; (void)n; (void)cam; (void)lights; (void)filt; (void)d_vis_center; (void)d_vis_cons;
-    (void)d_grad_rgba; (void)d_grad_layer_verts; (void)d_grad_albedo; (void)d_scratch; (void)stream;
-    return fail(HM_ERR_NOT_READY, "hm_shade_backward is not built in this version");
+    hm_status st = check_camera(cam);
+    if (st != HM_OK) return st;
+    if (!d_vis_center || !d_vis_cons || !d_grad_rgba || !d_scratch) return fail(HM_ERR_INVALID_ARG, "buffer is NULL");
+    if ((reinterpret_cast<uintptr_t>(d_grad_rgba) & 15) || (reinterpret_cast<uintptr_t>(d_scratch) & 15) ||
+        (reinterpret_cast<uintptr_t>(d_vis_center) & 7) || (reinterpret_cast<uintptr_t>(d_vis_cons) & 7))
+        return fail(HM_ERR_INVALID_ARG, "misaligned buffer");
+    hm::LightsDev ld;
+    hm::FilterDev fd;
+    if ((st = lights_dev(lights, ld)) != HM_OK) return st;
+    if ((st = filter_dev(filt, cam, fd)) != HM_OK) return st;
+    hm::CallTable tab;
+    st = build_table(grooms, n, tab);
+    if (st != HM_OK) return st;
+    uint32_t *sw = status_word();
+    if (!sw) return fail(HM_ERR_CUDA, "device status word unavailable");
+    HM_CUDA(hm::launch_resolve_adjoint(tab, cam_dev(cam), ld, fd, d_vis_center, d_vis_cons, d_grad_rgba,
+                                       d_grad_layer_verts, d_grad_albedo, d_scratch, sw,
+                                       static_cast<cudaStream_t>(stream)),
+            "resolve adjoint");
+    return HM_OK;
 }
 
 }  // extern "C"

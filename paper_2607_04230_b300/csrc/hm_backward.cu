@@ -1,0 +1,549 @@
+// hm_backward.cu -- adjoint of the deferred resolve (shading + strand
+// connection / bilateral filter) with visibility held fixed: the keys, the
+// pixel-centre projection parameters and every filter mask and strip count
+// are the forward's, so alpha is constant.  Gradients flow to the hair-mesh
+// layer vertices (through the pixel position, tangent and screen tangent of
+// every decoded strand segment: interpolation, styled tangents, Hermite
+// control points, base-spline tangents and chord lengths, barycentric layer
+// points) and to the per-strand albedo.
+//
+// Kernel 1 (tiles, as the forward): recompute the staged colours and each
+// tile pixel's reconstruction, then push dL/dC of every contributing
+// neighbour into a per-pixel colour-gradient buffer, and dL/d(screen
+// tangent) of the pixel's reference segment straight into the geometry.
+// Kernel 2 (pixels): shading adjoint of every centre-sample pixel with a
+// colour gradient.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hm_device.cuh"
+#include "hm_kernels.h"
+#include "hm_value.cuh"
+
+namespace hm {
+
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 add3(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 mul3(float3 a, float k) { return f3(a.x * k, a.y * k, a.z * k); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float len3(float3 a) { return sqrtf(dot3(a, a)); }
+
+// v -> v / |v|: given the unit result u = v/|v|, |v| and dL/du, dL/dv.
+__device__ __forceinline__ float3 unit_adjoint(float3 u, float len, float3 du) {
+    if (len == 0.0f) return f3(0.f, 0.f, 0.f);
+    return mul3(sub3(du, mul3(u, dot3(u, du))), 1.0f / len);
+}
+
+struct Sink {
+    float *glv;              // [L][V][3] or NULL
+    int V;
+};
+
+__device__ __forceinline__ void scatter_layer_point(const Sink &sk, const Root &r, int k, float3 dP) {
+    if (!sk.glv || (dP.x == 0.f && dP.y == 0.f && dP.z == 0.f)) return;
+    float *row = sk.glv + (int64_t)k * sk.V * 3;
+    const int idx[3] = {r.i0, r.i1, r.i2};
+    const float b[3] = {r.b0, r.b1, r.b2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float *p = row + 3 * idx[c];
+        atomicAdd(p + 0, b[c] * dP.x);
+        atomicAdd(p + 1, b[c] * dP.y);
+        atomicAdd(p + 2, b[c] * dP.z);
+    }
+}
+
+// Adjoint of control point j (Hermite with chord-scaled finite-difference
+// tangents) to its layer points and on to the layer vertices.
+__device__ void control_point_adjoint(const GroomDev &g, const Root &r, int C, int j, float3 dp, const Sink &sk) {
+    if (dp.x == 0.f && dp.y == 0.f && dp.z == 0.f) return;
+    const int L = g.L;
+    const int x = j * (L - 1);
+    int k = x / (C - 1);
+    if (k > L - 2) k = L - 2;
+    const float s = (float)(x - k * (C - 1)) / (float)(C - 1);
+    const float3 P0 = layer_pt(g, r, k);
+    const float3 P1 = layer_pt(g, r, k + 1);
+    const bool hm_ = k > 0, hp = k + 2 <= L - 1;
+    const float3 Pm = hm_ ? layer_pt(g, r, k - 1) : P0;
+    const float3 P2 = hp ? layer_pt(g, r, k + 2) : P1;
+    const float3 v0 = (k == 0) ? sub3(P1, P0) : sub3(P1, Pm);
+    const float3 v1 = (k + 1 == L - 1) ? sub3(P1, P0) : sub3(P2, P0);
+    const float n0 = len3(v0), n1 = len3(v1);
+    const float3 t0 = n0 > 0.f ? mul3(v0, 1.f / n0) : f3(0.f, 0.f, 0.f);
+    const float3 t1 = n1 > 0.f ? mul3(v1, 1.f / n1) : f3(0.f, 0.f, 0.f);
+    const float3 ch = sub3(P1, P0);
+    const float ell = len3(ch);
+    const float s2 = s * s, s3 = s2 * s;
+    const float h00 = 2.f * s3 - 3.f * s2 + 1.f, h10 = s3 - 2.f * s2 + s;
+    const float h01 = 3.f * s2 - 2.f * s3, h11 = s3 - s2;
+    float3 dP0 = mul3(dp, h00), dP1 = mul3(dp, h01), dPm = f3(0.f, 0.f, 0.f), dP2 = f3(0.f, 0.f, 0.f);
+    const float dell = h10 * dot3(t0, dp) + h11 * dot3(t1, dp);
+    if (ell > 0.f) {
+        const float3 e = mul3(ch, dell / ell);
+        dP1 = add3(dP1, e);
+        dP0 = sub3(dP0, e);
+    }
+    const float3 dv0 = unit_adjoint(t0, n0, mul3(dp, h10 * ell));
+    if (k == 0) {
+        dP1 = add3(dP1, dv0);
+        dP0 = sub3(dP0, dv0);
+    } else {
+        dP1 = add3(dP1, dv0);
+        dPm = sub3(dPm, dv0);
+    }
+    const float3 dv1 = unit_adjoint(t1, n1, mul3(dp, h11 * ell));
+    if (k + 1 == L - 1) {
+        dP1 = add3(dP1, dv1);
+        dP0 = sub3(dP0, dv1);
+    } else {
+        dP2 = add3(dP2, dv1);
+        dP0 = sub3(dP0, dv1);
+    }
+    scatter_layer_point(sk, r, k, dP0);
+    scatter_layer_point(sk, r, k + 1, dP1);
+    if (hm_) scatter_layer_point(sk, r, k - 1, dPm);
+    if (hp) scatter_layer_point(sk, r, k + 2, dP2);
+}
+
+// Adjoint of the pixel position X = p_j + (p_{j+1} - p_j) t and unit tangent
+// T = unit(T_j + (T_{j+1} - T_j) t), t fixed, to the control points.
+__device__ void geometry_adjoint(const GroomDev &g, const Root &r, int C, int j, float t, float3 dX, float3 dT,
+                                 const Sink &sk) {
+    const float3 p0 = control_pt(g, r, C, j);
+    const float3 p1 = control_pt(g, r, C, j + 1);
+    const bool has_m = j >= 1, has_p = j + 2 <= C - 1;
+    const float3 pm = has_m ? control_pt(g, r, C, j - 1) : p0;
+    const float3 pp = has_p ? control_pt(g, r, C, j + 2) : p1;
+    const float3 va = (j == 0) ? sub3(p1, p0) : sub3(p1, pm);
+    const float3 vb = (j + 1 == C - 1) ? sub3(p1, p0) : sub3(pp, p0);
+    const float na = len3(va), nb = len3(vb);
+    const float3 Ta = na > 0.f ? mul3(va, 1.f / na) : f3(0.f, 0.f, 0.f);
+    const float3 Tb = nb > 0.f ? mul3(vb, 1.f / nb) : f3(0.f, 0.f, 0.f);
+    const float3 Tm = add3(Ta, mul3(sub3(Tb, Ta), t));
+    const float nm = len3(Tm);
+    const float3 T = nm > 0.f ? mul3(Tm, 1.f / nm) : f3(0.f, 0.f, 0.f);
+    const float3 dTm = unit_adjoint(T, nm, dT);
+    const float3 dTa = mul3(dTm, 1.f - t), dTb = mul3(dTm, t);
+    float3 dp0 = mul3(dX, 1.f - t), dp1 = mul3(dX, t), dpm = f3(0.f, 0.f, 0.f), dpp = f3(0.f, 0.f, 0.f);
+    const float3 dva = unit_adjoint(Ta, na, dTa);
+    if (j == 0) {
+        dp1 = add3(dp1, dva);
+        dp0 = sub3(dp0, dva);
+    } else {
+        dp1 = add3(dp1, dva);
+        dpm = sub3(dpm, dva);
+    }
+    const float3 dvb = unit_adjoint(Tb, nb, dTb);
+    if (j + 1 == C - 1) {
+        dp1 = add3(dp1, dvb);
+        dp0 = sub3(dp0, dvb);
+    } else {
+        dpp = add3(dpp, dvb);
+        dp0 = sub3(dp0, dvb);
+    }
+    control_point_adjoint(g, r, C, j, dp0, sk);
+    control_point_adjoint(g, r, C, j + 1, dp1, sk);
+    if (has_m) control_point_adjoint(g, r, C, j - 1, dpm, sk);
+    if (has_p) control_point_adjoint(g, r, C, j + 2, dpp, sk);
+}
+
+// Adjoint of the screen tangent Ts = J T / |J T| at X (J: Jacobian of the
+// pixel position with respect to the world position).
+__device__ void screen_tangent_adjoint(const CamDev &cam, float3 X, float3 T, float2 dTs, float3 &dX, float3 &dT) {
+    const float *m = cam.m;
+    const float3 M0 = f3(m[0], m[1], m[2]), M1 = f3(m[4], m[5], m[6]), M3 = f3(m[12], m[13], m[14]);
+    const float c0 = dot3(M0, X) + m[3], c1 = dot3(M1, X) + m[7], w = dot3(M3, X) + m[15];
+    const float a0 = dot3(M0, T), a1 = dot3(M1, T), a3 = dot3(M3, T);
+    const float hw = 0.5f * (float)cam.W, hh = 0.5f * (float)cam.H;
+    const float iw = 1.f / w, iw2 = iw * iw, iw3 = iw2 * iw;
+    const float jx = hw * (a0 * iw - c0 * a3 * iw2);
+    const float jy = -hh * (a1 * iw - c1 * a3 * iw2);
+    const float n = sqrtf(jx * jx + jy * jy);
+    dX = f3(0.f, 0.f, 0.f);
+    dT = f3(0.f, 0.f, 0.f);
+    if (n == 0.f) return;
+    const float tx = jx / n, ty = jy / n;
+    const float k = tx * dTs.x + ty * dTs.y;
+    const float djx = (dTs.x - tx * k) / n, djy = (dTs.y - ty * k) / n;
+    // d jx / d T, d jy / d T
+    dT = add3(mul3(sub3(mul3(M0, iw), mul3(M3, c0 * iw2)), djx * hw),
+              mul3(sub3(mul3(M1, iw), mul3(M3, c1 * iw2)), -djy * hh));
+    // d jx / d X = hw (-a0 iw2 M3 - a3 iw2 M0 + 2 c0 a3 iw3 M3), same for jy with -hh, a1, c1, M1
+    const float3 gx = add3(mul3(M3, -a0 * iw2 + 2.f * c0 * a3 * iw3), mul3(M0, -a3 * iw2));
+    const float3 gy = add3(mul3(M3, -a1 * iw2 + 2.f * c1 * a3 * iw3), mul3(M1, -a3 * iw2));
+    dX = add3(mul3(gx, djx * hw), mul3(gy, -djy * hh));
+}
+
+// Adjoint of the shading model (Sec. 3.4) at one pixel.
+__device__ void shade_adjoint(float3 X, float3 T, float3 alb, const CamDev &cam, const LightsDev &Ls, float rough,
+                              float tilt, float3 dC, float3 &dX, float3 &dT, float3 &dalb) {
+    const float3 Vr = f3(cam.cam_pos[0] - X.x, cam.cam_pos[1] - X.y, cam.cam_pos[2] - X.z);
+    const float vl = len3(Vr);
+    const float3 V = vl > 0.f ? mul3(Vr, 1.f / vl) : f3(0.f, 0.f, 0.f);
+    const float sa = sinf(tilt);
+    const float b2 = rough * rough;
+    dalb = mul3(dC, Ls.ambient);
+    dT = f3(0.f, 0.f, 0.f);
+    float3 dV = f3(0.f, 0.f, 0.f);
+    for (int l = 0; l < Ls.n; ++l) {
+        const float3 Ld = f3(Ls.dir[l][0], Ls.dir[l][1], Ls.dir[l][2]);
+        const float tl = dot3(T, Ld), tv = dot3(T, V);
+        const float sin2 = 1.f - tl * tl;
+        const float sq = sin2 > 0.f ? sqrtf(sin2) : 0.f;
+        const float u = (tl + tv) * 0.5f + sa;
+        const float fs = Ls.ks * __expf(-(u * u) / (2.f * b2));
+        const float3 gE = f3(dC.x * Ls.rad[l][0], dC.y * Ls.rad[l][1], dC.z * Ls.rad[l][2]);
+        dalb = add3(dalb, mul3(gE, Ls.kd * sq));
+        const float dsq = Ls.kd * dot3(gE, alb);
+        const float dfs = gE.x + gE.y + gE.z;
+        float dtl = sq > 0.f ? -dsq * tl / sq : 0.f;
+        const float du = dfs * fs * (-u / b2);
+        dtl += 0.5f * du;
+        const float dtv = 0.5f * du;
+        dT = add3(dT, add3(mul3(Ld, dtl), mul3(V, dtv)));
+        dV = add3(dV, mul3(T, dtv));
+    }
+    dX = mul3(unit_adjoint(V, vl, dV), -1.f);
+}
+
+struct BwdSinks {
+    float *glv[HM_MAX_GROOMS_PER_CALL];
+    float *galb[HM_MAX_GROOMS_PER_CALL];
+};
+
+// Adjoint of one normalized reconstruction R = sum w C / sum w given
+// dL/dR: colour gradients of the contributing neighbours (and of the centre
+// colour through the colour term) into s_dC, returns dL/d(screen tangent).
+__device__ __forceinline__ float2 reconstruct_adjoint(const int *s_dg, const float3 *s_col, float3 *s_dC, int sw,
+                                                      int lx, int ly, int gx, int gy, int W, int H, int R, int ref,
+                                                      float tsx, float tsy, bool iso, bool use_color, float3 Cp,
+                                                      int mid, const Recon &rc, float3 gR, const FilterDev &fp) {
+    float2 dTs = make_float2(0.f, 0.f);
+    if (rc.cnt == 0) return dTs;
+    const float invW = 1.0f / rc.W;
+    const float3 Rv = mul3(rc.S, invW);
+    float3 dCp = f3(0.f, 0.f, 0.f);
+    for (int dy = -R; dy <= R; ++dy) {
+        const int qy = gy + dy;
+        if (qy < 0 || qy >= H) continue;
+        const int row = (ly + dy + R) * sw + R + lx;
+        for (int dx = -R; dx <= R; ++dx) {
+            const int qx = gx + dx;
+            if (qx < 0 || qx >= W) continue;
+            const int idx = row + dx;
+            const int dq = s_dg[idx];
+            if (dq < 0 || abs(dq - ref) > fp.drej) continue;
+            float dpar, perp2;
+            in_strip(iso, tsx, tsy, dx, dy, fp.hw2, dpar, perp2);
+            const float3 cq = s_col[idx];
+            const float e = weight_exponent(iso, dx, dy, dpar, perp2, use_color, Cp, cq, fp);
+            const float om = __expf(rc.m - e) * invW;      // normalized weight
+            const float3 dcq = mul3(gR, om);
+            // dR/de_Q = -om (C_Q - R)
+            const float de = -om * dot3(gR, sub3(cq, Rv));
+            float3 dq3 = dcq;
+            if (!iso) {
+                // e_spatial = dpar^2 / s_par^2 + (|d|^2 - dpar^2) / s_perp^2, dpar = d . Ts
+                const float k = de * 2.f * dpar * (fp.inv_spar2 - fp.inv_sperp2);
+                dTs.x += k * (float)dx;
+                dTs.y += k * (float)dy;
+            }
+            if (use_color) {
+                const float3 dd = mul3(sub3(Cp, cq), 2.f * fp.inv_sc2 * de);
+                dCp = add3(dCp, dd);
+                dq3 = sub3(dq3, dd);
+            }
+            atomicAdd(&s_dC[idx].x, dq3.x);
+            atomicAdd(&s_dC[idx].y, dq3.y);
+            atomicAdd(&s_dC[idx].z, dq3.z);
+        }
+    }
+    if (use_color) {
+        atomicAdd(&s_dC[mid].x, dCp.x);
+        atomicAdd(&s_dC[mid].y, dCp.y);
+        atomicAdd(&s_dC[mid].z, dCp.z);
+    }
+    return dTs;
+}
+
+__device__ __forceinline__ void ts_to_geometry(const CallTable &tab, const uint64_t *bases, const CamDev &cam,
+                                               const BwdSinks &sinks, uint64_t key, int px, int py, float2 dTs,
+                                               uint32_t *status) {
+    if (dTs.x == 0.f && dTs.y == 0.f) return;
+    const Decoded d = decode_key(tab, bases, cam, key, px, py, status);
+    if (!d.ok || d.iso) return;
+    const GroomDev &g = tab.g[d.gi];
+    Sink sk;
+    sk.glv = sinks.glv[d.gi];
+    sk.V = g.V;
+    if (!sk.glv) return;
+    float3 dX, dT;
+    screen_tangent_adjoint(cam, d.X, d.T, dTs, dX, dT);
+    const Root r = make_root(g, d.s, __ldg(&g.sface[d.s]));
+    geometry_adjoint(g, r, d.C, d.j, d.t, dX, dT, sk);
+}
+
+__global__ void __launch_bounds__(kResolveThreads) resolve_adjoint_kernel(
+    CallTable tab, CamDev cam, LightsDev Ls, FilterDev fp, const uint64_t *__restrict__ vis_c,
+    const uint64_t *__restrict__ vis_a, const float4 *__restrict__ grad_rgba, float4 *__restrict__ dC,
+    BwdSinks sinks, uint32_t *status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int R = fp.enabled ? fp.radius : 0;
+    const int sw = kTileW + 2 * R, sh = kTileH + 2 * R, ns = sw * sh;
+    uint64_t *s_bases = reinterpret_cast<uint64_t *>(smem);
+    float3 *s_col = reinterpret_cast<float3 *>(s_bases + HM_MAX_GROOMS_PER_CALL + 1);
+    float3 *s_dC = s_col + ns;
+    int *s_dg = reinterpret_cast<int *>(s_dC + ns);
+    uint16_t *s_list = reinterpret_cast<uint16_t *>(s_dg + ns);
+    float2 *s_tsG = reinterpret_cast<float2 *>(
+        (reinterpret_cast<uintptr_t>(s_list + ((ns + 7) & ~7)) + 15) & ~(uintptr_t)15);
+    float2 *s_tsA = s_tsG + kResolveThreads;
+    uint8_t *s_isoG = reinterpret_cast<uint8_t *>(s_tsA + kResolveThreads);
+    uint8_t *s_isoA = s_isoG + kResolveThreads;
+    uint8_t *s_fa = s_isoA + kResolveThreads;
+    __shared__ int s_count;
+
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
+    const int W = cam.W, H = cam.H;
+    if (tid <= tab.n) {
+        uint64_t b = 0;
+        for (int i = 0; i < tid; ++i) b += (uint64_t)tab.g[i].S;
+        s_bases[tid] = b;
+    }
+    if (tid == 0) s_count = 0;
+    __syncthreads();
+    for (int i = tid; i < ns; i += kResolveThreads) {
+        const int gx = x0 - R + i % sw, gy = y0 - R + i / sw;
+        int dg = -1;
+        uint8_t fa = 0;
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+            const int64_t p = (int64_t)gy * W + gx;
+            const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + p));
+            const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + p));
+            if (!key_empty(kg)) {
+                dg = (int)(kg >> 40);
+                s_list[atomicAdd(&s_count, 1)] = (uint16_t)i;
+            }
+            fa = !key_empty(ka);
+        }
+        s_dg[i] = dg;
+        s_fa[i] = fa;
+        s_dC[i] = f3(0.f, 0.f, 0.f);
+    }
+    s_isoG[tid] = 1;
+    s_isoA[tid] = 1;
+    __syncthreads();
+    const int ncen = s_count;
+    for (int li = tid; li < ncen; li += kResolveThreads) {
+        const int i = s_list[li];
+        const int lx = i % sw, ly = i / sw;
+        const int gx = x0 - R + lx, gy = y0 - R + ly;
+        const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + (int64_t)gy * W + gx));
+        const Decoded d = decode_key(tab, s_bases, cam, kg, gx, gy, status);
+        float3 c = f3(0.f, 0.f, 0.f);
+        if (d.ok) {
+            const GroomDev &g = tab.g[d.gi];
+            const float4 a = __ldg(&g.albedo[d.s]);
+            c = shade(d.X, d.T, f3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt);
+        }
+        s_col[i] = c;
+        const int tx = lx - R, ty = ly - R;
+        if (tx >= 0 && tx < kTileW && ty >= 0 && ty < kTileH) {
+            const int t = ty * kTileW + tx;
+            s_tsG[t] = make_float2(d.tsx, d.tsy);
+            s_isoG[t] = d.iso;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) s_count = 0;
+    __syncthreads();
+    const int tx = tid % kTileW, ty = tid / kTileW;
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool inside = gx < W && gy < H;
+    const int mid = (ty + R) * sw + tx + R;
+    uint64_t ka = kEmptyKey, kgP = kEmptyKey;
+    int dA = -1;
+    if (inside) {
+        kgP = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + (int64_t)gy * W + gx));
+        ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx));
+        if (fp.enabled && !key_empty(ka)) {
+            dA = (int)(ka >> 40);
+            const int dgP = s_dg[mid];
+            if (dgP < 0 || dA + fp.dmis <= dgP) s_list[atomicAdd(&s_count, 1)] = (uint16_t)tid;
+        }
+    }
+    __syncthreads();
+    const int nA = s_count;
+    for (int li = tid; li < nA; li += kResolveThreads) {
+        const int t = s_list[li];
+        const int px = x0 + t % kTileW, py = y0 + t / kTileW;
+        const uint64_t k = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)py * W + px));
+        const Decoded d = decode_key(tab, s_bases, cam, k, px, py, status);
+        s_tsA[t] = make_float2(d.tsx, d.tsy);
+        s_isoA[t] = d.iso;
+    }
+    __syncthreads();
+
+    float2 dTsG = make_float2(0.f, 0.f), dTsA = make_float2(0.f, 0.f);
+    if (inside) {
+        const float4 g4 = __ldg(&grad_rgba[(int64_t)gy * W + gx]);
+        const float3 g = f3(g4.x, g4.y, g4.z);
+        const bool nz = g.x != 0.f || g.y != 0.f || g.z != 0.f;
+        const int dG = s_dg[mid];
+        const bool gP = dG >= 0, aP = s_fa[mid];
+        if (nz && !fp.enabled) {
+            if (gP) {
+                atomicAdd(&s_dC[mid].x, g.x);
+                atomicAdd(&s_dC[mid].y, g.y);
+                atomicAdd(&s_dC[mid].z, g.z);
+            }
+        } else if (nz && gP) {
+            const float3 Cp = s_col[mid];
+            const float2 ts = s_tsG[tid];
+            const bool isoG = s_isoG[tid] != 0;
+            const Recon rg = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dG, ts.x, ts.y, isoG, true,
+                                         Cp, fp);
+            float3 gG = g, gA = f3(0.f, 0.f, 0.f);
+            Recon ra;
+            ra.cnt = 0;
+            const bool mism = aP && dA + fp.dmis <= dG;
+            if (mism) {
+                const float2 tsa = s_tsA[tid];
+                ra = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y, s_isoA[tid] != 0,
+                                 false, Cp, fp);
+                if (ra.cnt > 0) {
+                    const float al = (float)ra.hc / (float)ra.ha;
+                    gA = mul3(g, al);
+                    gG = mul3(g, 1.f - al);
+                }
+            }
+            dTsG = reconstruct_adjoint(s_dg, s_col, s_dC, sw, tx, ty, gx, gy, W, H, R, dG, ts.x, ts.y, isoG, true,
+                                       Cp, mid, rg, gG, fp);
+            if (mism && ra.cnt > 0) {
+                const float2 tsa = s_tsA[tid];
+                dTsA = reconstruct_adjoint(s_dg, s_col, s_dC, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y,
+                                           s_isoA[tid] != 0, false, Cp, mid, ra, gA, fp);
+            }
+        } else if (nz && aP) {
+            const float2 tsa = s_tsA[tid];
+            const bool isoA = s_isoA[tid] != 0;
+            const float3 z = f3(0.f, 0.f, 0.f);
+            const Recon ra = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y, isoA,
+                                         false, z, fp);
+            dTsA = reconstruct_adjoint(s_dg, s_col, s_dC, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y, isoA, false,
+                                       z, mid, ra, g, fp);
+        }
+    }
+    __syncthreads();
+    // colour gradients of the staged pixels to the global buffer
+    for (int i = tid; i < ns; i += kResolveThreads) {
+        const float3 v = s_dC[i];
+        if (v.x == 0.f && v.y == 0.f && v.z == 0.f) continue;
+        const int qx = x0 - R + i % sw, qy = y0 - R + i / sw;
+        if (qx < 0 || qx >= W || qy < 0 || qy >= H) continue;
+        float4 *p = dC + (int64_t)qy * W + qx;
+        atomicAdd(&p->x, v.x);
+        atomicAdd(&p->y, v.y);
+        atomicAdd(&p->z, v.z);
+    }
+    // screen-tangent gradients to the geometry of the reference segments
+    if (inside) {
+        ts_to_geometry(tab, s_bases, cam, sinks, kgP, gx, gy, dTsG, status);
+        ts_to_geometry(tab, s_bases, cam, sinks, ka, gx, gy, dTsA, status);
+    }
+}
+
+// Shading adjoint of every centre-sample pixel with a colour gradient.
+__global__ void __launch_bounds__(256) shade_adjoint_kernel(CallTable tab, CamDev cam, LightsDev Ls,
+                                                            const uint64_t *__restrict__ vis_c,
+                                                            const float4 *__restrict__ dC, BwdSinks sinks,
+                                                            uint32_t *status) {
+    __shared__ uint64_t s_bases[HM_MAX_GROOMS_PER_CALL + 1];
+    if (threadIdx.x <= tab.n) {
+        uint64_t b = 0;
+        for (int i = 0; i < (int)threadIdx.x; ++i) b += (uint64_t)tab.g[i].S;
+        s_bases[threadIdx.x] = b;
+    }
+    __syncthreads();
+    const int64_t npx = (int64_t)cam.W * cam.H;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npx; p += (int64_t)gridDim.x * blockDim.x) {
+        const float4 g4 = __ldg(&dC[p]);
+        if (g4.x == 0.f && g4.y == 0.f && g4.z == 0.f) continue;
+        const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + p));
+        if (key_empty(kg)) continue;
+        const int px = (int)(p % cam.W), py = (int)(p / cam.W);
+        const Decoded d = decode_key(tab, s_bases, cam, kg, px, py, status);
+        if (!d.ok) continue;
+        const GroomDev &g = tab.g[d.gi];
+        const float4 a = __ldg(&g.albedo[d.s]);
+        float3 dX, dT, dalb;
+        shade_adjoint(d.X, d.T, f3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt, f3(g4.x, g4.y, g4.z), dX, dT,
+                      dalb);
+        float *ga = sinks.galb[d.gi];
+        if (ga) {
+            atomicAdd(ga + 3 * d.s + 0, dalb.x);
+            atomicAdd(ga + 3 * d.s + 1, dalb.y);
+            atomicAdd(ga + 3 * d.s + 2, dalb.z);
+        }
+        Sink sk;
+        sk.glv = sinks.glv[d.gi];
+        sk.V = g.V;
+        if (sk.glv) {
+            const Root r = make_root(g, d.s, __ldg(&g.sface[d.s]));
+            geometry_adjoint(g, r, d.C, d.j, d.t, dX, dT, sk);
+        }
+    }
+}
+
+__global__ void zero_float4_kernel(float4 *p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+size_t adjoint_smem_bytes(int radius) {
+    const int sw = kTileW + 2 * radius, sh = kTileH + 2 * radius, ns = sw * sh;
+    size_t b = sizeof(uint64_t) * (HM_MAX_GROOMS_PER_CALL + 1);
+    b += 2 * sizeof(float3) * ns;
+    b += sizeof(int) * ns;
+    b += sizeof(uint16_t) * ((ns + 7) & ~7) + 16;
+    b += sizeof(float2) * 2 * kResolveThreads;
+    b += 2 * kResolveThreads;
+    b += ns;
+    return (b + 15) & ~(size_t)15;
+}
+
+cudaError_t launch_resolve_adjoint(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
+                                   const uint64_t *vis_c, const uint64_t *vis_a, const float *grad_rgba,
+                                   float *const *glv, float *const *galb, void *scratch, uint32_t *status,
+                                   cudaStream_t st) {
+    const int64_t npx = (int64_t)cam.W * cam.H;
+    float4 *dC = static_cast<float4 *>(scratch);
+    BwdSinks sinks;
+    for (int i = 0; i < HM_MAX_GROOMS_PER_CALL; ++i) {
+        sinks.glv[i] = (i < tab.n && glv) ? glv[i] : nullptr;
+        sinks.galb[i] = (i < tab.n && galb) ? galb[i] : nullptr;
+    }
+    const int sms = num_sms();
+    zero_float4_kernel<<<sms * 8, 256, 0, st>>>(dC, npx);
+    const int R = fp.enabled ? fp.radius : 0;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(resolve_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)adjoint_smem_bytes(HM_MAX_FILTER_RADIUS));
+        attr_set = true;
+    }
+    dim3 grid((cam.W + kTileW - 1) / kTileW, (cam.H + kTileH - 1) / kTileH);
+    resolve_adjoint_kernel<<<grid, kResolveThreads, adjoint_smem_bytes(R), st>>>(
+        tab, cam, Ls, fp, vis_c, vis_a, reinterpret_cast<const float4 *>(grad_rgba), dC, sinks, status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t want = (npx + 255) / 256;
+    const int g2 = (int)(want < (int64_t)sms * 16 ? (want > 0 ? want : 1) : (int64_t)sms * 16);
+    shade_adjoint_kernel<<<g2, 256, 0, st>>>(tab, cam, Ls, vis_c, dC, sinks, status);
+    return cudaGetLastError();
+}
+
+}  // namespace hm

@@ -35,6 +35,10 @@ cudaError_t launch_probe_atomic_min(uint64_t *buf, int64_t n, int rounds, int pa
 cudaError_t launch_resolve(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                            const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status,
                            cudaStream_t st);
+cudaError_t launch_resolve_adjoint(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
+                                   const uint64_t *vis_c, const uint64_t *vis_a, const float *grad_rgba,
+                                   float *const *glv, float *const *galb, void *scratch, uint32_t *status,
+                                   cudaStream_t st);
 cudaError_t launch_pack_float3(const float *src, float4 *dst, int64_t n, cudaStream_t st);
 
 }  // namespace hm

@@ -12,88 +12,9 @@
 
 #include "hm_device.cuh"
 #include "hm_kernels.h"
+#include "hm_value.cuh"
 
 namespace hm {
-
-constexpr int kTileW = 32, kTileH = 16;
-constexpr int kResolveThreads = kTileW * kTileH;
-
-__device__ __forceinline__ float3 shade(float3 X, float3 T, float3 alb, const CamDev &cam, const LightsDev &Ls,
-                                        float rough, float tilt) {
-    float3 V = make_float3(cam.cam_pos[0] - X.x, cam.cam_pos[1] - X.y, cam.cam_pos[2] - X.z);
-    float vn = rsqrtf(fmaxf(V.x * V.x + V.y * V.y + V.z * V.z, 1e-30f));
-    V = make_float3(V.x * vn, V.y * vn, V.z * vn);
-    const float sa = sinf(tilt);
-    const float inv2b2 = 1.0f / (2.0f * rough * rough);
-    float3 out = make_float3(Ls.ambient * alb.x, Ls.ambient * alb.y, Ls.ambient * alb.z);
-    for (int l = 0; l < Ls.n; ++l) {
-        const float tl = T.x * Ls.dir[l][0] + T.y * Ls.dir[l][1] + T.z * Ls.dir[l][2];
-        const float tv = T.x * V.x + T.y * V.y + T.z * V.z;
-        const float sin2 = 1.0f - tl * tl;
-        const float kk = Ls.kd * (sin2 > 0.0f ? sqrtf(sin2) : 0.0f);
-        const float u = (tl + tv) * 0.5f + sa;
-        const float fs = Ls.ks * __expf(-(u * u) * inv2b2);
-        out.x += Ls.rad[l][0] * (alb.x * kk + fs);
-        out.y += Ls.rad[l][1] * (alb.y * kk + fs);
-        out.z += Ls.rad[l][2] * (alb.z * kk + fs);
-    }
-    return out;
-}
-
-struct Recon {
-    float3 S;
-    float W;
-    int hc, ha;
-};
-
-// Normalized bilateral sum around tile pixel (lx, ly) against reference depth
-// `ref`, screen tangent (tsx, tsy) / iso, with or without the colour term
-// (Eqs. 6-7), plus the strip hit counts of Sec. 3.3.3.
-__device__ __forceinline__ Recon reconstruct(const int *s_dg, const uint8_t *s_fa, const float3 *s_col, int sw,
-                                             int lx, int ly, int gx, int gy, int W, int H, int R, int ref, float tsx,
-                                             float tsy, bool iso, bool use_color, float3 Cp, const FilterDev &fp) {
-    Recon o;
-    o.S = make_float3(0.f, 0.f, 0.f);
-    o.W = 0.f;
-    o.hc = 0;
-    o.ha = 0;
-    for (int dy = -R; dy <= R; ++dy) {
-        const int qy = gy + dy;
-        if (qy < 0 || qy >= H) continue;
-        const int row = (ly + dy + R) * sw + R + lx;
-        for (int dx = -R; dx <= R; ++dx) {
-            const int qx = gx + dx;
-            if (qx < 0 || qx >= W) continue;
-            const int idx = row + dx;
-            float dpar, perp2;
-            const bool strip = in_strip(iso, tsx, tsy, dx, dy, fp.hw2, dpar, perp2);
-            const int dq = s_dg[idx];
-            const bool gq = dq >= 0;
-            if (strip) {
-                o.hc += gq;
-                o.ha += s_fa[idx];
-            }
-            if (gq && abs(dq - ref) <= fp.drej) {
-                float ws;
-                if (iso)
-                    ws = __expf(-(float)(dx * dx + dy * dy) * fp.inv_siso2);
-                else
-                    ws = __expf(-(dpar * dpar) * fp.inv_spar2 - perp2 * fp.inv_sperp2);
-                const float3 cq = s_col[idx];
-                float w = ws;
-                if (use_color) {
-                    const float ex = Cp.x - cq.x, ey = Cp.y - cq.y, ez = Cp.z - cq.z;
-                    w *= __expf(-(ex * ex + ey * ey + ez * ez) * fp.inv_sc2);
-                }
-                o.S.x += w * cq.x;
-                o.S.y += w * cq.y;
-                o.S.z += w * cq.z;
-                o.W += w;
-            }
-        }
-    }
-    return o;
-}
 
 __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(CallTable tab, CamDev cam, LightsDev Ls,
                                                                   FilterDev fp, const uint64_t *__restrict__ vis_c,
@@ -107,7 +28,8 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(CallTable tab,
     float3 *s_col = reinterpret_cast<float3 *>(s_bases + HM_MAX_GROOMS_PER_CALL + 1);
     int *s_dg = reinterpret_cast<int *>(s_col + ns);
     uint16_t *s_list = reinterpret_cast<uint16_t *>(s_dg + ns);
-    float2 *s_tsG = reinterpret_cast<float2 *>(s_list + ((ns + 7) & ~7));
+    float2 *s_tsG = reinterpret_cast<float2 *>(
+        (reinterpret_cast<uintptr_t>(s_list + ((ns + 7) & ~7)) + 15) & ~(uintptr_t)15);
     float2 *s_tsA = s_tsG + kResolveThreads;
     uint8_t *s_isoG = reinterpret_cast<uint8_t *>(s_tsA + kResolveThreads);
     uint8_t *s_isoA = s_isoG + kResolveThreads;
@@ -222,7 +144,7 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(CallTable tab,
             const Recon ra = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y,
                                          s_isoA[tid] != 0, false, Cp, fp);
             float3 c = CG;
-            if (ra.W > 0.0f) {
+            if (ra.cnt > 0) {
                 const float al = __fdiv_rn((float)ra.hc, (float)ra.ha);
                 const float iw = 1.0f / ra.W;
                 c = make_float3(al * (ra.S.x * iw) + (1.0f - al) * CG.x, al * (ra.S.y * iw) + (1.0f - al) * CG.y,
@@ -236,7 +158,7 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(CallTable tab,
         const float2 tsa = s_tsA[tid];
         const Recon ra = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y,
                                      s_isoA[tid] != 0, false, make_float3(0.f, 0.f, 0.f), fp);
-        if (ra.W > 0.0f) {
+        if (ra.cnt > 0) {
             const float iw = 1.0f / ra.W;
             out = make_float4(ra.S.x * iw, ra.S.y * iw, ra.S.z * iw, __fdiv_rn((float)ra.hc, (float)ra.ha));
         }
@@ -249,7 +171,7 @@ size_t resolve_smem_bytes(int radius) {
     size_t b = sizeof(uint64_t) * (HM_MAX_GROOMS_PER_CALL + 1);
     b += sizeof(float3) * ns;
     b += sizeof(int) * ns;
-    b += sizeof(uint16_t) * ((ns + 7) & ~7);
+    b += sizeof(uint16_t) * ((ns + 7) & ~7) + 16;
     b += sizeof(float2) * 2 * kResolveThreads;
     b += 2 * kResolveThreads;
     b += ns;

@@ -1,0 +1,120 @@
+// hm_value.cuh -- the continuous ("value") part of the deferred resolve,
+// shared by the forward resolve and its adjoint: the shading model (Sec. 3.4)
+// and the normalized elliptical bilateral sum with strip hit counts
+// (Sec. 3.3.1-3.3.3).  Masks inside come from the exact decision layer in
+// hm_device.cuh; the arithmetic here is ordinary FP32 (FMA allowed).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hm_device.cuh"
+#include "hm_kernels.h"
+
+namespace hm {
+
+constexpr int kTileW = 32, kTileH = 16;
+constexpr int kResolveThreads = kTileW * kTileH;
+
+__device__ __forceinline__ float3 shade(float3 X, float3 T, float3 alb, const CamDev &cam, const LightsDev &Ls,
+                                        float rough, float tilt) {
+    float3 V = make_float3(cam.cam_pos[0] - X.x, cam.cam_pos[1] - X.y, cam.cam_pos[2] - X.z);
+    float vn = rsqrtf(fmaxf(V.x * V.x + V.y * V.y + V.z * V.z, 1e-30f));
+    V = make_float3(V.x * vn, V.y * vn, V.z * vn);
+    const float sa = sinf(tilt);
+    const float inv2b2 = 1.0f / (2.0f * rough * rough);
+    float3 out = make_float3(Ls.ambient * alb.x, Ls.ambient * alb.y, Ls.ambient * alb.z);
+    for (int l = 0; l < Ls.n; ++l) {
+        const float tl = T.x * Ls.dir[l][0] + T.y * Ls.dir[l][1] + T.z * Ls.dir[l][2];
+        const float tv = T.x * V.x + T.y * V.y + T.z * V.z;
+        const float sin2 = 1.0f - tl * tl;
+        const float kk = Ls.kd * (sin2 > 0.0f ? sqrtf(sin2) : 0.0f);
+        const float u = (tl + tv) * 0.5f + sa;
+        const float fs = Ls.ks * __expf(-(u * u) * inv2b2);
+        out.x += Ls.rad[l][0] * (alb.x * kk + fs);
+        out.y += Ls.rad[l][1] * (alb.y * kk + fs);
+        out.z += Ls.rad[l][2] * (alb.z * kk + fs);
+    }
+    return out;
+}
+
+struct Recon {
+    float3 S;       // sum of w' C over contributing neighbours
+    float W;        // sum of w', where w' = w / max w (so W >= 1 when cnt > 0)
+    float m;        // exponent of the largest weight: max w = exp(-m)
+    int cnt;        // contributing neighbours (exact)
+    int hc, ha;     // strip hit counts
+};
+
+// Exponent e of the bilateral weight w = exp(-e) of offset (dx, dy) (Eq. 7):
+// elliptical spatial term, or the isotropic fallback, plus the colour term.
+__device__ __forceinline__ float weight_exponent(bool iso, int dx, int dy, float dpar, float perp2, bool use_color,
+                                                 float3 Cp, float3 cq, const FilterDev &fp) {
+    float e = iso ? (float)(dx * dx + dy * dy) * fp.inv_siso2 : (dpar * dpar) * fp.inv_spar2 + perp2 * fp.inv_sperp2;
+    if (use_color) {
+        const float ex = Cp.x - cq.x, ey = Cp.y - cq.y, ez = Cp.z - cq.z;
+        e += (ex * ex + ey * ey + ez * ez) * fp.inv_sc2;
+    }
+    return e;
+}
+
+// Normalized bilateral sum around tile pixel (lx, ly) against reference depth
+// `ref`, screen tangent (tsx, tsy) / iso, with or without the colour term
+// (Eqs. 6-7), plus the strip hit counts of Sec. 3.3.3.  The weights are
+// accumulated relative to the largest one seen so far (online rescaling),
+// so tiny weights far off the strand axis never underflow the normalizer.
+__device__ __forceinline__ Recon reconstruct(const int *s_dg, const uint8_t *s_fa, const float3 *s_col, int sw,
+                                             int lx, int ly, int gx, int gy, int W, int H, int R, int ref, float tsx,
+                                             float tsy, bool iso, bool use_color, float3 Cp, const FilterDev &fp) {
+    Recon o;
+    o.S = make_float3(0.f, 0.f, 0.f);
+    o.W = 0.f;
+    o.m = 0.f;
+    o.cnt = 0;
+    o.hc = 0;
+    o.ha = 0;
+    for (int dy = -R; dy <= R; ++dy) {
+        const int qy = gy + dy;
+        if (qy < 0 || qy >= H) continue;
+        const int row = (ly + dy + R) * sw + R + lx;
+        for (int dx = -R; dx <= R; ++dx) {
+            const int qx = gx + dx;
+            if (qx < 0 || qx >= W) continue;
+            const int idx = row + dx;
+            float dpar, perp2;
+            const bool strip = in_strip(iso, tsx, tsy, dx, dy, fp.hw2, dpar, perp2);
+            const int dq = s_dg[idx];
+            const bool gq = dq >= 0;
+            if (strip) {
+                o.hc += gq;
+                o.ha += s_fa[idx];
+            }
+            if (gq && abs(dq - ref) <= fp.drej) {
+                const float3 cq = s_col[idx];
+                const float e = weight_exponent(iso, dx, dy, dpar, perp2, use_color, Cp, cq, fp);
+                if (o.cnt == 0) {
+                    o.m = e;
+                    o.S = cq;
+                    o.W = 1.0f;
+                } else if (e >= o.m) {
+                    const float w = __expf(o.m - e);
+                    o.S.x += w * cq.x;
+                    o.S.y += w * cq.y;
+                    o.S.z += w * cq.z;
+                    o.W += w;
+                } else {
+                    const float sc = __expf(e - o.m);
+                    o.S.x = o.S.x * sc + cq.x;
+                    o.S.y = o.S.y * sc + cq.y;
+                    o.S.z = o.S.z * sc + cq.z;
+                    o.W = o.W * sc + 1.0f;
+                    o.m = e;
+                }
+                o.cnt += 1;
+            }
+        }
+    }
+    return o;
+}
+
+}  // namespace hm

@@ -273,6 +273,9 @@ def set_phase_events(events):
     if not events:
         check(lib().hm_set_phase_events(None, 0))
         return
+    for e in events:
+        if e is not None and not e.cuda_event:
+            raise ValueError("record each torch.cuda.Event once before handing it to the library")
     arr = (ctypes.c_void_p * len(events))(*[(e.cuda_event if e is not None else None) for e in events])
     check(lib().hm_set_phase_events(arr, len(events)))
 

@@ -1,0 +1,96 @@
+"""Adjoint kernel vs the FP64 oracle's autograd gradient (visibility held
+fixed), through hm_shade_backward / the torch.autograd.Function.
+
+Loss: L2 norm of the premultiplied RGB against a target rendered by the
+oracle from the same hair mesh with every layer vertex perturbed by
+N(0, 2 mm).  Criterion: norm-wise relative error <= 1e-2, and per entry
+<= 1e-2 relative for entries above 1e-3 of the largest.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import value64 as v64
+from paper_2607_04230_b300 import synth
+
+from _parity import assert_keys_equal, oracle_keys
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_image(scene, layer_verts):
+    g = scene.grooms[0]
+    gp = synth.Groom(layer_verts=layer_verts, faces=g.faces, strand_face=g.strand_face, strand_bary=g.strand_bary,
+                     strand_albedo=g.strand_albedo, bundle_delta=g.bundle_delta,
+                     segments_per_strand=g.segments_per_strand)
+    sp = synth.Scene([gp], scene.camera, scene.lights, scene.filt, scene.lod)
+    lods, vc, va, _ = oracle_keys(sp)
+    dec = oracle.resolve_decisions(sp.grooms, sp.camera, lods, sp.filt, vc, va)
+    rgba, pix = v64.resolve([v64.GroomT(gp, lods[0][1], 0)], sp.camera, sp.lights, sp.filt, vc, va, dec)
+    img = v64.full_image(rgba, pix, sp.camera.width, sp.camera.height).reshape(-1, 4)
+    return (img[:, :3] * img[:, 3:4]).numpy()
+
+
+def _compare(g_gpu, g_ref, what):
+    g_gpu = g_gpu.reshape(-1).astype(np.float64)
+    g_ref = g_ref.reshape(-1)
+    nrm = np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref)
+    assert nrm <= 1e-2, f"{what}: norm-wise relative error {nrm:.3e}"
+    big = np.abs(g_ref) > 1e-3 * np.abs(g_ref).max()
+    rel = np.abs(g_gpu[big] - g_ref[big]) / np.abs(g_ref[big])
+    assert rel.max() <= 1e-2, f"{what}: worst per-entry relative error {rel.max():.3e} over {big.sum()} entries"
+    return nrm, rel.max()
+
+
+def _grad_case(scene):
+    from paper_2607_04230_b300 import autograd, hm
+    g = scene.grooms[0]
+    W, H = scene.camera.width, scene.camera.height
+    target = _oracle_image(scene, synth.perturbed_layer_verts(g))
+    # GPU: forward + hand-written adjoint
+    handle = hm.upload_scene(scene)[0]
+    frame = hm.Frame(W, H)
+    lv = torch.from_numpy(g.layer_verts).cuda().requires_grad_(True)
+    alb = torch.from_numpy(g.strand_albedo).cuda().requires_grad_(True)
+    rgba = autograd.render(handle, scene, frame, lv, alb)
+    t = torch.from_numpy(target).float().cuda()
+    loss = torch.sqrt(((rgba.reshape(-1, 4)[:, :3] * rgba.reshape(-1, 4)[:, 3:4] - t) ** 2).sum())
+    loss.backward()
+    torch.cuda.synchronize()
+    hm.get_device_status()
+    # oracle: FP64 forward with the same (bit-exact) visibility, autograd
+    lods, vc, va, _ = oracle_keys(scene)
+    gk, ak = frame.keys_numpy()
+    assert_keys_equal(gk, vc, "centre layer")
+    assert_keys_equal(ak, va, "conservative layer")
+    dec = oracle.resolve_decisions(scene.grooms, scene.camera, lods, scene.filt, vc, va)
+    lv64 = torch.from_numpy(g.layer_verts.astype(np.float64)).requires_grad_(True)
+    alb64 = torch.from_numpy(g.strand_albedo.astype(np.float64)).requires_grad_(True)
+    gt = v64.GroomT(g, lods[0][1], 0, layer_verts=lv64, albedo=alb64)
+    r64, pix = v64.resolve([gt], scene.camera, scene.lights, scene.filt, vc, va, dec)
+    img = torch.zeros((W * H, 3), dtype=torch.float64).index_put((torch.from_numpy(pix),), r64[:, :3] * r64[:, 3:4])
+    l64 = torch.sqrt(((img - torch.from_numpy(target)) ** 2).sum())
+    l64.backward()
+    assert abs(loss.item() - l64.item()) <= 1e-4 * l64.item()
+    out = {}
+    out["layer_verts"] = _compare(lv.grad.cpu().numpy(), lv64.grad.numpy(), "layer-vertex gradient")
+    out["albedo"] = _compare(alb.grad.cpu().numpy(), alb64.grad.numpy(), "albedo gradient")
+    return out
+
+
+def test_gradient_small_scene():
+    sc = synth.tiny_scene(21, width=96, height=80, num_strands=400, dist_m=0.3)
+    _grad_case(sc)
+
+
+def test_gradient_mismatch_and_promoted_heavy():
+    # sparse strands far away: mostly promoted pixels and depth mismatches
+    sc = synth.tiny_scene(22, width=128, height=96, num_strands=1500, dist_m=0.9, jitter_m=0.006)
+    _grad_case(sc)
+
+
+def test_gradient_512_workload():
+    """256 scalp triangles, 6 layers, 20k strands x 12 segments, 512x512."""
+    out = _grad_case(synth.scene_grad_512())
+    print(out)
