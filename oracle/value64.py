@@ -251,9 +251,12 @@ def resolve(gts, cam, lights, filt, vis_c, vis_a, dec, pixels=None):
         TsA[torch.from_numpy(aidx)] = screen_tangent(XA, TA, cam)
 
     r = int(filt.radius)
-    sp = float(np.float32(filt.s_par)) * r
-    sq = float(np.float32(filt.s_perp)) * r
-    siso = float(np.float32(filt.iso_scale)) * r
+    # Eq. 7 scales the standard deviations by r; reading: a radius-0 window
+    # (the pixel alone) uses r = 1 there, where the weights cannot matter
+    rs = max(r, 1)
+    sp = float(np.float32(filt.s_par)) * rs
+    sq = float(np.float32(filt.s_perp)) * rs
+    siso = float(np.float32(filt.iso_scale)) * rs
     sc = float(np.float32(filt.sigma_c))
     px = torch.from_numpy(pixels % W)
     py = torch.from_numpy(pixels // W)

@@ -111,11 +111,10 @@ __device__ void control_point_adjoint(const GroomDev &g, const Root &r, int C, i
 // T = unit(T_j + (T_{j+1} - T_j) t), t fixed, to the control points.
 __device__ void geometry_adjoint(const GroomDev &g, const Root &r, int C, int j, float t, float3 dX, float3 dT,
                                  const Sink &sk) {
-    const float3 p0 = control_pt(g, r, C, j);
-    const float3 p1 = control_pt(g, r, C, j + 1);
+    float3 cp[4];
+    control_pts<4>(g, r, C, j - 1, cp);
     const bool has_m = j >= 1, has_p = j + 2 <= C - 1;
-    const float3 pm = has_m ? control_pt(g, r, C, j - 1) : p0;
-    const float3 pp = has_p ? control_pt(g, r, C, j + 2) : p1;
+    const float3 pm = cp[0], p0 = cp[1], p1 = cp[2], pp = cp[3];
     const float3 va = (j == 0) ? sub3(p1, p0) : sub3(p1, pm);
     const float3 vb = (j + 1 == C - 1) ? sub3(p1, p0) : sub3(pp, p0);
     const float na = len3(va), nb = len3(vb);

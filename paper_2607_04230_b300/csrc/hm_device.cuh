@@ -156,6 +156,48 @@ __device__ __forceinline__ float3 control_pt(const GroomDev &g, const Root &r, i
         fadd(fadd(fadd(fmul(h00, P0.z), fmul(h10, m0.z)), fmul(h01, P1.z)), fmul(h11, m1.z)));
 }
 
+// Control points j0, j0+1, ..., j0+N-1 (each clamped to [0, C-1]); the
+// layer points, tangents and chord of an interval are evaluated once and
+// reused by consecutive control points in the same interval.  Each result is
+// bit-identical to control_pt().
+template <int N>
+__device__ __forceinline__ void control_pts(const GroomDev &g, const Root &r, int C, int j0, float3 (&out)[N]) {
+    const int L = g.L;
+    int kcur = -1;
+    float3 P0 = make_float3(0.f, 0.f, 0.f), P1 = P0, m0 = P0, m1 = P0;
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        int j = j0 + c;
+        j = j < 0 ? 0 : (j > C - 1 ? C - 1 : j);
+        const int x = j * (L - 1);
+        int k = x / (C - 1);
+        if (k > L - 2) k = L - 2;
+        if (k != kcur) {
+            P0 = layer_pt(g, r, k);
+            P1 = layer_pt(g, r, k + 1);
+            const float3 Pm = (k > 0) ? layer_pt(g, r, k - 1) : P0;
+            const float3 P2 = (k + 2 <= L - 1) ? layer_pt(g, r, k + 2) : P1;
+            const float3 t0 = fd_tangent(k, L, Pm, P0, P1);
+            const float3 t1 = fd_tangent(k + 1, L, P0, P1, P2);
+            const float ell = __fsqrt_rn(v3len2(v3sub(P1, P0)));
+            m0 = make_float3(fmul(t0.x, ell), fmul(t0.y, ell), fmul(t0.z, ell));
+            m1 = make_float3(fmul(t1.x, ell), fmul(t1.y, ell), fmul(t1.z, ell));
+            kcur = k;
+        }
+        const float s = fdiv(__int2float_rn(x - k * (C - 1)), __int2float_rn(C - 1));
+        const float s2 = fmul(s, s);
+        const float s3 = fmul(s2, s);
+        const float h00 = fadd(fsub(fmul(2.0f, s3), fmul(3.0f, s2)), 1.0f);
+        const float h10 = fadd(fsub(s3, fmul(2.0f, s2)), s);
+        const float h01 = fsub(fmul(3.0f, s2), fmul(2.0f, s3));
+        const float h11 = fsub(s3, s2);
+        out[c] = make_float3(
+            fadd(fadd(fadd(fmul(h00, P0.x), fmul(h10, m0.x)), fmul(h01, P1.x)), fmul(h11, m1.x)),
+            fadd(fadd(fadd(fmul(h00, P0.y), fmul(h10, m0.y)), fmul(h01, P1.y)), fmul(h11, m1.y)),
+            fadd(fadd(fadd(fmul(h00, P0.z), fmul(h10, m0.z)), fmul(h01, P1.z)), fmul(h11, m1.z)));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // projection, 16.8 snap, depth (Sec. 3.1.2)
 // ---------------------------------------------------------------------------
@@ -338,10 +380,9 @@ __device__ __forceinline__ Decoded decode_key(const CallTable &tab, const uint64
     int C = (int)g.lod[f].y;
     if (j + 1 >= C) { atomicOr(status, kStatusBadKey); return d; }
     Root r = make_root(g, s, f);
-    float3 p0 = control_pt(g, r, C, j);
-    float3 p1 = control_pt(g, r, C, j + 1);
-    float3 pm = (j >= 1) ? control_pt(g, r, C, j - 1) : p0;
-    float3 pp = (j + 2 <= C - 1) ? control_pt(g, r, C, j + 2) : p1;
+    float3 cp[4];
+    control_pts<4>(g, r, C, j - 1, cp);
+    const float3 pm = cp[0], p0 = cp[1], p1 = cp[2], pp = cp[3];
     Proj a = project(cam, p0), b = project(cam, p1);
     float t = seg_t(a.X, a.Y, b.X, b.Y, 256 * (int64_t)px + 128, 256 * (int64_t)py + 128);
     d.X = make_float3(fadd(p0.x, fmul(fsub(p1.x, p0.x), t)), fadd(p0.y, fmul(fsub(p1.y, p0.y), t)),

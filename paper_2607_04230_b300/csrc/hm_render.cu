@@ -205,11 +205,20 @@ struct SegRec {
     uint32_t id_lo, id_hi;       // payload strand << 7 | segment
     int32_t start;               // first work item of this segment
     int32_t xmajor;
+    float fden;                  // float(|B - A|^2), the depth parameter's denominator
+    int32_t pad_;
 };
 
 constexpr int kRasterThreads = 256;
 constexpr int kRasterWarps = kRasterThreads / 32;
 
+// The exact segment-vs-box predicate (bounding boxes overlap and the box's
+// corners are not all strictly on one side of the line) in incremental form:
+// the corner cross products are e0 + h (sy dX - sx dY) for sx, sy = +-1, with
+// e0 = dX (cy - YA) - dY (cx - XA) the cross product at the box centre, so
+// "min <= 0 <= max" is |e0| <= h (|dX| + |dY|).  e0 and the depth numerator
+// num = (cx - XA) dX + (cy - YA) dY change by constants from one pixel to the
+// next along the minor axis.
 template <bool kPrecheck>
 __global__ void __launch_bounds__(kRasterThreads) raster_kernel(CallTable tab, CamDev cam, uint64_t *__restrict__ vis_c,
                                                                 uint64_t *__restrict__ vis_a, hm_frame_stats *stats) {
@@ -251,8 +260,10 @@ __global__ void __launch_bounds__(kRasterThreads) raster_kernel(CallTable tab, C
             const int64_t s = (int64_t)__ldg(&g.faces[f]).w + sl / (uint32_t)(C - 1);
             const int j = (int)(sl % (uint32_t)(C - 1));
             const Root rt = make_root(g, s, f);
-            const Proj A = project(cam, control_pt(g, rt, C, j));
-            const Proj B = project(cam, control_pt(g, rt, C, j + 1));
+            float3 cp[2];
+            control_pts<2>(g, rt, C, j, cp);
+            const Proj A = project(cam, cp[0]);
+            const Proj B = project(cam, cp[1]);
             if (A.valid && B.valid) {
                 const bool xm = abs(B.X - A.X) >= abs(B.Y - A.Y);
                 r.uA = xm ? A.X : A.Y;
@@ -266,6 +277,8 @@ __global__ void __launch_bounds__(kRasterThreads) raster_kernel(CallTable tab, C
                 r.id_lo = (uint32_t)id;
                 r.id_hi = (uint32_t)(id >> 32);
                 r.xmajor = xm;
+                const int64_t dX = (int64_t)B.X - A.X, dY = (int64_t)B.Y - A.Y;
+                r.fden = __ll2float_rn(dX * dX + dY * dY);
                 const int du = xm ? W : H, dv = xm ? H : W;
                 const int32_t umin = min(r.uA, r.uB), umax = max(r.uA, r.uB);
                 const int32_t vmin = min(r.vA, r.vB), vmax = max(r.vA, r.vB);
@@ -301,6 +314,7 @@ __global__ void __launch_bounds__(kRasterThreads) raster_kernel(CallTable tab, C
             const int i = q.ilo + (item - q.start);
             const int32_t du = q.uB - q.uA, dvv = q.vB - q.vA;
             const int32_t umin = min(q.uA, q.uB), umax = max(q.uA, q.uB);
+            const int32_t vmin = min(q.vA, q.vB), vmax = max(q.vA, q.vB);
             const int32_t ua = max(256 * i, umin), ub = min(256 * i + 256, umax);
             float flo, fhi;
             if (du == 0) {
@@ -319,15 +333,30 @@ __global__ void __launch_bounds__(kRasterThreads) raster_kernel(CallTable tab, C
             const int dimv = q.xmajor ? H : W;
             const int mlo = (int)max(((vlo + 255) >> 8) - 1, (int64_t)0);
             const int mhi = (int)min(vhi >> 8, (int64_t)(dimv - 1));
-            const int32_t XA = q.xmajor ? q.uA : q.vA, YA = q.xmajor ? q.vA : q.uA;
-            const int32_t XB = q.xmajor ? q.uB : q.vB, YB = q.xmajor ? q.vB : q.uB;
+            if (mlo > mhi) continue;
+            // (u, v) frame: e0 = du (cv - vA) - dv (cu - uA) is the x/y cross
+            // product up to sign, num is symmetric; both step along v
+            const int32_t cu = 256 * i + 128;
+            const int64_t du64 = du, dv64 = dvv;
+            int64_t e0 = du64 * (int64_t)(256 * mlo + 128 - q.vA) - dv64 * (int64_t)(cu - q.uA);
+            int64_t num = (int64_t)(cu - q.uA) * du64 + (int64_t)(256 * mlo + 128 - q.vA) * dv64;
+            const int64_t de = 256 * du64, dn = 256 * dv64;
+            const int64_t span = (int64_t)abs(du) + (int64_t)abs(dvv);
+            const int64_t k_cons = 128 * span, k_cen = (int64_t)q.hc * span;
+            // box overlap along u for half-width h: umin <= cu + h and umax >= cu - h
+            const bool ucen = (umin <= cu + q.hc) && (umax >= cu - q.hc);
             const uint64_t id = ((uint64_t)q.id_hi << 32) | q.id_lo;
-            for (int m = mlo; m <= mhi; ++m) {
+            const bool degenerate = (du == 0 && dvv == 0);
+            for (int m = mlo; m <= mhi; ++m, e0 += de, num += dn) {
+                const int32_t cv = 256 * m + 128;
+                // conservative: v-overlap (u-overlap holds by construction) and line test
+                if (vmin > cv + 128 || vmax < cv - 128) continue;
+                if (e0 > k_cons || e0 < -k_cons) continue;
+                const bool cen = ucen && vmin <= cv + q.hc && vmax >= cv - q.hc && e0 <= k_cen && e0 >= -k_cen;
+                float t = 0.0f;
+                if (!degenerate) t = fclamp(fdiv(__ll2float_rn(num), q.fden), 0.0f, 1.0f);
+                const uint64_t key = ((uint64_t)depth24(q.zA, q.zB, t) << 40) | id;
                 const int px = q.xmajor ? i : m, py = q.xmajor ? m : i;
-                const int64_t cx = 256 * (int64_t)px + 128, cy = 256 * (int64_t)py + 128;
-                if (!seg_covers(XA, YA, XB, YB, cx, cy, 128)) continue;
-                const bool cen = (q.hc >= 128) || seg_covers(XA, YA, XB, YB, cx, cy, q.hc);
-                const uint64_t key = ((uint64_t)depth24(q.zA, q.zB, seg_t(XA, YA, XB, YB, cx, cy)) << 40) | id;
                 const int64_t p = (int64_t)py * W + px;
                 n_cons += 1;
                 n_cen += cen;

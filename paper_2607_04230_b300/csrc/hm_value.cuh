@@ -73,21 +73,21 @@ __device__ __forceinline__ Recon reconstruct(const int *s_dg, const uint8_t *s_f
     o.cnt = 0;
     o.hc = 0;
     o.ha = 0;
+    // Staged pixels outside the screen hold neither layer (s_dg < 0,
+    // s_fa = 0), so skipping empty taps also clips the window to the screen.
     for (int dy = -R; dy <= R; ++dy) {
-        const int qy = gy + dy;
-        if (qy < 0 || qy >= H) continue;
         const int row = (ly + dy + R) * sw + R + lx;
         for (int dx = -R; dx <= R; ++dx) {
-            const int qx = gx + dx;
-            if (qx < 0 || qx >= W) continue;
             const int idx = row + dx;
+            const int dq = s_dg[idx];
+            const int fa = s_fa[idx];
+            if (dq < 0 && fa == 0) continue;
             float dpar, perp2;
             const bool strip = in_strip(iso, tsx, tsy, dx, dy, fp.hw2, dpar, perp2);
-            const int dq = s_dg[idx];
             const bool gq = dq >= 0;
             if (strip) {
                 o.hc += gq;
-                o.ha += s_fa[idx];
+                o.ha += fa;
             }
             if (gq && abs(dq - ref) <= fp.drej) {
                 const float3 cq = s_col[idx];

@@ -46,6 +46,8 @@ def assert_keys_equal(got, ref, what):
 
 def assert_rgba_close(gpu_rgba, ref_rgba, pixels, tol=RGBA_TOL):
     g = gpu_rgba.reshape(-1, 4)[pixels]
+    if len(pixels) == 0:
+        return 0.0
     err = np.abs(g - ref_rgba)
     i = np.unravel_index(np.argmax(err), err.shape)
     assert err.max() <= tol, f"max |rgba - oracle| = {err.max():.3e} at pixel {pixels[i[0]]} channel {i[1]}: " \
