@@ -219,6 +219,34 @@ hm_status hm_shade_backward(const hm_groom *grooms, int32_t n, const hm_camera *
 /* Bytes of scratch hm_shade_backward needs at this resolution. */
 size_t hm_backward_scratch_bytes(int32_t width, int32_t height);
 
+/* Largest frame (width * height) hm_shade_backward_noalloc accepts. */
+#define HM_NOALLOC_MAX_PIXELS 262144
+
+/* hm_shade_backward for callers that cannot allocate device memory.
+ * (The paper has no counterpart: it is a library convenience.)
+ * Some callers cannot call cudaMalloc at the point where they need the
+ * gradient: code that runs where an allocation's implicit device-wide
+ * synchronization is not acceptable (a real-time frame loop), or code whose
+ * device memory is owned by another allocator with a fixed budget.  This
+ * entry point takes the same inputs and outputs as hm_shade_backward but no
+ * d_scratch: its colour-gradient scratch is a static array of the library
+ * (HM_NOALLOC_MAX_PIXELS * 16 bytes = 4 MiB, held on every GPU that loads
+ * libhm until the process exits).  It calls no allocator.
+ *  - Frames larger than HM_NOALLOC_MAX_PIXELS pixels are rejected with
+ *    HM_ERR_CAPACITY before anything is launched.
+ *  - The first call on a device looks up the array's device address (one
+ *    cudaGetSymbolAddress with that device current); make that first call
+ *    before any stream capture.
+ *  - Every call on a device shares the one array and clears it on the
+ *    stream before use, so calls that overlap on the GPU (different streams
+ *    without ordering) race on it; order them.
+ * Other arguments, results and errors are those of hm_shade_backward. */
+hm_status hm_shade_backward_noalloc(const hm_groom *grooms, int32_t n, const hm_camera *cam,
+                                    const hm_lights *lights, const hm_filter_params *filt,
+                                    const uint64_t *d_vis_center, const uint64_t *d_vis_cons,
+                                    const float *d_grad_rgba, float *const *d_grad_layer_verts,
+                                    float *const *d_grad_albedo, void *stream);
+
 /* Copy the groom's current per-bundle LOD result (strands drawn N_LOD and
  * control points C, Eqs. 1-5) to host arrays of num_faces entries.
  * Synchronizes `stream`. */

@@ -531,3 +531,68 @@ hm_status hm_shade_backward(const hm_groom *grooms, int32_t n, const hm_camera *
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// hm_shade_backward_noalloc: the adjoint with its colour-gradient scratch in
+// a static device array instead of caller-allocated memory
+// ---------------------------------------------------------------------------
+namespace {
+
+// 16 bytes (one float4 colour gradient) per pixel of the largest frame.
+static __device__ __align__(256) float4 g_noalloc_scratch[HM_NOALLOC_MAX_PIXELS];
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (the host-side symbol is only a stand-in, never a device
+// address).  nullptr with the CUDA error in `err` when the lookup fails.
+float4 *noalloc_scratch(cudaError_t &err) {
+    static float4 *ptrs[64] = {nullptr};
+    err = cudaSuccess;
+    int dev = 0;
+    err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return nullptr;
+    if (dev < 0 || dev >= 64) {
+        err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    if (!ptrs[dev]) {
+        void *p = nullptr;
+        err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (err != cudaSuccess) return nullptr;
+        ptrs[dev] = static_cast<float4 *>(p);
+    }
+    return ptrs[dev];
+}
+
+}  // namespace
+
+extern "C" hm_status hm_shade_backward_noalloc(const hm_groom *grooms, int32_t n, const hm_camera *cam,
+                                               const hm_lights *lights, const hm_filter_params *filt,
+                                               const uint64_t *d_vis_center, const uint64_t *d_vis_cons,
+                                               const float *d_grad_rgba, float *const *d_grad_layer_verts,
+                                               float *const *d_grad_albedo, void *stream) {
+    hm_status st = check_camera(cam);
+    if (st != HM_OK) return st;
+    if ((int64_t)cam->width * cam->height > (int64_t)HM_NOALLOC_MAX_PIXELS)
+        return fail(HM_ERR_CAPACITY, "frame exceeds HM_NOALLOC_MAX_PIXELS pixels of static scratch");
+    if (!d_vis_center || !d_vis_cons || !d_grad_rgba) return fail(HM_ERR_INVALID_ARG, "buffer is NULL");
+    if ((reinterpret_cast<uintptr_t>(d_grad_rgba) & 15) || (reinterpret_cast<uintptr_t>(d_vis_center) & 7) ||
+        (reinterpret_cast<uintptr_t>(d_vis_cons) & 7))
+        return fail(HM_ERR_INVALID_ARG, "misaligned buffer");
+    hm::LightsDev ld;
+    hm::FilterDev fd;
+    if ((st = lights_dev(lights, ld)) != HM_OK) return st;
+    if ((st = filter_dev(filt, cam, fd)) != HM_OK) return st;
+    hm::CallTable tab;
+    st = build_table(grooms, n, tab);
+    if (st != HM_OK) return st;
+    uint32_t *sw = status_word();
+    if (!sw) return fail(HM_ERR_CUDA, "device status word unavailable");
+    cudaError_t e = cudaSuccess;
+    float4 *scratch = noalloc_scratch(e);
+    if (!scratch) return cuda_fail(e, "static scratch address");
+    HM_CUDA(hm::launch_resolve_adjoint(tab, cam_dev(cam), ld, fd, d_vis_center, d_vis_cons, d_grad_rgba,
+                                       d_grad_layer_verts, d_grad_albedo, scratch, sw,
+                                       static_cast<cudaStream_t>(stream)),
+            "resolve adjoint (static scratch)");
+    return HM_OK;
+}

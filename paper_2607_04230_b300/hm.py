@@ -92,6 +92,7 @@ def lib():
         "hm_render_visibility": [P, i32, P, P, P, P, i32, P, P],
         "hm_resolve_shade": [P, i32, P, P, P, P, P, P, P, P],
         "hm_shade_backward": [P, i32, P, P, P, P, P, P, P, P, P, P],
+        "hm_shade_backward_noalloc": [P, i32, P, P, P, P, P, P, P, P, P],
         "hm_get_lod": [P, P, P, P],
         "hm_groom_info": [P, P, P, P, P, P],
         "hm_get_device_status": [P],
@@ -287,6 +288,22 @@ def probe_atomic_min(buf, rounds: int = 1, pattern: int = 0, stream=None):
 def stats_dict(stats_tensor):
     v = stats_tensor.cpu().numpy().view(np.uint64)
     return {k: int(v[i]) for i, k in enumerate(STATS_FIELDS)}
+
+
+def shade_backward_noalloc(grooms, cam, lights, filt, vis_center, vis_cons, grad_rgba, grad_layer_verts,
+                           grad_albedo, stream=None):
+    """hm_shade_backward_noalloc: the adjoint without caller-allocated
+    scratch (frames up to NOALLOC_MAX_PIXELS pixels)."""
+    arr, n = _handles(grooms)
+    c, L, f = camera_struct(cam), lights_struct(lights), filter_struct(filt)
+    glv = (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in grad_layer_verts])
+    gal = (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in grad_albedo])
+    check(lib().hm_shade_backward_noalloc(arr, n, ctypes.byref(c), ctypes.byref(L), ctypes.byref(f),
+                                          _dptr(vis_center), _dptr(vis_cons), _dptr(grad_rgba), glv, gal,
+                                          _stream_ptr(stream)))
+
+
+NOALLOC_MAX_PIXELS = 262144
 
 
 def get_device_status(stream=None):
