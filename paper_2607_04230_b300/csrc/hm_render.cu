@@ -2,6 +2,7 @@
 // (arXiv 2607.04230, Sec. 3.1-3.2): clear, LOD pre-pass with the device work
 // list, and the strand-generation + 64-bit atomicMin rasterizer.
 #include <cstdint>
+#include <cstdlib>
 #include <cuda_runtime.h>
 
 #include "hm_device.cuh"
@@ -219,8 +220,8 @@ constexpr int kRasterWarps = kRasterThreads / 32;
 // "min <= 0 <= max" is |e0| <= h (|dX| + |dY|).  e0 and the depth numerator
 // num = (cx - XA) dX + (cy - YA) dY change by constants from one pixel to the
 // next along the minor axis.
-template <bool kPrecheck>
-__global__ void __launch_bounds__(kRasterThreads) raster_kernel(CallTable tab, CamDev cam, uint64_t *__restrict__ vis_c,
+template <bool kPrecheck, int kMinBlocks>
+__global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(CallTable tab, CamDev cam, uint64_t *__restrict__ vis_c,
                                                                 uint64_t *__restrict__ vis_a, hm_frame_stats *stats) {
     __shared__ uint32_t s_goff[HM_MAX_GROOMS_PER_CALL + 1];
     __shared__ SegRec s_rec[kRasterWarps][32];
@@ -423,29 +424,44 @@ cudaError_t launch_lod(const CallTable &tab, const CamDev &cam, hm_frame_stats *
     return cudaGetLastError();
 }
 
-int raster_grid(bool precheck) {
-    static int cached[2] = {0, 0};
-    int &c = cached[precheck ? 1 : 0];
-    if (c == 0) {
+// Raster variants: read-before-atomic on/off, and the register budget
+// (min resident CTAs per SM of 256 threads: 3 -> up to 80 registers,
+// 4 -> 64).  HM_RASTER_MINBLOCKS=3 selects the larger budget.
+template <bool P, int M>
+static int raster_grid_of() {
+    static int cached = 0;
+    if (cached == 0) {
         int per_sm = 0;
-        if (precheck)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<true>, kRasterThreads, 0);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<false>, kRasterThreads, 0);
-        if (per_sm < 1) per_sm = 1;
-        c = per_sm * num_sms();
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<P, M>, kRasterThreads, 0);
+        cached = (per_sm < 1 ? 1 : per_sm) * num_sms();
     }
-    return c;
+    return cached;
+}
+
+static int raster_min_blocks() {
+    static int v = 0;
+    if (v == 0) {
+        const char *e = std::getenv("HM_RASTER_MINBLOCKS");
+        v = (e && e[0] == '3') ? 3 : 4;
+    }
+    return v;
+}
+
+template <bool P, int M>
+static cudaError_t launch_raster_v(const CallTable &tab, const CamDev &cam, uint64_t *vis_c, uint64_t *vis_a,
+                                   hm_frame_stats *stats, cudaStream_t st) {
+    raster_kernel<P, M><<<raster_grid_of<P, M>(), kRasterThreads, 0, st>>>(tab, cam, vis_c, vis_a, stats);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_raster(const CallTable &tab, const CamDev &cam, uint64_t *vis_c, uint64_t *vis_a, bool precheck,
                           hm_frame_stats *stats, cudaStream_t st) {
-    int grid = raster_grid(precheck);
+    const bool m3 = raster_min_blocks() == 3;
     if (precheck)
-        raster_kernel<true><<<grid, kRasterThreads, 0, st>>>(tab, cam, vis_c, vis_a, stats);
-    else
-        raster_kernel<false><<<grid, kRasterThreads, 0, st>>>(tab, cam, vis_c, vis_a, stats);
-    return cudaGetLastError();
+        return m3 ? launch_raster_v<true, 3>(tab, cam, vis_c, vis_a, stats, st)
+                  : launch_raster_v<true, 4>(tab, cam, vis_c, vis_a, stats, st);
+    return m3 ? launch_raster_v<false, 3>(tab, cam, vis_c, vis_a, stats, st)
+              : launch_raster_v<false, 4>(tab, cam, vis_c, vis_a, stats, st);
 }
 
 }  // namespace hm

@@ -16,39 +16,50 @@
 
 namespace hm {
 
-__global__ void __launch_bounds__(kResolveThreads) resolve_kernel(CallTable tab, CamDev cam, LightsDev Ls,
-                                                                  FilterDev fp, const uint64_t *__restrict__ vis_c,
-                                                                  const uint64_t *__restrict__ vis_a,
-                                                                  float4 *__restrict__ rgba, uint32_t *status) {
+// Forward resolve tiles: 32x32 output pixels per CTA of 512 threads, so the
+// halo recompute is (32 + 2r)^2 / 32^2.  Work runs in uniform phases over
+// compacted lists: decode + shade the staged centre-sample pixels; decode the
+// conservative key where it is the reference (promoted pixels, depth
+// mismatch); the centre-referenced reconstruction of every centre pixel; the
+// conservative-referenced one where needed; then one combine pass writes RGBA.
+constexpr int kFwdTileW = 32, kFwdTileH = 32, kFwdThreads = 512, kFwdTilePx = kFwdTileW * kFwdTileH;
+
+__global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, CamDev cam, LightsDev Ls, FilterDev fp,
+                                                              const uint64_t *__restrict__ vis_c,
+                                                              const uint64_t *__restrict__ vis_a,
+                                                              float4 *__restrict__ rgba, uint32_t *status) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int R = fp.enabled ? fp.radius : 0;
-    const int sw = kTileW + 2 * R, sh = kTileH + 2 * R, ns = sw * sh;
-    // shared layout: bases | s_col[ns] | s_dg[ns] | s_list[ns] | s_fa[ns] | tile arrays
+    const int sw = kFwdTileW + 2 * R, sh = kFwdTileH + 2 * R, ns = sw * sh;
+    // shared layout: bases | s_col[ns] | s_dg[ns] | s_list[ns] | s_lg[tile] | s_out[tile] | s_ts[tile] | s_flag[tile] | s_fa[ns]
     uint64_t *s_bases = reinterpret_cast<uint64_t *>(smem);
     float3 *s_col = reinterpret_cast<float3 *>(s_bases + HM_MAX_GROOMS_PER_CALL + 1);
     int *s_dg = reinterpret_cast<int *>(s_col + ns);
-    uint16_t *s_list = reinterpret_cast<uint16_t *>(s_dg + ns);
-    float2 *s_tsG = reinterpret_cast<float2 *>(
-        (reinterpret_cast<uintptr_t>(s_list + ((ns + 7) & ~7)) + 15) & ~(uintptr_t)15);
-    float2 *s_tsA = s_tsG + kResolveThreads;
-    uint8_t *s_isoG = reinterpret_cast<uint8_t *>(s_tsA + kResolveThreads);
-    uint8_t *s_isoA = s_isoG + kResolveThreads;
-    uint8_t *s_fa = s_isoA + kResolveThreads;
-    __shared__ int s_count;
+    uint16_t *s_list = reinterpret_cast<uint16_t *>(s_dg + ns);      // staged centre list, then A list
+    uint16_t *s_lg = s_list + ((ns + 7) & ~7);                         // tile centre list
+    float4 *s_out = reinterpret_cast<float4 *>(
+        (reinterpret_cast<uintptr_t>(s_lg + kFwdTilePx) + 15) & ~(uintptr_t)15);  // centre result (rgb, alpha)
+    float2 *s_ts = reinterpret_cast<float2 *>(s_out + kFwdTilePx);   // G screen tangent, then A's
+    uint8_t *s_flag = reinterpret_cast<uint8_t *>(s_ts + kFwdTilePx); // bit0 isoG, bit1 isoA, bit2 needs A
+    uint8_t *s_fa = s_flag + kFwdTilePx;
+    __shared__ int s_count, s_ng;
 
-    const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int x0 = blockIdx.x * kFwdTileW, y0 = blockIdx.y * kFwdTileH;
     const int W = cam.W, H = cam.H;
     if (tid <= tab.n) {
         uint64_t b = 0;
         for (int i = 0; i < tid; ++i) b += (uint64_t)tab.g[i].S;
         s_bases[tid] = b;
     }
-    if (tid == 0) s_count = 0;
+    if (tid == 0) {
+        s_count = 0;
+        s_ng = 0;
+    }
     __syncthreads();
 
-    // stage keys of tile + halo; list staged centre-sample pixels
-    for (int i = tid; i < ns; i += kResolveThreads) {
+    // 1. stage keys of tile + halo; list staged centre-sample pixels
+    for (int i = tid; i < ns; i += kFwdThreads) {
         const int gx = x0 - R + i % sw, gy = y0 - R + i / sw;
         int dg = -1;
         uint8_t fa = 0;
@@ -64,13 +75,14 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(CallTable tab,
         }
         s_dg[i] = dg;
         s_fa[i] = fa;
+        s_col[i] = make_float3(0.f, 0.f, 0.f);
     }
-    if (tid < kResolveThreads) s_isoG[tid] = 1, s_isoA[tid] = 1;
+    for (int t = tid; t < kFwdTilePx; t += kFwdThreads) s_flag[t] = 3;
     __syncthreads();
 
-    // decode + shade every staged centre-sample pixel
+    // 2. decode + shade every staged centre-sample pixel
     const int ncen = s_count;
-    for (int li = tid; li < ncen; li += kResolveThreads) {
+    for (int li = tid; li < ncen; li += kFwdThreads) {
         const int i = s_list[li];
         const int lx = i % sw, ly = i / sw;
         const int gx = x0 - R + lx, gy = y0 - R + ly;
@@ -84,96 +96,120 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(CallTable tab,
         }
         s_col[i] = c;
         const int tx = lx - R, ty = ly - R;
-        if (tx >= 0 && tx < kTileW && ty >= 0 && ty < kTileH) {
-            const int t = ty * kTileW + tx;
-            s_tsG[t] = make_float2(d.tsx, d.tsy);
-            s_isoG[t] = d.iso;
+        if (tx >= 0 && tx < kFwdTileW && ty >= 0 && ty < kFwdTileH) {
+            const int t = ty * kFwdTileW + tx;
+            s_ts[t] = make_float2(d.tsx, d.tsy);
+            if (!d.iso) s_flag[t] = 2;        // isoG cleared, isoA still set
         }
     }
     __syncthreads();
     if (tid == 0) s_count = 0;
     __syncthreads();
 
-    // tile pixels that need the conservative layer as reference: promoted
-    // (centre empty) or depth mismatch (a closer conservative strand)
-    const int tx = tid % kTileW, ty = tid / kTileW;
-    const int gx = x0 + tx, gy = y0 + ty;
-    const bool inside = gx < W && gy < H;
-    const int mid = (ty + R) * sw + tx + R;
-    uint64_t ka = kEmptyKey;
-    int dA = -1;
-    if (inside && fp.enabled) {
-        ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx));
-        if (!key_empty(ka)) {
-            dA = (int)(ka >> 40);
-            const int dgP = s_dg[mid];
-            if (dgP < 0 || dA + fp.dmis <= dgP) s_list[atomicAdd(&s_count, 1)] = (uint16_t)tid;
+    // 3. lists: tile centre pixels (row-major per warp); pixels needing the
+    // conservative reference
+    for (int t = tid; t < kFwdTilePx; t += kFwdThreads) {
+        const int tx = t % kFwdTileW, ty = t / kFwdTileW;
+        const int gx = x0 + tx, gy = y0 + ty;
+        const bool in = gx < W && gy < H;
+        const int mid = (ty + R) * sw + tx + R;
+        const int dgP = in ? s_dg[mid] : -1;
+        const bool gP = dgP >= 0, aP = in && s_fa[mid] != 0;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, gP);
+        int wbase = 0;
+        if (lane == 0 && bal) wbase = atomicAdd(&s_ng, __popc(bal));
+        wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
+        if (gP) s_lg[wbase + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)t;
+        bool needA = false;
+        if (aP && fp.enabled) {
+            const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx));
+            needA = dgP < 0 || (int)(ka >> 40) + fp.dmis <= dgP;
+        }
+        const unsigned bala = __ballot_sync(0xFFFFFFFFu, needA);
+        int abase = 0;
+        if (lane == 0 && bala) abase = atomicAdd(&s_count, __popc(bala));
+        abase = __shfl_sync(0xFFFFFFFFu, abase, 0);
+        if (needA) {
+            s_list[abase + __popc(bala & ((1u << lane) - 1u))] = (uint16_t)t;
+            s_flag[t] |= 4;
         }
     }
     __syncthreads();
-    const int nA = s_count;
-    for (int li = tid; li < nA; li += kResolveThreads) {
-        const int t = s_list[li];
-        const int px = x0 + t % kTileW, py = y0 + t / kTileW;
-        const uint64_t k = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)py * W + px));
-        const Decoded d = decode_key(tab, s_bases, cam, k, px, py, status);
-        s_tsA[t] = make_float2(d.tsx, d.tsy);
-        s_isoA[t] = d.iso;
-    }
-    __syncthreads();
-    if (!inside) return;
+    const int ng = s_ng, nA = s_count;
 
-    // filter the tile pixel
-    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int dG = s_dg[mid];
-    const bool gP = dG >= 0, aP = s_fa[mid];
-    if (!fp.enabled) {
-        if (gP) {
-            const float3 c = s_col[mid];
-            out = make_float4(c.x, c.y, c.z, 1.0f);
-        }
-    } else if (gP) {
+    // 4. centre-referenced reconstruction of every centre pixel
+    for (int li = tid; li < ng; li += kFwdThreads) {
+        const int t = s_lg[li];
+        const int tx = t % kFwdTileW, ty = t / kFwdTileW;
+        const int mid = (ty + R) * sw + tx + R;
         const float3 Cp = s_col[mid];
-        const float2 ts = s_tsG[tid];
-        const Recon rg = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dG, ts.x, ts.y, s_isoG[tid] != 0,
-                                     true, Cp, fp);
-        const float invW = 1.0f / rg.W;
-        const float3 CG = make_float3(rg.S.x * invW, rg.S.y * invW, rg.S.z * invW);
-        if (aP && dA + fp.dmis <= dG) {
-            const float2 tsa = s_tsA[tid];
-            const Recon ra = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y,
-                                         s_isoA[tid] != 0, false, Cp, fp);
-            float3 c = CG;
+        float4 o;
+        if (!fp.enabled) {
+            o = make_float4(Cp.x, Cp.y, Cp.z, 1.0f);
+        } else {
+            const float2 ts = s_ts[t];
+            const Recon rg = reconstruct_fast_r<true>(R, s_dg, s_fa, s_col, sw, tx, ty, s_dg[mid], ts.x, ts.y,
+                                                      (s_flag[t] & 1) != 0, Cp, fp);
+            const float invW = 1.0f / rg.W;
+            o = make_float4(rg.S.x * invW, rg.S.y * invW, rg.S.z * invW, __fdiv_rn((float)rg.hc, (float)rg.ha));
+        }
+        s_out[t] = o;
+    }
+    __syncthreads();
+
+    // 5. decode the conservative reference, then the conservative-referenced
+    // (promoted) reconstruction; combine with the centre result
+    for (int li = tid; li < nA; li += kFwdThreads) {
+        const int t = s_list[li];
+        const int tx = t % kFwdTileW, ty = t / kFwdTileW;
+        const int gx = x0 + tx, gy = y0 + ty;
+        const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx));
+        const Decoded d = decode_key(tab, s_bases, cam, ka, gx, gy, status);
+        const int dA = (int)(ka >> 40);
+        const float3 z = make_float3(0.f, 0.f, 0.f);
+        Recon ra = reconstruct_fast_r<false>(R, s_dg, s_fa, s_col, sw, tx, ty, dA, d.tsx, d.tsy, d.iso, z, fp);
+        if (ra.cnt > 0 && ra.W < 1e-20f)
+            ra = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, d.tsx, d.tsy, d.iso, false, z, fp);
+        const int mid = (ty + R) * sw + tx + R;
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (s_dg[mid] >= 0) {               // depth mismatch: blend over the centre result, alpha 1
+            const float4 cg = s_out[t];
+            float3 c = make_float3(cg.x, cg.y, cg.z);
             if (ra.cnt > 0) {
                 const float al = __fdiv_rn((float)ra.hc, (float)ra.ha);
                 const float iw = 1.0f / ra.W;
-                c = make_float3(al * (ra.S.x * iw) + (1.0f - al) * CG.x, al * (ra.S.y * iw) + (1.0f - al) * CG.y,
-                                al * (ra.S.z * iw) + (1.0f - al) * CG.z);
+                c = make_float3(al * (ra.S.x * iw) + (1.0f - al) * c.x, al * (ra.S.y * iw) + (1.0f - al) * c.y,
+                                al * (ra.S.z * iw) + (1.0f - al) * c.z);
             }
-            out = make_float4(c.x, c.y, c.z, 1.0f);
-        } else {
-            out = make_float4(CG.x, CG.y, CG.z, __fdiv_rn((float)rg.hc, (float)rg.ha));
-        }
-    } else if (aP) {
-        const float2 tsa = s_tsA[tid];
-        const Recon ra = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y,
-                                     s_isoA[tid] != 0, false, make_float3(0.f, 0.f, 0.f), fp);
-        if (ra.cnt > 0) {
+            o = make_float4(c.x, c.y, c.z, 1.0f);
+        } else if (ra.cnt > 0) {            // promoted
             const float iw = 1.0f / ra.W;
-            out = make_float4(ra.S.x * iw, ra.S.y * iw, ra.S.z * iw, __fdiv_rn((float)ra.hc, (float)ra.ha));
+            o = make_float4(ra.S.x * iw, ra.S.y * iw, ra.S.z * iw, __fdiv_rn((float)ra.hc, (float)ra.ha));
         }
+        s_out[t] = o;
     }
-    rgba[(int64_t)gy * W + gx] = out;
+    __syncthreads();
+
+    // 6. write the tile row-major
+    for (int t = tid; t < kFwdTilePx; t += kFwdThreads) {
+        const int tx = t % kFwdTileW, ty = t / kFwdTileW;
+        const int gx = x0 + tx, gy = y0 + ty;
+        if (gx >= W || gy >= H) continue;
+        const int mid = (ty + R) * sw + tx + R;
+        const bool written = s_dg[mid] >= 0 || (s_flag[t] & 4);
+        rgba[(int64_t)gy * W + gx] = written ? s_out[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 }
 
 size_t resolve_smem_bytes(int radius) {
-    const int sw = kTileW + 2 * radius, sh = kTileH + 2 * radius, ns = sw * sh;
+    const int sw = kFwdTileW + 2 * radius, sh = kFwdTileH + 2 * radius, ns = sw * sh;
     size_t b = sizeof(uint64_t) * (HM_MAX_GROOMS_PER_CALL + 1);
     b += sizeof(float3) * ns;
     b += sizeof(int) * ns;
-    b += sizeof(uint16_t) * ((ns + 7) & ~7) + 16;
-    b += sizeof(float2) * 2 * kResolveThreads;
-    b += 2 * kResolveThreads;
+    b += sizeof(uint16_t) * (((ns + 7) & ~7) + kFwdTilePx) + 16;
+    b += sizeof(float4) * kFwdTilePx;
+    b += sizeof(float2) * kFwdTilePx;
+    b += kFwdTilePx;
     b += ns;
     return (b + 15) & ~(size_t)15;
 }
@@ -189,9 +225,9 @@ cudaError_t launch_resolve(const CallTable &tab, const CamDev &cam, const Lights
                              (int)resolve_smem_bytes(HM_MAX_FILTER_RADIUS));
         attr_set = true;
     }
-    dim3 grid((cam.W + kTileW - 1) / kTileW, (cam.H + kTileH - 1) / kTileH);
-    resolve_kernel<<<grid, kResolveThreads, sm, st>>>(tab, cam, Ls, fp, vis_c, vis_a,
-                                                       reinterpret_cast<float4 *>(rgba), status);
+    dim3 grid((cam.W + kFwdTileW - 1) / kFwdTileW, (cam.H + kFwdTileH - 1) / kFwdTileH);
+    resolve_kernel<<<grid, kFwdThreads, sm, st>>>(tab, cam, Ls, fp, vis_c, vis_a, reinterpret_cast<float4 *>(rgba),
+                                                  status);
     return cudaGetLastError();
 }
 

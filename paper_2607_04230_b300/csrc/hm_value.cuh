@@ -117,4 +117,71 @@ __device__ __forceinline__ Recon reconstruct(const int *s_dg, const uint8_t *s_f
     return o;
 }
 
+// Straight-line reconstruction for a compile-time radius R (the dx loop is
+// unrolled, dy runs): every tap is evaluated with predication and no
+// divergent branch.  The weights are accumulated unscaled:
+//  - centre reference (kColor): the pixel itself contributes with exponent 0
+//    (zero offset, same depth, same colour) and every exponent is >= 0, so
+//    each weight is <= 1 and the sum is >= 1;
+//  - conservative reference: the sum is exact unless every weight is tiny;
+//    callers redo it with the online-rescaled reconstruct() when W < 1e-20.
+// Staged pixels without a centre key must hold a finite colour (zero).
+template <int R, bool kColor>
+__device__ __forceinline__ Recon reconstruct_fast(const int *s_dg, const uint8_t *s_fa, const float3 *s_col, int sw,
+                                                  int lx, int ly, int ref, float tsx, float tsy, bool iso, float3 Cp,
+                                                  const FilterDev &fp) {
+    float Sx = 0.f, Sy = 0.f, Sz = 0.f, Wt = 0.f;
+    int hc = 0, ha = 0, cnt = 0;
+    for (int dy = -R; dy <= R; ++dy) {
+        const int row = (ly + dy + R) * sw + lx + R;
+#pragma unroll
+        for (int dx = -R; dx <= R; ++dx) {
+            const int idx = row + dx;
+            const int dq = s_dg[idx];
+            const int fa = s_fa[idx];
+            float dpar, perp2;
+            const bool strip = in_strip(iso, tsx, tsy, dx, dy, fp.hw2, dpar, perp2);
+            const bool gq = dq >= 0;
+            hc += (strip && gq) ? 1 : 0;
+            ha += (strip && fa) ? 1 : 0;
+            const bool ok = gq && abs(dq - ref) <= fp.drej;
+            const float3 cq = s_col[idx];
+            float e = iso ? (float)(dx * dx + dy * dy) * fp.inv_siso2
+                          : (dpar * dpar) * fp.inv_spar2 + perp2 * fp.inv_sperp2;
+            if (kColor) {
+                const float ex = Cp.x - cq.x, ey = Cp.y - cq.y, ez = Cp.z - cq.z;
+                e += (ex * ex + ey * ey + ez * ez) * fp.inv_sc2;
+            }
+            const float w = ok ? __expf(-e) : 0.f;
+            Sx += w * cq.x;
+            Sy += w * cq.y;
+            Sz += w * cq.z;
+            Wt += w;
+            cnt += ok ? 1 : 0;
+        }
+    }
+    Recon o;
+    o.S = make_float3(Sx, Sy, Sz);
+    o.W = Wt;
+    o.m = 0.f;
+    o.cnt = cnt;
+    o.hc = hc;
+    o.ha = ha;
+    return o;
+}
+
+// reconstruct_fast<R, kColor> for a runtime radius 0..HM_MAX_FILTER_RADIUS.
+template <bool kColor>
+__device__ __forceinline__ Recon reconstruct_fast_r(int R, const int *s_dg, const uint8_t *s_fa, const float3 *s_col,
+                                                    int sw, int lx, int ly, int ref, float tsx, float tsy, bool iso,
+                                                    float3 Cp, const FilterDev &fp) {
+    switch (R) {
+#define HM_RF(r) \
+    case r: return reconstruct_fast<r, kColor>(s_dg, s_fa, s_col, sw, lx, ly, ref, tsx, tsy, iso, Cp, fp);
+        HM_RF(0) HM_RF(1) HM_RF(2) HM_RF(3) HM_RF(4) HM_RF(5) HM_RF(6) HM_RF(7)
+#undef HM_RF
+        default: return reconstruct_fast<8, kColor>(s_dg, s_fa, s_col, sw, lx, ly, ref, tsx, tsy, iso, Cp, fp);
+    }
+}
+
 }  // namespace hm
