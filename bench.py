@@ -46,7 +46,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=["single_1080p", "crowd_4k", "tiny_256"], default="single_1080p")
+    ap.add_argument("--workload", choices=["single_1080p", "crowd_4k", "tiny_256", "lod_sweep"],
+                    default="single_1080p")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -260,6 +262,151 @@ def run_reference(args, rank, world):
     return 0
 
 
+def _timed(torch, step, steps, flush):
+    """Per-step CUDA-event times (ms) of `step`, L2 flushed before each."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k)
+        evs[k][0].record()
+        step()
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def run_crowd(args, rank, world, local_rank):
+    """64 grooms at 4K: the autotuned batched frame (one render + one resolve
+    call, captured in a CUDA graph) against one render call per groom."""
+    import torch
+    import torch.distributed as dist
+    from paper_2607_04230_b300 import autotune, build, crowd, hm
+    build.build()
+    torch.cuda.set_device(local_rank)
+    scene, cfg = make_scene("crowd_4k")
+    cr = crowd.Crowd(scene)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    cr.render_batched()
+    torch.cuda.synchronize()
+    st = hm.stats_dict(cr.frame.stats)
+    segs = st["segments"]
+    tune = None
+    if not args.no_autotune:
+        tune = autotune.autotune(cr.render_batched, scene, segs, n=3)
+    # per-kernel phase times (same kernels, outside the graph)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(5)]
+    for row in ev:
+        for e in row:
+            e.record()
+    for k in range(5):
+        flush.fill_(k)
+        hm.set_phase_events(ev[k])
+        cr.render_batched()
+    hm.set_phase_events(None)
+    torch.cuda.synchronize()
+    phase_ms = {name: statistics.median(e[a].elapsed_time(e[b]) for e in ev)
+                for name, a, b in (("clear", 0, 1), ("lod", 1, 2), ("raster", 2, 3), ("resolve", 4, 5))}
+    cr.capture()
+    for _ in range(args.warmup):
+        cr.replay()
+    clocks = ClockSampler(_gpu_uuid(torch, local_rank))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_graph = _timed(torch, cr.replay, args.steps, flush)
+    clk = clocks.stop()
+    for _ in range(3):
+        cr.render_per_character()
+    t_pc = _timed(torch, cr.render_per_character, max(10, args.steps // 4), flush)
+    hm.get_device_status()
+    tg = sum(t_graph) * 1e-3
+    if world > 1:
+        tt = torch.tensor([tg], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tg = float(tt.item())
+    if rank != 0:
+        return 0
+    n = len(scene.grooms)
+    atomics = st["covered_cons"] + st["covered_center"]
+    ms_g = tg / args.steps * 1e3
+    ms_pc = statistics.mean(t_pc)
+    line = {"metric": METRIC, "value": segs * args.steps * world / tg, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_g, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
+            "config": dict(cfg, parallelism=f"replicas x{world}", batching="one render + one resolve call over "
+                           "all grooms, replayed as a CUDA graph"),
+            "strands_after_lod": st["strands"], "segments_per_frame": segs, "covered_pairs": atomics,
+            "frame_ms_phases": phase_ms,
+            "per_character": {"batched_graph_ms_per_character": ms_g / n,
+                              "per_character_launches_ms_per_character": ms_pc / n,
+                              "speedup": ms_pc / ms_g, "grooms": n},
+            "autotune": tune and {"tuning": tune["tuning"], "best_ms": tune["ms"], "candidates": len(tune["table"])},
+            "gpu_launches": 4 * args.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_lod_sweep(args, rank, world, local_rank):
+    """The 1080p groom at 8 distances (head height 8 ... 1000 px), LOD on:
+    strands drawn, visible strands, frame ms, segments/s, and the
+    premultiplied-RGB error against the same frame rendered at LOD 0."""
+    import torch
+    from paper_2607_04230_b300 import build, hm, synth
+    build.build()
+    torch.cuda.set_device(local_rank)
+    g = synth.groom_single_1080p()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    rows = []
+    handle = None
+    for i in range(8):
+        sc = synth.scene_lod_sweep(i, g)
+        if handle is None:
+            handle = hm.upload_scene(sc)
+        frame = hm.Frame(sc.camera.width, sc.camera.height)
+        out = {}
+        for lod in (0, 1):
+            handle[0].set_lod(lod, sc.lod.lam)
+
+            def step():
+                hm.render(handle, sc, frame)
+
+            for _ in range(3):
+                step()
+            ts = _timed(torch, step, max(10, args.steps // 8), flush)
+            stt = hm.stats_dict(frame.stats)
+            vc, va = frame.vis_center, frame.vis_cons
+            ids = torch.cat([vc, va])
+            ids = ids[(ids & 0xFFFFFFFFFF) != 0xFFFFFFFFFF]
+            visible = int(torch.unique((ids >> 7) & 0x1FFFFFFFF).numel())
+            img = frame.rgba[..., :3] * frame.rgba[..., 3:4]
+            out[lod] = {"ms": statistics.median(ts), "strands": stt["strands"], "segments": stt["segments"],
+                        "visible_strands": visible, "img": img.clone()}
+        err = (out[1]["img"] - out[0]["img"]).abs()
+        rows.append({"head_px": round(synth.LOD_SWEEP_HEIGHTS_PX[i], 1), "strands_lod": out[1]["strands"],
+                     "strands_full": out[0]["strands"], "visible_strands_lod": out[1]["visible_strands"],
+                     "segments_lod": out[1]["segments"], "frame_ms_lod": out[1]["ms"],
+                     "frame_ms_full": out[0]["ms"],
+                     "segments_per_s_lod": out[1]["segments"] / (out[1]["ms"] * 1e-3),
+                     "rgb_err_vs_lod0_max": float(err.max()), "rgb_err_vs_lod0_mean": float(err.mean())})
+    if rank != 0:
+        return 0
+    tot_s = sum(r["segments_lod"] for r in rows)
+    tot_t = sum(r["frame_ms_lod"] for r in rows) * 1e-3
+    line = {"metric": METRIC, "value": tot_s / tot_t, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_t / len(rows) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
+            "config": {"workload": "LOD sweep: 1080p groom at 8 distances, LOD on (lambda 3) vs LOD 0",
+                       "resolution": "1920x1080", "l2": "flushed between timed steps (256 MiB write)"},
+            "sweep": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _gpu_uuid(torch, dev):
+    u = str(torch.cuda.get_device_properties(dev).uuid)
+    return u if u.startswith("GPU-") else "GPU-" + u
+
+
 def run_native(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -283,6 +430,10 @@ def run_native(args, rank, world, local_rank):
     st = hm.stats_dict(frame.stats)
     segs = st["segments"]
     atomics = st["covered_cons"] + st["covered_center"]
+    tune = None
+    if not args.no_autotune:
+        from paper_2607_04230_b300 import autotune
+        tune = autotune.autotune(step, scene, segs, n=5)
 
     peak_rates = probe_atomic_peak(torch, hm, 2 * W * H)
 
@@ -291,10 +442,7 @@ def run_native(args, rank, world, local_rank):
         for e in row:
             e.record()
     torch.cuda.synchronize()
-    gpu_uuid = str(torch.cuda.get_device_properties(local_rank).uuid)
-    if not gpu_uuid.startswith("GPU-"):
-        gpu_uuid = "GPU-" + gpu_uuid
-    clocks = ClockSampler(gpu_uuid)
+    clocks = ClockSampler(_gpu_uuid(torch, local_rank))
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -385,7 +533,8 @@ def run_native(args, rank, world, local_rank):
             "frame_ms": {k: round(v, 5) for k, v in phase_ms.items()},
             "segments_per_frame": segs, "raster_segments_per_s": segs / t_r,
             "roofline": roofline, "kernels": kernels,
-            "e2e": e2e, "gpu_launches": 4 * args.steps, "clocks": clk, "wall_s": wall}
+            "e2e": e2e, "gpu_launches": 4 * args.steps, "clocks": clk, "wall_s": wall,
+            "autotune": tune and {"tuning": tune["tuning"], "best_ms": tune["ms"], "candidates": len(tune["table"])}}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(scene)
     print(json.dumps(line), flush=True)
@@ -404,8 +553,9 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
+    runner = {"crowd_4k": run_crowd, "lod_sweep": run_lod_sweep}.get(args.workload, run_native)
     try:
-        return run_native(args, rank, world, local_rank)
+        return runner(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

@@ -188,6 +188,17 @@ hm_status hm_render_visibility(const hm_groom *grooms, int32_t n, const hm_camer
                                const uint32_t *d_scene_d24, int32_t clear,
                                hm_frame_stats *d_stats, void *stream);
 
+/* hm_render_visibility for grooms[first .. first + count) only, with strand
+ * ids numbered as in the whole n-groom array, so that per-groom calls into
+ * the same buffers (clear only on the first) compose with one
+ * hm_resolve_shade over all n grooms: the sequential multi-groom scheme of
+ * Sec. 4 "Multiple Grooms".  Same errors as hm_render_visibility, plus
+ * HM_ERR_INVALID_ARG when the range is outside 0..n. */
+hm_status hm_render_visibility_range(const hm_groom *grooms, int32_t n, int32_t first, int32_t count,
+                                     const hm_camera *cam, uint64_t *d_vis_center, uint64_t *d_vis_cons,
+                                     const uint32_t *d_scene_d24, int32_t clear, hm_frame_stats *d_stats,
+                                     void *stream);
+
 /* Deferred resolve (Sec. 3.1.2 deferred shading, Sec. 3.3 filter, Sec. 3.4
  * shading): decode each key back to its strand segment, shade centre-sample
  * pixels, run the strand-connection / elliptical bilateral filter and alpha
@@ -258,6 +269,29 @@ hm_status hm_groom_info(hm_groom g, int32_t *L, int32_t *V, int32_t *F, int64_t 
 /* Synchronize `stream`, read and clear the device status word (set by a
  * failed device-side consistency check): HM_OK or HM_ERR_DEVICE_CHECK. */
 hm_status hm_get_device_status(void *stream);
+
+/* Launch shapes of the kernels, process-wide (the project's autotuner,
+ * paper_2607_04230_b300/autotune.py, searches these).  Results never depend
+ * on them: visibility is bit-identical and colours identical for every
+ * setting.
+ *   raster_precheck    0/1: read the key before each atomicMin and skip
+ *                      atomics that cannot lower it (default 0)
+ *   raster_min_blocks  3 or 4 resident 256-thread rasterizer CTAs per SM the
+ *                      register budget is sized for (default 4)
+ *   raster_ctas_per_sm persistent rasterizer CTAs per SM, 0 = as many as fit
+ *   resolve_tile_h     16 or 32: resolve tiles of 32 x tile_h pixels
+ *                      (default 32)
+ * Not thread-safe against concurrent render calls on other host threads. */
+typedef struct {
+    int32_t raster_precheck;
+    int32_t raster_min_blocks;
+    int32_t raster_ctas_per_sm;
+    int32_t resolve_tile_h;
+    int32_t reserved[4];
+} hm_tuning;
+
+hm_status hm_set_tuning(const hm_tuning *t);
+hm_status hm_get_tuning(hm_tuning *t);
 
 /* Profiling: record CUDA events (cudaEvent_t passed as void*) at phase
  * boundaries of later calls on this host thread, on the call's stream:

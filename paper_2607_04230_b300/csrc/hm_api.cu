@@ -168,17 +168,16 @@ void phase(int i, cudaStream_t s) {
     if (g_phase_events[i]) cudaEventRecord(static_cast<cudaEvent_t>(g_phase_events[i]), s);
 }
 
-// Read the current key before each atomicMin and skip it when it cannot
-// lower the key.  Off by default: on B300 the plain fire-and-forget
-// atomics are faster (1.07 vs 1.28 ms per 1080p frame).  HM_RASTER_PRECHECK=1
-// turns it on.
-bool raster_precheck() {
-    static int v = -1;
-    if (v < 0) {
-        const char *e = std::getenv("HM_RASTER_PRECHECK");
-        v = (e && e[0] == '1') ? 1 : 0;
-    }
-    return v == 1;
+// Launch-shape tuning shared by every call of the process (hm_set_tuning).
+// Defaults: plain atomics (on B300 the read-before-atomic variant is slower:
+// 1.28 vs 1.07 ms per 1080p frame), the 64-register raster, as many raster
+// CTAs per SM as fit, 32x32 resolve tiles.
+hm_tuning g_tuning = {0, 4, 0, 32, 0, 0, 0, 0};
+
+bool valid_tuning(const hm_tuning &t) {
+    return (t.raster_precheck == 0 || t.raster_precheck == 1) &&
+           (t.raster_min_blocks == 3 || t.raster_min_blocks == 4) && t.raster_ctas_per_sm >= 0 &&
+           t.raster_ctas_per_sm <= 32 && (t.resolve_tile_h == 16 || t.resolve_tile_h == 32);
 }
 
 }  // namespace
@@ -359,15 +358,28 @@ hm_status hm_update_albedo(hm_groom g, const float *d_albedo, void *stream) {
 hm_status hm_render_visibility(const hm_groom *grooms, int32_t n, const hm_camera *cam, uint64_t *d_vis_center,
                                uint64_t *d_vis_cons, const uint32_t *d_scene_d24, int32_t clear,
                                hm_frame_stats *d_stats, void *stream) {
+    return hm_render_visibility_range(grooms, n, 0, n, cam, d_vis_center, d_vis_cons, d_scene_d24, clear, d_stats,
+                                      stream);
+}
+
+hm_status hm_render_visibility_range(const hm_groom *grooms, int32_t n, int32_t first, int32_t count,
+                                     const hm_camera *cam, uint64_t *d_vis_center, uint64_t *d_vis_cons,
+                                     const uint32_t *d_scene_d24, int32_t clear, hm_frame_stats *d_stats,
+                                     void *stream) {
     hm_status st = check_camera(cam);
     if (st != HM_OK) return st;
     if (!d_vis_center || !d_vis_cons) return fail(HM_ERR_INVALID_ARG, "visibility buffer is NULL");
     if ((reinterpret_cast<uintptr_t>(d_vis_center) & 15) || (reinterpret_cast<uintptr_t>(d_vis_cons) & 15))
         return fail(HM_ERR_INVALID_ARG, "visibility buffers must be 16-byte aligned");
     if (d_vis_center == d_vis_cons) return fail(HM_ERR_INVALID_ARG, "the two layers must be distinct buffers");
-    hm::CallTable tab;
-    st = build_table(grooms, n, tab);
+    if (first < 0 || count < 1 || first > n - count) return fail(HM_ERR_INVALID_ARG, "groom range outside 0..n");
+    hm::CallTable full;
+    st = build_table(grooms, n, full);
     if (st != HM_OK) return st;
+    hm::CallTable tab;
+    std::memset(&tab, 0, sizeof tab);
+    tab.n = count;
+    for (int i = 0; i < count; ++i) tab.g[i] = full.g[first + i];   // keeps the whole array's strand ids
     const hm::CamDev cd = cam_dev(cam);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t npx = (int64_t)cam->width * cam->height;
@@ -376,7 +388,9 @@ hm_status hm_render_visibility(const hm_groom *grooms, int32_t n, const hm_camer
     phase(1, s);
     HM_CUDA(hm::launch_lod(tab, cd, d_stats, s), "lod");
     phase(2, s);
-    HM_CUDA(hm::launch_raster(tab, cd, d_vis_center, d_vis_cons, raster_precheck(), d_stats, s), "raster");
+    HM_CUDA(hm::launch_raster(tab, cd, d_vis_center, d_vis_cons, g_tuning.raster_precheck != 0,
+                              g_tuning.raster_min_blocks, g_tuning.raster_ctas_per_sm, d_stats, s),
+            "raster");
     phase(3, s);
     return HM_OK;
 }
@@ -441,9 +455,22 @@ hm_status hm_resolve_shade(const hm_groom *grooms, int32_t n, const hm_camera *c
     if (!sw) return fail(HM_ERR_CUDA, "device status word unavailable");
     phase(4, static_cast<cudaStream_t>(stream));
     HM_CUDA(hm::launch_resolve(tab, cam_dev(cam), ld, fd, d_vis_center, d_vis_cons, d_rgba, sw,
-                               static_cast<cudaStream_t>(stream)),
+                               g_tuning.resolve_tile_h, static_cast<cudaStream_t>(stream)),
             "resolve");
     phase(5, static_cast<cudaStream_t>(stream));
+    return HM_OK;
+}
+
+hm_status hm_set_tuning(const hm_tuning *t) {
+    if (!t) return fail(HM_ERR_INVALID_ARG, "tuning is NULL");
+    if (!valid_tuning(*t)) return fail(HM_ERR_INVALID_ARG, "tuning value out of range");
+    g_tuning = *t;
+    return HM_OK;
+}
+
+hm_status hm_get_tuning(hm_tuning *t) {
+    if (!t) return fail(HM_ERR_INVALID_ARG, "tuning is NULL");
+    *t = g_tuning;
     return HM_OK;
 }
 

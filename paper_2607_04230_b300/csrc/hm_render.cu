@@ -426,42 +426,36 @@ cudaError_t launch_lod(const CallTable &tab, const CamDev &cam, hm_frame_stats *
 
 // Raster variants: read-before-atomic on/off, and the register budget
 // (min resident CTAs per SM of 256 threads: 3 -> up to 80 registers,
-// 4 -> 64).  HM_RASTER_MINBLOCKS=3 selects the larger budget.
+// 4 -> 64).  The persistent grid is ctas_per_sm CTAs per SM, capped at what
+// fits (0 = as many as fit).
 template <bool P, int M>
-static int raster_grid_of() {
+static int raster_fit_per_sm() {
     static int cached = 0;
     if (cached == 0) {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<P, M>, kRasterThreads, 0);
-        cached = (per_sm < 1 ? 1 : per_sm) * num_sms();
+        cached = per_sm < 1 ? 1 : per_sm;
     }
     return cached;
 }
 
-static int raster_min_blocks() {
-    static int v = 0;
-    if (v == 0) {
-        const char *e = std::getenv("HM_RASTER_MINBLOCKS");
-        v = (e && e[0] == '3') ? 3 : 4;
-    }
-    return v;
-}
-
 template <bool P, int M>
 static cudaError_t launch_raster_v(const CallTable &tab, const CamDev &cam, uint64_t *vis_c, uint64_t *vis_a,
-                                   hm_frame_stats *stats, cudaStream_t st) {
-    raster_kernel<P, M><<<raster_grid_of<P, M>(), kRasterThreads, 0, st>>>(tab, cam, vis_c, vis_a, stats);
+                                   int ctas_per_sm, hm_frame_stats *stats, cudaStream_t st) {
+    const int fit = raster_fit_per_sm<P, M>();
+    const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < fit) ? ctas_per_sm : fit;
+    raster_kernel<P, M><<<per_sm * num_sms(), kRasterThreads, 0, st>>>(tab, cam, vis_c, vis_a, stats);
     return cudaGetLastError();
 }
 
 cudaError_t launch_raster(const CallTable &tab, const CamDev &cam, uint64_t *vis_c, uint64_t *vis_a, bool precheck,
-                          hm_frame_stats *stats, cudaStream_t st) {
-    const bool m3 = raster_min_blocks() == 3;
+                          int min_blocks, int ctas_per_sm, hm_frame_stats *stats, cudaStream_t st) {
+    const bool m3 = min_blocks == 3;
     if (precheck)
-        return m3 ? launch_raster_v<true, 3>(tab, cam, vis_c, vis_a, stats, st)
-                  : launch_raster_v<true, 4>(tab, cam, vis_c, vis_a, stats, st);
-    return m3 ? launch_raster_v<false, 3>(tab, cam, vis_c, vis_a, stats, st)
-              : launch_raster_v<false, 4>(tab, cam, vis_c, vis_a, stats, st);
+        return m3 ? launch_raster_v<true, 3>(tab, cam, vis_c, vis_a, ctas_per_sm, stats, st)
+                  : launch_raster_v<true, 4>(tab, cam, vis_c, vis_a, ctas_per_sm, stats, st);
+    return m3 ? launch_raster_v<false, 3>(tab, cam, vis_c, vis_a, ctas_per_sm, stats, st)
+              : launch_raster_v<false, 4>(tab, cam, vis_c, vis_a, ctas_per_sm, stats, st);
 }
 
 }  // namespace hm

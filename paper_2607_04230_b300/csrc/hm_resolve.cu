@@ -22,12 +22,14 @@ namespace hm {
 // conservative key where it is the reference (promoted pixels, depth
 // mismatch); the centre-referenced reconstruction of every centre pixel; the
 // conservative-referenced one where needed; then one combine pass writes RGBA.
-constexpr int kFwdTileW = 32, kFwdTileH = 32, kFwdThreads = 512, kFwdTilePx = kFwdTileW * kFwdTileH;
+constexpr int kFwdTileW = 32, kFwdThreads = 512;
 
+template <int kFwdTileH>
 __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, CamDev cam, LightsDev Ls, FilterDev fp,
                                                               const uint64_t *__restrict__ vis_c,
                                                               const uint64_t *__restrict__ vis_a,
                                                               float4 *__restrict__ rgba, uint32_t *status) {
+    constexpr int kFwdTilePx = kFwdTileW * kFwdTileH;
     extern __shared__ __align__(16) unsigned char smem[];
     const int R = fp.enabled ? fp.radius : 0;
     const int sw = kFwdTileW + 2 * R, sh = kFwdTileH + 2 * R, ns = sw * sh;
@@ -201,34 +203,43 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
     }
 }
 
-size_t resolve_smem_bytes(int radius) {
-    const int sw = kFwdTileW + 2 * radius, sh = kFwdTileH + 2 * radius, ns = sw * sh;
+size_t resolve_smem_bytes(int radius, int tile_h) {
+    const int tile_px = kFwdTileW * tile_h;
+    const int sw = kFwdTileW + 2 * radius, sh = tile_h + 2 * radius, ns = sw * sh;
     size_t b = sizeof(uint64_t) * (HM_MAX_GROOMS_PER_CALL + 1);
     b += sizeof(float3) * ns;
     b += sizeof(int) * ns;
-    b += sizeof(uint16_t) * (((ns + 7) & ~7) + kFwdTilePx) + 16;
-    b += sizeof(float4) * kFwdTilePx;
-    b += sizeof(float2) * kFwdTilePx;
-    b += kFwdTilePx;
+    b += sizeof(uint16_t) * (((ns + 7) & ~7) + tile_px) + 16;
+    b += sizeof(float4) * tile_px;
+    b += sizeof(float2) * tile_px;
+    b += tile_px;
     b += ns;
     return (b + 15) & ~(size_t)15;
 }
 
-cudaError_t launch_resolve(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
-                           const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status,
-                           cudaStream_t st) {
+template <int TH>
+static cudaError_t launch_resolve_t(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
+                                   const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status,
+                                   cudaStream_t st) {
     const int R = fp.enabled ? fp.radius : 0;
-    size_t sm = resolve_smem_bytes(R);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(resolve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)resolve_smem_bytes(HM_MAX_FILTER_RADIUS));
+        cudaFuncSetAttribute(resolve_kernel<TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)resolve_smem_bytes(HM_MAX_FILTER_RADIUS, TH));
         attr_set = true;
     }
-    dim3 grid((cam.W + kFwdTileW - 1) / kFwdTileW, (cam.H + kFwdTileH - 1) / kFwdTileH);
-    resolve_kernel<<<grid, kFwdThreads, sm, st>>>(tab, cam, Ls, fp, vis_c, vis_a, reinterpret_cast<float4 *>(rgba),
-                                                  status);
+    dim3 grid((cam.W + kFwdTileW - 1) / kFwdTileW, (cam.H + TH - 1) / TH);
+    resolve_kernel<TH><<<grid, kFwdThreads, resolve_smem_bytes(R, TH), st>>>(tab, cam, Ls, fp, vis_c, vis_a,
+                                                                             reinterpret_cast<float4 *>(rgba), status);
     return cudaGetLastError();
+}
+
+// Resolve tile: 32 x tile_h output pixels per CTA (tile_h 16 or 32).
+cudaError_t launch_resolve(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
+                           const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status, int tile_h,
+                           cudaStream_t st) {
+    if (tile_h == 16) return launch_resolve_t<16>(tab, cam, Ls, fp, vis_c, vis_a, rgba, status, st);
+    return launch_resolve_t<32>(tab, cam, Ls, fp, vis_c, vis_a, rgba, status, st);
 }
 
 }  // namespace hm

@@ -62,6 +62,14 @@ class FilterParams(ctypes.Structure):
                 ("depth_mismatch_m", ctypes.c_float)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("raster_precheck", ctypes.c_int32), ("raster_min_blocks", ctypes.c_int32),
+                ("raster_ctas_per_sm", ctypes.c_int32), ("resolve_tile_h", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+TUNING_FIELDS = ("raster_precheck", "raster_min_blocks", "raster_ctas_per_sm", "resolve_tile_h")
+
 STATS_FIELDS = ("strands", "segments", "bundles_culled", "covered_center", "covered_cons")
 
 
@@ -90,6 +98,7 @@ def lib():
         "hm_update_layer_verts": [P, P, P],
         "hm_update_albedo": [P, P, P],
         "hm_render_visibility": [P, i32, P, P, P, P, i32, P, P],
+        "hm_render_visibility_range": [P, i32, i32, i32, P, P, P, P, i32, P, P],
         "hm_resolve_shade": [P, i32, P, P, P, P, P, P, P, P],
         "hm_shade_backward": [P, i32, P, P, P, P, P, P, P, P, P, P],
         "hm_shade_backward_noalloc": [P, i32, P, P, P, P, P, P, P, P, P],
@@ -97,6 +106,8 @@ def lib():
         "hm_groom_info": [P, P, P, P, P, P],
         "hm_get_device_status": [P],
         "hm_set_phase_events": [P, i32],
+        "hm_set_tuning": [P],
+        "hm_get_tuning": [P],
         "hm_probe_atomic_min": [P, i64, i32, i32, P],
     }
     for name, args in sig.items():
@@ -247,6 +258,15 @@ def render_visibility(grooms, cam, vis_center, vis_cons, scene_d24=None, clear=T
                                      int(bool(clear)), _dptr(stats), _stream_ptr(stream)))
 
 
+def render_visibility_range(grooms, first, count, cam, vis_center, vis_cons, scene_d24=None, clear=True, stats=None,
+                            stream=None):
+    arr, n = _handles(grooms)
+    c = camera_struct(cam)
+    check(lib().hm_render_visibility_range(arr, n, int(first), int(count), ctypes.byref(c), _dptr(vis_center),
+                                           _dptr(vis_cons), _dptr(scene_d24), int(bool(clear)), _dptr(stats),
+                                           _stream_ptr(stream)))
+
+
 def resolve_shade(grooms, cam, lights, filt, vis_center, vis_cons, rgba, stream=None):
     arr, n = _handles(grooms)
     c, L, f = camera_struct(cam), lights_struct(lights), filter_struct(filt)
@@ -266,6 +286,24 @@ def shade_backward(grooms, cam, lights, filt, vis_center, vis_cons, grad_rgba, g
     gal = (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in grad_albedo])
     check(lib().hm_shade_backward(arr, n, ctypes.byref(c), ctypes.byref(L), ctypes.byref(f), _dptr(vis_center),
                                   _dptr(vis_cons), _dptr(grad_rgba), glv, gal, _dptr(scratch), _stream_ptr(stream)))
+
+
+def set_tuning(**kw):
+    """Set launch-shape knobs (see hm_tuning in include/hm.h); unnamed ones
+    keep their current value."""
+    t = Tuning()
+    check(lib().hm_get_tuning(ctypes.byref(t)))
+    for k, v in kw.items():
+        if k not in TUNING_FIELDS:
+            raise KeyError(k)
+        setattr(t, k, int(v))
+    check(lib().hm_set_tuning(ctypes.byref(t)))
+
+
+def get_tuning() -> dict:
+    t = Tuning()
+    check(lib().hm_get_tuning(ctypes.byref(t)))
+    return {k: int(getattr(t, k)) for k in TUNING_FIELDS}
 
 
 def set_phase_events(events):

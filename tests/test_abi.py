@@ -112,3 +112,23 @@ def test_render_and_resolve_reject_bad_arguments(L):
     assert L.hm_set_phase_events(None, 7) == INVALID
     assert L.hm_set_phase_events(None, 0) == 0
     assert L.hm_probe_atomic_min(None, 10, 1, 0, None) == INVALID
+
+
+def test_tuning_and_range_arguments(L):
+    t = hm.Tuning()
+    assert L.hm_get_tuning(ctypes.byref(t)) == 0
+    assert t.raster_min_blocks in (3, 4) and t.resolve_tile_h in (16, 32)
+    for field, bad in (("raster_precheck", 2), ("raster_min_blocks", 5), ("raster_ctas_per_sm", -1),
+                       ("resolve_tile_h", 24)):
+        b = hm.Tuning()
+        L.hm_get_tuning(ctypes.byref(b))
+        setattr(b, field, bad)
+        assert L.hm_set_tuning(ctypes.byref(b)) == INVALID, field
+    assert L.hm_set_tuning(None) == INVALID
+    sc = synth.tiny_scene(0, num_strands=10)
+    cam = hm.camera_struct(sc.camera)
+    fake = ctypes.c_void_p(1 << 20)
+    grooms = (ctypes.c_void_p * 2)(1 << 20, 2 << 20)
+    for first, count in ((-1, 1), (0, 0), (1, 2), (2, 1)):
+        assert L.hm_render_visibility_range(grooms, 2, first, count, ctypes.byref(cam), fake,
+                                            ctypes.c_void_p(2 << 20), None, 1, None, None) == INVALID
