@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=["single_1080p", "crowd_4k", "tiny_256", "lod_sweep"],
+    ap.add_argument("--workload", choices=["single_1080p", "crowd_4k", "tiny_256", "lod_sweep", "grad_512"],
                     default="single_1080p")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -262,6 +262,23 @@ def run_reference(args, rank, world):
     return 0
 
 
+def max_over_ranks(t: float, world: int, device="cuda") -> float:
+    """Slowest rank's time (the job's time) when running under
+    torch.distributed; t itself on a single process."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(units_per_rank: int, steps: int, world: int, t_max: float) -> float:
+    """Whole-job rate: every rank's units over the slowest rank's time."""
+    return units_per_rank * steps * world / t_max
+
+
 def _timed(torch, step, steps, flush):
     """Per-step CUDA-event times (ms) of `step`, L2 flushed before each."""
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -319,18 +336,14 @@ def run_crowd(args, rank, world, local_rank):
         cr.render_per_character()
     t_pc = _timed(torch, cr.render_per_character, max(10, args.steps // 4), flush)
     hm.get_device_status()
-    tg = sum(t_graph) * 1e-3
-    if world > 1:
-        tt = torch.tensor([tg], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tg = float(tt.item())
+    tg = max_over_ranks(sum(t_graph) * 1e-3, world)
     if rank != 0:
         return 0
     n = len(scene.grooms)
     atomics = st["covered_cons"] + st["covered_center"]
     ms_g = tg / args.steps * 1e3
     ms_pc = statistics.mean(t_pc)
-    line = {"metric": METRIC, "value": segs * args.steps * world / tg, "unit": UNIT, "n_gpus": world,
+    line = {"metric": METRIC, "value": job_throughput(segs, args.steps, world, tg), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_g, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
             "config": dict(cfg, parallelism=f"replicas x{world}", batching="one render + one resolve call over "
@@ -402,6 +415,72 @@ def run_lod_sweep(args, rank, world, local_rank):
     return 0
 
 
+def run_grad(args, rank, world, local_rank):
+    """One gradient step of the differentiation workload (512x512, 20k
+    strands x 12 segments): forward (visibility + resolve) and the adjoint
+    (hm_shade_backward) w.r.t. layer vertices and albedo."""
+    import torch
+    from paper_2607_04230_b300 import build, hm, synth
+    build.build()
+    torch.cuda.set_device(local_rank)
+    sc = synth.scene_grad_512()
+    g = sc.grooms[0]
+    grooms = hm.upload_scene(sc)
+    W, H = sc.camera.width, sc.camera.height
+    frame = hm.Frame(W, H)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    grad = torch.randn(frame.rgba.shape, device="cuda", generator=gen)
+    glv = torch.zeros(g.layer_verts.shape, device="cuda")
+    galb = torch.zeros(g.strand_albedo.shape, device="cuda")
+    scratch = torch.empty(hm.backward_scratch_bytes(W, H) // 4, device="cuda")
+    ev = {}
+
+    def fwd():
+        hm.render(grooms, sc, frame)
+
+    def bwd():
+        hm.shade_backward(grooms, sc.camera, sc.lights, sc.filt, frame.vis_center, frame.vis_cons, grad, [glv],
+                          [galb], scratch)
+
+    def step():
+        fwd()
+        bwd()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    segs = hm.stats_dict(frame.stats)["segments"]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(_gpu_uuid(torch, local_rank))
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(k)
+        evs[k][0].record()
+        fwd()
+        evs[k][1].record()
+        bwd()
+        evs[k][2].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    hm.get_device_status()
+    f_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    b_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": segs / ((f_ms + b_ms) * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": f_ms + b_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
+            "config": {"workload": "differentiation: forward + adjoint of the resolve, 512x512, 256 scalp "
+                                   "triangles, 6 layers, 20k strands x 12 segments",
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "forward_ms": f_ms, "backward_ms": b_ms, "gradient_steps_per_s": 1e3 / (f_ms + b_ms),
+            "gpu_launches": 7 * args.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _gpu_uuid(torch, dev):
     u = str(torch.cuda.get_device_properties(dev).uuid)
     return u if u.startswith("GPU-") else "GPU-" + u
@@ -461,12 +540,8 @@ def run_native(args, rank, world, local_rank):
     frame_ms = [e[0].elapsed_time(e[5]) for e in ev]
     phase_ms = {name: sum(e[a].elapsed_time(e[b]) for e in ev) / args.steps
                 for name, a, b in (("clear", 0, 1), ("lod", 1, 2), ("raster", 2, 3), ("resolve", 4, 5))}
-    t_total = sum(frame_ms) * 1e-3
-    if world > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-    value = segs * args.steps * world / t_total
+    t_total = max_over_ranks(sum(frame_ms) * 1e-3, world)
+    value = job_throughput(segs, args.steps, world, t_total)
     hm.get_device_status()
 
     # end to end through the public API with host buffers: H2D of the hair
@@ -492,12 +567,8 @@ def run_native(args, rank, world, local_rank):
             if k >= 3:
                 evs[k - 3][1].record()
         torch.cuda.synchronize()
-        te = sum(a.elapsed_time(b) for a, b in evs) * 1e-3
-        if world > 1:
-            tt = torch.tensor([te], dtype=torch.float64, device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": segs * e2e_steps * world / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        te = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) * 1e-3, world)
+        e2e = {"value": job_throughput(segs, e2e_steps, world, te), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": te / e2e_steps * 1e3}
 
     if rank != 0:
@@ -553,7 +624,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    runner = {"crowd_4k": run_crowd, "lod_sweep": run_lod_sweep}.get(args.workload, run_native)
+    runner = {"crowd_4k": run_crowd, "lod_sweep": run_lod_sweep, "grad_512": run_grad}.get(args.workload, run_native)
     try:
         return runner(args, rank, world, local_rank)
     finally:

@@ -139,10 +139,25 @@ hm_status build_table(const hm_groom *grooms, int32_t n, hm::CallTable &tab) {
     return HM_OK;
 }
 
+// Failure injection for tests: with HM_FAIL_ALLOC_AFTER=N in the
+// environment, the library's device allocations after the first N report
+// HM_ERR_OOM without calling the allocator (read once per process).
+bool injected_alloc_failure() {
+    static long limit = -2;
+    static long done = 0;
+    if (limit == -2) {
+        const char *e = std::getenv("HM_FAIL_ALLOC_AFTER");
+        limit = e ? std::strtol(e, nullptr, 10) : -1;
+    }
+    if (limit < 0) return false;
+    return done++ >= limit;
+}
+
 template <typename T>
 hm_status dev_alloc(T **p, size_t count, const char *what) {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (injected_alloc_failure()) return fail(HM_ERR_OOM, "device allocation failed (injected by HM_FAIL_ALLOC_AFTER)");
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
     if (e != cudaSuccess) return cuda_fail(e, what);
     return HM_OK;
