@@ -241,7 +241,7 @@ size_t hm_backward_scratch_bytes(int32_t width, int32_t height);
  * device memory is owned by another allocator with a fixed budget.  This
  * entry point takes the same inputs and outputs as hm_shade_backward but no
  * d_scratch: its colour-gradient scratch is a static array of the library
- * (HM_NOALLOC_MAX_PIXELS * 16 bytes = 4 MiB, held on every GPU that loads
+ * (HM_NOALLOC_MAX_PIXELS * 32 bytes = 8 MiB, held on every GPU that loads
  * libhm until the process exits).  It calls no allocator.
  *  - Frames larger than HM_NOALLOC_MAX_PIXELS pixels are rejected with
  *    HM_ERR_CAPACITY before anything is launched.

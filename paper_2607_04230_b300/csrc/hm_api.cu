@@ -547,7 +547,7 @@ extern "C" {
 
 size_t hm_backward_scratch_bytes(int32_t width, int32_t height) {
     if (width < 1 || height < 1) return 0;
-    return (size_t)width * (size_t)height * 16;
+    return (size_t)width * (size_t)height * 32;     // colour gradient + screen-tangent gradients per pixel
 }
 
 hm_status hm_shade_backward(const hm_groom *grooms, int32_t n, const hm_camera *cam, const hm_lights *lights,
@@ -584,8 +584,9 @@ hm_status hm_shade_backward(const hm_groom *grooms, int32_t n, const hm_camera *
 // ---------------------------------------------------------------------------
 namespace {
 
-// 16 bytes (one float4 colour gradient) per pixel of the largest frame.
-static __device__ __align__(256) float4 g_noalloc_scratch[HM_NOALLOC_MAX_PIXELS];
+// 32 bytes per pixel of the largest frame: the colour gradient and the
+// screen-tangent gradients (two float4).
+static __device__ __align__(256) float4 g_noalloc_scratch[2 * HM_NOALLOC_MAX_PIXELS];
 
 // Device address of g_noalloc_scratch on the current device, looked up once
 // per device (the host-side symbol is only a stand-in, never a device

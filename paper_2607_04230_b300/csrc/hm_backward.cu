@@ -36,13 +36,13 @@ __device__ __forceinline__ float3 unit_adjoint(float3 u, float len, float3 du) {
 }
 
 struct Sink {
-    float *glv;              // [L][V][3] or NULL
+    float *glv;              // [L][V][3] (global, or this CTA's shared copy) or NULL
     int V;
 };
 
 __device__ __forceinline__ void scatter_layer_point(const Sink &sk, const Root &r, int k, float3 dP) {
     if (!sk.glv || (dP.x == 0.f && dP.y == 0.f && dP.z == 0.f)) return;
-    float *row = sk.glv + (int64_t)k * sk.V * 3;
+    float *row = sk.glv + (int64_t)k * sk.V * 3;   // atomicAdd works on either address space
     const int idx[3] = {r.i0, r.i1, r.i2};
     const float b[3] = {r.b0, r.b1, r.b2};
 #pragma unroll
@@ -267,27 +267,10 @@ __device__ __forceinline__ float2 reconstruct_adjoint(const int *s_dg, const flo
     return dTs;
 }
 
-__device__ __forceinline__ void ts_to_geometry(const CallTable &tab, const uint64_t *bases, const CamDev &cam,
-                                               const BwdSinks &sinks, uint64_t key, int px, int py, float2 dTs,
-                                               uint32_t *status) {
-    if (dTs.x == 0.f && dTs.y == 0.f) return;
-    const Decoded d = decode_key(tab, bases, cam, key, px, py, status);
-    if (!d.ok || d.iso) return;
-    const GroomDev &g = tab.g[d.gi];
-    Sink sk;
-    sk.glv = sinks.glv[d.gi];
-    sk.V = g.V;
-    if (!sk.glv) return;
-    float3 dX, dT;
-    screen_tangent_adjoint(cam, d.X, d.T, dTs, dX, dT);
-    const Root r = make_root(g, d.s, __ldg(&g.sface[d.s]));
-    geometry_adjoint(g, r, d.C, d.j, d.t, dX, dT, sk);
-}
-
 __global__ void __launch_bounds__(kResolveThreads) resolve_adjoint_kernel(
     CallTable tab, CamDev cam, LightsDev Ls, FilterDev fp, const uint64_t *__restrict__ vis_c,
     const uint64_t *__restrict__ vis_a, const float4 *__restrict__ grad_rgba, float4 *__restrict__ dC,
-    BwdSinks sinks, uint32_t *status) {
+    float4 *__restrict__ dTs, uint32_t *status) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int R = fp.enabled ? fp.radius : 0;
     const int sw = kTileW + 2 * R, sh = kTileH + 2 * R, ns = sw * sh;
@@ -448,51 +431,110 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_adjoint_kernel(
         atomicAdd(&p->y, v.y);
         atomicAdd(&p->z, v.z);
     }
-    // screen-tangent gradients to the geometry of the reference segments
-    if (inside) {
-        ts_to_geometry(tab, s_bases, cam, sinks, kgP, gx, gy, dTsG, status);
-        ts_to_geometry(tab, s_bases, cam, sinks, ka, gx, gy, dTsA, status);
-    }
+    // screen-tangent gradients of the reference segments, for the geometry pass
+    if (inside) dTs[(int64_t)gy * W + gx] = make_float4(dTsG.x, dTsG.y, dTsA.x, dTsA.y);
 }
 
-// Shading adjoint of every centre-sample pixel with a colour gradient.
-__global__ void __launch_bounds__(256) shade_adjoint_kernel(CallTable tab, CamDev cam, LightsDev Ls,
-                                                            const uint64_t *__restrict__ vis_c,
-                                                            const float4 *__restrict__ dC, BwdSinks sinks,
-                                                            uint32_t *status) {
+// Geometry pass, one thread per pixel (persistent grid): the shading
+// adjoint of the centre-sample pixel (colour gradient from kernel 1) plus the
+// screen-tangent adjoints of the pixel's reference segments, chained through
+// the strand geometry to the layer vertices, and the albedo gradient.  When
+// every groom's layer-vertex gradient fits, a CTA accumulates it in shared
+// memory and adds it to the global arrays once at the end.
+constexpr int kGeoThreads = 512;
+
+struct GeoLayout {
+    int32_t off[HM_MAX_GROOMS_PER_CALL];   // float offset of groom i in the shared copy, -1: none
+    int32_t total;                         // floats in the shared copy, 0: accumulate globally
+};
+
+__device__ __forceinline__ Sink geo_sink(const GeoLayout &lay, float *s_g, const BwdSinks &sinks, int gi, int V) {
+    Sink sk;
+    sk.V = V;
+    sk.glv = sinks.glv[gi];
+    if (sk.glv && lay.total > 0) sk.glv = s_g + lay.off[gi];
+    return sk;
+}
+
+__global__ void __launch_bounds__(kGeoThreads) geometry_adjoint_kernel(CallTable tab, CamDev cam, LightsDev Ls,
+                                                                       const uint64_t *__restrict__ vis_c,
+                                                                       const uint64_t *__restrict__ vis_a,
+                                                                       const float4 *__restrict__ dC,
+                                                                       const float4 *__restrict__ dTs,
+                                                                       BwdSinks sinks, GeoLayout lay,
+                                                                       uint32_t *status) {
+    extern __shared__ __align__(16) float s_g[];
     __shared__ uint64_t s_bases[HM_MAX_GROOMS_PER_CALL + 1];
     if (threadIdx.x <= tab.n) {
         uint64_t b = 0;
         for (int i = 0; i < (int)threadIdx.x; ++i) b += (uint64_t)tab.g[i].S;
         s_bases[threadIdx.x] = b;
     }
+    for (int i = threadIdx.x; i < lay.total; i += blockDim.x) s_g[i] = 0.f;
     __syncthreads();
     const int64_t npx = (int64_t)cam.W * cam.H;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npx; p += (int64_t)gridDim.x * blockDim.x) {
-        const float4 g4 = __ldg(&dC[p]);
-        if (g4.x == 0.f && g4.y == 0.f && g4.z == 0.f) continue;
-        const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + p));
-        if (key_empty(kg)) continue;
+        const float4 gc = __ldg(&dC[p]);
+        const float4 gt = __ldg(&dTs[p]);
+        const bool hasC = gc.x != 0.f || gc.y != 0.f || gc.z != 0.f;
+        const bool hasG = gt.x != 0.f || gt.y != 0.f;
+        const bool hasA = gt.z != 0.f || gt.w != 0.f;
+        if (!hasC && !hasG && !hasA) continue;
         const int px = (int)(p % cam.W), py = (int)(p / cam.W);
-        const Decoded d = decode_key(tab, s_bases, cam, kg, px, py, status);
-        if (!d.ok) continue;
-        const GroomDev &g = tab.g[d.gi];
-        const float4 a = __ldg(&g.albedo[d.s]);
-        float3 dX, dT, dalb;
-        shade_adjoint(d.X, d.T, f3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt, f3(g4.x, g4.y, g4.z), dX, dT,
-                      dalb);
-        float *ga = sinks.galb[d.gi];
-        if (ga) {
-            atomicAdd(ga + 3 * d.s + 0, dalb.x);
-            atomicAdd(ga + 3 * d.s + 1, dalb.y);
-            atomicAdd(ga + 3 * d.s + 2, dalb.z);
+        if (hasC || hasG) {
+            const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + p));
+            if (!key_empty(kg)) {
+                const Decoded d = decode_key(tab, s_bases, cam, kg, px, py, status);
+                if (d.ok) {
+                    const GroomDev &g = tab.g[d.gi];
+                    float3 dX = f3(0.f, 0.f, 0.f), dT = f3(0.f, 0.f, 0.f);
+                    if (hasC) {
+                        const float4 a = __ldg(&g.albedo[d.s]);
+                        float3 dalb;
+                        shade_adjoint(d.X, d.T, f3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt,
+                                      f3(gc.x, gc.y, gc.z), dX, dT, dalb);
+                        float *ga = sinks.galb[d.gi];
+                        if (ga) {
+                            atomicAdd(ga + 3 * d.s + 0, dalb.x);
+                            atomicAdd(ga + 3 * d.s + 1, dalb.y);
+                            atomicAdd(ga + 3 * d.s + 2, dalb.z);
+                        }
+                    }
+                    if (hasG && !d.iso) {
+                        float3 tX, tT;
+                        screen_tangent_adjoint(cam, d.X, d.T, make_float2(gt.x, gt.y), tX, tT);
+                        dX = add3(dX, tX);
+                        dT = add3(dT, tT);
+                    }
+                    const Sink sk = geo_sink(lay, s_g, sinks, d.gi, g.V);
+                    if (sk.glv) geometry_adjoint(g, make_root(g, d.s, __ldg(&g.sface[d.s])), d.C, d.j, d.t, dX, dT, sk);
+                }
+            }
         }
-        Sink sk;
-        sk.glv = sinks.glv[d.gi];
-        sk.V = g.V;
-        if (sk.glv) {
-            const Root r = make_root(g, d.s, __ldg(&g.sface[d.s]));
-            geometry_adjoint(g, r, d.C, d.j, d.t, dX, dT, sk);
+        if (hasA) {
+            const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + p));
+            if (!key_empty(ka)) {
+                const Decoded d = decode_key(tab, s_bases, cam, ka, px, py, status);
+                if (d.ok && !d.iso) {
+                    const GroomDev &g = tab.g[d.gi];
+                    float3 tX, tT;
+                    screen_tangent_adjoint(cam, d.X, d.T, make_float2(gt.z, gt.w), tX, tT);
+                    const Sink sk = geo_sink(lay, s_g, sinks, d.gi, g.V);
+                    if (sk.glv) geometry_adjoint(g, make_root(g, d.s, __ldg(&g.sface[d.s])), d.C, d.j, d.t, tX, tT, sk);
+                }
+            }
+        }
+    }
+    if (lay.total == 0) return;
+    __syncthreads();
+    for (int gi = 0; gi < tab.n; ++gi) {
+        if (lay.off[gi] < 0) continue;
+        const int nf = tab.g[gi].L * tab.g[gi].V * 3;
+        float *dst = sinks.glv[gi];
+        const float *src = s_g + lay.off[gi];
+        for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+            const float v = src[i];
+            if (v != 0.f) atomicAdd(dst + i, v);
         }
     }
 }
@@ -514,34 +556,48 @@ size_t adjoint_smem_bytes(int radius) {
     return (b + 15) & ~(size_t)15;
 }
 
+// Shared-memory budget for the geometry pass's copy of the layer-vertex
+// gradients; larger sets (big crowds) accumulate straight into global memory.
+constexpr int kGeoSmemFloats = 48 * 1024;
+
 cudaError_t launch_resolve_adjoint(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                                    const uint64_t *vis_c, const uint64_t *vis_a, const float *grad_rgba,
                                    float *const *glv, float *const *galb, void *scratch, uint32_t *status,
                                    cudaStream_t st) {
     const int64_t npx = (int64_t)cam.W * cam.H;
     float4 *dC = static_cast<float4 *>(scratch);
+    float4 *dTs = dC + npx;
     BwdSinks sinks;
+    GeoLayout lay;
+    int32_t total = 0;
     for (int i = 0; i < HM_MAX_GROOMS_PER_CALL; ++i) {
         sinks.glv[i] = (i < tab.n && glv) ? glv[i] : nullptr;
         sinks.galb[i] = (i < tab.n && galb) ? galb[i] : nullptr;
+        lay.off[i] = -1;
+        if (sinks.glv[i]) {
+            lay.off[i] = total;
+            total += tab.g[i].L * tab.g[i].V * 3;
+        }
     }
+    lay.total = total <= kGeoSmemFloats ? total : 0;
     const int sms = num_sms();
-    zero_float4_kernel<<<sms * 8, 256, 0, st>>>(dC, npx);
+    zero_float4_kernel<<<sms * 8, 256, 0, st>>>(dC, 2 * npx);
     const int R = fp.enabled ? fp.radius : 0;
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(resolve_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)adjoint_smem_bytes(HM_MAX_FILTER_RADIUS));
+        cudaFuncSetAttribute(geometry_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kGeoSmemFloats * sizeof(float)));
         attr_set = true;
     }
     dim3 grid((cam.W + kTileW - 1) / kTileW, (cam.H + kTileH - 1) / kTileH);
     resolve_adjoint_kernel<<<grid, kResolveThreads, adjoint_smem_bytes(R), st>>>(
-        tab, cam, Ls, fp, vis_c, vis_a, reinterpret_cast<const float4 *>(grad_rgba), dC, sinks, status);
+        tab, cam, Ls, fp, vis_c, vis_a, reinterpret_cast<const float4 *>(grad_rgba), dC, dTs, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int64_t want = (npx + 255) / 256;
-    const int g2 = (int)(want < (int64_t)sms * 16 ? (want > 0 ? want : 1) : (int64_t)sms * 16);
-    shade_adjoint_kernel<<<g2, 256, 0, st>>>(tab, cam, Ls, vis_c, dC, sinks, status);
+    geometry_adjoint_kernel<<<sms, kGeoThreads, (size_t)lay.total * sizeof(float), st>>>(tab, cam, Ls, vis_c, vis_a,
+                                                                                          dC, dTs, sinks, lay, status);
     return cudaGetLastError();
 }
 
