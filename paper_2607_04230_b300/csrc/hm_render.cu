@@ -199,27 +199,84 @@ __global__ void __launch_bounds__(kLodThreads) lod_kernel(CallTable tab, CamDev 
 // exact predicate and issues the 64-bit atomicMin for each layer.
 // ---------------------------------------------------------------------------
 struct SegRec {
-    int32_t uA, vA, uB, vB;      // endpoints in the major (u) / minor (v) frame, 1/256 px
-    float zA, zB;
-    int32_t hc;
-    int32_t ilo;                 // first major pixel index
-    uint32_t id_lo, id_hi;       // payload strand << 7 | segment
-    int32_t start;               // first work item of this segment
-    int32_t xmajor;
+    int32_t uA, vA;              // start point in the major (u) / minor (v) frame, 1/256 px
+    int32_t du, dv;              // B - A in that frame
+    int32_t umin, umax, vmin, vmax;
+    float zA, dz;                // linear depth at A, zB - zA
     float fden;                  // float(|B - A|^2), the depth parameter's denominator
-    int32_t pad_;
+    float slope;                 // dv / du (0 for a point)
+    int32_t hc;                  // centre-sample half-width, 1/256 px
+    int32_t ilo;                 // first major pixel index
+    int32_t start;               // first work item of this segment
+    int32_t flags;               // bit0: u is x; bit1: short (32-bit arithmetic)
+    uint32_t id_lo, id_hi;       // payload strand << 7 | segment
 };
 
 constexpr int kRasterThreads = 256;
 constexpr int kRasterWarps = kRasterThreads / 32;
 
-// The exact segment-vs-box predicate (bounding boxes overlap and the box's
-// corners are not all strictly on one side of the line) in incremental form:
-// the corner cross products are e0 + h (sy dX - sx dY) for sx, sy = +-1, with
-// e0 = dX (cy - YA) - dY (cx - XA) the cross product at the box centre, so
-// "min <= 0 <= max" is |e0| <= h (|dX| + |dY|).  e0 and the depth numerator
-// num = (cx - XA) dX + (cy - YA) dY change by constants from one pixel to the
-// next along the minor axis.
+// Candidate pixels of one work item: the minor-axis pixels of major-axis
+// pixel i whose conservative box can meet the segment.  The exact
+// predicate (bounding boxes overlap and the box's corners are not all
+// strictly on one side of the line) is evaluated in incremental form: the
+// corner cross products are e0 + h (sy dU - sx dV) for sx, sy = +-1, with e0 =
+// dU (cv - vA) - dV (cu - uA) the cross product at the box centre (the x/y one
+// up to sign), so "min <= 0 <= max" is |e0| <= h (|dU| + |dV|); e0 and the
+// depth numerator num = (cu - uA) dU + (cv - vA) dV change by constants from
+// one pixel to the next along the minor axis.  For short segments (|dU|,
+// |dV| < 2^14) every quantity fits in 32 bits; long ones use 64 bits.
+template <typename I, bool kPrecheck>
+__device__ __forceinline__ void raster_item(const SegRec &q, int i, int W, int H, uint64_t *__restrict__ vis_c,
+                                            uint64_t *__restrict__ vis_a, uint32_t &n_cons, uint32_t &n_cen) {
+    const bool xm = q.flags & 1;
+    const int32_t ua = max(256 * i, q.umin), ub = min(256 * i + 256, q.umax);
+    const float va = (float)(ua - q.uA) * q.slope, vb = (float)(ub - q.uA) * q.slope;
+    const float flo = floorf(fminf(va, vb)), fhi = ceilf(fmaxf(va, vb));
+    // float error of the minor range is below |dV| 2^-21 + 1 unit
+    const int32_t slack = 8 + (abs(q.dv) >> 20);
+    const int64_t vlo = (int64_t)q.vA + (int64_t)flo - slack;
+    const int64_t vhi = (int64_t)q.vA + (int64_t)fhi + slack;
+    const int dimv = xm ? H : W;
+    const int mlo = (int)max(((vlo + 255) >> 8) - 1, (int64_t)0);
+    const int mhi = (int)min(vhi >> 8, (int64_t)(dimv - 1));
+    if (mlo > mhi) return;
+    const int32_t cu = 256 * i + 128;
+    const I ru = (I)(cu - q.uA), rv = (I)(256 * mlo + 128 - q.vA);
+    const I du = q.du, dv = q.dv;
+    I e0 = du * rv - dv * ru;
+    I num = ru * du + rv * dv;
+    const I de = du * 256, dn = dv * 256;
+    const I span = (I)abs(q.du) + (I)abs(q.dv);
+    const I k_cons = span * 128, k_cen = span * (I)q.hc;
+    const bool ucen = (q.umin <= cu + q.hc) && (q.umax >= cu - q.hc);
+    const uint64_t id = ((uint64_t)q.id_hi << 32) | q.id_lo;
+    const bool degenerate = (q.du == 0 && q.dv == 0);
+    for (int m = mlo; m <= mhi; ++m, e0 += de, num += dn) {
+        const int32_t cv = 256 * m + 128;
+        // conservative: v-overlap (u-overlap holds by construction) and line test
+        if (q.vmin > cv + 128 || q.vmax < cv - 128) continue;
+        if (e0 > k_cons || e0 < -k_cons) continue;
+        const bool cen = ucen && q.vmin <= cv + q.hc && q.vmax >= cv - q.hc && e0 <= k_cen && e0 >= -k_cen;
+        float t = 0.0f;
+        if (!degenerate) {
+            const float fn = sizeof(I) == 4 ? __int2float_rn((int32_t)num) : __ll2float_rn((int64_t)num);
+            t = fclamp(fdiv(fn, q.fden), 0.0f, 1.0f);
+        }
+        const float z = fclamp(fadd(q.zA, fmul(q.dz, t)), 0.0f, 1.0f);
+        uint32_t d24 = (uint32_t)floorf(fmul(z, 16777216.0f));
+        d24 = d24 > 16777215u ? 16777215u : d24;
+        const uint64_t key = ((uint64_t)d24 << 40) | id;
+        const int px = xm ? i : m, py = xm ? m : i;
+        const size_t p = (size_t)py * (size_t)W + (size_t)px;
+        n_cons += 1;
+        n_cen += cen;
+        if (!kPrecheck || key < __ldcg(reinterpret_cast<const unsigned long long *>(vis_a + p)))
+            atomicMin(reinterpret_cast<unsigned long long *>(vis_a + p), (unsigned long long)key);
+        if (cen && (!kPrecheck || key < __ldcg(reinterpret_cast<const unsigned long long *>(vis_c + p))))
+            atomicMin(reinterpret_cast<unsigned long long *>(vis_c + p), (unsigned long long)key);
+    }
+}
+
 template <bool kPrecheck, int kMinBlocks>
 __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(CallTable tab, CamDev cam, uint64_t *__restrict__ vis_c,
                                                                 uint64_t *__restrict__ vis_a, hm_frame_stats *stats) {
@@ -267,27 +324,33 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
             const Proj B = project(cam, cp[1]);
             if (A.valid && B.valid) {
                 const bool xm = abs(B.X - A.X) >= abs(B.Y - A.Y);
-                r.uA = xm ? A.X : A.Y;
-                r.vA = xm ? A.Y : A.X;
-                r.uB = xm ? B.X : B.Y;
-                r.vB = xm ? B.Y : B.X;
+                const int32_t uA = xm ? A.X : A.Y, vA = xm ? A.Y : A.X;
+                const int32_t uB = xm ? B.X : B.Y, vB = xm ? B.Y : B.X;
+                r.uA = uA;
+                r.vA = vA;
+                r.du = uB - uA;
+                r.dv = vB - vA;
+                r.umin = min(uA, uB);
+                r.umax = max(uA, uB);
+                r.vmin = min(vA, vB);
+                r.vmax = max(vA, vB);
                 r.zA = A.z;
-                r.zB = B.z;
+                r.dz = fsub(B.z, A.z);
                 r.hc = centre_halfwidth(cam, g.width_m, A.w, B.w);
                 const uint64_t id = ((g.base + (uint64_t)s) << 7) | (uint64_t)j;
                 r.id_lo = (uint32_t)id;
                 r.id_hi = (uint32_t)(id >> 32);
-                r.xmajor = xm;
                 const int64_t dX = (int64_t)B.X - A.X, dY = (int64_t)B.Y - A.Y;
                 r.fden = __ll2float_rn(dX * dX + dY * dY);
+                r.slope = r.du == 0 ? 0.0f : (float)r.dv / (float)r.du;
+                const bool shrt = abs(r.du) < (1 << 14) && abs(r.dv) < (1 << 14);
+                r.flags = (xm ? 1 : 0) | (shrt ? 2 : 0);
                 const int du = xm ? W : H, dv = xm ? H : W;
-                const int32_t umin = min(r.uA, r.uB), umax = max(r.uA, r.uB);
-                const int32_t vmin = min(r.vA, r.vB), vmax = max(r.vA, r.vB);
                 // pixel m's conservative box spans [256 m, 256 m + 256]
-                int ilo = ((umin + 255) >> 8) - 1, ihi = umax >> 8;
+                int ilo = ((r.umin + 255) >> 8) - 1, ihi = r.umax >> 8;
                 ilo = max(ilo, 0);
                 ihi = min(ihi, du - 1);
-                const bool vin = vmax >= 0 && vmin <= 256 * dv;
+                const bool vin = r.vmax >= 0 && r.vmin <= 256 * dv;
                 r.ilo = ilo;
                 nmaj = (vin && ihi >= ilo) ? ihi - ilo + 1 : 0;
             }
@@ -313,61 +376,10 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
             if (item >= items) continue;
             const SegRec &q = rec[src];
             const int i = q.ilo + (item - q.start);
-            const int32_t du = q.uB - q.uA, dvv = q.vB - q.vA;
-            const int32_t umin = min(q.uA, q.uB), umax = max(q.uA, q.uB);
-            const int32_t vmin = min(q.vA, q.vB), vmax = max(q.vA, q.vB);
-            const int32_t ua = max(256 * i, umin), ub = min(256 * i + 256, umax);
-            float flo, fhi;
-            if (du == 0) {
-                flo = 0.0f;
-                fhi = 0.0f;
-            } else {
-                const float slope = (float)dvv / (float)du;
-                const float va = (float)(ua - q.uA) * slope, vb = (float)(ub - q.uA) * slope;
-                flo = floorf(fminf(va, vb));
-                fhi = ceilf(fmaxf(va, vb));
-            }
-            // float error of the minor range is below |dv| 2^-21 + 1 unit
-            const int32_t slack = 8 + (abs(dvv) >> 20);
-            const int64_t vlo = (int64_t)q.vA + (int64_t)flo - slack;
-            const int64_t vhi = (int64_t)q.vA + (int64_t)fhi + slack;
-            const int dimv = q.xmajor ? H : W;
-            const int mlo = (int)max(((vlo + 255) >> 8) - 1, (int64_t)0);
-            const int mhi = (int)min(vhi >> 8, (int64_t)(dimv - 1));
-            if (mlo > mhi) continue;
-            // (u, v) frame: e0 = du (cv - vA) - dv (cu - uA) is the x/y cross
-            // product up to sign, num is symmetric; both step along v
-            const int32_t cu = 256 * i + 128;
-            const int64_t du64 = du, dv64 = dvv;
-            int64_t e0 = du64 * (int64_t)(256 * mlo + 128 - q.vA) - dv64 * (int64_t)(cu - q.uA);
-            int64_t num = (int64_t)(cu - q.uA) * du64 + (int64_t)(256 * mlo + 128 - q.vA) * dv64;
-            const int64_t de = 256 * du64, dn = 256 * dv64;
-            const int64_t span = (int64_t)abs(du) + (int64_t)abs(dvv);
-            const int64_t k_cons = 128 * span, k_cen = (int64_t)q.hc * span;
-            // box overlap along u for half-width h: umin <= cu + h and umax >= cu - h
-            const bool ucen = (umin <= cu + q.hc) && (umax >= cu - q.hc);
-            const uint64_t id = ((uint64_t)q.id_hi << 32) | q.id_lo;
-            const bool degenerate = (du == 0 && dvv == 0);
-            for (int m = mlo; m <= mhi; ++m, e0 += de, num += dn) {
-                const int32_t cv = 256 * m + 128;
-                // conservative: v-overlap (u-overlap holds by construction) and line test
-                if (vmin > cv + 128 || vmax < cv - 128) continue;
-                if (e0 > k_cons || e0 < -k_cons) continue;
-                const bool cen = ucen && vmin <= cv + q.hc && vmax >= cv - q.hc && e0 <= k_cen && e0 >= -k_cen;
-                float t = 0.0f;
-                if (!degenerate) t = fclamp(fdiv(__ll2float_rn(num), q.fden), 0.0f, 1.0f);
-                const uint64_t key = ((uint64_t)depth24(q.zA, q.zB, t) << 40) | id;
-                const int px = q.xmajor ? i : m, py = q.xmajor ? m : i;
-                const int64_t p = (int64_t)py * W + px;
-                n_cons += 1;
-                n_cen += cen;
-                if (!kPrecheck || key < __ldcg(reinterpret_cast<const unsigned long long *>(vis_a + p)))
-                    atomicMin(reinterpret_cast<unsigned long long *>(vis_a + p), (unsigned long long)key);
-                if (cen) {
-                    if (!kPrecheck || key < __ldcg(reinterpret_cast<const unsigned long long *>(vis_c + p)))
-                        atomicMin(reinterpret_cast<unsigned long long *>(vis_c + p), (unsigned long long)key);
-                }
-            }
+            if (q.flags & 2)
+                raster_item<int32_t, kPrecheck>(q, i, W, H, vis_c, vis_a, n_cons, n_cen);
+            else
+                raster_item<int64_t, kPrecheck>(q, i, W, H, vis_c, vis_a, n_cons, n_cen);
         }
         __syncwarp();
     }
