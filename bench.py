@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=["single_1080p", "crowd_4k", "tiny_256", "lod_sweep", "grad_512"],
+    ap.add_argument("--workload", choices=["single_1080p", "crowd_4k", "tiny_256", "lod_sweep", "grad_512",
+                                           "stereo_1080p"],
                     default="single_1080p")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -481,6 +482,52 @@ def run_grad(args, rank, world, local_rank):
     return 0
 
 
+def run_stereo(args, rank, world, local_rank):
+    """Two views (eyes 6.4 cm apart) of the 1080p groom: one multiview
+    render (strands assembled once) plus a resolve per view, against two
+    independent single-view frames."""
+    import torch
+    from paper_2607_04230_b300 import build, hm, synth
+    build.build()
+    torch.cuda.set_device(local_rank)
+    sc, cfg = make_scene("single_1080p")
+    ctr, _, _ = synth._aabb_center(sc.grooms)
+    cams = synth.view_offsets(sc.camera, [-0.032, 0.032], target=ctr)
+    grooms = hm.upload_scene(sc)
+    frames = [hm.Frame(c.width, c.height) for c in cams]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def multi():
+        hm.render_visibility_multiview(grooms, cams, [f.vis_center for f in frames], [f.vis_cons for f in frames],
+                                       stats=frames[0].stats)
+        for c, f in zip(cams, frames):
+            hm.resolve_shade(grooms, c, sc.lights, sc.filt, f.vis_center, f.vis_cons, f.rgba)
+
+    def separate():
+        for c, f in zip(cams, frames):
+            hm.render_visibility(grooms, c, f.vis_center, f.vis_cons, stats=f.stats)
+            hm.resolve_shade(grooms, c, sc.lights, sc.filt, f.vis_center, f.vis_cons, f.rgba)
+
+    for _ in range(args.warmup):
+        multi()
+        separate()
+    tm = _timed(torch, multi, args.steps, flush)
+    ts = _timed(torch, separate, args.steps, flush)
+    hm.get_device_status()
+    if rank != 0:
+        return 0
+    segs = hm.stats_dict(frames[0].stats)["segments"]
+    ms_m, ms_s = statistics.mean(tm), statistics.mean(ts)
+    line = {"metric": METRIC, "value": 2 * segs / (ms_m * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_m, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
+            "config": dict(cfg, workload="stereo: the 1080p groom seen by two eyes 6.4 cm apart"),
+            "multiview_ms_per_view": ms_m / 2, "separate_ms_per_view": ms_s / 2, "speedup": ms_s / ms_m,
+            "gpu_launches": 7 * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _gpu_uuid(torch, dev):
     u = str(torch.cuda.get_device_properties(dev).uuid)
     return u if u.startswith("GPU-") else "GPU-" + u
@@ -624,7 +671,8 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    runner = {"crowd_4k": run_crowd, "lod_sweep": run_lod_sweep, "grad_512": run_grad}.get(args.workload, run_native)
+    runner = {"crowd_4k": run_crowd, "lod_sweep": run_lod_sweep, "grad_512": run_grad,
+              "stereo_1080p": run_stereo}.get(args.workload, run_native)
     try:
         return runner(args, rank, world, local_rank)
     finally:

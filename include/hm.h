@@ -59,6 +59,7 @@ typedef enum {
 #define HM_MAX_LIGHTS 8
 #define HM_MAX_FILTER_RADIUS 8
 #define HM_MAX_RESOLUTION 16384
+#define HM_MAX_VIEWS 8
 
 typedef struct hm_groom_s *hm_groom;
 
@@ -187,6 +188,22 @@ hm_status hm_render_visibility(const hm_groom *grooms, int32_t n, const hm_camer
                                uint64_t *d_vis_center, uint64_t *d_vis_cons,
                                const uint32_t *d_scene_d24, int32_t clear,
                                hm_frame_stats *d_stats, void *stream);
+
+/* Multiview rendering (Sec. 5 "Multiview Rendering"): the strands of all
+ * grooms are assembled once and projected into n_views views, each with its
+ * own camera and pair of key layers (d_vis_center[v], d_vis_cons[v]); all
+ * views share width and height.  The LOD pre-pass runs once, for view 0's
+ * camera, and its result (kept in the grooms) serves every view, so each
+ * view's keys equal a single-view render of that camera under view 0's LOD.
+ * Resolve each view with hm_resolve_shade and its own camera.  Both layers
+ * of every view are cleared (or pre-filled from d_scene_d24[v] when
+ * d_scene_d24 and its entry are not NULL) when clear != 0.  d_stats sums
+ * over the views.  Errors as hm_render_visibility; n_views in
+ * 1..HM_MAX_VIEWS. */
+hm_status hm_render_visibility_multiview(const hm_groom *grooms, int32_t n, const hm_camera *cams,
+                                         int32_t n_views, uint64_t *const *d_vis_center,
+                                         uint64_t *const *d_vis_cons, const uint32_t *const *d_scene_d24,
+                                         int32_t clear, hm_frame_stats *d_stats, void *stream);
 
 /* hm_render_visibility for grooms[first .. first + count) only, with strand
  * ids numbered as in the whole n-groom array, so that per-groom calls into

@@ -377,16 +377,26 @@ hm_status hm_render_visibility(const hm_groom *grooms, int32_t n, const hm_camer
                                       stream);
 }
 
-hm_status hm_render_visibility_range(const hm_groom *grooms, int32_t n, int32_t first, int32_t count,
-                                     const hm_camera *cam, uint64_t *d_vis_center, uint64_t *d_vis_cons,
-                                     const uint32_t *d_scene_d24, int32_t clear, hm_frame_stats *d_stats,
-                                     void *stream) {
-    hm_status st = check_camera(cam);
-    if (st != HM_OK) return st;
-    if (!d_vis_center || !d_vis_cons) return fail(HM_ERR_INVALID_ARG, "visibility buffer is NULL");
-    if ((reinterpret_cast<uintptr_t>(d_vis_center) & 15) || (reinterpret_cast<uintptr_t>(d_vis_cons) & 15))
-        return fail(HM_ERR_INVALID_ARG, "visibility buffers must be 16-byte aligned");
-    if (d_vis_center == d_vis_cons) return fail(HM_ERR_INVALID_ARG, "the two layers must be distinct buffers");
+static hm_status render_views(const hm_groom *grooms, int32_t n, int32_t first, int32_t count, const hm_camera *cams,
+                               int32_t n_views, uint64_t *const *d_vis_center, uint64_t *const *d_vis_cons,
+                               const uint32_t *const *d_scene_d24, int32_t clear, hm_frame_stats *d_stats,
+                               void *stream) {
+    if (!cams || n_views < 1 || n_views > HM_MAX_VIEWS) return fail(HM_ERR_INVALID_ARG, "view count out of range");
+    if (!d_vis_center || !d_vis_cons) return fail(HM_ERR_INVALID_ARG, "visibility buffer array is NULL");
+    hm_status st;
+    for (int v = 0; v < n_views; ++v) {
+        if ((st = check_camera(&cams[v])) != HM_OK) return st;
+        if (cams[v].width != cams[0].width || cams[v].height != cams[0].height)
+            return fail(HM_ERR_INVALID_ARG, "views must share width and height");
+        uint64_t *vc = d_vis_center[v], *va = d_vis_cons[v];
+        if (!vc || !va) return fail(HM_ERR_INVALID_ARG, "visibility buffer is NULL");
+        if ((reinterpret_cast<uintptr_t>(vc) & 15) || (reinterpret_cast<uintptr_t>(va) & 15))
+            return fail(HM_ERR_INVALID_ARG, "visibility buffers must be 16-byte aligned");
+        if (vc == va) return fail(HM_ERR_INVALID_ARG, "the two layers must be distinct buffers");
+        for (int u = 0; u < v; ++u)
+            if (d_vis_center[u] == vc || d_vis_cons[u] == va || d_vis_center[u] == va || d_vis_cons[u] == vc)
+                return fail(HM_ERR_INVALID_ARG, "views must use distinct buffers");
+    }
     if (first < 0 || count < 1 || first > n - count) return fail(HM_ERR_INVALID_ARG, "groom range outside 0..n");
     hm::CallTable full;
     st = build_table(grooms, n, full);
@@ -395,19 +405,44 @@ hm_status hm_render_visibility_range(const hm_groom *grooms, int32_t n, int32_t 
     std::memset(&tab, 0, sizeof tab);
     tab.n = count;
     for (int i = 0; i < count; ++i) tab.g[i] = full.g[first + i];   // keeps the whole array's strand ids
-    const hm::CamDev cd = cam_dev(cam);
+    hm::ViewSet views;
+    std::memset(&views, 0, sizeof views);
+    views.n = n_views;
+    for (int v = 0; v < n_views; ++v) {
+        views.cam[v] = cam_dev(&cams[v]);
+        views.vis_c[v] = d_vis_center[v];
+        views.vis_a[v] = d_vis_cons[v];
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int64_t npx = (int64_t)cam->width * cam->height;
+    const int64_t npx = (int64_t)cams[0].width * cams[0].height;
     phase(0, s);
-    HM_CUDA(hm::launch_clear(d_vis_center, d_vis_cons, npx, d_scene_d24, clear, d_stats, s), "clear");
+    for (int v = 0; v < n_views; ++v)
+        HM_CUDA(hm::launch_clear(d_vis_center[v], d_vis_cons[v], npx, d_scene_d24 ? d_scene_d24[v] : nullptr, clear,
+                                 v == 0 ? d_stats : nullptr, s),
+                "clear");
     phase(1, s);
-    HM_CUDA(hm::launch_lod(tab, cd, d_stats, s), "lod");
+    HM_CUDA(hm::launch_lod(tab, views.cam[0], d_stats, s), "lod");
     phase(2, s);
-    HM_CUDA(hm::launch_raster(tab, cd, d_vis_center, d_vis_cons, g_tuning.raster_precheck != 0,
-                              g_tuning.raster_min_blocks, g_tuning.raster_ctas_per_sm, d_stats, s),
+    HM_CUDA(hm::launch_raster(tab, views, g_tuning.raster_precheck != 0, g_tuning.raster_min_blocks,
+                              g_tuning.raster_ctas_per_sm, d_stats, s),
             "raster");
     phase(3, s);
     return HM_OK;
+}
+
+hm_status hm_render_visibility_multiview(const hm_groom *grooms, int32_t n, const hm_camera *cams, int32_t n_views,
+                                         uint64_t *const *d_vis_center, uint64_t *const *d_vis_cons,
+                                         const uint32_t *const *d_scene_d24, int32_t clear, hm_frame_stats *d_stats,
+                                         void *stream) {
+    return render_views(grooms, n, 0, n, cams, n_views, d_vis_center, d_vis_cons, d_scene_d24, clear, d_stats, stream);
+}
+
+hm_status hm_render_visibility_range(const hm_groom *grooms, int32_t n, int32_t first, int32_t count,
+                                     const hm_camera *cam, uint64_t *d_vis_center, uint64_t *d_vis_cons,
+                                     const uint32_t *d_scene_d24, int32_t clear, hm_frame_stats *d_stats,
+                                     void *stream) {
+    return render_views(grooms, n, first, count, cam, 1, &d_vis_center, &d_vis_cons,
+                        d_scene_d24 ? &d_scene_d24 : nullptr, clear, d_stats, stream);
 }
 
 static hm_status filter_dev(const hm_filter_params *f, const hm_camera *cam, hm::FilterDev &fd) {

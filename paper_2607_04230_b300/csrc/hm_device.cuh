@@ -61,6 +61,16 @@ struct CamDev {
     int32_t W, H;
 };
 
+// The views of one rasterizer launch: the strands are assembled once and
+// projected into each view's pair of key layers (all views share W, H).
+struct ViewSet {
+    int32_t n;
+    int32_t pad_[3];
+    CamDev cam[HM_MAX_VIEWS];
+    uint64_t *vis_c[HM_MAX_VIEWS];
+    uint64_t *vis_a[HM_MAX_VIEWS];
+};
+
 // ---------------------------------------------------------------------------
 // binary32 helpers with a fixed evaluation order
 // ---------------------------------------------------------------------------

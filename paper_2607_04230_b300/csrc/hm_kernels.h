@@ -29,8 +29,8 @@ int num_sms();
 cudaError_t launch_clear(uint64_t *vis_c, uint64_t *vis_a, int64_t npx, const uint32_t *scene_d24, int do_clear,
                          hm_frame_stats *stats, cudaStream_t st);
 cudaError_t launch_lod(const CallTable &tab, const CamDev &cam, hm_frame_stats *stats, cudaStream_t st);
-cudaError_t launch_raster(const CallTable &tab, const CamDev &cam, uint64_t *vis_c, uint64_t *vis_a, bool precheck,
-                          int min_blocks, int ctas_per_sm, hm_frame_stats *stats, cudaStream_t st);
+cudaError_t launch_raster(const CallTable &tab, const ViewSet &views, bool precheck, int min_blocks, int ctas_per_sm,
+                          hm_frame_stats *stats, cudaStream_t st);
 cudaError_t launch_probe_atomic_min(uint64_t *buf, int64_t n, int rounds, int pattern, cudaStream_t st);
 cudaError_t launch_resolve(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                            const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status, int tile_h,

@@ -277,9 +277,9 @@ __device__ __forceinline__ void raster_item(const SegRec &q, int i, int W, int H
     }
 }
 
-template <bool kPrecheck, int kMinBlocks>
-__global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(CallTable tab, CamDev cam, uint64_t *__restrict__ vis_c,
-                                                                uint64_t *__restrict__ vis_a, hm_frame_stats *stats) {
+template <bool kPrecheck, int kMinBlocks, bool kMulti>
+__global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(CallTable tab, ViewSet views,
+                                                                            hm_frame_stats *stats) {
     __shared__ uint32_t s_goff[HM_MAX_GROOMS_PER_CALL + 1];
     __shared__ SegRec s_rec[kRasterWarps][32];
     if (threadIdx.x == 0) {
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
     const int lane = threadIdx.x & 31;
     SegRec *rec = s_rec[threadIdx.x >> 5];
     uint32_t *ticket = tab.g[0].counters + kCtrTicket;
-    const int W = cam.W, H = cam.H;
+    const int W = views.cam[0].W, H = views.cam[0].H;
     uint32_t n_cons = 0, n_cen = 0;
 
     for (;;) {
@@ -312,14 +312,24 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
         const int C = (int)lo.y;
         const uint32_t sl = (lb - lo.z) * kSegBatch + lane;
 
+        const bool active = sl < lo.w;
+        int64_t s = 0;
+        int j = 0;
+        float3 cp[2];
+        if (active) {
+            s = (int64_t)__ldg(&g.faces[f]).w + sl / (uint32_t)(C - 1);
+            j = (int)(sl % (uint32_t)(C - 1));
+            const Root rt = make_root(g, s, f);
+            control_pts<2>(g, rt, C, j, cp);
+        }
+        const int n_views = kMulti ? views.n : 1;
+        for (int view = 0; view < n_views; ++view) {
+        const CamDev &cam = views.cam[view];
+        uint64_t *__restrict__ vis_c = views.vis_c[view];
+        uint64_t *__restrict__ vis_a = views.vis_a[view];
         SegRec r;
         int nmaj = 0;
-        if (sl < lo.w) {
-            const int64_t s = (int64_t)__ldg(&g.faces[f]).w + sl / (uint32_t)(C - 1);
-            const int j = (int)(sl % (uint32_t)(C - 1));
-            const Root rt = make_root(g, s, f);
-            float3 cp[2];
-            control_pts<2>(g, rt, C, j, cp);
+        if (active) {
             const Proj A = project(cam, cp[0]);
             const Proj B = project(cam, cp[1]);
             if (A.valid && B.valid) {
@@ -382,6 +392,7 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
                 raster_item<int64_t, kPrecheck>(q, i, W, H, vis_c, vis_a, n_cons, n_cen);
         }
         __syncwarp();
+        }   // views
     }
     if (stats) {
         unsigned long long a = n_cons, c = n_cen;
@@ -440,34 +451,41 @@ cudaError_t launch_lod(const CallTable &tab, const CamDev &cam, hm_frame_stats *
 // (min resident CTAs per SM of 256 threads: 3 -> up to 80 registers,
 // 4 -> 64).  The persistent grid is ctas_per_sm CTAs per SM, capped at what
 // fits (0 = as many as fit).
-template <bool P, int M>
+template <bool P, int M, bool V>
 static int raster_fit_per_sm() {
     static int cached = 0;
     if (cached == 0) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<P, M>, kRasterThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<P, M, V>, kRasterThreads, 0);
         cached = per_sm < 1 ? 1 : per_sm;
     }
     return cached;
 }
 
-template <bool P, int M>
-static cudaError_t launch_raster_v(const CallTable &tab, const CamDev &cam, uint64_t *vis_c, uint64_t *vis_a,
-                                   int ctas_per_sm, hm_frame_stats *stats, cudaStream_t st) {
-    const int fit = raster_fit_per_sm<P, M>();
+template <bool P, int M, bool V>
+static cudaError_t launch_raster_v(const CallTable &tab, const ViewSet &views, int ctas_per_sm, hm_frame_stats *stats,
+                                   cudaStream_t st) {
+    const int fit = raster_fit_per_sm<P, M, V>();
     const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < fit) ? ctas_per_sm : fit;
-    raster_kernel<P, M><<<per_sm * num_sms(), kRasterThreads, 0, st>>>(tab, cam, vis_c, vis_a, stats);
+    raster_kernel<P, M, V><<<per_sm * num_sms(), kRasterThreads, 0, st>>>(tab, views, stats);
     return cudaGetLastError();
 }
 
-cudaError_t launch_raster(const CallTable &tab, const CamDev &cam, uint64_t *vis_c, uint64_t *vis_a, bool precheck,
-                          int min_blocks, int ctas_per_sm, hm_frame_stats *stats, cudaStream_t st) {
+template <bool V>
+static cudaError_t launch_raster_views(const CallTable &tab, const ViewSet &views, bool precheck, int min_blocks,
+                                       int ctas_per_sm, hm_frame_stats *stats, cudaStream_t st) {
     const bool m3 = min_blocks == 3;
     if (precheck)
-        return m3 ? launch_raster_v<true, 3>(tab, cam, vis_c, vis_a, ctas_per_sm, stats, st)
-                  : launch_raster_v<true, 4>(tab, cam, vis_c, vis_a, ctas_per_sm, stats, st);
-    return m3 ? launch_raster_v<false, 3>(tab, cam, vis_c, vis_a, ctas_per_sm, stats, st)
-              : launch_raster_v<false, 4>(tab, cam, vis_c, vis_a, ctas_per_sm, stats, st);
+        return m3 ? launch_raster_v<true, 3, V>(tab, views, ctas_per_sm, stats, st)
+                  : launch_raster_v<true, 4, V>(tab, views, ctas_per_sm, stats, st);
+    return m3 ? launch_raster_v<false, 3, V>(tab, views, ctas_per_sm, stats, st)
+              : launch_raster_v<false, 4, V>(tab, views, ctas_per_sm, stats, st);
+}
+
+cudaError_t launch_raster(const CallTable &tab, const ViewSet &views, bool precheck, int min_blocks, int ctas_per_sm,
+                          hm_frame_stats *stats, cudaStream_t st) {
+    if (views.n > 1) return launch_raster_views<true>(tab, views, precheck, min_blocks, ctas_per_sm, stats, st);
+    return launch_raster_views<false>(tab, views, precheck, min_blocks, ctas_per_sm, stats, st);
 }
 
 }  // namespace hm

@@ -99,6 +99,7 @@ def lib():
         "hm_update_albedo": [P, P, P],
         "hm_render_visibility": [P, i32, P, P, P, P, i32, P, P],
         "hm_render_visibility_range": [P, i32, i32, i32, P, P, P, P, i32, P, P],
+        "hm_render_visibility_multiview": [P, i32, P, i32, P, P, P, i32, P, P],
         "hm_resolve_shade": [P, i32, P, P, P, P, P, P, P, P],
         "hm_shade_backward": [P, i32, P, P, P, P, P, P, P, P, P, P],
         "hm_shade_backward_noalloc": [P, i32, P, P, P, P, P, P, P, P, P],
@@ -265,6 +266,20 @@ def render_visibility_range(grooms, first, count, cam, vis_center, vis_cons, sce
     check(lib().hm_render_visibility_range(arr, n, int(first), int(count), ctypes.byref(c), _dptr(vis_center),
                                            _dptr(vis_cons), _dptr(scene_d24), int(bool(clear)), _dptr(stats),
                                            _stream_ptr(stream)))
+
+
+def render_visibility_multiview(grooms, cams, vis_centers, vis_conses, clear=True, stats=None, stream=None):
+    """Assemble the strands once and rasterize them into every view's layers
+    (LOD from cams[0])."""
+    arr, n = _handles(grooms)
+    nv = len(cams)
+    cs = (Camera * nv)(*[camera_struct(c) for c in cams])
+    vc = (ctypes.c_void_p * nv)(*[t.data_ptr() for t in vis_centers])
+    va = (ctypes.c_void_p * nv)(*[t.data_ptr() for t in vis_conses])
+    for t in list(vis_centers) + list(vis_conses):
+        _dptr(t)
+    check(lib().hm_render_visibility_multiview(arr, n, cs, nv, vc, va, None, int(bool(clear)), _dptr(stats),
+                                               _stream_ptr(stream)))
 
 
 def resolve_shade(grooms, cam, lights, filt, vis_center, vis_cons, rgba, stream=None):

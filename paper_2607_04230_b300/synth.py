@@ -378,3 +378,16 @@ def scene_crowd_4k(grooms: list | None = None, width: int = 3840, height: int = 
     cam = make_camera((0.0, 6.0, 14.0), (0.0, 0.0, 0.0), 40.0, width, height)
     lights = make_lights([[1.0, 1.0, 1.0], [-1.0, 0.5, 0.5]], [0.8, 0.4])
     return Scene(gs, cam, lights, lod=LodParams(1, 3.0), name="crowd_4k")
+
+
+def view_offsets(cam: Camera, offsets_m, target=None) -> list:
+    """Cameras translated sideways (along the image's right axis) by each
+    offset, looking at the same target (stereo / multiview rigs)."""
+    vp = cam.view_proj.astype(np.float64)
+    right = vp[0, :3] / np.linalg.norm(vp[0, :3])
+    eye = np.asarray(cam.cam_pos, np.float64)
+    fwd_row = vp[3, :3] / np.linalg.norm(vp[3, :3])
+    tgt = eye + fwd_row * 0.5 if target is None else np.asarray(target, np.float64)
+    fovy = math.degrees(2 * math.atan(cam.tan_half_fovy))
+    return [make_camera(eye + right * o, tgt + right * o, fovy, cam.width, cam.height, cam.near, cam.far)
+            for o in offsets_m]
