@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", choices=["single_1080p", "crowd_4k", "tiny_256", "lod_sweep", "grad_512",
-                                           "stereo_1080p"],
+                                           "stereo_1080p", "single_1080p_ao"],
                     default="single_1080p")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -57,11 +57,14 @@ def parse():
 
 def make_scene(name):
     from paper_2607_04230_b300 import synth
-    if name == "single_1080p":
+    if name in ("single_1080p", "single_1080p_ao"):
         sc = synth.scene_single_1080p()
         cfg = {"workload": "single groom, 1920x1080, 1 spp", "strands": 100_000, "segments_per_strand": 16,
                "scalp_triangles": 2048, "layers": 8, "lod": "off (full detail)", "lights": 2,
                "filter": "on, r=5"}
+        if name == "single_1080p_ao":
+            sc.grooms[0].vert_ao = synth.baked_ao(sc.grooms[0], seed=1)
+            cfg["workload"] += ", baked ambient occlusion per hair-mesh vertex"
     elif name == "crowd_4k":
         sc = synth.scene_crowd_4k()
         cfg = {"workload": "crowd of 64 grooms, 3840x2160, 1 spp, one render call", "grooms": 64,

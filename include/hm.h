@@ -88,6 +88,8 @@ typedef struct {
     float strand_width_m;          /* sets the centre-sample box (Sec. 3.1.2) */
     float roughness;               /* longitudinal lobe width beta (Sec. 3.4) */
     float tilt;                    /* cuticle tilt alpha, radians (Sec. 3.4) */
+    const float *vert_ao;          /* [L][V] baked ambient occlusion in [0, 1] per hair-mesh
+                                      vertex (Sec. 3.4), or NULL for none (1) */
 } hm_groom_desc;
 
 /* Pinhole camera: clip = view_proj * (x, y, z, 1), row-major; clip.w is the

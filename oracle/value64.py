@@ -65,6 +65,9 @@ class GroomT:
         self.lod_c = torch.from_numpy(np.asarray(lod_c).astype(np.int64))
         self.roughness = float(np.float32(g.roughness))
         self.tilt = float(np.float32(g.tilt))
+        ao = getattr(g, "vert_ao", None)
+        self.ao = (torch.ones((self.L, g.num_verts), dtype=torch.float64) if ao is None
+                   else torch.from_numpy(np.asarray(ao, np.float64)))
 
 
 def _normalize(v):
@@ -111,6 +114,49 @@ def control_points(P, mh, C, j):
     return h00 * Pk + h10 * m0 + h01 * Pk1 + h11 * m1
 
 
+def layer_ao(gt: GroomT, strands):
+    """Baked ambient occlusion at every layer point of the strands [N][L]
+    (Sec. 3.4: interpolated like the position), barycentric on each layer."""
+    tri = gt.faces[gt.sface[strands]]
+    b1 = gt.bary[strands, 0][:, None]
+    b2 = gt.bary[strands, 1][:, None]
+    b0 = 1.0 - b1 - b2
+    return b0 * gt.ao[:, tri[:, 0]].T + b1 * gt.ao[:, tri[:, 1]].T + b2 * gt.ao[:, tri[:, 2]].T
+
+
+def control_ao(A, C, j):
+    """Scalar cubic Hermite of layer AO values at control point j of C, on
+    the position's interval and parameter, with finite-difference slopes
+    (central inside, one-sided at root and tip)."""
+    L = A.shape[1]
+    x = j * (L - 1)
+    k = torch.clamp(torch.div(x, C - 1, rounding_mode="floor"), max=L - 2)
+    s = (x - k * (C - 1)).double() / (C - 1).double()
+    rows = torch.arange(A.shape[0])
+    a0, a1 = A[rows, k], A[rows, k + 1]
+    am = A[rows, torch.clamp(k - 1, min=0)]
+    a2 = A[rows, torch.clamp(k + 2, max=L - 1)]
+    m0 = torch.where(k == 0, a1 - a0, 0.5 * (a1 - am))
+    m1 = torch.where(k + 1 == L - 1, a1 - a0, 0.5 * (a2 - a0))
+    s2, s3 = s * s, s * s * s
+    return (2 * s3 - 3 * s2 + 1) * a0 + (s3 - 2 * s2 + s) * m0 + (3 * s2 - 2 * s3) * a1 + (s3 - s2) * m1
+
+
+def pixel_ao(gt: GroomT, sg, seg, num, den):
+    """Ambient occlusion at the pixel centre: the segment's end values at t."""
+    s = torch.as_tensor(sg - gt.base, dtype=torch.long)
+    j = torch.as_tensor(seg, dtype=torch.long)
+    C = gt.lod_c[gt.sface[s]]
+    A = layer_ao(gt, s)
+    num_t = torch.as_tensor(num, dtype=torch.float64)
+    den_t = torch.as_tensor(den, dtype=torch.float64)
+    t = torch.where(den_t > 0, num_t / torch.where(den_t > 0, den_t, torch.ones_like(den_t)),
+                    torch.zeros_like(den_t))
+    t = torch.clamp(t, 0.0, 1.0)
+    a, b = control_ao(A, C, j), control_ao(A, C, j + 1)
+    return (a + (b - a) * t)[:, None]
+
+
 def pixel_geometry(gt: GroomT, sg, seg, num, den):
     """Position X and unit tangent T of the keyed segment at the pixel centre
     (deferred decode; t held fixed from the exact integer projection)."""
@@ -137,10 +183,11 @@ def pixel_geometry(gt: GroomT, sg, seg, num, den):
     return X, T, s
 
 
-def shade(X, T, albedo, cam, lights, roughness, tilt):
+def shade(X, T, albedo, cam, lights, roughness, tilt, ao=None):
     """Sec. 3.4: per directional light, Kajiya-Kay diffuse
     albedo k_d sqrt(1 - (T.L)^2) plus an R lobe
-    k_s exp(-((T.L + T.V)/2 + sin(tilt))^2 / (2 beta^2)); plus ambient albedo."""
+    k_s exp(-((T.L + T.V)/2 + sin(tilt))^2 / (2 beta^2)); plus ambient albedo,
+    darkened by the baked ambient occlusion ao [N][1] when given."""
     cam_pos = torch.from_numpy(np.asarray(cam.cam_pos, np.float64))
     V = _normalize(cam_pos[None, :] - X)
     kd = float(np.float32(lights.k_d))
@@ -148,7 +195,7 @@ def shade(X, T, albedo, cam, lights, roughness, tilt):
     amb = float(np.float32(lights.ambient))
     sa = math.sin(tilt)
     b2 = 2.0 * roughness * roughness
-    out = amb * albedo
+    out = amb * albedo if ao is None else amb * ao * albedo
     for li in range(lights.dirs.shape[0]):
         Ld = torch.from_numpy(lights.dirs[li].astype(np.float64))
         E = torch.from_numpy(lights.radiance[li].astype(np.float64))
@@ -222,8 +269,10 @@ def resolve(gts, cam, lights, filt, vis_c, vis_a, dec, pixels=None):
     Ccen = torch.zeros((cen.size, 3), dtype=torch.float64)
     for (gi, s), idx in zip(albs, idxs):
         gt = gts[gi]
+        sel = cen[idx.numpy()]
+        ao = pixel_ao(gt, sgG[sel], segG[sel], dec_full(dec, "numG", sel), dec_full(dec, "denG", sel))
         Ccen = Ccen.index_put((idx,), shade(Xc[idx], Tc[idx], gt.albedo[s], cam, lights,
-                                            gt.roughness, gt.tilt))
+                                            gt.roughness, gt.tilt, ao))
     Cimg = torch.zeros((npx, 3), dtype=torch.float64).index_put((torch.from_numpy(cen),), Ccen)
 
     if pixels is None:

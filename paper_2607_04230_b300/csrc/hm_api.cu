@@ -246,6 +246,10 @@ hm_status hm_create_groom(const hm_groom_desc *d, void *stream, hm_groom *out) {
     if (S > 0 && (!d->strand_face || !d->strand_bary || !d->strand_albedo))
         return fail(HM_ERR_INVALID_ARG, "strand arrays are NULL");
     if (!finite_all(d->layer_verts, L * V * 3)) return fail(HM_ERR_INVALID_ARG, "non-finite layer vertex");
+    if (d->vert_ao)
+        for (int64_t i = 0; i < (int64_t)L * V; ++i)
+            if (!(d->vert_ao[i] >= 0.0f && d->vert_ao[i] <= 1.0f))
+                return fail(HM_ERR_INVALID_ARG, "vert_ao outside [0, 1]");
     if (!(d->strand_width_m > 0.0f) || !std::isfinite(d->strand_width_m) || !(d->roughness > 0.0f) ||
         !std::isfinite(d->tilt))
         return fail(HM_ERR_INVALID_ARG, "strand width / roughness must be positive, tilt finite");
@@ -275,7 +279,8 @@ hm_status hm_create_groom(const hm_groom_desc *d, void *stream, hm_groom *out) {
     // host-side repack to the device layout
     std::vector<float4> lv((size_t)L * V);
     for (size_t i = 0; i < lv.size(); ++i)
-        lv[i] = make_float4(d->layer_verts[3 * i], d->layer_verts[3 * i + 1], d->layer_verts[3 * i + 2], 0.0f);
+        lv[i] = make_float4(d->layer_verts[3 * i], d->layer_verts[3 * i + 1], d->layer_verts[3 * i + 2],
+                            d->vert_ao ? d->vert_ao[i] : 1.0f);
     std::vector<int4> faces((size_t)F + 1);
     for (int32_t f = 0; f < F; ++f)
         faces[f] = make_int4(d->faces[3 * f], d->faces[3 * f + 1], d->faces[3 * f + 2], first[f]);

@@ -177,13 +177,13 @@ __device__ void screen_tangent_adjoint(const CamDev &cam, float3 X, float3 T, fl
 
 // Adjoint of the shading model (Sec. 3.4) at one pixel.
 __device__ void shade_adjoint(float3 X, float3 T, float3 alb, const CamDev &cam, const LightsDev &Ls, float rough,
-                              float tilt, float3 dC, float3 &dX, float3 &dT, float3 &dalb) {
+                              float tilt, float ao, float3 dC, float3 &dX, float3 &dT, float3 &dalb) {
     const float3 Vr = f3(cam.cam_pos[0] - X.x, cam.cam_pos[1] - X.y, cam.cam_pos[2] - X.z);
     const float vl = len3(Vr);
     const float3 V = vl > 0.f ? mul3(Vr, 1.f / vl) : f3(0.f, 0.f, 0.f);
     const float sa = sinf(tilt);
     const float b2 = rough * rough;
-    dalb = mul3(dC, Ls.ambient);
+    dalb = mul3(dC, Ls.ambient * ao);
     dT = f3(0.f, 0.f, 0.f);
     float3 dV = f3(0.f, 0.f, 0.f);
     for (int l = 0; l < Ls.n; ++l) {
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_adjoint_kernel(
         if (d.ok) {
             const GroomDev &g = tab.g[d.gi];
             const float4 a = __ldg(&g.albedo[d.s]);
-            c = shade(d.X, d.T, f3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt);
+            c = shade(d.X, d.T, f3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt, decoded_ao(g, d));
         }
         s_col[i] = c;
         const int tx = lx - R, ty = ly - R;
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(kGeoThreads) geometry_adjoint_kernel(CallTable
                     if (hasC) {
                         const float4 a = __ldg(&g.albedo[d.s]);
                         float3 dalb;
-                        shade_adjoint(d.X, d.T, f3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt,
+                        shade_adjoint(d.X, d.T, f3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt, decoded_ao(g, d),
                                       f3(gc.x, gc.y, gc.z), dX, dT, dalb);
                         float *ga = sinks.galb[d.gi];
                         if (ga) {

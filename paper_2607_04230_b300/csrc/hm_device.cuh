@@ -356,6 +356,31 @@ __device__ __forceinline__ int find_groom(const uint64_t *bases, int n, uint64_t
     return lo;
 }
 
+// Baked ambient occlusion of layer point k (w of the layer vertices), with
+// the root's barycentric coordinates.
+__device__ __forceinline__ float layer_ao(const GroomDev &g, const Root &r, int k) {
+    const float4 *row = g.lv + (int64_t)k * g.V;
+    return r.b0 * __ldg(&row[r.i0]).w + r.b1 * __ldg(&row[r.i1]).w + r.b2 * __ldg(&row[r.i2]).w;
+}
+
+// Ambient occlusion at control point j, interpolated along the strand like
+// the position (same interval and local parameter, cubic Hermite) with
+// finite-difference slopes of the scalar (one-sided at root and tip).
+__device__ __forceinline__ float control_ao(const GroomDev &g, const Root &r, int C, int j) {
+    const int L = g.L;
+    const int x = j * (L - 1);
+    int k = x / (C - 1);
+    if (k > L - 2) k = L - 2;
+    const float s = (float)(x - k * (C - 1)) / (float)(C - 1);
+    const float a0 = layer_ao(g, r, k), a1 = layer_ao(g, r, k + 1);
+    const float am = k > 0 ? layer_ao(g, r, k - 1) : a0;
+    const float a2 = k + 2 <= L - 1 ? layer_ao(g, r, k + 2) : a1;
+    const float m0 = k == 0 ? a1 - a0 : 0.5f * (a1 - am);
+    const float m1 = k + 1 == L - 1 ? a1 - a0 : 0.5f * (a2 - a0);
+    const float s2 = s * s, s3 = s2 * s;
+    return (2.f * s3 - 3.f * s2 + 1.f) * a0 + (s3 - 2.f * s2 + s) * m0 + (3.f * s2 - 2.f * s3) * a1 + (s3 - s2) * m1;
+}
+
 // The geometry a key decodes to at pixel (px, py).
 struct Decoded {
     float3 X, T;        // FP32 position and unit tangent at the pixel centre

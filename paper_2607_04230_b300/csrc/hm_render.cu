@@ -492,9 +492,11 @@ cudaError_t launch_raster(const CallTable &tab, const ViewSet &views, bool prech
 
 namespace hm {
 
+// xyz from a packed [n][3] array; w (ambient occlusion of layer vertices)
+// is kept.
 __global__ void pack_float3_kernel(const float *__restrict__ src, float4 *__restrict__ dst, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = make_float4(src[3 * i], src[3 * i + 1], src[3 * i + 2], 0.0f);
+    if (i < n) dst[i] = make_float4(src[3 * i], src[3 * i + 1], src[3 * i + 2], dst[i].w);
 }
 
 cudaError_t launch_pack_float3(const float *src, float4 *dst, int64_t n, cudaStream_t st) {

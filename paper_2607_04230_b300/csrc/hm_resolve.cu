@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
         if (d.ok) {
             const GroomDev &g = tab.g[d.gi];
             const float4 a = __ldg(&g.albedo[d.s]);
-            c = shade(d.X, d.T, make_float3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt);
+            c = shade(d.X, d.T, make_float3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt, decoded_ao(g, d));
         }
         s_col[i] = c;
         const int tx = lx - R, ty = ly - R;

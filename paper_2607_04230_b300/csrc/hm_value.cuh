@@ -16,14 +16,25 @@ namespace hm {
 constexpr int kTileW = 32, kTileH = 16;
 constexpr int kResolveThreads = kTileW * kTileH;
 
+// Ambient occlusion at the decoded pixel: the segment's two control points
+// interpolated at t.
+__device__ __forceinline__ float decoded_ao(const GroomDev &g, const Decoded &d) {
+    const Root r = make_root(g, d.s, __ldg(&g.sface[d.s]));
+    const float a = control_ao(g, r, d.C, d.j), b = control_ao(g, r, d.C, d.j + 1);
+    return a + (b - a) * d.t;
+}
+
+// Shading (Sec. 3.4) with the ambient term darkened by the baked ambient
+// occlusion ao.
 __device__ __forceinline__ float3 shade(float3 X, float3 T, float3 alb, const CamDev &cam, const LightsDev &Ls,
-                                        float rough, float tilt) {
+                                        float rough, float tilt, float ao) {
     float3 V = make_float3(cam.cam_pos[0] - X.x, cam.cam_pos[1] - X.y, cam.cam_pos[2] - X.z);
     float vn = rsqrtf(fmaxf(V.x * V.x + V.y * V.y + V.z * V.z, 1e-30f));
     V = make_float3(V.x * vn, V.y * vn, V.z * vn);
     const float sa = sinf(tilt);
     const float inv2b2 = 1.0f / (2.0f * rough * rough);
-    float3 out = make_float3(Ls.ambient * alb.x, Ls.ambient * alb.y, Ls.ambient * alb.z);
+    const float amb = Ls.ambient * ao;
+    float3 out = make_float3(amb * alb.x, amb * alb.y, amb * alb.z);
     for (int l = 0; l < Ls.n; ++l) {
         const float tl = T.x * Ls.dir[l][0] + T.y * Ls.dir[l][1] + T.z * Ls.dir[l][2];
         const float tv = T.x * V.x + T.y * V.y + T.z * V.z;

@@ -36,7 +36,7 @@ class GroomDesc(ctypes.Structure):
                 ("layer_verts", ctypes.c_void_p), ("faces", ctypes.c_void_p), ("strand_face", ctypes.c_void_p),
                 ("strand_bary", ctypes.c_void_p), ("strand_albedo", ctypes.c_void_p),
                 ("bundle_delta", ctypes.c_void_p), ("strand_width_m", ctypes.c_float),
-                ("roughness", ctypes.c_float), ("tilt", ctypes.c_float)]
+                ("roughness", ctypes.c_float), ("tilt", ctypes.c_float), ("vert_ao", ctypes.c_void_p)]
 
 
 class Camera(ctypes.Structure):
@@ -201,7 +201,8 @@ class Groom:
             sf=np.ascontiguousarray(g.strand_face, np.uint32),
             bary=np.ascontiguousarray(g.strand_bary, np.float32),
             alb=np.ascontiguousarray(g.strand_albedo, np.float32),
-            delta=np.ascontiguousarray(g.bundle_delta, np.float32))
+            delta=np.ascontiguousarray(g.bundle_delta, np.float32),
+            ao=None if getattr(g, "vert_ao", None) is None else np.ascontiguousarray(g.vert_ao, np.float32))
         d = GroomDesc()
         d.num_layers, d.num_verts, d.num_faces = g.num_layers, g.num_verts, g.num_faces
         d.segments_per_strand, d.num_strands = g.segments_per_strand, g.num_strands
@@ -209,6 +210,7 @@ class Groom:
         d.layer_verts, d.faces, d.strand_face = k["lv"].ctypes.data, k["faces"].ctypes.data, k["sf"].ctypes.data
         d.strand_bary, d.strand_albedo, d.bundle_delta = k["bary"].ctypes.data, k["alb"].ctypes.data, k["delta"].ctypes.data
         d.strand_width_m, d.roughness, d.tilt = g.strand_width_m, g.roughness, g.tilt
+        d.vert_ao = None if k["ao"] is None else k["ao"].ctypes.data
         h = ctypes.c_void_p()
         check(lib().hm_create_groom(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)))
         self.handle = h

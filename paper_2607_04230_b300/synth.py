@@ -50,6 +50,7 @@ class Groom:
     strand_width_m: float = STRAND_WIDTH_M
     roughness: float = ROUGHNESS
     tilt: float = TILT
+    vert_ao: np.ndarray | None = None   # float32 [L][V] in [0, 1], baked ambient occlusion, or None
 
     @property
     def num_layers(self) -> int:
@@ -391,3 +392,14 @@ def view_offsets(cam: Camera, offsets_m, target=None) -> list:
     fovy = math.degrees(2 * math.atan(cam.tan_half_fovy))
     return [make_camera(eye + right * o, tgt + right * o, fovy, cam.width, cam.height, cam.near, cam.far)
             for o in offsets_m]
+
+
+def baked_ao(groom: Groom, seed: int = 0, strength: float = 0.6) -> np.ndarray:
+    """A seeded stand-in for baked ambient occlusion per hair-mesh vertex:
+    darkest at the roots (inside the hair volume), opening toward the tips,
+    with per-vertex variation; float32 [L][V] in [0, 1]."""
+    rng = np.random.default_rng(seed)
+    L, V = groom.num_layers, groom.num_verts
+    depth = 1.0 - np.arange(L)[:, None] / max(L - 1, 1)
+    ao = 1.0 - strength * depth * rng.uniform(0.6, 1.0, size=(L, V))
+    return np.ascontiguousarray(np.clip(ao, 0.0, 1.0).astype(np.float32))

@@ -23,7 +23,7 @@ def _oracle_image(scene, layer_verts):
     g = scene.grooms[0]
     gp = synth.Groom(layer_verts=layer_verts, faces=g.faces, strand_face=g.strand_face, strand_bary=g.strand_bary,
                      strand_albedo=g.strand_albedo, bundle_delta=g.bundle_delta,
-                     segments_per_strand=g.segments_per_strand)
+                     segments_per_strand=g.segments_per_strand, vert_ao=g.vert_ao)
     sp = synth.Scene([gp], scene.camera, scene.lights, scene.filt, scene.lod)
     lods, vc, va, _ = oracle_keys(sp)
     dec = oracle.resolve_decisions(sp.grooms, sp.camera, lods, sp.filt, vc, va)
@@ -94,3 +94,10 @@ def test_gradient_512_workload():
     """256 scalp triangles, 6 layers, 20k strands x 12 segments, 512x512."""
     out = _grad_case(synth.scene_grad_512())
     print(out)
+
+
+def test_gradient_with_baked_ao():
+    sc = synth.tiny_scene(23, width=96, height=80, num_strands=500, dist_m=0.3, num_layers=5)
+    sc.grooms[0].vert_ao = synth.baked_ao(sc.grooms[0], seed=4)
+    sc.lights.ambient = float(np.float32(0.4))
+    _grad_case(sc)

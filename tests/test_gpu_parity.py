@@ -114,3 +114,12 @@ def test_crowd_4k_full_size():
     """64 grooms, 3840x2160, LOD by distance, one render call."""
     sc = synth.scene_crowd_4k()
     check_full(sc, sample=6000)
+
+
+def test_baked_ao_frame():
+    """Per-vertex baked ambient occlusion (Sec. 3.4) interpolated along the
+    strand and applied to the ambient term."""
+    sc = synth.tiny_scene(14, width=200, height=160, num_strands=2500, num_layers=5, length_m=0.06)
+    sc.grooms[0].vert_ao = synth.baked_ao(sc.grooms[0], seed=2)
+    sc.lights.ambient = float(np.float32(0.4))
+    check_full(sc)

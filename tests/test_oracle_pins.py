@@ -714,3 +714,53 @@ def test_value_layer_gradient_matches_central_differences():
         with torch.no_grad():
             fd = (loss(lv, alb + e) - loss(lv, alb - e)).item() / (2 * h)
         assert abs(fd - galb.ravel()[idx]) <= 1e-7 + 1e-5 * abs(fd)
+
+
+# ---------------------------------------------------------------------------
+# baked ambient occlusion (Sec. 3.4)
+# ---------------------------------------------------------------------------
+
+def test_ao_interpolation_reproduces_linear_layers_and_layer_values():
+    """AO interpolated like the position: at control points that fall on
+    layers it equals the layer's barycentric AO, and AO linear in the layer
+    index is reproduced exactly (finite-difference slopes make the cubic
+    exact for linear data)."""
+    sc = synth.tiny_scene(7, num_strands=40, num_layers=5)
+    g = sc.grooms[0]
+    L, V = g.num_layers, g.num_verts
+    ao_lin = (0.2 + 0.15 * np.arange(L)[:, None] * np.ones((1, V))).astype(np.float32)
+    g.vert_ao = ao_lin
+    gt = v64.GroomT(g, np.full(g.num_faces, 9), 0)
+    s = torch.arange(40)
+    A = v64.layer_ao(gt, s)
+    np.testing.assert_allclose(A.numpy(), np.tile(0.2 + 0.15 * np.arange(L), (40, 1)), atol=1e-7)
+    for C in (5, 9, 17, 4):
+        for j in range(C):
+            a = v64.control_ao(A, torch.full((40,), C), torch.full((40,), j)).numpy()
+            np.testing.assert_allclose(a, 0.2 + 0.15 * j * (L - 1) / (C - 1), atol=1e-12)
+    rng = np.random.default_rng(3)
+    g.vert_ao = rng.uniform(0.3, 1.0, (L, V)).astype(np.float32)
+    gt = v64.GroomT(g, np.full(g.num_faces, 5), 0)
+    A = v64.layer_ao(gt, s)
+    for j in range(5):   # C == L: control points sit on the layers
+        np.testing.assert_allclose(v64.control_ao(A, torch.full((40,), 5), torch.full((40,), j)).numpy(),
+                                   A[:, j].numpy(), atol=1e-12)
+
+
+def test_ao_one_is_no_ao_and_scales_only_the_ambient_term():
+    sc = synth.tiny_scene(8, num_strands=300, width=96, height=80)
+    g = sc.grooms[0]
+    rgba0, pix0, vc, va, dec, lods = _resolve_scene(sc)
+    g.vert_ao = np.ones((g.num_layers, g.num_verts), np.float32)
+    rgba1, pix1, _, _, _, _ = _resolve_scene(sc)
+    np.testing.assert_array_equal(rgba0.numpy(), rgba1.numpy())
+    # ambient only, shading without the (colour-nonlinear) filter: a uniform
+    # AO of 0.25 quarters every shaded pixel
+    lights = synth.make_lights([[0.0, 1.0, 0.0]], [0.0], ambient=0.5)
+    off = synth.FilterParams(enabled=0)
+    g.vert_ao = None
+    ra, pa, _, _, _, _ = _resolve_scene(sc, filt=off, lights=lights)
+    g.vert_ao = np.full((g.num_layers, g.num_verts), 0.25, np.float32)
+    rb, pb, _, _, _, _ = _resolve_scene(sc, filt=off, lights=lights)
+    sel = ra[:, 3] > 0
+    np.testing.assert_allclose(rb[sel, :3].numpy(), 0.25 * ra[sel, :3].numpy(), rtol=1e-12)
