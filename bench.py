@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", choices=["single_1080p", "crowd_4k", "tiny_256", "lod_sweep", "grad_512",
-                                           "stereo_1080p", "single_1080p_ao"],
+                                           "stereo_1080p", "single_1080p_ao", "msaa_1080p"],
                     default="single_1080p")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -531,6 +531,57 @@ def run_stereo(args, rank, world, local_rank):
     return 0
 
 
+def run_msaa(args, rank, world, local_rank):
+    """The 1080p groom rendered with the multisample reference (N = 2, 4, 8
+    sample layers, every sample shaded) against the paper's 1-spp frame
+    (two layers + strand-connection filter)."""
+    import torch
+    from paper_2607_04230_b300 import build, hm
+    build.build()
+    torch.cuda.set_device(local_rank)
+    sc, cfg = make_scene("single_1080p")
+    grooms = hm.upload_scene(sc)
+    cam = sc.camera
+    npx = cam.width * cam.height
+    frame = hm.Frame(cam.width, cam.height)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    vis = torch.empty((8, npx), dtype=torch.int64, device="cuda")
+    rgba = torch.empty((npx, 4), dtype=torch.float32, device="cuda")
+    stats = torch.zeros(8, dtype=torch.int64, device="cuda")
+    out = {}
+
+    def one_spp():
+        hm.render(grooms, sc, frame)
+
+    for _ in range(args.warmup):
+        one_spp()
+    out["1spp_filtered"] = statistics.mean(_timed(torch, one_spp, args.steps, flush))
+    samples = {}
+    for N in (2, 4, 8):
+        v = vis[:N]
+
+        def step():
+            hm.render_visibility_msaa(grooms, cam, N, v, stats=stats)
+            hm.resolve_msaa(grooms, cam, sc.lights, N, v, rgba)
+
+        for _ in range(args.warmup):
+            step()
+        out[f"msaa{N}"] = statistics.mean(_timed(torch, step, args.steps, flush))
+        samples[f"msaa{N}"] = hm.stats_dict(stats)["covered_center"]
+    hm.get_device_status()
+    if rank != 0:
+        return 0
+    segs = hm.stats_dict(frame.stats)["segments"]
+    ms = out["msaa4"]
+    line = {"metric": METRIC.replace("1 spp", "4x multisample"), "value": segs / (ms * 1e-3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)",
+            "data": "synthetic", "config": dict(cfg, workload="single groom, 1920x1080, multisample reference"),
+            "ms_per_frame": out, "covered_samples": samples, "gpu_launches": 4 * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _gpu_uuid(torch, dev):
     u = str(torch.cuda.get_device_properties(dev).uuid)
     return u if u.startswith("GPU-") else "GPU-" + u
@@ -675,7 +726,7 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     runner = {"crowd_4k": run_crowd, "lod_sweep": run_lod_sweep, "grad_512": run_grad,
-              "stereo_1080p": run_stereo}.get(args.workload, run_native)
+              "stereo_1080p": run_stereo, "msaa_1080p": run_msaa}.get(args.workload, run_native)
     try:
         return runner(args, rank, world, local_rank)
     finally:

@@ -207,6 +207,25 @@ hm_status hm_render_visibility_multiview(const hm_groom *grooms, int32_t n, cons
                                          uint64_t *const *d_vis_cons, const uint32_t *const *d_scene_d24,
                                          int32_t clear, hm_frame_stats *d_stats, void *stream);
 
+/* Multisample software rasterization, the paper's MSAA reference (Sec. 3.3:
+ * samples recorded into multiple uint64 layers and resolved later).
+ * samples in {1, 2, 4, 8}; sample k of each pixel sits at the standard
+ * position for that count (1/16 px units from the centre, y down: 2x (4,4)
+ * (-4,-4); 4x (-2,-6) (6,-2) (-6,2) (2,6); 8x (1,-3) (-1,3) (5,1) (-3,-5)
+ * (-5,5) (-7,-1) (3,7) (7,-7)) and is covered iff the strand's centre-sample
+ * box (the projected half-width) around that point meets the segment; its
+ * key's depth is taken at the sample.  d_vis_samples: [samples][H][W]
+ * uint64, 16-byte aligned, cleared to EMPTY when clear != 0.  LOD as in
+ * hm_render_visibility.  d_stats->covered_center counts covered samples. */
+hm_status hm_render_visibility_msaa(const hm_groom *grooms, int32_t n, const hm_camera *cam, int32_t samples,
+                                    uint64_t *d_vis_samples, int32_t clear, hm_frame_stats *d_stats, void *stream);
+
+/* Resolve of hm_render_visibility_msaa: each covered sample is decoded at its
+ * own sample point and shaded (Sec. 3.4); d_rgba [H][W][4] straight alpha,
+ * rgb = mean over covered samples, alpha = covered / samples. */
+hm_status hm_resolve_msaa(const hm_groom *grooms, int32_t n, const hm_camera *cam, const hm_lights *lights,
+                          int32_t samples, const uint64_t *d_vis_samples, float *d_rgba, void *stream);
+
 /* hm_render_visibility for grooms[first .. first + count) only, with strand
  * ids numbered as in the whole n-groom array, so that per-groom calls into
  * the same buffers (clear only on the first) compose with one

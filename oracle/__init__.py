@@ -87,6 +87,8 @@ def lib():
         _lib.orc_screen_tangent.argtypes = [P, P, P, P]
         _lib.orc_in_strip.argtypes = [ctypes.c_int, f32, f32, ctypes.c_int, ctypes.c_int, f32]
         _lib.orc_lod_counts.argtypes = [f32, i32, f32, i32, i32, P, P]
+        _lib.orc_raster_msaa.argtypes = [P, i32, P, i32, P, P, P, P, i32]
+        _lib.orc_msaa_decisions.argtypes = [P, i32, P, i32, P, P, P, P, P, i32]
     return _lib
 
 
@@ -175,6 +177,46 @@ def raster(grooms, cam, lods, prefill_d24=None, nthreads: int = 0):
                           _ptr(counts), int(nthreads))
     assert rc == 0
     return vis_c, vis_a, counts
+
+
+# Standard sample positions (1/16 px from the pixel centre, y down) for 2, 4
+# and 8 samples per pixel, scaled here to 1/256 px.
+MSAA_PATTERNS = {
+    1: [(0, 0)],
+    2: [(4, 4), (-4, -4)],
+    4: [(-2, -6), (6, -2), (-6, 2), (2, 6)],
+    8: [(1, -3), (-1, 3), (5, 1), (-3, -5), (-5, 5), (-7, -1), (3, 7), (7, -7)],
+}
+
+
+def msaa_offsets(n: int):
+    pat = MSAA_PATTERNS[n]
+    return (np.array([16 * p[0] for p in pat], np.int32), np.array([16 * p[1] for p in pat], np.int32))
+
+
+def raster_msaa(grooms, cam, lods, n_samples: int, nthreads: int = 0):
+    """Multisample visibility: uint64 [n_samples][H*W] and the number of
+    covered (pixel, sample) pairs."""
+    arr, refs = _groom_array(grooms, lods)
+    ox, oy = msaa_offsets(n_samples)
+    vis = np.full((n_samples, cam.width * cam.height), EMPTY, np.uint64)
+    count = np.zeros(1, np.int64)
+    rc = lib().orc_raster_msaa(arr, len(refs), ctypes.byref(camera_struct(cam)), n_samples, _ptr(ox), _ptr(oy),
+                               _ptr(vis), _ptr(count), int(nthreads))
+    assert rc == 0
+    return vis, int(count[0])
+
+
+def msaa_decisions(grooms, cam, lods, n_samples: int, vis, nthreads: int = 0):
+    arr, refs = _groom_array(grooms, lods)
+    ox, oy = msaa_offsets(n_samples)
+    vis = np.ascontiguousarray(vis, np.uint64)
+    num = np.zeros(vis.shape, np.int64)
+    den = np.zeros(vis.shape, np.int64)
+    rc = lib().orc_msaa_decisions(arr, len(refs), ctypes.byref(camera_struct(cam)), n_samples, _ptr(ox), _ptr(oy),
+                                  _ptr(vis), _ptr(num), _ptr(den), int(nthreads))
+    assert rc == 0
+    return num, den
 
 
 def resolve_decisions(grooms, cam, lods, filt, vis_c, vis_a, pixels=None, nthreads: int = 0):

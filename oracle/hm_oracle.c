@@ -586,6 +586,126 @@ int orc_resolve_decisions(const orc_groom *grooms, int32_t n_grooms, const orc_c
 }
 
 /* ---------------------------------------------------------------------------
+ * multisample rasterization (Sec. 3.3: "multisampling for the software
+ * rasterizer, recording samples into multiple layers")
+ *
+ * Reading: N point samples per pixel at offsets (ox[k], oy[k]) (1/256 px
+ * from the pixel centre); sample k of a pixel is covered by a segment iff the
+ * closed box of the segment's centre half-width h_c around the sample point
+ * meets it (the centre-sample predicate, moved to the sample), and its key
+ * uses the depth at the sample's projection parameter.  Layer k holds the
+ * minimum key of sample k: vis_s[k][H*W].
+ * ------------------------------------------------------------------------- */
+int orc_raster_msaa(const orc_groom *grooms, int32_t n_grooms, const orc_camera *cam, int32_t n_samples,
+                    const int32_t *ox, const int32_t *oy, uint64_t *vis_s, int64_t *count, int32_t nthreads) {
+    int64_t total = 0;
+    int64_t *gseg = (int64_t *)malloc(sizeof(int64_t) * (n_grooms + 1));
+    if (!gseg) return 1;
+    gseg[0] = 0;
+    for (int32_t gi = 0; gi < n_grooms; ++gi) {
+        const orc_groom *g = &grooms[gi];
+        int64_t t = 0;
+        for (int32_t f = 0; f < g->F; ++f) if (g->lod_c[f] >= 2) t += (int64_t)g->lod_n[f] * (g->lod_c[f] - 1);
+        gseg[gi + 1] = gseg[gi] + t;
+    }
+    total = gseg[n_grooms];
+    seg_t *segs = (seg_t *)malloc(sizeof(seg_t) * (total > 0 ? total : 1));
+    if (!segs) { free(gseg); return 1; }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    for (int32_t gi = 0; gi < n_grooms; ++gi) {
+        const orc_groom *g = &grooms[gi];
+        int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (g->F + 1));
+        if (!off) { free(segs); free(gseg); return 1; }
+        bundle_offsets(g, off);
+        int64_t w = gseg[gi];
+        for (int32_t f = 0; f < g->F; ++f) {
+            int32_t c = g->lod_c[f];
+            if (c < 2) continue;
+            for (int32_t i = 0; i < g->lod_n[f]; ++i) {
+                strand_segments(g, cam, off[f] + i, c, &segs[w]);
+                w += c - 1;
+            }
+        }
+        free(off);
+    }
+    const int W = cam->width, H = cam->height;
+    const int64_t npx = (int64_t)W * H;
+    const int band = 16;
+    const int nb = (H + band - 1) / band;
+    int64_t cnt = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : cnt)
+    for (int b = 0; b < nb; ++b) {
+        int64_t r0 = (int64_t)b * band, r1 = r0 + band - 1;
+        if (r1 > H - 1) r1 = H - 1;
+        for (int64_t q = 0; q < total; ++q) {
+            const seg_t *sg = &segs[q];
+            if (!sg->valid) continue;
+            int64_t xmin = sg->XA < sg->XB ? sg->XA : sg->XB, xmax = sg->XA < sg->XB ? sg->XB : sg->XA;
+            int64_t ymin = sg->YA < sg->YB ? sg->YA : sg->YB, ymax = sg->YA < sg->YB ? sg->YB : sg->YA;
+            /* sample boxes reach at most 240/256 px from the pixel centre */
+            int64_t i0 = floor_div256(xmin) - 2, i1 = floor_div256(xmax) + 1;
+            int64_t m0 = floor_div256(ymin) - 2, m1 = floor_div256(ymax) + 1;
+            if (i0 < 0) i0 = 0;
+            if (i1 > W - 1) i1 = W - 1;
+            if (m0 < r0) m0 = r0;
+            if (m1 > r1) m1 = r1;
+            for (int64_t m = m0; m <= m1; ++m) {
+                for (int64_t i = i0; i <= i1; ++i) {
+                    for (int k = 0; k < n_samples; ++k) {
+                        int64_t sx = 256 * i + 128 + ox[k], sy = 256 * m + 128 + oy[k];
+                        if (!segment_covers(sg->XA, sg->YA, sg->XB, sg->YB, sx, sy, sg->hc)) continue;
+                        float t = segment_t(sg->XA, sg->YA, sg->XB, sg->YB, sx, sy, 0, 0);
+                        uint64_t key = ((uint64_t)depth24(sg->zA, sg->zB, t) << 40) | sg->id;
+                        uint64_t *dst = &vis_s[(int64_t)k * npx + m * W + i];
+                        ++cnt;
+                        if (key < *dst) *dst = key;
+                    }
+                }
+            }
+        }
+    }
+    if (count) *count += cnt;
+    free(segs);
+    free(gseg);
+    return 0;
+}
+
+/* Projection parameter of every covered sample's key, as num/den (the
+ * multisample resolve shades each sample at its own position). */
+int orc_msaa_decisions(const orc_groom *grooms, int32_t n_grooms, const orc_camera *cam, int32_t n_samples,
+                       const int32_t *ox, const int32_t *oy, const uint64_t *vis_s, int64_t *num, int64_t *den,
+                       int32_t nthreads) {
+    const int W = cam->width, H = cam->height;
+    const int64_t npx = (int64_t)W * H;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t q = 0; q < npx * n_samples; ++q) {
+        int k = (int)(q / npx);
+        int64_t p = q % npx;
+        num[q] = den[q] = 0;
+        uint64_t key = vis_s[q];
+        if ((key & ORC_PAYLOAD_MASK) == ORC_PAYLOAD_MASK) continue;
+        int64_t s;
+        const orc_groom *g = find_groom(grooms, n_grooms, (key >> 7) & ORC_STRAND_MASK, &s);
+        if (!g) continue;
+        int j = (int)(key & 127);
+        int C = g->lod_c[g->strand_face[s]];
+        if (j + 1 >= C) continue;
+        f3 P[64], mh[64];
+        strand_layer_points(g, s, P);
+        layer_tangents(P, g->L, mh);
+        proj_t a = project(cam, control_point(P, mh, g->L, C, j));
+        proj_t b = project(cam, control_point(P, mh, g->L, C, j + 1));
+        segment_t(a.X, a.Y, b.X, b.Y, 256 * (p % W) + 128 + ox[k], 256 * (p / W) + 128 + oy[k], &num[q], &den[q]);
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
  * single-step entry points used by the pin tests
  * ------------------------------------------------------------------------- */
 int orc_strand_control_points(const orc_groom *g, int64_t s, int32_t C, float *out) {

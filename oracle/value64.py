@@ -389,3 +389,31 @@ def full_image(rgba, pixels, width, height):
     img = torch.zeros((width * height, 4), dtype=torch.float64)
     img[torch.from_numpy(pixels)] = rgba.detach() if rgba.requires_grad else rgba
     return img.reshape(height, width, 4)
+
+
+def resolve_msaa(gts, cam, lights, vis, num, den):
+    """Multisample resolve (Sec. 3.3's MSAA reference): every covered sample
+    is shaded at its own position; the premultiplied colour is the mean over
+    all N samples and alpha the covered fraction.  Returns straight-alpha
+    RGBA float64 [H*W][4]."""
+    N, npx = vis.shape
+    acc = torch.zeros((npx, 3), dtype=torch.float64)
+    cov = torch.zeros((npx, 1), dtype=torch.float64)
+    for k in range(N):
+        e, _, sg, seg = key_fields(vis[k])
+        idx = np.nonzero(~e)[0]
+        if idx.size == 0:
+            continue
+        X, T, parts_idx, parts_alb = _geometry_all(gts, sg[idx], seg[idx], num[k][idx], den[k][idx])
+        C = torch.zeros((idx.size, 3), dtype=torch.float64)
+        for (gi, s), pidx in zip(parts_alb, parts_idx):
+            gt = gts[gi]
+            sel = idx[pidx.numpy()]
+            ao = pixel_ao(gt, sg[sel], seg[sel], num[k][sel], den[k][sel])
+            C = C.index_put((pidx,), shade(X[pidx], T[pidx], gt.albedo[s], cam, lights, gt.roughness, gt.tilt, ao))
+        t = torch.from_numpy(idx)
+        acc = acc.index_add(0, t, C)
+        cov = cov.index_add(0, t, torch.ones((idx.size, 1), dtype=torch.float64))
+    a = cov / N
+    rgb = torch.where(cov > 0, acc / torch.where(cov > 0, cov, torch.ones_like(cov)), torch.zeros_like(acc))
+    return torch.cat([rgb, a], 1)

@@ -20,6 +20,7 @@ struct hm_groom_s {
     float width_m, roughness, tilt;
     hm_lod_params lod;
     int device;
+    int has_ao;
     size_t max_batches;
     float4 *d_lv;
     int4 *d_faces;
@@ -133,6 +134,7 @@ hm_status build_table(const hm_groom *grooms, int32_t n, hm::CallTable &tab) {
         d.tilt = g->tilt;
         d.lod_lambda = g->lod.lambda;
         d.lod_enabled = g->lod.enabled;
+        d.has_ao = g->has_ao;
         base += (uint64_t)g->S;
     }
     if (base > (1ull << 33) - 2) return fail(HM_ERR_CAPACITY, "strand ids exceed 33 bits");
@@ -301,6 +303,7 @@ hm_status hm_create_groom(const hm_groom_desc *d, void *stream, hm_groom *out) {
     g->tilt = d->tilt;
     g->lod.enabled = 0;
     g->lod.lambda = 3.0f;
+    g->has_ao = d->vert_ao ? 1 : 0;
     g->max_batches = max_batches;
     cudaGetDevice(&g->device);
     hm_status st = HM_OK;
@@ -432,6 +435,50 @@ static hm_status render_views(const hm_groom *grooms, int32_t n, int32_t first, 
                               g_tuning.raster_ctas_per_sm, d_stats, s),
             "raster");
     phase(3, s);
+    return HM_OK;
+}
+
+static hm_status lights_dev(const hm_lights *l, hm::LightsDev &ld);
+
+hm_status hm_render_visibility_msaa(const hm_groom *grooms, int32_t n, const hm_camera *cam, int32_t samples,
+                                    uint64_t *d_vis_samples, int32_t clear, hm_frame_stats *d_stats, void *stream) {
+    hm_status st = check_camera(cam);
+    if (st != HM_OK) return st;
+    if (samples != 1 && samples != 2 && samples != 4 && samples != 8)
+        return fail(HM_ERR_INVALID_ARG, "samples must be 1, 2, 4 or 8");
+    if (!d_vis_samples || (reinterpret_cast<uintptr_t>(d_vis_samples) & 15))
+        return fail(HM_ERR_INVALID_ARG, "sample layers NULL or not 16-byte aligned");
+    hm::CallTable tab;
+    if ((st = build_table(grooms, n, tab)) != HM_OK) return st;
+    const hm::CamDev cd = cam_dev(cam);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t npx = (int64_t)cam->width * cam->height;
+    // the sample planes are contiguous: cleared as one flat array (one pointer
+    // given twice, written once)
+    HM_CUDA(hm::launch_clear(d_vis_samples, d_vis_samples, npx * samples, nullptr, clear, d_stats, s), "clear");
+    HM_CUDA(hm::launch_lod(tab, cd, d_stats, s), "lod");
+    HM_CUDA(hm::launch_raster_msaa(tab, cd, samples, d_vis_samples, d_stats, s), "raster msaa");
+    return HM_OK;
+}
+
+hm_status hm_resolve_msaa(const hm_groom *grooms, int32_t n, const hm_camera *cam, const hm_lights *lights,
+                          int32_t samples, const uint64_t *d_vis_samples, float *d_rgba, void *stream) {
+    hm_status st = check_camera(cam);
+    if (st != HM_OK) return st;
+    if (samples != 1 && samples != 2 && samples != 4 && samples != 8)
+        return fail(HM_ERR_INVALID_ARG, "samples must be 1, 2, 4 or 8");
+    if (!d_vis_samples || !d_rgba || (reinterpret_cast<uintptr_t>(d_rgba) & 15) ||
+        (reinterpret_cast<uintptr_t>(d_vis_samples) & 7))
+        return fail(HM_ERR_INVALID_ARG, "buffer NULL or misaligned");
+    hm::LightsDev ld;
+    if ((st = lights_dev(lights, ld)) != HM_OK) return st;
+    hm::CallTable tab;
+    if ((st = build_table(grooms, n, tab)) != HM_OK) return st;
+    uint32_t *sw = status_word();
+    if (!sw) return fail(HM_ERR_CUDA, "device status word unavailable");
+    HM_CUDA(hm::launch_resolve_msaa(tab, cam_dev(cam), ld, samples, d_vis_samples, d_rgba, sw,
+                                    static_cast<cudaStream_t>(stream)),
+            "resolve msaa");
     return HM_OK;
 }
 

@@ -45,7 +45,7 @@ struct GroomDev {
     uint64_t base;           // global id of strand 0 in this call
     float width_m, roughness, tilt, lod_lambda;
     int32_t lod_enabled;
-    int32_t pad_;
+    int32_t has_ao;          // layer vertices carry baked ambient occlusion in w
 };
 
 struct CallTable {
@@ -392,8 +392,36 @@ struct Decoded {
     bool iso, ok;
 };
 
+// Standard multisample positions (1/256 px from the pixel centre, y down)
+// for N = 1, 2, 4, 8 samples per pixel.
+template <int N>
+__device__ __forceinline__ void sample_offset(int k, int &ox, int &oy) {
+    if (N == 1) { ox = 0; oy = 0; return; }
+    if (N == 2) {
+        const int t[2][2] = {{4, 4}, {-4, -4}};
+        ox = 16 * t[k][0]; oy = 16 * t[k][1]; return;
+    }
+    if (N == 4) {
+        const int t[4][2] = {{-2, -6}, {6, -2}, {-6, 2}, {2, 6}};
+        ox = 16 * t[k][0]; oy = 16 * t[k][1]; return;
+    }
+    const int t[8][2] = {{1, -3}, {-1, 3}, {5, 1}, {-3, -5}, {-5, 5}, {-7, -1}, {3, 7}, {7, -7}};
+    ox = 16 * t[k][0];
+    oy = 16 * t[k][1];
+}
+
+struct Decoded;
+__device__ __forceinline__ Decoded decode_key_at(const CallTable &tab, const uint64_t *bases, const CamDev &cam,
+                                                 uint64_t key, int64_t sx, int64_t sy, uint32_t *status);
+
 __device__ __forceinline__ Decoded decode_key(const CallTable &tab, const uint64_t *bases, const CamDev &cam,
                                               uint64_t key, int px, int py, uint32_t *status) {
+    return decode_key_at(tab, bases, cam, key, 256 * (int64_t)px + 128, 256 * (int64_t)py + 128, status);
+}
+
+// Decode at an arbitrary sample point (sx, sy) in 1/256 px.
+__device__ __forceinline__ Decoded decode_key_at(const CallTable &tab, const uint64_t *bases, const CamDev &cam,
+                                                 uint64_t key, int64_t sx, int64_t sy, uint32_t *status) {
     Decoded d;
     d.ok = false;
     d.iso = true;
@@ -419,7 +447,7 @@ __device__ __forceinline__ Decoded decode_key(const CallTable &tab, const uint64
     control_pts<4>(g, r, C, j - 1, cp);
     const float3 pm = cp[0], p0 = cp[1], p1 = cp[2], pp = cp[3];
     Proj a = project(cam, p0), b = project(cam, p1);
-    float t = seg_t(a.X, a.Y, b.X, b.Y, 256 * (int64_t)px + 128, 256 * (int64_t)py + 128);
+    float t = seg_t(a.X, a.Y, b.X, b.Y, sx, sy);
     d.X = make_float3(fadd(p0.x, fmul(fsub(p1.x, p0.x), t)), fadd(p0.y, fmul(fsub(p1.y, p0.y), t)),
                       fadd(p0.z, fmul(fsub(p1.z, p0.z), t)));
     float3 T0 = fd_tangent(j, C, pm, p0, p1);

@@ -39,6 +39,10 @@ cudaError_t launch_resolve_adjoint(const CallTable &tab, const CamDev &cam, cons
                                    const uint64_t *vis_c, const uint64_t *vis_a, const float *grad_rgba,
                                    float *const *glv, float *const *galb, void *scratch, uint32_t *status,
                                    cudaStream_t st);
+cudaError_t launch_raster_msaa(const CallTable &tab, const CamDev &cam, int samples, uint64_t *vis_s,
+                               hm_frame_stats *stats, cudaStream_t st);
+cudaError_t launch_resolve_msaa(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, int samples,
+                                const uint64_t *vis_s, float *rgba, uint32_t *status, cudaStream_t st);
 cudaError_t launch_pack_float3(const float *src, float4 *dst, int64_t n, cudaStream_t st);
 
 }  // namespace hm

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256) clear_kernel(ulonglong2 *vis_c, ulonglong
             v.y = kEmptyKey;
         }
         vis_c[i] = v;
-        vis_a[i] = v;
+        if (vis_a != vis_c) vis_a[i] = v;
     }
 }
 
@@ -406,6 +406,194 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
             atomicAdd((unsigned long long *)&stats->covered_center, c);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// multisample rasterizer (Sec. 3.3: samples recorded into multiple uint64
+// layers, the paper's MSAA reference)
+//
+// Sample k of pixel (i, m) sits at offset (ox_k, oy_k) from the pixel centre
+// and is covered iff the closed box of the segment's centre half-width h_c
+// around the sample point meets the segment (the centre-sample predicate at
+// the sample); its key's depth uses the sample's projection parameter.
+// Sample boxes reach at most 7/16 + 1/2 px from the pixel centre, so the
+// candidate pixels of a segment are taken one pixel wider on each side.
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void raster_item_msaa(const SegRec &q, int i, int W, int H, uint64_t *__restrict__ vis_s,
+                                                 int64_t npx, uint32_t &n_hits) {
+    const bool xm = q.flags & 1;
+    const int32_t cu = 256 * i + 128;
+    const int32_t ua = max(cu - 256, q.umin), ub = min(cu + 256, q.umax);
+    if (ua > ub) return;
+    const float va = (float)(ua - q.uA) * q.slope, vb = (float)(ub - q.uA) * q.slope;
+    const float flo = floorf(fminf(va, vb)), fhi = ceilf(fmaxf(va, vb));
+    const int32_t slack = 8 + (abs(q.dv) >> 20);
+    const int64_t vlo = (int64_t)q.vA + (int64_t)flo - slack;
+    const int64_t vhi = (int64_t)q.vA + (int64_t)fhi + slack;
+    const int dimv = xm ? H : W;
+    // rows m whose sample points (within 240/256 px of the centre) can reach [vlo, vhi]
+    const int mlo = (int)max(((vlo - 368 + 255) >> 8), (int64_t)0);
+    const int mhi = (int)min((vhi + 112) >> 8, (int64_t)(dimv - 1));
+    const int64_t du = q.du, dv = q.dv;
+    const int64_t k_cen = (int64_t)q.hc * ((int64_t)abs(q.du) + (int64_t)abs(q.dv));
+    const uint64_t id = ((uint64_t)q.id_hi << 32) | q.id_lo;
+    const bool degenerate = (q.du == 0 && q.dv == 0);
+    for (int m = mlo; m <= mhi; ++m) {
+        const int32_t cv = 256 * m + 128;
+        const int64_t e0 = du * (int64_t)(cv - q.vA) - dv * (int64_t)(cu - q.uA);
+        const int64_t num0 = (int64_t)(cu - q.uA) * du + (int64_t)(cv - q.vA) * dv;
+        const int px = xm ? i : m, py = xm ? m : i;
+        const int64_t p = (int64_t)py * W + px;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            int ox, oy;
+            sample_offset<N>(k, ox, oy);
+            const int32_t ou = xm ? ox : oy, ov = xm ? oy : ox;
+            const int32_t su = cu + ou, sv = cv + ov;
+            if (q.umin > su + q.hc || q.umax < su - q.hc || q.vmin > sv + q.hc || q.vmax < sv - q.hc) continue;
+            const int64_t ek = e0 + du * ov - dv * ou;
+            if (ek > k_cen || ek < -k_cen) continue;
+            float t = 0.0f;
+            if (!degenerate) t = fclamp(fdiv(__ll2float_rn(num0 + ou * du + ov * dv), q.fden), 0.0f, 1.0f);
+            const float z = fclamp(fadd(q.zA, fmul(q.dz, t)), 0.0f, 1.0f);
+            uint32_t d24 = (uint32_t)floorf(fmul(z, 16777216.0f));
+            d24 = d24 > 16777215u ? 16777215u : d24;
+            atomicMin(reinterpret_cast<unsigned long long *>(vis_s + (int64_t)k * npx + p),
+                      (unsigned long long)(((uint64_t)d24 << 40) | id));
+            n_hits += 1;
+        }
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kRasterThreads, 4) raster_msaa_kernel(CallTable tab, CamDev cam,
+                                                                        uint64_t *__restrict__ vis_s,
+                                                                        hm_frame_stats *stats) {
+    __shared__ uint32_t s_goff[HM_MAX_GROOMS_PER_CALL + 1];
+    __shared__ SegRec s_rec[kRasterWarps][32];
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int i = 0; i < tab.n; ++i) {
+            s_goff[i] = acc;
+            acc += tab.g[i].counters[kCtrBatches];
+        }
+        s_goff[tab.n] = acc;
+    }
+    __syncthreads();
+    const uint32_t total = s_goff[tab.n];
+    const int lane = threadIdx.x & 31;
+    SegRec *rec = s_rec[threadIdx.x >> 5];
+    uint32_t *ticket = tab.g[0].counters + kCtrTicket;
+    const int W = cam.W, H = cam.H;
+    const int64_t npx = (int64_t)W * H;
+    uint32_t n_hits = 0;
+    for (;;) {
+        uint32_t b = 0;
+        if (lane == 0) b = atomicAdd(ticket, 1u);
+        b = __shfl_sync(kFull, b, 0);
+        if (b >= total) break;
+        int gi = 0;
+        while (gi + 1 < tab.n && s_goff[gi + 1] <= b) ++gi;
+        const GroomDev &g = tab.g[gi];
+        const uint32_t lb = b - s_goff[gi];
+        const uint32_t f = __ldg(&g.batch_map[lb]);
+        const uint4 lo = g.lod[f];
+        const int C = (int)lo.y;
+        const uint32_t sl = (lb - lo.z) * kSegBatch + lane;
+        SegRec r;
+        int nmaj = 0;
+        if (sl < lo.w) {
+            const int64_t s = (int64_t)__ldg(&g.faces[f]).w + sl / (uint32_t)(C - 1);
+            const int j = (int)(sl % (uint32_t)(C - 1));
+            float3 cp[2];
+            control_pts<2>(g, make_root(g, s, f), C, j, cp);
+            const Proj A = project(cam, cp[0]);
+            const Proj B = project(cam, cp[1]);
+            if (A.valid && B.valid) {
+                const bool xm = abs(B.X - A.X) >= abs(B.Y - A.Y);
+                r.uA = xm ? A.X : A.Y;
+                r.vA = xm ? A.Y : A.X;
+                const int32_t uB = xm ? B.X : B.Y, vB = xm ? B.Y : B.X;
+                r.du = uB - r.uA;
+                r.dv = vB - r.vA;
+                r.umin = min(r.uA, uB);
+                r.umax = max(r.uA, uB);
+                r.vmin = min(r.vA, vB);
+                r.vmax = max(r.vA, vB);
+                r.zA = A.z;
+                r.dz = fsub(B.z, A.z);
+                r.hc = centre_halfwidth(cam, g.width_m, A.w, B.w);
+                const uint64_t id = ((g.base + (uint64_t)s) << 7) | (uint64_t)j;
+                r.id_lo = (uint32_t)id;
+                r.id_hi = (uint32_t)(id >> 32);
+                const int64_t dX = (int64_t)B.X - A.X, dY = (int64_t)B.Y - A.Y;
+                r.fden = __ll2float_rn(dX * dX + dY * dY);
+                r.slope = r.du == 0 ? 0.0f : (float)r.dv / (float)r.du;
+                r.flags = xm ? 1 : 0;
+                const int du = xm ? W : H, dv = xm ? H : W;
+                int ilo = ((r.umin + 255) >> 8) - 2, ihi = (r.umax >> 8) + 1;
+                ilo = max(ilo, 0);
+                ihi = min(ihi, du - 1);
+                const bool vin = r.vmax >= -256 && r.vmin <= 256 * dv + 256;
+                r.ilo = ilo;
+                nmaj = (vin && ihi >= ilo) ? ihi - ilo + 1 : 0;
+            }
+        }
+        int incl = nmaj;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        r.start = incl - nmaj;
+        rec[lane] = r;
+        __syncwarp();
+        const int items = __shfl_sync(kFull, incl, 31);
+        for (int base = 0; base < items; base += 32) {
+            const int item = base + lane;
+            int src = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                int v = __shfl_sync(kFull, incl, src + step - 1);
+                if (v <= item) src += step;
+            }
+            if (item >= items) continue;
+            const SegRec &q = rec[src];
+            raster_item_msaa<N>(q, q.ilo + (item - q.start), W, H, vis_s, npx, n_hits);
+        }
+        __syncwarp();
+    }
+    if (stats) {
+        unsigned long long a = n_hits;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(kFull, a, o);
+        if (lane == 0) atomicAdd((unsigned long long *)&stats->covered_center, a);
+    }
+}
+
+cudaError_t launch_raster_msaa(const CallTable &tab, const CamDev &cam, int samples, uint64_t *vis_s,
+                               hm_frame_stats *stats, cudaStream_t st) {
+    int per_sm = 0;
+    switch (samples) {
+        case 1:
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_msaa_kernel<1>, kRasterThreads, 0);
+            raster_msaa_kernel<1><<<(per_sm > 0 ? per_sm : 1) * num_sms(), kRasterThreads, 0, st>>>(tab, cam, vis_s, stats);
+            break;
+        case 2:
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_msaa_kernel<2>, kRasterThreads, 0);
+            raster_msaa_kernel<2><<<(per_sm > 0 ? per_sm : 1) * num_sms(), kRasterThreads, 0, st>>>(tab, cam, vis_s, stats);
+            break;
+        case 4:
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_msaa_kernel<4>, kRasterThreads, 0);
+            raster_msaa_kernel<4><<<(per_sm > 0 ? per_sm : 1) * num_sms(), kRasterThreads, 0, st>>>(tab, cam, vis_s, stats);
+            break;
+        default:
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_msaa_kernel<8>, kRasterThreads, 0);
+            raster_msaa_kernel<8><<<(per_sm > 0 ? per_sm : 1) * num_sms(), kRasterThreads, 0, st>>>(tab, cam, vis_s, stats);
+            break;
+    }
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

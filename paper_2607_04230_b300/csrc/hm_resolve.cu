@@ -203,6 +203,67 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
     }
 }
 
+// Multisample resolve: every covered sample is decoded at its own sample
+// point and shaded; straight-alpha output with rgb the mean over covered
+// samples and alpha the covered fraction (premultiplied: the mean over all).
+template <int N>
+__global__ void __launch_bounds__(256) resolve_msaa_kernel(CallTable tab, CamDev cam, LightsDev Ls,
+                                                           const uint64_t *__restrict__ vis_s,
+                                                           float4 *__restrict__ rgba, uint32_t *status) {
+    __shared__ uint64_t s_bases[HM_MAX_GROOMS_PER_CALL + 1];
+    if ((int)threadIdx.x <= tab.n) {
+        uint64_t b = 0;
+        for (int i = 0; i < (int)threadIdx.x; ++i) b += (uint64_t)tab.g[i].S;
+        s_bases[threadIdx.x] = b;
+    }
+    __syncthreads();
+    const int64_t npx = (int64_t)cam.W * cam.H;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npx; p += (int64_t)gridDim.x * blockDim.x) {
+        const int px = (int)(p % cam.W), py = (int)(p / cam.W);
+        float3 acc = make_float3(0.f, 0.f, 0.f);
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const uint64_t key = __ldg(reinterpret_cast<const unsigned long long *>(vis_s + (int64_t)k * npx + p));
+            if (key_empty(key)) continue;
+            int ox, oy;
+            sample_offset<N>(k, ox, oy);
+            const Decoded d = decode_key_at(tab, s_bases, cam, key, 256 * (int64_t)px + 128 + ox,
+                                            256 * (int64_t)py + 128 + oy, status);
+            if (!d.ok) continue;
+            const GroomDev &g = tab.g[d.gi];
+            const float4 a = __ldg(&g.albedo[d.s]);
+            const float3 c = shade(d.X, d.T, make_float3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt,
+                                   decoded_ao(g, d));
+            acc.x += c.x;
+            acc.y += c.y;
+            acc.z += c.z;
+            ++cnt;
+        }
+        float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (cnt > 0) {
+            const float ic = 1.0f / (float)cnt;
+            out = make_float4(acc.x * ic, acc.y * ic, acc.z * ic, __fdiv_rn((float)cnt, (float)N));
+        }
+        rgba[p] = out;
+    }
+}
+
+cudaError_t launch_resolve_msaa(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, int samples,
+                                const uint64_t *vis_s, float *rgba, uint32_t *status, cudaStream_t st) {
+    const int64_t npx = (int64_t)cam.W * cam.H;
+    const int64_t want = (npx + 255) / 256;
+    const int grid = (int)(want < (int64_t)num_sms() * 16 ? (want > 0 ? want : 1) : (int64_t)num_sms() * 16);
+    float4 *out = reinterpret_cast<float4 *>(rgba);
+    switch (samples) {
+        case 1: resolve_msaa_kernel<1><<<grid, 256, 0, st>>>(tab, cam, Ls, vis_s, out, status); break;
+        case 2: resolve_msaa_kernel<2><<<grid, 256, 0, st>>>(tab, cam, Ls, vis_s, out, status); break;
+        case 4: resolve_msaa_kernel<4><<<grid, 256, 0, st>>>(tab, cam, Ls, vis_s, out, status); break;
+        default: resolve_msaa_kernel<8><<<grid, 256, 0, st>>>(tab, cam, Ls, vis_s, out, status); break;
+    }
+    return cudaGetLastError();
+}
+
 size_t resolve_smem_bytes(int radius, int tile_h) {
     const int tile_px = kFwdTileW * tile_h;
     const int sw = kFwdTileW + 2 * radius, sh = tile_h + 2 * radius, ns = sw * sh;

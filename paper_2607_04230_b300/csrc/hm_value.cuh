@@ -19,6 +19,7 @@ constexpr int kResolveThreads = kTileW * kTileH;
 // Ambient occlusion at the decoded pixel: the segment's two control points
 // interpolated at t.
 __device__ __forceinline__ float decoded_ao(const GroomDev &g, const Decoded &d) {
+    if (!g.has_ao) return 1.0f;
     const Root r = make_root(g, d.s, __ldg(&g.sface[d.s]));
     const float a = control_ao(g, r, d.C, d.j), b = control_ao(g, r, d.C, d.j + 1);
     return a + (b - a) * d.t;
@@ -135,7 +136,8 @@ __device__ __forceinline__ Recon reconstruct(const int *s_dg, const uint8_t *s_f
 //    (zero offset, same depth, same colour) and every exponent is >= 0, so
 //    each weight is <= 1 and the sum is >= 1;
 //  - conservative reference: the sum is exact unless every weight is tiny;
-//    callers redo it with the online-rescaled reconstruct() when W < 1e-20.
+//    callers redo it with the online-rescaled reconstruct() when some
+//    neighbour contributes but W < 1e-20.
 // Staged pixels without a centre key must hold a finite colour (zero).
 template <int R, bool kColor>
 __device__ __forceinline__ Recon reconstruct_fast(const int *s_dg, const uint8_t *s_fa, const float3 *s_col, int sw,
@@ -153,9 +155,10 @@ __device__ __forceinline__ Recon reconstruct_fast(const int *s_dg, const uint8_t
             float dpar, perp2;
             const bool strip = in_strip(iso, tsx, tsy, dx, dy, fp.hw2, dpar, perp2);
             const bool gq = dq >= 0;
+            const bool ok = gq && abs(dq - ref) <= fp.drej;
+            cnt += ok ? 1 : 0;
             hc += (strip && gq) ? 1 : 0;
             ha += (strip && fa) ? 1 : 0;
-            const bool ok = gq && abs(dq - ref) <= fp.drej;
             const float3 cq = s_col[idx];
             float e = iso ? (float)(dx * dx + dy * dy) * fp.inv_siso2
                           : (dpar * dpar) * fp.inv_spar2 + perp2 * fp.inv_sperp2;
@@ -168,7 +171,6 @@ __device__ __forceinline__ Recon reconstruct_fast(const int *s_dg, const uint8_t
             Sy += w * cq.y;
             Sz += w * cq.z;
             Wt += w;
-            cnt += ok ? 1 : 0;
         }
     }
     Recon o;

@@ -101,6 +101,8 @@ def lib():
         "hm_render_visibility_range": [P, i32, i32, i32, P, P, P, P, i32, P, P],
         "hm_render_visibility_multiview": [P, i32, P, i32, P, P, P, i32, P, P],
         "hm_resolve_shade": [P, i32, P, P, P, P, P, P, P, P],
+        "hm_render_visibility_msaa": [P, i32, P, i32, P, i32, P, P],
+        "hm_resolve_msaa": [P, i32, P, P, i32, P, P, P],
         "hm_shade_backward": [P, i32, P, P, P, P, P, P, P, P, P, P],
         "hm_shade_backward_noalloc": [P, i32, P, P, P, P, P, P, P, P, P],
         "hm_get_lod": [P, P, P, P],
@@ -289,6 +291,24 @@ def resolve_shade(grooms, cam, lights, filt, vis_center, vis_cons, rgba, stream=
     c, L, f = camera_struct(cam), lights_struct(lights), filter_struct(filt)
     check(lib().hm_resolve_shade(arr, n, ctypes.byref(c), ctypes.byref(L), ctypes.byref(f), _dptr(vis_center),
                                  _dptr(vis_cons), _dptr(rgba), None, _stream_ptr(stream)))
+
+
+def render_visibility_msaa(grooms, cam, samples: int, vis_samples, clear=True, stats=None, stream=None):
+    """Multisample visibility into vis_samples, uint64 (int64 view)
+    [samples][H*W]; samples in 1, 2, 4, 8."""
+    arr, n = _handles(grooms)
+    c = camera_struct(cam)
+    check(lib().hm_render_visibility_msaa(arr, n, ctypes.byref(c), int(samples), _dptr(vis_samples),
+                                          int(bool(clear)), _dptr(stats), _stream_ptr(stream)))
+
+
+def resolve_msaa(grooms, cam, lights, samples: int, vis_samples, rgba, stream=None):
+    """Shade every covered sample at its own position; rgba float32 [H*W][4]
+    straight alpha (rgb mean over covered samples, alpha covered fraction)."""
+    arr, n = _handles(grooms)
+    c, L = camera_struct(cam), lights_struct(lights)
+    check(lib().hm_resolve_msaa(arr, n, ctypes.byref(c), ctypes.byref(L), int(samples), _dptr(vis_samples),
+                                _dptr(rgba), _stream_ptr(stream)))
 
 
 def backward_scratch_bytes(width: int, height: int) -> int:

@@ -109,6 +109,15 @@ def test_render_and_resolve_reject_bad_arguments(L):
     f = hm.filter_struct(synth.FilterParams())
     assert L.hm_resolve_shade(grooms, 1, ctypes.byref(cam), ctypes.byref(lights), ctypes.byref(f), fake, fake, fake,
                               None, None) == INVALID
+    for n_s in (0, 3, 16):
+        assert L.hm_render_visibility_msaa(grooms, 1, ctypes.byref(cam), n_s, fake, 1, None, None) == INVALID
+    assert L.hm_render_visibility_msaa(grooms, 1, ctypes.byref(cam), 4, None, 1, None, None) == INVALID
+    assert L.hm_render_visibility_msaa(grooms, 1, ctypes.byref(cam), 4, ctypes.c_void_p((1 << 20) + 8), 1, None,
+                                       None) == INVALID
+    assert L.hm_resolve_msaa(grooms, 1, ctypes.byref(cam), ctypes.byref(lights), 4, fake, fake, None) == INVALID
+    lights.count = 1
+    assert L.hm_resolve_msaa(grooms, 1, ctypes.byref(cam), ctypes.byref(lights), 5, fake, fake, None) == INVALID
+    assert L.hm_resolve_msaa(grooms, 1, ctypes.byref(cam), ctypes.byref(lights), 4, fake, None, None) == INVALID
     assert L.hm_set_phase_events(None, 7) == INVALID
     assert L.hm_set_phase_events(None, 0) == 0
     assert L.hm_probe_atomic_min(None, 10, 1, 0, None) == INVALID

@@ -259,13 +259,12 @@ def test_depth24_endpoints_and_quantization():
     assert oracle.depth24(0, 0, 512, 0, zA, zB, 256, 0) == int(0.5 * 2 ** 24)
 
 
-def _brute_force_keys(g, cam, C, base=0):
-    """Per-pixel nearest-segment search over every segment of every strand
-    (exact rational coverage), recomputing d24 in float32 numpy."""
-    W, H = cam.width, cam.height
+def _brute_segments(g, cam, C, base=0):
+    """Every projected segment (XA, YA, XB, YB, zA, zB, h_c, id) recomputed
+    from the oracle's control points and projection."""
     segs = []
     f32 = np.float32
-    focal = f32(f32(0.5) * f32(H)) / f32(cam.tan_half_fovy)
+    focal = f32(f32(0.5) * f32(cam.height)) / f32(cam.tan_half_fovy)
     for s in range(g.num_strands):
         cp = oracle.strand_control_points(g, s, C)
         pr = [oracle.project_point(cam, p) for p in cp]
@@ -277,6 +276,24 @@ def _brute_force_keys(g, cam, C, base=0):
             r = f32(f32(f32(128.0) * f32(g.strand_width_m)) * focal) / wm
             hc = int(min(max(np.rint(r), 1), 128))
             segs.append((XA, YA, XB, YB, f32(wa[1]), f32(wb[1]), hc, ((base + s) << 7) | j))
+    return segs
+
+
+def _brute_key(XA, YA, XB, YB, zA, zB, sid, cx, cy):
+    f32 = np.float32
+    dX, dY = XB - XA, YB - YA
+    num, den = (cx - XA) * dX + (cy - YA) * dY, dX * dX + dY * dY
+    t = f32(0) if den == 0 else min(max(f32(num) / f32(den), f32(0)), f32(1))
+    z = min(max(f32(zA + f32(f32(zB - zA) * t)), f32(0)), f32(1))
+    d = min(int(np.floor(f32(z * f32(16777216.0)))), 2 ** 24 - 1)
+    return np.uint64((d << 40) | sid)
+
+
+def _brute_force_keys(g, cam, C, base=0):
+    """Per-pixel nearest-segment search over every segment of every strand
+    (exact rational coverage), recomputing d24 in float32 numpy."""
+    W, H = cam.width, cam.height
+    segs = _brute_segments(g, cam, C, base)
     vc = np.full(W * H, oracle.EMPTY, np.uint64)
     va = vc.copy()
     for (XA, YA, XB, YB, zA, zB, hc, sid) in segs:
@@ -292,12 +309,7 @@ def _brute_force_keys(g, cam, C, base=0):
                 cc = _lb_intersects((XA, YA), (XB, YB), cx, cy, hc)
                 if not (ca or cc):
                     continue
-                dX, dY = XB - XA, YB - YA
-                num, den = (cx - XA) * dX + (cy - YA) * dY, dX * dX + dY * dY
-                t = f32(0) if den == 0 else min(max(f32(num) / f32(den), f32(0)), f32(1))
-                z = min(max(f32(zA + f32(f32(zB - zA) * t)), f32(0)), f32(1))
-                d = min(int(np.floor(f32(z * f32(16777216.0)))), 2 ** 24 - 1)
-                key = np.uint64((d << 40) | sid)
+                key = _brute_key(XA, YA, XB, YB, zA, zB, sid, cx, cy)
                 px = m * W + i
                 if ca:
                     va[px] = min(va[px], key)
@@ -317,6 +329,86 @@ def test_raster_equals_bruteforce_nearest_segment(seed, W, H, C):
     assert (va != oracle.EMPTY).sum() > 50
     np.testing.assert_array_equal(va, ba)
     np.testing.assert_array_equal(vc, bc)
+
+
+# Standard multisample positions (1/16 px, y down), written out independently
+# of the oracle's table.
+_MSAA_POS = {2: [(4, 4), (-4, -4)],
+             4: [(-2, -6), (6, -2), (-6, 2), (2, 6)],
+             8: [(1, -3), (-1, 3), (5, 1), (-3, -5), (-5, 5), (-7, -1), (3, 7), (7, -7)]}
+
+
+def _brute_force_msaa(g, cam, C, N):
+    """Per-sample nearest-segment search: sample k of pixel (i, m) at
+    (256 i + 128 + 16 ox_k, 256 m + 128 + 16 oy_k), covered when the closed
+    box of half-width h_c around it meets the segment (exact rational clip)."""
+    W, H = cam.width, cam.height
+    pos = [(0, 0)] if N == 1 else _MSAA_POS[N]
+    vis = np.full((N, W * H), oracle.EMPTY, np.uint64)
+    for (XA, YA, XB, YB, zA, zB, hc, sid) in _brute_segments(g, cam, C):
+        for m in range(H):
+            if min(YA, YB) > 256 * m + 512 or max(YA, YB) < 256 * m - 256:
+                continue
+            for i in range(W):
+                if min(XA, XB) > 256 * i + 512 or max(XA, XB) < 256 * i - 256:
+                    continue
+                for k, (ox, oy) in enumerate(pos):
+                    sx, sy = 256 * i + 128 + 16 * ox, 256 * m + 128 + 16 * oy
+                    if _lb_intersects((XA, YA), (XB, YB), sx, sy, hc):
+                        key = _brute_key(XA, YA, XB, YB, zA, zB, sid, sx, sy)
+                        vis[k, m * W + i] = min(vis[k, m * W + i], key)
+    return vis
+
+
+@pytest.mark.parametrize("seed,W,H,C,N", [(21, 23, 19, 4, 2), (22, 30, 17, 5, 4), (23, 19, 21, 4, 8)])
+def test_msaa_raster_equals_bruteforce(seed, W, H, C, N):
+    """Sec. 3.3's multisample reference: every sample layer against an
+    independent per-sample search."""
+    sc = synth.tiny_scene(seed, width=W, height=H, num_strands=30, segments=C - 1,
+                          dist_m=0.35, jitter_m=0.004)
+    g = sc.grooms[0]
+    g.strand_width_m = 0.005           # h_c of a few tenths of a pixel: samples both hit and missed
+    lods = [oracle.lod(g, sc.camera, synth.LodParams(0))]
+    vis, cnt = oracle.raster_msaa([g], sc.camera, lods, N)
+    ref = _brute_force_msaa(g, sc.camera, C, N)
+    assert (vis != oracle.EMPTY).sum() > 40
+    for k in range(N):
+        np.testing.assert_array_equal(vis[k], ref[k], err_msg=f"sample {k}")
+    assert cnt >= (vis != oracle.EMPTY).sum()
+
+
+def test_msaa_single_sample_is_the_centre_layer():
+    sc = synth.scene_tiny_256()
+    lods = oracle.lods_for(sc)
+    vc, _, c = oracle.raster(sc.grooms, sc.camera, lods)
+    vis, cnt = oracle.raster_msaa(sc.grooms, sc.camera, lods, 1)
+    np.testing.assert_array_equal(vis[0], vc)
+    assert cnt == c[0]
+
+
+def test_msaa_resolve_uniform_colour_and_coverage_alpha():
+    """With ambient light only and one albedo, every covered sample has the
+    colour ambient * albedo: rgb is that constant wherever a sample is
+    covered (mean over covered samples, not over all) and alpha is the
+    covered fraction."""
+    sc = synth.tiny_scene(24, width=40, height=32, num_strands=60, segments=5, dist_m=0.3)
+    g = sc.grooms[0]
+    g.strand_width_m = 0.004
+    g.strand_albedo[:] = np.float32([0.3, 0.5, 0.7])
+    lights = synth.Lights(dirs=np.zeros((0, 3), np.float32), radiance=np.zeros((0, 3), np.float32),
+                          ambient=float(np.float32(0.5)))
+    lods = oracle.lods_for(sc)
+    for N in (2, 4):
+        vis, _ = oracle.raster_msaa(sc.grooms, sc.camera, lods, N)
+        num, den = oracle.msaa_decisions(sc.grooms, sc.camera, lods, N, vis)
+        gts = [v64.GroomT(gg, l[1], b) for gg, l, b in zip(sc.grooms, lods, oracle.strand_bases(sc.grooms))]
+        out = v64.resolve_msaa(gts, sc.camera, lights, vis, num, den).numpy()
+        cov = (vis != oracle.EMPTY).sum(0)
+        assert (cov > 0).sum() > 30 and ((cov > 0) & (cov < N)).sum() > 10
+        np.testing.assert_allclose(out[:, 3], cov / N, rtol=0, atol=1e-15)
+        exp = 0.5 * np.float32([0.3, 0.5, 0.7]).astype(np.float64)
+        np.testing.assert_allclose(out[cov > 0, :3], np.broadcast_to(exp, (int((cov > 0).sum()), 3)), rtol=1e-12)
+        assert np.all(out[cov == 0] == 0)
 
 
 def test_raster_invariants_and_thread_independence():
