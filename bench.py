@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", choices=["single_1080p", "crowd_4k", "tiny_256", "lod_sweep", "grad_512",
-                                           "stereo_1080p", "single_1080p_ao", "msaa_1080p"],
+                                           "stereo_1080p", "single_1080p_ao", "msaa_1080p", "shadow_1080p"],
                     default="single_1080p")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -582,6 +582,61 @@ def run_msaa(args, rank, world, local_rank):
     return 0
 
 
+def run_shadow(args, rank, world, local_rank):
+    """The 1080p groom at LOD on (lambda 1, so the depth correction acts)
+    lit through a 1024x1024 shadow map of the key light: the map pass (full
+    geometry from the light) and the shadowed frame, against the same frame
+    without the map."""
+    import torch
+    from paper_2607_04230_b300 import build, hm, synth
+    build.build()
+    torch.cuda.set_device(local_rank)
+    sc, cfg = make_scene("single_1080p")
+    sc.lod = synth.LodParams(1, 1.0)
+    grooms = hm.upload_scene(sc)
+    frame = hm.Frame(sc.camera.width, sc.camera.height)
+    lcam = synth.light_camera(sc.grooms, sc.lights.dirs[0], size=1024, dist_m=1.0)
+    spec = synth.ShadowSpec(light=0, cam=lcam, sigma=100.0, bias_m=0.001, depth_correction=1)
+    npx = lcam.width * lcam.height
+    mc = torch.empty(npx, dtype=torch.int64, device="cuda")
+    ma = torch.empty(npx, dtype=torch.int64, device="cuda")
+    mstats = torch.zeros(8, dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    shadows = [(spec, ma)]
+
+    def map_pass():
+        hm.render_shadow_map(grooms, lcam, mc, ma, stats=mstats)
+
+    def shadowed():
+        hm.render(grooms, sc, frame, shadows=shadows)
+
+    def plain():
+        hm.render(grooms, sc, frame)
+
+    for _ in range(args.warmup):
+        map_pass()
+        shadowed()
+        plain()
+    t_map = statistics.mean(_timed(torch, map_pass, args.steps, flush))
+    t_sh = statistics.mean(_timed(torch, shadowed, args.steps, flush))
+    t_pl = statistics.mean(_timed(torch, plain, args.steps, flush))
+    hm.get_device_status()
+    if rank != 0:
+        return 0
+    st = hm.stats_dict(frame.stats)
+    segs = st["segments"]
+    line = {"metric": METRIC, "value": segs / (t_sh * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_sh, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
+            "config": dict(cfg, workload="single groom, 1920x1080, LOD lambda 1, key light through a 1024^2 "
+                                         "shadow map with the LOD depth correction", lod="on, lambda 1"),
+            "ms": {"shadow_map_pass": t_map, "frame_shadowed": t_sh, "frame_unshadowed": t_pl},
+            "segments_frame": segs, "segments_map": hm.stats_dict(mstats)["segments"],
+            "gpu_launches": 4 * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _gpu_uuid(torch, dev):
     u = str(torch.cuda.get_device_properties(dev).uuid)
     return u if u.startswith("GPU-") else "GPU-" + u
@@ -726,7 +781,8 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     runner = {"crowd_4k": run_crowd, "lod_sweep": run_lod_sweep, "grad_512": run_grad,
-              "stereo_1080p": run_stereo, "msaa_1080p": run_msaa}.get(args.workload, run_native)
+              "stereo_1080p": run_stereo, "msaa_1080p": run_msaa,
+              "shadow_1080p": run_shadow}.get(args.workload, run_native)
     try:
         return runner(args, rank, world, local_rank)
     finally:

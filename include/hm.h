@@ -108,6 +108,28 @@ typedef struct {
     float lambda;                  /* LOD sensitivity, Eq. 2 */
 } hm_lod_params;
 
+/* A shadow map of one light (Sec. 3.4 queries shadow/opacity maps with the
+ * depth correction of Sec. 3.2 "Depth Comparison Artifact Fix").
+ * d_map: [cam.height][cam.width] uint64 keys, the conservative layer of
+ * hm_render_shadow_map with the same camera (device memory, caller's, read
+ * only).  A shaded point X is projected with cam like a strand control point
+ * (16.8 snap); its texel is (floor(X/256), floor(Y/256)).  With z_map the
+ * texel's 24-bit depth / 2^24 and w the point's view depth in the light's
+ * camera, the light reaching X is
+ *     V = exp(-sigma * beta * max(d - bias_m, 0)),  d = (w - near) - z_map (far - near)
+ * (Beer-Lambert past the front-most hair; beta = N_LOD / N of the receiver's
+ * bundle when depth_correction != 0, which is the shift by
+ * Delta = -log(beta) in log depth; else beta = 1).  V = 1 off the map, in
+ * front of the light's near plane, and over an empty texel. */
+typedef struct {
+    const uint64_t *d_map;
+    hm_camera cam;
+    int32_t light;                 /* index of the light this map shadows */
+    float sigma;                   /* hair density, 1/m, >= 0 */
+    float bias_m;                  /* >= 0 */
+    int32_t depth_correction;      /* 0 or 1 */
+} hm_shadow_map;
+
 /* Directional lights plus ambient for the shading model of Sec. 3.4. */
 typedef struct {
     int32_t count;                 /* 0..HM_MAX_LIGHTS */
@@ -115,6 +137,8 @@ typedef struct {
     float radiance[HM_MAX_LIGHTS][3];
     float ambient;
     float k_d, k_s;
+    int32_t n_shadows;             /* 0..count shadow maps, at most one per light */
+    const hm_shadow_map *shadows;  /* host array of n_shadows, read during the call */
 } hm_lights;
 
 /* Reconstruction filter of Sec. 3.3 (defaults in parentheses). */
@@ -206,6 +230,17 @@ hm_status hm_render_visibility_multiview(const hm_groom *grooms, int32_t n, cons
                                          int32_t n_views, uint64_t *const *d_vis_center,
                                          uint64_t *const *d_vis_cons, const uint32_t *const *d_scene_d24,
                                          int32_t clear, hm_frame_stats *d_stats, void *stream);
+
+/* Shadow map for hm_shadow_map: every groom of grooms[0..n) at full detail
+ * (LOD off whatever hm_set_lod holds, no culling: the full geometry set of
+ * Sec. 3.2's depth fix), seen from light_cam, into d_map_center /
+ * d_map_cons ([H][W] uint64 each, 16-byte aligned, cleared first); the
+ * conservative layer is the map.  Uses per-groom LOD buffers of its own, so
+ * the LOD state of the camera's render is left as it was (the two may run
+ * on different streams).  Errors as hm_render_visibility. */
+hm_status hm_render_shadow_map(const hm_groom *grooms, int32_t n, const hm_camera *light_cam,
+                               uint64_t *d_map_center, uint64_t *d_map_cons, hm_frame_stats *d_stats,
+                               void *stream);
 
 /* Multisample software rasterization, the paper's MSAA reference (Sec. 3.3:
  * samples recorded into multiple uint64 layers and resolved later).

@@ -89,6 +89,7 @@ def lib():
         _lib.orc_lod_counts.argtypes = [f32, i32, f32, i32, i32, P, P]
         _lib.orc_raster_msaa.argtypes = [P, i32, P, i32, P, P, P, P, i32]
         _lib.orc_msaa_decisions.argtypes = [P, i32, P, i32, P, P, P, P, P, i32]
+        _lib.orc_shadow_texels.argtypes = [P, i32, P, P, P, P, i64, P, P, i32]
     return _lib
 
 
@@ -217,6 +218,56 @@ def msaa_decisions(grooms, cam, lods, n_samples: int, vis, nthreads: int = 0):
                                   _ptr(vis), _ptr(num), _ptr(den), int(nthreads))
     assert rc == 0
     return num, den
+
+
+def shadow_map(grooms, spec, nthreads: int = 0):
+    """The shadow map of Sec. 3.2's depth fix: every groom at full detail
+    (LOD off) seen from the light's camera spec.cam; returns the
+    conservative key layer uint64 [h*w] (front-most hair depth per texel)."""
+    from paper_2607_04230_b300.synth import LodParams
+    lods = [lod(g, spec.cam, LodParams(0)) for g in grooms]
+    _, va, _ = raster(grooms, spec.cam, lods, nthreads=nthreads)
+    return va
+
+
+def shadow_texels(grooms, cam, lods, keys, sx, sy, light_cam, nthreads: int = 0):
+    """Texel of the light's map under each key's decoded position at the
+    sample point (sx, sy) in 1/256 px; -1 for none (hm_oracle.c)."""
+    arr, refs = _groom_array(grooms, lods)
+    keys = np.ascontiguousarray(keys, np.uint64)
+    sx = np.ascontiguousarray(sx, np.int64)
+    sy = np.ascontiguousarray(sy, np.int64)
+    out = np.full(keys.shape, -1, np.int64)
+    rc = lib().orc_shadow_texels(arr, len(refs), ctypes.byref(camera_struct(cam)), _ptr(keys), _ptr(sx), _ptr(sy),
+                                 keys.size, ctypes.byref(camera_struct(light_cam)), _ptr(out), int(nthreads))
+    assert rc == 0
+    return out
+
+
+def centre_shadow_texels(grooms, cam, lods, vis_c, maps, nthreads: int = 0):
+    """Per shadow map, the texel under every centre key decoded at its pixel
+    centre ([H*W] int64, -1 where none): the decisions the shadowed resolve
+    takes for the shaded colours."""
+    W = cam.width
+    p = np.arange(vis_c.size, dtype=np.int64)
+    sx, sy = 256 * (p % W) + 128, 256 * (p // W) + 128
+    return [shadow_texels(grooms, cam, lods, vis_c, sx, sy, spec.cam, nthreads) for spec, _ in maps]
+
+
+def sample_shadow_texels(grooms, cam, lods, n_samples: int, vis_s, maps, nthreads: int = 0):
+    """Per shadow map, [n_samples][H*W] texels of each sample layer's keys
+    decoded at their own sample points."""
+    W = cam.width
+    ox, oy = msaa_offsets(n_samples)
+    p = np.arange(vis_s.shape[1], dtype=np.int64)
+    out = []
+    for spec, _ in maps:
+        t = np.empty(vis_s.shape, np.int64)
+        for k in range(n_samples):
+            t[k] = shadow_texels(grooms, cam, lods, vis_s[k], 256 * (p % W) + 128 + int(ox[k]),
+                                 256 * (p // W) + 128 + int(oy[k]), spec.cam, nthreads)
+        out.append(t)
+    return out
 
 
 def resolve_decisions(grooms, cam, lods, filt, vis_c, vis_a, pixels=None, nthreads: int = 0):

@@ -496,8 +496,10 @@ static int screen_tangent(const orc_camera *cam, f3 X, f3 T, float *tsx, float *
     return 0;
 }
 
-static decode_t decode_key(const orc_groom *gs, int32_t n, const orc_camera *cam, uint64_t key,
-                           int64_t px, int64_t py) {
+/* Decode of a key at the sample point (sx, sy) in 1/256 px: the segment's
+ * projection parameter there, the FP32 position and unit tangent. */
+static decode_t decode_key_at(const orc_groom *gs, int32_t n, const orc_camera *cam, uint64_t key,
+                              int64_t sx, int64_t sy) {
     decode_t d;
     memset(&d, 0, sizeof d);
     int64_t s;
@@ -514,7 +516,7 @@ static decode_t decode_key(const orc_groom *gs, int32_t n, const orc_camera *cam
     f3 p1 = control_point(P, mh, g->L, C, j + 1);
     f3 pp = (j + 2 <= C - 1) ? control_point(P, mh, g->L, C, j + 2) : mk(0, 0, 0);
     proj_t a = project(cam, p0), b = project(cam, p1);
-    float t = segment_t(a.X, a.Y, b.X, b.Y, 256 * px + 128, 256 * py + 128, &d.num, &d.den);
+    float t = segment_t(a.X, a.Y, b.X, b.Y, sx, sy, &d.num, &d.den);
     d.X = mk(p0.x + ((p1.x - p0.x) * t), p0.y + ((p1.y - p0.y) * t), p0.z + ((p1.z - p0.z) * t));
     f3 T0 = calc_tangent(j, C, pm, p0, p1);
     f3 T1 = calc_tangent(j + 1, C, p0, p1, pp);
@@ -522,6 +524,11 @@ static decode_t decode_key(const orc_groom *gs, int32_t n, const orc_camera *cam
     d.iso = screen_tangent(cam, d.X, d.T, &d.tsx, &d.tsy);
     d.ok = 1;
     return d;
+}
+
+static decode_t decode_key(const orc_groom *gs, int32_t n, const orc_camera *cam, uint64_t key,
+                           int64_t px, int64_t py) {
+    return decode_key_at(gs, n, cam, key, 256 * px + 128, 256 * py + 128);
 }
 
 /* Strip membership of window offset (dx, dy) for a unit screen tangent:
@@ -586,8 +593,8 @@ int orc_resolve_decisions(const orc_groom *grooms, int32_t n_grooms, const orc_c
 }
 
 /* ---------------------------------------------------------------------------
- * multisample rasterization (Sec. 3.3: "multisampling for the software
- * rasterizer, recording samples into multiple layers")
+ * multisample rasterization (Sec. 3.3 keeps a multisampled variant of the
+ * software rasterizer, one uint64 layer per sample, as its quality reference)
  *
  * Reading: N point samples per pixel at offsets (ox[k], oy[k]) (1/256 px
  * from the pixel centre); sample k of a pixel is covered by a segment iff the
@@ -708,6 +715,39 @@ int orc_msaa_decisions(const orc_groom *grooms, int32_t n_grooms, const orc_came
 /* ---------------------------------------------------------------------------
  * single-step entry points used by the pin tests
  * ------------------------------------------------------------------------- */
+/* ---------------------------------------------------------------------------
+ * shadow-map texel of a shaded point (Sec. 3.2 "Depth Comparison Artifact
+ * Fix"; Sec. 3.4 queries shadow/opacity maps with that correction)
+ *
+ * Reading: the FP32 position X decoded from the key at the sample point is
+ * projected with the light's camera exactly like a strand control point
+ * (same clip rows, divide, guard band and 1/256 px snap); its texel is
+ * (floor(X / 256), floor(Y / 256)).  texel[q] = row-major texel index, or -1
+ * when X is in front of the light's near plane, off the map, or the key does
+ * not decode.  Everything continuous (the depth past the occluder, the
+ * visibility) is the value layer's.
+ * ------------------------------------------------------------------------- */
+int orc_shadow_texels(const orc_groom *grooms, int32_t n_grooms, const orc_camera *cam, const uint64_t *keys,
+                      const int64_t *sx, const int64_t *sy, int64_t n_keys, const orc_camera *light,
+                      int64_t *texel, int32_t nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t q = 0; q < n_keys; ++q) {
+        texel[q] = -1;
+        if (key_empty(keys[q])) continue;
+        decode_t d = decode_key_at(grooms, n_grooms, cam, keys[q], sx[q], sy[q]);
+        if (!d.ok) continue;
+        proj_t p = project(light, d.X);
+        if (!p.valid) continue;
+        int64_t tx = floor_div256(p.X), ty = floor_div256(p.Y);
+        if (tx < 0 || ty < 0 || tx >= light->width || ty >= light->height) continue;
+        texel[q] = ty * light->width + tx;
+    }
+    return 0;
+}
+
 int orc_strand_control_points(const orc_groom *g, int64_t s, int32_t C, float *out) {
     f3 P[64], mh[64];
     if (g->L < 2 || g->L > 64 || C < 2) return 1;

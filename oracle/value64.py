@@ -51,7 +51,7 @@ def key_fields(vis: np.ndarray):
 class GroomT:
     """float64 tensors of one groom for the value layer."""
 
-    def __init__(self, g, lod_c, base, layer_verts=None, albedo=None):
+    def __init__(self, g, lod_c, base, layer_verts=None, albedo=None, lod_n=None):
         self.L = g.num_layers
         self.S = g.num_strands
         self.base = int(base)
@@ -63,6 +63,9 @@ class GroomT:
         self.sface = torch.from_numpy(g.strand_face.astype(np.int64))
         self.bary = torch.from_numpy(g.strand_bary.astype(np.float64))
         self.lod_c = torch.from_numpy(np.asarray(lod_c).astype(np.int64))
+        # strands per bundle and, when given, the LOD's strands drawn per bundle
+        self.n_face = np.bincount(np.asarray(g.strand_face, np.int64), minlength=g.num_faces)
+        self.lod_n = None if lod_n is None else np.asarray(lod_n, np.int64)
         self.roughness = float(np.float32(g.roughness))
         self.tilt = float(np.float32(g.tilt))
         ao = getattr(g, "vert_ao", None)
@@ -183,11 +186,53 @@ def pixel_geometry(gt: GroomT, sg, seg, num, den):
     return X, T, s
 
 
-def shade(X, T, albedo, cam, lights, roughness, tilt, ao=None):
+def shadow_visibility(gt: GroomT, X, s, texels, maps, n_lights):
+    """Per-light visibility [N][n_lights] of the shaded points X through the
+    shadow maps (1 for lights without one).
+
+    Sec. 3.2's depth fix: light through hair falls off as exp(-sigma d)
+    (Beer-Lambert, d the depth travelled past the front-most hair); with only
+    a fraction beta = N_remaining / N_total of the strands drawn the density
+    is sigma beta, i.e. the depth is shifted by Delta = -log(beta) in log
+    space: V = exp(-sigma exp(log d - Delta)) = exp(-sigma beta d).
+    Readings: the map is the front-most hair depth of the full geometry (a
+    one-layer opacity map with uniform density sigma); d = w_X - near -
+    z_map (far - near) in metres of the light's view depth, less a bias,
+    clamped at 0; beta is the receiver bundle's N_LOD / N when the map asks
+    for the correction, else 1.  `texels` holds, per map, the texel index
+    under each point (-1: unshadowed), decided in FP32 by hm_oracle.c."""
+    Vis = torch.ones((X.shape[0], n_lights), dtype=torch.float64)
+    s_np = np.asarray(s, np.int64)
+    face = gt.sface[torch.as_tensor(s_np)].numpy()
+    for (spec, keys), tex in zip(maps, texels):
+        tex = np.asarray(tex, np.int64)
+        keys = np.asarray(keys, np.uint64)
+        hit = tex >= 0
+        k = np.where(hit, keys[np.maximum(tex, 0)], PAYLOAD_MASK)
+        hit &= (k & PAYLOAD_MASK) != PAYLOAD_MASK
+        zmap = (k >> np.uint64(40)).astype(np.float64) / float(1 << 24)
+        M = torch.from_numpy(np.asarray(spec.cam.view_proj, np.float64))
+        w = X @ M[3, :3] + M[3, 3]
+        near, far = float(np.float32(spec.cam.near)), float(np.float32(spec.cam.far))
+        d = (w - near) - torch.from_numpy(zmap) * (far - near) - float(np.float32(spec.bias_m))
+        beta = np.ones(X.shape[0])
+        if spec.depth_correction:
+            if gt.lod_n is None:
+                raise ValueError("depth correction needs the LOD strand counts (GroomT lod_n)")
+            beta = gt.lod_n[face] / np.maximum(gt.n_face[face], 1)
+        sig = float(np.float32(spec.sigma)) * torch.from_numpy(beta)
+        v = torch.exp(-sig * torch.clamp(d, min=0.0))
+        v = torch.where(torch.from_numpy(hit), v, torch.ones_like(v))
+        Vis = Vis.index_put((torch.arange(X.shape[0]), torch.full((X.shape[0],), int(spec.light))), v)
+    return Vis
+
+
+def shade(X, T, albedo, cam, lights, roughness, tilt, ao=None, vis=None):
     """Sec. 3.4: per directional light, Kajiya-Kay diffuse
     albedo k_d sqrt(1 - (T.L)^2) plus an R lobe
-    k_s exp(-((T.L + T.V)/2 + sin(tilt))^2 / (2 beta^2)); plus ambient albedo,
-    darkened by the baked ambient occlusion ao [N][1] when given."""
+    k_s exp(-((T.L + T.V)/2 + sin(tilt))^2 / (2 beta^2)), times the light's
+    visibility vis [N][lights] when given; plus ambient albedo, darkened by
+    the baked ambient occlusion ao [N][1] when given."""
     cam_pos = torch.from_numpy(np.asarray(cam.cam_pos, np.float64))
     V = _normalize(cam_pos[None, :] - X)
     kd = float(np.float32(lights.k_d))
@@ -207,7 +252,8 @@ def shade(X, T, albedo, cam, lights, roughness, tilt, ao=None):
                                        torch.zeros_like(sin2))
         u = (tl + tv) * 0.5 + sa
         fs = ks * torch.exp(-(u * u) / b2)
-        out = out + E[None, :] * (fd + fs)
+        term = E[None, :] * (fd + fs)
+        out = out + (term if vis is None else vis[:, li:li + 1] * term)
     return out
 
 
@@ -255,9 +301,11 @@ def _geometry_all(gts, sg, seg, num, den):
     return X, T, parts_idx, parts_alb
 
 
-def resolve(gts, cam, lights, filt, vis_c, vis_a, dec, pixels=None):
+def resolve(gts, cam, lights, filt, vis_c, vis_a, dec, pixels=None, shadows=None):
     """RGBA (straight alpha, float64 [N][4]) for the given pixels (all when
-    None), Sec. 3.3-3.4.  Returns (rgba, pixel_index)."""
+    None), Sec. 3.3-3.4.  Returns (rgba, pixel_index).  shadows: optional
+    list of (spec, map keys) with dec["shadow_texels"] the per-map texel of
+    every centre key (oracle.centre_shadow_texels)."""
     W, H = cam.width, cam.height
     eG, dG, sgG, segG = key_fields(vis_c)
     eA, dA, sgA, segA = key_fields(vis_a)
@@ -271,8 +319,12 @@ def resolve(gts, cam, lights, filt, vis_c, vis_a, dec, pixels=None):
         gt = gts[gi]
         sel = cen[idx.numpy()]
         ao = pixel_ao(gt, sgG[sel], segG[sel], dec_full(dec, "numG", sel), dec_full(dec, "denG", sel))
+        vis = None
+        if shadows:
+            vis = shadow_visibility(gt, Xc[idx], s, [t[sel] for t in dec["shadow_texels"]], shadows,
+                                    lights.dirs.shape[0])
         Ccen = Ccen.index_put((idx,), shade(Xc[idx], Tc[idx], gt.albedo[s], cam, lights,
-                                            gt.roughness, gt.tilt, ao))
+                                            gt.roughness, gt.tilt, ao, vis))
     Cimg = torch.zeros((npx, 3), dtype=torch.float64).index_put((torch.from_numpy(cen),), Ccen)
 
     if pixels is None:
@@ -391,11 +443,12 @@ def full_image(rgba, pixels, width, height):
     return img.reshape(height, width, 4)
 
 
-def resolve_msaa(gts, cam, lights, vis, num, den):
+def resolve_msaa(gts, cam, lights, vis, num, den, shadows=None, texels=None):
     """Multisample resolve (Sec. 3.3's MSAA reference): every covered sample
     is shaded at its own position; the premultiplied colour is the mean over
     all N samples and alpha the covered fraction.  Returns straight-alpha
-    RGBA float64 [H*W][4]."""
+    RGBA float64 [H*W][4].  shadows: optional list of (spec, map keys) with
+    texels[m][k] the texel of sample layer k's keys in map m."""
     N, npx = vis.shape
     acc = torch.zeros((npx, 3), dtype=torch.float64)
     cov = torch.zeros((npx, 1), dtype=torch.float64)
@@ -410,7 +463,11 @@ def resolve_msaa(gts, cam, lights, vis, num, den):
             gt = gts[gi]
             sel = idx[pidx.numpy()]
             ao = pixel_ao(gt, sg[sel], seg[sel], num[k][sel], den[k][sel])
-            C = C.index_put((pidx,), shade(X[pidx], T[pidx], gt.albedo[s], cam, lights, gt.roughness, gt.tilt, ao))
+            vs = None
+            if shadows:
+                vs = shadow_visibility(gt, X[pidx], s, [t[k][sel] for t in texels], shadows, lights.dirs.shape[0])
+            C = C.index_put((pidx,), shade(X[pidx], T[pidx], gt.albedo[s], cam, lights, gt.roughness, gt.tilt, ao,
+                                           vs))
         t = torch.from_numpy(idx)
         acc = acc.index_add(0, t, C)
         cov = cov.index_add(0, t, torch.ones((idx.size, 1), dtype=torch.float64))

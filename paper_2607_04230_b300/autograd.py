@@ -16,11 +16,11 @@ from . import hm
 
 class HairRender(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, layer_verts, albedo, groom, scene, frame):
+    def forward(ctx, layer_verts, albedo, groom, scene, frame, shadows=None):
         groom.update_layer_verts(layer_verts.detach().float().contiguous())
         groom.update_albedo(albedo.detach().float().contiguous())
-        hm.render([groom], scene, frame)
-        ctx.groom, ctx.scene = groom, scene
+        hm.render([groom], scene, frame, shadows=shadows)
+        ctx.groom, ctx.scene, ctx.shadows = groom, scene, shadows
         ctx.vis = (frame.vis_center.clone(), frame.vis_cons.clone())
         ctx.lv_shape, ctx.alb_shape = layer_verts.shape, albedo.shape
         return frame.rgba.clone()
@@ -34,10 +34,12 @@ class HairRender(torch.autograd.Function):
         nbytes = hm.backward_scratch_bytes(sc.camera.width, sc.camera.height)
         scratch = torch.empty(nbytes // 4, dtype=torch.float32, device=dev)
         hm.shade_backward([ctx.groom], sc.camera, sc.lights, sc.filt, ctx.vis[0], ctx.vis[1],
-                          grad_rgba.float().contiguous(), [glv], [galb], scratch)
-        return glv, galb, None, None, None
+                          grad_rgba.float().contiguous(), [glv], [galb], scratch, shadows=ctx.shadows)
+        return glv, galb, None, None, None, None
 
 
-def render(groom, scene, frame, layer_verts, albedo):
-    """Differentiable RGBA of one groom w.r.t. its layer vertices and albedo."""
-    return HairRender.apply(layer_verts, albedo, groom, scene, frame)
+def render(groom, scene, frame, layer_verts, albedo, shadows=None):
+    """Differentiable RGBA of one groom w.r.t. its layer vertices and albedo
+    (shadow maps, when given, are held fixed: gradients flow through the
+    receiver's depth, not through the map)."""
+    return HairRender.apply(layer_verts, albedo, groom, scene, frame, shadows)

@@ -31,6 +31,10 @@ struct hm_groom_s {
     uint4 *d_lod;
     uint32_t *d_batch_map;
     uint32_t *d_counters;
+    // full-detail LOD state of the shadow-map pass, kept apart from the camera's
+    uint4 *d_lod_full;
+    uint32_t *d_batch_map_full;
+    uint32_t *d_counters_full;
 };
 
 namespace {
@@ -176,6 +180,9 @@ void free_groom(hm_groom g) {
     cudaFree(g->d_lod);
     cudaFree(g->d_batch_map);
     cudaFree(g->d_counters);
+    cudaFree(g->d_lod_full);
+    cudaFree(g->d_batch_map_full);
+    cudaFree(g->d_counters_full);
     delete g;
 }
 
@@ -318,6 +325,9 @@ hm_status hm_create_groom(const hm_groom_desc *d, void *stream, hm_groom *out) {
     HM_ALLOC(g->d_lod, (size_t)F, "alloc lod")
     HM_ALLOC(g->d_batch_map, max_batches, "alloc batch map")
     HM_ALLOC(g->d_counters, (size_t)hm::kCtrWords, "alloc counters")
+    HM_ALLOC(g->d_lod_full, (size_t)F, "alloc shadow-pass lod")
+    HM_ALLOC(g->d_batch_map_full, max_batches, "alloc shadow-pass batch map")
+    HM_ALLOC(g->d_counters_full, (size_t)hm::kCtrWords, "alloc shadow-pass counters")
 #undef HM_ALLOC
     if (st != HM_OK) {
         free_groom(g);
@@ -335,6 +345,7 @@ hm_status hm_create_groom(const hm_groom_desc *d, void *stream, hm_groom *out) {
     cp(g->d_albedo, alb.data(), (size_t)S * sizeof(float4));
     cp(g->d_delta, d->bundle_delta, (size_t)F * sizeof(float));
     if (e == cudaSuccess) e = cudaMemsetAsync(g->d_counters, 0, hm::kCtrWords * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_counters_full, 0, hm::kCtrWords * sizeof(uint32_t), s);
     // LOD state starts at full detail so a resolve before any render decodes safely
     if (e == cudaSuccess) {
         std::vector<uint4> lod0(F);
@@ -440,6 +451,40 @@ static hm_status render_views(const hm_groom *grooms, int32_t n, int32_t first, 
 
 static hm_status lights_dev(const hm_lights *l, hm::LightsDev &ld);
 
+hm_status hm_render_shadow_map(const hm_groom *grooms, int32_t n, const hm_camera *light_cam,
+                               uint64_t *d_map_center, uint64_t *d_map_cons, hm_frame_stats *d_stats,
+                               void *stream) {
+    hm_status st = check_camera(light_cam);
+    if (st != HM_OK) return st;
+    if (!d_map_center || !d_map_cons) return fail(HM_ERR_INVALID_ARG, "shadow map buffer is NULL");
+    if ((reinterpret_cast<uintptr_t>(d_map_center) & 15) || (reinterpret_cast<uintptr_t>(d_map_cons) & 15))
+        return fail(HM_ERR_INVALID_ARG, "shadow map buffers must be 16-byte aligned");
+    if (d_map_center == d_map_cons) return fail(HM_ERR_INVALID_ARG, "the two layers must be distinct buffers");
+    hm::CallTable tab;
+    if ((st = build_table(grooms, n, tab)) != HM_OK) return st;
+    for (int i = 0; i < n; ++i) {
+        // full geometry into the pass's own LOD buffers
+        tab.g[i].lod = grooms[i]->d_lod_full;
+        tab.g[i].batch_map = grooms[i]->d_batch_map_full;
+        tab.g[i].counters = grooms[i]->d_counters_full;
+        tab.g[i].lod_enabled = 0;
+    }
+    hm::ViewSet views;
+    std::memset(&views, 0, sizeof views);
+    views.n = 1;
+    views.cam[0] = cam_dev(light_cam);
+    views.vis_c[0] = d_map_center;
+    views.vis_a[0] = d_map_cons;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t npx = (int64_t)light_cam->width * light_cam->height;
+    HM_CUDA(hm::launch_clear(d_map_center, d_map_cons, npx, nullptr, 1, d_stats, s), "clear");
+    HM_CUDA(hm::launch_lod(tab, views.cam[0], d_stats, s), "lod");
+    HM_CUDA(hm::launch_raster(tab, views, g_tuning.raster_precheck != 0, g_tuning.raster_min_blocks,
+                              g_tuning.raster_ctas_per_sm, d_stats, s),
+            "raster");
+    return HM_OK;
+}
+
 hm_status hm_render_visibility_msaa(const hm_groom *grooms, int32_t n, const hm_camera *cam, int32_t samples,
                                     uint64_t *d_vis_samples, int32_t clear, hm_frame_stats *d_stats, void *stream) {
     hm_status st = check_camera(cam);
@@ -533,6 +578,29 @@ static hm_status lights_dev(const hm_lights *l, hm::LightsDev &ld) {
     ld.ambient = l->ambient;
     ld.kd = l->k_d;
     ld.ks = l->k_s;
+    for (int i = 0; i < HM_MAX_LIGHTS; ++i) ld.shadow_of[i] = -1;
+    if (l->n_shadows < 0 || l->n_shadows > l->count)
+        return fail(HM_ERR_INVALID_ARG, "shadow map count out of range");
+    if (l->n_shadows > 0 && !l->shadows) return fail(HM_ERR_INVALID_ARG, "shadow maps are NULL");
+    ld.n_shadow = l->n_shadows;
+    for (int i = 0; i < l->n_shadows; ++i) {
+        const hm_shadow_map &m = l->shadows[i];
+        if (m.light < 0 || m.light >= l->count) return fail(HM_ERR_INVALID_ARG, "shadow map light out of range");
+        if (ld.shadow_of[m.light] >= 0) return fail(HM_ERR_INVALID_ARG, "two shadow maps for one light");
+        if (!m.d_map || (reinterpret_cast<uintptr_t>(m.d_map) & 7))
+            return fail(HM_ERR_INVALID_ARG, "shadow map NULL or misaligned");
+        if (!(m.sigma >= 0.0f) || !std::isfinite(m.sigma) || !(m.bias_m >= 0.0f) || !std::isfinite(m.bias_m) ||
+            (m.depth_correction != 0 && m.depth_correction != 1))
+            return fail(HM_ERR_INVALID_ARG, "shadow map sigma, bias or depth_correction invalid");
+        hm_status st = check_camera(&m.cam);
+        if (st != HM_OK) return st;
+        ld.shadow_of[m.light] = i;
+        ld.sh[i].map = m.d_map;
+        ld.sh[i].cam = cam_dev(&m.cam);
+        ld.sh[i].sigma = m.sigma;
+        ld.sh[i].bias = m.bias_m;
+        ld.sh[i].corr = m.depth_correction;
+    }
     return HM_OK;
 }
 

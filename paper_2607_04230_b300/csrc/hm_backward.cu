@@ -177,7 +177,7 @@ __device__ void screen_tangent_adjoint(const CamDev &cam, float3 X, float3 T, fl
 
 // Adjoint of the shading model (Sec. 3.4) at one pixel.
 __device__ void shade_adjoint(float3 X, float3 T, float3 alb, const CamDev &cam, const LightsDev &Ls, float rough,
-                              float tilt, float ao, float3 dC, float3 &dX, float3 &dT, float3 &dalb) {
+                              float tilt, float ao, float beta, float3 dC, float3 &dX, float3 &dT, float3 &dalb) {
     const float3 Vr = f3(cam.cam_pos[0] - X.x, cam.cam_pos[1] - X.y, cam.cam_pos[2] - X.z);
     const float vl = len3(Vr);
     const float3 V = vl > 0.f ? mul3(Vr, 1.f / vl) : f3(0.f, 0.f, 0.f);
@@ -186,6 +186,7 @@ __device__ void shade_adjoint(float3 X, float3 T, float3 alb, const CamDev &cam,
     dalb = mul3(dC, Ls.ambient * ao);
     dT = f3(0.f, 0.f, 0.f);
     float3 dV = f3(0.f, 0.f, 0.f);
+    float3 dXs = f3(0.f, 0.f, 0.f);       // through the shadow maps' receiver depth
     for (int l = 0; l < Ls.n; ++l) {
         const float3 Ld = f3(Ls.dir[l][0], Ls.dir[l][1], Ls.dir[l][2]);
         const float tl = dot3(T, Ld), tv = dot3(T, V);
@@ -193,7 +194,20 @@ __device__ void shade_adjoint(float3 X, float3 T, float3 alb, const CamDev &cam,
         const float sq = sin2 > 0.f ? sqrtf(sin2) : 0.f;
         const float u = (tl + tv) * 0.5f + sa;
         const float fs = Ls.ks * __expf(-(u * u) / (2.f * b2));
-        const float3 gE = f3(dC.x * Ls.rad[l][0], dC.y * Ls.rad[l][1], dC.z * Ls.rad[l][2]);
+        float vis = 1.f;
+        if (Ls.shadow_of[l] >= 0) {
+            const ShadowDev &m = Ls.sh[Ls.shadow_of[l]];
+            float dvw;
+            vis = shadow_visibility(m, X, beta, &dvw);
+            if (dvw != 0.f) {
+                // d(out)/dw = dvw E (alb kk + fs), w = row 3 of the light's view_proj . (X, 1)
+                const float kk = Ls.kd * sq;
+                const float g = dvw * (dC.x * Ls.rad[l][0] * (alb.x * kk + fs) + dC.y * Ls.rad[l][1] * (alb.y * kk + fs) +
+                                       dC.z * Ls.rad[l][2] * (alb.z * kk + fs));
+                dXs = add3(dXs, f3(g * m.cam.m[12], g * m.cam.m[13], g * m.cam.m[14]));
+            }
+        }
+        const float3 gE = f3(vis * dC.x * Ls.rad[l][0], vis * dC.y * Ls.rad[l][1], vis * dC.z * Ls.rad[l][2]);
         dalb = add3(dalb, mul3(gE, Ls.kd * sq));
         const float dsq = Ls.kd * dot3(gE, alb);
         const float dfs = gE.x + gE.y + gE.z;
@@ -204,7 +218,7 @@ __device__ void shade_adjoint(float3 X, float3 T, float3 alb, const CamDev &cam,
         dT = add3(dT, add3(mul3(Ld, dtl), mul3(V, dtv)));
         dV = add3(dV, mul3(T, dtv));
     }
-    dX = mul3(unit_adjoint(V, vl, dV), -1.f);
+    dX = add3(mul3(unit_adjoint(V, vl, dV), -1.f), dXs);
 }
 
 struct BwdSinks {
@@ -329,7 +343,8 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_adjoint_kernel(
         if (d.ok) {
             const GroomDev &g = tab.g[d.gi];
             const float4 a = __ldg(&g.albedo[d.s]);
-            c = shade(d.X, d.T, f3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt, decoded_ao(g, d));
+            c = shade(d.X, d.T, f3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt, decoded_ao(g, d),
+                      receiver_beta(g, Ls, d.s));
         }
         s_col[i] = c;
         const int tx = lx - R, ty = ly - R;
@@ -346,10 +361,9 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_adjoint_kernel(
     const int gx = x0 + tx, gy = y0 + ty;
     const bool inside = gx < W && gy < H;
     const int mid = (ty + R) * sw + tx + R;
-    uint64_t ka = kEmptyKey, kgP = kEmptyKey;
+    uint64_t ka = kEmptyKey;
     int dA = -1;
     if (inside) {
-        kgP = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + (int64_t)gy * W + gx));
         ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx));
         if (fp.enabled && !key_empty(ka)) {
             dA = (int)(ka >> 40);
@@ -492,6 +506,7 @@ __global__ void __launch_bounds__(kGeoThreads) geometry_adjoint_kernel(CallTable
                         const float4 a = __ldg(&g.albedo[d.s]);
                         float3 dalb;
                         shade_adjoint(d.X, d.T, f3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt, decoded_ao(g, d),
+                                      receiver_beta(g, Ls, d.s),
                                       f3(gc.x, gc.y, gc.z), dX, dT, dalb);
                         float *ga = sinks.galb[d.gi];
                         if (ga) {

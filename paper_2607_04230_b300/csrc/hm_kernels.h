@@ -10,11 +10,21 @@
 
 namespace hm {
 
+struct ShadowDev {
+    const uint64_t *map;       // [cam.H][cam.W] keys
+    CamDev cam;
+    float sigma, bias;
+    int32_t corr;              // apply beta = N_LOD / N of the receiver's bundle
+};
+
 struct LightsDev {
     int32_t n;
     float dir[HM_MAX_LIGHTS][3];
     float rad[HM_MAX_LIGHTS][3];
     float ambient, kd, ks;
+    int32_t n_shadow;
+    int32_t shadow_of[HM_MAX_LIGHTS];   // map of each light, -1 none
+    ShadowDev sh[HM_MAX_LIGHTS];
 };
 
 struct FilterDev {

@@ -94,7 +94,8 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
         if (d.ok) {
             const GroomDev &g = tab.g[d.gi];
             const float4 a = __ldg(&g.albedo[d.s]);
-            c = shade(d.X, d.T, make_float3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt, decoded_ao(g, d));
+            c = shade(d.X, d.T, make_float3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt, decoded_ao(g, d),
+                      receiver_beta(g, Ls, d.s));
         }
         s_col[i] = c;
         const int tx = lx - R, ty = ly - R;
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(256) resolve_msaa_kernel(CallTable tab, CamDev
             const GroomDev &g = tab.g[d.gi];
             const float4 a = __ldg(&g.albedo[d.s]);
             const float3 c = shade(d.X, d.T, make_float3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt,
-                                   decoded_ao(g, d));
+                                   decoded_ao(g, d), receiver_beta(g, Ls, d.s));
             acc.x += c.x;
             acc.y += c.y;
             acc.z += c.z;

@@ -27,8 +27,41 @@ __device__ __forceinline__ float decoded_ao(const GroomDev &g, const Decoded &d)
 
 // Shading (Sec. 3.4) with the ambient term darkened by the baked ambient
 // occlusion ao.
+// Fraction beta = N_LOD / N of the receiver's bundle drawn at the current
+// LOD (Sec. 3.2 depth fix); 1 when no shadow map is bound.
+__device__ __forceinline__ float receiver_beta(const GroomDev &g, const LightsDev &Ls, int64_t s) {
+    if (Ls.n_shadow == 0) return 1.0f;
+    const uint32_t f = __ldg(&g.sface[s]);
+    const int n = __ldg(&g.faces[f + 1]).w - __ldg(&g.faces[f]).w;
+    const uint32_t nl = g.lod[f].x;
+    return n > 0 ? __fdiv_rn((float)nl, (float)n) : 1.0f;
+}
+
+// Light reaching X through a shadow map: Beer-Lambert exp(-sigma beta d)
+// over the depth d travelled past the map's front-most hair (Sec. 3.2: the
+// LOD's strand fraction beta shifts log depth by -log beta).  The texel is
+// the one under X's snapped projection, a decision taken in the same
+// binary32 operations as the rasterizer's projection.  *dvis_dw receives
+// dV/dw (w the light-view depth of X) for the adjoint.
+__device__ __forceinline__ float shadow_visibility(const ShadowDev &m, float3 X, float beta, float *dvis_dw) {
+    *dvis_dw = 0.0f;
+    const Proj P = project(m.cam, X);
+    if (!P.valid) return 1.0f;
+    const int32_t tx = P.X >> 8, ty = P.Y >> 8;
+    if (tx < 0 || ty < 0 || tx >= m.cam.W || ty >= m.cam.H) return 1.0f;
+    const uint64_t key = __ldg(reinterpret_cast<const unsigned long long *>(m.map) + (int64_t)ty * m.cam.W + tx);
+    if (key_empty(key)) return 1.0f;
+    const float zmap = (float)(uint32_t)(key >> 40) * (1.0f / 16777216.0f);
+    const float d = (P.w - m.cam.near_m) - zmap * (m.cam.far_m - m.cam.near_m) - m.bias;
+    if (!(d > 0.0f)) return 1.0f;
+    const float k = m.sigma * (m.corr ? beta : 1.0f);
+    const float v = __expf(-k * d);
+    *dvis_dw = -k * v;
+    return v;
+}
+
 __device__ __forceinline__ float3 shade(float3 X, float3 T, float3 alb, const CamDev &cam, const LightsDev &Ls,
-                                        float rough, float tilt, float ao) {
+                                        float rough, float tilt, float ao, float beta) {
     float3 V = make_float3(cam.cam_pos[0] - X.x, cam.cam_pos[1] - X.y, cam.cam_pos[2] - X.z);
     float vn = rsqrtf(fmaxf(V.x * V.x + V.y * V.y + V.z * V.z, 1e-30f));
     V = make_float3(V.x * vn, V.y * vn, V.z * vn);
@@ -43,9 +76,14 @@ __device__ __forceinline__ float3 shade(float3 X, float3 T, float3 alb, const Ca
         const float kk = Ls.kd * (sin2 > 0.0f ? sqrtf(sin2) : 0.0f);
         const float u = (tl + tv) * 0.5f + sa;
         const float fs = Ls.ks * __expf(-(u * u) * inv2b2);
-        out.x += Ls.rad[l][0] * (alb.x * kk + fs);
-        out.y += Ls.rad[l][1] * (alb.y * kk + fs);
-        out.z += Ls.rad[l][2] * (alb.z * kk + fs);
+        float vis = 1.0f;
+        if (Ls.shadow_of[l] >= 0) {
+            float dvw;
+            vis = shadow_visibility(Ls.sh[Ls.shadow_of[l]], X, beta, &dvw);
+        }
+        out.x += vis * (Ls.rad[l][0] * (alb.x * kk + fs));
+        out.y += vis * (Ls.rad[l][1] * (alb.y * kk + fs));
+        out.z += vis * (Ls.rad[l][2] * (alb.z * kk + fs));
     }
     return out;
 }

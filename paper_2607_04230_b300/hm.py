@@ -49,10 +49,16 @@ class LodParams(ctypes.Structure):
     _fields_ = [("enabled", ctypes.c_int32), ("lambda_", ctypes.c_float)]
 
 
+class ShadowMap(ctypes.Structure):
+    _fields_ = [("d_map", ctypes.c_void_p), ("cam", Camera), ("light", ctypes.c_int32), ("sigma", ctypes.c_float),
+                ("bias_m", ctypes.c_float), ("depth_correction", ctypes.c_int32)]
+
+
 class Lights(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int32), ("dir", (ctypes.c_float * 3) * MAX_LIGHTS),
                 ("radiance", (ctypes.c_float * 3) * MAX_LIGHTS), ("ambient", ctypes.c_float),
-                ("k_d", ctypes.c_float), ("k_s", ctypes.c_float)]
+                ("k_d", ctypes.c_float), ("k_s", ctypes.c_float), ("n_shadows", ctypes.c_int32),
+                ("shadows", ctypes.POINTER(ShadowMap))]
 
 
 class FilterParams(ctypes.Structure):
@@ -102,6 +108,7 @@ def lib():
         "hm_render_visibility_multiview": [P, i32, P, i32, P, P, P, i32, P, P],
         "hm_resolve_shade": [P, i32, P, P, P, P, P, P, P, P],
         "hm_render_visibility_msaa": [P, i32, P, i32, P, i32, P, P],
+        "hm_render_shadow_map": [P, i32, P, P, P, P, P],
         "hm_resolve_msaa": [P, i32, P, P, i32, P, P, P],
         "hm_shade_backward": [P, i32, P, P, P, P, P, P, P, P, P, P],
         "hm_shade_backward_noalloc": [P, i32, P, P, P, P, P, P, P, P, P],
@@ -167,7 +174,9 @@ def camera_struct(cam) -> Camera:
     return c
 
 
-def lights_struct(lights) -> Lights:
+def lights_struct(lights, shadows=None) -> Lights:
+    """hm_lights of a synth.Lights; shadows: optional list of
+    (synth.ShadowSpec, CUDA int64 tensor holding that light's map)."""
     L = Lights()
     n = lights.dirs.shape[0]
     if n > MAX_LIGHTS:
@@ -178,6 +187,18 @@ def lights_struct(lights) -> Lights:
             L.dir[i][k] = float(lights.dirs[i, k])
             L.radiance[i][k] = float(lights.radiance[i, k])
     L.ambient, L.k_d, L.k_s = lights.ambient, lights.k_d, lights.k_s
+    shadows = list(shadows or [])
+    arr = (ShadowMap * max(len(shadows), 1))()
+    for i, (spec, t) in enumerate(shadows):
+        arr[i].d_map = _dptr(t)
+        arr[i].cam = camera_struct(spec.cam)
+        arr[i].light = int(spec.light)
+        arr[i].sigma = float(spec.sigma)
+        arr[i].bias_m = float(spec.bias_m)
+        arr[i].depth_correction = int(spec.depth_correction)
+    L.n_shadows = len(shadows)
+    L.shadows = ctypes.cast(arr, ctypes.POINTER(ShadowMap)) if shadows else None
+    L._keep = arr                      # the array lives as long as the struct
     return L
 
 
@@ -286,9 +307,18 @@ def render_visibility_multiview(grooms, cams, vis_centers, vis_conses, clear=Tru
                                                _stream_ptr(stream)))
 
 
-def resolve_shade(grooms, cam, lights, filt, vis_center, vis_cons, rgba, stream=None):
+def render_shadow_map(grooms, light_cam, map_center, map_cons, stats=None, stream=None):
+    """Full-detail keys of every groom seen from the light (hm_render_shadow_map);
+    map_cons is the map."""
     arr, n = _handles(grooms)
-    c, L, f = camera_struct(cam), lights_struct(lights), filter_struct(filt)
+    c = camera_struct(light_cam)
+    check(lib().hm_render_shadow_map(arr, n, ctypes.byref(c), _dptr(map_center), _dptr(map_cons), _dptr(stats),
+                                     _stream_ptr(stream)))
+
+
+def resolve_shade(grooms, cam, lights, filt, vis_center, vis_cons, rgba, stream=None, shadows=None):
+    arr, n = _handles(grooms)
+    c, L, f = camera_struct(cam), lights_struct(lights, shadows), filter_struct(filt)
     check(lib().hm_resolve_shade(arr, n, ctypes.byref(c), ctypes.byref(L), ctypes.byref(f), _dptr(vis_center),
                                  _dptr(vis_cons), _dptr(rgba), None, _stream_ptr(stream)))
 
@@ -302,11 +332,11 @@ def render_visibility_msaa(grooms, cam, samples: int, vis_samples, clear=True, s
                                           int(bool(clear)), _dptr(stats), _stream_ptr(stream)))
 
 
-def resolve_msaa(grooms, cam, lights, samples: int, vis_samples, rgba, stream=None):
+def resolve_msaa(grooms, cam, lights, samples: int, vis_samples, rgba, stream=None, shadows=None):
     """Shade every covered sample at its own position; rgba float32 [H*W][4]
     straight alpha (rgb mean over covered samples, alpha covered fraction)."""
     arr, n = _handles(grooms)
-    c, L = camera_struct(cam), lights_struct(lights)
+    c, L = camera_struct(cam), lights_struct(lights, shadows)
     check(lib().hm_resolve_msaa(arr, n, ctypes.byref(c), ctypes.byref(L), int(samples), _dptr(vis_samples),
                                 _dptr(rgba), _stream_ptr(stream)))
 
@@ -316,9 +346,9 @@ def backward_scratch_bytes(width: int, height: int) -> int:
 
 
 def shade_backward(grooms, cam, lights, filt, vis_center, vis_cons, grad_rgba, grad_layer_verts, grad_albedo,
-                   scratch, stream=None):
+                   scratch, stream=None, shadows=None):
     arr, n = _handles(grooms)
-    c, L, f = camera_struct(cam), lights_struct(lights), filter_struct(filt)
+    c, L, f = camera_struct(cam), lights_struct(lights, shadows), filter_struct(filt)
     glv = (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in grad_layer_verts])
     gal = (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in grad_albedo])
     check(lib().hm_shade_backward(arr, n, ctypes.byref(c), ctypes.byref(L), ctypes.byref(f), _dptr(vis_center),
@@ -366,11 +396,11 @@ def stats_dict(stats_tensor):
 
 
 def shade_backward_noalloc(grooms, cam, lights, filt, vis_center, vis_cons, grad_rgba, grad_layer_verts,
-                           grad_albedo, stream=None):
+                           grad_albedo, stream=None, shadows=None):
     """hm_shade_backward_noalloc: the adjoint without caller-allocated
     scratch (frames up to NOALLOC_MAX_PIXELS pixels)."""
     arr, n = _handles(grooms)
-    c, L, f = camera_struct(cam), lights_struct(lights), filter_struct(filt)
+    c, L, f = camera_struct(cam), lights_struct(lights, shadows), filter_struct(filt)
     glv = (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in grad_layer_verts])
     gal = (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in grad_albedo])
     check(lib().hm_shade_backward_noalloc(arr, n, ctypes.byref(c), ctypes.byref(L), ctypes.byref(f),
@@ -401,11 +431,12 @@ class Frame:
         return (self.vis_center.cpu().numpy().view(np.uint64), self.vis_cons.cpu().numpy().view(np.uint64))
 
 
-def render(grooms, scene, frame: Frame, stream=None):
-    """Visibility + resolve of one frame (both on the current stream)."""
+def render(grooms, scene, frame: Frame, stream=None, shadows=None):
+    """Visibility + resolve of one frame (both on the current stream);
+    shadows as for lights_struct."""
     render_visibility(grooms, scene.camera, frame.vis_center, frame.vis_cons, stats=frame.stats, stream=stream)
     resolve_shade(grooms, scene.camera, scene.lights, scene.filt, frame.vis_center, frame.vis_cons, frame.rgba,
-                  stream=stream)
+                  stream=stream, shadows=shadows)
 
 
 def upload_scene(scene, stream=None):

@@ -94,6 +94,18 @@ class Lights:
 
 
 @dataclass
+class ShadowSpec:
+    """A shadow map for one light (Sec. 3.2 depth fix, Sec. 3.4): the light's
+    camera, the hair density sigma (1/m) of the Beer-Lambert falloff, a depth
+    bias (m) and whether the LOD depth correction is applied."""
+    light: int
+    cam: "Camera"
+    sigma: float = 100.0
+    bias_m: float = 0.001
+    depth_correction: int = 1
+
+
+@dataclass
 class FilterParams:
     """Reconstruction-filter knobs (Sec. 3.3).  Defaults follow the paper's
     text where it gives a number: r = 5, sigma_c = 0.9, sigma_iso = 0.4 r,
@@ -271,6 +283,19 @@ def make_lights(dirs, radiance, ambient=AMBIENT) -> Lights:
     return Lights(dirs=np.ascontiguousarray(d.astype(np.float32)),
                   radiance=np.ascontiguousarray(r.astype(np.float32)),
                   ambient=float(np.float32(ambient)))
+
+
+def light_camera(grooms, light_dir, size: int = 512, dist_m: float = 1.0) -> Camera:
+    """A square perspective camera looking at the grooms' AABB centre from
+    dist_m along light_dir (toward the light), its field of view fitted to
+    the AABB, depth range near 0.05 m to just past the far side."""
+    ctr, lo, hi = _aabb_center(grooms)
+    rad = 0.5 * float(np.linalg.norm(hi - lo))
+    d = np.asarray(light_dir, np.float64)
+    d = d / np.linalg.norm(d)
+    up = (0.0, 1.0, 0.0) if abs(d[1]) < 0.9 else (1.0, 0.0, 0.0)
+    fov = 2.0 * math.degrees(math.atan(1.05 * rad / dist_m))
+    return make_camera(ctr + d * dist_m, ctr, fov, size, size, near=NEAR_M, far=dist_m + 2.0 * rad, up=up)
 
 
 def _aabb_center(grooms):

@@ -43,7 +43,9 @@ def _compare(g_gpu, g_ref, what):
     return nrm, rel.max()
 
 
-def _grad_case(scene):
+def _grad_case(scene, shadow=None):
+    """shadow: optional synth.ShadowSpec; its map (rendered once from the
+    unperturbed groom) is held fixed on both sides."""
     from paper_2607_04230_b300 import autograd, hm
     g = scene.grooms[0]
     W, H = scene.camera.width, scene.camera.height
@@ -51,9 +53,16 @@ def _grad_case(scene):
     # GPU: forward + hand-written adjoint
     handle = hm.upload_scene(scene)[0]
     frame = hm.Frame(W, H)
+    shadows = None
+    if shadow is not None:
+        npx = shadow.cam.width * shadow.cam.height
+        mc = torch.empty(npx, dtype=torch.int64, device="cuda")
+        ma = torch.empty(npx, dtype=torch.int64, device="cuda")
+        hm.render_shadow_map([handle], shadow.cam, mc, ma)
+        shadows = [(shadow, ma)]
     lv = torch.from_numpy(g.layer_verts).cuda().requires_grad_(True)
     alb = torch.from_numpy(g.strand_albedo).cuda().requires_grad_(True)
-    rgba = autograd.render(handle, scene, frame, lv, alb)
+    rgba = autograd.render(handle, scene, frame, lv, alb, shadows=shadows)
     t = torch.from_numpy(target).float().cuda()
     loss = torch.sqrt(((rgba.reshape(-1, 4)[:, :3] * rgba.reshape(-1, 4)[:, 3:4] - t) ** 2).sum())
     loss.backward()
@@ -67,8 +76,13 @@ def _grad_case(scene):
     dec = oracle.resolve_decisions(scene.grooms, scene.camera, lods, scene.filt, vc, va)
     lv64 = torch.from_numpy(g.layer_verts.astype(np.float64)).requires_grad_(True)
     alb64 = torch.from_numpy(g.strand_albedo.astype(np.float64)).requires_grad_(True)
-    gt = v64.GroomT(g, lods[0][1], 0, layer_verts=lv64, albedo=alb64)
-    r64, pix = v64.resolve([gt], scene.camera, scene.lights, scene.filt, vc, va, dec)
+    gt = v64.GroomT(g, lods[0][1], 0, layer_verts=lv64, albedo=alb64, lod_n=lods[0][0])
+    maps = None
+    if shadow is not None:
+        maps = [(shadow, oracle.shadow_map(scene.grooms, shadow))]
+        assert_keys_equal(shadows[0][1].cpu().numpy().view(np.uint64), maps[0][1], "shadow map")
+        dec["shadow_texels"] = oracle.centre_shadow_texels(scene.grooms, scene.camera, lods, vc, maps)
+    r64, pix = v64.resolve([gt], scene.camera, scene.lights, scene.filt, vc, va, dec, shadows=maps)
     img = torch.zeros((W * H, 3), dtype=torch.float64).index_put((torch.from_numpy(pix),), r64[:, :3] * r64[:, 3:4])
     l64 = torch.sqrt(((img - torch.from_numpy(target)) ** 2).sum())
     l64.backward()
@@ -101,3 +115,12 @@ def test_gradient_with_baked_ao():
     sc.grooms[0].vert_ao = synth.baked_ao(sc.grooms[0], seed=4)
     sc.lights.ambient = float(np.float32(0.4))
     _grad_case(sc)
+
+
+def test_gradient_with_shadow_map():
+    """A shadow map on light 0 (held fixed): gradients also flow through the
+    receiver's depth in the light's view."""
+    sc = synth.tiny_scene(24, width=96, height=80, num_strands=600, dist_m=0.3, num_layers=5)
+    sc.lod = synth.LodParams(1, 3.0)
+    lcam = synth.light_camera(sc.grooms, sc.lights.dirs[0], size=160, dist_m=0.5)
+    _grad_case(sc, synth.ShadowSpec(light=0, cam=lcam, sigma=200.0, bias_m=0.0005, depth_correction=1))

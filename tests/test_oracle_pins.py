@@ -856,3 +856,109 @@ def test_ao_one_is_no_ao_and_scales_only_the_ambient_term():
     rb, pb, _, _, _, _ = _resolve_scene(sc, filt=off, lights=lights)
     sel = ra[:, 3] > 0
     np.testing.assert_allclose(rb[sel, :3].numpy(), 0.25 * ra[sel, :3].numpy(), rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# shadow maps with the LOD depth correction (Sec. 3.2 "Depth Comparison
+# Artifact Fix", queried by the shading of Sec. 3.4)
+# ---------------------------------------------------------------------------
+
+def _two_strand_shadow_setup(width_m=0.003):
+    """Two straight strands along x (5 collinear, equally spaced layers):
+    A at z = 1 cm, B at z = 0, both at y = 0; a light camera 1 m up the z
+    axis looking down sees A in front of B; the main camera looks down -y so
+    A and B are separate rows of the image."""
+    xs = [-0.04 + 0.02 * k for k in range(5)]
+    layers = [[[x, -0.01, 0.0], [x, 0.01, 0.0], [x, 0.0, 0.02]] for x in xs]
+    g = _groom_from_layers(layers, [[0.25, 0.5], [0.5, 0.0]], 8)      # A: (y, z) = (0, 0.01); B: (0, 0)
+    g.strand_width_m = width_m
+    light = synth.make_camera([0.0, 0.0, 1.0], [0.0, 0.0, 0.0], 10.0, 256, 256, near=0.05, far=2.0)
+    cam = synth.make_camera([0.0, 0.3, 0.005], [0.0, 0.0, 0.005], 40.0, 192, 128, up=(0.0, 0.0, 1.0))
+    return g, light, cam
+
+
+def _shadow_vis_of_centre_keys(g, light, cam, spec, lod_n=None):
+    lods = [oracle.lod(g, cam, synth.LodParams(0))]
+    vc, _, _ = oracle.raster([g], cam, lods)
+    smap = oracle.shadow_map([g], spec)
+    tex = oracle.centre_shadow_texels([g], cam, lods, vc, [(spec, smap)])
+    e, _, sg, seg = v64.key_fields(vc)
+    idx = np.nonzero(~e)[0]
+    W = cam.width
+    num, den = oracle.msaa_decisions([g], cam, lods, 1, vc[None, :])
+    gt = v64.GroomT(g, lods[0][1], 0, lod_n=lod_n)
+    X, _, s = v64.pixel_geometry(gt, sg[idx], seg[idx], num[0][idx], den[0][idx])
+    V = v64.shadow_visibility(gt, X, s, [tex[0][idx]], [(spec, smap)], 1)
+    return V[:, 0].numpy(), sg[idx], tex[0][idx], X, smap
+
+
+def test_shadow_closed_form_two_strands():
+    """The back strand sees exp(-sigma (d - bias)) with d = 1 cm, the depth
+    between the strands along the light's view axis; the front strand is
+    unshadowed (its own depth, within the bias)."""
+    g, light, cam = _two_strand_shadow_setup()
+    spec = synth.ShadowSpec(light=0, cam=light, sigma=100.0, bias_m=0.001, depth_correction=0)
+    V, sg, tex, X, smap = _shadow_vis_of_centre_keys(g, light, cam, spec)
+    a, b = sg == 0, sg == 1
+    assert a.sum() > 40 and b.sum() > 40 and np.all(tex >= 0)
+    np.testing.assert_allclose(V[a], 1.0, rtol=0, atol=1e-12)
+    sig, bias = float(np.float32(100.0)), float(np.float32(0.001))
+    np.testing.assert_allclose(V[b], math.exp(-sig * (0.01 - bias)), rtol=2e-4)
+    # the map holds A's depth wherever B's points look up
+    d24 = (smap[tex[b]] >> np.uint64(40)).astype(np.float64)
+    z_a = (0.99 - float(np.float32(0.05))) / (float(np.float32(2.0)) - float(np.float32(0.05)))
+    assert np.all(np.abs(d24 / 2 ** 24 - z_a) < 3e-7)
+    # the texel column is the floor of the FP64 projection (away from texel edges)
+    M = light.view_proj.astype(np.float64)
+    Xh = np.c_[X.numpy(), np.ones(len(X))]
+    clip = Xh @ M.T
+    xs = (clip[:, 0] / clip[:, 3] + 1.0) * 0.5 * light.width
+    far = np.abs(xs - np.round(xs)) > 1e-3
+    np.testing.assert_array_equal((tex % light.width)[far], np.floor(xs[far]).astype(np.int64))
+
+
+def test_shadow_depth_correction_is_the_log_depth_shift():
+    """With half the bundle's strands drawn (beta = 1/2) the corrected
+    visibility is exp(-sigma exp(log d - Delta)), Delta = -log beta; without
+    the correction it does not depend on the LOD."""
+    g, light, cam = _two_strand_shadow_setup()
+    sig, bias = float(np.float32(100.0)), float(np.float32(0.001))
+    d = 0.01 - bias
+    on = synth.ShadowSpec(light=0, cam=light, sigma=100.0, bias_m=0.001, depth_correction=1)
+    V, sg, _, _, _ = _shadow_vis_of_centre_keys(g, light, cam, on, lod_n=[1])
+    delta = -math.log(0.5)
+    np.testing.assert_allclose(V[sg == 1], math.exp(-sig * math.exp(math.log(d) - delta)), rtol=2e-4)
+    V1, sg1, _, _, _ = _shadow_vis_of_centre_keys(g, light, cam, on, lod_n=[2])
+    np.testing.assert_allclose(V1[sg1 == 1], math.exp(-sig * d), rtol=2e-4)
+    off = synth.ShadowSpec(light=0, cam=light, sigma=100.0, bias_m=0.001, depth_correction=0)
+    V0, sg0, _, _, _ = _shadow_vis_of_centre_keys(g, light, cam, off, lod_n=[1])
+    np.testing.assert_allclose(V0[sg0 == 1], math.exp(-sig * d), rtol=2e-4)
+
+
+def test_shadowed_resolve_zero_density_is_unshadowed_and_light_selective():
+    """sigma = 0 leaves the image unchanged; a map on one light scales only
+    that light's term (with the filter off, where colours pass through)."""
+    sc = synth.tiny_scene(3, width=96, height=80, num_strands=500)
+    sc.lights = synth.make_lights([[1.0, 1.0, 1.0], [-1.0, 0.5, 0.5]], [0.8, 0.4])
+    lods = oracle.lods_for(sc)
+    off = synth.FilterParams(enabled=0)
+    vc, va, _ = oracle.raster(sc.grooms, sc.camera, lods)
+    dec = oracle.resolve_decisions(sc.grooms, sc.camera, lods, off, vc, va)
+    gts = [v64.GroomT(g, l[1], b, lod_n=l[0]) for g, l, b in zip(sc.grooms, lods, oracle.strand_bases(sc.grooms))]
+    base, pix = v64.resolve(gts, sc.camera, sc.lights, off, vc, va, dec)
+    lcam = synth.light_camera(sc.grooms, sc.lights.dirs[0], size=128, dist_m=0.6)
+    for sigma in (0.0, 300.0):
+        spec = synth.ShadowSpec(light=0, cam=lcam, sigma=sigma, bias_m=0.0005)
+        maps = [(spec, oracle.shadow_map(sc.grooms, spec))]
+        dec["shadow_texels"] = oracle.centre_shadow_texels(sc.grooms, sc.camera, lods, vc, maps)
+        out, _ = v64.resolve(gts, sc.camera, sc.lights, off, vc, va, dec, shadows=maps)
+        if sigma == 0.0:
+            np.testing.assert_array_equal(out.numpy(), base.numpy())
+        else:
+            # light 1 alone (light 0 off) is unaffected by light 0's map
+            l1 = synth.make_lights(sc.lights.dirs, np.array([[0, 0, 0], [0.4, 0.4, 0.4]], np.float32))
+            a, _ = v64.resolve(gts, sc.camera, l1, off, vc, va, dec)
+            b, _ = v64.resolve(gts, sc.camera, l1, off, vc, va, dec, shadows=maps)
+            np.testing.assert_allclose(b.numpy(), a.numpy(), rtol=0, atol=1e-15)
+            darker = (out[:, :3] < base[:, :3] - 1e-6).any(1).sum().item()
+            assert darker > 50 and bool((out[:, :3] <= base[:, :3] + 1e-12).all())
