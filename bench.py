@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", choices=["single_1080p", "crowd_4k", "tiny_256", "lod_sweep", "grad_512",
-                                           "stereo_1080p", "single_1080p_ao", "msaa_1080p", "shadow_1080p"],
+                                           "stereo_1080p", "single_1080p_ao", "msaa_1080p", "shadow_1080p",
+                                           "compressed_1080p"],
                     default="single_1080p")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -637,6 +638,63 @@ def run_shadow(args, rank, world, local_rank):
     return 0
 
 
+def run_compressed(args, rank, world, local_rank):
+    """The 1080p groom with the compressed G-buffer payload (Sec. 3.1.2:
+    shading data in the key, resolve reads no hair mesh) against the
+    strand-id payload, phase by phase."""
+    import torch
+    from paper_2607_04230_b300 import build, hm, synth
+    build.build()
+    torch.cuda.set_device(local_rank)
+    sc, cfg = make_scene("single_1080p")
+    grooms = hm.upload_scene(sc)
+    frame = hm.Frame(sc.camera.width, sc.camera.height)
+    table = torch.from_numpy(synth.appearance_table(0)).cuda()
+    g0 = sc.grooms[0]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    res = {}
+    for name in ("id", "compressed"):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        for e in ev:
+            e.record()
+        hm.set_phase_events(ev)
+
+        def step():
+            if name == "id":
+                hm.render(grooms, sc, frame)
+            else:
+                hm.render_visibility_compressed(grooms, sc.camera, frame.vis_center, frame.vis_cons,
+                                                stats=frame.stats)
+                hm.resolve_compressed(sc.camera, sc.lights, sc.filt, table, g0.roughness, g0.tilt,
+                                      frame.vis_center, frame.vis_cons, frame.rgba)
+
+        for _ in range(args.warmup):
+            step()
+        raster, resolve, total = [], [], []
+        for k in range(args.steps):
+            flush.fill_(k)
+            step()
+            torch.cuda.synchronize()
+            raster.append(ev[2].elapsed_time(ev[3]))
+            resolve.append(ev[4].elapsed_time(ev[5]))
+            total.append(ev[0].elapsed_time(ev[5]))
+        res[name] = {"frame": statistics.mean(total), "raster": statistics.mean(raster),
+                     "resolve": statistics.mean(resolve)}
+    hm.set_phase_events(None)
+    hm.get_device_status()
+    if rank != 0:
+        return 0
+    segs = hm.stats_dict(frame.stats)["segments"]
+    ms = res["compressed"]["frame"]
+    line = {"metric": METRIC, "value": segs / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
+            "config": dict(cfg, workload="single groom, 1920x1080, compressed G-buffer payload"),
+            "ms": res, "gpu_launches": 4 * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _gpu_uuid(torch, dev):
     u = str(torch.cuda.get_device_properties(dev).uuid)
     return u if u.startswith("GPU-") else "GPU-" + u
@@ -782,7 +840,7 @@ def main():
         dist.init_process_group("nccl")
     runner = {"crowd_4k": run_crowd, "lod_sweep": run_lod_sweep, "grad_512": run_grad,
               "stereo_1080p": run_stereo, "msaa_1080p": run_msaa,
-              "shadow_1080p": run_shadow}.get(args.workload, run_native)
+              "shadow_1080p": run_shadow, "compressed_1080p": run_compressed}.get(args.workload, run_native)
     try:
         return runner(args, rank, world, local_rank)
     finally:

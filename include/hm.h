@@ -90,6 +90,8 @@ typedef struct {
     float tilt;                    /* cuticle tilt alpha, radians (Sec. 3.4) */
     const float *vert_ao;          /* [L][V] baked ambient occlusion in [0, 1] per hair-mesh
                                       vertex (Sec. 3.4), or NULL for none (1) */
+    const float *vert_uv;          /* [V][2] scalp texture coordinates in [0, 1] (the uv of
+                                      the compressed payload's uvw, Sec. 3.1.2), or NULL (0) */
 } hm_groom_desc;
 
 /* Pinhole camera: clip = view_proj * (x, y, z, 1), row-major; clip.w is the
@@ -230,6 +232,43 @@ hm_status hm_render_visibility_multiview(const hm_groom *grooms, int32_t n, cons
                                          int32_t n_views, uint64_t *const *d_vis_center,
                                          uint64_t *const *d_vis_cons, const uint32_t *const *d_scene_d24,
                                          int32_t clear, hm_frame_stats *d_stats, void *stream);
+
+/* Compressed G-buffer (Sec. 3.1.2): hm_render_visibility, but the low 40
+ * bits of every key hold the shading data instead of the strand-segment id:
+ *   bits 39..32 / 31..24  octahedral code of the segment's chord direction
+ *                         (8 + 8 bits, Cigolle et al. 2014, sign(0) = +1);
+ *   bits 23..18 / 17..12  the root's scalp coordinates u, v (vert_uv), 6 bits;
+ *   bits 11..6            w = (j + t) / (C - 1), the position along the strand;
+ *   bits 5..0             ambient occlusion, rint(ao 62) (63 unused, so no
+ *                         payload equals the all-ones empty marker).
+ * Each code is rint(x scale) clamped, ties to even, from binary32 values in
+ * fixed operation order.  Same coverage, depths and counts as
+ * hm_render_visibility; equal depths are broken by the payload bits.
+ * Arguments and errors as hm_render_visibility. */
+hm_status hm_render_visibility_compressed(const hm_groom *grooms, int32_t n, const hm_camera *cam,
+                                          uint64_t *d_vis_center, uint64_t *d_vis_cons,
+                                          const uint32_t *d_scene_d24, int32_t clear, hm_frame_stats *d_stats,
+                                          void *stream);
+
+/* Shading parameters of the compressed payload: d_table [64][64][4] float
+ * (device), indexed by the (u, v) codes: tip albedo rgb and the root / tip
+ * ratio r; albedo = rgb (r + (1 - r) w / 63).  roughness > 0, tilt finite. */
+typedef struct {
+    const float *d_table;
+    float roughness, tilt;
+} hm_appearance;
+
+/* Resolve of compressed keys (Sec. 3.1.2 "Position reconstruction"): no
+ * hair mesh is read.  Position = the point at depth
+ * w = near + ((d24 + 0.5) 2^-24)(far - near) on the ray through the pixel
+ * centre; tangent = octahedral decode; AO = code / 62; then shading (Sec.
+ * 3.4) and the filter (Sec. 3.3) exactly as hm_resolve_shade.  Shadow maps
+ * are not supported here (their depth correction needs the strand's
+ * bundle): lights->n_shadows must be 0.  d_rgba [H][W][4] straight alpha,
+ * 16-byte aligned. */
+hm_status hm_resolve_compressed(const hm_camera *cam, const hm_lights *lights, const hm_filter_params *filt,
+                                const hm_appearance *appearance, const uint64_t *d_vis_center,
+                                const uint64_t *d_vis_cons, float *d_rgba, void *stream);
 
 /* Shadow map for hm_shadow_map: every groom of grooms[0..n) at full detail
  * (LOD off whatever hm_set_lod holds, no culling: the full geometry set of

@@ -55,7 +55,8 @@ class OrcGroom(ctypes.Structure):
                 ("layer_verts", ctypes.c_void_p), ("faces", ctypes.c_void_p),
                 ("strand_face", ctypes.c_void_p), ("strand_bary", ctypes.c_void_p),
                 ("lod_n", ctypes.c_void_p), ("lod_c", ctypes.c_void_p),
-                ("strand_base", ctypes.c_uint64), ("width_m", ctypes.c_float)]
+                ("strand_base", ctypes.c_uint64), ("width_m", ctypes.c_float),
+                ("vert_ao", ctypes.c_void_p), ("vert_uv", ctypes.c_void_p)]
 
 
 class OrcCamera(ctypes.Structure):
@@ -74,8 +75,12 @@ def lib():
         P = ctypes.c_void_p
         i32, i64, f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float
         _lib.orc_lod.argtypes = [P, P, i32, f32, P, P, P]
-        _lib.orc_raster.argtypes = [P, i32, P, P, P, P, i32]
-        _lib.orc_resolve_decisions.argtypes = [P, i32, P, i32, f32, P, P, P, i64] + [P] * 10 + [i32]
+        _lib.orc_raster.argtypes = [P, i32, P, P, P, P, i32, i32]
+        _lib.orc_resolve_decisions.argtypes = [P, i32, P, i32, f32, P, P, P, i64] + [P] * 10 + [i32, i32]
+        _lib.orc_oct_encode.argtypes = [P]
+        _lib.orc_oct_encode.restype = ctypes.c_uint32
+        _lib.orc_oct_decode.argtypes = [ctypes.c_uint32, P]
+        _lib.orc_unproject.argtypes = [P, f32, f32, f32, P]
         _lib.orc_strand_control_points.argtypes = [P, i64, i32, P]
         _lib.orc_strand_tangents.argtypes = [P, i64, i32, P]
         _lib.orc_project_point.argtypes = [P, P, P, P]
@@ -133,6 +138,11 @@ class _GroomRef:
         s.strand_face, s.strand_bary = self.sf.ctypes.data, self.bary.ctypes.data
         s.lod_n, s.lod_c = self.lod_n.ctypes.data, self.lod_c.ctypes.data
         s.strand_base, s.width_m = base, g.strand_width_m
+        ao, uv = getattr(g, "vert_ao", None), getattr(g, "vert_uv", None)
+        self.ao = None if ao is None else np.ascontiguousarray(ao, np.float32)
+        self.uv = None if uv is None else np.ascontiguousarray(uv, np.float32)
+        s.vert_ao = None if self.ao is None else self.ao.ctypes.data
+        s.vert_uv = None if self.uv is None else self.uv.ctypes.data
         self.s = s
 
 
@@ -160,12 +170,13 @@ def lods_for(scene):
     return [lod(g, scene.camera, scene.lod) for g in scene.grooms]
 
 
-def raster(grooms, cam, lods, prefill_d24=None, nthreads: int = 0):
+def raster(grooms, cam, lods, prefill_d24=None, nthreads: int = 0, compressed: bool = False):
     """Both visibility layers as uint64 [H*W]: (vis_center, vis_cons, counts).
 
     counts = (covered centre pairs, covered conservative pairs), i.e. the
     number of atomicMin operations the method performs (before any
-    early-out)."""
+    early-out).  compressed: the keys carry the compressed G-buffer payload
+    (tangent, uvw, AO) instead of the strand-segment id."""
     arr, refs = _groom_array(grooms, lods)
     npx = cam.width * cam.height
     if prefill_d24 is None:
@@ -175,7 +186,7 @@ def raster(grooms, cam, lods, prefill_d24=None, nthreads: int = 0):
     vis_a = vis_c.copy()
     counts = np.zeros(2, np.int64)
     rc = lib().orc_raster(arr, len(refs), ctypes.byref(camera_struct(cam)), _ptr(vis_c), _ptr(vis_a),
-                          _ptr(counts), int(nthreads))
+                          _ptr(counts), int(bool(compressed)), int(nthreads))
     assert rc == 0
     return vis_c, vis_a, counts
 
@@ -270,10 +281,11 @@ def sample_shadow_texels(grooms, cam, lods, n_samples: int, vis_s, maps, nthread
     return out
 
 
-def resolve_decisions(grooms, cam, lods, filt, vis_c, vis_a, pixels=None, nthreads: int = 0):
+def resolve_decisions(grooms, cam, lods, filt, vis_c, vis_a, pixels=None, nthreads: int = 0,
+                      compressed: bool = False):
     """FP32 decisions per pixel for the G (centre) and A (conservative)
-    references: num/den of the pixel-centre projection, isotropic flag,
-    strip hit counts."""
+    references: num/den of the pixel-centre projection (0 for compressed
+    keys), isotropic flag, strip hit counts."""
     arr, refs = _groom_array(grooms, lods)
     if pixels is None:
         n = cam.width * cam.height
@@ -291,12 +303,29 @@ def resolve_decisions(grooms, cam, lods, filt, vis_c, vis_a, pixels=None, nthrea
         arr, len(refs), ctypes.byref(camera_struct(cam)), int(filt.radius), float(filt.strip_halfwidth),
         _ptr(vc), _ptr(va), pix_ptr, n,
         *[_ptr(out[k]) for k in ("numG", "denG", "numA", "denA", "isoG", "isoA", "HcG", "HaG", "HcA", "HaA")],
-        int(nthreads))
+        int(bool(compressed)), int(nthreads))
     assert rc == 0
     return out
 
 
 # ---- single-step helpers for the pin tests ---------------------------------
+
+def oct_encode(T) -> int:
+    t = np.ascontiguousarray(T, np.float32)
+    return int(lib().orc_oct_encode(_ptr(t)))
+
+
+def oct_decode(code: int) -> np.ndarray:
+    out = np.zeros(3, np.float32)
+    lib().orc_oct_decode(int(code), _ptr(out))
+    return out
+
+
+def unproject(cam, xs: float, ys: float, w: float) -> np.ndarray:
+    out = np.zeros(3, np.float32)
+    lib().orc_unproject(ctypes.byref(camera_struct(cam)), float(xs), float(ys), float(w), _ptr(out))
+    return out
+
 
 def strand_control_points(groom, s: int, C: int) -> np.ndarray:
     ref = _GroomRef(groom, np.zeros(groom.num_faces, np.int32), np.zeros(groom.num_faces, np.int32), 0)

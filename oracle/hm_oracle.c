@@ -42,6 +42,8 @@ typedef struct {
     const int32_t *lod_c;          /* [F] control points per strand of the bundle */
     uint64_t strand_base;          /* global strand id of local strand 0 */
     float width_m;                 /* strand width */
+    const float *vert_ao;          /* [L][V] baked ambient occlusion, or NULL (= 1) */
+    const float *vert_uv;          /* [V][2] scalp texture coordinates, or NULL (= 0) */
 } orc_groom;
 
 typedef struct {
@@ -336,18 +338,129 @@ typedef struct {
     int32_t hc;
     int32_t valid;
     uint64_t id;
+    /* compressed payload only: bits 39..12 (tangent, u, v), segment index,
+     * C - 1 and the AO at both ends */
+    uint64_t cgb_hi;
+    int32_t j, cm1;
+    float aoA, aoB;
 } seg_t;
+
+/* ---------------------------------------------------------------------------
+ * compressed G-buffer payload (Sec. 3.1.2: uvw styling coordinates instead
+ * of shading parameters, an octahedral tangent, every value but depth
+ * quantized to 8 or 6 bits, all of it next to the 24-bit depth in 64 bits)
+ *
+ * Readings (the inset with the bit layout is lost):
+ *   bits 39..32 / 31..24  octahedral tangent x / y, 8 bits each;
+ *   bits 23..18 / 17..12  the root's scalp texture coordinates u / v, 6 bits;
+ *   bits 11..6            w = (j + t) / (C - 1), the position along the strand;
+ *   bits 5..0             ambient occlusion, 0..62 (63 is never written, so a
+ *                         payload is never all ones, the empty marker).
+ * The tangent is the segment's chord p_{j+1} - p_j, encoded once per
+ * segment; AO is the control points' AO (Hermite along the strand, as the
+ * positions) interpolated linearly in t.  Each quantization is
+ * rint(x * scale) clamped, ties to even.  Octahedral encoding after Cigolle
+ * et al. 2014 (sign(0) = +1).
+ * ------------------------------------------------------------------------- */
+static int32_t quantize(float x, float scale, int32_t hi) {
+    float q = rintf(x * scale);
+    if (!(q >= 0.0f)) return 0;
+    if (q >= (float)hi) return hi;
+    return (int32_t)q;
+}
+
+static float sgn1(float v) { return v >= 0.0f ? 1.0f : -1.0f; }
+
+static uint32_t oct_encode(f3 T) {
+    float s = (fabsf(T.x) + fabsf(T.y)) + fabsf(T.z);
+    float ox = 0.0f, oy = 0.0f;
+    if (s > 0.0f) { ox = T.x / s; oy = T.y / s; }
+    if (T.z < 0.0f) {
+        float nx = (1.0f - fabsf(oy)) * sgn1(ox);
+        float ny = (1.0f - fabsf(ox)) * sgn1(oy);
+        ox = nx; oy = ny;
+    }
+    uint32_t cx = (uint32_t)quantize((ox * 0.5f) + 0.5f, 255.0f, 255);
+    uint32_t cy = (uint32_t)quantize((oy * 0.5f) + 0.5f, 255.0f, 255);
+    return (cx << 8) | cy;
+}
+
+static f3 oct_decode(uint32_t code) {
+    float ox = (((float)(code >> 8) / 255.0f) * 2.0f) - 1.0f;
+    float oy = (((float)(code & 255u) / 255.0f) * 2.0f) - 1.0f;
+    float z = (1.0f - fabsf(ox)) - fabsf(oy);
+    if (z < 0.0f) {
+        float nx = (1.0f - fabsf(oy)) * sgn1(ox);
+        float ny = (1.0f - fabsf(ox)) * sgn1(oy);
+        ox = nx; oy = ny;
+    }
+    return normalize3(mk(ox, oy, z));
+}
+
+/* AO of layer point k and of control point j (cubic Hermite over the layer
+ * values with finite-difference slopes, one-sided at root and tip). */
+static float layer_ao_f32(const orc_groom *g, int64_t s, int k) {
+    if (!g->vert_ao) return 1.0f;
+    const int32_t *f = &g->faces[3 * g->strand_face[s]];
+    float b1 = g->strand_bary[2 * s], b2 = g->strand_bary[2 * s + 1];
+    float b0 = (1.0f - b1) - b2;
+    const float *row = &g->vert_ao[(int64_t)k * g->V];
+    return ((b0 * row[f[0]]) + (b1 * row[f[1]])) + (b2 * row[f[2]]);
+}
+
+static float control_ao_f32(const orc_groom *g, int64_t s, int C, int j) {
+    int L = g->L;
+    int x = j * (L - 1);
+    int k = x / (C - 1);
+    if (k > L - 2) k = L - 2;
+    float t = (float)(x - k * (C - 1)) / (float)(C - 1);
+    float a0 = layer_ao_f32(g, s, k), a1 = layer_ao_f32(g, s, k + 1);
+    float am = k > 0 ? layer_ao_f32(g, s, k - 1) : a0;
+    float a2 = k + 2 <= L - 1 ? layer_ao_f32(g, s, k + 2) : a1;
+    float m0 = k == 0 ? a1 - a0 : 0.5f * (a1 - am);
+    float m1 = k + 1 == L - 1 ? a1 - a0 : 0.5f * (a2 - a0);
+    float t2 = t * t, t3 = t2 * t;
+    float h00 = ((2.0f * t3) - (3.0f * t2)) + 1.0f, h10 = (t3 - (2.0f * t2)) + t;
+    float h01 = (3.0f * t2) - (2.0f * t3), h11 = t3 - t2;
+    return (((h00 * a0) + (h10 * m0)) + (h01 * a1)) + (h11 * m1);
+}
+
+static void root_uv(const orc_groom *g, int64_t s, float *u, float *v) {
+    *u = *v = 0.0f;
+    if (!g->vert_uv) return;
+    const int32_t *f = &g->faces[3 * g->strand_face[s]];
+    float b1 = g->strand_bary[2 * s], b2 = g->strand_bary[2 * s + 1];
+    float b0 = (1.0f - b1) - b2;
+    const float *uv = g->vert_uv;
+    *u = ((b0 * uv[2 * f[0]]) + (b1 * uv[2 * f[1]])) + (b2 * uv[2 * f[2]]);
+    *v = ((b0 * uv[2 * f[0] + 1]) + (b1 * uv[2 * f[1] + 1])) + (b2 * uv[2 * f[2] + 1]);
+}
+
+/* Low 40 bits of the compressed key at projection parameter t. */
+static uint64_t cgb_payload(const seg_t *q, float t) {
+    uint32_t cw = (uint32_t)quantize(((float)q->j + t) / (float)q->cm1, 63.0f, 63);
+    uint32_t ca = (uint32_t)quantize(q->aoA + ((q->aoB - q->aoA) * t), 62.0f, 62);
+    return q->cgb_hi | ((uint64_t)cw << 6) | (uint64_t)ca;
+}
 
 /* Per strand: layer points, base tangents, C control points, projection;
  * segment j joins control points j and j+1 and is dropped when either end
  * is in front of the near plane. */
 static void strand_segments(const orc_groom *g, const orc_camera *cam, int64_t s, int C, seg_t *out) {
-    f3 P[64], mh[64];
+    f3 P[64], mh[64], cp[128];
     proj_t pr[128];
+    float ao[128];
     strand_layer_points(g, s, P);
     layer_tangents(P, g->L, mh);
-    for (int j = 0; j < C; ++j) pr[j] = project(cam, control_point(P, mh, g->L, C, j));
+    for (int j = 0; j < C; ++j) {
+        cp[j] = control_point(P, mh, g->L, C, j);
+        pr[j] = project(cam, cp[j]);
+        ao[j] = control_ao_f32(g, s, C, j);
+    }
     uint64_t sg = g->strand_base + (uint64_t)s;
+    float u, v;
+    root_uv(g, s, &u, &v);
+    uint64_t uv_bits = ((uint64_t)quantize(u, 63.0f, 63) << 18) | ((uint64_t)quantize(v, 63.0f, 63) << 12);
     for (int j = 0; j + 1 < C; ++j) {
         seg_t *q = &out[j];
         q->valid = pr[j].valid && pr[j + 1].valid;
@@ -355,6 +468,11 @@ static void strand_segments(const orc_groom *g, const orc_camera *cam, int64_t s
         q->zA = pr[j].z; q->zB = pr[j + 1].z;
         q->hc = q->valid ? center_halfwidth(cam, g->width_m, pr[j].w, pr[j + 1].w) : 0;
         q->id = (sg << 7) | (uint64_t)j;
+        q->cgb_hi = ((uint64_t)oct_encode(normalize3(sub3(cp[j + 1], cp[j]))) << 24) | uv_bits;
+        q->j = j;
+        q->cm1 = C - 1;
+        q->aoA = ao[j];
+        q->aoB = ao[j + 1];
     }
 }
 
@@ -367,7 +485,7 @@ static int64_t floor_div256(int64_t v) { return v >= 0 ? v / 256 : -((-v + 255) 
  * one thread; min is order independent.  counts[0] += covered (pixel,
  * centre) pairs, counts[1] += covered (pixel, conservative) pairs. */
 int orc_raster(const orc_groom *grooms, int32_t n_grooms, const orc_camera *cam,
-               uint64_t *vis_c, uint64_t *vis_a, int64_t *counts, int32_t nthreads) {
+               uint64_t *vis_c, uint64_t *vis_a, int64_t *counts, int32_t compressed, int32_t nthreads) {
     int64_t total = 0;
     int64_t *gseg = (int64_t *)malloc(sizeof(int64_t) * (n_grooms + 1));
     int64_t **boff = (int64_t **)calloc(n_grooms, sizeof(int64_t *));
@@ -431,7 +549,8 @@ int orc_raster(const orc_groom *grooms, int32_t n_grooms, const orc_camera *cam,
                     int cc = segment_covers(sg->XA, sg->YA, sg->XB, sg->YB, cx, cy, sg->hc);
                     if (!ca && !cc) continue;
                     float t = segment_t(sg->XA, sg->YA, sg->XB, sg->YB, cx, cy, 0, 0);
-                    uint64_t key = ((uint64_t)depth24(sg->zA, sg->zB, t) << 40) | sg->id;
+                    uint64_t key = ((uint64_t)depth24(sg->zA, sg->zB, t) << 40) |
+                                   (compressed ? cgb_payload(sg, t) : sg->id);
                     int64_t px = m * W + i;
                     if (ca) { ++cnt_a; if (key < vis_a[px]) vis_a[px] = key; }
                     if (cc) { ++cnt_c; if (key < vis_c[px]) vis_c[px] = key; }
@@ -531,6 +650,45 @@ static decode_t decode_key(const orc_groom *gs, int32_t n, const orc_camera *cam
     return decode_key_at(gs, n, cam, key, 256 * px + 128, 256 * py + 128);
 }
 
+/* Compressed payload decode (Sec. 3.1.2 position reconstruction): the
+ * position is the point at the key's depth on the ray through the pixel
+ * centre, taken at the middle of the 24-bit depth bin,
+ * w = near + ((d24 + 0.5) 2^-24) (far - near), solved from the projection's
+ * rows (M0 - xn M3) X = xn M33 - M03, (M1 - yn M3) X = yn M33 - M13,
+ * M3 X = w - M33 by Cramer's rule; the tangent is the octahedral decode. */
+static f3 cross3(f3 a, f3 b) {
+    return mk((a.y * b.z) - (a.z * b.y), (a.z * b.x) - (a.x * b.z), (a.x * b.y) - (a.y * b.x));
+}
+
+static f3 unproject(const orc_camera *cam, float xs, float ys, float w) {
+    const float *m = cam->m;
+    float xn = ((2.0f * xs) / (float)cam->width) - 1.0f;
+    float yn = 1.0f - ((2.0f * ys) / (float)cam->height);
+    f3 ra = mk(m[0] - (xn * m[12]), m[1] - (xn * m[13]), m[2] - (xn * m[14]));
+    f3 rb = mk(m[4] - (yn * m[12]), m[5] - (yn * m[13]), m[6] - (yn * m[14]));
+    f3 rc = mk(m[12], m[13], m[14]);
+    float ka = (xn * m[15]) - m[3];
+    float kb = (yn * m[15]) - m[7];
+    float kc = w - m[15];
+    f3 bc = cross3(rb, rc), ca = cross3(rc, ra), ab = cross3(ra, rb);
+    float det = ((ra.x * bc.x) + (ra.y * bc.y)) + (ra.z * bc.z);
+    return mk((((ka * bc.x) + (kb * ca.x)) + (kc * ab.x)) / det,
+              (((ka * bc.y) + (kb * ca.y)) + (kc * ab.y)) / det,
+              (((ka * bc.z) + (kb * ca.z)) + (kc * ab.z)) / det);
+}
+
+static decode_t decode_cgb(const orc_camera *cam, uint64_t key, int64_t px, int64_t py) {
+    decode_t d;
+    memset(&d, 0, sizeof d);
+    float z = ((float)(uint32_t)(key >> 40) + 0.5f) * 5.9604644775390625e-8f;
+    float w = cam->near + (z * (cam->far - cam->near));
+    d.X = unproject(cam, (float)px + 0.5f, (float)py + 0.5f, w);
+    d.T = oct_decode((uint32_t)((key >> 24) & 0xFFFFu));
+    d.iso = screen_tangent(cam, d.X, d.T, &d.tsx, &d.tsy);
+    d.ok = 1;
+    return d;
+}
+
 /* Strip membership of window offset (dx, dy) for a unit screen tangent:
  * d_par = d . Ts, e = d - d_par Ts, in iff |e|^2 <= hw^2 (Sec. 3.3.3).
  * Reading: with a degenerate tangent the strip is the pixel itself. */
@@ -553,7 +711,7 @@ int orc_resolve_decisions(const orc_groom *grooms, int32_t n_grooms, const orc_c
                           const int64_t *pixels, int64_t n_pixels,
                           int64_t *numG, int64_t *denG, int64_t *numA, int64_t *denA,
                           uint8_t *isoG, uint8_t *isoA, int32_t *HcG, int32_t *HaG,
-                          int32_t *HcA, int32_t *HaA, int32_t nthreads) {
+                          int32_t *HcA, int32_t *HaA, int32_t compressed, int32_t nthreads) {
     const int W = cam->width, H = cam->height;
     const float hw2 = strip_hw * strip_hw;
     int64_t npx = pixels ? n_pixels : (int64_t)W * H;
@@ -570,7 +728,7 @@ int orc_resolve_decisions(const orc_groom *grooms, int32_t n_grooms, const orc_c
         for (int layer = 0; layer < 2; ++layer) {
             uint64_t key = layer == 0 ? vis_c[p] : vis_a[p];
             if (key_empty(key)) continue;
-            decode_t d = decode_key(grooms, n_grooms, cam, key, px, py);
+            decode_t d = compressed ? decode_cgb(cam, key, px, py) : decode_key(grooms, n_grooms, cam, key, px, py);
             if (!d.ok) continue;
             int hc = 0, ha = 0;
             for (int dy = -radius; dy <= radius; ++dy) {
@@ -746,6 +904,18 @@ int orc_shadow_texels(const orc_groom *grooms, int32_t n_grooms, const orc_camer
         texel[q] = ty * light->width + tx;
     }
     return 0;
+}
+
+uint32_t orc_oct_encode(const float *T) { return oct_encode(mk(T[0], T[1], T[2])); }
+
+void orc_oct_decode(uint32_t code, float *T) {
+    f3 v = oct_decode(code);
+    T[0] = v.x; T[1] = v.y; T[2] = v.z;
+}
+
+void orc_unproject(const orc_camera *cam, float xs, float ys, float w, float *X) {
+    f3 v = unproject(cam, xs, ys, w);
+    X[0] = v.x; X[1] = v.y; X[2] = v.z;
 }
 
 int orc_strand_control_points(const orc_groom *g, int64_t s, int32_t C, float *out) {

@@ -306,10 +306,8 @@ def resolve(gts, cam, lights, filt, vis_c, vis_a, dec, pixels=None, shadows=None
     None), Sec. 3.3-3.4.  Returns (rgba, pixel_index).  shadows: optional
     list of (spec, map keys) with dec["shadow_texels"] the per-map texel of
     every centre key (oracle.centre_shadow_texels)."""
-    W, H = cam.width, cam.height
     eG, dG, sgG, segG = key_fields(vis_c)
     eA, dA, sgA, segA = key_fields(vis_a)
-    npx = W * H
     # shading of every centre-sample pixel (the deferred shading pass)
     cen = np.nonzero(~eG)[0]
     Xc, Tc, idxs, albs = _geometry_all(gts, sgG[cen], segG[cen], dec_full(dec, "numG", cen),
@@ -325,6 +323,93 @@ def resolve(gts, cam, lights, filt, vis_c, vis_a, dec, pixels=None, shadows=None
                                     lights.dirs.shape[0])
         Ccen = Ccen.index_put((idx,), shade(Xc[idx], Tc[idx], gt.albedo[s], cam, lights,
                                             gt.roughness, gt.tilt, ao, vis))
+
+    def geom_a(pix):
+        XA, TA, _, _ = _geometry_all(gts, sgA[pix], segA[pix], dec["numA"][pix], dec["denA"][pix])
+        return XA, TA
+
+    return _filter(cam, filt, vis_c, vis_a, dec, pixels, cen, Xc, Tc, Ccen, geom_a)
+
+
+# ---------------------------------------------------------------------------
+# compressed G-buffer payload (Sec. 3.1.2): shading from the key alone
+# ---------------------------------------------------------------------------
+
+def cgb_fields(vis):
+    """(empty, d24, tangent code, u, v, w, ao codes) of compressed keys."""
+    vis = np.asarray(vis, np.uint64)
+    empty = (vis & PAYLOAD_MASK) == PAYLOAD_MASK
+    f = lambda sh, m: ((vis >> np.uint64(sh)) & np.uint64(m)).astype(np.int64)
+    return empty, f(40, 0xFFFFFF), f(24, 0xFFFF), f(18, 63), f(12, 63), f(6, 63), f(0, 63)
+
+
+def cgb_position(cam, pixels, d24):
+    """Position at the middle of the key's depth bin on the ray through the
+    pixel centre (linear view depth w = near + z (far - near))."""
+    W = cam.width
+    near, far = float(np.float32(cam.near)), float(np.float32(cam.far))
+    w = near + (d24.astype(np.float64) + 0.5) / float(1 << 24) * (far - near)
+    xs = (pixels % W).astype(np.float64) + 0.5
+    ys = (pixels // W).astype(np.float64) + 0.5
+    xn = 2.0 * xs / cam.width - 1.0
+    yn = 1.0 - 2.0 * ys / cam.height
+    M = np.asarray(cam.view_proj, np.float64)
+    # rows: (M0 - xn M3) X = xn M33 - M03, (M1 - yn M3) X = yn M33 - M13, M3 X = w - M33
+    A = np.stack([M[0, :3][None, :] - xn[:, None] * M[3, :3][None, :],
+                  M[1, :3][None, :] - yn[:, None] * M[3, :3][None, :],
+                  np.broadcast_to(M[3, :3], (len(w), 3))], 1)
+    b = np.stack([xn * M[3, 3] - M[0, 3], yn * M[3, 3] - M[1, 3], w - M[3, 3]], 1)
+    return torch.from_numpy(np.linalg.solve(A, b[:, :, None])[:, :, 0] if len(w) else np.zeros((0, 3)))
+
+
+def oct_decode64(code):
+    """Octahedral unit vector decode (Cigolle et al. 2014) of the 8+8-bit
+    codes, in float64."""
+    ox = (code >> 8).astype(np.float64) / 255.0 * 2.0 - 1.0
+    oy = (code & 255).astype(np.float64) / 255.0 * 2.0 - 1.0
+    z = 1.0 - np.abs(ox) - np.abs(oy)
+    sx = np.where(ox >= 0, 1.0, -1.0)
+    sy = np.where(oy >= 0, 1.0, -1.0)
+    fx = np.where(z < 0, (1.0 - np.abs(oy)) * sx, ox)
+    fy = np.where(z < 0, (1.0 - np.abs(ox)) * sy, oy)
+    return _normalize(torch.from_numpy(np.stack([fx, fy, z], 1)))
+
+
+def cgb_albedo(table, cu, cv, cw):
+    """Appearance query at the quantized uvw: the table's (u, v) texel holds
+    the tip albedo (rgb) and the root / tip ratio r; albedo = rgb (r + (1 - r) w)."""
+    t = torch.from_numpy(np.asarray(table, np.float64).reshape(64 * 64, 4)[cu * 64 + cv])
+    w = torch.from_numpy(cw.astype(np.float64) / 63.0)[:, None]
+    return t[:, :3] * (t[:, 3:4] + (1.0 - t[:, 3:4]) * w)
+
+
+def resolve_cgb(cam, lights, filt, vis_c, vis_a, dec, table, roughness, tilt, pixels=None):
+    """resolve() for keys carrying the compressed payload: position from
+    depth, tangent from the octahedral code, shading parameters from the
+    appearance table at (u, v, w), AO from its 6-bit code."""
+    eG, dG, tG, uG, vG, wG, aG = cgb_fields(vis_c)
+    eA, dA, tA, _, _, _, _ = cgb_fields(vis_a)
+    cen = np.nonzero(~eG)[0]
+    Xc = cgb_position(cam, cen, dG[cen])
+    Tc = oct_decode64(tG[cen])
+    alb = cgb_albedo(table, uG[cen], vG[cen], wG[cen])
+    ao = torch.from_numpy(aG[cen].astype(np.float64) / 62.0)[:, None]
+    Ccen = shade(Xc, Tc, alb, cam, lights, float(np.float32(roughness)), float(np.float32(tilt)), ao)
+
+    def geom_a(pix):
+        return cgb_position(cam, pix, dA[pix]), oct_decode64(tA[pix])
+
+    return _filter(cam, filt, vis_c, vis_a, dec, pixels, cen, Xc, Tc, Ccen, geom_a)
+
+
+def _filter(cam, filt, vis_c, vis_a, dec, pixels, cen, Xc, Tc, Ccen, geom_a):
+    """Strand connection, elliptical bilateral filter and alpha (Sec. 3.3)
+    over the shaded centre pixels cen (colours Ccen, geometry Xc, Tc);
+    geom_a(pixels) gives the conservative keys' geometry."""
+    W, H = cam.width, cam.height
+    eG, dG, _, _ = key_fields(vis_c)
+    eA, dA, _, _ = key_fields(vis_a)
+    npx = W * H
     Cimg = torch.zeros((npx, 3), dtype=torch.float64).index_put((torch.from_numpy(cen),), Ccen)
 
     if pixels is None:
@@ -345,8 +430,7 @@ def resolve(gts, cam, lights, filt, vis_c, vis_a, dec, pixels=None, shadows=None
         TsG[torch.from_numpy(np.nonzero(isc)[0])] = screen_tangent(Xc[cpos], Tc[cpos], cam)
     rej, mis = depth_thresholds(cam, filt)
     aidx = np.nonzero(isa)[0]
-    XA, TA, _, _ = _geometry_all(gts, sgA[pixels[aidx]], segA[pixels[aidx]],
-                                 dec_at(dec, "numA", pixels, aidx), dec_at(dec, "denA", pixels, aidx))
+    XA, TA = geom_a(pixels[aidx])
     TsA = torch.zeros((pixels.size, 2), dtype=torch.float64)
     if aidx.size:
         TsA[torch.from_numpy(aidx)] = screen_tangent(XA, TA, cam)

@@ -35,6 +35,7 @@ struct hm_groom_s {
     uint4 *d_lod_full;
     uint32_t *d_batch_map_full;
     uint32_t *d_counters_full;
+    float2 *d_uv;            // scalp texture coordinates, or null
 };
 
 namespace {
@@ -139,6 +140,7 @@ hm_status build_table(const hm_groom *grooms, int32_t n, hm::CallTable &tab) {
         d.lod_lambda = g->lod.lambda;
         d.lod_enabled = g->lod.enabled;
         d.has_ao = g->has_ao;
+        d.uv = g->d_uv;
         base += (uint64_t)g->S;
     }
     if (base > (1ull << 33) - 2) return fail(HM_ERR_CAPACITY, "strand ids exceed 33 bits");
@@ -183,6 +185,7 @@ void free_groom(hm_groom g) {
     cudaFree(g->d_lod_full);
     cudaFree(g->d_batch_map_full);
     cudaFree(g->d_counters_full);
+    cudaFree(g->d_uv);
     delete g;
 }
 
@@ -259,6 +262,10 @@ hm_status hm_create_groom(const hm_groom_desc *d, void *stream, hm_groom *out) {
         for (int64_t i = 0; i < (int64_t)L * V; ++i)
             if (!(d->vert_ao[i] >= 0.0f && d->vert_ao[i] <= 1.0f))
                 return fail(HM_ERR_INVALID_ARG, "vert_ao outside [0, 1]");
+    if (d->vert_uv)
+        for (int64_t i = 0; i < 2ll * V; ++i)
+            if (!(d->vert_uv[i] >= 0.0f && d->vert_uv[i] <= 1.0f))
+                return fail(HM_ERR_INVALID_ARG, "vert_uv outside [0, 1]");
     if (!(d->strand_width_m > 0.0f) || !std::isfinite(d->strand_width_m) || !(d->roughness > 0.0f) ||
         !std::isfinite(d->tilt))
         return fail(HM_ERR_INVALID_ARG, "strand width / roughness must be positive, tilt finite");
@@ -328,6 +335,7 @@ hm_status hm_create_groom(const hm_groom_desc *d, void *stream, hm_groom *out) {
     HM_ALLOC(g->d_lod_full, (size_t)F, "alloc shadow-pass lod")
     HM_ALLOC(g->d_batch_map_full, max_batches, "alloc shadow-pass batch map")
     HM_ALLOC(g->d_counters_full, (size_t)hm::kCtrWords, "alloc shadow-pass counters")
+    if (d->vert_uv) HM_ALLOC(g->d_uv, (size_t)V, "alloc vert_uv")
 #undef HM_ALLOC
     if (st != HM_OK) {
         free_groom(g);
@@ -344,6 +352,7 @@ hm_status hm_create_groom(const hm_groom_desc *d, void *stream, hm_groom *out) {
     cp(g->d_bary, d->strand_bary, (size_t)S * sizeof(float2));
     cp(g->d_albedo, alb.data(), (size_t)S * sizeof(float4));
     cp(g->d_delta, d->bundle_delta, (size_t)F * sizeof(float));
+    if (d->vert_uv) cp(g->d_uv, d->vert_uv, (size_t)V * sizeof(float2));
     if (e == cudaSuccess) e = cudaMemsetAsync(g->d_counters, 0, hm::kCtrWords * sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->d_counters_full, 0, hm::kCtrWords * sizeof(uint32_t), s);
     // LOD state starts at full detail so a resolve before any render decodes safely
@@ -399,7 +408,7 @@ hm_status hm_render_visibility(const hm_groom *grooms, int32_t n, const hm_camer
 static hm_status render_views(const hm_groom *grooms, int32_t n, int32_t first, int32_t count, const hm_camera *cams,
                                int32_t n_views, uint64_t *const *d_vis_center, uint64_t *const *d_vis_cons,
                                const uint32_t *const *d_scene_d24, int32_t clear, hm_frame_stats *d_stats,
-                               void *stream) {
+                               void *stream, bool compressed = false) {
     if (!cams || n_views < 1 || n_views > HM_MAX_VIEWS) return fail(HM_ERR_INVALID_ARG, "view count out of range");
     if (!d_vis_center || !d_vis_cons) return fail(HM_ERR_INVALID_ARG, "visibility buffer array is NULL");
     hm_status st;
@@ -443,7 +452,7 @@ static hm_status render_views(const hm_groom *grooms, int32_t n, int32_t first, 
     HM_CUDA(hm::launch_lod(tab, views.cam[0], d_stats, s), "lod");
     phase(2, s);
     HM_CUDA(hm::launch_raster(tab, views, g_tuning.raster_precheck != 0, g_tuning.raster_min_blocks,
-                              g_tuning.raster_ctas_per_sm, d_stats, s),
+                              g_tuning.raster_ctas_per_sm, d_stats, s, compressed),
             "raster");
     phase(3, s);
     return HM_OK;
@@ -542,6 +551,14 @@ hm_status hm_render_visibility_range(const hm_groom *grooms, int32_t n, int32_t 
                         d_scene_d24 ? &d_scene_d24 : nullptr, clear, d_stats, stream);
 }
 
+hm_status hm_render_visibility_compressed(const hm_groom *grooms, int32_t n, const hm_camera *cam,
+                                          uint64_t *d_vis_center, uint64_t *d_vis_cons,
+                                          const uint32_t *d_scene_d24, int32_t clear, hm_frame_stats *d_stats,
+                                          void *stream) {
+    return render_views(grooms, n, 0, n, cam, 1, &d_vis_center, &d_vis_cons, d_scene_d24 ? &d_scene_d24 : nullptr,
+                        clear, d_stats, stream, true);
+}
+
 static hm_status filter_dev(const hm_filter_params *f, const hm_camera *cam, hm::FilterDev &fd) {
     if (!f) return fail(HM_ERR_INVALID_ARG, "filter params are NULL");
     std::memset(&fd, 0, sizeof fd);
@@ -627,6 +644,38 @@ hm_status hm_resolve_shade(const hm_groom *grooms, int32_t n, const hm_camera *c
     HM_CUDA(hm::launch_resolve(tab, cam_dev(cam), ld, fd, d_vis_center, d_vis_cons, d_rgba, sw,
                                g_tuning.resolve_tile_h, static_cast<cudaStream_t>(stream)),
             "resolve");
+    phase(5, static_cast<cudaStream_t>(stream));
+    return HM_OK;
+}
+
+hm_status hm_resolve_compressed(const hm_camera *cam, const hm_lights *lights, const hm_filter_params *filt,
+                                const hm_appearance *appearance, const uint64_t *d_vis_center,
+                                const uint64_t *d_vis_cons, float *d_rgba, void *stream) {
+    hm_status st = check_camera(cam);
+    if (st != HM_OK) return st;
+    if (!d_vis_center || !d_vis_cons || !d_rgba) return fail(HM_ERR_INVALID_ARG, "buffer is NULL");
+    if ((reinterpret_cast<uintptr_t>(d_rgba) & 15) || (reinterpret_cast<uintptr_t>(d_vis_center) & 7) ||
+        (reinterpret_cast<uintptr_t>(d_vis_cons) & 7))
+        return fail(HM_ERR_INVALID_ARG, "misaligned buffer");
+    if (!appearance || !appearance->d_table || (reinterpret_cast<uintptr_t>(appearance->d_table) & 15))
+        return fail(HM_ERR_INVALID_ARG, "appearance table NULL or not 16-byte aligned");
+    if (!(appearance->roughness > 0.0f) || !std::isfinite(appearance->roughness) || !std::isfinite(appearance->tilt))
+        return fail(HM_ERR_INVALID_ARG, "appearance roughness must be positive, tilt finite");
+    hm::LightsDev ld;
+    hm::FilterDev fd;
+    if ((st = lights_dev(lights, ld)) != HM_OK) return st;
+    if (ld.n_shadow != 0) return fail(HM_ERR_INVALID_ARG, "shadow maps need the strand-id payload");
+    if ((st = filter_dev(filt, cam, fd)) != HM_OK) return st;
+    hm::CallTable tab;
+    std::memset(&tab, 0, sizeof tab);
+    const hm::CgbDev cg{reinterpret_cast<const float4 *>(appearance->d_table), appearance->roughness,
+                        appearance->tilt};
+    uint32_t *sw = status_word();
+    if (!sw) return fail(HM_ERR_CUDA, "device status word unavailable");
+    phase(4, static_cast<cudaStream_t>(stream));
+    HM_CUDA(hm::launch_resolve(tab, cam_dev(cam), ld, fd, d_vis_center, d_vis_cons, d_rgba, sw,
+                               g_tuning.resolve_tile_h, static_cast<cudaStream_t>(stream), &cg),
+            "resolve compressed");
     phase(5, static_cast<cudaStream_t>(stream));
     return HM_OK;
 }

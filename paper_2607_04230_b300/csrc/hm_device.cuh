@@ -46,6 +46,7 @@ struct GroomDev {
     float width_m, roughness, tilt, lod_lambda;
     int32_t lod_enabled;
     int32_t has_ao;          // layer vertices carry baked ambient occlusion in w
+    const float2 *uv;        // [V] scalp texture coordinates, or null (compressed payload)
 };
 
 struct CallTable {
@@ -461,6 +462,146 @@ __device__ __forceinline__ Decoded decode_key_at(const CallTable &tab, const uin
     d.j = j;
     d.C = C;
     d.ok = true;
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// compressed G-buffer payload (Sec. 3.1.2: uvw styling coordinates, an
+// octahedral tangent and 8/6-bit quantization beside the 24-bit depth)
+//
+// Low 40 bits of a compressed key: tangent code x (39..32) and y (31..24),
+// the root's scalp coordinates u (23..18) and v (17..12), w = (j + t)/(C-1)
+// along the strand (11..6), ambient occlusion 0..62 (5..0; 63 is never used,
+// so no payload is all ones).  Every quantization is rint(x scale) clamped;
+// the tangent is the segment's chord, octahedral-encoded (Cigolle et al.
+// 2014, sign(0) = +1) once per segment; AO is the control points' AO
+// interpolated linearly along the segment.  All of it in fixed binary32
+// operation order, so the codes are reproducible bit for bit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t quantize(float x, float scale, uint32_t hi) {
+    const float q = rintf(fmul(x, scale));
+    if (!(q >= 0.0f)) return 0u;
+    if (q >= __uint2float_rn(hi)) return hi;
+    return (uint32_t)q;
+}
+
+__device__ __forceinline__ float sgn1(float v) { return v >= 0.0f ? 1.0f : -1.0f; }
+
+__device__ __forceinline__ uint32_t oct_encode(float3 T) {
+    const float s = fadd(fadd(fabsf(T.x), fabsf(T.y)), fabsf(T.z));
+    float ox = 0.0f, oy = 0.0f;
+    if (s > 0.0f) {
+        ox = fdiv(T.x, s);
+        oy = fdiv(T.y, s);
+    }
+    if (T.z < 0.0f) {
+        const float nx = fmul(fsub(1.0f, fabsf(oy)), sgn1(ox));
+        const float ny = fmul(fsub(1.0f, fabsf(ox)), sgn1(oy));
+        ox = nx;
+        oy = ny;
+    }
+    const uint32_t cx = quantize(fadd(fmul(ox, 0.5f), 0.5f), 255.0f, 255u);
+    const uint32_t cy = quantize(fadd(fmul(oy, 0.5f), 0.5f), 255.0f, 255u);
+    return (cx << 8) | cy;
+}
+
+__device__ __forceinline__ float3 oct_decode(uint32_t code) {
+    float ox = fsub(fmul(fdiv(__uint2float_rn(code >> 8), 255.0f), 2.0f), 1.0f);
+    float oy = fsub(fmul(fdiv(__uint2float_rn(code & 255u), 255.0f), 2.0f), 1.0f);
+    const float z = fsub(fsub(1.0f, fabsf(ox)), fabsf(oy));
+    if (z < 0.0f) {
+        const float nx = fmul(fsub(1.0f, fabsf(oy)), sgn1(ox));
+        const float ny = fmul(fsub(1.0f, fabsf(ox)), sgn1(oy));
+        ox = nx;
+        oy = ny;
+    }
+    return v3unit(make_float3(ox, oy, z));
+}
+
+// AO of layer point k and of control point j: cubic Hermite over the layer
+// values with finite-difference slopes (one-sided at root and tip), in the
+// Hermite basis order of the positions.
+__device__ __forceinline__ float layer_ao_exact(const GroomDev &g, const Root &r, int k) {
+    if (!g.has_ao) return 1.0f;
+    const float4 *row = g.lv + (int64_t)k * g.V;
+    return fadd(fadd(fmul(r.b0, __ldg(&row[r.i0]).w), fmul(r.b1, __ldg(&row[r.i1]).w)),
+                fmul(r.b2, __ldg(&row[r.i2]).w));
+}
+
+__device__ __forceinline__ float control_ao_exact(const GroomDev &g, const Root &r, int C, int j) {
+    const int L = g.L;
+    const int x = j * (L - 1);
+    int k = x / (C - 1);
+    if (k > L - 2) k = L - 2;
+    const float t = fdiv(__int2float_rn(x - k * (C - 1)), __int2float_rn(C - 1));
+    const float a0 = layer_ao_exact(g, r, k), a1 = layer_ao_exact(g, r, k + 1);
+    const float am = k > 0 ? layer_ao_exact(g, r, k - 1) : a0;
+    const float a2 = k + 2 <= L - 1 ? layer_ao_exact(g, r, k + 2) : a1;
+    const float m0 = k == 0 ? fsub(a1, a0) : fmul(0.5f, fsub(a1, am));
+    const float m1 = k + 1 == L - 1 ? fsub(a1, a0) : fmul(0.5f, fsub(a2, a0));
+    const float t2 = fmul(t, t), t3 = fmul(t2, t);
+    const float h00 = fadd(fsub(fmul(2.0f, t3), fmul(3.0f, t2)), 1.0f);
+    const float h10 = fadd(fsub(t3, fmul(2.0f, t2)), t);
+    const float h01 = fsub(fmul(3.0f, t2), fmul(2.0f, t3));
+    const float h11 = fsub(t3, t2);
+    return fadd(fadd(fadd(fmul(h00, a0), fmul(h10, m0)), fmul(h01, a1)), fmul(h11, m1));
+}
+
+// u (bits 11..6) and v (5..0) codes of the root's scalp coordinates.
+__device__ __forceinline__ uint32_t root_uv_codes(const GroomDev &g, const Root &r) {
+    if (!g.uv) return 0u;
+    const float2 a = __ldg(&g.uv[r.i0]), b = __ldg(&g.uv[r.i1]), c = __ldg(&g.uv[r.i2]);
+    const float u = fadd(fadd(fmul(r.b0, a.x), fmul(r.b1, b.x)), fmul(r.b2, c.x));
+    const float v = fadd(fadd(fmul(r.b0, a.y), fmul(r.b1, b.y)), fmul(r.b2, c.y));
+    return (quantize(u, 63.0f, 63u) << 6) | quantize(v, 63.0f, 63u);
+}
+
+__device__ __forceinline__ float3 cross3x(float3 a, float3 b) {
+    return make_float3(fsub(fmul(a.y, b.z), fmul(a.z, b.y)), fsub(fmul(a.z, b.x), fmul(a.x, b.z)),
+                       fsub(fmul(a.x, b.y), fmul(a.y, b.x)));
+}
+
+// Position on the ray through pixel position (xs, ys) at view depth w:
+// (M0 - xn M3) X = xn M33 - M03, (M1 - yn M3) X = yn M33 - M13,
+// M3 X = w - M33, by Cramer's rule.
+__device__ __forceinline__ float3 unproject(const CamDev &c, float xs, float ys, float w) {
+    const float *m = c.m;
+    const float xn = fsub(fdiv(fmul(2.0f, xs), __int2float_rn(c.W)), 1.0f);
+    const float yn = fsub(1.0f, fdiv(fmul(2.0f, ys), __int2float_rn(c.H)));
+    const float3 ra = make_float3(fsub(m[0], fmul(xn, m[12])), fsub(m[1], fmul(xn, m[13])), fsub(m[2], fmul(xn, m[14])));
+    const float3 rb = make_float3(fsub(m[4], fmul(yn, m[12])), fsub(m[5], fmul(yn, m[13])), fsub(m[6], fmul(yn, m[14])));
+    const float3 rc = make_float3(m[12], m[13], m[14]);
+    const float ka = fsub(fmul(xn, m[15]), m[3]);
+    const float kb = fsub(fmul(yn, m[15]), m[7]);
+    const float kc = fsub(w, m[15]);
+    const float3 bc = cross3x(rb, rc), ca = cross3x(rc, ra), ab = cross3x(ra, rb);
+    const float det = fadd(fadd(fmul(ra.x, bc.x), fmul(ra.y, bc.y)), fmul(ra.z, bc.z));
+    return make_float3(fdiv(fadd(fadd(fmul(ka, bc.x), fmul(kb, ca.x)), fmul(kc, ab.x)), det),
+                       fdiv(fadd(fadd(fmul(ka, bc.y), fmul(kb, ca.y)), fmul(kc, ab.y)), det),
+                       fdiv(fadd(fadd(fmul(ka, bc.z), fmul(kb, ca.z)), fmul(kc, ab.z)), det));
+}
+
+// Decode of a compressed key at pixel (px, py): position at the middle of
+// the depth bin on the pixel-centre ray, tangent from its code, screen
+// tangent and isotropic flag as for the id payload.
+struct DecodedC {
+    float3 X, T;
+    float tsx, tsy;
+    uint32_t u, v, w, ao;    // payload codes
+    bool iso;
+};
+
+__device__ __forceinline__ DecodedC decode_compressed(const CamDev &cam, uint64_t key, int px, int py) {
+    DecodedC d;
+    const float z = fmul(fadd(__uint2float_rn((uint32_t)(key >> 40)), 0.5f), 5.9604644775390625e-8f);
+    const float w = fadd(cam.near_m, fmul(z, fsub(cam.far_m, cam.near_m)));
+    d.X = unproject(cam, fadd(__int2float_rn(px), 0.5f), fadd(__int2float_rn(py), 0.5f), w);
+    d.T = oct_decode((uint32_t)(key >> 24) & 0xFFFFu);
+    d.u = (uint32_t)(key >> 18) & 63u;
+    d.v = (uint32_t)(key >> 12) & 63u;
+    d.w = (uint32_t)(key >> 6) & 63u;
+    d.ao = (uint32_t)key & 63u;
+    d.iso = screen_tangent(cam, d.X, d.T, d.tsx, d.tsy);
     return d;
 }
 

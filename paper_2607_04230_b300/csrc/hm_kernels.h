@@ -27,6 +27,13 @@ struct LightsDev {
     ShadowDev sh[HM_MAX_LIGHTS];
 };
 
+// Appearance of the compressed payload: per (u, v) code a float4 (tip
+// albedo rgb, root / tip ratio), 64 x 64 entries; roughness and tilt.
+struct CgbDev {
+    const float4 *table;
+    float rough, tilt;
+};
+
 struct FilterDev {
     int32_t enabled, radius;
     float hw2;                 // strip half-width squared (binary32 product)
@@ -40,11 +47,11 @@ cudaError_t launch_clear(uint64_t *vis_c, uint64_t *vis_a, int64_t npx, const ui
                          hm_frame_stats *stats, cudaStream_t st);
 cudaError_t launch_lod(const CallTable &tab, const CamDev &cam, hm_frame_stats *stats, cudaStream_t st);
 cudaError_t launch_raster(const CallTable &tab, const ViewSet &views, bool precheck, int min_blocks, int ctas_per_sm,
-                          hm_frame_stats *stats, cudaStream_t st);
+                          hm_frame_stats *stats, cudaStream_t st, bool compressed = false);
 cudaError_t launch_probe_atomic_min(uint64_t *buf, int64_t n, int rounds, int pattern, cudaStream_t st);
 cudaError_t launch_resolve(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                            const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status, int tile_h,
-                           cudaStream_t st);
+                           cudaStream_t st, const CgbDev *compressed = nullptr);
 cudaError_t launch_resolve_adjoint(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                                    const uint64_t *vis_c, const uint64_t *vis_a, const float *grad_rgba,
                                    float *const *glv, float *const *galb, void *scratch, uint32_t *status,

@@ -209,7 +209,9 @@ struct SegRec {
     int32_t ilo;                 // first major pixel index
     int32_t start;               // first work item of this segment
     int32_t flags;               // bit0: u is x; bit1: short (32-bit arithmetic)
-    uint32_t id_lo, id_hi;       // payload strand << 7 | segment
+    uint32_t id_lo, id_hi;       // payload strand << 7 | segment; compressed: j, C - 1
+    uint32_t cgb_hi;             // compressed: payload bits 39..12 (tangent, u, v) >> 12
+    float aoA, dao;              // compressed: AO at A, AO(B) - AO(A)
 };
 
 constexpr int kRasterThreads = 256;
@@ -225,7 +227,15 @@ constexpr int kRasterWarps = kRasterThreads / 32;
 // depth numerator num = (cu - uA) dU + (cv - vA) dV change by constants from
 // one pixel to the next along the minor axis.  For short segments (|dU|,
 // |dV| < 2^14) every quantity fits in 32 bits; long ones use 64 bits.
-template <typename I, bool kPrecheck>
+// Low 40 bits of a compressed key at projection parameter t.
+__device__ __forceinline__ uint64_t compressed_payload(const SegRec &q, float t) {
+    const float w = fdiv(fadd(__uint2float_rn(q.id_lo), t), __uint2float_rn(q.id_hi));
+    const uint32_t cw = quantize(w, 63.0f, 63u);
+    const uint32_t ca = quantize(fadd(q.aoA, fmul(q.dao, t)), 62.0f, 62u);
+    return ((uint64_t)q.cgb_hi << 12) | (uint64_t)((cw << 6) | ca);
+}
+
+template <typename I, bool kPrecheck, bool kCgb>
 __device__ __forceinline__ void raster_item(const SegRec &q, int i, int W, int H, uint64_t *__restrict__ vis_c,
                                             uint64_t *__restrict__ vis_a, uint32_t &n_cons, uint32_t &n_cen) {
     const bool xm = q.flags & 1;
@@ -265,7 +275,7 @@ __device__ __forceinline__ void raster_item(const SegRec &q, int i, int W, int H
         const float z = fclamp(fadd(q.zA, fmul(q.dz, t)), 0.0f, 1.0f);
         uint32_t d24 = (uint32_t)floorf(fmul(z, 16777216.0f));
         d24 = d24 > 16777215u ? 16777215u : d24;
-        const uint64_t key = ((uint64_t)d24 << 40) | id;
+        const uint64_t key = ((uint64_t)d24 << 40) | (kCgb ? compressed_payload(q, t) : id);
         const int px = xm ? i : m, py = xm ? m : i;
         const size_t p = (size_t)py * (size_t)W + (size_t)px;
         n_cons += 1;
@@ -277,9 +287,12 @@ __device__ __forceinline__ void raster_item(const SegRec &q, int i, int W, int H
     }
 }
 
-template <bool kPrecheck, int kMinBlocks, bool kMulti>
+// kMode: 0 one view, 1 several views (strands assembled once), 2 one view
+// with the compressed payload.
+template <bool kPrecheck, int kMinBlocks, int kMode>
 __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(CallTable tab, ViewSet views,
                                                                             hm_frame_stats *stats) {
+    constexpr bool kMulti = kMode == 1, kCgb = kMode == 2;
     __shared__ uint32_t s_goff[HM_MAX_GROOMS_PER_CALL + 1];
     __shared__ SegRec s_rec[kRasterWarps][32];
     if (threadIdx.x == 0) {
@@ -316,11 +329,18 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
         int64_t s = 0;
         int j = 0;
         float3 cp[2];
+        uint32_t cgb_hi = 0;
+        float aoA = 1.0f, aoB = 1.0f;
         if (active) {
             s = (int64_t)__ldg(&g.faces[f]).w + sl / (uint32_t)(C - 1);
             j = (int)(sl % (uint32_t)(C - 1));
             const Root rt = make_root(g, s, f);
             control_pts<2>(g, rt, C, j, cp);
+            if (kCgb) {
+                cgb_hi = (oct_encode(v3unit(v3sub(cp[1], cp[0]))) << 12) | root_uv_codes(g, rt);
+                aoA = control_ao_exact(g, rt, C, j);
+                aoB = control_ao_exact(g, rt, C, j + 1);
+            }
         }
         const int n_views = kMulti ? views.n : 1;
         for (int view = 0; view < n_views; ++view) {
@@ -347,9 +367,17 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
                 r.zA = A.z;
                 r.dz = fsub(B.z, A.z);
                 r.hc = centre_halfwidth(cam, g.width_m, A.w, B.w);
-                const uint64_t id = ((g.base + (uint64_t)s) << 7) | (uint64_t)j;
-                r.id_lo = (uint32_t)id;
-                r.id_hi = (uint32_t)(id >> 32);
+                if (kCgb) {
+                    r.id_lo = (uint32_t)j;
+                    r.id_hi = (uint32_t)(C - 1);
+                    r.cgb_hi = cgb_hi;
+                    r.aoA = aoA;
+                    r.dao = fsub(aoB, aoA);
+                } else {
+                    const uint64_t id = ((g.base + (uint64_t)s) << 7) | (uint64_t)j;
+                    r.id_lo = (uint32_t)id;
+                    r.id_hi = (uint32_t)(id >> 32);
+                }
                 const int64_t dX = (int64_t)B.X - A.X, dY = (int64_t)B.Y - A.Y;
                 r.fden = __ll2float_rn(dX * dX + dY * dY);
                 r.slope = r.du == 0 ? 0.0f : (float)r.dv / (float)r.du;
@@ -387,9 +415,9 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
             const SegRec &q = rec[src];
             const int i = q.ilo + (item - q.start);
             if (q.flags & 2)
-                raster_item<int32_t, kPrecheck>(q, i, W, H, vis_c, vis_a, n_cons, n_cen);
+                raster_item<int32_t, kPrecheck, kCgb>(q, i, W, H, vis_c, vis_a, n_cons, n_cen);
             else
-                raster_item<int64_t, kPrecheck>(q, i, W, H, vis_c, vis_a, n_cons, n_cen);
+                raster_item<int64_t, kPrecheck, kCgb>(q, i, W, H, vis_c, vis_a, n_cons, n_cen);
         }
         __syncwarp();
         }   // views
@@ -639,7 +667,7 @@ cudaError_t launch_lod(const CallTable &tab, const CamDev &cam, hm_frame_stats *
 // (min resident CTAs per SM of 256 threads: 3 -> up to 80 registers,
 // 4 -> 64).  The persistent grid is ctas_per_sm CTAs per SM, capped at what
 // fits (0 = as many as fit).
-template <bool P, int M, bool V>
+template <bool P, int M, int V>
 static int raster_fit_per_sm() {
     static int cached = 0;
     if (cached == 0) {
@@ -650,7 +678,7 @@ static int raster_fit_per_sm() {
     return cached;
 }
 
-template <bool P, int M, bool V>
+template <bool P, int M, int V>
 static cudaError_t launch_raster_v(const CallTable &tab, const ViewSet &views, int ctas_per_sm, hm_frame_stats *stats,
                                    cudaStream_t st) {
     const int fit = raster_fit_per_sm<P, M, V>();
@@ -659,7 +687,7 @@ static cudaError_t launch_raster_v(const CallTable &tab, const ViewSet &views, i
     return cudaGetLastError();
 }
 
-template <bool V>
+template <int V>
 static cudaError_t launch_raster_views(const CallTable &tab, const ViewSet &views, bool precheck, int min_blocks,
                                        int ctas_per_sm, hm_frame_stats *stats, cudaStream_t st) {
     const bool m3 = min_blocks == 3;
@@ -671,9 +699,10 @@ static cudaError_t launch_raster_views(const CallTable &tab, const ViewSet &view
 }
 
 cudaError_t launch_raster(const CallTable &tab, const ViewSet &views, bool precheck, int min_blocks, int ctas_per_sm,
-                          hm_frame_stats *stats, cudaStream_t st) {
-    if (views.n > 1) return launch_raster_views<true>(tab, views, precheck, min_blocks, ctas_per_sm, stats, st);
-    return launch_raster_views<false>(tab, views, precheck, min_blocks, ctas_per_sm, stats, st);
+                          hm_frame_stats *stats, cudaStream_t st, bool compressed) {
+    if (compressed) return launch_raster_views<2>(tab, views, precheck, min_blocks, ctas_per_sm, stats, st);
+    if (views.n > 1) return launch_raster_views<1>(tab, views, precheck, min_blocks, ctas_per_sm, stats, st);
+    return launch_raster_views<0>(tab, views, precheck, min_blocks, ctas_per_sm, stats, st);
 }
 
 }  // namespace hm

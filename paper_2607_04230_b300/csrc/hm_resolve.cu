@@ -24,11 +24,15 @@ namespace hm {
 // conservative-referenced one where needed; then one combine pass writes RGBA.
 constexpr int kFwdTileW = 32, kFwdThreads = 512;
 
-template <int kFwdTileH>
+// kCgb: the keys carry the compressed payload (Sec. 3.1.2) and shading
+// reads it alone: position from depth, tangent from its code, albedo from
+// the appearance table at (u, v) scaled along w, AO from its code.
+template <int kFwdTileH, bool kCgb>
 __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, CamDev cam, LightsDev Ls, FilterDev fp,
                                                               const uint64_t *__restrict__ vis_c,
                                                               const uint64_t *__restrict__ vis_a,
-                                                              float4 *__restrict__ rgba, uint32_t *status) {
+                                                              float4 *__restrict__ rgba, uint32_t *status,
+                                                              CgbDev cg) {
     constexpr int kFwdTilePx = kFwdTileW * kFwdTileH;
     extern __shared__ __align__(16) unsigned char smem[];
     const int R = fp.enabled ? fp.radius : 0;
@@ -89,20 +93,36 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
         const int lx = i % sw, ly = i / sw;
         const int gx = x0 - R + lx, gy = y0 - R + ly;
         const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + (int64_t)gy * W + gx));
-        const Decoded d = decode_key(tab, s_bases, cam, kg, gx, gy, status);
         float3 c = make_float3(0.f, 0.f, 0.f);
-        if (d.ok) {
-            const GroomDev &g = tab.g[d.gi];
-            const float4 a = __ldg(&g.albedo[d.s]);
-            c = shade(d.X, d.T, make_float3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt, decoded_ao(g, d),
-                      receiver_beta(g, Ls, d.s));
+        float tsx, tsy;
+        bool iso;
+        if (kCgb) {
+            const DecodedC d = decode_compressed(cam, kg, gx, gy);
+            const float4 a = __ldg(&cg.table[d.u * 64u + d.v]);
+            const float sc = a.w + (1.0f - a.w) * __fdiv_rn((float)d.w, 63.0f);
+            c = shade(d.X, d.T, make_float3(a.x * sc, a.y * sc, a.z * sc), cam, Ls, cg.rough, cg.tilt,
+                      __fdiv_rn((float)d.ao, 62.0f), 1.0f);
+            tsx = d.tsx;
+            tsy = d.tsy;
+            iso = d.iso;
+        } else {
+            const Decoded d = decode_key(tab, s_bases, cam, kg, gx, gy, status);
+            if (d.ok) {
+                const GroomDev &g = tab.g[d.gi];
+                const float4 a = __ldg(&g.albedo[d.s]);
+                c = shade(d.X, d.T, make_float3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt, decoded_ao(g, d),
+                          receiver_beta(g, Ls, d.s));
+            }
+            tsx = d.tsx;
+            tsy = d.tsy;
+            iso = d.iso;
         }
         s_col[i] = c;
         const int tx = lx - R, ty = ly - R;
         if (tx >= 0 && tx < kFwdTileW && ty >= 0 && ty < kFwdTileH) {
             const int t = ty * kFwdTileW + tx;
-            s_ts[t] = make_float2(d.tsx, d.tsy);
-            if (!d.iso) s_flag[t] = 2;        // isoG cleared, isoA still set
+            s_ts[t] = make_float2(tsx, tsy);
+            if (!iso) s_flag[t] = 2;          // isoG cleared, isoA still set
         }
     }
     __syncthreads();
@@ -167,12 +187,24 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
         const int tx = t % kFwdTileW, ty = t / kFwdTileW;
         const int gx = x0 + tx, gy = y0 + ty;
         const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx));
-        const Decoded d = decode_key(tab, s_bases, cam, ka, gx, gy, status);
+        float tsx, tsy;
+        bool iso;
+        if (kCgb) {
+            const DecodedC d = decode_compressed(cam, ka, gx, gy);
+            tsx = d.tsx;
+            tsy = d.tsy;
+            iso = d.iso;
+        } else {
+            const Decoded d = decode_key(tab, s_bases, cam, ka, gx, gy, status);
+            tsx = d.tsx;
+            tsy = d.tsy;
+            iso = d.iso;
+        }
         const int dA = (int)(ka >> 40);
         const float3 z = make_float3(0.f, 0.f, 0.f);
-        Recon ra = reconstruct_fast_r<false>(R, s_dg, s_fa, s_col, sw, tx, ty, dA, d.tsx, d.tsy, d.iso, z, fp);
+        Recon ra = reconstruct_fast_r<false>(R, s_dg, s_fa, s_col, sw, tx, ty, dA, tsx, tsy, iso, z, fp);
         if (ra.cnt > 0 && ra.W < 1e-20f)
-            ra = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, d.tsx, d.tsy, d.iso, false, z, fp);
+            ra = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, tsx, tsy, iso, false, z, fp);
         const int mid = (ty + R) * sw + tx + R;
         float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
         if (s_dg[mid] >= 0) {               // depth mismatch: blend over the centre result, alpha 1
@@ -279,29 +311,34 @@ size_t resolve_smem_bytes(int radius, int tile_h) {
     return (b + 15) & ~(size_t)15;
 }
 
-template <int TH>
+template <int TH, bool C>
 static cudaError_t launch_resolve_t(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                                    const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, const CgbDev &cg) {
     const int R = fp.enabled ? fp.radius : 0;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(resolve_kernel<TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(resolve_kernel<TH, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)resolve_smem_bytes(HM_MAX_FILTER_RADIUS, TH));
         attr_set = true;
     }
     dim3 grid((cam.W + kFwdTileW - 1) / kFwdTileW, (cam.H + TH - 1) / TH);
-    resolve_kernel<TH><<<grid, kFwdThreads, resolve_smem_bytes(R, TH), st>>>(tab, cam, Ls, fp, vis_c, vis_a,
-                                                                             reinterpret_cast<float4 *>(rgba), status);
+    resolve_kernel<TH, C><<<grid, kFwdThreads, resolve_smem_bytes(R, TH), st>>>(
+        tab, cam, Ls, fp, vis_c, vis_a, reinterpret_cast<float4 *>(rgba), status, cg);
     return cudaGetLastError();
 }
 
 // Resolve tile: 32 x tile_h output pixels per CTA (tile_h 16 or 32).
 cudaError_t launch_resolve(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                            const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status, int tile_h,
-                           cudaStream_t st) {
-    if (tile_h == 16) return launch_resolve_t<16>(tab, cam, Ls, fp, vis_c, vis_a, rgba, status, st);
-    return launch_resolve_t<32>(tab, cam, Ls, fp, vis_c, vis_a, rgba, status, st);
+                           cudaStream_t st, const CgbDev *compressed) {
+    if (compressed) {
+        if (tile_h == 16) return launch_resolve_t<16, true>(tab, cam, Ls, fp, vis_c, vis_a, rgba, status, st, *compressed);
+        return launch_resolve_t<32, true>(tab, cam, Ls, fp, vis_c, vis_a, rgba, status, st, *compressed);
+    }
+    const CgbDev none{nullptr, 0.0f, 0.0f};
+    if (tile_h == 16) return launch_resolve_t<16, false>(tab, cam, Ls, fp, vis_c, vis_a, rgba, status, st, none);
+    return launch_resolve_t<32, false>(tab, cam, Ls, fp, vis_c, vis_a, rgba, status, st, none);
 }
 
 }  // namespace hm

@@ -36,7 +36,8 @@ class GroomDesc(ctypes.Structure):
                 ("layer_verts", ctypes.c_void_p), ("faces", ctypes.c_void_p), ("strand_face", ctypes.c_void_p),
                 ("strand_bary", ctypes.c_void_p), ("strand_albedo", ctypes.c_void_p),
                 ("bundle_delta", ctypes.c_void_p), ("strand_width_m", ctypes.c_float),
-                ("roughness", ctypes.c_float), ("tilt", ctypes.c_float), ("vert_ao", ctypes.c_void_p)]
+                ("roughness", ctypes.c_float), ("tilt", ctypes.c_float), ("vert_ao", ctypes.c_void_p),
+                ("vert_uv", ctypes.c_void_p)]
 
 
 class Camera(ctypes.Structure):
@@ -109,6 +110,8 @@ def lib():
         "hm_resolve_shade": [P, i32, P, P, P, P, P, P, P, P],
         "hm_render_visibility_msaa": [P, i32, P, i32, P, i32, P, P],
         "hm_render_shadow_map": [P, i32, P, P, P, P, P],
+        "hm_render_visibility_compressed": [P, i32, P, P, P, P, i32, P, P],
+        "hm_resolve_compressed": [P, P, P, P, P, P, P, P],
         "hm_resolve_msaa": [P, i32, P, P, i32, P, P, P],
         "hm_shade_backward": [P, i32, P, P, P, P, P, P, P, P, P, P],
         "hm_shade_backward_noalloc": [P, i32, P, P, P, P, P, P, P, P, P],
@@ -225,7 +228,8 @@ class Groom:
             bary=np.ascontiguousarray(g.strand_bary, np.float32),
             alb=np.ascontiguousarray(g.strand_albedo, np.float32),
             delta=np.ascontiguousarray(g.bundle_delta, np.float32),
-            ao=None if getattr(g, "vert_ao", None) is None else np.ascontiguousarray(g.vert_ao, np.float32))
+            ao=None if getattr(g, "vert_ao", None) is None else np.ascontiguousarray(g.vert_ao, np.float32),
+            uv=None if getattr(g, "vert_uv", None) is None else np.ascontiguousarray(g.vert_uv, np.float32))
         d = GroomDesc()
         d.num_layers, d.num_verts, d.num_faces = g.num_layers, g.num_verts, g.num_faces
         d.segments_per_strand, d.num_strands = g.segments_per_strand, g.num_strands
@@ -234,6 +238,7 @@ class Groom:
         d.strand_bary, d.strand_albedo, d.bundle_delta = k["bary"].ctypes.data, k["alb"].ctypes.data, k["delta"].ctypes.data
         d.strand_width_m, d.roughness, d.tilt = g.strand_width_m, g.roughness, g.tilt
         d.vert_ao = None if k["ao"] is None else k["ao"].ctypes.data
+        d.vert_uv = None if k["uv"] is None else k["uv"].ctypes.data
         h = ctypes.c_void_p()
         check(lib().hm_create_groom(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)))
         self.handle = h
@@ -305,6 +310,30 @@ def render_visibility_multiview(grooms, cams, vis_centers, vis_conses, clear=Tru
         _dptr(t)
     check(lib().hm_render_visibility_multiview(arr, n, cs, nv, vc, va, None, int(bool(clear)), _dptr(stats),
                                                _stream_ptr(stream)))
+
+
+class Appearance(ctypes.Structure):
+    _fields_ = [("d_table", ctypes.c_void_p), ("roughness", ctypes.c_float), ("tilt", ctypes.c_float)]
+
+
+def render_visibility_compressed(grooms, cam, vis_center, vis_cons, scene_d24=None, clear=True, stats=None,
+                                 stream=None):
+    """hm_render_visibility with the compressed payload (tangent, uvw, AO)
+    in the keys' low 40 bits."""
+    arr, n = _handles(grooms)
+    c = camera_struct(cam)
+    check(lib().hm_render_visibility_compressed(arr, n, ctypes.byref(c), _dptr(vis_center), _dptr(vis_cons),
+                                                _dptr(scene_d24), int(bool(clear)), _dptr(stats),
+                                                _stream_ptr(stream)))
+
+
+def resolve_compressed(cam, lights, filt, table, roughness, tilt, vis_center, vis_cons, rgba, stream=None):
+    """Resolve of compressed keys; table: CUDA float32 [64][64][4]
+    appearance (tip albedo rgb, root / tip ratio)."""
+    c, L, f = camera_struct(cam), lights_struct(lights), filter_struct(filt)
+    a = Appearance(_dptr(table).value, float(roughness), float(tilt))
+    check(lib().hm_resolve_compressed(ctypes.byref(c), ctypes.byref(L), ctypes.byref(f), ctypes.byref(a),
+                                      _dptr(vis_center), _dptr(vis_cons), _dptr(rgba), _stream_ptr(stream)))
 
 
 def render_shadow_map(grooms, light_cam, map_center, map_cons, stats=None, stream=None):

@@ -51,6 +51,7 @@ class Groom:
     roughness: float = ROUGHNESS
     tilt: float = TILT
     vert_ao: np.ndarray | None = None   # float32 [L][V] in [0, 1], baked ambient occlusion, or None
+    vert_uv: np.ndarray | None = None   # float32 [V][2] in [0, 1], scalp texture coordinates, or None
 
     @property
     def num_layers(self) -> int:
@@ -170,6 +171,13 @@ def fan_disk(k: int, n: int):
     return np.asarray(verts, np.float64), np.asarray(faces, np.int32)
 
 
+def scalp_uv(k: int, n: int) -> np.ndarray:
+    """Scalp texture coordinates: the planar fan's unit disk mapped to
+    [0, 1]^2 (float32 [V][2])."""
+    v2, _ = fan_disk(k, n)
+    return np.ascontiguousarray(((v2 + 1.0) * 0.5).astype(np.float32))
+
+
 def scalp_cap(k: int, n: int, radius: float = 0.1, cap_deg: float = 60.0):
     """Map the planar fan onto a spherical cap with its pole along +y.
 
@@ -239,7 +247,23 @@ def make_groom(seed: int, k: int, n: int, num_layers: int, length_m: float,
         strand_albedo=np.ascontiguousarray(albedo),
         bundle_delta=np.ascontiguousarray(delta),
         segments_per_strand=int(segments),
+        vert_uv=scalp_uv(k, n),
     )
+
+
+def appearance_table(seed: int = 0, albedo_range=(0.2, 0.6), ratio_range=(0.5, 1.0)) -> np.ndarray:
+    """Shading parameters over the quantized scalp coordinates for the
+    compressed payload: float32 [64][64][4], per (u, v) texel the tip albedo
+    (rgb) and the root / tip albedo ratio; smooth in (u, v) plus per-texel
+    variation, seeded."""
+    rng = np.random.default_rng(seed)
+    u = np.linspace(0.0, 1.0, 64)
+    base = rng.uniform(albedo_range[0], albedo_range[1], size=3)
+    grad = rng.normal(scale=0.1, size=(2, 3))
+    smooth = base[None, None, :] + u[:, None, None] * grad[0][None, None, :] + u[None, :, None] * grad[1][None, None, :]
+    rgb = np.clip(smooth + rng.normal(scale=0.05, size=(64, 64, 3)), albedo_range[0], albedo_range[1])
+    ratio = rng.uniform(ratio_range[0], ratio_range[1], size=(64, 64, 1))
+    return np.ascontiguousarray(np.concatenate([rgb, ratio], 2).astype(np.float32))
 
 
 # --------------------------------------------------------------------------

@@ -962,3 +962,144 @@ def test_shadowed_resolve_zero_density_is_unshadowed_and_light_selective():
             np.testing.assert_allclose(b.numpy(), a.numpy(), rtol=0, atol=1e-15)
             darker = (out[:, :3] < base[:, :3] - 1e-6).any(1).sum().item()
             assert darker > 50 and bool((out[:, :3] <= base[:, :3] + 1e-12).all())
+
+
+# ---------------------------------------------------------------------------
+# compressed G-buffer payload (Sec. 3.1.2)
+# ---------------------------------------------------------------------------
+
+def test_octahedral_codes_closed_forms_and_error_bound():
+    """Cigolle et al.'s octahedral map: the poles and the equator's axis
+    points have closed-form codes (0.5 -> 127.5 rounds to even 128), the
+    lower hemisphere folds onto the corners, and every unit vector decodes
+    within 1 degree of itself at 8 + 8 bits."""
+    assert oracle.oct_encode([0, 0, 1]) == (128 << 8) | 128
+    assert oracle.oct_encode([1, 0, 0]) == (255 << 8) | 128
+    assert oracle.oct_encode([0, -1, 0]) == (128 << 8) | 0
+    assert oracle.oct_encode([0, 0, -1]) == (255 << 8) | 255
+    np.testing.assert_array_equal(oracle.oct_decode((255 << 8) | 255), np.float32([0, 0, -1]))
+    np.testing.assert_allclose(oracle.oct_decode((128 << 8) | 128), [0.00392, 0.00392, 0.99998], atol=1e-4)
+    rng = np.random.default_rng(0)
+    v = rng.normal(size=(4000, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    worst = 0.0
+    for t in v.astype(np.float32):
+        code = oracle.oct_encode(t)
+        d = oracle.oct_decode(code).astype(np.float64)
+        d64 = v64.oct_decode64(np.array([code])).numpy()[0]
+        worst = max(worst, math.degrees(math.acos(min(1.0, float(d64 @ t.astype(np.float64))))))
+        assert abs(np.linalg.norm(d) - 1.0) < 1e-6 and np.abs(d - d64).max() < 1e-6
+    assert worst < 1.0, worst
+
+
+def test_unproject_inverts_the_projection():
+    """The compressed decode's position: projecting it back gives the pixel
+    centre and the view depth (FP32 C and FP64 value layer alike)."""
+    sc = synth.tiny_scene(5, width=160, height=120)
+    cam = sc.camera
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        px, py = int(rng.integers(0, 160)), int(rng.integers(0, 120))
+        w = float(np.float32(rng.uniform(0.2, 3.0)))
+        X = oracle.unproject(cam, px + 0.5, py + 0.5, w)
+        ok, _, _, wz = oracle.project_point(cam, X)          # wz = (w, z, xs, ys)
+        assert ok and abs(wz[2] - (px + 0.5)) < 2e-3 and abs(wz[3] - (py + 0.5)) < 2e-3
+        assert abs(wz[0] - w) < 2e-6 * w
+    d24 = np.array([1000, 2 ** 23, 2 ** 24 - 1], np.int64)
+    pix = np.array([0, 77, 160 * 120 - 1], np.int64)
+    X = v64.cgb_position(cam, pix, d24).numpy()
+    M = cam.view_proj.astype(np.float64)
+    clip = np.c_[X, np.ones(3)] @ M.T
+    near, far = float(np.float32(cam.near)), float(np.float32(cam.far))
+    np.testing.assert_allclose(clip[:, 3], near + (d24 + 0.5) / 2 ** 24 * (far - near), rtol=1e-12)
+    np.testing.assert_allclose((clip[:, 0] / clip[:, 3] + 1) * 0.5 * 160, pix % 160 + 0.5, atol=1e-9)
+    np.testing.assert_allclose((1 - clip[:, 1] / clip[:, 3]) * 0.5 * 120, pix // 160 + 0.5, atol=1e-9)
+
+
+def test_compressed_keys_against_the_segment_they_came_from():
+    """Same coverage and depths as the id keys; each payload field, decoded,
+    agrees with the FP64 quantity of the segment the id key names (bit
+    layout, scales and meaning): root uv and w and AO codes within one step
+    of the FP64 rounding, the tangent within 1 degree of the chord."""
+    sc = synth.tiny_scene(31, width=120, height=96, num_strands=600, num_layers=5, length_m=0.06)
+    g = sc.grooms[0]
+    g.vert_ao = synth.baked_ao(g, seed=1)
+    lods = oracle.lods_for(sc)
+    vc, va, cnt = oracle.raster(sc.grooms, sc.camera, lods)
+    cc, ca, cnt2 = oracle.raster(sc.grooms, sc.camera, lods, compressed=True)
+    assert tuple(cnt) == tuple(cnt2)
+    for idk, ck in ((vc, cc), (va, ca)):
+        np.testing.assert_array_equal(idk == oracle.EMPTY, ck == oracle.EMPTY)
+        np.testing.assert_array_equal(idk >> np.uint64(40), ck >> np.uint64(40))
+    e, _, sg, seg = v64.key_fields(vc)
+    ce, _, tcode, cu, cv, cw, cao = v64.cgb_fields(cc)
+    idx = np.nonzero(~e)[0]
+    # pixels whose minimum depth is held by one segment only carry its payload
+    W = sc.camera.width
+    C = lods[0][1][g.strand_face[sg[idx]]]
+    num, den = oracle.msaa_decisions(sc.grooms, sc.camera, lods, 1, vc[None, :])
+    t = np.clip(num[0][idx] / np.maximum(den[0][idx], 1), 0, 1)
+    uv = g.vert_uv.astype(np.float64)
+    f = g.faces[g.strand_face[sg[idx]]]
+    b = g.strand_bary[sg[idx]].astype(np.float64)
+    b0 = 1.0 - b[:, 0] - b[:, 1]
+    u = b0 * uv[f[:, 0], 0] + b[:, 0] * uv[f[:, 1], 0] + b[:, 1] * uv[f[:, 2], 0]
+    v = b0 * uv[f[:, 0], 1] + b[:, 0] * uv[f[:, 1], 1] + b[:, 1] * uv[f[:, 2], 1]
+    w = (seg[idx] + t) / (C - 1)
+    gt = v64.GroomT(g, lods[0][1], 0)
+    ao = v64.pixel_ao(gt, sg[idx], seg[idx], num[0][idx], den[0][idx]).numpy()[:, 0]
+    for name, code, ref, scale in (("u", cu[idx], u, 63), ("v", cv[idx], v, 63), ("w", cw[idx], w, 63),
+                                   ("ao", cao[idx], ao, 62)):
+        err = np.abs(code - np.clip(np.rint(ref * scale), 0, scale))
+        assert err.max() <= 1 and (err == 0).mean() > 0.97, (name, err.max(), (err == 0).mean())
+    # tangent: the chord of the keyed segment; where two segments of a strand
+    # meet they have the same depth and the two payloads break the tie
+    # differently, so the neighbouring chord is accepted there
+    P = {}
+    T = v64.oct_decode64(tcode[idx]).numpy()
+    own, best = [], []
+    for q, (s, j, c) in enumerate(zip(sg[idx], seg[idx], C)):
+        if (s, c) not in P:
+            P[(s, c)] = oracle.strand_control_points(g, int(s), int(c)).astype(np.float64)
+        angs = []
+        for jj in (j, j - 1, j + 1):
+            if 0 <= jj < c - 1:
+                ch = P[(s, c)][jj + 1] - P[(s, c)][jj]
+                ch /= np.linalg.norm(ch)
+                angs.append(math.degrees(math.acos(min(1.0, float(ch @ T[q])))))
+        own.append(angs[0])
+        best.append(min(angs))
+    assert max(best) < 1.0 and (np.array(own) < 1.0).mean() > 0.95
+    assert np.all(cao[~ce] <= 62)
+
+
+def test_compressed_resolve_uniform_appearance_and_id_path_agreement():
+    """A constant appearance table, ambient light and no AO: every shaded
+    colour is ambient * albedo and the filter keeps it; with the synthetic
+    lights the compressed image stays close to the id-path image (the
+    payload's quantization, chord tangent and depth-bin position)."""
+    sc = synth.tiny_scene(32, width=128, height=96, num_strands=800)
+    lods = oracle.lods_for(sc)
+    cc, ca, _ = oracle.raster(sc.grooms, sc.camera, lods, compressed=True)
+    dec = oracle.resolve_decisions(sc.grooms, sc.camera, lods, sc.filt, cc, ca, compressed=True)
+    table = np.zeros((64, 64, 4), np.float32)
+    table[..., :3] = np.float32([0.3, 0.4, 0.5])
+    table[..., 3] = 1.0
+    amb = synth.make_lights([[0.0, 1.0, 0.0]], [0.0], ambient=0.5)
+    rgba, pix = v64.resolve_cgb(sc.camera, amb, sc.filt, cc, ca, dec, table, 0.15, -0.05)
+    on = rgba[:, 3] > 0
+    exp = 0.5 * np.float32([0.3, 0.4, 0.5]).astype(np.float64)
+    np.testing.assert_allclose(rgba[on, :3].numpy(), np.broadcast_to(exp, (int(on.sum()), 3)), rtol=1e-12)
+    # against the id path with per-strand albedo replaced by the table's
+    g = sc.grooms[0]
+    tab = synth.appearance_table(3)
+    vc, va, _ = oracle.raster(sc.grooms, sc.camera, lods)
+    deci = oracle.resolve_decisions(sc.grooms, sc.camera, lods, sc.filt, vc, va)
+    gt = v64.GroomT(g, lods[0][1], 0)
+    ref, rpix = v64.resolve([gt], sc.camera, sc.lights, sc.filt, vc, va, deci)
+    got, gpix = v64.resolve_cgb(sc.camera, sc.lights, sc.filt, cc, ca, dec, tab, g.roughness, g.tilt)
+    np.testing.assert_array_equal(rpix, gpix)
+    # the strip of a promoted pixel follows its (now chord) tangent: a few
+    # pixels gain or lose their last contributor
+    assert ((ref[:, 3].numpy() > 0) != (got[:, 3].numpy() > 0)).mean() < 0.02
+    assert float((ref[:, 3] - got[:, 3]).abs().mean()) < 0.02
