@@ -577,6 +577,7 @@ static hm_status filter_dev(const hm_filter_params *f, const hm_camera *cam, hm:
     fd.inv_sc2 = 1.0f / (f->sigma_c * f->sigma_c);
     volatile float hw = f->strip_halfwidth;
     fd.hw2 = hw * hw;
+    fd.hw = hw;
     const double span = (double)cam->far_m - (double)cam->near_m;
     const double rej = std::floor((double)f->depth_reject_m / span * 16777216.0 + 0.5);
     const double mis = std::floor((double)f->depth_mismatch_m / span * 16777216.0 + 0.5);

@@ -37,6 +37,7 @@ struct CgbDev {
 struct FilterDev {
     int32_t enabled, radius;
     float hw2;                 // strip half-width squared (binary32 product)
+    float hw;                  // strip half-width
     float inv_spar2, inv_sperp2, inv_siso2, inv_sc2;
     int32_t drej, dmis;        // depth thresholds in d24 units
 };

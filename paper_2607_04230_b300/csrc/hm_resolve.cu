@@ -23,6 +23,9 @@ namespace hm {
 // mismatch); the centre-referenced reconstruction of every centre pixel; the
 // conservative-referenced one where needed; then one combine pass writes RGBA.
 constexpr int kFwdTileW = 32, kFwdThreads = 512;
+// staged depth of a pixel without a centre key: far below any d24, so a
+// depth-difference test alone rejects it
+constexpr int kNoDepth = -(1 << 30);
 
 // kCgb: the keys carry the compressed payload (Sec. 3.1.2) and shading
 // reads it alone: position from depth, tangent from its code, albedo from
@@ -67,7 +70,7 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
     // 1. stage keys of tile + halo; list staged centre-sample pixels
     for (int i = tid; i < ns; i += kFwdThreads) {
         const int gx = x0 - R + i % sw, gy = y0 - R + i / sw;
-        int dg = -1;
+        int dg = kNoDepth;
         uint8_t fa = 0;
         if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
             const int64_t p = (int64_t)gy * W + gx;

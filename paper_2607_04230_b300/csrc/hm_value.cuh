@@ -177,47 +177,94 @@ __device__ __forceinline__ Recon reconstruct(const int *s_dg, const uint8_t *s_f
 //    callers redo it with the online-rescaled reconstruct() when some
 //    neighbour contributes but W < 1e-20.
 // Staged pixels without a centre key must hold a finite colour (zero).
+// Strip hit counts H_center, H_cons of Sec. 3.3.3 over the window: taps
+// within the strip |d - (d.Ts) Ts| <= hw of the screen tangent (the pixel
+// alone for a degenerate tangent).  Only the taps that can be in the strip
+// are visited: with the tangent's major axis as k, a tap (k, m) is within
+// hw of the line iff |m - k slope| <= hw / |major component| <= hw sqrt(2),
+// so per k at most the integers of [k slope - hw sqrt(2) - 0.01,
+// k slope + hw sqrt(2) + 0.01] are candidates (0.01 px covers the binary32
+// rounding of slope and of the test); each candidate then takes the exact
+// test of in_strip, so the counts equal a full-window scan.
+__device__ __forceinline__ int2 strip_counts(const int *s_dg, const uint8_t *s_fa, int sw, int lx, int ly, int R,
+                                             float tsx, float tsy, bool iso, const FilterDev &fp) {
+    int hc = 0, ha = 0;
+    if (iso) {
+        const int idx = (ly + R) * sw + lx + R;
+        return make_int2(s_dg[idx] >= 0 ? 1 : 0, s_fa[idx] ? 1 : 0);
+    }
+    const bool xmaj = fabsf(tsx) >= fabsf(tsy);
+    const float slope = xmaj ? tsy / tsx : tsx / tsy;
+    const float half = fp.hw * 1.41422f + 0.01f;
+    for (int k = -R; k <= R; ++k) {
+        const float c = (float)k * slope;
+        const int m0 = max((int)ceilf(c - half), -R), m1 = min((int)floorf(c + half), R);
+        for (int m = m0; m <= m1; ++m) {
+            const int dx = xmaj ? k : m, dy = xmaj ? m : k;
+            float dpar, perp2;
+            if (!in_strip(false, tsx, tsy, dx, dy, fp.hw2, dpar, perp2)) continue;
+            const int idx = (ly + dy + R) * sw + lx + dx + R;
+            hc += s_dg[idx] >= 0 ? 1 : 0;
+            ha += s_fa[idx] ? 1 : 0;
+        }
+    }
+    return make_int2(hc, ha);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Bilateral reconstruction of one pixel with unscaled weights (straight-line
+// code for radius R).  The spatial exponent is written as
+// dpar^2 (1/s_par^2 - 1/s_perp^2) + |d|^2 / s_perp^2 (perp^2 = |d|^2 - dpar^2),
+// which with the isotropic coefficients (0, 1/s_iso^2) and a zero tangent is
+// the isotropic exponent, so one loop serves both modes; exponents are
+// scaled by log2(e) for ex2.  Empty centre-layer taps hold a large negative
+// depth, so the depth test alone rejects them.
 template <int R, bool kColor>
 __device__ __forceinline__ Recon reconstruct_fast(const int *s_dg, const uint8_t *s_fa, const float3 *s_col, int sw,
                                                   int lx, int ly, int ref, float tsx, float tsy, bool iso, float3 Cp,
                                                   const FilterDev &fp) {
+    constexpr float kL2e = 1.4426950408889634f;
+    const float a = iso ? 0.0f : (fp.inv_spar2 - fp.inv_sperp2) * kL2e;
+    const float b = (iso ? fp.inv_siso2 : fp.inv_sperp2) * kL2e;
+    const float c = fp.inv_sc2 * kL2e;
+    const float ux = iso ? 0.0f : tsx, uy = iso ? 0.0f : tsy;
     float Sx = 0.f, Sy = 0.f, Sz = 0.f, Wt = 0.f;
-    int hc = 0, ha = 0, cnt = 0;
+    int cnt = 0;
     for (int dy = -R; dy <= R; ++dy) {
         const int row = (ly + dy + R) * sw + lx + R;
 #pragma unroll
         for (int dx = -R; dx <= R; ++dx) {
             const int idx = row + dx;
             const int dq = s_dg[idx];
-            const int fa = s_fa[idx];
-            float dpar, perp2;
-            const bool strip = in_strip(iso, tsx, tsy, dx, dy, fp.hw2, dpar, perp2);
-            const bool gq = dq >= 0;
-            const bool ok = gq && abs(dq - ref) <= fp.drej;
+            const bool ok = abs(dq - ref) <= fp.drej;
             cnt += ok ? 1 : 0;
-            hc += (strip && gq) ? 1 : 0;
-            ha += (strip && fa) ? 1 : 0;
             const float3 cq = s_col[idx];
-            float e = iso ? (float)(dx * dx + dy * dy) * fp.inv_siso2
-                          : (dpar * dpar) * fp.inv_spar2 + perp2 * fp.inv_sperp2;
+            const float dpar = fmaf((float)dy, uy, (float)dx * ux);
+            float e = fmaf(dpar * a, dpar, (float)(dx * dx + dy * dy) * b);
             if (kColor) {
                 const float ex = Cp.x - cq.x, ey = Cp.y - cq.y, ez = Cp.z - cq.z;
-                e += (ex * ex + ey * ey + ez * ez) * fp.inv_sc2;
+                e = fmaf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)), c, e);
             }
-            const float w = ok ? __expf(-e) : 0.f;
-            Sx += w * cq.x;
-            Sy += w * cq.y;
-            Sz += w * cq.z;
+            const float w = ok ? ex2_approx(-e) : 0.f;
+            Sx = fmaf(w, cq.x, Sx);
+            Sy = fmaf(w, cq.y, Sy);
+            Sz = fmaf(w, cq.z, Sz);
             Wt += w;
         }
     }
+    const int2 h = strip_counts(s_dg, s_fa, sw, lx, ly, R, tsx, tsy, iso, fp);
     Recon o;
     o.S = make_float3(Sx, Sy, Sz);
     o.W = Wt;
     o.m = 0.f;
     o.cnt = cnt;
-    o.hc = hc;
-    o.ha = ha;
+    o.hc = h.x;
+    o.ha = h.y;
     return o;
 }
 
