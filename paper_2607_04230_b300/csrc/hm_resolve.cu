@@ -40,9 +40,11 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
     extern __shared__ __align__(16) unsigned char smem[];
     const int R = fp.enabled ? fp.radius : 0;
     const int sw = kFwdTileW + 2 * R, sh = kFwdTileH + 2 * R, ns = sw * sh;
-    // shared layout: bases | s_col[ns] | s_dg[ns] | s_list[ns] | s_lg[tile] | s_out[tile] | s_ts[tile] | s_flag[tile] | s_fa[ns]
+    // shared layout: bases | s_col[ns] (rgb + centre depth bits) | s_dg[ns] | s_list[ns] | s_lg[tile] |
+    // s_out[tile] | s_ts[tile] | s_flag[tile] | s_fa[ns]
     uint64_t *s_bases = reinterpret_cast<uint64_t *>(smem);
-    float3 *s_col = reinterpret_cast<float3 *>(s_bases + HM_MAX_GROOMS_PER_CALL + 1);
+    float4 *s_col = reinterpret_cast<float4 *>(
+        (reinterpret_cast<uintptr_t>(s_bases + HM_MAX_GROOMS_PER_CALL + 1) + 15) & ~(uintptr_t)15);  // 16-byte loads
     int *s_dg = reinterpret_cast<int *>(s_col + ns);
     uint16_t *s_list = reinterpret_cast<uint16_t *>(s_dg + ns);      // staged centre list, then A list
     uint16_t *s_lg = s_list + ((ns + 7) & ~7);                         // tile centre list
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
         }
         s_dg[i] = dg;
         s_fa[i] = fa;
-        s_col[i] = make_float3(0.f, 0.f, 0.f);
+        s_col[i] = make_float4(0.f, 0.f, 0.f, __int_as_float(dg));
     }
     for (int t = tid; t < kFwdTilePx; t += kFwdThreads) s_flag[t] = 3;
     __syncthreads();
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
             tsy = d.tsy;
             iso = d.iso;
         }
-        s_col[i] = c;
+        s_col[i] = make_float4(c.x, c.y, c.z, s_col[i].w);
         const int tx = lx - R, ty = ly - R;
         if (tx >= 0 && tx < kFwdTileW && ty >= 0 && ty < kFwdTileH) {
             const int t = ty * kFwdTileW + tx;
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
         const int t = s_lg[li];
         const int tx = t % kFwdTileW, ty = t / kFwdTileW;
         const int mid = (ty + R) * sw + tx + R;
-        const float3 Cp = s_col[mid];
+        const float3 Cp = make_float3(s_col[mid].x, s_col[mid].y, s_col[mid].z);
         float4 o;
         if (!fp.enabled) {
             o = make_float4(Cp.x, Cp.y, Cp.z, 1.0f);
@@ -303,8 +305,8 @@ cudaError_t launch_resolve_msaa(const CallTable &tab, const CamDev &cam, const L
 size_t resolve_smem_bytes(int radius, int tile_h) {
     const int tile_px = kFwdTileW * tile_h;
     const int sw = kFwdTileW + 2 * radius, sh = tile_h + 2 * radius, ns = sw * sh;
-    size_t b = sizeof(uint64_t) * (HM_MAX_GROOMS_PER_CALL + 1);
-    b += sizeof(float3) * ns;
+    size_t b = sizeof(uint64_t) * (HM_MAX_GROOMS_PER_CALL + 1) + 16;   // + alignment of the float4 array
+    b += sizeof(float4) * ns;
     b += sizeof(int) * ns;
     b += sizeof(uint16_t) * (((ns + 7) & ~7) + tile_px) + 16;
     b += sizeof(float4) * tile_px;

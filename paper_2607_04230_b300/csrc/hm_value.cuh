@@ -113,7 +113,8 @@ __device__ __forceinline__ float weight_exponent(bool iso, int dx, int dy, float
 // (Eqs. 6-7), plus the strip hit counts of Sec. 3.3.3.  The weights are
 // accumulated relative to the largest one seen so far (online rescaling),
 // so tiny weights far off the strand axis never underflow the normalizer.
-__device__ __forceinline__ Recon reconstruct(const int *s_dg, const uint8_t *s_fa, const float3 *s_col, int sw,
+template <typename ColT>
+__device__ __forceinline__ Recon reconstruct(const int *s_dg, const uint8_t *s_fa, const ColT *s_col, int sw,
                                              int lx, int ly, int gx, int gy, int W, int H, int R, int ref, float tsx,
                                              float tsy, bool iso, bool use_color, float3 Cp, const FilterDev &fp) {
     Recon o;
@@ -140,7 +141,7 @@ __device__ __forceinline__ Recon reconstruct(const int *s_dg, const uint8_t *s_f
                 o.ha += fa;
             }
             if (gq && abs(dq - ref) <= fp.drej) {
-                const float3 cq = s_col[idx];
+                const float3 cq = make_float3(s_col[idx].x, s_col[idx].y, s_col[idx].z);
                 const float e = weight_exponent(iso, dx, dy, dpar, perp2, use_color, Cp, cq, fp);
                 if (o.cnt == 0) {
                     o.m = e;
@@ -225,7 +226,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // scaled by log2(e) for ex2.  Empty centre-layer taps hold a large negative
 // depth, so the depth test alone rejects them.
 template <int R, bool kColor>
-__device__ __forceinline__ Recon reconstruct_fast(const int *s_dg, const uint8_t *s_fa, const float3 *s_col, int sw,
+__device__ __forceinline__ Recon reconstruct_fast(const int *s_dg, const uint8_t *s_fa, const float4 *s_col, int sw,
                                                   int lx, int ly, int ref, float tsx, float tsy, bool iso, float3 Cp,
                                                   const FilterDev &fp) {
     constexpr float kL2e = 1.4426950408889634f;
@@ -240,10 +241,9 @@ __device__ __forceinline__ Recon reconstruct_fast(const int *s_dg, const uint8_t
 #pragma unroll
         for (int dx = -R; dx <= R; ++dx) {
             const int idx = row + dx;
-            const int dq = s_dg[idx];
-            const bool ok = abs(dq - ref) <= fp.drej;
+            const float4 cq = s_col[idx];          // rgb, centre depth bits
+            const bool ok = abs(__float_as_int(cq.w) - ref) <= fp.drej;
             cnt += ok ? 1 : 0;
-            const float3 cq = s_col[idx];
             const float dpar = fmaf((float)dy, uy, (float)dx * ux);
             float e = fmaf(dpar * a, dpar, (float)(dx * dx + dy * dy) * b);
             if (kColor) {
@@ -270,7 +270,7 @@ __device__ __forceinline__ Recon reconstruct_fast(const int *s_dg, const uint8_t
 
 // reconstruct_fast<R, kColor> for a runtime radius 0..HM_MAX_FILTER_RADIUS.
 template <bool kColor>
-__device__ __forceinline__ Recon reconstruct_fast_r(int R, const int *s_dg, const uint8_t *s_fa, const float3 *s_col,
+__device__ __forceinline__ Recon reconstruct_fast_r(int R, const int *s_dg, const uint8_t *s_fa, const float4 *s_col,
                                                     int sw, int lx, int ly, int ref, float tsx, float tsy, bool iso,
                                                     float3 Cp, const FilterDev &fp) {
     switch (R) {
