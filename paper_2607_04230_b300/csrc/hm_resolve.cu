@@ -40,13 +40,13 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
     extern __shared__ __align__(16) unsigned char smem[];
     const int R = fp.enabled ? fp.radius : 0;
     const int sw = kFwdTileW + 2 * R, sh = kFwdTileH + 2 * R, ns = sw * sh;
-    // shared layout: bases | s_col[ns] (rgb + centre depth bits) | s_dg[ns] | s_list[ns] | s_lg[tile] |
+    // shared layout: bases | s_col[ns] (rgb + centre depth bits) | s_list[ns] | s_lg[tile] |
     // s_out[tile] | s_ts[tile] | s_flag[tile] | s_fa[ns]
     uint64_t *s_bases = reinterpret_cast<uint64_t *>(smem);
     float4 *s_col = reinterpret_cast<float4 *>(
         (reinterpret_cast<uintptr_t>(s_bases + HM_MAX_GROOMS_PER_CALL + 1) + 15) & ~(uintptr_t)15);  // 16-byte loads
-    int *s_dg = reinterpret_cast<int *>(s_col + ns);
-    uint16_t *s_list = reinterpret_cast<uint16_t *>(s_dg + ns);      // staged centre list, then A list
+    uint16_t *s_list = reinterpret_cast<uint16_t *>(s_col + ns);     // staged centre list, then A list
+    auto dg_at = [&](int i) { return __float_as_int(s_col[i].w); };    // staged centre depth
     uint16_t *s_lg = s_list + ((ns + 7) & ~7);                         // tile centre list
     float4 *s_out = reinterpret_cast<float4 *>(
         (reinterpret_cast<uintptr_t>(s_lg + kFwdTilePx) + 15) & ~(uintptr_t)15);  // centre result (rgb, alpha)
@@ -84,7 +84,6 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
             }
             fa = !key_empty(ka);
         }
-        s_dg[i] = dg;
         s_fa[i] = fa;
         s_col[i] = make_float4(0.f, 0.f, 0.f, __int_as_float(dg));
     }
@@ -141,7 +140,7 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
         const int gx = x0 + tx, gy = y0 + ty;
         const bool in = gx < W && gy < H;
         const int mid = (ty + R) * sw + tx + R;
-        const int dgP = in ? s_dg[mid] : -1;
+        const int dgP = in ? dg_at(mid) : -1;
         const bool gP = dgP >= 0, aP = in && s_fa[mid] != 0;
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, gP);
         int wbase = 0;
@@ -176,7 +175,7 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
             o = make_float4(Cp.x, Cp.y, Cp.z, 1.0f);
         } else {
             const float2 ts = s_ts[t];
-            const Recon rg = reconstruct_fast_r<true>(R, s_dg, s_fa, s_col, sw, tx, ty, s_dg[mid], ts.x, ts.y,
+            const Recon rg = reconstruct_fast_r<true>(R, s_fa, s_col, sw, tx, ty, dg_at(mid), ts.x, ts.y,
                                                       (s_flag[t] & 1) != 0, Cp, fp);
             const float invW = 1.0f / rg.W;
             o = make_float4(rg.S.x * invW, rg.S.y * invW, rg.S.z * invW, __fdiv_rn((float)rg.hc, (float)rg.ha));
@@ -207,12 +206,13 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
         }
         const int dA = (int)(ka >> 40);
         const float3 z = make_float3(0.f, 0.f, 0.f);
-        Recon ra = reconstruct_fast_r<false>(R, s_dg, s_fa, s_col, sw, tx, ty, dA, tsx, tsy, iso, z, fp);
+        Recon ra = reconstruct_fast_r<false>(R, s_fa, s_col, sw, tx, ty, dA, tsx, tsy, iso, z, fp);
         if (ra.cnt > 0 && ra.W < 1e-20f)
-            ra = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, tsx, tsy, iso, false, z, fp);
+            ra = reconstruct(static_cast<const int *>(nullptr), s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, tsx, tsy,
+                             iso, false, z, fp);
         const int mid = (ty + R) * sw + tx + R;
         float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (s_dg[mid] >= 0) {               // depth mismatch: blend over the centre result, alpha 1
+        if (dg_at(mid) >= 0) {              // depth mismatch: blend over the centre result, alpha 1
             const float4 cg = s_out[t];
             float3 c = make_float3(cg.x, cg.y, cg.z);
             if (ra.cnt > 0) {
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, Cam
         const int gx = x0 + tx, gy = y0 + ty;
         if (gx >= W || gy >= H) continue;
         const int mid = (ty + R) * sw + tx + R;
-        const bool written = s_dg[mid] >= 0 || (s_flag[t] & 4);
+        const bool written = dg_at(mid) >= 0 || (s_flag[t] & 4);
         rgba[(int64_t)gy * W + gx] = written ? s_out[t] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
@@ -307,7 +307,6 @@ size_t resolve_smem_bytes(int radius, int tile_h) {
     const int sw = kFwdTileW + 2 * radius, sh = tile_h + 2 * radius, ns = sw * sh;
     size_t b = sizeof(uint64_t) * (HM_MAX_GROOMS_PER_CALL + 1) + 16;   // + alignment of the float4 array
     b += sizeof(float4) * ns;
-    b += sizeof(int) * ns;
     b += sizeof(uint16_t) * (((ns + 7) & ~7) + tile_px) + 16;
     b += sizeof(float4) * tile_px;
     b += sizeof(float2) * tile_px;

@@ -113,6 +113,11 @@ __device__ __forceinline__ float weight_exponent(bool iso, int dx, int dy, float
 // (Eqs. 6-7), plus the strip hit counts of Sec. 3.3.3.  The weights are
 // accumulated relative to the largest one seen so far (online rescaling),
 // so tiny weights far off the strand axis never underflow the normalizer.
+// Staged centre-layer depth of tap i: a separate int array, or the depth
+// bits packed into the colour record's w.
+__device__ __forceinline__ int tap_depth(const int *s_dg, const float3 *, int i) { return s_dg[i]; }
+__device__ __forceinline__ int tap_depth(const int *, const float4 *s_col, int i) { return __float_as_int(s_col[i].w); }
+
 template <typename ColT>
 __device__ __forceinline__ Recon reconstruct(const int *s_dg, const uint8_t *s_fa, const ColT *s_col, int sw,
                                              int lx, int ly, int gx, int gy, int W, int H, int R, int ref, float tsx,
@@ -130,7 +135,7 @@ __device__ __forceinline__ Recon reconstruct(const int *s_dg, const uint8_t *s_f
         const int row = (ly + dy + R) * sw + R + lx;
         for (int dx = -R; dx <= R; ++dx) {
             const int idx = row + dx;
-            const int dq = s_dg[idx];
+            const int dq = tap_depth(s_dg, s_col, idx);
             const int fa = s_fa[idx];
             if (dq < 0 && fa == 0) continue;
             float dpar, perp2;
@@ -187,12 +192,12 @@ __device__ __forceinline__ Recon reconstruct(const int *s_dg, const uint8_t *s_f
 // k slope + hw sqrt(2) + 0.01] are candidates (0.01 px covers the binary32
 // rounding of slope and of the test); each candidate then takes the exact
 // test of in_strip, so the counts equal a full-window scan.
-__device__ __forceinline__ int2 strip_counts(const int *s_dg, const uint8_t *s_fa, int sw, int lx, int ly, int R,
+__device__ __forceinline__ int2 strip_counts(const float4 *s_col, const uint8_t *s_fa, int sw, int lx, int ly, int R,
                                              float tsx, float tsy, bool iso, const FilterDev &fp) {
     int hc = 0, ha = 0;
     if (iso) {
         const int idx = (ly + R) * sw + lx + R;
-        return make_int2(s_dg[idx] >= 0 ? 1 : 0, s_fa[idx] ? 1 : 0);
+        return make_int2(__float_as_int(s_col[idx].w) >= 0 ? 1 : 0, s_fa[idx] ? 1 : 0);
     }
     const bool xmaj = fabsf(tsx) >= fabsf(tsy);
     const float slope = xmaj ? tsy / tsx : tsx / tsy;
@@ -205,7 +210,7 @@ __device__ __forceinline__ int2 strip_counts(const int *s_dg, const uint8_t *s_f
             float dpar, perp2;
             if (!in_strip(false, tsx, tsy, dx, dy, fp.hw2, dpar, perp2)) continue;
             const int idx = (ly + dy + R) * sw + lx + dx + R;
-            hc += s_dg[idx] >= 0 ? 1 : 0;
+            hc += __float_as_int(s_col[idx].w) >= 0 ? 1 : 0;
             ha += s_fa[idx] ? 1 : 0;
         }
     }
@@ -226,7 +231,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // scaled by log2(e) for ex2.  Empty centre-layer taps hold a large negative
 // depth, so the depth test alone rejects them.
 template <int R, bool kColor>
-__device__ __forceinline__ Recon reconstruct_fast(const int *s_dg, const uint8_t *s_fa, const float4 *s_col, int sw,
+__device__ __forceinline__ Recon reconstruct_fast(const uint8_t *s_fa, const float4 *s_col, int sw,
                                                   int lx, int ly, int ref, float tsx, float tsy, bool iso, float3 Cp,
                                                   const FilterDev &fp) {
     constexpr float kL2e = 1.4426950408889634f;
@@ -257,7 +262,7 @@ __device__ __forceinline__ Recon reconstruct_fast(const int *s_dg, const uint8_t
             Wt += w;
         }
     }
-    const int2 h = strip_counts(s_dg, s_fa, sw, lx, ly, R, tsx, tsy, iso, fp);
+    const int2 h = strip_counts(s_col, s_fa, sw, lx, ly, R, tsx, tsy, iso, fp);
     Recon o;
     o.S = make_float3(Sx, Sy, Sz);
     o.W = Wt;
@@ -270,15 +275,15 @@ __device__ __forceinline__ Recon reconstruct_fast(const int *s_dg, const uint8_t
 
 // reconstruct_fast<R, kColor> for a runtime radius 0..HM_MAX_FILTER_RADIUS.
 template <bool kColor>
-__device__ __forceinline__ Recon reconstruct_fast_r(int R, const int *s_dg, const uint8_t *s_fa, const float4 *s_col,
+__device__ __forceinline__ Recon reconstruct_fast_r(int R, const uint8_t *s_fa, const float4 *s_col,
                                                     int sw, int lx, int ly, int ref, float tsx, float tsy, bool iso,
                                                     float3 Cp, const FilterDev &fp) {
     switch (R) {
 #define HM_RF(r) \
-    case r: return reconstruct_fast<r, kColor>(s_dg, s_fa, s_col, sw, lx, ly, ref, tsx, tsy, iso, Cp, fp);
+    case r: return reconstruct_fast<r, kColor>(s_fa, s_col, sw, lx, ly, ref, tsx, tsy, iso, Cp, fp);
         HM_RF(0) HM_RF(1) HM_RF(2) HM_RF(3) HM_RF(4) HM_RF(5) HM_RF(6) HM_RF(7)
 #undef HM_RF
-        default: return reconstruct_fast<8, kColor>(s_dg, s_fa, s_col, sw, lx, ly, ref, tsx, tsy, iso, Cp, fp);
+        default: return reconstruct_fast<8, kColor>(s_fa, s_col, sw, lx, ly, ref, tsx, tsy, iso, Cp, fp);
     }
 }
 
