@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kLodThreads) lod_kernel(CallTable tab, CamDev 
 // by a prefix sum, and each item tests its 2-4 minor-axis pixels with the
 // exact predicate and issues the 64-bit atomicMin for each layer.
 // ---------------------------------------------------------------------------
-struct SegRec {
+struct __align__(16) SegRec {
     int32_t uA, vA;              // start point in the major (u) / minor (v) frame, 1/256 px
     int32_t du, dv;              // B - A in that frame
     int32_t umin, umax, vmin, vmax;
@@ -212,7 +212,9 @@ struct SegRec {
     uint32_t id_lo, id_hi;       // payload strand << 7 | segment; compressed: j, C - 1
     uint32_t cgb_hi;             // compressed: payload bits 39..12 (tangent, u, v) >> 12
     float aoA, dao;              // compressed: AO at A, AO(B) - AO(A)
+    uint32_t pad_[3];            // 96 bytes: read back with 16-byte loads
 };
+static_assert(sizeof(SegRec) == 96, "SegRec is read as six 16-byte words");
 
 constexpr int kRasterThreads = 256;
 constexpr int kRasterWarps = kRasterThreads / 32;
@@ -236,19 +238,22 @@ __device__ __forceinline__ uint64_t compressed_payload(const SegRec &q, float t)
 }
 
 template <typename I, bool kPrecheck, bool kCgb>
-__device__ __forceinline__ void raster_item(const SegRec &q, int i, int W, int H, uint64_t *__restrict__ vis_c,
-                                            uint64_t *__restrict__ vis_a, uint32_t &n_cons, uint32_t &n_cen) {
+__device__ __forceinline__ void raster_item(const SegRec &q_shared, int i, int W, int H,
+                                            uint64_t *__restrict__ vis_c, uint64_t *__restrict__ vis_a,
+                                            uint32_t &n_cons, uint32_t &n_cen) {
+    const SegRec q = q_shared;
     const bool xm = q.flags & 1;
     const int32_t ua = max(256 * i, q.umin), ub = min(256 * i + 256, q.umax);
     const float va = (float)(ua - q.uA) * q.slope, vb = (float)(ub - q.uA) * q.slope;
     const float flo = floorf(fminf(va, vb)), fhi = ceilf(fmaxf(va, vb));
-    // float error of the minor range is below |dV| 2^-21 + 1 unit
+    // float error of the minor range is below |dV| 2^-21 + 1 unit; with
+    // |vA| <= 2^28 (guard band) and |slope| <= 1 every term fits 32 bits
     const int32_t slack = 8 + (abs(q.dv) >> 20);
-    const int64_t vlo = (int64_t)q.vA + (int64_t)flo - slack;
-    const int64_t vhi = (int64_t)q.vA + (int64_t)fhi + slack;
+    const int32_t vlo = q.vA + (int32_t)flo - slack;
+    const int32_t vhi = q.vA + (int32_t)fhi + slack;
     const int dimv = xm ? H : W;
-    const int mlo = (int)max(((vlo + 255) >> 8) - 1, (int64_t)0);
-    const int mhi = (int)min(vhi >> 8, (int64_t)(dimv - 1));
+    const int mlo = max(((vlo + 255) >> 8) - 1, 0);
+    const int mhi = min(vhi >> 8, dimv - 1);
     if (mlo > mhi) return;
     const int32_t cu = 256 * i + 128;
     const I ru = (I)(cu - q.uA), rv = (I)(256 * mlo + 128 - q.vA);
@@ -277,7 +282,7 @@ __device__ __forceinline__ void raster_item(const SegRec &q, int i, int W, int H
         d24 = d24 > 16777215u ? 16777215u : d24;
         const uint64_t key = ((uint64_t)d24 << 40) | (kCgb ? compressed_payload(q, t) : id);
         const int px = xm ? i : m, py = xm ? m : i;
-        const size_t p = (size_t)py * (size_t)W + (size_t)px;
+        const uint32_t p = (uint32_t)py * (uint32_t)W + (uint32_t)px;   // < 2^28 pixels
         n_cons += 1;
         n_cen += cen;
         if (!kPrecheck || key < __ldcg(reinterpret_cast<const unsigned long long *>(vis_a + p)))
