@@ -2,6 +2,7 @@
 // (arXiv 2607.04230, Sec. 3.1-3.2): clear, LOD pre-pass with the device work
 // list, and the strand-generation + 64-bit atomicMin rasterizer.
 #include <cstdint>
+#include <type_traits>
 #include <cstdlib>
 #include <cuda_runtime.h>
 
@@ -252,8 +253,10 @@ __device__ __forceinline__ void raster_item(const SegRec &q_shared, int i, int W
     const int32_t vlo = q.vA + (int32_t)flo - slack;
     const int32_t vhi = q.vA + (int32_t)fhi + slack;
     const int dimv = xm ? H : W;
-    const int mlo = max(((vlo + 255) >> 8) - 1, 0);
-    const int mhi = min(vhi >> 8, dimv - 1);
+    // rows whose conservative box can meet the line, and whose box overlaps
+    // the segment's minor extent: vmin <= 256 m + 256 and vmax >= 256 m
+    const int mlo = max(max(((vlo + 255) >> 8) - 1, (q.vmin - 1) >> 8), 0);
+    const int mhi = min(min(vhi >> 8, q.vmax >> 8), dimv - 1);
     if (mlo > mhi) return;
     const int32_t cu = 256 * i + 128;
     const I ru = (I)(cu - q.uA), rv = (I)(256 * mlo + 128 - q.vA);
@@ -266,12 +269,12 @@ __device__ __forceinline__ void raster_item(const SegRec &q_shared, int i, int W
     const bool ucen = (q.umin <= cu + q.hc) && (q.umax >= cu - q.hc);
     const uint64_t id = ((uint64_t)q.id_hi << 32) | q.id_lo;
     const bool degenerate = (q.du == 0 && q.dv == 0);
+    typedef typename std::make_unsigned<I>::type U;
     for (int m = mlo; m <= mhi; ++m, e0 += de, num += dn) {
         const int32_t cv = 256 * m + 128;
-        // conservative: v-overlap (u-overlap holds by construction) and line test
-        if (q.vmin > cv + 128 || q.vmax < cv - 128) continue;
-        if (e0 > k_cons || e0 < -k_cons) continue;
-        const bool cen = ucen && q.vmin <= cv + q.hc && q.vmax >= cv - q.hc && e0 <= k_cen && e0 >= -k_cen;
+        // conservative line test |e0| <= k_cons (the overlaps hold by the row range)
+        if ((U)(e0 + k_cons) > (U)(2 * k_cons)) continue;
+        const bool cen = ucen && q.vmin <= cv + q.hc && q.vmax >= cv - q.hc && (U)(e0 + k_cen) <= (U)(2 * k_cen);
         float t = 0.0f;
         if (!degenerate) {
             const float fn = sizeof(I) == 4 ? __int2float_rn((int32_t)num) : __ll2float_rn((int64_t)num);
