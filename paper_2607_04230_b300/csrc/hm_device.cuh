@@ -175,7 +175,7 @@ template <int N>
 __device__ __forceinline__ void control_pts(const GroomDev &g, const Root &r, int C, int j0, float3 (&out)[N]) {
     const int L = g.L;
     int kcur = -1;
-    float3 P0 = make_float3(0.f, 0.f, 0.f), P1 = P0, m0 = P0, m1 = P0;
+    float3 P0 = make_float3(0.f, 0.f, 0.f), P1 = P0, m0 = P0, m1 = P0, Pm = P0, P2 = P0, t0 = P0, t1 = P0;
 #pragma unroll
     for (int c = 0; c < N; ++c) {
         int j = j0 + c;
@@ -184,12 +184,22 @@ __device__ __forceinline__ void control_pts(const GroomDev &g, const Root &r, in
         int k = x / (C - 1);
         if (k > L - 2) k = L - 2;
         if (k != kcur) {
-            P0 = layer_pt(g, r, k);
-            P1 = layer_pt(g, r, k + 1);
-            const float3 Pm = (k > 0) ? layer_pt(g, r, k - 1) : P0;
-            const float3 P2 = (k + 2 <= L - 1) ? layer_pt(g, r, k + 2) : P1;
-            const float3 t0 = fd_tangent(k, L, Pm, P0, P1);
-            const float3 t1 = fd_tangent(k + 1, L, P0, P1, P2);
+            if (kcur >= 0 && k == kcur + 1) {
+                // next interval: its first layer point, the one before it and
+                // its first tangent are the previous interval's (the same
+                // values from the same operations)
+                Pm = P0;
+                P0 = P1;
+                P1 = P2;
+                t0 = t1;
+            } else {
+                P0 = layer_pt(g, r, k);
+                P1 = layer_pt(g, r, k + 1);
+                Pm = (k > 0) ? layer_pt(g, r, k - 1) : P0;
+                t0 = fd_tangent(k, L, Pm, P0, P1);
+            }
+            P2 = (k + 2 <= L - 1) ? layer_pt(g, r, k + 2) : P1;
+            t1 = fd_tangent(k + 1, L, P0, P1, P2);
             const float ell = __fsqrt_rn(v3len2(v3sub(P1, P0)));
             m0 = make_float3(fmul(t0.x, ell), fmul(t0.y, ell), fmul(t0.z, ell));
             m1 = make_float3(fmul(t1.x, ell), fmul(t1.y, ell), fmul(t1.z, ell));
