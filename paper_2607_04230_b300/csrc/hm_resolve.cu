@@ -31,7 +31,7 @@ constexpr int kNoDepth = -(1 << 30);
 // reads it alone: position from depth, tangent from its code, albedo from
 // the appearance table at (u, v) scaled along w, AO from its code.
 template <int kFwdTileH, bool kCgb>
-__global__ void __launch_bounds__(kFwdThreads) resolve_kernel(CallTable tab, CamDev cam, LightsDev Ls, FilterDev fp,
+__global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, CamDev cam, LightsDev Ls, FilterDev fp,
                                                               const uint64_t *__restrict__ vis_c,
                                                               const uint64_t *__restrict__ vis_a,
                                                               float4 *__restrict__ rgba, uint32_t *status,
