@@ -455,32 +455,36 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
 // Sample boxes reach at most 7/16 + 1/2 px from the pixel centre, so the
 // candidate pixels of a segment are taken one pixel wider on each side.
 // ---------------------------------------------------------------------------
-template <int N>
-__device__ __forceinline__ void raster_item_msaa(const SegRec &q, int i, int W, int H, uint64_t *__restrict__ vis_s,
-                                                 int64_t npx, uint32_t &n_hits) {
+template <typename I, int N>
+__device__ __forceinline__ void raster_item_msaa(const SegRec &q_shared, int i, int W, int H,
+                                                 uint64_t *__restrict__ vis_s, int64_t npx, uint32_t &n_hits) {
+    const SegRec q = q_shared;
     const bool xm = q.flags & 1;
     const int32_t cu = 256 * i + 128;
     const int32_t ua = max(cu - 256, q.umin), ub = min(cu + 256, q.umax);
     if (ua > ub) return;
     const float va = (float)(ua - q.uA) * q.slope, vb = (float)(ub - q.uA) * q.slope;
     const float flo = floorf(fminf(va, vb)), fhi = ceilf(fmaxf(va, vb));
+    // 32-bit bounds as in raster_column (guard band, |slope| <= 1)
     const int32_t slack = 8 + (abs(q.dv) >> 20);
-    const int64_t vlo = (int64_t)q.vA + (int64_t)flo - slack;
-    const int64_t vhi = (int64_t)q.vA + (int64_t)fhi + slack;
+    const int32_t vlo = q.vA + (int32_t)flo - slack;
+    const int32_t vhi = q.vA + (int32_t)fhi + slack;
     const int dimv = xm ? H : W;
     // rows m whose sample points (within 240/256 px of the centre) can reach [vlo, vhi]
-    const int mlo = (int)max(((vlo - 368 + 255) >> 8), (int64_t)0);
-    const int mhi = (int)min((vhi + 112) >> 8, (int64_t)(dimv - 1));
-    const int64_t du = q.du, dv = q.dv;
-    const int64_t k_cen = (int64_t)q.hc * ((int64_t)abs(q.du) + (int64_t)abs(q.dv));
+    const int mlo = max((vlo - 368 + 255) >> 8, 0);
+    const int mhi = min((vhi + 112) >> 8, dimv - 1);
+    // I: 32-bit for short segments (|dU|, |dV| < 2^14), whose cross products
+    // and numerators at the candidate samples stay below 2^30
+    const I du = q.du, dv = q.dv;
+    const I k_cen = (I)q.hc * ((I)abs(q.du) + (I)abs(q.dv));
     const uint64_t id = ((uint64_t)q.id_hi << 32) | q.id_lo;
     const bool degenerate = (q.du == 0 && q.dv == 0);
     for (int m = mlo; m <= mhi; ++m) {
         const int32_t cv = 256 * m + 128;
-        const int64_t e0 = du * (int64_t)(cv - q.vA) - dv * (int64_t)(cu - q.uA);
-        const int64_t num0 = (int64_t)(cu - q.uA) * du + (int64_t)(cv - q.vA) * dv;
+        const I e0 = du * (I)(cv - q.vA) - dv * (I)(cu - q.uA);
+        const I num0 = (I)(cu - q.uA) * du + (I)(cv - q.vA) * dv;
         const int px = xm ? i : m, py = xm ? m : i;
-        const int64_t p = (int64_t)py * W + px;
+        const int64_t p = (int64_t)((uint32_t)py * (uint32_t)W + (uint32_t)px);
 #pragma unroll
         for (int k = 0; k < N; ++k) {
             int ox, oy;
@@ -488,10 +492,14 @@ __device__ __forceinline__ void raster_item_msaa(const SegRec &q, int i, int W, 
             const int32_t ou = xm ? ox : oy, ov = xm ? oy : ox;
             const int32_t su = cu + ou, sv = cv + ov;
             if (q.umin > su + q.hc || q.umax < su - q.hc || q.vmin > sv + q.hc || q.vmax < sv - q.hc) continue;
-            const int64_t ek = e0 + du * ov - dv * ou;
+            const I ek = e0 + du * (I)ov - dv * (I)ou;
             if (ek > k_cen || ek < -k_cen) continue;
             float t = 0.0f;
-            if (!degenerate) t = fclamp(fdiv(__ll2float_rn(num0 + ou * du + ov * dv), q.fden), 0.0f, 1.0f);
+            if (!degenerate) {
+                const I nk = num0 + (I)ou * du + (I)ov * dv;
+                const float fn = sizeof(I) == 4 ? __int2float_rn((int32_t)nk) : __ll2float_rn((int64_t)nk);
+                t = fclamp(fdiv(fn, q.fden), 0.0f, 1.0f);
+            }
             const float z = fclamp(fadd(q.zA, fmul(q.dz, t)), 0.0f, 1.0f);
             uint32_t d24 = (uint32_t)floorf(fmul(z, 16777216.0f));
             d24 = d24 > 16777215u ? 16777215u : d24;
@@ -566,7 +574,7 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_msaa_kernel(CallTabl
                 const int64_t dX = (int64_t)B.X - A.X, dY = (int64_t)B.Y - A.Y;
                 r.fden = __ll2float_rn(dX * dX + dY * dY);
                 r.slope = r.du == 0 ? 0.0f : (float)r.dv / (float)r.du;
-                r.flags = xm ? 1 : 0;
+                r.flags = (xm ? 1 : 0) | ((abs(r.du) < (1 << 14) && abs(r.dv) < (1 << 14)) ? 2 : 0);
                 const int du = xm ? W : H, dv = xm ? H : W;
                 int ilo = ((r.umin + 255) >> 8) - 2, ihi = (r.umax >> 8) + 1;
                 ilo = max(ilo, 0);
@@ -596,7 +604,10 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_msaa_kernel(CallTabl
             }
             if (item >= items) continue;
             const SegRec &q = rec[src];
-            raster_item_msaa<N>(q, q.ilo + (item - q.start), W, H, vis_s, npx, n_hits);
+            if (q.flags & 2)
+                raster_item_msaa<int32_t, N>(q, q.ilo + (item - q.start), W, H, vis_s, npx, n_hits);
+            else
+                raster_item_msaa<int64_t, N>(q, q.ilo + (item - q.start), W, H, vis_s, npx, n_hits);
         }
         __syncwarp();
     }
