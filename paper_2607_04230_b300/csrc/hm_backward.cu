@@ -56,7 +56,8 @@ __device__ __forceinline__ void scatter_layer_point(const Sink &sk, const Root &
 
 // Adjoint of control point j (Hermite with chord-scaled finite-difference
 // tangents) to its layer points and on to the layer vertices.
-__device__ void control_point_adjoint(const GroomDev &g, const Root &r, int C, int j, float3 dp, const Sink &sk) {
+__device__ __noinline__ void control_point_adjoint(const GroomDev &g, const Root &r, int C, int j, float3 dp,
+                                                   const Sink &sk) {
     if (dp.x == 0.f && dp.y == 0.f && dp.z == 0.f) return;
     const int L = g.L;
     const int x = j * (L - 1);
@@ -455,7 +456,7 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_adjoint_kernel(
 // the strand geometry to the layer vertices, and the albedo gradient.  When
 // every groom's layer-vertex gradient fits, a CTA accumulates it in shared
 // memory and adds it to the global arrays once at the end.
-constexpr int kGeoThreads = 512;
+constexpr int kGeoThreads = 512, kGeoChunk = 4096;
 
 struct GeoLayout {
     int32_t off[HM_MAX_GROOMS_PER_CALL];   // float offset of groom i in the shared copy, -1: none
@@ -479,6 +480,8 @@ __global__ void __launch_bounds__(kGeoThreads) geometry_adjoint_kernel(CallTable
                                                                        uint32_t *status) {
     extern __shared__ __align__(16) float s_g[];
     __shared__ uint64_t s_bases[HM_MAX_GROOMS_PER_CALL + 1];
+    __shared__ uint16_t s_job[2 * kGeoChunk];
+    __shared__ int s_nj;
     if (threadIdx.x <= tab.n) {
         uint64_t b = 0;
         for (int i = 0; i < (int)threadIdx.x; ++i) b += (uint64_t)tab.g[i].S;
@@ -486,59 +489,81 @@ __global__ void __launch_bounds__(kGeoThreads) geometry_adjoint_kernel(CallTable
     }
     for (int i = threadIdx.x; i < lay.total; i += blockDim.x) s_g[i] = 0.f;
     __syncthreads();
+    // Chunks of kGeoChunk pixels: the keys with a gradient (a centre key with
+    // a colour or screen-tangent gradient, a conservative key with a
+    // screen-tangent gradient) are compacted into a job list so whole warps
+    // run the one decode + adjoint path.
     const int64_t npx = (int64_t)cam.W * cam.H;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npx; p += (int64_t)gridDim.x * blockDim.x) {
-        const float4 gc = __ldg(&dC[p]);
-        const float4 gt = __ldg(&dTs[p]);
-        const bool hasC = gc.x != 0.f || gc.y != 0.f || gc.z != 0.f;
-        const bool hasG = gt.x != 0.f || gt.y != 0.f;
-        const bool hasA = gt.z != 0.f || gt.w != 0.f;
-        if (!hasC && !hasG && !hasA) continue;
-        const int px = (int)(p % cam.W), py = (int)(p / cam.W);
-        if (hasC || hasG) {
-            const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + p));
-            if (!key_empty(kg)) {
-                const Decoded d = decode_key(tab, s_bases, cam, kg, px, py, status);
-                if (d.ok) {
-                    const GroomDev &g = tab.g[d.gi];
-                    float3 dX = f3(0.f, 0.f, 0.f), dT = f3(0.f, 0.f, 0.f);
-                    if (hasC) {
-                        const float4 a = __ldg(&g.albedo[d.s]);
-                        float3 dalb;
-                        shade_adjoint(d.X, d.T, f3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt, decoded_ao(g, d),
-                                      receiver_beta(g, Ls, d.s),
-                                      f3(gc.x, gc.y, gc.z), dX, dT, dalb);
-                        float *ga = sinks.galb[d.gi];
-                        if (ga) {
-                            atomicAdd(ga + 3 * d.s + 0, dalb.x);
-                            atomicAdd(ga + 3 * d.s + 1, dalb.y);
-                            atomicAdd(ga + 3 * d.s + 2, dalb.z);
-                        }
-                    }
-                    if (hasG && !d.iso) {
-                        float3 tX, tT;
-                        screen_tangent_adjoint(cam, d.X, d.T, make_float2(gt.x, gt.y), tX, tT);
-                        dX = add3(dX, tX);
-                        dT = add3(dT, tT);
-                    }
-                    const Sink sk = geo_sink(lay, s_g, sinks, d.gi, g.V);
-                    if (sk.glv) geometry_adjoint(g, make_root(g, d.s, __ldg(&g.sface[d.s])), d.C, d.j, d.t, dX, dT, sk);
-                }
+    // about four chunks per CTA (a multiple of the CTA size, at most kGeoChunk)
+    int64_t csz = (npx + 4 * (int64_t)gridDim.x - 1) / (4 * (int64_t)gridDim.x);
+    csz = ((csz + kGeoThreads - 1) / kGeoThreads) * kGeoThreads;
+    const int chunk_px = (int)(csz < kGeoThreads ? kGeoThreads : (csz > kGeoChunk ? kGeoChunk : csz));
+    const int64_t nchunk = (npx + chunk_px - 1) / chunk_px;
+    const int lane = threadIdx.x & 31;
+    for (int64_t chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
+        const int64_t q0 = chunk * chunk_px;
+        if (threadIdx.x == 0) s_nj = 0;
+        __syncthreads();
+        for (int k = threadIdx.x; k < chunk_px; k += kGeoThreads) {
+            const int64_t p = q0 + k;
+            bool jg = false, ja = false;
+            if (p < npx) {
+                const float4 gc = __ldg(&dC[p]);
+                const float4 gt = __ldg(&dTs[p]);
+                jg = (gc.x != 0.f || gc.y != 0.f || gc.z != 0.f || gt.x != 0.f || gt.y != 0.f) &&
+                     !key_empty(__ldg(reinterpret_cast<const unsigned long long *>(vis_c + p)));
+                ja = (gt.z != 0.f || gt.w != 0.f) &&
+                     !key_empty(__ldg(reinterpret_cast<const unsigned long long *>(vis_a + p)));
+            }
+#pragma unroll
+            for (int layer = 0; layer < 2; ++layer) {
+                const bool want = layer ? ja : jg;
+                const unsigned bal = __ballot_sync(0xFFFFFFFFu, want);
+                int base = 0;
+                if (lane == 0 && bal) base = atomicAdd(&s_nj, __popc(bal));
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (want) s_job[base + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)(k | (layer << 15));
             }
         }
-        if (hasA) {
-            const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + p));
-            if (!key_empty(ka)) {
-                const Decoded d = decode_key(tab, s_bases, cam, ka, px, py, status);
-                if (d.ok && !d.iso) {
-                    const GroomDev &g = tab.g[d.gi];
-                    float3 tX, tT;
-                    screen_tangent_adjoint(cam, d.X, d.T, make_float2(gt.z, gt.w), tX, tT);
-                    const Sink sk = geo_sink(lay, s_g, sinks, d.gi, g.V);
-                    if (sk.glv) geometry_adjoint(g, make_root(g, d.s, __ldg(&g.sface[d.s])), d.C, d.j, d.t, tX, tT, sk);
+        __syncthreads();
+        const int nj = s_nj;
+        for (int jj = threadIdx.x; jj < nj; jj += kGeoThreads) {
+            const int e = s_job[jj];
+            const bool cons = (e & 0x8000) != 0;
+            const int64_t p = q0 + (e & 0x7FFF);
+            const int px = (int)(p % cam.W), py = (int)(p / cam.W);
+            const uint64_t key = __ldg(reinterpret_cast<const unsigned long long *>((cons ? vis_a : vis_c) + p));
+            const Decoded d = decode_key(tab, s_bases, cam, key, px, py, status);
+            if (!d.ok) continue;
+            const GroomDev &g = tab.g[d.gi];
+            const float4 gt = __ldg(&dTs[p]);
+            const float2 gts = cons ? make_float2(gt.z, gt.w) : make_float2(gt.x, gt.y);
+            float3 dX = f3(0.f, 0.f, 0.f), dT = f3(0.f, 0.f, 0.f);
+            if (!cons) {
+                const float4 gc = __ldg(&dC[p]);
+                if (gc.x != 0.f || gc.y != 0.f || gc.z != 0.f) {
+                    const float4 a = __ldg(&g.albedo[d.s]);
+                    float3 dalb;
+                    shade_adjoint(d.X, d.T, f3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt, decoded_ao(g, d),
+                                  receiver_beta(g, Ls, d.s), f3(gc.x, gc.y, gc.z), dX, dT, dalb);
+                    float *ga = sinks.galb[d.gi];
+                    if (ga) {
+                        atomicAdd(ga + 3 * d.s + 0, dalb.x);
+                        atomicAdd(ga + 3 * d.s + 1, dalb.y);
+                        atomicAdd(ga + 3 * d.s + 2, dalb.z);
+                    }
                 }
             }
+            if ((gts.x != 0.f || gts.y != 0.f) && !d.iso) {
+                float3 tX, tT;
+                screen_tangent_adjoint(cam, d.X, d.T, gts, tX, tT);
+                dX = add3(dX, tX);
+                dT = add3(dT, tT);
+            }
+            const Sink sk = geo_sink(lay, s_g, sinks, d.gi, g.V);
+            if (sk.glv) geometry_adjoint(g, make_root(g, d.s, __ldg(&g.sface[d.s])), d.C, d.j, d.t, dX, dT, sk);
         }
+        __syncthreads();
     }
     if (lay.total == 0) return;
     __syncthreads();
