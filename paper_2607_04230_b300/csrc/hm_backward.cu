@@ -282,7 +282,7 @@ __device__ __forceinline__ float2 reconstruct_adjoint(const int *s_dg, const flo
     return dTs;
 }
 
-__global__ void __launch_bounds__(kResolveThreads) resolve_adjoint_kernel(
+__global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
     CallTable tab, CamDev cam, LightsDev Ls, FilterDev fp, const uint64_t *__restrict__ vis_c,
     const uint64_t *__restrict__ vis_a, const float4 *__restrict__ grad_rgba, float4 *__restrict__ dC,
     float4 *__restrict__ dTs, uint32_t *status) {
