@@ -35,6 +35,8 @@ if ROOT not in sys.path:
 METRIC = "strand segments rasterized/s (resolved frame, 1 spp)"
 UNIT = "segments/s"
 L2_FLUSH_BYTES = 256 << 20
+# kernels of one frame: clear, LOD select, LOD scan (work list), raster, resolve
+LAUNCHES_PER_FRAME = 5
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 FALLBACK_HBM_GBS = 6400.0
@@ -359,7 +361,7 @@ def run_crowd(args, rank, world, local_rank):
                               "per_character_launches_ms_per_character": ms_pc / n,
                               "speedup": ms_pc / ms_g, "grooms": n},
             "autotune": tune and {"tuning": tune["tuning"], "best_ms": tune["ms"], "candidates": len(tune["table"])},
-            "gpu_launches": 4 * args.steps, "clocks": clk}
+            "gpu_launches": LAUNCHES_PER_FRAME * args.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -481,7 +483,7 @@ def run_grad(args, rank, world, local_rank):
                                    "triangles, 6 layers, 20k strands x 12 segments",
                        "l2": "flushed between timed steps (256 MiB write)"},
             "forward_ms": f_ms, "backward_ms": b_ms, "gradient_steps_per_s": 1e3 / (f_ms + b_ms),
-            "gpu_launches": 7 * args.steps, "clocks": clk}
+            "gpu_launches": (LAUNCHES_PER_FRAME + 3) * args.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -527,7 +529,7 @@ def run_stereo(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
             "config": dict(cfg, workload="stereo: the 1080p groom seen by two eyes 6.4 cm apart"),
             "multiview_ms_per_view": ms_m / 2, "separate_ms_per_view": ms_s / 2, "speedup": ms_s / ms_m,
-            "gpu_launches": 7 * args.steps}
+            "gpu_launches": (LAUNCHES_PER_FRAME + 2) * args.steps}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -578,7 +580,7 @@ def run_msaa(args, rank, world, local_rank):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)",
             "data": "synthetic", "config": dict(cfg, workload="single groom, 1920x1080, multisample reference"),
-            "ms_per_frame": out, "covered_samples": samples, "gpu_launches": 4 * args.steps}
+            "ms_per_frame": out, "covered_samples": samples, "gpu_launches": LAUNCHES_PER_FRAME * args.steps}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -633,7 +635,7 @@ def run_shadow(args, rank, world, local_rank):
                                          "shadow map with the LOD depth correction", lod="on, lambda 1"),
             "ms": {"shadow_map_pass": t_map, "frame_shadowed": t_sh, "frame_unshadowed": t_pl},
             "segments_frame": segs, "segments_map": hm.stats_dict(mstats)["segments"],
-            "gpu_launches": 4 * args.steps}
+            "gpu_launches": LAUNCHES_PER_FRAME * args.steps}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -690,7 +692,7 @@ def run_compressed(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
             "config": dict(cfg, workload="single groom, 1920x1080, compressed G-buffer payload"),
-            "ms": res, "gpu_launches": 4 * args.steps}
+            "ms": res, "gpu_launches": LAUNCHES_PER_FRAME * args.steps}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -818,7 +820,7 @@ def run_native(args, rank, world, local_rank):
             "frame_ms": {k: round(v, 5) for k, v in phase_ms.items()},
             "segments_per_frame": segs, "raster_segments_per_s": segs / t_r,
             "roofline": roofline, "kernels": kernels,
-            "e2e": e2e, "gpu_launches": 4 * args.steps, "clocks": clk, "wall_s": wall,
+            "e2e": e2e, "gpu_launches": LAUNCHES_PER_FRAME * args.steps, "clocks": clk, "wall_s": wall,
             "autotune": tune and {"tuning": tune["tuning"], "best_ms": tune["ms"], "candidates": len(tune["table"])}}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(scene)

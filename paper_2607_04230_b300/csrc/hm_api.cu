@@ -141,6 +141,7 @@ hm_status build_table(const hm_groom *grooms, int32_t n, hm::CallTable &tab) {
         d.lod_enabled = g->lod.enabled;
         d.has_ao = g->has_ao;
         d.uv = g->d_uv;
+        d.max_batches = (uint32_t)g->max_batches;
         base += (uint64_t)g->S;
     }
     if (base > (1ull << 33) - 2) return fail(HM_ERR_CAPACITY, "strand ids exceed 33 bits");

@@ -47,6 +47,7 @@ struct GroomDev {
     int32_t lod_enabled;
     int32_t has_ao;          // layer vertices carry baked ambient occlusion in w
     const float2 *uv;        // [V] scalp texture coordinates, or null (compressed payload)
+    uint32_t max_batches;    // 32-segment batches at full detail (batch_map capacity)
 };
 
 struct CallTable {

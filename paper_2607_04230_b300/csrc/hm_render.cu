@@ -132,59 +132,99 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t &total,
     return off + x - v;
 }
 
-constexpr int kLodThreads = 512;
+// The LOD decision of every bundle, all grooms at once (one thread per
+// bundle): lod[f] = (N_LOD, C, -, segments).
+constexpr int kLodSelThreads = 256;
 
-__global__ void __launch_bounds__(kLodThreads) lod_kernel(CallTable tab, CamDev cam, hm_frame_stats *stats) {
-    __shared__ uint32_t sm[kLodThreads / 32];
-    const GroomDev &g = tab.g[blockIdx.x];
-    uint32_t running = 0;
+__global__ void __launch_bounds__(kLodSelThreads) lod_select_kernel(CallTable tab, CamDev cam,
+                                                                    hm_frame_stats *stats) {
+    const GroomDev &g = tab.g[blockIdx.y];
+    const int f = blockIdx.x * kLodSelThreads + (int)threadIdx.x;
     unsigned long long strands = 0, segs = 0, culled = 0;
-    for (int base = 0; base < g.F; base += kLodThreads) {
-        int f = base + (int)threadIdx.x;
-        int n = 0, c = g.cmax;
-        if (f < g.F) {
-            int nfull = __ldg(&g.faces[f + 1]).w - __ldg(&g.faces[f]).w;
-            if (!g.lod_enabled) {
-                n = nfull;
+    if (f < g.F) {
+        const int nfull = __ldg(&g.faces[f + 1]).w - __ldg(&g.faces[f]).w;
+        int n = nfull, c = g.cmax;
+        if (g.lod_enabled) {
+            float Lf = 0.0f;
+            if (lod_select(g, cam, f, Lf)) {
+                lod_counts(Lf, nfull, __ldg(&g.delta[f]), g.L, g.cmax, n, c);
             } else {
-                float Lf = 0.0f;
-                if (lod_select(g, cam, f, Lf)) {
-                    lod_counts(Lf, nfull, __ldg(&g.delta[f]), g.L, g.cmax, n, c);
-                } else {
-                    n = 0;
-                    culled += 1;
-                }
+                n = 0;
+                culled = 1;
             }
         }
-        uint32_t nseg = (uint32_t)n * (uint32_t)(c - 1);
-        uint32_t nb = (nseg + kSegBatch - 1) / kSegBatch;
-        uint32_t tot;
-        uint32_t first = running + block_excl_scan<kLodThreads>(nb, tot, sm);
-        if (f < g.F) {
-            g.lod[f] = make_uint4((uint32_t)n, (uint32_t)c, first, nseg);
-            for (uint32_t b = 0; b < nb; ++b) g.batch_map[first + b] = (uint32_t)f;
-            strands += (unsigned long long)n;
-            segs += nseg;
-        }
-        running += tot;
-    }
-    if (threadIdx.x == 0) {
-        g.counters[kCtrBatches] = running;
-        if (blockIdx.x == 0) g.counters[kCtrTicket] = 0;
+        const uint32_t nseg = (uint32_t)n * (uint32_t)(c - 1);
+        g.lod[f] = make_uint4((uint32_t)n, (uint32_t)c, 0u, nseg);
+        strands = (unsigned long long)n;
+        segs = nseg;
     }
     if (stats) {
-        // warp-reduce then one atomic per warp
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             strands += __shfl_down_sync(kFull, strands, o);
             segs += __shfl_down_sync(kFull, segs, o);
             culled += __shfl_down_sync(kFull, culled, o);
         }
-        if ((threadIdx.x & 31) == 0) {
+        if ((threadIdx.x & 31) == 0 && (strands | segs | culled)) {
             atomicAdd((unsigned long long *)&stats->strands, strands);
             atomicAdd((unsigned long long *)&stats->segments, segs);
             atomicAdd((unsigned long long *)&stats->bundles_culled, culled);
         }
+    }
+}
+
+// The bundles' first 32-segment batch (exclusive scan of their batch
+// counts) and the batch -> bundle work list the rasterizer pulls from.
+// grid.y = groom, grid.x = slices of kLodFillPerCta batches: every CTA of a
+// groom repeats the (short) scan over its bundles, the first one publishes
+// it, and each fills its slice one batch per thread: batch b belongs to the
+// last bundle whose first batch is <= b (a bundle with no batch shares its
+// first batch with the next one, so the search lands on a bundle with
+// batches).
+constexpr int kLodScanThreads = 1024, kLodScanCache = 12000, kLodFillPerCta = 8192;
+
+__global__ void __launch_bounds__(kLodScanThreads) lod_scan_kernel(CallTable tab) {
+    __shared__ uint32_t sm[kLodScanThreads / 32];
+    __shared__ uint32_t s_first[kLodScanCache + 1];
+    const GroomDev &g = tab.g[blockIdx.y];
+    const bool cache = g.F <= kLodScanCache;
+    const bool lead = blockIdx.x == 0;
+    if (!cache && !lead) return;                  // large meshes: the first CTA fills serially
+    if (!lead && blockIdx.x * (uint32_t)kLodFillPerCta >= g.max_batches) return;   // beyond this groom's list
+    uint32_t running = 0;
+    for (int base = 0; base < g.F; base += kLodScanThreads) {
+        const int f = base + (int)threadIdx.x;
+        uint32_t nb = 0;
+        if (f < g.F) nb = (g.lod[f].w + kSegBatch - 1) / kSegBatch;
+        uint32_t tot;
+        const uint32_t first = running + block_excl_scan<kLodScanThreads>(nb, tot, sm);
+        if (f < g.F) {
+            if (lead) g.lod[f].z = first;
+            if (cache) {
+                s_first[f] = first;
+            } else {
+                for (uint32_t b = 0; b < nb; ++b) g.batch_map[first + b] = (uint32_t)f;
+            }
+        }
+        running += tot;
+    }
+    if (cache) {
+        if (threadIdx.x == 0) s_first[g.F] = running;
+        __syncthreads();
+        const uint32_t b0 = blockIdx.x * (uint32_t)kLodFillPerCta;
+        const uint32_t b1 = min(b0 + (uint32_t)kLodFillPerCta, running);
+        for (uint32_t b = b0 + threadIdx.x; b < b1; b += kLodScanThreads) {
+            int lo = 0, hi = g.F;                 // s_first[lo] <= b < s_first[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_first[mid] <= b) lo = mid; else hi = mid;
+            }
+            g.batch_map[b] = (uint32_t)lo;
+        }
+    }
+    if (lead && threadIdx.x == 0) {
+        g.counters[kCtrBatches] = running;
+        if (blockIdx.y == 0) g.counters[kCtrTicket] = 0;
     }
 }
 
@@ -678,7 +718,14 @@ cudaError_t launch_clear(uint64_t *vis_c, uint64_t *vis_a, int64_t npx, const ui
 }
 
 cudaError_t launch_lod(const CallTable &tab, const CamDev &cam, hm_frame_stats *stats, cudaStream_t st) {
-    lod_kernel<<<tab.n, kLodThreads, 0, st>>>(tab, cam, stats);
+    int fmax = 1;
+    for (int i = 0; i < tab.n; ++i) fmax = tab.g[i].F > fmax ? tab.g[i].F : fmax;
+    const dim3 grid((unsigned)((fmax + kLodSelThreads - 1) / kLodSelThreads), (unsigned)tab.n);
+    lod_select_kernel<<<grid, kLodSelThreads, 0, st>>>(tab, cam, stats);
+    uint32_t bmax = 1;
+    for (int i = 0; i < tab.n; ++i) bmax = tab.g[i].max_batches > bmax ? tab.g[i].max_batches : bmax;
+    const dim3 sgrid((unsigned)((bmax + kLodFillPerCta - 1) / kLodFillPerCta), (unsigned)tab.n);
+    lod_scan_kernel<<<sgrid, kLodScanThreads, 0, st>>>(tab);
     return cudaGetLastError();
 }
 
