@@ -175,9 +175,16 @@ def ncu_traffic(kernel: str, workload: str):
     return e.get("dram_bytes_per_launch")
 
 
-def probe_atomic_peak(torch, hm, n_elems):
+# L2 sectors (32 B) one 64-bit atomicMin of each probe pattern touches:
+# pattern 0, consecutive lanes on consecutive keys, puts four in a sector;
+# pattern 1, multiplicatively hashed addresses, gives every atomic its own
+# sector.  Both saturate the same L2 RED sector rate (ncu, profiles/).
+PROBE_SECTORS_PER_ATOMIC = {0: 0.25, 1: 1.0}
+
+
+def probe_atomic_peak(torch, hm, n_elems, rounds=32):
     """Best 64-bit atomicMin rate (ops/s) of the probe kernel over a buffer of
-    frame size: coalesced distinct addresses and hashed addresses."""
+    frame size for each address pattern (0 coalesced, 1 hashed)."""
     buf = torch.empty(n_elems, dtype=torch.int64, device="cuda")
     best = {}
     for pattern in (0, 1):
@@ -186,13 +193,27 @@ def probe_atomic_peak(torch, hm, n_elems):
             buf.fill_(-1)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            hm.probe_atomic_min(buf, rounds=8, pattern=pattern)
+            hm.probe_atomic_min(buf, rounds=rounds, pattern=pattern)
             b.record()
             b.synchronize()
-            rates.append(n_elems * 8 / (a.elapsed_time(b) * 1e-3))
+            rates.append(n_elems * rounds / (a.elapsed_time(b) * 1e-3))
         best[pattern] = max(rates)
     del buf
     return best
+
+
+def ncu_red_sectors_per_atomic(workload: str):
+    """L2 RED sectors per 64-bit atomicMin of the raster kernel from the
+    committed ncu summary (same kernel sources), else None."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = t.get(workload, {}).get("raster_kernel")
+    if not e or e.get("src_hash") != kernel_src_hash():
+        return None
+    return e.get("red_sectors_per_atomic")
 
 
 # ---------------------------------------------------------------------------
@@ -791,14 +812,22 @@ def run_native(args, rank, world, local_rank):
         return 0
     peaks, peaks_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
-    atom_peak = max(peak_rates.values())
+    # the L2 atomic roofline in the unit the hardware spends: RED sector
+    # operations (a 64-bit atomicMin updates one 32-byte sector; atomics of
+    # one instruction that share a sector share the operation)
+    sector_peak = max(r * PROBE_SECTORS_PER_ATOMIC[p] for p, r in peak_rates.items())
+    spa = ncu_red_sectors_per_atomic(args.workload)
+    spa_note = "ncu-measured" if spa is not None else "assumed one per atomic (no ncu summary for these sources)"
+    spa = spa if spa is not None else 1.0
     t_r = phase_ms["raster"] * 1e-3
     t_s = phase_ms["resolve"] * 1e-3
     res_bytes = 32 * W * H            # both keys read once + RGBA written once
     kernels = {
-        "raster_kernel": {"bound": "l2_atomic", "achieved": atomics / t_r / 1e9, "peak": atom_peak / 1e9,
-                          "unit": "Gatom/s", "ms": phase_ms["raster"],
-                          "work": f"{atomics} covered (pixel, layer) pairs per launch = 64-bit atomicMin ops"},
+        "raster_kernel": {"bound": "l2_atomic", "achieved": atomics * spa / t_r / 1e9, "peak": sector_peak / 1e9,
+                          "unit": "G L2 RED sectors/s", "ms": phase_ms["raster"],
+                          "atomics_per_s": atomics / t_r, "red_sectors_per_atomic": spa,
+                          "work": f"{atomics} covered (pixel, layer) pairs per launch = 64-bit atomicMin ops, "
+                                  f"x {spa:.4f} L2 RED sectors each ({spa_note})"},
         "resolve_kernel": {"bound": "hbm", "achieved": res_bytes / t_s / 1e9, "peak": hbm, "unit": "GB/s",
                            "ms": phase_ms["resolve"], "work": f"{res_bytes} B per launch (32 B/px)"},
     }
@@ -806,10 +835,12 @@ def run_native(args, rank, world, local_rank):
     d = kernels[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
                 "frac": d["achieved"] / d["peak"], "traffic": ncu_traffic(dom, args.workload), "kernel": dom,
-                "peak_source": ("live probe: best 64-bit atomicMin rate of hm_probe_atomic_min over a "
-                                f"{2 * W * H}-element buffer (coalesced {peak_rates[0] / 1e9:.1f}, hashed "
-                                f"{peak_rates[1] / 1e9:.1f} Gatom/s)") if d["bound"] == "l2_atomic"
-                else f"{peaks_kind} hbm_gbs of MEASURED_PEAKS.json",
+                "peak_source": ("live probe hm_probe_atomic_min over a "
+                                f"{2 * W * H}-element buffer: coalesced {peak_rates[0] / 1e9:.1f} Gatom/s "
+                                f"(4 per sector = {peak_rates[0] * 0.25 / 1e9:.1f} G sectors/s), hashed "
+                                f"{peak_rates[1] / 1e9:.1f} Gatom/s (1 per sector); ncu shows both patterns "
+                                "at the same L2 RED sector rate (profiles/l2_red_sector_rate.md)")
+                if d["bound"] == "l2_atomic" else f"{peaks_kind} hbm_gbs of MEASURED_PEAKS.json",
                 "work_per_launch": d["work"]}
     for k in kernels.values():
         k["frac"] = k["achieved"] / k["peak"]
