@@ -123,3 +123,31 @@ def test_baked_ao_frame():
     sc.grooms[0].vert_ao = synth.baked_ao(sc.grooms[0], seed=2)
     sc.lights.ambient = float(np.float32(0.4))
     check_full(sc)
+
+
+@pytest.mark.parametrize("W,H,fovy", [(16384, 6, 0.5), (7, 16384, 170.0)])
+def test_maximum_resolution_edges(W, H, fovy):
+    """The largest frame side the library accepts, in either axis: the
+    32-bit pixel-index and range arithmetic at its limit (a thin slice of
+    the groom fills the long side)."""
+    sc = synth.tiny_scene(17, width=W, height=H, num_strands=400, dist_m=0.35)
+    ctr, _, _ = synth._aabb_center(sc.grooms)
+    sc.camera = synth.make_camera(ctr + np.array([0.0, 0.0, 0.35]), ctr, fovy, W, H)
+    out, _ = check_full(sc, sample=4000)
+    assert (out["vis_a"] != oracle.EMPTY).sum() > 300
+
+
+def test_degenerate_and_near_plane_segments():
+    """Strands collapsed to a point (every layer at the same place: zero-length
+    segments) and a camera whose near plane cuts the groom."""
+    sc = synth.tiny_scene(18, width=96, height=80, num_strands=300, dist_m=0.3)
+    g = sc.grooms[0]
+    g.layer_verts[:] = g.layer_verts[0][None, :, :]
+    out, _ = check_full(sc)
+    assert (out["vis_a"] != oracle.EMPTY).sum() > 0
+    sc2 = synth.tiny_scene(19, width=96, height=80, num_strands=600, dist_m=0.3)
+    ctr, lo, hi = synth._aabb_center(sc2.grooms)
+    sc2.camera = synth.make_camera(ctr + np.array([0.0, 0.0, 0.06]), ctr, 60, 96, 80, near=0.05)
+    for lod in (0, 1):
+        sc2.lod = synth.LodParams(lod, 3.0)
+        check_full(sc2)
