@@ -291,7 +291,8 @@ hm_status hm_create_groom(const hm_groom_desc *d, void *stream, hm_groom *out) {
         int64_t nseg = (int64_t)(first[f + 1] - first[f]) * segs;
         max_batches += (size_t)((nseg + hm::kSegBatch - 1) / hm::kSegBatch);
     }
-    if (max_batches > 0xFFFFFFF0ull) return fail(HM_ERR_CAPACITY, "too many segment batches");
+    if (max_batches > 0xFFFFFFF0ull || (uint64_t)S * (uint64_t)segs > 0xFFFFFF00ull)
+        return fail(HM_ERR_CAPACITY, "too many segments in one groom (32-bit segment index)");
 
     // host-side repack to the device layout
     std::vector<float4> lv((size_t)L * V);

@@ -23,7 +23,7 @@ constexpr float kGuard = 1048576.0f;               // 2^20 px guard band
 constexpr int kSegBatch = 32;                      // segments per warp batch
 
 // Per-groom device counters (one block of words per groom).
-enum CounterWord : int { kCtrBatches = 0, kCtrTicket = 1, kCtrWords = 4 };
+enum CounterWord : int { kCtrBatches = 0, kCtrTicket = 1, kCtrSegs = 2, kCtrWords = 4 };
 
 // Device status bits (read by hm_get_device_status).
 enum StatusBit : uint32_t { kStatusBadKey = 1u, kStatusBadBatch = 2u };
@@ -37,8 +37,8 @@ struct GroomDev {
     const float2 *bary;      // [S] (b1, b2)
     const float4 *albedo;    // [S] rgb
     const float *delta;      // [F] LOD offset of Eq. 1
-    uint4 *lod;              // [F] (N_LOD, C, first batch, segments)
-    uint32_t *batch_map;     // [max_batches] bundle of each 32-segment batch
+    uint4 *lod;              // [F] (N_LOD, C, first segment, segments)
+    uint32_t *batch_map;     // [max_batches] bundle holding the first segment of each 32-segment batch
     uint32_t *counters;      // [kCtrWords]
     int32_t L, V, F, cmax;
     int64_t S;

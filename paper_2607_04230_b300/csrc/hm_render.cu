@@ -173,14 +173,16 @@ __global__ void __launch_bounds__(kLodSelThreads) lod_select_kernel(CallTable ta
     }
 }
 
-// The bundles' first 32-segment batch (exclusive scan of their batch
-// counts) and the batch -> bundle work list the rasterizer pulls from.
-// grid.y = groom, grid.x = slices of kLodFillPerCta batches: every CTA of a
-// groom repeats the (short) scan over its bundles, the first one publishes
-// it, and each fills its slice one batch per thread: batch b belongs to the
-// last bundle whose first batch is <= b (a bundle with no batch shares its
-// first batch with the next one, so the search lands on a bundle with
-// batches).
+// The bundles' first segment (exclusive scan of their drawn segment counts)
+// and the work list the rasterizer pulls from: batches of 32 consecutive
+// segments of the groom in bundle order (one batch may span several
+// bundles, so lanes stay busy when LOD leaves bundles a few segments), each
+// listed with the bundle holding its first segment.  grid.y = groom, grid.x =
+// slices of kLodFillPerCta batches: every CTA of a groom repeats the (short)
+// scan over its bundles, the first one publishes it, and each fills its
+// slice one batch per thread by a binary search over the scan (a bundle
+// without segments shares its first segment with the next one, so the
+// search lands on the bundle that holds the segment).
 constexpr int kLodScanThreads = 1024, kLodScanCache = 12000, kLodFillPerCta = 8192;
 
 __global__ void __launch_bounds__(kLodScanThreads) lod_scan_kernel(CallTable tab) {
@@ -194,38 +196,54 @@ __global__ void __launch_bounds__(kLodScanThreads) lod_scan_kernel(CallTable tab
     uint32_t running = 0;
     for (int base = 0; base < g.F; base += kLodScanThreads) {
         const int f = base + (int)threadIdx.x;
-        uint32_t nb = 0;
-        if (f < g.F) nb = (g.lod[f].w + kSegBatch - 1) / kSegBatch;
+        const uint32_t ns = f < g.F ? g.lod[f].w : 0u;
         uint32_t tot;
-        const uint32_t first = running + block_excl_scan<kLodScanThreads>(nb, tot, sm);
+        const uint32_t first = running + block_excl_scan<kLodScanThreads>(ns, tot, sm);
         if (f < g.F) {
             if (lead) g.lod[f].z = first;
             if (cache) {
                 s_first[f] = first;
-            } else {
-                for (uint32_t b = 0; b < nb; ++b) g.batch_map[first + b] = (uint32_t)f;
+            } else if (ns > 0) {
+                for (uint32_t b = (first + kSegBatch - 1) / kSegBatch; b * kSegBatch < first + ns; ++b)
+                    g.batch_map[b] = (uint32_t)f;
             }
         }
         running += tot;
     }
+    const uint32_t nbatch = (running + kSegBatch - 1) / kSegBatch;
     if (cache) {
         if (threadIdx.x == 0) s_first[g.F] = running;
         __syncthreads();
         const uint32_t b0 = blockIdx.x * (uint32_t)kLodFillPerCta;
-        const uint32_t b1 = min(b0 + (uint32_t)kLodFillPerCta, running);
+        const uint32_t b1 = min(b0 + (uint32_t)kLodFillPerCta, nbatch);
         for (uint32_t b = b0 + threadIdx.x; b < b1; b += kLodScanThreads) {
-            int lo = 0, hi = g.F;                 // s_first[lo] <= b < s_first[hi]
+            const uint32_t x = b * kSegBatch;    // first segment of the batch
+            int lo = 0, hi = g.F;                 // s_first[lo] <= x < s_first[hi]
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
-                if (s_first[mid] <= b) lo = mid; else hi = mid;
+                if (s_first[mid] <= x) lo = mid; else hi = mid;
             }
             g.batch_map[b] = (uint32_t)lo;
         }
     }
     if (lead && threadIdx.x == 0) {
-        g.counters[kCtrBatches] = running;
+        g.counters[kCtrBatches] = nbatch;
+        g.counters[kCtrSegs] = running;
         if (blockIdx.y == 0) g.counters[kCtrTicket] = 0;
     }
+}
+
+// Segment `seg` (0 <= seg < drawn segments of the groom) of the batch whose
+// first segment lies in bundle f0: its bundle f, strand s and segment j.
+__device__ __forceinline__ void batch_segment(const GroomDev &g, uint32_t f0, uint32_t seg, uint32_t &f, int64_t &s,
+                                              int &j, int &C) {
+    f = f0;
+    while (f + 1 < (uint32_t)g.F && g.lod[f + 1].z <= seg) ++f;
+    const uint4 lo = g.lod[f];
+    C = (int)lo.y;
+    const uint32_t sl = seg - lo.z;
+    s = (int64_t)__ldg(&g.faces[f]).w + sl / (uint32_t)(C - 1);
+    j = (int)(sl % (uint32_t)(C - 1));
 }
 
 // ---------------------------------------------------------------------------
@@ -368,20 +386,16 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
         while (gi + 1 < tab.n && s_goff[gi + 1] <= b) ++gi;
         const GroomDev &g = tab.g[gi];
         const uint32_t lb = b - s_goff[gi];
-        const uint32_t f = __ldg(&g.batch_map[lb]);
-        const uint4 lo = g.lod[f];
-        const int C = (int)lo.y;
-        const uint32_t sl = (lb - lo.z) * kSegBatch + lane;
-
-        const bool active = sl < lo.w;
+        const uint32_t seg = lb * kSegBatch + lane;
+        const bool active = seg < g.counters[kCtrSegs];
         int64_t s = 0;
-        int j = 0;
+        int j = 0, C = 2;
+        uint32_t f = 0;
         float3 cp[2];
         uint32_t cgb_hi = 0;
         float aoA = 1.0f, aoB = 1.0f;
         if (active) {
-            s = (int64_t)__ldg(&g.faces[f]).w + sl / (uint32_t)(C - 1);
-            j = (int)(sl % (uint32_t)(C - 1));
+            batch_segment(g, __ldg(&g.batch_map[lb]), seg, f, s, j, C);
             const Root rt = make_root(g, s, f);
             control_pts<2>(g, rt, C, j, cp);
             if (kCgb) {
@@ -581,15 +595,14 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_msaa_kernel(CallTabl
         while (gi + 1 < tab.n && s_goff[gi + 1] <= b) ++gi;
         const GroomDev &g = tab.g[gi];
         const uint32_t lb = b - s_goff[gi];
-        const uint32_t f = __ldg(&g.batch_map[lb]);
-        const uint4 lo = g.lod[f];
-        const int C = (int)lo.y;
-        const uint32_t sl = (lb - lo.z) * kSegBatch + lane;
+        const uint32_t seg = lb * kSegBatch + lane;
         SegRec r;
         int nmaj = 0;
-        if (sl < lo.w) {
-            const int64_t s = (int64_t)__ldg(&g.faces[f]).w + sl / (uint32_t)(C - 1);
-            const int j = (int)(sl % (uint32_t)(C - 1));
+        if (seg < g.counters[kCtrSegs]) {
+            uint32_t f;
+            int64_t s;
+            int j, C;
+            batch_segment(g, __ldg(&g.batch_map[lb]), seg, f, s, j, C);
             float3 cp[2];
             control_pts<2>(g, make_root(g, s, f), C, j, cp);
             const Proj A = project(cam, cp[0]);
