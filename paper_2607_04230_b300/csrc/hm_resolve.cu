@@ -67,7 +67,21 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
         s_count = 0;
         s_ng = 0;
     }
-    __syncthreads();
+    // 0. a tile whose pixels hold no conservative key has nothing to resolve
+    // (no centre key either: centre keys are a subset): write zeros, done
+    bool any = false;
+    for (int t = tid; t < kFwdTilePx; t += kFwdThreads) {
+        const int gx = x0 + t % kFwdTileW, gy = y0 + t / kFwdTileW;
+        if (gx < W && gy < H)
+            any |= !key_empty(__ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx)));
+    }
+    if (!__syncthreads_or(any)) {
+        for (int t = tid; t < kFwdTilePx; t += kFwdThreads) {
+            const int gx = x0 + t % kFwdTileW, gy = y0 + t / kFwdTileW;
+            if (gx < W && gy < H) rgba[(int64_t)gy * W + gx] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        return;
+    }
 
     // 1. stage keys of tile + halo; list staged centre-sample pixels
     for (int i = tid; i < ns; i += kFwdThreads) {
