@@ -141,3 +141,67 @@ def test_tuning_and_range_arguments(L):
     for first, count in ((-1, 1), (0, 0), (1, 2), (2, 1)):
         assert L.hm_render_visibility_range(grooms, 2, first, count, ctypes.byref(cam), fake,
                                             ctypes.c_void_p(2 << 20), None, 1, None, None) == INVALID
+
+
+def test_shadow_and_compressed_entries_reject_bad_arguments(L):
+    """Validation of the shadow-map, compressed-payload and shadowed-lights
+    arguments happens on the host before anything is launched."""
+    sc = synth.tiny_scene(0, num_strands=10)
+    cam = hm.camera_struct(sc.camera)
+    fake, fake2 = ctypes.c_void_p(1 << 20), ctypes.c_void_p(2 << 20)
+    grooms = (ctypes.c_void_p * 1)(1 << 20)
+    bad = hm.camera_struct(sc.camera)
+    bad.width = 0
+    assert L.hm_render_shadow_map(grooms, 1, ctypes.byref(bad), fake, fake2, None, None) == INVALID
+    assert L.hm_render_shadow_map(grooms, 1, ctypes.byref(cam), None, fake2, None, None) == INVALID
+    assert L.hm_render_shadow_map(grooms, 1, ctypes.byref(cam), fake, fake, None, None) == INVALID
+    assert L.hm_render_shadow_map(grooms, 1, ctypes.byref(cam), ctypes.c_void_p((1 << 20) + 8), fake2, None,
+                                  None) == INVALID
+    assert L.hm_render_visibility_compressed(grooms, 1, ctypes.byref(bad), fake, fake2, None, 1, None,
+                                             None) == INVALID
+    lights = hm.lights_struct(sc.lights)
+    f = hm.filter_struct(synth.FilterParams())
+    app = hm.Appearance(None, 0.15, -0.05)
+    assert L.hm_resolve_compressed(ctypes.byref(cam), ctypes.byref(lights), ctypes.byref(f), ctypes.byref(app),
+                                   fake, fake, fake, None, None) == INVALID
+    app = hm.Appearance((1 << 20) + 4, 0.15, -0.05)
+    assert L.hm_resolve_compressed(ctypes.byref(cam), ctypes.byref(lights), ctypes.byref(f), ctypes.byref(app),
+                                   fake, fake, fake, None, None) == INVALID
+    app = hm.Appearance(1 << 20, 0.0, -0.05)
+    assert L.hm_resolve_compressed(ctypes.byref(cam), ctypes.byref(lights), ctypes.byref(f), ctypes.byref(app),
+                                   fake, fake, fake, None, None) == INVALID
+    # shadow maps on the lights: count, light index, duplicates, sigma, camera
+    arr = (hm.ShadowMap * 2)()
+    for i in range(2):
+        arr[i].d_map = 1 << 20
+        arr[i].cam = cam
+        arr[i].light = 0
+        arr[i].sigma = 10.0
+        arr[i].bias_m = 0.0
+        arr[i].depth_correction = 1
+    def lights_with(n, mutate=None):
+        Ls = hm.lights_struct(sc.lights)
+        a = (hm.ShadowMap * 2)()
+        ctypes.memmove(a, arr, ctypes.sizeof(arr))
+        if mutate:
+            mutate(a)
+        Ls.n_shadows = n
+        Ls.shadows = ctypes.cast(a, ctypes.POINTER(hm.ShadowMap))
+        Ls._keep = a
+        return Ls
+    cases = [lights_with(2),                                               # more maps than lights
+             lights_with(1, lambda a: setattr(a[0], "light", 1)),          # light out of range
+             lights_with(1, lambda a: setattr(a[0], "sigma", -1.0)),
+             lights_with(1, lambda a: setattr(a[0], "depth_correction", 2)),
+             lights_with(1, lambda a: setattr(a[0], "d_map", (1 << 20) + 4))]
+    bad_cam_map = lights_with(1)
+    bad_cam_map._keep[0].cam.width = 0
+    cases.append(bad_cam_map)
+    for Ls in cases:
+        assert L.hm_resolve_shade(grooms, 1, ctypes.byref(cam), ctypes.byref(Ls), ctypes.byref(f), fake, fake, fake,
+                                  None, None) == INVALID
+    # shadow maps are not taken by the compressed resolve
+    app = hm.Appearance(1 << 20, 0.15, -0.05)
+    Ls = lights_with(1)
+    assert L.hm_resolve_compressed(ctypes.byref(cam), ctypes.byref(Ls), ctypes.byref(f), ctypes.byref(app),
+                                   fake, fake, fake, None, None) == INVALID
