@@ -230,7 +230,8 @@ struct BwdSinks {
 // Adjoint of one normalized reconstruction R = sum w C / sum w given
 // dL/dR: colour gradients of the contributing neighbours (and of the centre
 // colour through the colour term) into s_dC, returns dL/d(screen tangent).
-__device__ __forceinline__ float2 reconstruct_adjoint(const int *s_dg, const float3 *s_col, float3 *s_dC, int sw,
+template <typename ColT>
+__device__ __forceinline__ float2 reconstruct_adjoint(const int *s_dg, const ColT *s_col, float3 *s_dC, int sw,
                                                       int lx, int ly, int gx, int gy, int W, int H, int R, int ref,
                                                       float tsx, float tsy, bool iso, bool use_color, float3 Cp,
                                                       int mid, const Recon &rc, float3 gR, const FilterDev &fp) {
@@ -247,11 +248,11 @@ __device__ __forceinline__ float2 reconstruct_adjoint(const int *s_dg, const flo
             const int qx = gx + dx;
             if (qx < 0 || qx >= W) continue;
             const int idx = row + dx;
-            const int dq = s_dg[idx];
+            const int dq = tap_depth(s_dg, s_col, idx);
             if (dq < 0 || abs(dq - ref) > fp.drej) continue;
             float dpar, perp2;
             in_strip(iso, tsx, tsy, dx, dy, fp.hw2, dpar, perp2);
-            const float3 cq = s_col[idx];
+            const float3 cq = make_float3(s_col[idx].x, s_col[idx].y, s_col[idx].z);
             const float e = weight_exponent(iso, dx, dy, dpar, perp2, use_color, Cp, cq, fp);
             const float om = __expf(rc.m - e) * invW;      // normalized weight
             const float3 dcq = mul3(gR, om);
@@ -290,10 +291,12 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
     const int R = fp.enabled ? fp.radius : 0;
     const int sw = kTileW + 2 * R, sh = kTileH + 2 * R, ns = sw * sh;
     uint64_t *s_bases = reinterpret_cast<uint64_t *>(smem);
-    float3 *s_col = reinterpret_cast<float3 *>(s_bases + HM_MAX_GROOMS_PER_CALL + 1);
-    float3 *s_dC = s_col + ns;
-    int *s_dg = reinterpret_cast<int *>(s_dC + ns);
-    uint16_t *s_list = reinterpret_cast<uint16_t *>(s_dg + ns);
+    float4 *s_col = reinterpret_cast<float4 *>(
+        (reinterpret_cast<uintptr_t>(s_bases + HM_MAX_GROOMS_PER_CALL + 1) + 15) & ~(uintptr_t)15);  // rgb, centre depth bits
+    float3 *s_dC = reinterpret_cast<float3 *>(s_col + ns);
+    uint16_t *s_list = reinterpret_cast<uint16_t *>(s_dC + ns);
+    auto dg_at = [&](int i) { return __float_as_int(s_col[i].w); };
+    const int *s_dg = nullptr;            // the depth rides in s_col.w
     float2 *s_tsG = reinterpret_cast<float2 *>(
         (reinterpret_cast<uintptr_t>(s_list + ((ns + 7) & ~7)) + 15) & ~(uintptr_t)15);
     float2 *s_tsA = s_tsG + kResolveThreads;
@@ -314,7 +317,7 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
     __syncthreads();
     for (int i = tid; i < ns; i += kResolveThreads) {
         const int gx = x0 - R + i % sw, gy = y0 - R + i / sw;
-        int dg = -1;
+        int dg = -(1 << 30);                 // far below any d24: the depth test alone rejects it
         uint8_t fa = 0;
         if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
             const int64_t p = (int64_t)gy * W + gx;
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
             }
             fa = !key_empty(ka);
         }
-        s_dg[i] = dg;
+        s_col[i] = make_float4(0.f, 0.f, 0.f, __int_as_float(dg));
         s_fa[i] = fa;
         s_dC[i] = f3(0.f, 0.f, 0.f);
     }
@@ -347,7 +350,7 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
             c = shade(d.X, d.T, f3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt, decoded_ao(g, d),
                       receiver_beta(g, Ls, d.s));
         }
-        s_col[i] = c;
+        s_col[i] = make_float4(c.x, c.y, c.z, s_col[i].w);
         const int tx = lx - R, ty = ly - R;
         if (tx >= 0 && tx < kTileW && ty >= 0 && ty < kTileH) {
             const int t = ty * kTileW + tx;
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
         ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx));
         if (fp.enabled && !key_empty(ka)) {
             dA = (int)(ka >> 40);
-            const int dgP = s_dg[mid];
+            const int dgP = dg_at(mid);
             if (dgP < 0 || dA + fp.dmis <= dgP) s_list[atomicAdd(&s_count, 1)] = (uint16_t)tid;
         }
     }
@@ -389,7 +392,7 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
         const float4 g4 = __ldg(&grad_rgba[(int64_t)gy * W + gx]);
         const float3 g = f3(g4.x, g4.y, g4.z);
         const bool nz = g.x != 0.f || g.y != 0.f || g.z != 0.f;
-        const int dG = s_dg[mid];
+        const int dG = dg_at(mid);
         const bool gP = dG >= 0, aP = s_fa[mid];
         if (nz && !fp.enabled) {
             if (gP) {
@@ -398,19 +401,21 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
                 atomicAdd(&s_dC[mid].z, g.z);
             }
         } else if (nz && gP) {
-            const float3 Cp = s_col[mid];
+            const float3 Cp = make_float3(s_col[mid].x, s_col[mid].y, s_col[mid].z);
             const float2 ts = s_tsG[tid];
             const bool isoG = s_isoG[tid] != 0;
-            const Recon rg = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dG, ts.x, ts.y, isoG, true,
-                                         Cp, fp);
+            const Recon rg = reconstruct_fast_r<true>(R, s_fa, s_col, sw, tx, ty, dG, ts.x, ts.y, isoG, Cp, fp);
             float3 gG = g, gA = f3(0.f, 0.f, 0.f);
             Recon ra;
             ra.cnt = 0;
             const bool mism = aP && dA + fp.dmis <= dG;
             if (mism) {
                 const float2 tsa = s_tsA[tid];
-                ra = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y, s_isoA[tid] != 0,
-                                 false, Cp, fp);
+                ra = reconstruct_fast_r<false>(R, s_fa, s_col, sw, tx, ty, dA, tsa.x, tsa.y, s_isoA[tid] != 0,
+                                               f3(0.f, 0.f, 0.f), fp);
+                if (ra.cnt > 0 && ra.W < 1e-20f)
+                    ra = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y,
+                                     s_isoA[tid] != 0, false, Cp, fp);
                 if (ra.cnt > 0) {
                     const float al = (float)ra.hc / (float)ra.ha;
                     gA = mul3(g, al);
@@ -428,8 +433,10 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
             const float2 tsa = s_tsA[tid];
             const bool isoA = s_isoA[tid] != 0;
             const float3 z = f3(0.f, 0.f, 0.f);
-            const Recon ra = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y, isoA,
-                                         false, z, fp);
+            Recon ra = reconstruct_fast_r<false>(R, s_fa, s_col, sw, tx, ty, dA, tsa.x, tsa.y, isoA, z, fp);
+            if (ra.cnt > 0 && ra.W < 1e-20f)
+                ra = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y, isoA, false, z,
+                                 fp);
             dTsA = reconstruct_adjoint(s_dg, s_col, s_dC, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y, isoA, false,
                                        z, mid, ra, g, fp);
         }
@@ -456,7 +463,11 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
 // the strand geometry to the layer vertices, and the albedo gradient.  When
 // every groom's layer-vertex gradient fits, a CTA accumulates it in shared
 // memory and adds it to the global arrays once at the end.
-constexpr int kGeoThreads = 512, kGeoChunk = 4096;
+// 256 threads and four CTAs per SM (a 64-register budget): the decode and
+// adjoint chains are latency-bound, so 32 resident warps beat fewer warps
+// with more registers each (measured: 16 warps at 128 registers were 27%
+// slower at 512x512).
+constexpr int kGeoThreads = 256, kGeoMinBlocks = 4, kGeoChunk = 2048;
 
 struct GeoLayout {
     int32_t off[HM_MAX_GROOMS_PER_CALL];   // float offset of groom i in the shared copy, -1: none
@@ -471,7 +482,7 @@ __device__ __forceinline__ Sink geo_sink(const GeoLayout &lay, float *s_g, const
     return sk;
 }
 
-__global__ void __launch_bounds__(kGeoThreads) geometry_adjoint_kernel(CallTable tab, CamDev cam, LightsDev Ls,
+__global__ void __launch_bounds__(kGeoThreads, kGeoMinBlocks) geometry_adjoint_kernel(CallTable tab, CamDev cam, LightsDev Ls,
                                                                        const uint64_t *__restrict__ vis_c,
                                                                        const uint64_t *__restrict__ vis_a,
                                                                        const float4 *__restrict__ dC,
@@ -586,9 +597,8 @@ __global__ void zero_float4_kernel(float4 *p, int64_t n) {
 
 size_t adjoint_smem_bytes(int radius) {
     const int sw = kTileW + 2 * radius, sh = kTileH + 2 * radius, ns = sw * sh;
-    size_t b = sizeof(uint64_t) * (HM_MAX_GROOMS_PER_CALL + 1);
-    b += 2 * sizeof(float3) * ns;
-    b += sizeof(int) * ns;
+    size_t b = sizeof(uint64_t) * (HM_MAX_GROOMS_PER_CALL + 1) + 16;   // + alignment of s_col
+    b += sizeof(float4) * ns + sizeof(float3) * ns;
     b += sizeof(uint16_t) * ((ns + 7) & ~7) + 16;
     b += sizeof(float2) * 2 * kResolveThreads;
     b += 2 * kResolveThreads;
@@ -597,8 +607,9 @@ size_t adjoint_smem_bytes(int radius) {
 }
 
 // Shared-memory budget for the geometry pass's copy of the layer-vertex
-// gradients; larger sets (big crowds) accumulate straight into global memory.
-constexpr int kGeoSmemFloats = 48 * 1024;
+// gradients, sized so that four CTAs still fit on an SM; larger sets (big
+// grooms, crowds) accumulate straight into global memory.
+constexpr int kGeoSmemFloats = 11 * 1024;
 
 cudaError_t launch_resolve_adjoint(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                                    const uint64_t *vis_c, const uint64_t *vis_a, const float *grad_rgba,
@@ -636,7 +647,7 @@ cudaError_t launch_resolve_adjoint(const CallTable &tab, const CamDev &cam, cons
         tab, cam, Ls, fp, vis_c, vis_a, reinterpret_cast<const float4 *>(grad_rgba), dC, dTs, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    geometry_adjoint_kernel<<<sms, kGeoThreads, (size_t)lay.total * sizeof(float), st>>>(tab, cam, Ls, vis_c, vis_a,
+    geometry_adjoint_kernel<<<sms * kGeoMinBlocks, kGeoThreads, (size_t)lay.total * sizeof(float), st>>>(tab, cam, Ls, vis_c, vis_a,
                                                                                           dC, dTs, sinks, lay, status);
     return cudaGetLastError();
 }

@@ -124,3 +124,12 @@ def test_gradient_with_shadow_map():
     sc.lod = synth.LodParams(1, 3.0)
     lcam = synth.light_camera(sc.grooms, sc.lights.dirs[0], size=160, dist_m=0.5)
     _grad_case(sc, synth.ShadowSpec(light=0, cam=lcam, sigma=200.0, bias_m=0.0005, depth_correction=1))
+
+
+def test_gradient_large_layer_vertex_set():
+    """2,048 scalp triangles x 4 layers: 13,068 layer-vertex gradient floats,
+    more than the geometry pass keeps in shared memory per CTA (11,264), so
+    the gradients accumulate straight into global memory."""
+    sc = synth.tiny_scene(25, width=96, height=80, num_strands=600, dist_m=0.3, k=8, n=4, num_layers=4)
+    assert sc.grooms[0].layer_verts.size > 11 * 1024
+    _grad_case(sc)
