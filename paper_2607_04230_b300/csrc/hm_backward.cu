@@ -108,6 +108,107 @@ __device__ __noinline__ void control_point_adjoint(const GroomDev &g, const Root
     if (hp) scatter_layer_point(sk, r, k + 2, dP2);
 }
 
+// Adjoint of control points j-1 .. j+2 (dp[c] for point j-1+c; points
+// outside [0, C-1] and zero gradients are skipped).  When their layer
+// intervals span at most three consecutive intervals, the six layer points
+// they read are evaluated once, the four control points' layer-point
+// gradients are summed in registers, and each layer point is scattered to
+// its vertices once (instead of once per control point); otherwise each
+// control point takes control_point_adjoint on its own.
+__device__ __forceinline__ float3 pick6(const float3 (&P)[6], int i) {
+    float3 v = P[0];
+#pragma unroll
+    for (int w = 1; w < 6; ++w)
+        if (i == w) v = P[w];
+    return v;
+}
+
+__device__ void control_points_adjoint(const GroomDev &g, const Root &r, int C, int j, const float3 (&dp)[4],
+                                       const Sink &sk) {
+    const int L = g.L;
+    int kc[4];
+    float sc[4];
+    bool v[4];
+    int kmin = L, kmax = -1;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int i = j - 1 + c;
+        v[c] = i >= 0 && i <= C - 1 && (dp[c].x != 0.f || dp[c].y != 0.f || dp[c].z != 0.f);
+        const int x = i * (L - 1);
+        int k = v[c] ? x / (C - 1) : 0;
+        if (k > L - 2) k = L - 2;
+        kc[c] = k;
+        sc[c] = (float)(x - k * (C - 1)) / (float)(C - 1);
+        if (v[c]) {
+            kmin = min(kmin, k);
+            kmax = max(kmax, k);
+        }
+    }
+    if (kmax < 0) return;
+    if (kmax - kmin > 2) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (v[c]) control_point_adjoint(g, r, C, j - 1 + c, dp[c], sk);
+        return;
+    }
+    const int base = kmin - 1;     // layer of window slot 0
+    float3 P[6], acc[6];
+#pragma unroll
+    for (int w = 0; w < 6; ++w) {
+        const int layer = base + w;
+        P[w] = (layer >= 0 && layer <= L - 1 && layer <= kmax + 2) ? layer_pt(g, r, layer) : f3(0.f, 0.f, 0.f);
+        acc[w] = f3(0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (!v[c]) continue;
+        const int k = kc[c], o = k - kmin;      // slots o .. o+3 hold layers k-1 .. k+2
+        const float s = sc[c];
+        const float3 P0 = pick6(P, o + 1), P1 = pick6(P, o + 2);
+        const float3 Pm = k > 0 ? pick6(P, o) : P0;
+        const float3 P2 = k + 2 <= L - 1 ? pick6(P, o + 3) : P1;
+        const float3 v0 = (k == 0) ? sub3(P1, P0) : sub3(P1, Pm);
+        const float3 v1 = (k + 1 == L - 1) ? sub3(P1, P0) : sub3(P2, P0);
+        const float n0 = len3(v0), n1 = len3(v1);
+        const float3 t0 = n0 > 0.f ? mul3(v0, 1.f / n0) : f3(0.f, 0.f, 0.f);
+        const float3 t1 = n1 > 0.f ? mul3(v1, 1.f / n1) : f3(0.f, 0.f, 0.f);
+        const float3 ch = sub3(P1, P0);
+        const float ell = len3(ch);
+        const float s2 = s * s, s3 = s2 * s;
+        const float h00 = 2.f * s3 - 3.f * s2 + 1.f, h10 = s3 - 2.f * s2 + s;
+        const float h01 = 3.f * s2 - 2.f * s3, h11 = s3 - s2;
+        const float3 d = dp[c];
+        float3 dP0 = mul3(d, h00), dP1 = mul3(d, h01), dPm = f3(0.f, 0.f, 0.f), dP2 = f3(0.f, 0.f, 0.f);
+        const float dell = h10 * dot3(t0, d) + h11 * dot3(t1, d);
+        if (ell > 0.f) {
+            const float3 e = mul3(ch, dell / ell);
+            dP1 = add3(dP1, e);
+            dP0 = sub3(dP0, e);
+        }
+        const float3 dv0 = unit_adjoint(t0, n0, mul3(d, h10 * ell));
+        dP1 = add3(dP1, dv0);
+        if (k == 0) dP0 = sub3(dP0, dv0);
+        else dPm = sub3(dPm, dv0);
+        const float3 dv1 = unit_adjoint(t1, n1, mul3(d, h11 * ell));
+        dP0 = sub3(dP0, dv1);
+        if (k + 1 == L - 1) dP1 = add3(dP1, dv1);
+        else dP2 = add3(dP2, dv1);
+#pragma unroll
+        for (int oo = 0; oo < 3; ++oo) {
+            if (o != oo) continue;
+            acc[oo] = add3(acc[oo], dPm);
+            acc[oo + 1] = add3(acc[oo + 1], dP0);
+            acc[oo + 2] = add3(acc[oo + 2], dP1);
+            acc[oo + 3] = add3(acc[oo + 3], dP2);
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < 6; ++w) {
+        const int layer = base + w;
+        if (layer >= 0 && layer <= L - 1) scatter_layer_point(sk, r, layer, acc[w]);
+    }
+}
+
 // Adjoint of the pixel position X = p_j + (p_{j+1} - p_j) t and unit tangent
 // T = unit(T_j + (T_{j+1} - T_j) t), t fixed, to the control points.
 __device__ void geometry_adjoint(const GroomDev &g, const Root &r, int C, int j, float t, float3 dX, float3 dT,
@@ -143,10 +244,8 @@ __device__ void geometry_adjoint(const GroomDev &g, const Root &r, int C, int j,
         dpp = add3(dpp, dvb);
         dp0 = sub3(dp0, dvb);
     }
-    control_point_adjoint(g, r, C, j, dp0, sk);
-    control_point_adjoint(g, r, C, j + 1, dp1, sk);
-    if (has_m) control_point_adjoint(g, r, C, j - 1, dpm, sk);
-    if (has_p) control_point_adjoint(g, r, C, j + 2, dpp, sk);
+    const float3 dps[4] = {has_m ? dpm : f3(0.f, 0.f, 0.f), dp0, dp1, has_p ? dpp : f3(0.f, 0.f, 0.f)};
+    control_points_adjoint(g, r, C, j, dps, sk);
 }
 
 // Adjoint of the screen tangent Ts = J T / |J T| at X (J: Jacobian of the
