@@ -152,12 +152,20 @@ def measured_peaks():
         return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
 
 
-def kernel_src_hash():
+# Sources each profiled kernel is compiled from: a committed ncu figure
+# stays valid while these files are unchanged.
+KERNEL_SOURCES = {
+    "raster_kernel": ["csrc/hm_render.cu", "csrc/hm_device.cuh", "csrc/hm_kernels.h", "../include/hm.h"],
+    "resolve_kernel": ["csrc/hm_resolve.cu", "csrc/hm_value.cuh", "csrc/hm_device.cuh", "csrc/hm_kernels.h",
+                       "../include/hm.h"],
+}
+
+
+def kernel_src_hash(kernel: str):
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_2607_04230_b300", "csrc")
-    for n in sorted(os.listdir(d)):
-        if n.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, n), "rb").read())
+    d = os.path.join(ROOT, "paper_2607_04230_b300")
+    for n in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.normpath(os.path.join(d, n)), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -170,7 +178,7 @@ def ncu_traffic(kernel: str, workload: str):
     except (OSError, ValueError):
         return None
     e = t.get(workload, {}).get(kernel)
-    if not e or e.get("src_hash") != kernel_src_hash():
+    if not e or kernel not in KERNEL_SOURCES or e.get("src_hash") != kernel_src_hash(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -211,7 +219,7 @@ def ncu_red_sectors_per_atomic(workload: str):
     except (OSError, ValueError):
         return None
     e = t.get(workload, {}).get("raster_kernel")
-    if not e or e.get("src_hash") != kernel_src_hash():
+    if not e or e.get("src_hash") != kernel_src_hash("raster_kernel"):
         return None
     return e.get("red_sectors_per_atomic")
 
