@@ -169,7 +169,9 @@ typedef struct {
 
 /* Copy a hair mesh to the device and return a handle (allocates device
  * memory with cudaMalloc; enqueues the copies on `stream` and synchronizes
- * it before returning).  LOD starts disabled.
+ * it before returning).  LOD starts disabled.  Besides the mesh the groom
+ * holds 32 bytes per strand segment at full detail for the control points
+ * the camera renders record (see hm_render_visibility).
  * Errors: HM_ERR_INVALID_ARG (null pointer, size out of range, unsorted
  * strand_face, bad face index, bary outside [0, 1], delta outside [0, 1)),
  * HM_ERR_CAPACITY (more than 2^33 - 2 strands), HM_ERR_OOM, HM_ERR_CUDA. */
@@ -183,7 +185,9 @@ hm_status hm_destroy_groom(hm_groom g);
 hm_status hm_set_lod(hm_groom g, const hm_lod_params *p);
 
 /* Replace the layer vertices from a DEVICE buffer [L][V][3] (animation or an
- * optimisation step); enqueued on `stream`. */
+ * optimisation step); enqueued on `stream`.  The control points recorded by
+ * the last render become stale: until the next render, key decoding
+ * regenerates strands from the new vertices. */
 hm_status hm_update_layer_verts(hm_groom g, const float *d_layer_verts, void *stream);
 
 /* Replace the per-strand albedo from a DEVICE buffer [S][3]; enqueued on
@@ -204,7 +208,12 @@ hm_status hm_update_albedo(hm_groom g, const float *d_albedo, void *stream);
  * Strand ids: groom i's strands are numbered after those of grooms 0..i-1
  * in this call.  The LOD result is kept in each groom and used by
  * hm_resolve_shade / hm_shade_backward, which must receive the same groom
- * array in the same order.
+ * array in the same order.  The rasterizer also records the two control
+ * points of every drawn segment in the groom (device memory it owns); key
+ * decoding in the resolves and the adjoint reads them instead of
+ * regenerating the strand (bit-identical values) until the groom's layer
+ * vertices are replaced or its LOD state is rebuilt by another camera render
+ * (hm_render_shadow_map neither writes nor disturbs them).
  *
  * d_vis_center, d_vis_cons: [height][width] uint64, 8-byte aligned.
  * d_scene_d24: [height][width] uint32 (24-bit depth) or NULL.

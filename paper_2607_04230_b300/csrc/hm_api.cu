@@ -36,6 +36,11 @@ struct hm_groom_s {
     uint32_t *d_batch_map_full;
     uint32_t *d_counters_full;
     float2 *d_uv;            // scalp texture coordinates, or null
+    // control points of every drawn segment, written by the camera renders
+    // (two float4 per segment at full detail); valid while they match the
+    // LOD state of the last camera render and the current layer vertices
+    float4 *d_segpts;
+    bool segpts_valid;
 };
 
 namespace {
@@ -142,6 +147,7 @@ hm_status build_table(const hm_groom *grooms, int32_t n, hm::CallTable &tab) {
         d.has_ao = g->has_ao;
         d.uv = g->d_uv;
         d.max_batches = (uint32_t)g->max_batches;
+        d.segpts = g->segpts_valid ? g->d_segpts : nullptr;
         base += (uint64_t)g->S;
     }
     if (base > (1ull << 33) - 2) return fail(HM_ERR_CAPACITY, "strand ids exceed 33 bits");
@@ -183,6 +189,7 @@ void free_groom(hm_groom g) {
     cudaFree(g->d_lod);
     cudaFree(g->d_batch_map);
     cudaFree(g->d_counters);
+    cudaFree(g->d_segpts);
     cudaFree(g->d_lod_full);
     cudaFree(g->d_batch_map_full);
     cudaFree(g->d_counters_full);
@@ -338,6 +345,7 @@ hm_status hm_create_groom(const hm_groom_desc *d, void *stream, hm_groom *out) {
     HM_ALLOC(g->d_batch_map_full, max_batches, "alloc shadow-pass batch map")
     HM_ALLOC(g->d_counters_full, (size_t)hm::kCtrWords, "alloc shadow-pass counters")
     if (d->vert_uv) HM_ALLOC(g->d_uv, (size_t)V, "alloc vert_uv")
+    HM_ALLOC(g->d_segpts, 2 * (size_t)S * (size_t)segs, "alloc segment records")
 #undef HM_ALLOC
     if (st != HM_OK) {
         free_groom(g);
@@ -388,6 +396,7 @@ hm_status hm_set_lod(hm_groom g, const hm_lod_params *p) {
 
 hm_status hm_update_layer_verts(hm_groom g, const float *d_layer_verts, void *stream) {
     if (!g || !d_layer_verts) return fail(HM_ERR_INVALID_ARG, "groom/buffer is NULL");
+    g->segpts_valid = false;     // the recorded control points are of the old vertices
     HM_CUDA(hm::launch_pack_float3(d_layer_verts, g->d_lv, (int64_t)g->L * g->V, static_cast<cudaStream_t>(stream)),
             "pack layer verts");
     return HM_OK;
@@ -434,7 +443,10 @@ static hm_status render_views(const hm_groom *grooms, int32_t n, int32_t first, 
     hm::CallTable tab;
     std::memset(&tab, 0, sizeof tab);
     tab.n = count;
-    for (int i = 0; i < count; ++i) tab.g[i] = full.g[first + i];   // keeps the whole array's strand ids
+    for (int i = 0; i < count; ++i) {
+        tab.g[i] = full.g[first + i];   // keeps the whole array's strand ids
+        tab.g[i].segpts = grooms[first + i]->d_segpts;
+    }
     hm::ViewSet views;
     std::memset(&views, 0, sizeof views);
     views.n = n_views;
@@ -451,12 +463,14 @@ static hm_status render_views(const hm_groom *grooms, int32_t n, int32_t first, 
                                  v == 0 ? d_stats : nullptr, s),
                 "clear");
     phase(1, s);
+    for (int i = 0; i < count; ++i) grooms[first + i]->segpts_valid = false;   // until the raster has rewritten them
     HM_CUDA(hm::launch_lod(tab, views.cam[0], d_stats, s), "lod");
     phase(2, s);
     HM_CUDA(hm::launch_raster(tab, views, g_tuning.raster_precheck != 0, g_tuning.raster_min_blocks,
                               g_tuning.raster_ctas_per_sm, d_stats, s, compressed),
             "raster");
     phase(3, s);
+    for (int i = 0; i < count; ++i) grooms[first + i]->segpts_valid = true;
     return HM_OK;
 }
 
@@ -479,6 +493,7 @@ hm_status hm_render_shadow_map(const hm_groom *grooms, int32_t n, const hm_camer
         tab.g[i].batch_map = grooms[i]->d_batch_map_full;
         tab.g[i].counters = grooms[i]->d_counters_full;
         tab.g[i].lod_enabled = 0;
+        tab.g[i].segpts = nullptr;      // the records follow the camera's LOD state, not this pass's
     }
     hm::ViewSet views;
     std::memset(&views, 0, sizeof views);
@@ -506,14 +521,17 @@ hm_status hm_render_visibility_msaa(const hm_groom *grooms, int32_t n, const hm_
         return fail(HM_ERR_INVALID_ARG, "sample layers NULL or not 16-byte aligned");
     hm::CallTable tab;
     if ((st = build_table(grooms, n, tab)) != HM_OK) return st;
+    for (int i = 0; i < n; ++i) tab.g[i].segpts = grooms[i]->d_segpts;
     const hm::CamDev cd = cam_dev(cam);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t npx = (int64_t)cam->width * cam->height;
     // the sample planes are contiguous: cleared as one flat array (one pointer
     // given twice, written once)
     HM_CUDA(hm::launch_clear(d_vis_samples, d_vis_samples, npx * samples, nullptr, clear, d_stats, s), "clear");
+    for (int i = 0; i < n; ++i) grooms[i]->segpts_valid = false;   // until the raster has rewritten them
     HM_CUDA(hm::launch_lod(tab, cd, d_stats, s), "lod");
     HM_CUDA(hm::launch_raster_msaa(tab, cd, samples, d_vis_samples, d_stats, s), "raster msaa");
+    for (int i = 0; i < n; ++i) grooms[i]->segpts_valid = true;
     return HM_OK;
 }
 

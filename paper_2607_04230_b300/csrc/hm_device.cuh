@@ -48,6 +48,13 @@ struct GroomDev {
     int32_t has_ao;          // layer vertices carry baked ambient occlusion in w
     const float2 *uv;        // [V] scalp texture coordinates, or null (compressed payload)
     uint32_t max_batches;    // 32-segment batches at full detail (batch_map capacity)
+    // [drawn segments][2] control points j and j+1 of every drawn segment,
+    // (p_j.xyz, p_j+1.x), (p_j+1.yz, 0, 0), indexed like the batch list
+    // (lod[f].z + strand-in-bundle (C - 1) + j).  The rasterizer writes them
+    // when non-null; key decoding reads them instead of regenerating the
+    // strand when non-null (the host passes them only while they match the
+    // groom's LOD state and layer vertices).
+    float4 *segpts;
 };
 
 struct CallTable {
@@ -166,6 +173,14 @@ __device__ __forceinline__ float3 control_pt(const GroomDev &g, const Root &r, i
         fadd(fadd(fadd(fmul(h00, P0.x), fmul(h10, m0.x)), fmul(h01, P1.x)), fmul(h11, m1.x)),
         fadd(fadd(fadd(fmul(h00, P0.y), fmul(h10, m0.y)), fmul(h01, P1.y)), fmul(h11, m1.y)),
         fadd(fadd(fadd(fmul(h00, P0.z), fmul(h10, m0.z)), fmul(h01, P1.z)), fmul(h11, m1.z)));
+}
+
+// Record of drawn segment `seg`: its two control points (bit-identical to
+// control_pts<2>; the decode rebuilds X and T from the same values).
+__device__ __forceinline__ void store_segment_points(float4 *segpts, uint32_t seg, const float3 (&cp)[2]) {
+    float4 *p = segpts + 2 * (size_t)seg;
+    p[0] = make_float4(cp[0].x, cp[0].y, cp[0].z, cp[1].x);
+    p[1] = make_float4(cp[1].y, cp[1].z, 0.0f, 0.0f);
 }
 
 // Control points j0, j0+1, ..., j0+N-1 (each clamped to [0, C-1]); the
@@ -422,6 +437,14 @@ __device__ __forceinline__ void sample_offset(int k, int &ox, int &oy) {
     oy = 16 * t[k][1];
 }
 
+// Control points j-1 .. j+2 regenerated from the hair mesh (decode without
+// the rasterizer's records); kept out of line so the record path's register
+// allocation does not carry it.
+static __device__ __noinline__ void regenerate_points4(const GroomDev &g, int64_t s, uint32_t f, int C, int j,
+                                                float3 (&cp)[4]) {
+    control_pts<4>(g, make_root(g, s, f), C, j - 1, cp);
+}
+
 struct Decoded;
 __device__ __forceinline__ Decoded decode_key_at(const CallTable &tab, const uint64_t *bases, const CamDev &cam,
                                                  uint64_t key, int64_t sx, int64_t sy, uint32_t *status);
@@ -454,9 +477,31 @@ __device__ __forceinline__ Decoded decode_key_at(const CallTable &tab, const uin
     if (f >= (uint32_t)g.F) { atomicOr(status, kStatusBadKey); return d; }
     int C = (int)g.lod[f].y;
     if (j + 1 >= C) { atomicOr(status, kStatusBadKey); return d; }
-    Root r = make_root(g, s, f);
     float3 cp[4];
-    control_pts<4>(g, r, C, j - 1, cp);
+    if (g.segpts) {
+        // the rasterizer's records of segments j-1, j, j+1 of this strand:
+        // control points j-1 .. j+2 (clamped to the strand like control_pts)
+        const uint32_t sl = (uint32_t)(s - (int64_t)__ldg(&g.faces[f]).w);
+        if (sl >= g.lod[f].x) { atomicOr(status, kStatusBadKey); return d; }   // strand not drawn at this LOD
+        const float4 *rp = g.segpts + 2 * ((size_t)g.lod[f].z + (size_t)sl * (uint32_t)(C - 1) + (uint32_t)j);
+        const float4 a0 = __ldg(rp), a1 = __ldg(rp + 1);
+        cp[1] = make_float3(a0.x, a0.y, a0.z);
+        cp[2] = make_float3(a0.w, a1.x, a1.y);
+        if (j >= 1) {
+            const float4 m0 = __ldg(rp - 2);
+            cp[0] = make_float3(m0.x, m0.y, m0.z);
+        } else {
+            cp[0] = cp[1];
+        }
+        if (j + 2 <= C - 1) {
+            const float4 q0 = __ldg(rp + 2), q1 = __ldg(rp + 3);
+            cp[3] = make_float3(q0.w, q1.x, q1.y);
+        } else {
+            cp[3] = cp[2];
+        }
+    } else {
+        regenerate_points4(g, s, f, C, j, cp);
+    }
     const float3 pm = cp[0], p0 = cp[1], p1 = cp[2], pp = cp[3];
     Proj a = project(cam, p0), b = project(cam, p1);
     float t = seg_t(a.X, a.Y, b.X, b.Y, sx, sy);

@@ -398,6 +398,7 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
             batch_segment(g, __ldg(&g.batch_map[lb]), seg, f, s, j, C);
             const Root rt = make_root(g, s, f);
             control_pts<2>(g, rt, C, j, cp);
+            if (g.segpts) store_segment_points(g.segpts, seg, cp);
             if (kCgb) {
                 cgb_hi = (oct_encode(v3unit(v3sub(cp[1], cp[0]))) << 12) | root_uv_codes(g, rt);
                 aoA = control_ao_exact(g, rt, C, j);
@@ -605,6 +606,7 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_msaa_kernel(CallTabl
             batch_segment(g, __ldg(&g.batch_map[lb]), seg, f, s, j, C);
             float3 cp[2];
             control_pts<2>(g, make_root(g, s, f), C, j, cp);
+            if (g.segpts) store_segment_points(g.segpts, seg, cp);
             const Proj A = project(cam, cp[0]);
             const Proj B = project(cam, cp[1]);
             if (A.valid && B.valid) {

@@ -151,3 +151,35 @@ def test_degenerate_and_near_plane_segments():
     for lod in (0, 1):
         sc2.lod = synth.LodParams(lod, 3.0)
         check_full(sc2)
+
+
+def test_segment_records_and_regeneration_agree():
+    """The resolve decodes keys from the control points the visibility render
+    recorded; after hm_update_layer_verts those records are stale and it
+    regenerates the strands from the new layer vertices instead.  Same
+    vertices: both decodes give the same image bit for bit.  New vertices
+    without a new render: the image is the oracle's for the old keys and the
+    new hair mesh (the records must not be used)."""
+    import torch
+    from paper_2607_04230_b300 import hm
+    sc = synth.tiny_scene(13, width=120, height=96, num_strands=900, num_layers=5, jitter_m=0.004)
+    sc.lod = synth.LodParams(1, 3.0)
+    out = gpu_frame(sc)
+    g, frame = out["grooms"][0], out["frame"]
+    lv = torch.from_numpy(sc.grooms[0].layer_verts).cuda()
+    rgba_rec = frame.rgba.clone()
+    g.update_layer_verts(lv)                      # same vertices: records invalidated
+    hm.resolve_shade(out["grooms"], sc.camera, sc.lights, sc.filt, frame.vis_center, frame.vis_cons, frame.rgba)
+    torch.cuda.synchronize()
+    assert torch.equal(frame.rgba, rgba_rec)
+    # perturbed vertices, keys of the unperturbed render
+    lv2 = synth.perturbed_layer_verts(sc.grooms[0], sigma_m=0.001, seed=5)
+    g.update_layer_verts(torch.from_numpy(lv2).cuda())
+    hm.resolve_shade(out["grooms"], sc.camera, sc.lights, sc.filt, frame.vis_center, frame.vis_cons, frame.rgba)
+    torch.cuda.synchronize()
+    hm.get_device_status()
+    lods, vc, va, _ = oracle_keys(sc)
+    sc.grooms[0].layer_verts = lv2
+    ref, pix = oracle_rgba(sc, lods, vc, va)
+    assert_rgba_close(frame.rgba.cpu().numpy().astype(np.float64), ref, pix)
+    assert not np.allclose(frame.rgba.cpu().numpy().reshape(-1, 4)[pix], rgba_rec.cpu().numpy().reshape(-1, 4)[pix])
