@@ -211,10 +211,13 @@ __device__ void control_points_adjoint(const GroomDev &g, const Root &r, int C, 
 
 // Adjoint of the pixel position X = p_j + (p_{j+1} - p_j) t and unit tangent
 // T = unit(T_j + (T_{j+1} - T_j) t), t fixed, to the control points.
-__device__ void geometry_adjoint(const GroomDev &g, const Root &r, int C, int j, float t, float3 dX, float3 dT,
-                                 const Sink &sk) {
+__device__ void geometry_adjoint(const GroomDev &g, const Root &r, uint32_t f, int64_t s, int C, int j, float t,
+                                 float3 dX, float3 dT, const Sink &sk) {
     float3 cp[4];
-    control_pts<4>(g, r, C, j - 1, cp);
+    if (g.segpts)    // a decoded key's strand is drawn (checked by the decode)
+        recorded_points4(g, f, (uint32_t)(s - (int64_t)__ldg(&g.faces[f]).w), C, j, cp);
+    else
+        control_pts<4>(g, r, C, j - 1, cp);
     const bool has_m = j >= 1, has_p = j + 2 <= C - 1;
     const float3 pm = cp[0], p0 = cp[1], p1 = cp[2], pp = cp[3];
     const float3 va = (j == 0) ? sub3(p1, p0) : sub3(p1, pm);
@@ -671,7 +674,10 @@ __global__ void __launch_bounds__(kGeoThreads, kGeoMinBlocks) geometry_adjoint_k
                 dT = add3(dT, tT);
             }
             const Sink sk = geo_sink(lay, s_g, sinks, d.gi, g.V);
-            if (sk.glv) geometry_adjoint(g, make_root(g, d.s, __ldg(&g.sface[d.s])), d.C, d.j, d.t, dX, dT, sk);
+            if (sk.glv) {
+                const uint32_t f = __ldg(&g.sface[d.s]);
+                geometry_adjoint(g, make_root(g, d.s, f), f, d.s, d.C, d.j, d.t, dX, dT, sk);
+            }
         }
         __syncthreads();
     }

@@ -445,6 +445,29 @@ static __device__ __noinline__ void regenerate_points4(const GroomDev &g, int64_
     control_pts<4>(g, make_root(g, s, f), C, j - 1, cp);
 }
 
+// Control points j-1 .. j+2 (clamped to the strand like control_pts) from
+// the rasterizer's records of segments j-1, j, j+1 of drawn strand sl of
+// bundle f.
+__device__ __forceinline__ void recorded_points4(const GroomDev &g, uint32_t f, uint32_t sl, int C, int j,
+                                                 float3 (&cp)[4]) {
+    const float4 *rp = g.segpts + 2 * ((size_t)g.lod[f].z + (size_t)sl * (uint32_t)(C - 1) + (uint32_t)j);
+    const float4 a0 = __ldg(rp), a1 = __ldg(rp + 1);
+    cp[1] = make_float3(a0.x, a0.y, a0.z);
+    cp[2] = make_float3(a0.w, a1.x, a1.y);
+    if (j >= 1) {
+        const float4 m0 = __ldg(rp - 2);
+        cp[0] = make_float3(m0.x, m0.y, m0.z);
+    } else {
+        cp[0] = cp[1];
+    }
+    if (j + 2 <= C - 1) {
+        const float4 q0 = __ldg(rp + 2), q1 = __ldg(rp + 3);
+        cp[3] = make_float3(q0.w, q1.x, q1.y);
+    } else {
+        cp[3] = cp[2];
+    }
+}
+
 struct Decoded;
 __device__ __forceinline__ Decoded decode_key_at(const CallTable &tab, const uint64_t *bases, const CamDev &cam,
                                                  uint64_t key, int64_t sx, int64_t sy, uint32_t *status);
@@ -479,26 +502,9 @@ __device__ __forceinline__ Decoded decode_key_at(const CallTable &tab, const uin
     if (j + 1 >= C) { atomicOr(status, kStatusBadKey); return d; }
     float3 cp[4];
     if (g.segpts) {
-        // the rasterizer's records of segments j-1, j, j+1 of this strand:
-        // control points j-1 .. j+2 (clamped to the strand like control_pts)
         const uint32_t sl = (uint32_t)(s - (int64_t)__ldg(&g.faces[f]).w);
         if (sl >= g.lod[f].x) { atomicOr(status, kStatusBadKey); return d; }   // strand not drawn at this LOD
-        const float4 *rp = g.segpts + 2 * ((size_t)g.lod[f].z + (size_t)sl * (uint32_t)(C - 1) + (uint32_t)j);
-        const float4 a0 = __ldg(rp), a1 = __ldg(rp + 1);
-        cp[1] = make_float3(a0.x, a0.y, a0.z);
-        cp[2] = make_float3(a0.w, a1.x, a1.y);
-        if (j >= 1) {
-            const float4 m0 = __ldg(rp - 2);
-            cp[0] = make_float3(m0.x, m0.y, m0.z);
-        } else {
-            cp[0] = cp[1];
-        }
-        if (j + 2 <= C - 1) {
-            const float4 q0 = __ldg(rp + 2), q1 = __ldg(rp + 3);
-            cp[3] = make_float3(q0.w, q1.x, q1.y);
-        } else {
-            cp[3] = cp[2];
-        }
+        recorded_points4(g, f, sl, C, j, cp);
     } else {
         regenerate_points4(g, s, f, C, j, cp);
     }
