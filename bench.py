@@ -233,7 +233,8 @@ def _subsample_groom(g, every: int, offset: int = 0):
     return synth.Groom(layer_verts=g.layer_verts, faces=g.faces, strand_face=g.strand_face[idx],
                        strand_bary=g.strand_bary[idx], strand_albedo=g.strand_albedo[idx],
                        bundle_delta=g.bundle_delta, segments_per_strand=g.segments_per_strand,
-                       strand_width_m=g.strand_width_m, roughness=g.roughness, tilt=g.tilt), idx.size
+                       strand_width_m=g.strand_width_m, roughness=g.roughness, tilt=g.tilt,
+                       vert_ao=g.vert_ao), idx.size
 
 
 def oracle_frame_sample(scene, every: int, offset: int = 0):
@@ -262,11 +263,20 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(scene, budget_s: float = 20.0):
-    every = 25
+def cpu_baseline(scene, max_segments: int = 2_000_000):
+    """The oracle on the workload itself when it has at most max_segments
+    strand segments (the 1080p groom: the whole frame, a few seconds on the
+    host cores), else on every k-th strand of every groom with k chosen to
+    keep about max_segments.  The oracle's per-frame work (full-frame
+    decisions and FP64 arrays) does not shrink with the strand count, so a
+    sparse sample would understate its throughput."""
+    total = sum(g.num_strands * g.segments_per_strand for g in scene.grooms)
+    every = max(1, int(np.ceil(total / max_segments)))
+    oracle_frame_sample(scene, 1000)              # warm-up (library load, thread pool)
     segs, dt = oracle_frame_sample(scene, every)
+    what = "the whole workload" if every == 1 else f"every {every}th strand of every groom"
     return {"value": segs / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-            "sample": f"every {every}th strand of every groom ({segs} segments) rasterized by the C oracle "
+            "sample": f"{what} ({segs} segments, one frame) rasterized by the C oracle "
                       f"(OpenMP, all host threads) and resolved by the FP64 torch oracle, {dt:.1f} s"}
 
 
@@ -277,7 +287,12 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     scene, cfg = make_scene(args.workload)
-    every = {"single_1080p": 400, "crowd_4k": 800, "tiny_256": 10}[args.workload]
+    # each step: every k-th strand, k set by a pilot so that warm-up + steps
+    # take about two minutes (at most 10 s a step)
+    base = {"single_1080p": 400, "crowd_4k": 800, "tiny_256": 10}[args.workload]
+    _, tp = oracle_frame_sample(scene, base)
+    budget = min(10.0, max(0.2, 120.0 / max(1, args.steps + args.warmup)))
+    every = int(min(max(round(base * tp / budget), 1), 100 * base))
     for i in range(args.warmup):
         oracle_frame_sample(scene, every, offset=i)
     tot_s, tot_t = 0, 0.0
