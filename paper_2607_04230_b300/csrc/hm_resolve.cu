@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
     const int R = fp.enabled ? fp.radius : 0;
     const int sw = kFwdTileW + 2 * R, sh = kFwdTileH + 2 * R, ns = sw * sh;
     // shared layout: bases | s_col[ns] (rgb + centre depth bits) | s_list[ns] | s_lg[tile] |
-    // s_out[tile] | s_ts[tile] | s_flag[tile] | s_fa[ns]
+    // s_out[tile] | s_outA[tile] | s_ts[tile] | s_flag[tile] | s_fa[ns]
     uint64_t *s_bases = reinterpret_cast<uint64_t *>(smem);
     float4 *s_col = reinterpret_cast<float4 *>(
         (reinterpret_cast<uintptr_t>(s_bases + HM_MAX_GROOMS_PER_CALL + 1) + 15) & ~(uintptr_t)15);  // 16-byte loads
@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
     uint16_t *s_lg = s_list + ((ns + 7) & ~7);                         // tile centre list
     float4 *s_out = reinterpret_cast<float4 *>(
         (reinterpret_cast<uintptr_t>(s_lg + kFwdTilePx) + 15) & ~(uintptr_t)15);  // centre result (rgb, alpha)
-    float2 *s_ts = reinterpret_cast<float2 *>(s_out + kFwdTilePx);   // G screen tangent, then A's
+    float4 *s_outA = s_out + kFwdTilePx;                              // conservative result (rgb, alpha or -1)
+    float2 *s_ts = reinterpret_cast<float2 *>(s_outA + kFwdTilePx);  // G screen tangent
     uint8_t *s_flag = reinterpret_cast<uint8_t *>(s_ts + kFwdTilePx); // bit0 isoG, bit1 isoA, bit2 needs A
     uint8_t *s_fa = s_flag + kFwdTilePx;
     __shared__ int s_count, s_ng;
@@ -178,69 +179,61 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
     __syncthreads();
     const int ng = s_ng, nA = s_count;
 
-    // 4. centre-referenced reconstruction of every centre pixel
-    for (int li = tid; li < ng; li += kFwdThreads) {
-        const int t = s_lg[li];
-        const int tx = t % kFwdTileW, ty = t / kFwdTileW;
-        const int mid = (ty + R) * sw + tx + R;
-        const float3 Cp = make_float3(s_col[mid].x, s_col[mid].y, s_col[mid].z);
-        float4 o;
-        if (!fp.enabled) {
-            o = make_float4(Cp.x, Cp.y, Cp.z, 1.0f);
-        } else {
-            const float2 ts = s_ts[t];
-            const Recon rg = reconstruct_fast_r<true>(R, s_fa, s_col, sw, tx, ty, dg_at(mid), ts.x, ts.y,
-                                                      (s_flag[t] & 1) != 0, Cp, fp);
-            const float invW = 1.0f / rg.W;
-            o = make_float4(rg.S.x * invW, rg.S.y * invW, rg.S.z * invW, __fdiv_rn((float)rg.hc, (float)rg.ha));
-        }
-        s_out[t] = o;
-    }
-    __syncthreads();
-
-    // 5. decode the conservative reference, then the conservative-referenced
-    // (promoted) reconstruction; combine with the centre result
-    for (int li = tid; li < nA; li += kFwdThreads) {
-        const int t = s_list[li];
-        const int tx = t % kFwdTileW, ty = t / kFwdTileW;
-        const int gx = x0 + tx, gy = y0 + ty;
-        const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx));
-        float tsx, tsy;
-        bool iso;
-        if (kCgb) {
-            const DecodedC d = decode_compressed(cam, ka, gx, gy);
-            tsx = d.tsx;
-            tsy = d.tsy;
-            iso = d.iso;
-        } else {
-            const Decoded d = decode_key(tab, s_bases, cam, ka, gx, gy, status);
-            tsx = d.tsx;
-            tsy = d.tsy;
-            iso = d.iso;
-        }
-        const int dA = (int)(ka >> 40);
-        const float3 z = make_float3(0.f, 0.f, 0.f);
-        Recon ra = reconstruct_fast_r<false>(R, s_fa, s_col, sw, tx, ty, dA, tsx, tsy, iso, z, fp);
-        if (ra.cnt > 0 && ra.W < 1e-20f)
-            ra = reconstruct(static_cast<const int *>(nullptr), s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, tsx, tsy,
-                             iso, false, z, fp);
-        const int mid = (ty + R) * sw + tx + R;
-        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (dg_at(mid) >= 0) {              // depth mismatch: blend over the centre result, alpha 1
-            const float4 cg = s_out[t];
-            float3 c = make_float3(cg.x, cg.y, cg.z);
-            if (ra.cnt > 0) {
-                const float al = __fdiv_rn((float)ra.hc, (float)ra.ha);
-                const float iw = 1.0f / ra.W;
-                c = make_float3(al * (ra.S.x * iw) + (1.0f - al) * c.x, al * (ra.S.y * iw) + (1.0f - al) * c.y,
-                                al * (ra.S.z * iw) + (1.0f - al) * c.z);
+    // 4. one pass over the jobs: the centre-referenced reconstruction of
+    // every centre pixel, then the decode of the conservative reference and
+    // the conservative-referenced reconstruction of every pixel that needs
+    // it (as one list, so the few conservative jobs past a multiple of the
+    // CTA size share a round with centre jobs instead of taking a round of
+    // their own)
+    for (int li = tid; li < ng + nA; li += kFwdThreads) {
+        if (li < ng) {
+            const int t = s_lg[li];
+            const int tx = t % kFwdTileW, ty = t / kFwdTileW;
+            const int mid = (ty + R) * sw + tx + R;
+            const float3 Cp = make_float3(s_col[mid].x, s_col[mid].y, s_col[mid].z);
+            float4 o;
+            if (!fp.enabled) {
+                o = make_float4(Cp.x, Cp.y, Cp.z, 1.0f);
+            } else {
+                const float2 ts = s_ts[t];
+                const Recon rg = reconstruct_fast_r<true>(R, s_fa, s_col, sw, tx, ty, dg_at(mid), ts.x, ts.y,
+                                                          (s_flag[t] & 1) != 0, Cp, fp);
+                const float invW = 1.0f / rg.W;
+                o = make_float4(rg.S.x * invW, rg.S.y * invW, rg.S.z * invW,
+                                __fdiv_rn((float)rg.hc, (float)rg.ha));
             }
-            o = make_float4(c.x, c.y, c.z, 1.0f);
-        } else if (ra.cnt > 0) {            // promoted
-            const float iw = 1.0f / ra.W;
-            o = make_float4(ra.S.x * iw, ra.S.y * iw, ra.S.z * iw, __fdiv_rn((float)ra.hc, (float)ra.ha));
+            s_out[t] = o;
+        } else {
+            const int t = s_list[li - ng];
+            const int tx = t % kFwdTileW, ty = t / kFwdTileW;
+            const int gx = x0 + tx, gy = y0 + ty;
+            const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx));
+            float tsx, tsy;
+            bool iso;
+            if (kCgb) {
+                const DecodedC d = decode_compressed(cam, ka, gx, gy);
+                tsx = d.tsx;
+                tsy = d.tsy;
+                iso = d.iso;
+            } else {
+                const Decoded d = decode_key(tab, s_bases, cam, ka, gx, gy, status);
+                tsx = d.tsx;
+                tsy = d.tsy;
+                iso = d.iso;
+            }
+            const int dA = (int)(ka >> 40);
+            const float3 z = make_float3(0.f, 0.f, 0.f);
+            Recon ra = reconstruct_fast_r<false>(R, s_fa, s_col, sw, tx, ty, dA, tsx, tsy, iso, z, fp);
+            if (ra.cnt > 0 && ra.W < 1e-20f)
+                ra = reconstruct(static_cast<const int *>(nullptr), s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA,
+                                 tsx, tsy, iso, false, z, fp);
+            float4 oa = make_float4(0.f, 0.f, 0.f, -1.0f);   // no contributor
+            if (ra.cnt > 0) {
+                const float iw = 1.0f / ra.W;
+                oa = make_float4(ra.S.x * iw, ra.S.y * iw, ra.S.z * iw, __fdiv_rn((float)ra.hc, (float)ra.ha));
+            }
+            s_outA[t] = oa;
         }
-        s_out[t] = o;
     }
     __syncthreads();
 
@@ -250,8 +243,26 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
         const int gx = x0 + tx, gy = y0 + ty;
         if (gx >= W || gy >= H) continue;
         const int mid = (ty + R) * sw + tx + R;
-        const bool written = dg_at(mid) >= 0 || (s_flag[t] & 4);
-        rgba[(int64_t)gy * W + gx] = written ? s_out[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool gP = dg_at(mid) >= 0;
+        if (s_flag[t] & 4) {
+            const float4 a = s_outA[t];
+            if (gP) {                       // depth mismatch: blend over the centre result, alpha 1
+                const float4 cg = s_out[t];
+                float3 c = make_float3(cg.x, cg.y, cg.z);
+                if (a.w >= 0.0f) {
+                    const float al = a.w;
+                    c = make_float3(al * a.x + (1.0f - al) * c.x, al * a.y + (1.0f - al) * c.y,
+                                    al * a.z + (1.0f - al) * c.z);
+                }
+                o = make_float4(c.x, c.y, c.z, 1.0f);
+            } else if (a.w >= 0.0f) {       // promoted
+                o = a;
+            }
+        } else if (gP) {
+            o = s_out[t];
+        }
+        rgba[(int64_t)gy * W + gx] = o;
     }
 }
 
@@ -322,7 +333,7 @@ size_t resolve_smem_bytes(int radius, int tile_h) {
     size_t b = sizeof(uint64_t) * (HM_MAX_GROOMS_PER_CALL + 1) + 16;   // + alignment of the float4 array
     b += sizeof(float4) * ns;
     b += sizeof(uint16_t) * (((ns + 7) & ~7) + tile_px) + 16;
-    b += sizeof(float4) * tile_px;
+    b += 2 * sizeof(float4) * tile_px;
     b += sizeof(float2) * tile_px;
     b += tile_px;
     b += ns;
