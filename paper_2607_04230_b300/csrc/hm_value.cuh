@@ -202,6 +202,28 @@ __device__ __forceinline__ int2 strip_counts(const float4 *s_col, const uint8_t 
     const bool xmaj = fabsf(tsx) >= fabsf(tsy);
     const float slope = xmaj ? tsy / tsx : tsx / tsy;
     const float half = fp.hw * 1.41422f + 0.01f;
+    if (half < 1.0f) {
+        // a range narrower than 2 holds at most two integers: m0 and m0 + 1,
+        // evaluated without a data-dependent loop (the paper's 0.5 px strip)
+#pragma unroll
+        for (int k = -R; k <= R; ++k) {
+            const float c = (float)k * slope;
+            const int m0 = (int)ceilf(c - half), m1 = (int)floorf(c + half);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int m = m0 + j;
+                const bool cand = m <= m1 && m >= -R && m <= R;
+                const int mc = min(max(m, -R), R);
+                const int dx = xmaj ? k : mc, dy = xmaj ? mc : k;
+                float dpar, perp2;
+                const bool in = cand && in_strip(false, tsx, tsy, dx, dy, fp.hw2, dpar, perp2);
+                const int idx = (ly + dy + R) * sw + lx + dx + R;
+                hc += (in && __float_as_int(s_col[idx].w) >= 0) ? 1 : 0;
+                ha += (in && s_fa[idx]) ? 1 : 0;
+            }
+        }
+        return make_int2(hc, ha);
+    }
     for (int k = -R; k <= R; ++k) {
         const float c = (float)k * slope;
         const int m0 = max((int)ceilf(c - half), -R), m1 = min((int)floorf(c + half), R);
