@@ -187,7 +187,9 @@ hm_status hm_set_lod(hm_groom g, const hm_lod_params *p);
 /* Replace the layer vertices from a DEVICE buffer [L][V][3] (animation or an
  * optimisation step); enqueued on `stream`.  The control points recorded by
  * the last render become stale: until the next render, key decoding
- * regenerates strands from the new vertices. */
+ * regenerates strands from the new vertices.  (A CUDA graph keeps the
+ * arguments of the calls it captured: replay a captured resolve only
+ * together with the render that rewrites the records.) */
 hm_status hm_update_layer_verts(hm_groom g, const float *d_layer_verts, void *stream);
 
 /* Replace the per-strand albedo from a DEVICE buffer [S][3]; enqueued on
