@@ -27,6 +27,21 @@ constexpr int kFwdTileW = 32, kFwdThreads = 512;
 // depth-difference test alone rejects it
 constexpr int kNoDepth = -(1 << 30);
 
+// Centre-referenced result of tile pixel (tx, ty): the normalized
+// reconstruction and alpha H_center / H_cons (Sec. 3.3), or the pixel's
+// own colour with alpha 1 when the filter is off.
+__device__ __forceinline__ float4 centre_result(int R, const uint8_t *s_fa, const float4 *s_col, int sw, int tx,
+                                                int ty, float2 ts, bool iso, const FilterDev &fp) {
+    const int mid = (ty + R) * sw + tx + R;
+    const float4 c4 = s_col[mid];
+    const float3 Cp = make_float3(c4.x, c4.y, c4.z);
+    if (!fp.enabled) return make_float4(Cp.x, Cp.y, Cp.z, 1.0f);
+    const Recon rg = reconstruct_fast_r<true>(R, s_fa, s_col, sw, tx, ty, __float_as_int(c4.w), ts.x, ts.y, iso, Cp,
+                                              fp);
+    const float invW = 1.0f / rg.W;
+    return make_float4(rg.S.x * invW, rg.S.y * invW, rg.S.z * invW, __fdiv_rn((float)rg.hc, (float)rg.ha));
+}
+
 // kCgb: the keys carry the compressed payload (Sec. 3.1.2) and shading
 // reads it alone: position from depth, tangent from its code, albedo from
 // the appearance table at (u, v) scaled along w, AO from its code.
@@ -41,20 +56,21 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
     const int R = fp.enabled ? fp.radius : 0;
     const int sw = kFwdTileW + 2 * R, sh = kFwdTileH + 2 * R, ns = sw * sh;
     // shared layout: bases | s_col[ns] (rgb + centre depth bits) | s_list[ns] | s_lg[tile] |
-    // s_out[tile] | s_outA[tile] | s_ts[tile] | s_flag[tile] | s_fa[ns]
+    // s_lb[tile] | s_out[tile] | s_outA[tile] | s_ts[tile] | s_flag[tile] | s_fa[ns]
     uint64_t *s_bases = reinterpret_cast<uint64_t *>(smem);
     float4 *s_col = reinterpret_cast<float4 *>(
         (reinterpret_cast<uintptr_t>(s_bases + HM_MAX_GROOMS_PER_CALL + 1) + 15) & ~(uintptr_t)15);  // 16-byte loads
     uint16_t *s_list = reinterpret_cast<uint16_t *>(s_col + ns);     // staged centre list, then A list
     auto dg_at = [&](int i) { return __float_as_int(s_col[i].w); };    // staged centre depth
-    uint16_t *s_lg = s_list + ((ns + 7) & ~7);                         // tile centre list
+    uint16_t *s_lg = s_list + ((ns + 7) & ~7);                         // centre pixels without a mismatch
+    uint16_t *s_lb = s_lg + kFwdTilePx;                                // mismatches that blend (al < 1)
     float4 *s_out = reinterpret_cast<float4 *>(
-        (reinterpret_cast<uintptr_t>(s_lg + kFwdTilePx) + 15) & ~(uintptr_t)15);  // centre result (rgb, alpha)
+        (reinterpret_cast<uintptr_t>(s_lb + kFwdTilePx) + 15) & ~(uintptr_t)15);  // result (rgb, alpha)
     float4 *s_outA = s_out + kFwdTilePx;                              // conservative result (rgb, alpha or -1)
     float2 *s_ts = reinterpret_cast<float2 *>(s_outA + kFwdTilePx);  // G screen tangent
     uint8_t *s_flag = reinterpret_cast<uint8_t *>(s_ts + kFwdTilePx); // bit0 isoG, bit1 isoA, bit2 needs A
     uint8_t *s_fa = s_flag + kFwdTilePx;
-    __shared__ int s_count, s_ng;
+    __shared__ int s_count, s_ng, s_nb;
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int x0 = blockIdx.x * kFwdTileW, y0 = blockIdx.y * kFwdTileH;
@@ -67,6 +83,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
     if (tid == 0) {
         s_count = 0;
         s_ng = 0;
+        s_nb = 0;
     }
     // 0. a tile whose pixels hold no conservative key has nothing to resolve
     // (no centre key either: centre keys are a subset): write zeros, done
@@ -148,8 +165,9 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
     if (tid == 0) s_count = 0;
     __syncthreads();
 
-    // 3. lists: tile centre pixels (row-major per warp); pixels needing the
-    // conservative reference
+    // 3. lists: centre pixels whose result is the centre reconstruction
+    // (row-major per warp); pixels needing the conservative reference
+    // (promoted pixels and depth mismatches)
     for (int t = tid; t < kFwdTilePx; t += kFwdThreads) {
         const int tx = t % kFwdTileW, ty = t / kFwdTileW;
         const int gx = x0 + tx, gy = y0 + ty;
@@ -157,16 +175,17 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
         const int mid = (ty + R) * sw + tx + R;
         const int dgP = in ? dg_at(mid) : -1;
         const bool gP = dgP >= 0, aP = in && s_fa[mid] != 0;
-        const unsigned bal = __ballot_sync(0xFFFFFFFFu, gP);
-        int wbase = 0;
-        if (lane == 0 && bal) wbase = atomicAdd(&s_ng, __popc(bal));
-        wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
-        if (gP) s_lg[wbase + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)t;
         bool needA = false;
         if (aP && fp.enabled) {
             const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx));
             needA = dgP < 0 || (int)(ka >> 40) + fp.dmis <= dgP;
         }
+        const bool gOnly = gP && !needA;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, gOnly);
+        int wbase = 0;
+        if (lane == 0 && bal) wbase = atomicAdd(&s_ng, __popc(bal));
+        wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
+        if (gOnly) s_lg[wbase + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)t;
         const unsigned bala = __ballot_sync(0xFFFFFFFFu, needA);
         int abase = 0;
         if (lane == 0 && bala) abase = atomicAdd(&s_count, __popc(bala));
@@ -179,30 +198,21 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
     __syncthreads();
     const int ng = s_ng, nA = s_count;
 
-    // 4. one pass over the jobs: the centre-referenced reconstruction of
-    // every centre pixel, then the decode of the conservative reference and
-    // the conservative-referenced reconstruction of every pixel that needs
-    // it (as one list, so the few conservative jobs past a multiple of the
-    // CTA size share a round with centre jobs instead of taking a round of
-    // their own)
+    // 4. one pass over the jobs: the centre-referenced reconstruction of the
+    // centre pixels without a mismatch, then the decode of the conservative
+    // reference and the conservative-referenced reconstruction of every pixel
+    // that needs it (as one list, so the few conservative jobs past a
+    // multiple of the CTA size share a round with centre jobs).  A mismatch
+    // blends al R_A + (1 - al) R_G with al = H_center / H_cons of the
+    // conservative strip; when al is exactly 1 (the strip's conservative hits
+    // all carry a centre key: most mismatches in dense hair) the result is
+    // R_A with alpha 1 and the centre reconstruction is not needed; the
+    // others go to a second list.
     for (int li = tid; li < ng + nA; li += kFwdThreads) {
         if (li < ng) {
             const int t = s_lg[li];
             const int tx = t % kFwdTileW, ty = t / kFwdTileW;
-            const int mid = (ty + R) * sw + tx + R;
-            const float3 Cp = make_float3(s_col[mid].x, s_col[mid].y, s_col[mid].z);
-            float4 o;
-            if (!fp.enabled) {
-                o = make_float4(Cp.x, Cp.y, Cp.z, 1.0f);
-            } else {
-                const float2 ts = s_ts[t];
-                const Recon rg = reconstruct_fast_r<true>(R, s_fa, s_col, sw, tx, ty, dg_at(mid), ts.x, ts.y,
-                                                          (s_flag[t] & 1) != 0, Cp, fp);
-                const float invW = 1.0f / rg.W;
-                o = make_float4(rg.S.x * invW, rg.S.y * invW, rg.S.z * invW,
-                                __fdiv_rn((float)rg.hc, (float)rg.ha));
-            }
-            s_out[t] = o;
+            s_out[t] = centre_result(R, s_fa, s_col, sw, tx, ty, s_ts[t], (s_flag[t] & 1) != 0, fp);
         } else {
             const int t = s_list[li - ng];
             const int tx = t % kFwdTileW, ty = t / kFwdTileW;
@@ -232,8 +242,33 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
                 const float iw = 1.0f / ra.W;
                 oa = make_float4(ra.S.x * iw, ra.S.y * iw, ra.S.z * iw, __fdiv_rn((float)ra.hc, (float)ra.ha));
             }
-            s_outA[t] = oa;
+            const int mid = (ty + R) * sw + tx + R;
+            if (dg_at(mid) < 0) {                           // promoted
+                s_out[t] = oa.w >= 0.0f ? oa : make_float4(0.f, 0.f, 0.f, 0.f);
+            } else if (ra.cnt > 0 && ra.hc == ra.ha) {       // mismatch, al = 1
+                s_out[t] = make_float4(oa.x, oa.y, oa.z, 1.0f);
+            } else {                                         // mismatch to blend over the centre result
+                s_outA[t] = oa;
+                s_lb[atomicAdd(&s_nb, 1)] = (uint16_t)t;
+            }
         }
+    }
+    __syncthreads();
+
+    // 5. the blended mismatches: centre reconstruction, then
+    // al R_A + (1 - al) R_G (R_G alone without a conservative contributor), alpha 1
+    const int nb = s_nb;
+    for (int li = tid; li < nb; li += kFwdThreads) {
+        const int t = s_lb[li];
+        const int tx = t % kFwdTileW, ty = t / kFwdTileW;
+        const float4 cg = centre_result(R, s_fa, s_col, sw, tx, ty, s_ts[t], (s_flag[t] & 1) != 0, fp);
+        const float4 a = s_outA[t];
+        float3 c = make_float3(cg.x, cg.y, cg.z);
+        if (a.w >= 0.0f) {
+            const float al = a.w;
+            c = make_float3(al * a.x + (1.0f - al) * c.x, al * a.y + (1.0f - al) * c.y, al * a.z + (1.0f - al) * c.z);
+        }
+        s_out[t] = make_float4(c.x, c.y, c.z, 1.0f);
     }
     __syncthreads();
 
@@ -243,26 +278,8 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
         const int gx = x0 + tx, gy = y0 + ty;
         if (gx >= W || gy >= H) continue;
         const int mid = (ty + R) * sw + tx + R;
-        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-        const bool gP = dg_at(mid) >= 0;
-        if (s_flag[t] & 4) {
-            const float4 a = s_outA[t];
-            if (gP) {                       // depth mismatch: blend over the centre result, alpha 1
-                const float4 cg = s_out[t];
-                float3 c = make_float3(cg.x, cg.y, cg.z);
-                if (a.w >= 0.0f) {
-                    const float al = a.w;
-                    c = make_float3(al * a.x + (1.0f - al) * c.x, al * a.y + (1.0f - al) * c.y,
-                                    al * a.z + (1.0f - al) * c.z);
-                }
-                o = make_float4(c.x, c.y, c.z, 1.0f);
-            } else if (a.w >= 0.0f) {       // promoted
-                o = a;
-            }
-        } else if (gP) {
-            o = s_out[t];
-        }
-        rgba[(int64_t)gy * W + gx] = o;
+        const bool written = dg_at(mid) >= 0 || (s_flag[t] & 4);
+        rgba[(int64_t)gy * W + gx] = written ? s_out[t] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -332,7 +349,7 @@ size_t resolve_smem_bytes(int radius, int tile_h) {
     const int sw = kFwdTileW + 2 * radius, sh = tile_h + 2 * radius, ns = sw * sh;
     size_t b = sizeof(uint64_t) * (HM_MAX_GROOMS_PER_CALL + 1) + 16;   // + alignment of the float4 array
     b += sizeof(float4) * ns;
-    b += sizeof(uint16_t) * (((ns + 7) & ~7) + tile_px) + 16;
+    b += sizeof(uint16_t) * (((ns + 7) & ~7) + 2 * tile_px) + 16;
     b += 2 * sizeof(float4) * tile_px;
     b += sizeof(float2) * tile_px;
     b += tile_px;
