@@ -504,9 +504,6 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
             }
         } else if (nz && gP) {
             const float3 Cp = make_float3(s_col[mid].x, s_col[mid].y, s_col[mid].z);
-            const float2 ts = s_tsG[tid];
-            const bool isoG = s_isoG[tid] != 0;
-            const Recon rg = reconstruct_fast_r<true>(R, s_fa, s_col, sw, tx, ty, dG, ts.x, ts.y, isoG, Cp, fp);
             float3 gG = g, gA = f3(0.f, 0.f, 0.f);
             Recon ra;
             ra.cnt = 0;
@@ -524,8 +521,15 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
                     gG = mul3(g, 1.f - al);
                 }
             }
-            dTsG = reconstruct_adjoint(s_dg, s_col, s_dC, sw, tx, ty, gx, gy, W, H, R, dG, ts.x, ts.y, isoG, true,
-                                       Cp, mid, rg, gG, fp);
+            // blend weight exactly 1: the centre reconstruction gets a zero
+            // gradient and contributes nothing
+            if (!(mism && ra.cnt > 0 && ra.hc == ra.ha)) {
+                const float2 ts = s_tsG[tid];
+                const bool isoG = s_isoG[tid] != 0;
+                const Recon rg = reconstruct_fast_r<true>(R, s_fa, s_col, sw, tx, ty, dG, ts.x, ts.y, isoG, Cp, fp);
+                dTsG = reconstruct_adjoint(s_dg, s_col, s_dC, sw, tx, ty, gx, gy, W, H, R, dG, ts.x, ts.y, isoG,
+                                           true, Cp, mid, rg, gG, fp);
+            }
             if (mism && ra.cnt > 0) {
                 const float2 tsa = s_tsA[tid];
                 dTsA = reconstruct_adjoint(s_dg, s_col, s_dC, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y,
