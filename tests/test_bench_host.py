@@ -1,0 +1,54 @@
+"""Host-side checks of bench.py's contract that need no GPU: the reference
+arm (the CPU oracle) prints one JSON line with the required keys, the CPU
+baseline leg describes its sample, and committed ncu figures are tied to the
+sources of the kernel they were taken on."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def test_reference_arm_json_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "tiny_256", "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=300,
+                       cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1
+    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert "workload" in d["config"]
+
+
+def test_cpu_baseline_whole_small_workload():
+    import bench
+    scene, _ = bench.make_scene("tiny_256")
+    cb = bench.cpu_baseline(scene)
+    assert cb["kind"] == "oracle" and cb["value"] > 0 and cb["unit"] == bench.UNIT
+    assert cb["sample"].startswith("the whole workload (8000 segments")
+
+
+def test_traffic_record_follows_kernel_sources(tmp_path, monkeypatch):
+    import bench
+    h = bench.kernel_src_hash("raster_kernel")
+    assert h == bench.kernel_src_hash("raster_kernel") and h != bench.kernel_src_hash("resolve_kernel")
+    rec = {"single_1080p": {"raster_kernel": {"dram_bytes_per_launch": 123.0, "red_sectors_per_atomic": 0.9,
+                                              "src_hash": h},
+                            "resolve_kernel": {"dram_bytes_per_launch": 456.0, "src_hash": "stale"}}}
+    f = tmp_path / "traffic.json"
+    f.write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench.ncu_traffic("raster_kernel", "single_1080p") == 123.0
+    assert bench.ncu_red_sectors_per_atomic("single_1080p") == 0.9
+    assert bench.ncu_traffic("resolve_kernel", "single_1080p") is None     # taken on other sources
+    assert bench.ncu_traffic("raster_kernel", "crowd_4k") is None          # other workload
