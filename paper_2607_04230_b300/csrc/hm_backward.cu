@@ -11,8 +11,11 @@
 // tile pixel's reconstruction, then push dL/dC of every contributing
 // neighbour into a per-pixel colour-gradient buffer, and dL/d(screen
 // tangent) of the pixel's reference segment straight into the geometry.
-// Kernel 2 (pixels): shading adjoint of every centre-sample pixel with a
-// colour gradient.
+// Kernel 2 (keys): every key with a gradient (a centre key with a colour or
+// screen-tangent gradient, a conservative key with a screen-tangent
+// gradient), compacted into job lists per pixel chunk: shading and
+// screen-tangent adjoints chained through the strand geometry to the layer
+// vertices, plus the albedo gradient.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -563,10 +566,11 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
     if (inside) dTs[(int64_t)gy * W + gx] = make_float4(dTsG.x, dTsG.y, dTsA.x, dTsA.y);
 }
 
-// Geometry pass, one thread per pixel (persistent grid): the shading
-// adjoint of the centre-sample pixel (colour gradient from kernel 1) plus the
-// screen-tangent adjoints of the pixel's reference segments, chained through
-// the strand geometry to the layer vertices, and the albedo gradient.  When
+// Geometry pass, one thread per key with a gradient (persistent grid over
+// pixel chunks compacted into job lists): the shading adjoint of a centre
+// key (colour gradient from kernel 1) or the screen-tangent adjoint of a
+// reference segment, chained through the strand geometry to the layer
+// vertices, and the albedo gradient.  When
 // every groom's layer-vertex gradient fits, a CTA accumulates it in shared
 // memory and adds it to the global arrays once at the end.
 // 256 threads and four CTAs per SM (a 64-register budget): the decode and

@@ -2,11 +2,11 @@
 // key decode and shading (Sec. 3.1.2, Sec. 3.4), strand connection,
 // elliptical bilateral filter and alpha estimation (Sec. 3.3.1-3.3.3).
 //
-// One CTA per 32x16 output tile.  The tile plus an r-pixel halo is staged in
-// shared memory: per staged pixel the centre-layer depth (or -1 when empty),
-// the conservative-layer occupancy and the shaded colour of centre-sample
-// pixels.  Decode + shading work is compacted into lists so whole warps stay
-// busy, then every thread filters its own tile pixel from shared memory.
+// One CTA per 32x32 (or 32x16) output tile.  The tile plus an r-pixel halo
+// is staged in shared memory: per staged pixel the centre-layer depth (a
+// large negative value when empty), the conservative-layer occupancy and the
+// shaded colour of centre-sample pixels.  Decode, shading and the
+// reconstructions run over compacted lists so whole warps stay busy.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -18,10 +18,12 @@ namespace hm {
 
 // Forward resolve tiles: 32x32 output pixels per CTA of 512 threads, so the
 // halo recompute is (32 + 2r)^2 / 32^2.  Work runs in uniform phases over
-// compacted lists: decode + shade the staged centre-sample pixels; decode the
-// conservative key where it is the reference (promoted pixels, depth
-// mismatch); the centre-referenced reconstruction of every centre pixel; the
-// conservative-referenced one where needed; then one combine pass writes RGBA.
+// compacted lists: decode + shade the staged centre-sample pixels; one list
+// of centre-referenced reconstructions (centre pixels without a depth
+// mismatch) and conservative-key decodes + conservative-referenced
+// reconstructions (promoted pixels, depth mismatches); the centre
+// reconstruction of the mismatches that blend (weight below 1); then the
+// tile is written row-major.
 constexpr int kFwdTileW = 32, kFwdThreads = 512;
 // staged depth of a pixel without a centre key: far below any d24, so a
 // depth-difference test alone rejects it
