@@ -534,24 +534,43 @@ __device__ __forceinline__ void raster_item_msaa(const SegRec &q_shared, int i, 
     const I k_cen = (I)q.hc * ((I)abs(q.du) + (I)abs(q.dv));
     const uint64_t id = ((uint64_t)q.id_hi << 32) | q.id_lo;
     const bool degenerate = (q.du == 0 && q.dv == 0);
-    for (int m = mlo; m <= mhi; ++m) {
+    typedef typename std::make_unsigned<I>::type U;
+    // per sample k: offsets of the line cross product and of the depth
+    // numerator from the pixel centre's, and the major-axis part of the box
+    // overlap (the same for every row of this column)
+    I dk[N], dnk[N];
+    int32_t ovk[N];
+    bool uin[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        int ox, oy;
+        sample_offset<N>(k, ox, oy);
+        const int32_t ou = xm ? ox : oy, ov = xm ? oy : ox;
+        dk[k] = du * (I)ov - dv * (I)ou;
+        dnk[k] = (I)ou * du + (I)ov * dv;
+        ovk[k] = ov;
+        const int32_t su = cu + ou;
+        uin[k] = q.umin <= su + q.hc && q.umax >= su - q.hc;
+    }
+    // cross product and depth numerator at the pixel centre, advanced by
+    // constants from row to row
+    I e0 = du * (I)(256 * mlo + 128 - q.vA) - dv * (I)(cu - q.uA);
+    I num0 = (I)(cu - q.uA) * du + (I)(256 * mlo + 128 - q.vA) * dv;
+    const I de = du * 256, dn = dv * 256;
+    for (int m = mlo; m <= mhi; ++m, e0 += de, num0 += dn) {
         const int32_t cv = 256 * m + 128;
-        const I e0 = du * (I)(cv - q.vA) - dv * (I)(cu - q.uA);
-        const I num0 = (I)(cu - q.uA) * du + (I)(cv - q.vA) * dv;
         const int px = xm ? i : m, py = xm ? m : i;
         const int64_t p = (int64_t)((uint32_t)py * (uint32_t)W + (uint32_t)px);
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            int ox, oy;
-            sample_offset<N>(k, ox, oy);
-            const int32_t ou = xm ? ox : oy, ov = xm ? oy : ox;
-            const int32_t su = cu + ou, sv = cv + ov;
-            if (q.umin > su + q.hc || q.umax < su - q.hc || q.vmin > sv + q.hc || q.vmax < sv - q.hc) continue;
-            const I ek = e0 + du * (I)ov - dv * (I)ou;
-            if (ek > k_cen || ek < -k_cen) continue;
+            const int32_t sv = cv + ovk[k];
+            // closed box of half-width hc around the sample: boxes overlap and
+            // |cross product| <= hc (|dU| + |dV|) (one unsigned compare)
+            if (!uin[k] || q.vmin > sv + q.hc || q.vmax < sv - q.hc) continue;
+            if ((U)(e0 + dk[k] + k_cen) > (U)(2 * k_cen)) continue;
             float t = 0.0f;
             if (!degenerate) {
-                const I nk = num0 + (I)ou * du + (I)ov * dv;
+                const I nk = num0 + dnk[k];
                 const float fn = sizeof(I) == 4 ? __int2float_rn((int32_t)nk) : __ll2float_rn((int64_t)nk);
                 t = fclamp(fdiv(fn, q.fden), 0.0f, 1.0f);
             }
