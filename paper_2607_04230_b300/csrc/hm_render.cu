@@ -516,7 +516,12 @@ __device__ __forceinline__ void raster_item_msaa(const SegRec &q_shared, int i, 
     const SegRec q = q_shared;
     const bool xm = q.flags & 1;
     const int32_t cu = 256 * i + 128;
-    const int32_t ua = max(cu - 256, q.umin), ub = min(cu + 256, q.umax);
+    // largest sample offset from the pixel centre (1/256 px) and the box
+    // half-width: a covered sample's box holds a segment point within
+    // kOff + hc of the centre along either axis
+    constexpr int32_t kOff = N == 1 ? 0 : (N == 2 ? 64 : (N == 4 ? 96 : 112));
+    const int32_t reach = kOff + q.hc;
+    const int32_t ua = max(cu - reach, q.umin), ub = min(cu + reach, q.umax);
     if (ua > ub) return;
     const float va = (float)(ua - q.uA) * q.slope, vb = (float)(ub - q.uA) * q.slope;
     const float flo = floorf(fminf(va, vb)), fhi = ceilf(fmaxf(va, vb));
@@ -525,9 +530,9 @@ __device__ __forceinline__ void raster_item_msaa(const SegRec &q_shared, int i, 
     const int32_t vlo = q.vA + (int32_t)flo - slack;
     const int32_t vhi = q.vA + (int32_t)fhi + slack;
     const int dimv = xm ? H : W;
-    // rows m whose sample points (within 240/256 px of the centre) can reach [vlo, vhi]
-    const int mlo = max((vlo - 368 + 255) >> 8, 0);
-    const int mhi = min((vhi + 112) >> 8, dimv - 1);
+    // rows m whose sample boxes can reach [vlo, vhi]: vlo - reach <= 256 m + 128 <= vhi + reach
+    const int mlo = max((vlo - reach - 128 + 255) >> 8, 0);
+    const int mhi = min((vhi + reach - 128) >> 8, dimv - 1);
     // I: 32-bit for short segments (|dU|, |dV| < 2^14), whose cross products
     // and numerators at the candidate samples stay below 2^30
     const I du = q.du, dv = q.dv;
@@ -650,7 +655,11 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_msaa_kernel(CallTabl
                 r.slope = r.du == 0 ? 0.0f : (float)r.dv / (float)r.du;
                 r.flags = (xm ? 1 : 0) | ((abs(r.du) < (1 << 14) && abs(r.dv) < (1 << 14)) ? 2 : 0);
                 const int du = xm ? W : H, dv = xm ? H : W;
-                int ilo = ((r.umin + 255) >> 8) - 2, ihi = (r.umax >> 8) + 1;
+                // columns i whose sample boxes (centre 256 i + 128, sample
+                // offsets up to kOff, half-width hc) can reach [umin, umax]
+                constexpr int32_t kOff = N == 1 ? 0 : (N == 2 ? 64 : (N == 4 ? 96 : 112));
+                const int32_t reach = kOff + r.hc;
+                int ilo = (r.umin - reach - 128 + 255) >> 8, ihi = (r.umax + reach - 128) >> 8;
                 ilo = max(ilo, 0);
                 ihi = min(ihi, du - 1);
                 const bool vin = r.vmax >= -256 && r.vmin <= 256 * dv + 256;
