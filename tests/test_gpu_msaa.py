@@ -101,3 +101,16 @@ def test_msaa_1080p_full_size():
     sc = synth.scene_single_1080p()
     cov, _ = _check(sc, 4, sample=5000)
     assert (cov > 0).sum() > 100_000
+
+
+@pytest.mark.parametrize("N", [2, 4, 8])
+def test_msaa_thick_strands_largest_reach(N):
+    """Strands wide enough that the sample box half-width saturates at half a
+    pixel and short segments at grazing angles: the candidate columns and rows
+    reach the farthest a sample box can (largest sample offset + 128/256 px),
+    and every sample must still match the oracle."""
+    sc = synth.tiny_scene(34, width=120, height=90, num_strands=500, segments=5, num_layers=4,
+                          length_m=0.03, dist_m=0.25, jitter_m=0.004)
+    sc.grooms[0].strand_width_m = np.float32(0.004)
+    cov, err = _check(sc, N)
+    assert (cov == N).sum() > 500 and err <= RGBA_TOL
