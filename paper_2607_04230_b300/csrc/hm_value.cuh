@@ -265,14 +265,15 @@ __device__ __forceinline__ Recon reconstruct_fast(const uint8_t *s_fa, const flo
     int cnt = 0;
     for (int dy = -R; dy <= R; ++dy) {
         const int row = (ly + dy + R) * sw + lx + R;
+        const float ypar = (float)dy * uy, yb = (float)(dy * dy) * b;   // per-row parts of dpar and |d|^2 b
 #pragma unroll
         for (int dx = -R; dx <= R; ++dx) {
             const int idx = row + dx;
             const float4 cq = s_col[idx];          // rgb, centre depth bits
             const bool ok = abs(__float_as_int(cq.w) - ref) <= fp.drej;
             cnt += ok ? 1 : 0;
-            const float dpar = fmaf((float)dy, uy, (float)dx * ux);
-            float e = fmaf(dpar * a, dpar, (float)(dx * dx + dy * dy) * b);
+            const float dpar = fmaf((float)dx, ux, ypar);
+            float e = fmaf(dpar * a, dpar, fmaf((float)(dx * dx), b, yb));
             if (kColor) {
                 const float ex = Cp.x - cq.x, ey = Cp.y - cq.y, ez = Cp.z - cq.z;
                 e = fmaf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)), c, e);
