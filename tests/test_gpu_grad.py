@@ -133,3 +133,54 @@ def test_gradient_large_layer_vertex_set():
     sc = synth.tiny_scene(25, width=96, height=80, num_strands=600, dist_m=0.3, k=8, n=4, num_layers=4)
     assert sc.grooms[0].layer_verts.size > 11 * 1024
     _grad_case(sc)
+
+
+def test_gradient_vs_central_differences():
+    """The GPU layer-vertex and albedo gradients against central differences
+    (step 1e-5 m, and 1e-5 in albedo) of the FP64 oracle's forward with the
+    GPU's (bit-exact) visibility held fixed, on the largest entries and a
+    few random ones."""
+    from paper_2607_04230_b300 import autograd, hm
+    sc = synth.tiny_scene(26, width=80, height=64, num_strands=300, dist_m=0.3)
+    g = sc.grooms[0]
+    W, H = sc.camera.width, sc.camera.height
+    rng = np.random.default_rng(3)
+    target = rng.random((W * H, 3)) * 0.2
+    handle = hm.upload_scene(sc)[0]
+    frame = hm.Frame(W, H)
+    lv = torch.from_numpy(g.layer_verts).cuda().requires_grad_(True)
+    alb = torch.from_numpy(g.strand_albedo).cuda().requires_grad_(True)
+    rgba = autograd.render(handle, sc, frame, lv, alb)
+    t = torch.from_numpy(target).float().cuda()
+    loss = torch.sqrt(((rgba.reshape(-1, 4)[:, :3] * rgba.reshape(-1, 4)[:, 3:4] - t) ** 2).sum())
+    loss.backward()
+    glv, galb = lv.grad.cpu().numpy().astype(np.float64), alb.grad.cpu().numpy().astype(np.float64)
+    lods, vc, va, _ = oracle_keys(sc)
+    gk, ak = frame.keys_numpy()
+    assert_keys_equal(gk, vc, "centre layer")
+    assert_keys_equal(ak, va, "conservative layer")
+    dec = oracle.resolve_decisions(sc.grooms, sc.camera, lods, sc.filt, vc, va)
+    tgt = torch.from_numpy(target)
+
+    def f(lv64, alb64):
+        gt = v64.GroomT(g, lods[0][1], 0, layer_verts=lv64, albedo=alb64, lod_n=lods[0][0])
+        r, pix = v64.resolve([gt], sc.camera, sc.lights, sc.filt, vc, va, dec)
+        img = torch.zeros((W * H, 3), dtype=torch.float64).index_put((torch.from_numpy(pix),), r[:, :3] * r[:, 3:4])
+        return torch.sqrt(((img - tgt) ** 2).sum()).item()
+
+    lv0 = torch.from_numpy(g.layer_verts.astype(np.float64))
+    alb0 = torch.from_numpy(g.strand_albedo.astype(np.float64))
+    h = 1e-5
+    scale = np.abs(glv).max()
+    for idx in list(np.argsort(-np.abs(glv).ravel())[:8]) + list(rng.integers(0, glv.size, 4)):
+        e = torch.zeros(glv.size, dtype=torch.float64)
+        e[idx] = h
+        e = e.reshape(lv0.shape)
+        fd = (f(lv0 + e, alb0) - f(lv0 - e, alb0)) / (2 * h)
+        assert abs(fd - glv.ravel()[idx]) <= 1e-2 * max(abs(fd), 1e-3 * scale), (idx, fd, glv.ravel()[idx])
+    for idx in np.argsort(-np.abs(galb).ravel())[:4]:
+        e = torch.zeros(galb.size, dtype=torch.float64)
+        e[idx] = h
+        e = e.reshape(alb0.shape)
+        fd = (f(lv0, alb0 + e) - f(lv0, alb0 - e)) / (2 * h)
+        assert abs(fd - galb.ravel()[idx]) <= 1e-2 * abs(fd), (idx, fd, galb.ravel()[idx])
