@@ -891,6 +891,7 @@ def run_native(args, rank, world, local_rank):
             "config": dict(cfg, parallelism=f"replicas x{world}"),
             "frame_ms": {k: round(v, 5) for k, v in phase_ms.items()},
             "segments_per_frame": segs, "raster_segments_per_s": segs / t_r,
+            "lod_raster_segments_per_s": segs / ((phase_ms["lod"] + phase_ms["raster"]) * 1e-3),
             "roofline": roofline, "kernels": kernels,
             "e2e": e2e, "gpu_launches": LAUNCHES_PER_FRAME * args.steps, "clocks": clk, "wall_s": wall,
             "autotune": tune and {"tuning": tune["tuning"], "best_ms": tune["ms"], "candidates": len(tune["table"])}}
