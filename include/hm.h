@@ -326,14 +326,25 @@ hm_status hm_render_visibility_range(const hm_groom *grooms, int32_t n, int32_t 
  * shading): decode each key back to its strand segment, shade centre-sample
  * pixels, run the strand-connection / elliptical bilateral filter and alpha
  * estimation, and write straight-alpha RGBA.
- * d_rgba: [height][width][4] float32, 16-byte aligned.  d_tape: reserved,
- * pass NULL.  Same grooms, in the same order, as the render call that wrote
- * the keys.
+ * d_rgba: [height][width][4] float32, 16-byte aligned.
+ * d_tile_scratch: NULL, or DEVICE scratch of hm_resolve_scratch_bytes(width,
+ * height) bytes, 4-byte aligned, owned by the caller and not used by any
+ * other work in flight.  NULL: one CTA per output tile, each finding out
+ * whether its tile holds keys (best when most tiles do, a single groom
+ * filling the frame).  With scratch: a pre-pass lists the tiles that hold
+ * conservative keys (zero-filling the others) and a persistent grid resolves
+ * the listed tiles only (best for sparse frames such as a crowd at 4K).  The
+ * image is bit-identical either way.
+ * Same grooms, in the same order, as the render call that wrote the keys.
  * Errors: HM_ERR_INVALID_ARG, HM_ERR_CUDA. */
 hm_status hm_resolve_shade(const hm_groom *grooms, int32_t n, const hm_camera *cam,
                            const hm_lights *lights, const hm_filter_params *filt,
                            const uint64_t *d_vis_center, const uint64_t *d_vis_cons,
-                           float *d_rgba, void *d_tape, void *stream);
+                           float *d_rgba, void *d_tile_scratch, void *stream);
+
+/* Bytes of hm_resolve_shade's optional tile scratch at this resolution (0
+ * for a resolution out of range). */
+size_t hm_resolve_scratch_bytes(int32_t width, int32_t height);
 
 /* Adjoint of hm_resolve_shade with the visibility keys, the pixel-centre
  * projection parameters and every filter mask held fixed (the alpha is then

@@ -18,7 +18,9 @@ class Crowd:
         import torch
         self.scene = scene
         self.grooms = hm.upload_scene(scene, stream=stream)
-        self.frame = hm.Frame(scene.camera.width, scene.camera.height)
+        # a crowd covers a small part of the frame: the resolve lists its
+        # occupied tiles first
+        self.frame = hm.Frame(scene.camera.width, scene.camera.height, tile_list=True)
         self.graph = None
         self._torch = torch
 
@@ -46,4 +48,5 @@ class Crowd:
         sc, fr = self.scene, self.frame
         for i in range(len(self.grooms)):
             hm.render_visibility_range(self.grooms, i, 1, sc.camera, fr.vis_center, fr.vis_cons, clear=(i == 0))
-        hm.resolve_shade(self.grooms, sc.camera, sc.lights, sc.filt, fr.vis_center, fr.vis_cons, fr.rgba)
+        hm.resolve_shade(self.grooms, sc.camera, sc.lights, sc.filt, fr.vis_center, fr.vis_cons, fr.rgba,
+                         tile_scratch=fr.tile_scratch)

@@ -644,11 +644,11 @@ static hm_status lights_dev(const hm_lights *l, hm::LightsDev &ld) {
 
 hm_status hm_resolve_shade(const hm_groom *grooms, int32_t n, const hm_camera *cam, const hm_lights *lights,
                            const hm_filter_params *filt, const uint64_t *d_vis_center, const uint64_t *d_vis_cons,
-                           float *d_rgba, void *d_tape, void *stream) {
-    (void)d_tape;
+                           float *d_rgba, void *d_tile_scratch, void *stream) {
     hm_status st = check_camera(cam);
     if (st != HM_OK) return st;
     if (!d_vis_center || !d_vis_cons || !d_rgba) return fail(HM_ERR_INVALID_ARG, "buffer is NULL");
+    if (reinterpret_cast<uintptr_t>(d_tile_scratch) & 3) return fail(HM_ERR_INVALID_ARG, "misaligned tile scratch");
     if ((reinterpret_cast<uintptr_t>(d_rgba) & 15) || (reinterpret_cast<uintptr_t>(d_vis_center) & 7) ||
         (reinterpret_cast<uintptr_t>(d_vis_cons) & 7))
         return fail(HM_ERR_INVALID_ARG, "misaligned buffer");
@@ -663,10 +663,16 @@ hm_status hm_resolve_shade(const hm_groom *grooms, int32_t n, const hm_camera *c
     if (!sw) return fail(HM_ERR_CUDA, "device status word unavailable");
     phase(4, static_cast<cudaStream_t>(stream));
     HM_CUDA(hm::launch_resolve(tab, cam_dev(cam), ld, fd, d_vis_center, d_vis_cons, d_rgba, sw,
-                               g_tuning.resolve_tile_h, static_cast<cudaStream_t>(stream)),
+                               g_tuning.resolve_tile_h, static_cast<cudaStream_t>(stream), nullptr,
+                               static_cast<int *>(d_tile_scratch)),
             "resolve");
     phase(5, static_cast<cudaStream_t>(stream));
     return HM_OK;
+}
+
+size_t hm_resolve_scratch_bytes(int32_t width, int32_t height) {
+    if (width < 1 || height < 1 || width > HM_MAX_RESOLUTION || height > HM_MAX_RESOLUTION) return 0;
+    return hm::resolve_list_bytes(width, height);
 }
 
 hm_status hm_resolve_compressed(const hm_camera *cam, const hm_lights *lights, const hm_filter_params *filt,

@@ -52,7 +52,9 @@ cudaError_t launch_raster(const CallTable &tab, const ViewSet &views, bool prech
 cudaError_t launch_probe_atomic_min(uint64_t *buf, int64_t n, int rounds, int pattern, cudaStream_t st);
 cudaError_t launch_resolve(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                            const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status, int tile_h,
-                           cudaStream_t st, const CgbDev *compressed = nullptr);
+                           cudaStream_t st, const CgbDev *compressed = nullptr, int *tile_list = nullptr);
+// Bytes of the resolve's optional tile-list scratch at this resolution.
+size_t resolve_list_bytes(int W, int H);
 cudaError_t launch_resolve_adjoint(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                                    const uint64_t *vis_c, const uint64_t *vis_a, const float *grad_rgba,
                                    float *const *glv, float *const *galb, void *scratch, uint32_t *status,

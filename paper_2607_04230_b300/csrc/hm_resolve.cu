@@ -47,12 +47,38 @@ __device__ __forceinline__ float4 centre_result(int R, const uint8_t *s_fa, cons
 // kCgb: the keys carry the compressed payload (Sec. 3.1.2) and shading
 // reads it alone: position from depth, tangent from its code, albedo from
 // the appearance table at (u, v) scaled along w, AO from its code.
+// Tile list for sparse frames: every tile that holds at least one
+// conservative key is appended to list[2 ..] (list[0] = count); every other
+// tile is written with zeros here (no key: RGBA 0).  One warp per tile, lane
+// = column, rows walked.
+template <int kFwdTileH>
+__global__ void __launch_bounds__(256) resolve_tiles_kernel(const uint64_t *__restrict__ vis_a,
+                                                            float4 *__restrict__ rgba, int W, int H, int ntx,
+                                                            int ntiles, int *list) {
+    const int tile = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (tile >= ntiles) return;
+    const int gx = (tile % ntx) * kFwdTileW + lane, y0 = (tile / ntx) * kFwdTileH;
+    const int y1 = min(y0 + kFwdTileH, H);
+    bool any = false;
+    if (gx < W)
+        for (int y = y0; y < y1; ++y)
+            any |= !key_empty(__ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)y * W + gx)));
+    if (__any_sync(0xFFFFFFFFu, any)) {
+        if (lane == 0) list[2 + atomicAdd(&list[0], 1)] = tile;
+    } else if (gx < W) {
+        for (int y = y0; y < y1; ++y) rgba[(int64_t)y * W + gx] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// list == nullptr: one CTA per tile (grid = tiles); tiles without keys are
+// found and zero-filled here.  list != nullptr: a persistent grid takes the
+// listed tiles one at a time from the work counter list[1].
 template <int kFwdTileH, bool kCgb>
 __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, CamDev cam, LightsDev Ls, FilterDev fp,
                                                               const uint64_t *__restrict__ vis_c,
                                                               const uint64_t *__restrict__ vis_a,
                                                               float4 *__restrict__ rgba, uint32_t *status,
-                                                              CgbDev cg) {
+                                                              CgbDev cg, int *list) {
     constexpr int kFwdTilePx = kFwdTileW * kFwdTileH;
     extern __shared__ __align__(16) unsigned char smem[];
     const int R = fp.enabled ? fp.radius : 0;
@@ -72,35 +98,51 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
     float2 *s_ts = reinterpret_cast<float2 *>(s_outA + kFwdTilePx);  // G screen tangent
     uint8_t *s_flag = reinterpret_cast<uint8_t *>(s_ts + kFwdTilePx); // bit0 isoG, bit1 isoA, bit2 needs A
     uint8_t *s_fa = s_flag + kFwdTilePx;
-    __shared__ int s_count, s_ng, s_nb;
+    __shared__ int s_count, s_ng, s_nb, s_tile;
 
     const int tid = threadIdx.x, lane = tid & 31;
-    const int x0 = blockIdx.x * kFwdTileW, y0 = blockIdx.y * kFwdTileH;
     const int W = cam.W, H = cam.H;
+    const int ntx = (W + kFwdTileW - 1) / kFwdTileW;
+    const int nlisted = list ? list[0] : 0;
     if (tid <= tab.n) {
         uint64_t b = 0;
         for (int i = 0; i < tid; ++i) b += (uint64_t)tab.g[i].S;
         s_bases[tid] = b;
     }
+    for (int it = 0;; ++it) {
     if (tid == 0) {
+        if (list) s_tile = atomicAdd(&list[1], 1);
         s_count = 0;
         s_ng = 0;
         s_nb = 0;
     }
-    // 0. a tile whose pixels hold no conservative key has nothing to resolve
-    // (no centre key either: centre keys are a subset): write zeros, done
-    bool any = false;
-    for (int t = tid; t < kFwdTilePx; t += kFwdThreads) {
-        const int gx = x0 + t % kFwdTileW, gy = y0 + t / kFwdTileW;
-        if (gx < W && gy < H)
-            any |= !key_empty(__ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx)));
+    int tile;
+    if (list) {
+        __syncthreads();
+        if (s_tile >= nlisted) break;
+        tile = list[2 + s_tile];
+    } else {
+        if (it > 0) break;
+        tile = blockIdx.y * ntx + blockIdx.x;
     }
-    if (!__syncthreads_or(any)) {
+    const int x0 = (tile % ntx) * kFwdTileW, y0 = (tile / ntx) * kFwdTileH;
+    if (!list) {
+        // 0. a tile whose pixels hold no conservative key has nothing to
+        // resolve (no centre key either: centre keys are a subset): zeros
+        bool any = false;
         for (int t = tid; t < kFwdTilePx; t += kFwdThreads) {
             const int gx = x0 + t % kFwdTileW, gy = y0 + t / kFwdTileW;
-            if (gx < W && gy < H) rgba[(int64_t)gy * W + gx] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gx < W && gy < H)
+                any |= !key_empty(
+                    __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx)));
         }
-        return;
+        if (!__syncthreads_or(any)) {
+            for (int t = tid; t < kFwdTilePx; t += kFwdThreads) {
+                const int gx = x0 + t % kFwdTileW, gy = y0 + t / kFwdTileW;
+                if (gx < W && gy < H) rgba[(int64_t)gy * W + gx] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            continue;
+        }
     }
 
     // 1. stage keys of tile + halo; list staged centre-sample pixels
@@ -283,6 +325,8 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
         const bool written = dg_at(mid) >= 0 || (s_flag[t] & 4);
         rgba[(int64_t)gy * W + gx] = written ? s_out[t] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    __syncthreads();                // shared memory is reused by the next tile
+    }
 }
 
 // Multisample resolve: every covered sample is decoded at its own sample
@@ -362,31 +406,52 @@ size_t resolve_smem_bytes(int radius, int tile_h) {
 template <int TH, bool C>
 static cudaError_t launch_resolve_t(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                                    const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status,
-                                   cudaStream_t st, const CgbDev &cg) {
+                                   cudaStream_t st, const CgbDev &cg, int *tile_list) {
     const int R = fp.enabled ? fp.radius : 0;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static int resident = 0;
+    if (resident == 0) {
         cudaFuncSetAttribute(resolve_kernel<TH, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)resolve_smem_bytes(HM_MAX_FILTER_RADIUS, TH));
-        attr_set = true;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resolve_kernel<TH, C>, kFwdThreads,
+                                                      resolve_smem_bytes(HM_MAX_FILTER_RADIUS, TH));
+        resident = (per_sm > 0 ? per_sm : 1) * num_sms();
     }
     dim3 grid((cam.W + kFwdTileW - 1) / kFwdTileW, (cam.H + TH - 1) / TH);
-    resolve_kernel<TH, C><<<grid, kFwdThreads, resolve_smem_bytes(R, TH), st>>>(
-        tab, cam, Ls, fp, vis_c, vis_a, reinterpret_cast<float4 *>(rgba), status, cg);
+    float4 *out = reinterpret_cast<float4 *>(rgba);
+    if (!tile_list) {
+        resolve_kernel<TH, C><<<grid, kFwdThreads, resolve_smem_bytes(R, TH), st>>>(tab, cam, Ls, fp, vis_c, vis_a,
+                                                                                    out, status, cg, nullptr);
+        return cudaGetLastError();
+    }
+    const int ntiles = (int)(grid.x * grid.y);
+    cudaError_t e = cudaMemsetAsync(tile_list, 0, 2 * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    resolve_tiles_kernel<TH><<<(ntiles + 7) / 8, 256, 0, st>>>(vis_a, out, cam.W, cam.H, (int)grid.x, ntiles,
+                                                             tile_list);
+    resolve_kernel<TH, C><<<resident < ntiles ? resident : ntiles, kFwdThreads, resolve_smem_bytes(R, TH), st>>>(
+        tab, cam, Ls, fp, vis_c, vis_a, out, status, cg, tile_list);
     return cudaGetLastError();
+}
+
+size_t resolve_list_bytes(int W, int H) {
+    const size_t ntiles = (size_t)((W + kFwdTileW - 1) / kFwdTileW) * (size_t)((H + 15) / 16);   // 32 x 16 tiles at most
+    return sizeof(int) * (ntiles + 2);
 }
 
 // Resolve tile: 32 x tile_h output pixels per CTA (tile_h 16 or 32).
 cudaError_t launch_resolve(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                            const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status, int tile_h,
-                           cudaStream_t st, const CgbDev *compressed) {
+                           cudaStream_t st, const CgbDev *compressed, int *tile_list) {
     if (compressed) {
-        if (tile_h == 16) return launch_resolve_t<16, true>(tab, cam, Ls, fp, vis_c, vis_a, rgba, status, st, *compressed);
-        return launch_resolve_t<32, true>(tab, cam, Ls, fp, vis_c, vis_a, rgba, status, st, *compressed);
+        if (tile_h == 16)
+            return launch_resolve_t<16, true>(tab, cam, Ls, fp, vis_c, vis_a, rgba, status, st, *compressed, tile_list);
+        return launch_resolve_t<32, true>(tab, cam, Ls, fp, vis_c, vis_a, rgba, status, st, *compressed, tile_list);
     }
     const CgbDev none{nullptr, 0.0f, 0.0f};
-    if (tile_h == 16) return launch_resolve_t<16, false>(tab, cam, Ls, fp, vis_c, vis_a, rgba, status, st, none);
-    return launch_resolve_t<32, false>(tab, cam, Ls, fp, vis_c, vis_a, rgba, status, st, none);
+    if (tile_h == 16)
+        return launch_resolve_t<16, false>(tab, cam, Ls, fp, vis_c, vis_a, rgba, status, st, none, tile_list);
+    return launch_resolve_t<32, false>(tab, cam, Ls, fp, vis_c, vis_a, rgba, status, st, none, tile_list);
 }
 
 }  // namespace hm

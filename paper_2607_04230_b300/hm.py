@@ -131,6 +131,8 @@ def lib():
     if hasattr(L, "hm_backward_scratch_bytes"):
         L.hm_backward_scratch_bytes.argtypes = [i32, i32]
         L.hm_backward_scratch_bytes.restype = ctypes.c_size_t
+        L.hm_resolve_scratch_bytes.argtypes = [i32, i32]
+        L.hm_resolve_scratch_bytes.restype = ctypes.c_size_t
     L.hm_status_string.argtypes = [ctypes.c_int]
     L.hm_status_string.restype = ctypes.c_char_p
     L.hm_last_error.argtypes = []
@@ -345,11 +347,19 @@ def render_shadow_map(grooms, light_cam, map_center, map_cons, stats=None, strea
                                      _stream_ptr(stream)))
 
 
-def resolve_shade(grooms, cam, lights, filt, vis_center, vis_cons, rgba, stream=None, shadows=None):
+def resolve_shade(grooms, cam, lights, filt, vis_center, vis_cons, rgba, stream=None, shadows=None,
+                  tile_scratch=None):
+    """tile_scratch: None, or a device tensor of resolve_scratch_bytes(W, H)
+    bytes: list the tiles holding keys first and resolve only those (sparse
+    frames)."""
     arr, n = _handles(grooms)
     c, L, f = camera_struct(cam), lights_struct(lights, shadows), filter_struct(filt)
     check(lib().hm_resolve_shade(arr, n, ctypes.byref(c), ctypes.byref(L), ctypes.byref(f), _dptr(vis_center),
-                                 _dptr(vis_cons), _dptr(rgba), None, _stream_ptr(stream)))
+                                 _dptr(vis_cons), _dptr(rgba), _dptr(tile_scratch), _stream_ptr(stream)))
+
+
+def resolve_scratch_bytes(width: int, height: int) -> int:
+    return int(lib().hm_resolve_scratch_bytes(int(width), int(height)))
 
 
 def render_visibility_msaa(grooms, cam, samples: int, vis_samples, clear=True, stats=None, stream=None):
@@ -447,7 +457,8 @@ def get_device_status(stream=None):
 class Frame:
     """Device buffers of one frame: two key layers, RGBA, counters."""
 
-    def __init__(self, width: int, height: int, device="cuda"):
+    def __init__(self, width: int, height: int, device="cuda", tile_list: bool = False):
+        """tile_list: hold the resolve's tile-list scratch (sparse frames)."""
         import torch
         npx = width * height
         self.width, self.height = width, height
@@ -455,6 +466,10 @@ class Frame:
         self.vis_cons = torch.empty(npx, dtype=torch.int64, device=device)
         self.rgba = torch.empty((height, width, 4), dtype=torch.float32, device=device)
         self.stats = torch.zeros(8, dtype=torch.int64, device=device)
+        self.tile_scratch = None
+        if tile_list:
+            self.tile_scratch = torch.empty((resolve_scratch_bytes(width, height) + 3) // 4, dtype=torch.int32,
+                                            device=device)
 
     def keys_numpy(self):
         return (self.vis_center.cpu().numpy().view(np.uint64), self.vis_cons.cpu().numpy().view(np.uint64))
@@ -465,7 +480,7 @@ def render(grooms, scene, frame: Frame, stream=None, shadows=None):
     shadows as for lights_struct."""
     render_visibility(grooms, scene.camera, frame.vis_center, frame.vis_cons, stats=frame.stats, stream=stream)
     resolve_shade(grooms, scene.camera, scene.lights, scene.filt, frame.vis_center, frame.vis_cons, frame.rgba,
-                  stream=stream, shadows=shadows)
+                  stream=stream, shadows=shadows, tile_scratch=frame.tile_scratch)
 
 
 def upload_scene(scene, stream=None):

@@ -183,3 +183,36 @@ def test_segment_records_and_regeneration_agree():
     ref, pix = oracle_rgba(sc, lods, vc, va)
     assert_rgba_close(frame.rgba.cpu().numpy().astype(np.float64), ref, pix)
     assert not np.allclose(frame.rgba.cpu().numpy().reshape(-1, 4)[pix], rgba_rec.cpu().numpy().reshape(-1, 4)[pix])
+
+
+@pytest.mark.parametrize("tile_h", [32, 16])
+def test_tile_list_resolve_bit_identical(tile_h):
+    """hm_resolve_shade with the tile-list scratch (pre-pass listing the tiles
+    that hold keys, persistent grid over them) writes the same image, bit for
+    bit, as one CTA per tile, including the zeros of empty tiles and ragged
+    edges; checked against the oracle too."""
+    import torch
+    from paper_2607_04230_b300 import hm
+    sc = synth.tiny_scene(14, width=203, height=117, num_strands=600, dist_m=0.5)
+    grooms = hm.upload_scene(sc)
+    old = hm.get_tuning()
+    hm.set_tuning(resolve_tile_h=tile_h)
+    try:
+        plain = hm.Frame(sc.camera.width, sc.camera.height)
+        listed = hm.Frame(sc.camera.width, sc.camera.height, tile_list=True)
+        hm.render(grooms, sc, plain)
+        listed.vis_center.copy_(plain.vis_center)
+        listed.vis_cons.copy_(plain.vis_cons)
+        listed.rgba.fill_(float("nan"))          # every pixel must be written
+        for _ in range(2):                        # the scratch is reused
+            hm.resolve_shade(grooms, sc.camera, sc.lights, sc.filt, listed.vis_center, listed.vis_cons,
+                             listed.rgba, tile_scratch=listed.tile_scratch)
+        torch.cuda.synchronize()
+        hm.get_device_status()
+        assert torch.equal(plain.rgba, listed.rgba)
+    finally:
+        hm.set_tuning(**old)
+    lods, vc, va, _ = oracle_keys(sc)
+    covered = np.nonzero((va & oracle.PAYLOAD_MASK) != oracle.PAYLOAD_MASK)[0]
+    ref, pix = oracle_rgba(sc, lods, vc, va, pixels=covered)
+    assert_rgba_close(listed.rgba.cpu().numpy().astype(np.float64), ref, pix)
