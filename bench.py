@@ -405,7 +405,7 @@ def run_crowd(args, rank, world, local_rank):
                               "per_character_launches_ms_per_character": ms_pc / n,
                               "speedup": ms_pc / ms_g, "grooms": n},
             "autotune": tune and {"tuning": tune["tuning"], "best_ms": tune["ms"], "candidates": len(tune["table"])},
-            "gpu_launches": LAUNCHES_PER_FRAME * args.steps, "clocks": clk}
+            "gpu_launches": (LAUNCHES_PER_FRAME + 1) * args.steps, "clocks": clk}   # + the resolve's tile-list pass
     print(json.dumps(line), flush=True)
     return 0
 
