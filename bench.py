@@ -426,7 +426,9 @@ def run_lod_sweep(args, rank, world, local_rank):
         sc = synth.scene_lod_sweep(i, g)
         if handle is None:
             handle = hm.upload_scene(sc)
-        frame = hm.Frame(sc.camera.width, sc.camera.height)
+        # distant heads cover a few tiles of the frame: the resolve lists the
+        # occupied tiles first (same for both LOD settings)
+        frame = hm.Frame(sc.camera.width, sc.camera.height, tile_list=True)
         out = {}
         for lod in (0, 1):
             handle[0].set_lod(lod, sc.lod.lam)
