@@ -463,7 +463,10 @@ def run_lod_sweep(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
             "config": {"workload": "LOD sweep: 1080p groom at 8 distances, LOD on (lambda 3) vs LOD 0",
                        "resolution": "1920x1080", "l2": "flushed between timed steps (256 MiB write)"},
-            "sweep": rows}
+            "sweep": rows,
+            # 8 distances x 2 LOD settings, each timed over max(10, steps / 8) frames of
+            # LAUNCHES_PER_FRAME kernels plus the resolve's tile-list pass
+            "gpu_launches": (LAUNCHES_PER_FRAME + 1) * 16 * max(10, args.steps // 8)}
     print(json.dumps(line), flush=True)
     return 0
 
