@@ -516,23 +516,10 @@ __device__ __forceinline__ void raster_item_msaa(const SegRec &q_shared, int i, 
     const SegRec q = q_shared;
     const bool xm = q.flags & 1;
     const int32_t cu = 256 * i + 128;
-    // largest sample offset from the pixel centre (1/256 px) and the box
-    // half-width: a covered sample's box holds a segment point within
-    // kOff + hc of the centre along either axis
-    constexpr int32_t kOff = N == 1 ? 0 : (N == 2 ? 64 : (N == 4 ? 96 : 112));
-    const int32_t reach = kOff + q.hc;
-    const int32_t ua = max(cu - reach, q.umin), ub = min(cu + reach, q.umax);
-    if (ua > ub) return;
-    const float va = (float)(ua - q.uA) * q.slope, vb = (float)(ub - q.uA) * q.slope;
-    const float flo = floorf(fminf(va, vb)), fhi = ceilf(fmaxf(va, vb));
-    // 32-bit bounds as in raster_column (guard band, |slope| <= 1)
-    const int32_t slack = 8 + (abs(q.dv) >> 20);
-    const int32_t vlo = q.vA + (int32_t)flo - slack;
-    const int32_t vhi = q.vA + (int32_t)fhi + slack;
     const int dimv = xm ? H : W;
-    // rows m whose sample boxes can reach [vlo, vhi]: vlo - reach <= 256 m + 128 <= vhi + reach
-    const int mlo = max((vlo - reach - 128 + 255) >> 8, 0);
-    const int mhi = min((vhi + reach - 128) >> 8, dimv - 1);
+    // float error of a minor-axis value on the line is below |dV| 2^-21 + 1
+    // unit; with |vA| <= 2^28 (guard band) and |slope| <= 1 every term fits 32 bits
+    const int32_t slack = 8 + (abs(q.dv) >> 20);
     // I: 32-bit for short segments (|dU|, |dV| < 2^14), whose cross products
     // and numerators at the candidate samples stay below 2^30
     const I du = q.du, dv = q.dv;
@@ -540,48 +527,42 @@ __device__ __forceinline__ void raster_item_msaa(const SegRec &q_shared, int i, 
     const uint64_t id = ((uint64_t)q.id_hi << 32) | q.id_lo;
     const bool degenerate = (q.du == 0 && q.dv == 0);
     typedef typename std::make_unsigned<I>::type U;
-    // per sample k: offsets of the line cross product and of the depth
-    // numerator from the pixel centre's, and the major-axis part of the box
-    // overlap (the same for every row of this column)
-    I dk[N], dnk[N];
-    int32_t ovk[N];
-    bool uin[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) {
         int ox, oy;
         sample_offset<N>(k, ox, oy);
         const int32_t ou = xm ? ox : oy, ov = xm ? oy : ox;
-        dk[k] = du * (I)ov - dv * (I)ou;
-        dnk[k] = (I)ou * du + (I)ov * dv;
-        ovk[k] = ov;
         const int32_t su = cu + ou;
-        uin[k] = q.umin <= su + q.hc && q.umax >= su - q.hc;
-    }
-    // cross product and depth numerator at the pixel centre, advanced by
-    // constants from row to row
-    I e0 = du * (I)(256 * mlo + 128 - q.vA) - dv * (I)(cu - q.uA);
-    I num0 = (I)(cu - q.uA) * du + (I)(256 * mlo + 128 - q.vA) * dv;
-    const I de = du * 256, dn = dv * 256;
-    for (int m = mlo; m <= mhi; ++m, e0 += de, num0 += dn) {
-        const int32_t cv = 256 * m + 128;
-        const int px = xm ? i : m, py = xm ? m : i;
-        const int64_t p = (int64_t)((uint32_t)py * (uint32_t)W + (uint32_t)px);
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const int32_t sv = cv + ovk[k];
+        // a covered sample's box [su +- hc] x [sv +- hc] holds a segment point
+        // (u*, v*): u* in [su - hc, su + hc] clipped to the segment, v* on the
+        // line there (within the float range [vlo, vhi]), |v* - sv| <= hc; so
+        // the sample's row m has vlo - hc <= 256 m + 128 + ov <= vhi + hc
+        const int32_t ua = max(su - q.hc, q.umin), ub = min(su + q.hc, q.umax);
+        if (ua > ub) continue;
+        const float va = (float)(ua - q.uA) * q.slope, vb = (float)(ub - q.uA) * q.slope;
+        const int32_t vlo = q.vA + (int32_t)floorf(fminf(va, vb)) - slack;
+        const int32_t vhi = q.vA + (int32_t)ceilf(fmaxf(va, vb)) + slack;
+        const int mlo = max((vlo - q.hc - 128 - ov + 255) >> 8, 0);
+        const int mhi = min((vhi + q.hc - 128 - ov) >> 8, dimv - 1);
+        const I ru = (I)(su - q.uA);
+        for (int m = mlo; m <= mhi; ++m) {
+            const int32_t sv = 256 * m + 128 + ov;
             // closed box of half-width hc around the sample: boxes overlap and
             // |cross product| <= hc (|dU| + |dV|) (one unsigned compare)
-            if (!uin[k] || q.vmin > sv + q.hc || q.vmax < sv - q.hc) continue;
-            if ((U)(e0 + dk[k] + k_cen) > (U)(2 * k_cen)) continue;
+            if (q.vmin > sv + q.hc || q.vmax < sv - q.hc) continue;
+            const I rv = (I)(sv - q.vA);
+            if ((U)(du * rv - dv * ru + k_cen) > (U)(2 * k_cen)) continue;
             float t = 0.0f;
             if (!degenerate) {
-                const I nk = num0 + dnk[k];
+                const I nk = ru * du + rv * dv;
                 const float fn = sizeof(I) == 4 ? __int2float_rn((int32_t)nk) : __ll2float_rn((int64_t)nk);
                 t = fclamp(fdiv(fn, q.fden), 0.0f, 1.0f);
             }
             const float z = fclamp(fadd(q.zA, fmul(q.dz, t)), 0.0f, 1.0f);
             uint32_t d24 = (uint32_t)floorf(fmul(z, 16777216.0f));
             d24 = d24 > 16777215u ? 16777215u : d24;
+            const int px = xm ? i : m, py = xm ? m : i;
+            const int64_t p = (int64_t)((uint32_t)py * (uint32_t)W + (uint32_t)px);
             atomicMin(reinterpret_cast<unsigned long long *>(vis_s + (int64_t)k * npx + p),
                       (unsigned long long)(((uint64_t)d24 << 40) | id));
             n_hits += 1;
