@@ -210,6 +210,20 @@ def probe_atomic_peak(torch, hm, n_elems, rounds=32):
     return best
 
 
+def ncu_warp_inst(kernel: str, workload: str):
+    """Warp instructions one launch of `kernel` issues (ncu, same kernel
+    sources and workload), else None."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = t.get(workload, {}).get(kernel)
+    if not e or kernel not in KERNEL_SOURCES or e.get("src_hash") != kernel_src_hash(kernel):
+        return None
+    return e.get("warp_inst_per_launch")
+
+
 def ncu_red_sectors_per_atomic(workload: str):
     """L2 RED sectors per 64-bit atomicMin of the raster kernel from the
     committed ncu summary (same kernel sources), else None."""
@@ -877,6 +891,19 @@ def run_native(args, rank, world, local_rank):
         "resolve_kernel": {"bound": "hbm", "achieved": res_bytes / t_s / 1e9, "peak": hbm, "unit": "GB/s",
                            "ms": phase_ms["resolve"], "work": f"{res_bytes} B per launch (32 B/px)"},
     }
+    # instruction-issue view (both kernels issue-heavy): warp instructions
+    # per launch (ncu) / event time, against one warp instruction per cycle
+    # per SM sub-partition (4 per SM) at the sampled SM clock
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz")
+    for kname, tk in (("raster_kernel", t_r), ("resolve_kernel", t_s)):
+        wi = ncu_warp_inst(kname, args.workload)
+        if wi is not None and mhz:
+            peak_issue = sms * 4 * float(mhz) * 1e6
+            kernels[kname]["issue"] = {"achieved": wi / tk / 1e9, "peak": peak_issue / 1e9,
+                                       "unit": "G warp instructions/s", "frac": wi / tk / peak_issue,
+                                       "warp_inst_per_launch": wi,
+                                       "peak_source": f"{sms} SMs x 4 issue slots x {float(mhz):.0f} MHz (sampled)"}
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     d = kernels[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
