@@ -207,9 +207,11 @@ static int segment_covers(int64_t XA, int64_t YA, int64_t XB, int64_t YB,
     int64_t e2 = dX * ((cy + h) - YA) - dY * ((cx - h) - XA);
     int64_t e3 = dX * ((cy + h) - YA) - dY * ((cx + h) - XA);
     int64_t emin = e0, emax = e0;
-    if (e1 < emin) emin = e1; if (e1 > emax) emax = e1;
-    if (e2 < emin) emin = e2; if (e2 > emax) emax = e2;
-    if (e3 < emin) emin = e3; if (e3 > emax) emax = e3;
+    const int64_t e[3] = {e1, e2, e3};
+    for (int i = 0; i < 3; ++i) {
+        if (e[i] < emin) emin = e[i];
+        if (e[i] > emax) emax = e[i];
+    }
     return emin <= 0 && 0 <= emax;
 }
 
