@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", choices=["single_1080p", "crowd_4k", "tiny_256", "lod_sweep", "grad_512",
                                            "stereo_1080p", "single_1080p_ao", "msaa_1080p", "shadow_1080p",
-                                           "compressed_1080p"],
+                                           "compressed_1080p", "atomic_probe"],
                     default="single_1080p")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -703,6 +703,41 @@ def run_shadow(args, rank, world, local_rank):
     return 0
 
 
+def run_atomic_probe(args, rank, world, local_rank):
+    """The L2 atomic denominators on their own: 64-bit atomicMin throughput
+    of the probe over a 1080p frame's two key layers (4,147,200 elements,
+    32 rounds), for consecutive, hashed and 32-way-contended addresses; best
+    of five launches each."""
+    import torch
+    from paper_2607_04230_b300 import build, hm
+    build.build()
+    torch.cuda.set_device(local_rank)
+    n = 2 * 1920 * 1080
+    buf = torch.empty(n, dtype=torch.int64, device="cuda")
+    names = {0: "coalesced (4 atomics per 32 B sector)", 1: "hashed (1 per sector)",
+             2: "32-way contended (one element per warp)"}
+    out = {}
+    for pattern in (0, 1, 2):
+        hm.probe_atomic_min(buf, rounds=2, pattern=pattern)        # warm-up
+        rates = []
+        for _ in range(5):
+            buf.fill_(-1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            hm.probe_atomic_min(buf, rounds=32, pattern=pattern)
+            b.record()
+            b.synchronize()
+            rates.append(n * 32 / (a.elapsed_time(b) * 1e-3))
+        sectors = PROBE_SECTORS_PER_ATOMIC.get(pattern)     # contended: not a sector-rate measure
+        out[names[pattern]] = {"atomics_per_s": max(rates),
+                               "l2_red_sectors_per_s": max(rates) * sectors if sectors else None}
+    if rank == 0:
+        print(json.dumps({"metric": "64-bit atomicMin throughput (probe)", "unit": "atomics/s",
+                          "value": out[names[1]]["atomics_per_s"], "higher_is_better": True, "n_gpus": world,
+                          "patterns": out, "elements": n, "rounds": 32, "gpu_launches": 18}), flush=True)
+    return 0
+
+
 def run_compressed(args, rank, world, local_rank):
     """The 1080p groom with the compressed G-buffer payload (Sec. 3.1.2:
     shading data in the key, resolve reads no hair mesh) against the
@@ -947,7 +982,8 @@ def main():
         dist.init_process_group("nccl")
     runner = {"crowd_4k": run_crowd, "lod_sweep": run_lod_sweep, "grad_512": run_grad,
               "stereo_1080p": run_stereo, "msaa_1080p": run_msaa,
-              "shadow_1080p": run_shadow, "compressed_1080p": run_compressed}.get(args.workload, run_native)
+              "shadow_1080p": run_shadow, "compressed_1080p": run_compressed,
+              "atomic_probe": run_atomic_probe}.get(args.workload, run_native)
     try:
         return runner(args, rank, world, local_rank)
     finally:

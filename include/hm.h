@@ -437,9 +437,10 @@ hm_status hm_set_phase_events(void *const *events, int32_t count);
 
 /* Measurement probe for the roofline denominator, not part of rendering:
  * one launch of 64-bit atomicMin over d_buf[0..n) with `rounds` operations
- * per element, addresses coalesced and distinct within a warp (pattern 0)
- * or scattered by a multiplicative hash (pattern 1).  Contents of d_buf are
- * overwritten.  16-byte aligned, n >= 1. */
+ * per element, addresses coalesced and distinct within a warp (pattern 0),
+ * scattered by a multiplicative hash (pattern 1), or one hashed element per
+ * warp, all 32 lanes on it (pattern 2, 32-way contention).  Contents of d_buf
+ * are overwritten.  16-byte aligned, n >= 1. */
 hm_status hm_probe_atomic_min(uint64_t *d_buf, int64_t n, int32_t rounds, int32_t pattern, void *stream);
 
 const char *hm_status_string(hm_status s);

@@ -727,7 +727,7 @@ hm_status hm_set_phase_events(void *const *events, int32_t count) {
 }
 
 hm_status hm_probe_atomic_min(uint64_t *d_buf, int64_t n, int32_t rounds, int32_t pattern, void *stream) {
-    if (!d_buf || n < 1 || rounds < 1 || (pattern != 0 && pattern != 1))
+    if (!d_buf || n < 1 || rounds < 1 || pattern < 0 || pattern > 2)
         return fail(HM_ERR_INVALID_ARG, "bad probe arguments");
     HM_CUDA(hm::launch_probe_atomic_min(d_buf, n, rounds, pattern, static_cast<cudaStream_t>(stream)), "probe");
     return HM_OK;

@@ -715,7 +715,10 @@ __global__ void __launch_bounds__(256) probe_atomic_min_kernel(unsigned long lon
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int r = 0; r < rounds; ++r) {
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-            int64_t a = pattern ? (int64_t)(((uint64_t)i * 0x9E3779B97F4A7C15ull) % (uint64_t)n) : i;
+            // 0: consecutive lanes on consecutive elements; 1: multiplicatively
+            // hashed element per lane; 2: one hashed element per warp (32-way contended)
+            const uint64_t h = pattern == 2 ? (uint64_t)(i >> 5) : (uint64_t)i;
+            int64_t a = pattern ? (int64_t)((h * 0x9E3779B97F4A7C15ull) % (uint64_t)n) : i;
             atomicMin(buf + a, (unsigned long long)((int64_t)rounds - r) << 40 | (unsigned long long)i);
         }
     }
