@@ -440,9 +440,7 @@ def run_lod_sweep(args, rank, world, local_rank):
         sc = synth.scene_lod_sweep(i, g)
         if handle is None:
             handle = hm.upload_scene(sc)
-        # distant heads cover a few tiles of the frame: the resolve lists the
-        # occupied tiles first (same for both LOD settings)
-        frame = hm.Frame(sc.camera.width, sc.camera.height, tile_list=True)
+        frame = hm.Frame(sc.camera.width, sc.camera.height)
         out = {}
         for lod in (0, 1):
             handle[0].set_lod(lod, sc.lod.lam)
@@ -478,9 +476,8 @@ def run_lod_sweep(args, rank, world, local_rank):
             "config": {"workload": "LOD sweep: 1080p groom at 8 distances, LOD on (lambda 3) vs LOD 0",
                        "resolution": "1920x1080", "l2": "flushed between timed steps (256 MiB write)"},
             "sweep": rows,
-            # 8 distances x 2 LOD settings, each timed over max(10, steps / 8) frames of
-            # LAUNCHES_PER_FRAME kernels plus the resolve's tile-list pass
-            "gpu_launches": (LAUNCHES_PER_FRAME + 1) * 16 * max(10, args.steps // 8)}
+            # 8 distances x 2 LOD settings, each timed over max(10, steps / 8) frames
+            "gpu_launches": LAUNCHES_PER_FRAME * 16 * max(10, args.steps // 8)}
     print(json.dumps(line), flush=True)
     return 0
 
