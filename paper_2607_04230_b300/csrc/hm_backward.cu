@@ -408,7 +408,11 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
     uint8_t *s_isoG = reinterpret_cast<uint8_t *>(s_tsA + kResolveThreads);
     uint8_t *s_isoA = s_isoG + kResolveThreads;
     uint8_t *s_fa = s_isoA + kResolveThreads;
-    __shared__ int s_count;
+    __shared__ int s_count, s_nJA, s_nJG;
+    __shared__ float4 s_dTs[kResolveThreads];    // per tile pixel: d(screen tangent) of G (xy) and A (zw)
+    __shared__ float s_gs[kResolveThreads];      // share of the pixel's gradient the centre reconstruction gets
+    __shared__ int s_dAv[kResolveThreads];       // conservative-layer depth of the pixel
+    __shared__ uint16_t s_jA[kResolveThreads], s_jG[kResolveThreads];
 
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
@@ -418,7 +422,11 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
         for (int i = 0; i < tid; ++i) b += (uint64_t)tab.g[i].S;
         s_bases[tid] = b;
     }
-    if (tid == 0) s_count = 0;
+    if (tid == 0) {
+        s_count = 0;
+        s_nJA = 0;
+        s_nJG = 0;
+    }
     __syncthreads();
     for (int i = tid; i < ns; i += kResolveThreads) {
         const int gx = x0 - R + i % sw, gy = y0 - R + i / sw;
@@ -492,63 +500,97 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
     }
     __syncthreads();
 
-    float2 dTsG = make_float2(0.f, 0.f), dTsA = make_float2(0.f, 0.f);
+    // Per-pixel flags, then two compacted job lists so that whole warps run
+    // one kind of reconstruction adjoint: first the conservative-referenced
+    // ones (promoted pixels and depth mismatches), which also fix the share
+    // (1 - al) of a mismatch's gradient the centre reconstruction receives;
+    // then the centre-referenced ones that receive any.
+    const int lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    float3 g = f3(0.f, 0.f, 0.f);
+    bool nz = false;
     if (inside) {
         const float4 g4 = __ldg(&grad_rgba[(int64_t)gy * W + gx]);
-        const float3 g = f3(g4.x, g4.y, g4.z);
-        const bool nz = g.x != 0.f || g.y != 0.f || g.z != 0.f;
-        const int dG = dg_at(mid);
-        const bool gP = dG >= 0, aP = s_fa[mid];
-        if (nz && !fp.enabled) {
-            if (gP) {
-                atomicAdd(&s_dC[mid].x, g.x);
-                atomicAdd(&s_dC[mid].y, g.y);
-                atomicAdd(&s_dC[mid].z, g.z);
-            }
-        } else if (nz && gP) {
-            const float3 Cp = make_float3(s_col[mid].x, s_col[mid].y, s_col[mid].z);
-            float3 gG = g, gA = f3(0.f, 0.f, 0.f);
-            Recon ra;
-            ra.cnt = 0;
-            const bool mism = aP && dA + fp.dmis <= dG;
-            if (mism) {
-                const float2 tsa = s_tsA[tid];
-                ra = reconstruct_fast_r<false>(R, s_fa, s_col, sw, tx, ty, dA, tsa.x, tsa.y, s_isoA[tid] != 0,
-                                               f3(0.f, 0.f, 0.f), fp);
-                if (ra.cnt > 0 && ra.W < 1e-20f)
-                    ra = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y,
-                                     s_isoA[tid] != 0, false, Cp, fp);
-                if (ra.cnt > 0) {
-                    const float al = (float)ra.hc / (float)ra.ha;
-                    gA = mul3(g, al);
-                    gG = mul3(g, 1.f - al);
-                }
-            }
-            // blend weight exactly 1: the centre reconstruction gets a zero
-            // gradient and contributes nothing
-            if (!(mism && ra.cnt > 0 && ra.hc == ra.ha)) {
-                const float2 ts = s_tsG[tid];
-                const bool isoG = s_isoG[tid] != 0;
-                const Recon rg = reconstruct_fast_r<true>(R, s_fa, s_col, sw, tx, ty, dG, ts.x, ts.y, isoG, Cp, fp);
-                dTsG = reconstruct_adjoint(s_dg, s_col, s_dC, sw, tx, ty, gx, gy, W, H, R, dG, ts.x, ts.y, isoG,
-                                           true, Cp, mid, rg, gG, fp);
-            }
-            if (mism && ra.cnt > 0) {
-                const float2 tsa = s_tsA[tid];
-                dTsA = reconstruct_adjoint(s_dg, s_col, s_dC, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y,
-                                           s_isoA[tid] != 0, false, Cp, mid, ra, gA, fp);
-            }
-        } else if (nz && aP) {
-            const float2 tsa = s_tsA[tid];
-            const bool isoA = s_isoA[tid] != 0;
-            const float3 z = f3(0.f, 0.f, 0.f);
-            Recon ra = reconstruct_fast_r<false>(R, s_fa, s_col, sw, tx, ty, dA, tsa.x, tsa.y, isoA, z, fp);
-            if (ra.cnt > 0 && ra.W < 1e-20f)
-                ra = reconstruct(s_dg, s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y, isoA, false, z,
-                                 fp);
-            dTsA = reconstruct_adjoint(s_dg, s_col, s_dC, sw, tx, ty, gx, gy, W, H, R, dA, tsa.x, tsa.y, isoA, false,
-                                       z, mid, ra, g, fp);
+        g = f3(g4.x, g4.y, g4.z);
+        nz = g.x != 0.f || g.y != 0.f || g.z != 0.f;
+    }
+    const int dG = dg_at(mid);
+    const bool gP = inside && dG >= 0, aP = inside && s_fa[mid];
+    s_dTs[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    s_gs[tid] = 1.0f;
+    s_dAv[tid] = dA;
+    bool jobA = false;
+    if (nz && !fp.enabled) {
+        if (gP) {
+            atomicAdd(&s_dC[mid].x, g.x);
+            atomicAdd(&s_dC[mid].y, g.y);
+            atomicAdd(&s_dC[mid].z, g.z);
         }
+    } else if (nz) {
+        jobA = gP ? (aP && dA + fp.dmis <= dG) : aP;
+    }
+    {
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, jobA);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&s_nJA, __popc(bal));
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (jobA) s_jA[base + __popc(bal & lt)] = (uint16_t)tid;
+    }
+    __syncthreads();
+    const int nJA = s_nJA;
+    for (int li = tid; li < nJA; li += kResolveThreads) {
+        const int t = s_jA[li];
+        const int jx = t % kTileW, jy = t / kTileW, qx = x0 + jx, qy = y0 + jy;
+        const int jm = (jy + R) * sw + jx + R;
+        const float4 g4 = __ldg(&grad_rgba[(int64_t)qy * W + qx]);
+        float3 gA = f3(g4.x, g4.y, g4.z);
+        const int dAq = s_dAv[t];
+        const float2 tsa = s_tsA[t];
+        const bool isoA = s_isoA[t] != 0;
+        const float3 z = f3(0.f, 0.f, 0.f);
+        Recon ra = reconstruct_fast_r<false>(R, s_fa, s_col, sw, jx, jy, dAq, tsa.x, tsa.y, isoA, z, fp);
+        if (ra.cnt > 0 && ra.W < 1e-20f)
+            ra = reconstruct(s_dg, s_fa, s_col, sw, jx, jy, qx, qy, W, H, R, dAq, tsa.x, tsa.y, isoA, false, z, fp);
+        if (dg_at(jm) >= 0 && ra.cnt > 0) {            // depth mismatch: split al / (1 - al)
+            const float al = (float)ra.hc / (float)ra.ha;
+            gA = mul3(gA, al);
+            s_gs[t] = 1.f - al;                          // exactly 0 when al = 1: no centre adjoint
+        }
+        if (ra.cnt > 0) {
+            const float2 d = reconstruct_adjoint(s_dg, s_col, s_dC, sw, jx, jy, qx, qy, W, H, R, dAq, tsa.x, tsa.y,
+                                                 isoA, false, z, jm, ra, gA, fp);
+            s_dTs[t].z = d.x;
+            s_dTs[t].w = d.y;
+        }
+    }
+    __syncthreads();
+    {
+        const bool jobG = nz && fp.enabled && gP && s_gs[tid] != 0.0f;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, jobG);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&s_nJG, __popc(bal));
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (jobG) s_jG[base + __popc(bal & lt)] = (uint16_t)tid;
+    }
+    __syncthreads();
+    const int nJG = s_nJG;
+    for (int li = tid; li < nJG; li += kResolveThreads) {
+        const int t = s_jG[li];
+        const int jx = t % kTileW, jy = t / kTileW, qx = x0 + jx, qy = y0 + jy;
+        const int jm = (jy + R) * sw + jx + R;
+        const float4 g4 = __ldg(&grad_rgba[(int64_t)qy * W + qx]);
+        const float gs = s_gs[t];
+        const float3 gG = gs == 1.0f ? f3(g4.x, g4.y, g4.z) : mul3(f3(g4.x, g4.y, g4.z), gs);
+        const float4 c4 = s_col[jm];
+        const float3 Cp = make_float3(c4.x, c4.y, c4.z);
+        const int dGq = __float_as_int(c4.w);
+        const float2 ts = s_tsG[t];
+        const bool isoG = s_isoG[t] != 0;
+        const Recon rg = reconstruct_fast_r<true>(R, s_fa, s_col, sw, jx, jy, dGq, ts.x, ts.y, isoG, Cp, fp);
+        const float2 d = reconstruct_adjoint(s_dg, s_col, s_dC, sw, jx, jy, qx, qy, W, H, R, dGq, ts.x, ts.y, isoG,
+                                             true, Cp, jm, rg, gG, fp);
+        s_dTs[t].x = d.x;
+        s_dTs[t].y = d.y;
     }
     __syncthreads();
     // colour gradients of the staged pixels to the global buffer
@@ -563,7 +605,7 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
         atomicAdd(&p->z, v.z);
     }
     // screen-tangent gradients of the reference segments, for the geometry pass
-    if (inside) dTs[(int64_t)gy * W + gx] = make_float4(dTsG.x, dTsG.y, dTsA.x, dTsA.y);
+    if (inside) dTs[(int64_t)gy * W + gx] = s_dTs[tid];
 }
 
 // Geometry pass, one thread per key with a gradient (persistent grid over
