@@ -215,7 +215,9 @@ hm_status hm_update_albedo(hm_groom g, const float *d_albedo, void *stream);
  * decoding in the resolves and the adjoint reads them instead of
  * regenerating the strand (bit-identical values) until the groom's layer
  * vertices are replaced or its LOD state is rebuilt by another camera render
- * (hm_render_shadow_map neither writes nor disturbs them).
+ * (hm_render_shadow_map neither writes nor disturbs them).  Both belong to the
+ * groom, not to the frame: resolve (or differentiate) a frame before the same
+ * grooms are rendered for another camera.
  *
  * d_vis_center, d_vis_cons: [height][width] uint64, 8-byte aligned.
  * d_scene_d24: [height][width] uint32 (24-bit depth) or NULL.
