@@ -301,12 +301,23 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     scene, cfg = make_scene(args.workload)
-    # each step: every k-th strand, k set by a pilot so that warm-up + steps
-    # take about two minutes (at most 10 s a step)
+    # each step: every k-th strand, k as small (the sample as large) as fits
+    # about two minutes for warm-up + steps (at most 10 s a step).  The
+    # oracle's time is t0 + c / k (t0: per-frame work that does not shrink
+    # with the strands), fitted from two pilot samples after a warm-up.
     base = {"single_1080p": 400, "crowd_4k": 800, "tiny_256": 10}[args.workload]
-    _, tp = oracle_frame_sample(scene, base)
     budget = min(10.0, max(0.2, 120.0 / max(1, args.steps + args.warmup)))
-    every = int(min(max(round(base * tp / budget), 1), 100 * base))
+    oracle_frame_sample(scene, 4 * base)                 # warm-up (library load, thread pools)
+    _, t_a = oracle_frame_sample(scene, base)
+    _, t_b = oracle_frame_sample(scene, base // 4 if base >= 4 else 1)
+    kb = max(1, base // 4)
+    c = (t_b - t_a) / (1.0 / kb - 1.0 / base) if kb < base else 0.0
+    t0 = t_a - c / base
+    if c > 0 and budget > t0 * 1.05:
+        every = int(np.ceil(c / (budget - t0)))
+    else:
+        every = int(round(base * t_a / budget))
+    every = int(min(max(every, 1), 100 * base))
     for i in range(args.warmup):
         oracle_frame_sample(scene, every, offset=i)
     tot_s, tot_t = 0, 0.0
