@@ -184,3 +184,40 @@ def test_gradient_vs_central_differences():
         e = e.reshape(alb0.shape)
         fd = (f(lv0, alb0 + e) - f(lv0, alb0 - e)) / (2 * h)
         assert abs(fd - galb.ravel()[idx]) <= 1e-2 * abs(fd), (idx, fd, galb.ravel()[idx])
+
+
+def test_two_forwards_then_backward():
+    """Two differentiable renders of the same groom (different layer
+    vertices) before one backward: each backward sees its own forward's
+    state, so the gradients equal those of two separate forward/backward
+    passes."""
+    from paper_2607_04230_b300 import autograd, hm
+    sc = synth.tiny_scene(27, width=96, height=80, num_strands=400, dist_m=0.3)
+    g = sc.grooms[0]
+    W, H = sc.camera.width, sc.camera.height
+    handle = hm.upload_scene(sc)[0]
+    lv_a = torch.from_numpy(g.layer_verts).cuda()
+    lv_b = torch.from_numpy(synth.perturbed_layer_verts(g, sigma_m=0.001, seed=8)).cuda()
+    alb = torch.from_numpy(g.strand_albedo).cuda()
+    t = torch.rand((W * H, 3), device="cuda", generator=torch.Generator(device="cuda").manual_seed(1)) * 0.2
+
+    def loss_of(rgba):
+        r = rgba.reshape(-1, 4)
+        return torch.sqrt(((r[:, :3] * r[:, 3:4] - t) ** 2).sum())
+
+    def grads(lv):
+        x = lv.clone().requires_grad_(True)
+        a = alb.clone().requires_grad_(True)
+        loss_of(autograd.render(handle, sc, hm.Frame(W, H), x, a)).backward()
+        return x.grad.clone(), a.grad.clone()
+
+    ga, gb = grads(lv_a), grads(lv_b)
+    xa, xb = lv_a.clone().requires_grad_(True), lv_b.clone().requires_grad_(True)
+    aa, ab = alb.clone().requires_grad_(True), alb.clone().requires_grad_(True)
+    la = loss_of(autograd.render(handle, sc, hm.Frame(W, H), xa, aa))
+    lb = loss_of(autograd.render(handle, sc, hm.Frame(W, H), xb, ab))
+    (la + lb).backward()
+    torch.cuda.synchronize()
+    for got, ref in ((xa.grad, ga[0]), (aa.grad, ga[1]), (xb.grad, gb[0]), (ab.grad, gb[1])):
+        assert torch.allclose(got, ref, rtol=1e-4, atol=1e-7 * float(ref.abs().max())), \
+            float((got - ref).abs().max())
