@@ -81,12 +81,23 @@ __device__ __forceinline__ bool lod_select(const GroomDev &g, const CamDev &cam,
     float xmin = __int_as_float(0x7f800000), xmax = -__int_as_float(0x7f800000);
     float ymin = xmin, ymax = xmax;
     bool behind = false, front = false;
+    // the next layer's three vertices are loaded while this layer's are
+    // projected (the AABB is a min/max, independent of the order)
+    float4 nv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) nv[c] = __ldg(&g.lv[c == 0 ? tri.x : (c == 1 ? tri.y : tri.z)]);
     for (int k = 0; k < g.L; ++k) {
-        const float4 *row = g.lv + (int64_t)k * g.V;
+        float4 cv[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cv[c] = nv[c];
+        if (k + 1 < g.L) {
+            const float4 *next = g.lv + (int64_t)(k + 1) * g.V;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) nv[c] = __ldg(&next[c == 0 ? tri.x : (c == 1 ? tri.y : tri.z)]);
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            int vi = c == 0 ? tri.x : (c == 1 ? tri.y : tri.z);
-            float4 v = __ldg(&row[vi]);
+            const float4 v = cv[c];
             Proj p = project(cam, make_float3(v.x, v.y, v.z));
             if (!p.valid) { behind = true; continue; }
             front = true;
