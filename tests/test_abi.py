@@ -205,3 +205,26 @@ def test_shadow_and_compressed_entries_reject_bad_arguments(L):
     Ls = lights_with(1)
     assert L.hm_resolve_compressed(ctypes.byref(cam), ctypes.byref(Ls), ctypes.byref(f), ctypes.byref(app),
                                    fake, fake, fake, None, None) == INVALID
+
+
+def test_resolve_scratch_and_probe_arguments(L):
+    """The tile-list scratch size covers the smallest resolve tiles (32 x 16),
+    0 outside the resolution range; a misaligned scratch and an unknown probe
+    pattern are rejected before anything is launched."""
+    L.hm_resolve_scratch_bytes.restype = ctypes.c_size_t
+    L.hm_resolve_scratch_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    assert L.hm_resolve_scratch_bytes(1920, 1080) == 4 * (60 * 68 + 2)
+    assert L.hm_resolve_scratch_bytes(33, 17) == 4 * (2 * 2 + 2)
+    assert L.hm_resolve_scratch_bytes(0, 10) == 0 and L.hm_resolve_scratch_bytes(10, 16385) == 0
+    sc = synth.tiny_scene(0, num_strands=10)
+    cam = hm.camera_struct(sc.camera)
+    fake = ctypes.c_void_p(1 << 20)
+    grooms = (ctypes.c_void_p * 1)(1 << 20)
+    lights = hm.lights_struct(sc.lights)
+    f = hm.filter_struct(synth.FilterParams())
+    assert L.hm_resolve_shade(grooms, 1, ctypes.byref(cam), ctypes.byref(lights), ctypes.byref(f), fake, fake, fake,
+                              ctypes.c_void_p((1 << 20) + 2), None) == INVALID
+    for pattern in (-1, 3):
+        assert L.hm_probe_atomic_min(fake, 16, 1, pattern, None) == INVALID
+    assert L.hm_probe_atomic_min(fake, 0, 1, 0, None) == INVALID
+    assert L.hm_probe_atomic_min(fake, 16, 0, 0, None) == INVALID
