@@ -332,10 +332,12 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
 // Multisample resolve: every covered sample is decoded at its own sample
 // point and shaded; straight-alpha output with rgb the mean over covered
 // samples and alpha the covered fraction (premultiplied: the mean over all).
+// The kernel waits mostly on the key, record and albedo loads, so it runs four
+// CTAs per SM (64 registers) with every sample layer's key requested first.
 template <int N>
-__global__ void __launch_bounds__(256) resolve_msaa_kernel(CallTable tab, CamDev cam, LightsDev Ls,
-                                                           const uint64_t *__restrict__ vis_s,
-                                                           float4 *__restrict__ rgba, uint32_t *status) {
+__global__ void __launch_bounds__(256, 4) resolve_msaa_kernel(CallTable tab, CamDev cam, LightsDev Ls,
+                                                              const uint64_t *__restrict__ vis_s,
+                                                              float4 *__restrict__ rgba, uint32_t *status) {
     __shared__ uint64_t s_bases[HM_MAX_GROOMS_PER_CALL + 1];
     if ((int)threadIdx.x <= tab.n) {
         uint64_t b = 0;
@@ -348,9 +350,13 @@ __global__ void __launch_bounds__(256) resolve_msaa_kernel(CallTable tab, CamDev
         const int px = (int)(p % cam.W), py = (int)(p / cam.W);
         float3 acc = make_float3(0.f, 0.f, 0.f);
         int cnt = 0;
+        uint64_t keys[N];   // all sample layers' loads in flight before the first decode
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            keys[k] = __ldg(reinterpret_cast<const unsigned long long *>(vis_s + (int64_t)k * npx + p));
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const uint64_t key = __ldg(reinterpret_cast<const unsigned long long *>(vis_s + (int64_t)k * npx + p));
+            const uint64_t key = keys[k];
             if (key_empty(key)) continue;
             int ox, oy;
             sample_offset<N>(k, ox, oy);
