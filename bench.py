@@ -398,6 +398,8 @@ def run_crowd(args, rank, world, local_rank):
     torch.cuda.synchronize()
     phase_ms = {name: statistics.median(e[a].elapsed_time(e[b]) for e in ev)
                 for name, a, b in (("clear", 0, 1), ("lod", 1, 2), ("raster", 2, 3), ("resolve", 4, 5))}
+    W, H = scene.camera.width, scene.camera.height
+    peak_rates = probe_atomic_peak(torch, hm, 2 * W * H)
     cr.capture()
     for _ in range(args.warmup):
         cr.replay()
@@ -418,6 +420,8 @@ def run_crowd(args, rank, world, local_rank):
     n = len(scene.grooms)
     atomics = st["covered_cons"] + st["covered_center"]
     ms_g = tg / args.steps * 1e3
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    kernels, roofline = frame_roofline(atomics, phase_ms, W, H, peak_rates, args.workload, clk, sms)
     ms_pc = statistics.mean(t_pc)
     line = {"metric": METRIC, "value": job_throughput(segs, args.steps, world, tg), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_g, "higher_is_better": True,
@@ -425,7 +429,7 @@ def run_crowd(args, rank, world, local_rank):
             "config": dict(cfg, parallelism=f"replicas x{world}", batching="one render + one resolve call over "
                            "all grooms, replayed as a CUDA graph"),
             "strands_after_lod": st["strands"], "segments_per_frame": segs, "covered_pairs": atomics,
-            "frame_ms_phases": phase_ms,
+            "frame_ms_phases": phase_ms, "roofline": roofline, "kernels": kernels,
             "per_character": {"batched_graph_ms_per_character": ms_g / n,
                               "per_character_launches_ms_per_character": ms_pc / n,
                               "speedup": ms_pc / ms_g, "grooms": n},
@@ -711,6 +715,62 @@ def run_shadow(args, rank, world, local_rank):
     return 0
 
 
+def frame_roofline(atomics, phase_ms, W, H, peak_rates, workload, clk, sms):
+    """Roofline of one frame's two main kernels: the rasterizer against the
+    L2 RED sector rate of the live atomic probe (`peak_rates`, atomics/s per
+    address pattern), the resolve against the measured HBM bandwidth, each
+    with the instruction-issue view when an ncu summary of the same sources
+    and workload gives its warp instructions.  Returns (kernels, roofline of
+    the longer kernel)."""
+    peaks, peaks_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    # the L2 atomic roofline in the unit the hardware spends: RED sector
+    # operations (a 64-bit atomicMin updates one 32-byte sector; atomics of
+    # one instruction that share a sector share the operation)
+    sector_peak = max(r * PROBE_SECTORS_PER_ATOMIC[p] for p, r in peak_rates.items())
+    spa = ncu_red_sectors_per_atomic(workload)
+    spa_note = "ncu-measured" if spa is not None else "assumed one per atomic (no ncu summary for these sources)"
+    spa = spa if spa is not None else 1.0
+    t_r = phase_ms["raster"] * 1e-3
+    t_s = phase_ms["resolve"] * 1e-3
+    res_bytes = 32 * W * H            # both keys read once + RGBA written once
+    kernels = {
+        "raster_kernel": {"bound": "l2_atomic", "achieved": atomics * spa / t_r / 1e9, "peak": sector_peak / 1e9,
+                          "unit": "G L2 RED sectors/s", "ms": phase_ms["raster"],
+                          "atomics_per_s": atomics / t_r, "red_sectors_per_atomic": spa,
+                          "work": f"{atomics} covered (pixel, layer) pairs per launch = 64-bit atomicMin ops, "
+                                  f"x {spa:.4f} L2 RED sectors each ({spa_note})"},
+        "resolve_kernel": {"bound": "hbm", "achieved": res_bytes / t_s / 1e9, "peak": hbm, "unit": "GB/s",
+                           "ms": phase_ms["resolve"], "work": f"{res_bytes} B per launch (32 B/px)"},
+    }
+    # instruction-issue view (both kernels issue-heavy): warp instructions
+    # per launch (ncu) / event time, against one warp instruction per cycle
+    # per SM sub-partition (4 per SM) at the sampled SM clock
+    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz")
+    for kname, tk in (("raster_kernel", t_r), ("resolve_kernel", t_s)):
+        wi = ncu_warp_inst(kname, workload)
+        if wi is not None and mhz:
+            peak_issue = sms * 4 * float(mhz) * 1e6
+            kernels[kname]["issue"] = {"achieved": wi / tk / 1e9, "peak": peak_issue / 1e9,
+                                       "unit": "G warp instructions/s", "frac": wi / tk / peak_issue,
+                                       "warp_inst_per_launch": wi,
+                                       "peak_source": f"{sms} SMs x 4 issue slots x {float(mhz):.0f} MHz (sampled)"}
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    d = kernels[dom]
+    roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+                "frac": d["achieved"] / d["peak"], "traffic": ncu_traffic(dom, workload), "kernel": dom,
+                "peak_source": ("live probe hm_probe_atomic_min over a "
+                                f"{2 * W * H}-element buffer: coalesced {peak_rates[0] / 1e9:.1f} Gatom/s "
+                                f"(4 per sector = {peak_rates[0] * 0.25 / 1e9:.1f} G sectors/s), hashed "
+                                f"{peak_rates[1] / 1e9:.1f} Gatom/s (1 per sector); ncu shows both patterns "
+                                "at the same L2 RED sector rate (profiles/l2_red_sector_rate.md)")
+                if d["bound"] == "l2_atomic" else f"{peaks_kind} hbm_gbs of MEASURED_PEAKS.json",
+                "work_per_launch": d["work"]}
+    for k in kernels.values():
+        k["frac"] = k["achieved"] / k["peak"]
+    return kernels, roofline
+
+
 def run_atomic_probe(args, rank, world, local_rank):
     """The L2 atomic denominators on their own: 64-bit atomicMin throughput
     of the probe over a 1080p frame's two key layers (4,147,200 elements,
@@ -913,59 +973,14 @@ def run_native(args, rank, world, local_rank):
 
     if rank != 0:
         return 0
-    peaks, peaks_kind = measured_peaks()
-    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
-    # the L2 atomic roofline in the unit the hardware spends: RED sector
-    # operations (a 64-bit atomicMin updates one 32-byte sector; atomics of
-    # one instruction that share a sector share the operation)
-    sector_peak = max(r * PROBE_SECTORS_PER_ATOMIC[p] for p, r in peak_rates.items())
-    spa = ncu_red_sectors_per_atomic(args.workload)
-    spa_note = "ncu-measured" if spa is not None else "assumed one per atomic (no ncu summary for these sources)"
-    spa = spa if spa is not None else 1.0
-    t_r = phase_ms["raster"] * 1e-3
-    t_s = phase_ms["resolve"] * 1e-3
-    res_bytes = 32 * W * H            # both keys read once + RGBA written once
-    kernels = {
-        "raster_kernel": {"bound": "l2_atomic", "achieved": atomics * spa / t_r / 1e9, "peak": sector_peak / 1e9,
-                          "unit": "G L2 RED sectors/s", "ms": phase_ms["raster"],
-                          "atomics_per_s": atomics / t_r, "red_sectors_per_atomic": spa,
-                          "work": f"{atomics} covered (pixel, layer) pairs per launch = 64-bit atomicMin ops, "
-                                  f"x {spa:.4f} L2 RED sectors each ({spa_note})"},
-        "resolve_kernel": {"bound": "hbm", "achieved": res_bytes / t_s / 1e9, "peak": hbm, "unit": "GB/s",
-                           "ms": phase_ms["resolve"], "work": f"{res_bytes} B per launch (32 B/px)"},
-    }
-    # instruction-issue view (both kernels issue-heavy): warp instructions
-    # per launch (ncu) / event time, against one warp instruction per cycle
-    # per SM sub-partition (4 per SM) at the sampled SM clock
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz")
-    for kname, tk in (("raster_kernel", t_r), ("resolve_kernel", t_s)):
-        wi = ncu_warp_inst(kname, args.workload)
-        if wi is not None and mhz:
-            peak_issue = sms * 4 * float(mhz) * 1e6
-            kernels[kname]["issue"] = {"achieved": wi / tk / 1e9, "peak": peak_issue / 1e9,
-                                       "unit": "G warp instructions/s", "frac": wi / tk / peak_issue,
-                                       "warp_inst_per_launch": wi,
-                                       "peak_source": f"{sms} SMs x 4 issue slots x {float(mhz):.0f} MHz (sampled)"}
-    dom = max(kernels, key=lambda k: kernels[k]["ms"])
-    d = kernels[dom]
-    roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-                "frac": d["achieved"] / d["peak"], "traffic": ncu_traffic(dom, args.workload), "kernel": dom,
-                "peak_source": ("live probe hm_probe_atomic_min over a "
-                                f"{2 * W * H}-element buffer: coalesced {peak_rates[0] / 1e9:.1f} Gatom/s "
-                                f"(4 per sector = {peak_rates[0] * 0.25 / 1e9:.1f} G sectors/s), hashed "
-                                f"{peak_rates[1] / 1e9:.1f} Gatom/s (1 per sector); ncu shows both patterns "
-                                "at the same L2 RED sector rate (profiles/l2_red_sector_rate.md)")
-                if d["bound"] == "l2_atomic" else f"{peaks_kind} hbm_gbs of MEASURED_PEAKS.json",
-                "work_per_launch": d["work"]}
-    for k in kernels.values():
-        k["frac"] = k["achieved"] / k["peak"]
+    kernels, roofline = frame_roofline(atomics, phase_ms, W, H, peak_rates, args.workload, clk, sms)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
             "config": dict(cfg, parallelism=f"replicas x{world}"),
             "frame_ms": {k: round(v, 5) for k, v in phase_ms.items()},
-            "segments_per_frame": segs, "raster_segments_per_s": segs / t_r,
+            "segments_per_frame": segs, "raster_segments_per_s": segs / (phase_ms["raster"] * 1e-3),
             "lod_raster_segments_per_s": segs / ((phase_ms["lod"] + phase_ms["raster"]) * 1e-3),
             "roofline": roofline, "kernels": kernels,
             "e2e": e2e, "gpu_launches": LAUNCHES_PER_FRAME * args.steps, "clocks": clk, "wall_s": wall,

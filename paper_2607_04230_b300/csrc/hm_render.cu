@@ -246,6 +246,18 @@ __global__ void __launch_bounds__(kLodScanThreads) lod_scan_kernel(CallTable tab
 
 // Segment `seg` (0 <= seg < drawn segments of the groom) of the batch whose
 // first segment lies in bundle f0: its bundle f, strand s and segment j.
+// Groom of work batch b: the last groom whose first batch is <= b (goff
+// holds the n + 1 prefix batch counts, so grooms without batches are passed
+// over); a binary search, as a crowd call holds up to 64 grooms.
+__device__ __forceinline__ int batch_groom(const uint32_t *goff, int n, uint32_t b) {
+    int lo = 0, hi = n;          // goff[lo] <= b < goff[n]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (goff[mid] <= b) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ void batch_segment(const GroomDev &g, uint32_t f0, uint32_t seg, uint32_t &f, int64_t &s,
                                               int &j, int &C) {
     f = f0;
@@ -393,8 +405,7 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
         if (lane == 0) b = atomicAdd(ticket, 1u);
         b = __shfl_sync(kFull, b, 0);
         if (b >= total) break;
-        int gi = 0;
-        while (gi + 1 < tab.n && s_goff[gi + 1] <= b) ++gi;
+        const int gi = batch_groom(s_goff, tab.n, b);
         const GroomDev &g = tab.g[gi];
         const uint32_t lb = b - s_goff[gi];
         const uint32_t seg = lb * kSegBatch + lane;
@@ -608,8 +619,7 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_msaa_kernel(CallTabl
         if (lane == 0) b = atomicAdd(ticket, 1u);
         b = __shfl_sync(kFull, b, 0);
         if (b >= total) break;
-        int gi = 0;
-        while (gi + 1 < tab.n && s_goff[gi + 1] <= b) ++gi;
+        const int gi = batch_groom(s_goff, tab.n, b);
         const GroomDev &g = tab.g[gi];
         const uint32_t lb = b - s_goff[gi];
         const uint32_t seg = lb * kSegBatch + lane;
