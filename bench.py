@@ -434,7 +434,7 @@ def run_crowd(args, rank, world, local_rank):
                               "per_character_launches_ms_per_character": ms_pc / n,
                               "speedup": ms_pc / ms_g, "grooms": n},
             "autotune": tune and {"tuning": tune["tuning"], "best_ms": tune["ms"], "candidates": len(tune["table"])},
-            "gpu_launches": (LAUNCHES_PER_FRAME + 1) * args.steps, "clocks": clk}   # + the resolve's tile-list pass
+            "gpu_launches": (LAUNCHES_PER_FRAME + 2) * args.steps, "clocks": clk}   # + the tile-list count and order passes
     print(json.dumps(line), flush=True)
     return 0
 
@@ -877,7 +877,8 @@ def run_native(args, rank, world, local_rank):
     scene, cfg = make_scene(args.workload)
     grooms = hm.upload_scene(scene)
     W, H = scene.camera.width, scene.camera.height
-    frame = hm.Frame(W, H)
+    # the resolve's tile list: occupied tiles heaviest first on a persistent grid
+    frame = hm.Frame(W, H, tile_list=True)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -957,7 +958,7 @@ def run_native(args, rank, world, local_rank):
                 hg.update_layer_verts(d)
             hm.render_visibility(grooms, scene.camera, frame.vis_center, frame.vis_cons, stats=frame.stats)
             hm.resolve_shade(grooms, scene.camera, scene.lights, scene.filt, frame.vis_center, frame.vis_cons,
-                             rgba2[k % 2])
+                             rgba2[k % 2], tile_scratch=frame.tile_scratch)
             done[k].record(comp)
             copy_s.wait_event(done[k])
             with torch.cuda.stream(copy_s):
@@ -983,7 +984,8 @@ def run_native(args, rank, world, local_rank):
             "segments_per_frame": segs, "raster_segments_per_s": segs / (phase_ms["raster"] * 1e-3),
             "lod_raster_segments_per_s": segs / ((phase_ms["lod"] + phase_ms["raster"]) * 1e-3),
             "roofline": roofline, "kernels": kernels,
-            "e2e": e2e, "gpu_launches": LAUNCHES_PER_FRAME * args.steps, "clocks": clk, "wall_s": wall,
+            "e2e": e2e, "gpu_launches": (LAUNCHES_PER_FRAME + 2) * args.steps,   # + the tile-list count and order passes
+            "clocks": clk, "wall_s": wall,
             "autotune": tune and {"tuning": tune["tuning"], "best_ms": tune["ms"], "candidates": len(tune["table"])}}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(scene)

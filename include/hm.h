@@ -333,9 +333,10 @@ hm_status hm_render_visibility_range(const hm_groom *grooms, int32_t n, int32_t 
  * height) bytes, 4-byte aligned, owned by the caller and not used by any
  * other work in flight.  NULL: one CTA per output tile, each finding out
  * whether its tile holds keys (best when most tiles do, a single groom
- * filling the frame).  With scratch: a pre-pass lists the tiles that hold
- * conservative keys (zero-filling the others) and a persistent grid resolves
- * the listed tiles only (best for sparse frames such as a crowd at 4K).  The
+ * filling the frame).  With scratch: a pre-pass counts each tile's
+ * conservative keys (zero-filling the tiles without any), a one-CTA pass
+ * lists the others heaviest first, and a persistent grid resolves the listed
+ * tiles in that order (best for sparse frames such as a crowd at 4K).  The
  * image is bit-identical either way.
  * Same grooms, in the same order, as the render call that wrote the keys.
  * Errors: HM_ERR_INVALID_ARG, HM_ERR_CUDA. */

@@ -47,26 +47,61 @@ __device__ __forceinline__ float4 centre_result(int R, const uint8_t *s_fa, cons
 // kCgb: the keys carry the compressed payload (Sec. 3.1.2) and shading
 // reads it alone: position from depth, tangent from its code, albedo from
 // the appearance table at (u, v) scaled along w, AO from its code.
-// Tile list for sparse frames: every tile that holds at least one
-// conservative key is appended to list[2 ..] (list[0] = count); every other
-// tile is written with zeros here (no key: RGBA 0).  One warp per tile, lane
-// = column, rows walked.
+// Tile list for sparse frames, first pass: every tile's conservative key
+// count goes to weights[tile] (0: no key); a tile without keys is written
+// with zeros here (no key: RGBA 0).  One warp per tile, lane = column, rows
+// walked.
 template <int kFwdTileH>
 __global__ void __launch_bounds__(256) resolve_tiles_kernel(const uint64_t *__restrict__ vis_a,
                                                             float4 *__restrict__ rgba, int W, int H, int ntx,
-                                                            int ntiles, int *list) {
+                                                            int ntiles, int *__restrict__ weights) {
     const int tile = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (tile >= ntiles) return;
     const int gx = (tile % ntx) * kFwdTileW + lane, y0 = (tile / ntx) * kFwdTileH;
     const int y1 = min(y0 + kFwdTileH, H);
-    bool any = false;
+    int cnt = 0;
     if (gx < W)
         for (int y = y0; y < y1; ++y)
-            any |= !key_empty(__ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)y * W + gx)));
-    if (__any_sync(0xFFFFFFFFu, any)) {
-        if (lane == 0) list[2 + atomicAdd(&list[0], 1)] = tile;
-    } else if (gx < W) {
+            cnt += !key_empty(__ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)y * W + gx)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+    if (lane == 0) weights[tile] = cnt;
+    if (cnt == 0 && gx < W)
         for (int y = y0; y < y1; ++y) rgba[(int64_t)y * W + gx] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Tile list, second pass (one CTA): the tiles with keys, heaviest first, by a
+// counting sort of their key counts into kOrderBuckets classes, so that the
+// persistent resolve starts its longest tiles first and ends without a long
+// tail.  Writes list[0] = listed tiles, list[1] = 0 (the resolve's work
+// counter) and list[2 ..] = tile indices.
+constexpr int kOrderBuckets = 64;
+__global__ void __launch_bounds__(1024) resolve_order_kernel(const int *__restrict__ weights, int ntiles,
+                                                             int tile_px, int *__restrict__ list) {
+    __shared__ int s_hist[kOrderBuckets];
+    if (threadIdx.x < kOrderBuckets) s_hist[threadIdx.x] = 0;
+    __syncthreads();
+    // 1 <= w <= tile_px: class 0 holds the heaviest tiles
+    auto bucket = [tile_px](int w) { return kOrderBuckets - 1 - (int)((int64_t)w * kOrderBuckets / (tile_px + 1)); };
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        const int w = weights[t];
+        if (w > 0) atomicAdd(&s_hist[bucket(w)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int c = 0; c < kOrderBuckets; ++c) {
+            const int n = s_hist[c];
+            s_hist[c] = acc;
+            acc += n;
+        }
+        list[0] = acc;
+        list[1] = 0;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        const int w = weights[t];
+        if (w > 0) list[2 + atomicAdd(&s_hist[bucket(w)], 1)] = t;
     }
 }
 
@@ -409,6 +444,12 @@ size_t resolve_smem_bytes(int radius, int tile_h) {
     return (b + 15) & ~(size_t)15;
 }
 
+// Tiles of the finest tiling (32 x 16), the most any tile height can have.
+static int resolve_max_tiles(int W, int H) { return ((W + kFwdTileW - 1) / kFwdTileW) * ((H + 15) / 16); }
+
+// list[0], list[1], the ordered tile list, then one key count per tile.
+size_t resolve_list_bytes(int W, int H) { return sizeof(int) * (2 + 2 * (size_t)resolve_max_tiles(W, H)); }
+
 template <int TH, bool C>
 static cudaError_t launch_resolve_t(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                                    const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status,
@@ -431,19 +472,15 @@ static cudaError_t launch_resolve_t(const CallTable &tab, const CamDev &cam, con
         return cudaGetLastError();
     }
     const int ntiles = (int)(grid.x * grid.y);
-    cudaError_t e = cudaMemsetAsync(tile_list, 0, 2 * sizeof(int), st);
-    if (e != cudaSuccess) return e;
+    int *weights = tile_list + 2 + resolve_max_tiles(cam.W, cam.H);
     resolve_tiles_kernel<TH><<<(ntiles + 7) / 8, 256, 0, st>>>(vis_a, out, cam.W, cam.H, (int)grid.x, ntiles,
-                                                             tile_list);
+                                                             weights);
+    resolve_order_kernel<<<1, 1024, 0, st>>>(weights, ntiles, kFwdTileW * TH, tile_list);
     resolve_kernel<TH, C><<<resident < ntiles ? resident : ntiles, kFwdThreads, resolve_smem_bytes(R, TH), st>>>(
         tab, cam, Ls, fp, vis_c, vis_a, out, status, cg, tile_list);
     return cudaGetLastError();
 }
 
-size_t resolve_list_bytes(int W, int H) {
-    const size_t ntiles = (size_t)((W + kFwdTileW - 1) / kFwdTileW) * (size_t)((H + 15) / 16);   // 32 x 16 tiles at most
-    return sizeof(int) * (ntiles + 2);
-}
 
 // Resolve tile: 32 x tile_h output pixels per CTA (tile_h 16 or 32).
 cudaError_t launch_resolve(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,

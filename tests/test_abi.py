@@ -213,8 +213,8 @@ def test_resolve_scratch_and_probe_arguments(L):
     pattern are rejected before anything is launched."""
     L.hm_resolve_scratch_bytes.restype = ctypes.c_size_t
     L.hm_resolve_scratch_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32]
-    assert L.hm_resolve_scratch_bytes(1920, 1080) == 4 * (60 * 68 + 2)
-    assert L.hm_resolve_scratch_bytes(33, 17) == 4 * (2 * 2 + 2)
+    assert L.hm_resolve_scratch_bytes(1920, 1080) == 4 * (2 + 2 * 60 * 68)
+    assert L.hm_resolve_scratch_bytes(33, 17) == 4 * (2 + 2 * 2 * 2)
     assert L.hm_resolve_scratch_bytes(0, 10) == 0 and L.hm_resolve_scratch_bytes(10, 16385) == 0
     sc = synth.tiny_scene(0, num_strands=10)
     cam = hm.camera_struct(sc.camera)
