@@ -558,7 +558,7 @@ def run_grad(args, rank, world, local_rank):
                                    "triangles, 6 layers, 20k strands x 12 segments",
                        "l2": "flushed between timed steps (256 MiB write)"},
             "forward_ms": f_ms, "backward_ms": b_ms, "gradient_steps_per_s": 1e3 / (f_ms + b_ms),
-            "gpu_launches": (LAUNCHES_PER_FRAME + 3) * args.steps, "clocks": clk}
+            "gpu_launches": (LAUNCHES_PER_FRAME + 5) * args.steps, "clocks": clk}   # + zero fill, tile-list count and order, two adjoint passes
     print(json.dumps(line), flush=True)
     return 0
 

@@ -778,7 +778,8 @@ extern "C" {
 
 size_t hm_backward_scratch_bytes(int32_t width, int32_t height) {
     if (width < 1 || height < 1) return 0;
-    return (size_t)width * (size_t)height * 32;     // colour gradient + screen-tangent gradients per pixel
+    // colour gradient + screen-tangent gradients per pixel, then the tile list
+    return (size_t)width * (size_t)height * 32 + hm::resolve_list_bytes(width, height);
 }
 
 hm_status hm_shade_backward(const hm_groom *grooms, int32_t n, const hm_camera *cam, const hm_lights *lights,

@@ -391,7 +391,7 @@ __device__ __forceinline__ float2 reconstruct_adjoint(const int *s_dg, const Col
 __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
     CallTable tab, CamDev cam, LightsDev Ls, FilterDev fp, const uint64_t *__restrict__ vis_c,
     const uint64_t *__restrict__ vis_a, const float4 *__restrict__ grad_rgba, float4 *__restrict__ dC,
-    float4 *__restrict__ dTs, uint32_t *status) {
+    float4 *__restrict__ dTs, uint32_t *status, int *list) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int R = fp.enabled ? fp.radius : 0;
     const int sw = kTileW + 2 * R, sh = kTileH + 2 * R, ns = sw * sh;
@@ -408,26 +408,35 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
     uint8_t *s_isoG = reinterpret_cast<uint8_t *>(s_tsA + kResolveThreads);
     uint8_t *s_isoA = s_isoG + kResolveThreads;
     uint8_t *s_fa = s_isoA + kResolveThreads;
-    __shared__ int s_count, s_nJA, s_nJG;
+    __shared__ int s_count, s_nJA, s_nJG, s_tile;
     __shared__ float4 s_dTs[kResolveThreads];    // per tile pixel: d(screen tangent) of G (xy) and A (zw)
     __shared__ float s_gs[kResolveThreads];      // share of the pixel's gradient the centre reconstruction gets
     __shared__ int s_dAv[kResolveThreads];       // conservative-layer depth of the pixel
     __shared__ uint16_t s_jA[kResolveThreads], s_jG[kResolveThreads];
 
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
     const int W = cam.W, H = cam.H;
+    const int ntx = (W + kTileW - 1) / kTileW;
+    const int nlisted = list[0];
     if (tid <= tab.n) {
         uint64_t b = 0;
         for (int i = 0; i < tid; ++i) b += (uint64_t)tab.g[i].S;
         s_bases[tid] = b;
     }
+    // persistent: the tiles holding conservative keys, heaviest first, from
+    // the work counter list[1] (a keyless tile's pixels have RGBA 0 whatever
+    // their neighbours hold, so they pass no gradient)
+    for (;;) {
     if (tid == 0) {
+        s_tile = atomicAdd(&list[1], 1);
         s_count = 0;
         s_nJA = 0;
         s_nJG = 0;
     }
     __syncthreads();
+    if (s_tile >= nlisted) break;
+    const int tile = list[2 + s_tile];
+    const int x0 = (tile % ntx) * kTileW, y0 = (tile / ntx) * kTileH;
     for (int i = tid; i < ns; i += kResolveThreads) {
         const int gx = x0 - R + i % sw, gy = y0 - R + i / sw;
         int dg = -(1 << 30);                 // far below any d24: the depth test alone rejects it
@@ -606,6 +615,8 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
     }
     // screen-tangent gradients of the reference segments, for the geometry pass
     if (inside) dTs[(int64_t)gy * W + gx] = s_dTs[tid];
+    __syncthreads();                // shared memory is reused by the next tile
+    }
 }
 
 // Geometry pass, one thread per key with a gradient (persistent grid over
@@ -773,6 +784,7 @@ cudaError_t launch_resolve_adjoint(const CallTable &tab, const CamDev &cam, cons
     const int64_t npx = (int64_t)cam.W * cam.H;
     float4 *dC = static_cast<float4 *>(scratch);
     float4 *dTs = dC + npx;
+    int *list = reinterpret_cast<int *>(dTs + npx);     // tile list (resolve_list_bytes)
     BwdSinks sinks;
     GeoLayout lay;
     int32_t total = 0;
@@ -797,10 +809,19 @@ cudaError_t launch_resolve_adjoint(const CallTable &tab, const CamDev &cam, cons
                              (int)(kGeoSmemFloats * sizeof(float)));
         attr_set = true;
     }
-    dim3 grid((cam.W + kTileW - 1) / kTileW, (cam.H + kTileH - 1) / kTileH);
-    resolve_adjoint_kernel<<<grid, kResolveThreads, adjoint_smem_bytes(R), st>>>(
-        tab, cam, Ls, fp, vis_c, vis_a, reinterpret_cast<const float4 *>(grad_rgba), dC, dTs, status);
-    cudaError_t e = cudaGetLastError();
+    static int resident = 0;
+    if (resident == 0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resolve_adjoint_kernel, kResolveThreads,
+                                                      adjoint_smem_bytes(HM_MAX_FILTER_RADIUS));
+        resident = (per_sm > 0 ? per_sm : 1) * sms;
+    }
+    cudaError_t e = launch_tile_list(vis_a, nullptr, cam.W, cam.H, kTileH, list, st);
+    if (e != cudaSuccess) return e;
+    const int ntiles = ((cam.W + kTileW - 1) / kTileW) * ((cam.H + kTileH - 1) / kTileH);
+    resolve_adjoint_kernel<<<resident < ntiles ? resident : ntiles, kResolveThreads, adjoint_smem_bytes(R), st>>>(
+        tab, cam, Ls, fp, vis_c, vis_a, reinterpret_cast<const float4 *>(grad_rgba), dC, dTs, status, list);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     geometry_adjoint_kernel<<<sms * kGeoMinBlocks, kGeoThreads, (size_t)lay.total * sizeof(float), st>>>(tab, cam, Ls, vis_c, vis_a,
                                                                                           dC, dTs, sinks, lay, status);

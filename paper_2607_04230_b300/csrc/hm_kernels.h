@@ -55,6 +55,11 @@ cudaError_t launch_resolve(const CallTable &tab, const CamDev &cam, const Lights
                            cudaStream_t st, const CgbDev *compressed = nullptr, int *tile_list = nullptr);
 // Bytes of the resolve's optional tile-list scratch at this resolution.
 size_t resolve_list_bytes(int W, int H);
+// Tile list of a frame's 32 x th tiles (th 16 or 32) into `list` (resolve_list_bytes):
+// per-tile conservative key counts (zero-filling keyless tiles of rgba when it
+// is given), then list[0] = occupied tiles, list[1] = 0, list[2 ..] = them,
+// heaviest first.
+cudaError_t launch_tile_list(const uint64_t *vis_a, float4 *rgba, int W, int H, int th, int *list, cudaStream_t st);
 cudaError_t launch_resolve_adjoint(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                                    const uint64_t *vis_c, const uint64_t *vis_a, const float *grad_rgba,
                                    float *const *glv, float *const *galb, void *scratch, uint32_t *status,

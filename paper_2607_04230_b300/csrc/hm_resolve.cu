@@ -49,8 +49,8 @@ __device__ __forceinline__ float4 centre_result(int R, const uint8_t *s_fa, cons
 // the appearance table at (u, v) scaled along w, AO from its code.
 // Tile list for sparse frames, first pass: every tile's conservative key
 // count goes to weights[tile] (0: no key); a tile without keys is written
-// with zeros here (no key: RGBA 0).  One warp per tile, lane = column, rows
-// walked.
+// with zeros here when rgba is given (no key: RGBA 0).  One warp per tile,
+// lane = column, rows walked.
 template <int kFwdTileH>
 __global__ void __launch_bounds__(256) resolve_tiles_kernel(const uint64_t *__restrict__ vis_a,
                                                             float4 *__restrict__ rgba, int W, int H, int ntx,
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) resolve_tiles_kernel(const uint64_t *__re
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
     if (lane == 0) weights[tile] = cnt;
-    if (cnt == 0 && gx < W)
+    if (rgba && cnt == 0 && gx < W)
         for (int y = y0; y < y1; ++y) rgba[(int64_t)y * W + gx] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
@@ -450,6 +450,17 @@ static int resolve_max_tiles(int W, int H) { return ((W + kFwdTileW - 1) / kFwdT
 // list[0], list[1], the ordered tile list, then one key count per tile.
 size_t resolve_list_bytes(int W, int H) { return sizeof(int) * (2 + 2 * (size_t)resolve_max_tiles(W, H)); }
 
+cudaError_t launch_tile_list(const uint64_t *vis_a, float4 *rgba, int W, int H, int th, int *list, cudaStream_t st) {
+    const int ntx = (W + kFwdTileW - 1) / kFwdTileW, ntiles = ntx * ((H + th - 1) / th);
+    int *weights = list + 2 + resolve_max_tiles(W, H);
+    if (th == 16)
+        resolve_tiles_kernel<16><<<(ntiles + 7) / 8, 256, 0, st>>>(vis_a, rgba, W, H, ntx, ntiles, weights);
+    else
+        resolve_tiles_kernel<32><<<(ntiles + 7) / 8, 256, 0, st>>>(vis_a, rgba, W, H, ntx, ntiles, weights);
+    resolve_order_kernel<<<1, 1024, 0, st>>>(weights, ntiles, kFwdTileW * th, list);
+    return cudaGetLastError();
+}
+
 template <int TH, bool C>
 static cudaError_t launch_resolve_t(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                                    const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status,
@@ -472,10 +483,8 @@ static cudaError_t launch_resolve_t(const CallTable &tab, const CamDev &cam, con
         return cudaGetLastError();
     }
     const int ntiles = (int)(grid.x * grid.y);
-    int *weights = tile_list + 2 + resolve_max_tiles(cam.W, cam.H);
-    resolve_tiles_kernel<TH><<<(ntiles + 7) / 8, 256, 0, st>>>(vis_a, out, cam.W, cam.H, (int)grid.x, ntiles,
-                                                             weights);
-    resolve_order_kernel<<<1, 1024, 0, st>>>(weights, ntiles, kFwdTileW * TH, tile_list);
+    cudaError_t e = launch_tile_list(vis_a, out, cam.W, cam.H, TH, tile_list, st);
+    if (e != cudaSuccess) return e;
     resolve_kernel<TH, C><<<resident < ntiles ? resident : ntiles, kFwdThreads, resolve_smem_bytes(R, TH), st>>>(
         tab, cam, Ls, fp, vis_c, vis_a, out, status, cg, tile_list);
     return cudaGetLastError();
