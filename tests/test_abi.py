@@ -216,6 +216,12 @@ def test_resolve_scratch_and_probe_arguments(L):
     assert L.hm_resolve_scratch_bytes(1920, 1080) == 4 * (2 + 2 * 60 * 68)
     assert L.hm_resolve_scratch_bytes(33, 17) == 4 * (2 + 2 * 2 * 2)
     assert L.hm_resolve_scratch_bytes(0, 10) == 0 and L.hm_resolve_scratch_bytes(10, 16385) == 0
+    # the adjoint's scratch: colour and screen-tangent gradients per pixel, then the same tile list
+    L.hm_backward_scratch_bytes.restype = ctypes.c_size_t
+    L.hm_backward_scratch_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    for w, h in ((1920, 1080), (512, 512), (33, 17)):
+        assert L.hm_backward_scratch_bytes(w, h) == 32 * w * h + L.hm_resolve_scratch_bytes(w, h)
+    assert L.hm_backward_scratch_bytes(0, 10) == 0
     sc = synth.tiny_scene(0, num_strands=10)
     cam = hm.camera_struct(sc.camera)
     fake = ctypes.c_void_p(1 << 20)
