@@ -816,9 +816,14 @@ hm_status hm_shade_backward(const hm_groom *grooms, int32_t n, const hm_camera *
 // ---------------------------------------------------------------------------
 namespace {
 
-// 32 bytes per pixel of the largest frame: the colour gradient and the
-// screen-tangent gradients (two float4).
-static __device__ __align__(256) float4 g_noalloc_scratch[2 * HM_NOALLOC_MAX_PIXELS];
+// 32 bytes per pixel of the largest frame (the colour gradient and the
+// screen-tangent gradients, two float4), then the adjoint's tile list
+// (resolve_list_bytes): a frame of at most HM_NOALLOC_MAX_PIXELS pixels with
+// sides up to 16384 has fewer than 1,600 tiles of 32 x 16, and the entry
+// point checks the list against this room.
+constexpr int kNoallocMaxTiles = 4096;
+constexpr int kNoallocListFloat4 = (4 * (2 + 2 * kNoallocMaxTiles) + 15) / 16;
+static __device__ __align__(256) float4 g_noalloc_scratch[2 * HM_NOALLOC_MAX_PIXELS + kNoallocListFloat4];
 
 // Device address of g_noalloc_scratch on the current device, looked up once
 // per device (the host-side symbol is only a stand-in, never a device
@@ -853,6 +858,8 @@ extern "C" hm_status hm_shade_backward_noalloc(const hm_groom *grooms, int32_t n
     if (st != HM_OK) return st;
     if ((int64_t)cam->width * cam->height > (int64_t)HM_NOALLOC_MAX_PIXELS)
         return fail(HM_ERR_CAPACITY, "frame exceeds HM_NOALLOC_MAX_PIXELS pixels of static scratch");
+    if (hm::resolve_list_bytes(cam->width, cam->height) > sizeof(float4) * (size_t)kNoallocListFloat4)
+        return fail(HM_ERR_CAPACITY, "frame has more tiles than the static scratch's tile list holds");
     if (!d_vis_center || !d_vis_cons || !d_grad_rgba) return fail(HM_ERR_INVALID_ARG, "buffer is NULL");
     if ((reinterpret_cast<uintptr_t>(d_grad_rgba) & 15) || (reinterpret_cast<uintptr_t>(d_vis_center) & 7) ||
         (reinterpret_cast<uintptr_t>(d_vis_cons) & 7))

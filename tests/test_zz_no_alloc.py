@@ -24,9 +24,10 @@ def _grads_close(a, b):
     assert ((a[big] - b[big]).abs() <= 1e-2 * b[big].abs()).all()
 
 
-def test_noalloc_backward_matches_backward_twice():
+@pytest.mark.parametrize("W,H", [(200, 150), (512, 512)])   # 512 x 512: the largest frame the static scratch takes
+def test_noalloc_backward_matches_backward_twice(W, H):
     from paper_2607_04230_b300 import hm
-    sc = synth.tiny_scene(31, width=200, height=150, num_strands=1500, dist_m=0.35)
+    sc = synth.tiny_scene(31, width=W, height=H, num_strands=1500, dist_m=0.35)
     g = sc.grooms[0]
     grooms = hm.upload_scene(sc)
     frame = hm.Frame(sc.camera.width, sc.camera.height)
