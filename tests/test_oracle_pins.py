@@ -1103,3 +1103,146 @@ def test_compressed_resolve_uniform_appearance_and_id_path_agreement():
     # pixels gain or lose their last contributor
     assert ((ref[:, 3].numpy() > 0) != (got[:, 3].numpy() > 0)).mean() < 0.02
     assert float((ref[:, 3] - got[:, 3]).abs().mean()) < 0.02
+
+
+# ---------------------------------------------------------------------------
+# alpha, promotion and the depth-mismatch blend in closed form (Sec. 3.3.2,
+# Sec. 3.3.3, Eq. 7): hand-built keys along a straight horizontal strand
+# (tests/_filter_cases.py), where the strip is the row and the weights are
+# exp(-dx^2 / sigma_par^2)
+# ---------------------------------------------------------------------------
+
+def _line():
+    import _filter_cases as fc
+    sc = fc.line_scene()
+    vc, va, lods = fc.raster(sc)
+    return fc, sc, vc, va, lods
+
+
+def test_alpha_straight_strand_through_centres_is_one():
+    """A strand through the pixel centres hits the same pixels in both layers
+    along its interior, so alpha = H_center / H_cons = 1 there; where the
+    window reaches the conservative-only end pixels it is the exact count
+    ratio (e.g. 6/7), never H_center / (H_center + H_cons)."""
+    fc, sc, vc, va, lods = _line()
+    x0, x1 = fc.span(vc)
+    assert va[fc.px(x0 - 1)] != oracle.EMPTY and vc[fc.px(x0 - 1)] == oracle.EMPTY
+    out, _ = fc.oracle_filter(sc, lods, vc, va)
+    for x in range(x0 + 5, x1 - 4):
+        assert out[fc.px(x), 3] == 1.0
+    assert out[fc.px(x0), 3] == 6 / 7 and out[fc.px(x1), 3] == 6 / 7
+    assert out[fc.px(x0 + 4), 3] == 10 / 11
+
+
+def test_alpha_is_exact_count_ratio_over_the_strip():
+    """Centre keys erased at two pixels of the row (conservative keys kept),
+    conservative-only keys added on the next row: alpha at a centre pixel of
+    the row is 9/11 (rows off the strip do not count), and every pixel of the
+    row matches the closed form."""
+    fc, sc, vc, va, lods = _line()
+    x0, x1 = fc.span(vc)
+    c = (x0 + x1) // 2
+    vc = vc.copy()
+    va = va.copy()
+    for dx in (1, -3):
+        vc[fc.px(c + dx)] = oracle.EMPTY
+    for x in range(c - 4, c + 5):
+        va[fc.px(x, fc.ROW + 1)] = va[fc.px(x)]
+    out, dec = fc.oracle_filter(sc, lods, vc, va)
+    assert dec["HcG"][fc.px(c)] == 9 and dec["HaG"][fc.px(c)] == 11
+    assert out[fc.px(c), 3] == 9 / 11
+    cols = fc.shaded_colours(sc, lods, vc, va)
+    for x in range(x0 - 1, x1 + 2):
+        np.testing.assert_allclose(out[fc.px(x)], fc.expected_row_pixel(x, vc, va, cols), rtol=1e-12, atol=1e-15)
+
+
+def test_promoted_pixel_is_the_colour_free_average_of_its_contributors():
+    """A promoted pixel (conservative key only) with exactly two contributing
+    centre neighbours of different colours (dx = +1 relabelled to a second
+    strand, dx = -2) and one neighbour beyond the depth-reject threshold
+    (dx = +3): Eq. 7 with the colour term off gives
+    (w(1) C_1 + w(2) C_2) / (w(1) + w(2)), w(d) = exp(-d^2 / sigma_par^2),
+    and alpha = 3 / 11."""
+    fc, sc, vc, va, lods = _line()
+    x0, x1 = fc.span(vc)
+    c = (x0 + x1) // 2
+    rej, _ = oracle.depth_thresholds(sc.camera, sc.filt)
+    vc = vc.copy()
+    keep = {c + 1, c - 2, c + 3}
+    for x in range(c - 5, c + 6):
+        if x not in keep:
+            vc[fc.px(x)] = oracle.EMPTY
+    vc[fc.px(c + 1)] = fc.with_strand(vc[fc.px(c + 1)], 1)
+    d = int(vc[fc.px(c + 3)]) >> 40
+    vc[fc.px(c + 3)] = fc.with_depth(vc[fc.px(c + 3)], d + rej + 1)
+    out, _ = fc.oracle_filter(sc, lods, vc, va)
+    cols = fc.shaded_colours(sc, lods, vc, va)
+    c1, c2 = cols[fc.px(c + 1)], cols[fc.px(c - 2)]
+    assert np.abs(c1 - c2).max() > 0.1                       # distinct colours
+    sp = 0.5 * 5
+    w1, w2 = math.exp(-1 / sp ** 2), math.exp(-4 / sp ** 2)
+    np.testing.assert_allclose(out[fc.px(c), :3], (w1 * c1 + w2 * c2) / (w1 + w2), rtol=1e-12)
+    assert out[fc.px(c), 3] == 3 / 11
+    # the neighbour just inside the threshold contributes
+    vc[fc.px(c + 3)] = fc.with_depth(vc[fc.px(c + 3)], d + rej)
+    out2, _ = fc.oracle_filter(sc, lods, vc, va)
+    c3 = cols[fc.px(c + 3)]
+    w3 = math.exp(-9 / sp ** 2)
+    np.testing.assert_allclose(out2[fc.px(c), :3], (w1 * c1 + w2 * c2 + w3 * c3) / (w1 + w2 + w3), rtol=1e-12)
+
+
+def test_depth_mismatch_blend_closed_form():
+    """A centre pixel whose conservative key is 50 d24 units closer than its
+    centre key (mismatch threshold 33): rgb = a' C' + (1 - a') C_G with alpha
+    1, where C' is the colour-free reconstruction at the conservative depth,
+    C_G the colour-weighted one at the centre depth, a' = 9/11; a pixel whose
+    closer key has no contributor within the reject threshold outputs C_G; a
+    difference below the threshold is no mismatch."""
+    fc, sc, vc, va, lods = _line()
+    x0, x1 = fc.span(vc)
+    c = (x0 + x1) // 2
+    rej, mis = oracle.depth_thresholds(sc.camera, sc.filt)
+    assert mis == 33
+    vc = vc.copy()
+    va = va.copy()
+    for dx in (-4, -1, 2):                       # a second colour in the window
+        for buf in (vc, va):
+            buf[fc.px(c + dx)] = fc.with_strand(buf[fc.px(c + dx)], 1)
+    for dx in (3, -5):                           # two promoted pixels: a' = 9/11
+        vc[fc.px(c + dx)] = oracle.EMPTY
+    D = int(vc[fc.px(c)]) >> 40
+    va[fc.px(c)] = fc.with_strand(fc.with_depth(va[fc.px(c)], D - 50), 2)
+    far_px, near_px = c + 7, c - 7
+    va[fc.px(far_px)] = fc.with_depth(va[fc.px(far_px)], D - 500)
+    va[fc.px(near_px)] = fc.with_depth(va[fc.px(near_px)], D - (mis - 1))
+    out, dec = fc.oracle_filter(sc, lods, vc, va)
+    cols = fc.shaded_colours(sc, lods, vc, va)
+    sp, sc_ = 0.5 * 5, float(np.float32(0.9))     # sigma_c is a binary32 parameter
+    CP = cols[fc.px(c)]
+    num_g, den_g, num_a, den_a = np.zeros(3), 0.0, np.zeros(3), 0.0
+    for dx in range(-5, 6):
+        q = fc.px(c + dx)
+        if vc[q] == oracle.EMPTY:
+            continue
+        ws = math.exp(-dx * dx / sp ** 2)
+        wc = math.exp(-float(((CP - cols[q]) ** 2).sum()) / sc_ ** 2)
+        num_g += ws * wc * cols[q]
+        den_g += ws * wc
+        num_a += ws * cols[q]
+        den_a += ws
+    CG, CA = num_g / den_g, num_a / den_a
+    assert np.abs(CG - CA).max() > 1e-3
+    assert dec["HcA"][fc.px(c)] == 9 and dec["HaA"][fc.px(c)] == 11
+    a = 9 / 11
+    np.testing.assert_allclose(out[fc.px(c), :3], a * CA + (1 - a) * CG, rtol=1e-12)
+    assert out[fc.px(c), 3] == 1.0
+    # closer key with no centre neighbour near its depth: C_G, alpha 1
+    e = fc.expected_row_pixel(far_px, vc, va, cols)
+    np.testing.assert_allclose(out[fc.px(far_px)], e, rtol=1e-12)
+    assert e[3] == 1.0
+    # a difference of mis - 1 is no mismatch: C_G with alpha H_c / H_a
+    e = fc.expected_row_pixel(near_px, vc, va, cols)
+    np.testing.assert_allclose(out[fc.px(near_px)], e, rtol=1e-12)
+    assert out[fc.px(near_px), 3] == e[3] == dec["HcG"][fc.px(near_px)] / dec["HaG"][fc.px(near_px)]
+    for x in range(x0 - 1, x1 + 2):
+        np.testing.assert_allclose(out[fc.px(x)], fc.expected_row_pixel(x, vc, va, cols), rtol=1e-12, atol=1e-15)
