@@ -86,18 +86,78 @@ def make_scene(name):
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
+class _Nvml:
+    """The few read-only NVML queries the clock record needs, through ctypes
+    on the driver's libnvidia-ml (no Python binding is needed on the box)."""
+    CLOCK_SM = 1
+
+    def __init__(self, uuid: str):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        for name in ("nvmlInit_v2", "nvmlShutdown"):
+            getattr(self.lib, name).restype = ctypes.c_int
+        self._ok(self.lib.nvmlInit_v2())
+        self.h = ctypes.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)))
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def _ok(self, rc):
+        if rc != 0:
+            raise RuntimeError(f"NVML error {rc}")
+
+    def clock(self, max_clock=False):
+        v = self.ct.c_uint()
+        fn = self.lib.nvmlDeviceGetMaxClockInfo if max_clock else self.lib.nvmlDeviceGetClockInfo
+        self._ok(fn(self.h, self.CLOCK_SM, self.ct.byref(v)))
+        return float(v.value)
+
+    def reasons(self):
+        v = self.ct.c_ulonglong()
+        self._ok(self.reasons_fn(self.h, self.ct.byref(v)))
+        return int(v.value)
+
+    def close(self):
+        self.lib.nvmlShutdown()
+
+
 class ClockSampler:
+    """SM clock and clock-event reasons of one GPU, read (never set) while
+    the timed region runs.  NVML is polled every ~2 ms from a thread, so a
+    timed region of a few tens of milliseconds still gets samples; without
+    NVML, nvidia-smi's 100 ms loop is the fallback."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    REASON_BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+                   "hw_thermal_slowdown": 0x40, "hw_power_brake_slowdown": 0x80}
 
-    def __init__(self, gpu_id: str):
+    def __init__(self, gpu_id: str, period_s: float = 0.002):
         self.gpu_id = gpu_id
+        self.period_s = period_s
         self.proc = None
         self.lines = []
         self.thread = None
+        self.nvml = None
+        self.nvml_error = None
+        self.samples = []            # (sm MHz, reason bits)
+        self.sm_max = 0.0
+        self.running = False
 
     def start(self):
+        try:
+            self.nvml = _Nvml(self.gpu_id)
+            self.sm_max = self.nvml.clock(max_clock=True)
+        except Exception as e:      # no NVML library or device: nvidia-smi
+            self.nvml_error = str(e)
+            self.nvml = None
+        self.running = True
+        if self.nvml is not None:
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -108,11 +168,33 @@ class ClockSampler:
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
 
+    def _poll(self):
+        while self.running:
+            try:
+                self.samples.append((self.nvml.clock(), self.nvml.reasons()))
+            except Exception as e:
+                self.nvml_error = str(e)
+                return
+            time.sleep(self.period_s)
+
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
     def stop(self):
+        self.running = False
+        if self.nvml is not None:
+            if self.thread:
+                self.thread.join(timeout=5)
+            try:
+                self.nvml.close()
+            except Exception:
+                pass
+            if not self.samples:
+                return {"samples": 0, "error": self.nvml_error}
+            reasons = sorted({n for _, bits in self.samples for n, b in self.REASON_BITS.items() if bits & b})
+            return {"sm_mhz": statistics.median(s for s, _ in self.samples), "sm_max_mhz": self.sm_max,
+                    "reasons": reasons, "samples": len(self.samples), "source": "NVML, polled every 2 ms"}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -136,9 +218,9 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(name)
         if not sm:
-            return None
+            return {"samples": 0, "error": self.nvml_error}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi, every 100 ms", "nvml_error": self.nvml_error}
 
 
 # ---------------------------------------------------------------------------
@@ -186,7 +268,8 @@ def ncu_traffic(kernel: str, workload: str):
 # L2 sectors (32 B) one 64-bit atomicMin of each probe pattern touches:
 # pattern 0, consecutive lanes on consecutive keys, puts four in a sector;
 # pattern 1, multiplicatively hashed addresses, gives every atomic its own
-# sector.  Both saturate the same L2 RED sector rate (ncu, profiles/).
+# sector.  Both saturate the same L2 RED sector rate: ncu counts of
+# lts__t_sectors_srcunit_tex_op_red.sum over the probe's event time agree within a few %.
 PROBE_SECTORS_PER_ATOMIC = {0: 0.25, 1: 1.0}
 
 
@@ -385,12 +468,12 @@ def run_crowd(args, rank, world, local_rank):
     tune = None
     if not args.no_autotune:
         tune = autotune.autotune(cr.render_batched, scene, segs, n=3)
-    # per-kernel phase times (same kernels, outside the graph)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(5)]
+    # per-kernel phase times (same kernels, outside the graph): medians of 20 frames
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(20)]
     for row in ev:
         for e in row:
             e.record()
-    for k in range(5):
+    for k in range(20):
         flush.fill_(k)
         hm.set_phase_events(ev[k])
         cr.render_batched()
@@ -412,7 +495,12 @@ def run_crowd(args, rank, world, local_rank):
     clk = clocks.stop()
     for _ in range(3):
         cr.render_per_character()
-    t_pc = _timed(torch, cr.render_per_character, max(10, args.steps // 4), flush)
+    n_pc = max(10, args.steps // 4)
+    t_pc = _timed(torch, cr.render_per_character, n_pc, flush)
+    cr.capture_per_character()
+    for _ in range(3):
+        cr.replay_per_character()
+    t_pcg = _timed(torch, cr.replay_per_character, n_pc, flush)
     hm.get_device_status()
     tg = max_over_ranks(sum(t_graph) * 1e-3, world)
     if rank != 0:
@@ -422,19 +510,25 @@ def run_crowd(args, rank, world, local_rank):
     ms_g = tg / args.steps * 1e3
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
     kernels, roofline = frame_roofline(atomics, phase_ms, W, H, peak_rates, args.workload, clk, sms)
-    ms_pc = statistics.mean(t_pc)
+    frame = frame_bound(kernels, phase_ms, W, H, statistics.median(t_graph))
+    ms_pc, ms_pcg = statistics.median(t_pc), statistics.median(t_pcg)
     line = {"metric": METRIC, "value": job_throughput(segs, args.steps, world, tg), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_g, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
             "config": dict(cfg, parallelism=f"replicas x{world}", batching="one render + one resolve call over "
                            "all grooms, replayed as a CUDA graph"),
             "strands_after_lod": st["strands"], "segments_per_frame": segs, "covered_pairs": atomics,
-            "frame_ms_phases": phase_ms, "roofline": roofline, "kernels": kernels,
+            "frame_ms_phases": phase_ms, "roofline": roofline, "kernels": kernels, "frame_roofline": frame,
             "per_character": {"batched_graph_ms_per_character": ms_g / n,
-                              "per_character_launches_ms_per_character": ms_pc / n,
-                              "speedup": ms_pc / ms_g, "grooms": n},
+                              "per_character_graph_ms_per_character": ms_pcg / n,
+                              "speedup_graph_vs_graph": ms_pcg / ms_g,
+                              "per_character_eager_ms_per_character": ms_pc / n,
+                              "speedup_vs_eager": ms_pc / ms_g, "grooms": n,
+                              "per_character_path": "one hm_render_visibility_range call per groom into the shared "
+                                                    "key buffers, then one resolve"},
             "autotune": tune and {"tuning": tune["tuning"], "best_ms": tune["ms"], "candidates": len(tune["table"])},
-            "gpu_launches": (LAUNCHES_PER_FRAME + 2) * args.steps, "clocks": clk}   # + the tile-list count and order passes
+            # graph replays: + the tile-list count and order passes per frame
+            "gpu_launches": (LAUNCHES_PER_FRAME + 2) * args.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -715,6 +809,25 @@ def run_shadow(args, rank, world, local_rank):
     return 0
 
 
+def frame_bound(kernels, phase_ms, W, H, frame_ms):
+    """Roofline of a whole frame: each phase's time at its bound (clear: 16 B/px
+    written at the measured HBM bandwidth; LOD pre-pass: taken as zero, a
+    latency-bound pass of a few hundred thousand threads; raster: its atomics'
+    L2 RED sectors at the probe's sector rate; resolve: 32 B/px at HBM), summed,
+    over the measured frame time."""
+    peaks, _ = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) * 1e9
+    rk, sk = kernels["raster_kernel"], kernels["resolve_kernel"]
+    t_clear = 16 * W * H / hbm * 1e3
+    t_raster = rk["ms"] * rk["achieved"] / rk["peak"]
+    t_resolve = sk["ms"] * sk["achieved"] / sk["peak"]
+    total = t_clear + t_raster + t_resolve
+    return {"bound_ms": {"clear": t_clear, "lod": 0.0, "raster": t_raster, "resolve": t_resolve, "total": total},
+            "frame_ms": frame_ms, "frac": total / frame_ms,
+            "phase_frac": {k: (b / phase_ms[k] if phase_ms.get(k) else None)
+                           for k, b in (("clear", t_clear), ("raster", t_raster), ("resolve", t_resolve))}}
+
+
 def frame_roofline(atomics, phase_ms, W, H, peak_rates, workload, clk, sms):
     """Roofline of one frame's two main kernels: the rasterizer against the
     L2 RED sector rate of the live atomic probe (`peak_rates`, atomics/s per
@@ -763,7 +876,8 @@ def frame_roofline(atomics, phase_ms, W, H, peak_rates, workload, clk, sms):
                                 f"{2 * W * H}-element buffer: coalesced {peak_rates[0] / 1e9:.1f} Gatom/s "
                                 f"(4 per sector = {peak_rates[0] * 0.25 / 1e9:.1f} G sectors/s), hashed "
                                 f"{peak_rates[1] / 1e9:.1f} Gatom/s (1 per sector); ncu shows both patterns "
-                                "at the same L2 RED sector rate (profiles/l2_red_sector_rate.md)")
+                                "at the same L2 RED sector rate (ncu lts__t_sectors_srcunit_tex_op_red.sum over the "
+                                "probe's event time)")
                 if d["bound"] == "l2_atomic" else f"{peaks_kind} hbm_gbs of MEASURED_PEAKS.json",
                 "work_per_launch": d["work"]}
     for k in kernels.values():
@@ -921,7 +1035,7 @@ def run_native(args, rank, world, local_rank):
         dist.barrier()
     clk = clocks.stop()
     frame_ms = [e[0].elapsed_time(e[5]) for e in ev]
-    phase_ms = {name: sum(e[a].elapsed_time(e[b]) for e in ev) / args.steps
+    phase_ms = {name: statistics.median(e[a].elapsed_time(e[b]) for e in ev)
                 for name, a, b in (("clear", 0, 1), ("lod", 1, 2), ("raster", 2, 3), ("resolve", 4, 5))}
     t_total = max_over_ranks(sum(frame_ms) * 1e-3, world)
     value = job_throughput(segs, args.steps, world, t_total)

@@ -377,14 +377,20 @@ size_t hm_backward_scratch_bytes(int32_t width, int32_t height);
  * synchronization is not acceptable (a real-time frame loop), or code whose
  * device memory is owned by another allocator with a fixed budget.  This
  * entry point takes the same inputs and outputs as hm_shade_backward but no
- * d_scratch: its colour-gradient scratch is a static array of the library
- * (HM_NOALLOC_MAX_PIXELS * 32 bytes = 8 MiB, held on every GPU that loads
- * libhm until the process exits).  It calls no allocator.
- *  - Frames larger than HM_NOALLOC_MAX_PIXELS pixels are rejected with
- *    HM_ERR_CAPACITY before anything is launched.
+ * d_scratch: its scratch is a static array of the library, held on every GPU
+ * that loads libhm until the process exits: HM_NOALLOC_MAX_PIXELS * 32 bytes
+ * (8 MiB) of per-pixel colour and screen-tangent gradients, then about
+ * 32 KiB for the adjoint's tile list (room for 4,096 tiles of 32 x 16
+ * pixels).  It calls no allocator.
+ *  - Errors beyond hm_shade_backward's: HM_ERR_CAPACITY, before anything is
+ *    launched, for a frame of more than HM_NOALLOC_MAX_PIXELS pixels, or for
+ *    one with more tiles than the list room (no frame within the pixel
+ *    limit has: at most 1,600 tiles with sides up to HM_MAX_RESOLUTION).
  *  - The first call on a device looks up the array's device address (one
- *    cudaGetSymbolAddress with that device current); make that first call
- *    before any stream capture.
+ *    cudaGetSymbolAddress with that device current; concurrent first calls
+ *    from several host threads look it up once); make that first call
+ *    before any stream capture.  The address is kept for the process: do
+ *    not call the library again on a device after cudaDeviceReset.
  *  - Every call on a device shares the one array and clears it on the
  *    stream before use, so calls that overlap on the GPU (different streams
  *    without ordering) race on it; order them.

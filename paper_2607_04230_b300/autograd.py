@@ -55,8 +55,12 @@ class HairRender(torch.autograd.Function):
         galb = torch.zeros(ctx.alb_shape, dtype=torch.float32, device=dev)
         nbytes = hm.backward_scratch_bytes(sc.camera.width, sc.camera.height)
         scratch = torch.empty(nbytes // 4, dtype=torch.float32, device=dev)
+        g = grad_rgba.float().contiguous()
+        if g.data_ptr() % 16:
+            # the adjoint reads float4 rows: a view at an unaligned offset is copied
+            g = g.clone(memory_format=torch.contiguous_format)
         hm.shade_backward([ctx.groom], sc.camera, sc.lights, sc.filt, ctx.vis[0], ctx.vis[1],
-                          grad_rgba.float().contiguous(), [glv], [galb], scratch, shadows=ctx.shadows)
+                          g, [glv], [galb], scratch, shadows=ctx.shadows)
         return glv, galb, None, None, None, None
 
 

@@ -22,6 +22,7 @@ class Crowd:
         # occupied tiles first
         self.frame = hm.Frame(scene.camera.width, scene.camera.height, tile_list=True)
         self.graph = None
+        self.graph_pc = None
         self._torch = torch
 
     # -- one call over all grooms ------------------------------------------
@@ -42,6 +43,22 @@ class Crowd:
 
     def replay(self):
         self.graph.replay()
+
+    def capture_per_character(self):
+        """The per-character path (one render call per groom, then one
+        resolve) captured into a CUDA graph of its own, so the two paths are
+        compared without host launch overhead on either side."""
+        torch = self._torch
+        self.render_per_character()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.render_per_character()
+        self.graph_pc = g
+        return g
+
+    def replay_per_character(self):
+        self.graph_pc.replay()
 
     # -- one call per groom ------------------------------------------------
     def render_per_character(self):

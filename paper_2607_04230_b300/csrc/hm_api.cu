@@ -1,6 +1,7 @@
 // hm_api.cu -- the C ABI declared in include/hm.h: argument validation, groom
 // upload, per-call groom tables, kernel launches, device status.
 #include <cmath>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -73,15 +74,11 @@ bool finite_all(const float *v, int n) {
 }
 
 uint32_t *status_word() {
-    static uint32_t *ptrs[64] = {nullptr};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    if (!ptrs[dev]) {
+    static hm::PerDevice<uint32_t *> addr;
+    return addr.get([](int) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) return nullptr;
-        ptrs[dev] = static_cast<uint32_t *>(p);
-    }
-    return ptrs[dev];
+        return cudaGetSymbolAddress(&p, g_device_status) == cudaSuccess ? static_cast<uint32_t *>(p) : nullptr;
+    });
 }
 
 hm_status check_camera(const hm_camera *cam) {
@@ -158,14 +155,13 @@ hm_status build_table(const hm_groom *grooms, int32_t n, hm::CallTable &tab) {
 // environment, the library's device allocations after the first N report
 // HM_ERR_OOM without calling the allocator (read once per process).
 bool injected_alloc_failure() {
-    static long limit = -2;
-    static long done = 0;
-    if (limit == -2) {
+    static const long limit = [] {
         const char *e = std::getenv("HM_FAIL_ALLOC_AFTER");
-        limit = e ? std::strtol(e, nullptr, 10) : -1;
-    }
+        return e ? std::strtol(e, nullptr, 10) : -1L;
+    }();
+    static std::atomic<long> done{0};
     if (limit < 0) return false;
-    return done++ >= limit;
+    return done.fetch_add(1) >= limit;
 }
 
 template <typename T>
@@ -219,16 +215,13 @@ bool valid_tuning(const hm_tuning &t) {
 
 namespace hm {
 int num_sms() {
-    static int cache[64] = {0};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) dev = 0;
-    if (!cache[dev]) {
-        int v = 0;
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        cache[dev] = v > 0 ? v : 1;
-    }
-    return cache[dev];
+    static PerDevice<int> count;
+    const int v = count.get([](int dev) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n;
+    });
+    return v > 0 ? v : 1;
 }
 }  // namespace hm
 
@@ -826,25 +819,23 @@ constexpr int kNoallocListFloat4 = (4 * (2 + 2 * kNoallocMaxTiles) + 15) / 16;
 static __device__ __align__(256) float4 g_noalloc_scratch[2 * HM_NOALLOC_MAX_PIXELS + kNoallocListFloat4];
 
 // Device address of g_noalloc_scratch on the current device, looked up once
-// per device (the host-side symbol is only a stand-in, never a device
-// address).  nullptr with the CUDA error in `err` when the lookup fails.
+// per device with that device current (the host-side symbol is only a
+// stand-in, never a device address); concurrent first calls from several
+// host threads look it up once.  nullptr with the CUDA error in `err` when
+// the lookup fails (the next call tries again).
 float4 *noalloc_scratch(cudaError_t &err) {
-    static float4 *ptrs[64] = {nullptr};
+    static hm::PerDevice<float4 *> addr;
     err = cudaSuccess;
-    int dev = 0;
-    err = cudaGetDevice(&dev);
-    if (err != cudaSuccess) return nullptr;
-    if (dev < 0 || dev >= 64) {
-        err = cudaErrorInvalidDevice;
-        return nullptr;
+    float4 *p = addr.get([&err](int) {
+        void *q = nullptr;
+        err = cudaGetSymbolAddress(&q, g_noalloc_scratch);
+        return err == cudaSuccess ? static_cast<float4 *>(q) : nullptr;
+    });
+    if (!p && err == cudaSuccess) {
+        const cudaError_t e = cudaGetLastError();
+        err = e != cudaSuccess ? e : cudaErrorInvalidDevice;
     }
-    if (!ptrs[dev]) {
-        void *p = nullptr;
-        err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (err != cudaSuccess) return nullptr;
-        ptrs[dev] = static_cast<float4 *>(p);
-    }
-    return ptrs[dev];
+    return p;
 }
 
 }  // namespace

@@ -801,21 +801,19 @@ cudaError_t launch_resolve_adjoint(const CallTable &tab, const CamDev &cam, cons
     const int sms = num_sms();
     zero_float4_kernel<<<sms * 8, 256, 0, st>>>(dC, 2 * npx);
     const int R = fp.enabled ? fp.radius : 0;
-    static bool attr_set = false;
-    if (!attr_set) {
+    // per device: the kernels' shared-memory limits (an attribute of the
+    // current device) and the persistent tile grid that fits
+    static PerDevice<int> resident_tiles;
+    const int resident = resident_tiles.get([sms](int) {
         cudaFuncSetAttribute(resolve_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)adjoint_smem_bytes(HM_MAX_FILTER_RADIUS));
         cudaFuncSetAttribute(geometry_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kGeoSmemFloats * sizeof(float)));
-        attr_set = true;
-    }
-    static int resident = 0;
-    if (resident == 0) {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resolve_adjoint_kernel, kResolveThreads,
                                                       adjoint_smem_bytes(HM_MAX_FILTER_RADIUS));
-        resident = (per_sm > 0 ? per_sm : 1) * sms;
-    }
+        return (per_sm > 0 ? per_sm : 1) * sms;
+    });
     cudaError_t e = launch_tile_list(vis_a, nullptr, cam.W, cam.H, kTileH, list, st);
     if (e != cudaSuccess) return e;
     const int ntiles = ((cam.W + kTileW - 1) / kTileW) * ((cam.H + kTileH - 1) / kTileH);

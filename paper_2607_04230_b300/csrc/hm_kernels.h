@@ -2,8 +2,10 @@
 // kernels take by value.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "hm_device.cuh"
@@ -40,6 +42,38 @@ struct FilterDev {
     float hw;                  // strip half-width
     float inv_spar2, inv_sperp2, inv_siso2, inv_sc2;
     int32_t drej, dmis;        // depth thresholds in d24 units
+};
+
+constexpr int kMaxDevices = 64;
+
+// A value per CUDA device, made on first use with that device current and
+// kept for the life of the process (symbol addresses, kernel attributes,
+// occupancy-derived grid sizes).  Thread-safe: concurrent first calls on one
+// device run `make` once; a zero result (a failed lookup) is not kept, so the
+// next call tries again.  The cached device state does not survive
+// cudaDeviceReset: a process does not use the library again on a device it
+// has reset.
+template <typename T>
+class PerDevice {
+  public:
+    template <typename F>
+    T get(F &&make) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return T{};
+        T v = val_[dev].load(std::memory_order_acquire);
+        if (v != T{}) return v;
+        std::lock_guard<std::mutex> lock(mu_);
+        v = val_[dev].load(std::memory_order_relaxed);
+        if (v == T{}) {
+            v = make(dev);
+            val_[dev].store(v, std::memory_order_release);
+        }
+        return v;
+    }
+
+  private:
+    std::mutex mu_;
+    std::atomic<T> val_[kMaxDevices] = {};
 };
 
 int num_sms();

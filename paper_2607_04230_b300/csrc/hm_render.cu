@@ -783,13 +783,13 @@ cudaError_t launch_lod(const CallTable &tab, const CamDev &cam, hm_frame_stats *
 // fits (0 = as many as fit).
 template <bool P, int M, int V>
 static int raster_fit_per_sm() {
-    static int cached = 0;
-    if (cached == 0) {
+    static PerDevice<int> fit;
+    const int v = fit.get([](int) {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<P, M, V>, kRasterThreads, 0);
-        cached = per_sm < 1 ? 1 : per_sm;
-    }
-    return cached;
+        return per_sm;
+    });
+    return v < 1 ? 1 : v;
 }
 
 template <bool P, int M, int V>

@@ -466,15 +466,17 @@ static cudaError_t launch_resolve_t(const CallTable &tab, const CamDev &cam, con
                                    const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status,
                                    cudaStream_t st, const CgbDev &cg, int *tile_list) {
     const int R = fp.enabled ? fp.radius : 0;
-    static int resident = 0;
-    if (resident == 0) {
+    // per device: the kernel's shared-memory limit (an attribute of the
+    // current device) and the persistent tile grid that fits
+    static PerDevice<int> resident_tiles;
+    const int resident = resident_tiles.get([](int) {
         cudaFuncSetAttribute(resolve_kernel<TH, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)resolve_smem_bytes(HM_MAX_FILTER_RADIUS, TH));
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resolve_kernel<TH, C>, kFwdThreads,
                                                       resolve_smem_bytes(HM_MAX_FILTER_RADIUS, TH));
-        resident = (per_sm > 0 ? per_sm : 1) * num_sms();
-    }
+        return (per_sm > 0 ? per_sm : 1) * num_sms();
+    });
     dim3 grid((cam.W + kFwdTileW - 1) / kFwdTileW, (cam.H + TH - 1) / TH);
     float4 *out = reinterpret_cast<float4 *>(rgba);
     if (!tile_list) {

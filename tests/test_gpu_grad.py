@@ -221,3 +221,30 @@ def test_two_forwards_then_backward():
     for got, ref in ((xa.grad, ga[0]), (aa.grad, ga[1]), (xb.grad, gb[0]), (ab.grad, gb[1])):
         assert torch.allclose(got, ref, rtol=1e-4, atol=1e-7 * float(ref.abs().max())), \
             float((got - ref).abs().max())
+
+
+def test_unaligned_upstream_gradient():
+    """An upstream gradient that is a contiguous view at an odd float offset
+    (not 16-byte aligned) gives the same layer-vertex and albedo gradients as
+    the same values in an aligned tensor."""
+    from paper_2607_04230_b300 import autograd, hm
+    sc = synth.tiny_scene(28, width=64, height=48, num_strands=300, dist_m=0.3)
+    g = sc.grooms[0]
+    W, H = sc.camera.width, sc.camera.height
+    handle = hm.upload_scene(sc)[0]
+    lv = torch.from_numpy(g.layer_verts).cuda()
+    alb = torch.from_numpy(g.strand_albedo).cuda()
+    n = H * W * 4
+    big = torch.randn(n + 1, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+    unaligned = big[1:].view(H, W, 4)
+    assert unaligned.is_contiguous() and unaligned.data_ptr() % 16 != 0
+    out = []
+    for grad in (unaligned, unaligned.clone()):
+        x, a = lv.clone().requires_grad_(True), alb.clone().requires_grad_(True)
+        rgba = autograd.render(handle, sc, hm.Frame(W, H), x, a)
+        torch.autograd.backward(rgba, grad_tensors=grad)
+        out.append((x.grad.clone(), a.grad.clone()))
+    torch.cuda.synchronize()
+    assert float(out[0][0].abs().max()) > 0
+    for got, ref in zip(out[0], out[1]):     # float atomics: equal up to summation order
+        assert torch.allclose(got, ref, rtol=1e-5, atol=1e-6 * float(ref.abs().max()))
