@@ -527,8 +527,8 @@ def run_crowd(args, rank, world, local_rank):
                               "per_character_path": "one hm_render_visibility_range call per groom into the shared "
                                                     "key buffers, then one resolve"},
             "autotune": tune and {"tuning": tune["tuning"], "best_ms": tune["ms"], "candidates": len(tune["table"])},
-            # graph replays: + the tile-list count and order passes per frame
-            "gpu_launches": (LAUNCHES_PER_FRAME + 2) * args.steps, "clocks": clk}
+            # graph replays: + the tile-list count and order passes and the decode pass per frame
+            "gpu_launches": (LAUNCHES_PER_FRAME + 3) * args.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -1098,7 +1098,7 @@ def run_native(args, rank, world, local_rank):
             "segments_per_frame": segs, "raster_segments_per_s": segs / (phase_ms["raster"] * 1e-3),
             "lod_raster_segments_per_s": segs / ((phase_ms["lod"] + phase_ms["raster"]) * 1e-3),
             "roofline": roofline, "kernels": kernels,
-            "e2e": e2e, "gpu_launches": (LAUNCHES_PER_FRAME + 2) * args.steps,   # + the tile-list count and order passes
+            "e2e": e2e, "gpu_launches": (LAUNCHES_PER_FRAME + 3) * args.steps,   # + the tile-list count and order passes and the decode pass
             "clocks": clk, "wall_s": wall,
             "autotune": tune and {"tuning": tune["tuning"], "best_ms": tune["ms"], "candidates": len(tune["table"])}}
     if not args.no_cpu_baseline and world == 1:

@@ -330,14 +330,20 @@ hm_status hm_render_visibility_range(const hm_groom *grooms, int32_t n, int32_t 
  * estimation, and write straight-alpha RGBA.
  * d_rgba: [height][width][4] float32, 16-byte aligned.
  * d_tile_scratch: NULL, or DEVICE scratch of hm_resolve_scratch_bytes(width,
- * height) bytes, 4-byte aligned, owned by the caller and not used by any
- * other work in flight.  NULL: one CTA per output tile, each finding out
- * whether its tile holds keys (best when most tiles do, a single groom
- * filling the frame).  With scratch: a pre-pass counts each tile's
- * conservative keys (zero-filling the tiles without any), a one-CTA pass
- * lists the others heaviest first, and a persistent grid resolves the listed
- * tiles in that order (best for sparse frames such as a crowd at 4K).  The
- * image is bit-identical either way.
+ * height) bytes (about 32 bytes per pixel), 16-byte aligned, owned by the
+ * caller and not used by any other work in flight.  NULL: one CTA per output
+ * tile, each finding out whether its tile holds keys, decoding the centre
+ * keys of the tile and its filter halo and filtering (best when most tiles
+ * hold keys, a single groom filling the frame).  With scratch: a pre-pass
+ * counts each tile's conservative keys (zero-filling the tiles without any),
+ * a one-CTA pass lists the others heaviest first, a decode pass shades every
+ * centre key of the listed tiles and finds every screen tangent the filter
+ * needs, once per pixel, into the scratch, and a persistent grid filters the
+ * listed tiles in that order.  The image is bit-identical either way for
+ * keys written by the render calls, whose centre-layer keys lie at pixels
+ * the conservative layer also covers (a centre sample box lies inside the
+ * pixel box); with scratch, a centre key in a tile without any conservative
+ * key is treated as absent.
  * Same grooms, in the same order, as the render call that wrote the keys.
  * Errors: HM_ERR_INVALID_ARG, HM_ERR_CUDA. */
 hm_status hm_resolve_shade(const hm_groom *grooms, int32_t n, const hm_camera *cam,

@@ -641,7 +641,7 @@ hm_status hm_resolve_shade(const hm_groom *grooms, int32_t n, const hm_camera *c
     hm_status st = check_camera(cam);
     if (st != HM_OK) return st;
     if (!d_vis_center || !d_vis_cons || !d_rgba) return fail(HM_ERR_INVALID_ARG, "buffer is NULL");
-    if (reinterpret_cast<uintptr_t>(d_tile_scratch) & 3) return fail(HM_ERR_INVALID_ARG, "misaligned tile scratch");
+    if (reinterpret_cast<uintptr_t>(d_tile_scratch) & 15) return fail(HM_ERR_INVALID_ARG, "misaligned tile scratch");
     if ((reinterpret_cast<uintptr_t>(d_rgba) & 15) || (reinterpret_cast<uintptr_t>(d_vis_center) & 7) ||
         (reinterpret_cast<uintptr_t>(d_vis_cons) & 7))
         return fail(HM_ERR_INVALID_ARG, "misaligned buffer");
@@ -665,7 +665,7 @@ hm_status hm_resolve_shade(const hm_groom *grooms, int32_t n, const hm_camera *c
 
 size_t hm_resolve_scratch_bytes(int32_t width, int32_t height) {
     if (width < 1 || height < 1 || width > HM_MAX_RESOLUTION || height > HM_MAX_RESOLUTION) return 0;
-    return hm::resolve_list_bytes(width, height);
+    return hm::resolve_scratch_bytes(width, height);
 }
 
 hm_status hm_resolve_compressed(const hm_camera *cam, const hm_lights *lights, const hm_filter_params *filt,

@@ -87,8 +87,11 @@ cudaError_t launch_probe_atomic_min(uint64_t *buf, int64_t n, int rounds, int pa
 cudaError_t launch_resolve(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                            const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status, int tile_h,
                            cudaStream_t st, const CgbDev *compressed = nullptr, int *tile_list = nullptr);
-// Bytes of the resolve's optional tile-list scratch at this resolution.
+// Bytes of the tile list alone (list, order, per-tile key counts).
 size_t resolve_list_bytes(int W, int H);
+// Bytes of the resolve's optional scratch at this resolution: the tile list
+// (16-byte aligned) and the two-pass resolve's per-pixel arrays.
+size_t resolve_scratch_bytes(int W, int H);
 // Tile list of a frame's 32 x th tiles (th 16 or 32) into `list` (resolve_list_bytes):
 // per-tile conservative key counts (zero-filling keyless tiles of rgba when it
 // is given), then list[0] = occupied tiles, list[1] = 0, list[2 ..] = them,

@@ -105,15 +105,115 @@ __global__ void __launch_bounds__(1024) resolve_order_kernel(const int *__restri
     }
 }
 
+// Two-pass resolve with the tile-list scratch, first pass: over strips of 8
+// rows of the listed tiles (the tiles heaviest first, a tile's strips on
+// consecutive CTAs of a persistent grid, round-robin, so a heavy tile is
+// spread over several SMs), every centre key is decoded and shaded once
+// (px_col = shaded colour, centre depth bits) and every screen tangent the
+// filter needs is found once: px_ts.xy of the centre key, px_ts.zw of the
+// conservative key of a promoted pixel or a depth mismatch, (0, 0) for a
+// degenerate tangent.  The jobs of a strip are listed first (centre decodes,
+// then conservative ones) so whole warps run one kind.  Entries of pixels
+// without those keys are left unwritten; the filter pass reads only the ones
+// its keys say exist.
+constexpr int kDecThreads = 256, kDecRows = 8, kDecPx = kFwdTileW * kDecRows;
+static_assert(kDecPx == kDecThreads, "one strip pixel per thread");
+
+template <int kFwdTileH>
+__global__ void __launch_bounds__(kDecThreads, 4) resolve_decode_kernel(CallTable tab, CamDev cam, LightsDev Ls,
+                                                                       FilterDev fp, const uint64_t *__restrict__ vis_c,
+                                                                       const uint64_t *__restrict__ vis_a,
+                                                                       const int *__restrict__ list,
+                                                                       float4 *__restrict__ px_col,
+                                                                       float4 *__restrict__ px_ts, uint32_t *status) {
+    constexpr int kStrips = kFwdTileH / kDecRows;
+    __shared__ uint64_t s_bases[HM_MAX_GROOMS_PER_CALL + 1];
+    __shared__ uint16_t s_job[2 * kDecPx];
+    __shared__ int s_ng, s_na;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int W = cam.W, H = cam.H;
+    const int ntx = (W + kFwdTileW - 1) / kFwdTileW;
+    if (tid <= tab.n) {
+        uint64_t b = 0;
+        for (int i = 0; i < tid; ++i) b += (uint64_t)tab.g[i].S;
+        s_bases[tid] = b;
+    }
+    const int nwork = list[0] * kStrips;
+    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+        const int tile = list[2 + wi / kStrips];
+        const int x0 = (tile % ntx) * kFwdTileW, y0 = (tile / ntx) * kFwdTileH + (wi % kStrips) * kDecRows;
+        if (tid == 0) {
+            s_ng = 0;
+            s_na = 0;
+        }
+        __syncthreads();
+        // centre decodes go to s_job[0 ..), conservative ones to s_job[kDecPx ..)
+        {
+            const int t = tid;                   // one strip pixel per thread
+            const int gx = x0 + t % kFwdTileW, gy = y0 + t / kFwdTileW;
+            bool gP = false, needA = false;
+            if (gx < W && gy < H) {
+                const int64_t p = (int64_t)gy * W + gx;
+                const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + p));
+                const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + p));
+                gP = !key_empty(kg);
+                needA = !key_empty(ka) && fp.enabled && (!gP || (int)(ka >> 40) + fp.dmis <= (int)(kg >> 40));
+            }
+            const unsigned bg = __ballot_sync(0xFFFFFFFFu, gP), ba = __ballot_sync(0xFFFFFFFFu, needA);
+            int gb = 0, ab = 0;
+            if (lane == 0) {
+                if (bg) gb = atomicAdd(&s_ng, __popc(bg));
+                if (ba) ab = atomicAdd(&s_na, __popc(ba));
+            }
+            gb = __shfl_sync(0xFFFFFFFFu, gb, 0);
+            ab = __shfl_sync(0xFFFFFFFFu, ab, 0);
+            const unsigned below = (1u << lane) - 1u;
+            if (gP) s_job[gb + __popc(bg & below)] = (uint16_t)t;
+            if (needA) s_job[kDecPx + ab + __popc(ba & below)] = (uint16_t)t;
+        }
+        __syncthreads();
+        const int ng = s_ng, na = s_na;
+        for (int j = tid; j < ng + na; j += kDecThreads) {
+            const bool cen = j < ng;
+            const int t = cen ? s_job[j] : s_job[kDecPx + j - ng];
+            const int gx = x0 + t % kFwdTileW, gy = y0 + t / kFwdTileW;
+            const int64_t p = (int64_t)gy * W + gx;
+            const uint64_t key =
+                __ldg(reinterpret_cast<const unsigned long long *>((cen ? vis_c : vis_a) + p));
+            const Decoded d = decode_key(tab, s_bases, cam, key, gx, gy, status);
+            if (cen) {
+                float3 c = make_float3(0.f, 0.f, 0.f);
+                if (d.ok) {
+                    const GroomDev &g = tab.g[d.gi];
+                    const float4 a = __ldg(&g.albedo[d.s]);
+                    c = shade(d.X, d.T, make_float3(a.x, a.y, a.z), cam, Ls, g.roughness, g.tilt, decoded_ao(g, d),
+                              receiver_beta(g, Ls, d.s));
+                }
+                px_col[p] = make_float4(c.x, c.y, c.z, __int_as_float((int)(key >> 40)));
+                reinterpret_cast<float2 *>(px_ts + p)[0] = make_float2(d.tsx, d.tsy);
+            } else {
+                reinterpret_cast<float2 *>(px_ts + p)[1] = make_float2(d.tsx, d.tsy);
+            }
+        }
+        __syncthreads();        // s_job and the counters are reused by the next strip
+    }
+}
+
 // list == nullptr: one CTA per tile (grid = tiles); tiles without keys are
 // found and zero-filled here.  list != nullptr: a persistent grid takes the
 // listed tiles one at a time from the work counter list[1].
-template <int kFwdTileH, bool kCgb>
+//
+// kPre: the decode pass (resolve_decode_kernel) has already shaded every
+// centre key of the listed tiles into px_col and found the screen tangents
+// the filter needs into px_ts, so the tile stages those instead of decoding
+// (no decode of halo keys, which a neighbouring tile decodes again).
+template <int kFwdTileH, bool kCgb, bool kPre>
 __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, CamDev cam, LightsDev Ls, FilterDev fp,
                                                               const uint64_t *__restrict__ vis_c,
                                                               const uint64_t *__restrict__ vis_a,
                                                               float4 *__restrict__ rgba, uint32_t *status,
-                                                              CgbDev cg, int *list) {
+                                                              CgbDev cg, int *list, const float4 *__restrict__ px_col,
+                                                              const float4 *__restrict__ px_ts) {
     constexpr int kFwdTilePx = kFwdTileW * kFwdTileH;
     extern __shared__ __align__(16) unsigned char smem[];
     const int R = fp.enabled ? fp.radius : 0;
@@ -139,6 +239,8 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
     const int W = cam.W, H = cam.H;
     const int ntx = (W + kFwdTileW - 1) / kFwdTileW;
     const int nlisted = list ? list[0] : 0;
+    // per-tile key counts follow the list (room for the finest, 32 x 16, tiling)
+    const int list_cap = ntx * ((H + 15) / 16);
     if (tid <= tab.n) {
         uint64_t b = 0;
         for (int i = 0; i < tid; ++i) b += (uint64_t)tab.g[i].S;
@@ -189,11 +291,25 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
             const int64_t p = (int64_t)gy * W + gx;
             const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + p));
             const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + p));
+            float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
             if (!key_empty(kg)) {
                 dg = (int)(kg >> 40);
-                s_list[atomicAdd(&s_count, 1)] = (uint16_t)i;
+                if (!kPre) {
+                    s_list[atomicAdd(&s_count, 1)] = (uint16_t)i;
+                } else if (gx >= x0 && gx < x0 + kFwdTileW && gy >= y0 && gy < y0 + kFwdTileH) {
+                    c = px_col[p];
+                } else {
+                    // a halo key lies in a neighbouring tile, which the decode
+                    // pass covered if it is listed (it holds a conservative
+                    // key, as every rendered tile with a centre key does)
+                    const int nt = (gy / kFwdTileH) * ntx + gx / kFwdTileW;
+                    if (__ldg(&list[2 + list_cap + nt]) > 0) c = px_col[p];
+                }
             }
             fa = !key_empty(ka);
+            s_fa[i] = fa;
+            s_col[i] = make_float4(c.x, c.y, c.z, __int_as_float(dg));
+            continue;
         }
         s_fa[i] = fa;
         s_col[i] = make_float4(0.f, 0.f, 0.f, __int_as_float(dg));
@@ -201,8 +317,20 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
     for (int t = tid; t < kFwdTilePx; t += kFwdThreads) s_flag[t] = 3;
     __syncthreads();
 
-    // 2. decode + shade every staged centre-sample pixel
-    const int ncen = s_count;
+    // 2. decode + shade every staged centre-sample pixel (kPre: the decode
+    // pass did; only the tile pixels' centre screen tangents are read)
+    if (kPre) {
+        for (int t = tid; t < kFwdTilePx; t += kFwdThreads) {
+            const int gx = x0 + t % kFwdTileW, gy = y0 + t / kFwdTileW;
+            if (gx >= W || gy >= H) continue;
+            const int mid = (t / kFwdTileW + R) * sw + t % kFwdTileW + R;
+            if (dg_at(mid) < 0) continue;
+            const float4 ts = px_ts[(int64_t)gy * W + gx];
+            s_ts[t] = make_float2(ts.x, ts.y);
+            if (ts.x != 0.0f || ts.y != 0.0f) s_flag[t] = 2;     // a degenerate tangent is stored as (0, 0)
+        }
+    }
+    const int ncen = kPre ? 0 : s_count;
     for (int li = tid; li < ncen; li += kFwdThreads) {
         const int i = s_list[li];
         const int lx = i % sw, ly = i / sw;
@@ -299,7 +427,12 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
             const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx));
             float tsx, tsy;
             bool iso;
-            if (kCgb) {
+            if (kPre) {
+                const float4 ts = px_ts[(int64_t)gy * W + gx];
+                tsx = ts.z;
+                tsy = ts.w;
+                iso = tsx == 0.0f && tsy == 0.0f;
+            } else if (kCgb) {
                 const DecodedC d = decode_compressed(cam, ka, gx, gy);
                 tsx = d.tsx;
                 tsy = d.tsy;
@@ -461,34 +594,65 @@ cudaError_t launch_tile_list(const uint64_t *vis_a, float4 *rgba, int W, int H, 
     return cudaGetLastError();
 }
 
+// The two-pass resolve's per-pixel arrays follow the tile list in the
+// scratch: px_col [H][W] float4, then px_ts [H][W] float4.
+static size_t resolve_list_bytes_aligned(int W, int H) { return (resolve_list_bytes(W, H) + 15) & ~(size_t)15; }
+
+size_t resolve_scratch_bytes(int W, int H) {
+    return resolve_list_bytes_aligned(W, H) + 2 * sizeof(float4) * (size_t)W * (size_t)H;
+}
+
+template <int TH, bool C, bool P>
+static int resolve_resident() {
+    // per device: the kernel's shared-memory limit (an attribute of the
+    // current device) and the persistent tile grid that fits
+    static PerDevice<int> resident_tiles;
+    return resident_tiles.get([](int) {
+        cudaFuncSetAttribute(resolve_kernel<TH, C, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)resolve_smem_bytes(HM_MAX_FILTER_RADIUS, TH));
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resolve_kernel<TH, C, P>, kFwdThreads,
+                                                      resolve_smem_bytes(HM_MAX_FILTER_RADIUS, TH));
+        return (per_sm > 0 ? per_sm : 1) * num_sms();
+    });
+}
+
 template <int TH, bool C>
 static cudaError_t launch_resolve_t(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                                    const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status,
                                    cudaStream_t st, const CgbDev &cg, int *tile_list) {
     const int R = fp.enabled ? fp.radius : 0;
-    // per device: the kernel's shared-memory limit (an attribute of the
-    // current device) and the persistent tile grid that fits
-    static PerDevice<int> resident_tiles;
-    const int resident = resident_tiles.get([](int) {
-        cudaFuncSetAttribute(resolve_kernel<TH, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)resolve_smem_bytes(HM_MAX_FILTER_RADIUS, TH));
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resolve_kernel<TH, C>, kFwdThreads,
-                                                      resolve_smem_bytes(HM_MAX_FILTER_RADIUS, TH));
-        return (per_sm > 0 ? per_sm : 1) * num_sms();
-    });
     dim3 grid((cam.W + kFwdTileW - 1) / kFwdTileW, (cam.H + TH - 1) / TH);
     float4 *out = reinterpret_cast<float4 *>(rgba);
     if (!tile_list) {
-        resolve_kernel<TH, C><<<grid, kFwdThreads, resolve_smem_bytes(R, TH), st>>>(tab, cam, Ls, fp, vis_c, vis_a,
-                                                                                    out, status, cg, nullptr);
+        const int resident = resolve_resident<TH, C, false>();   // sets the shared-memory limit
+        (void)resident;
+        resolve_kernel<TH, C, false><<<grid, kFwdThreads, resolve_smem_bytes(R, TH), st>>>(
+            tab, cam, Ls, fp, vis_c, vis_a, out, status, cg, nullptr, nullptr, nullptr);
         return cudaGetLastError();
     }
     const int ntiles = (int)(grid.x * grid.y);
     cudaError_t e = launch_tile_list(vis_a, out, cam.W, cam.H, TH, tile_list, st);
     if (e != cudaSuccess) return e;
-    resolve_kernel<TH, C><<<resident < ntiles ? resident : ntiles, kFwdThreads, resolve_smem_bytes(R, TH), st>>>(
-        tab, cam, Ls, fp, vis_c, vis_a, out, status, cg, tile_list);
+    if (C) {
+        const int resident = resolve_resident<TH, C, false>();
+        resolve_kernel<TH, C, false><<<resident < ntiles ? resident : ntiles, kFwdThreads, resolve_smem_bytes(R, TH),
+                                       st>>>(tab, cam, Ls, fp, vis_c, vis_a, out, status, cg, tile_list, nullptr,
+                                             nullptr);
+        return cudaGetLastError();
+    }
+    // two passes: decode every key once, then filter the tiles
+    float4 *px_col = reinterpret_cast<float4 *>(reinterpret_cast<char *>(tile_list) +
+                                                resolve_list_bytes_aligned(cam.W, cam.H));
+    float4 *px_ts = px_col + (size_t)cam.W * cam.H;
+    const int dec_grid = num_sms() * 4 < ntiles * (TH / kDecRows) ? num_sms() * 4 : ntiles * (TH / kDecRows);
+    resolve_decode_kernel<TH><<<dec_grid, kDecThreads, 0, st>>>(tab, cam, Ls, fp, vis_c, vis_a, tile_list, px_col,
+                                                                 px_ts, status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int resident = resolve_resident<TH, false, true>();
+    resolve_kernel<TH, false, true><<<resident < ntiles ? resident : ntiles, kFwdThreads, resolve_smem_bytes(R, TH),
+                                      st>>>(tab, cam, Ls, fp, vis_c, vis_a, out, status, cg, tile_list, px_col, px_ts);
     return cudaGetLastError();
 }
 

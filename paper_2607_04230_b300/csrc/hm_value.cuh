@@ -173,16 +173,6 @@ __device__ __forceinline__ Recon reconstruct(const int *s_dg, const uint8_t *s_f
     return o;
 }
 
-// Straight-line reconstruction for a compile-time radius R (the dx loop is
-// unrolled, dy runs): every tap is evaluated with predication and no
-// divergent branch.  The weights are accumulated unscaled:
-//  - centre reference (kColor): the pixel itself contributes with exponent 0
-//    (zero offset, same depth, same colour) and every exponent is >= 0, so
-//    each weight is <= 1 and the sum is >= 1;
-//  - conservative reference: the sum is exact unless every weight is tiny;
-//    callers redo it with the online-rescaled reconstruct() when some
-//    neighbour contributes but W < 1e-20.
-// Staged pixels without a centre key must hold a finite colour (zero).
 // Strip hit counts H_center, H_cons of Sec. 3.3.3 over the window: taps
 // within the strip |d - (d.Ts) Ts| <= hw of the screen tangent (the pixel
 // alone for a degenerate tangent).  Only the taps that can be in the strip
@@ -245,51 +235,104 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// Bilateral reconstruction of one pixel with unscaled weights (straight-line
-// code for radius R).  The spatial exponent is written as
-// dpar^2 (1/s_par^2 - 1/s_perp^2) + |d|^2 / s_perp^2 (perp^2 = |d|^2 - dpar^2),
-// which with the isotropic coefficients (0, 1/s_iso^2) and a zero tangent is
-// the isotropic exponent, so one loop serves both modes; exponents are
-// scaled by log2(e) for ex2.  Empty centre-layer taps hold a large negative
-// depth, so the depth test alone rejects them.
+// Bilateral reconstruction of one pixel (Eq. 7).  The spatial exponent is
+// written as dpar^2 (1/s_par^2 - 1/s_perp^2) + |d|^2 / s_perp^2
+// (perp^2 = |d|^2 - dpar^2), which with the isotropic coefficients
+// (0, 1/s_iso^2) and a zero tangent is the isotropic exponent, so one loop
+// serves both modes; exponents are scaled by log2(e) for ex2.
+// The depth test |d_Q - ref| <= D_rej of Eq. 7's contributors (integer, one
+// shared-memory word per tap; empty centre-layer taps hold a large negative
+// depth, so the test alone rejects them) first builds a bit mask per window
+// row, then only the contributing taps are weighted and summed, in (dy, dx)
+// order: most windows hold few contributors (a sparse crowd's
+// centre-referenced windows about 2 of 121, a close-up's 12).
+//  - centre reference (kColor): the pixel itself contributes with exponent 0
+//    (zero offset, same depth, same colour) and every exponent is >= 0, so
+//    the weights are summed unscaled: each is <= 1 and the sum is >= 1;
+//  - conservative reference: the weights are summed unscaled too; when that
+//    sum underflows (every contributor far off the strand axis: W < 1e-20)
+//    they are summed again relative to the largest, exp(e_min - e) with
+//    e_min the smallest exponent of a contributor (m = e_min), so the sum is
+//    >= 1 however far off the axis the contributors lie.
 template <int R, bool kColor>
 __device__ __forceinline__ Recon reconstruct_fast(const uint8_t *s_fa, const float4 *s_col, int sw,
                                                   int lx, int ly, int ref, float tsx, float tsy, bool iso, float3 Cp,
                                                   const FilterDev &fp) {
     constexpr float kL2e = 1.4426950408889634f;
+    constexpr int D = 2 * R + 1;
     const float a = iso ? 0.0f : (fp.inv_spar2 - fp.inv_sperp2) * kL2e;
     const float b = (iso ? fp.inv_siso2 : fp.inv_sperp2) * kL2e;
     const float c = fp.inv_sc2 * kL2e;
     const float ux = iso ? 0.0f : tsx, uy = iso ? 0.0f : tsy;
-    float Sx = 0.f, Sy = 0.f, Sz = 0.f, Wt = 0.f;
+    // |dq - ref| <= drej  <=>  (unsigned)(dq - ref + drej) <= 2 drej (no
+    // overflow: depths are in [0, 2^24) or -2^30)
+    const int lo = fp.drej - ref;
+    const unsigned span = 2u * (unsigned)fp.drej;
+    const int base = (ly + R) * sw + lx + R;      // the pixel's own staged index
+    uint32_t mk[D];
     int cnt = 0;
-    for (int dy = -R; dy <= R; ++dy) {
-        const int row = (ly + dy + R) * sw + lx + R;
-        const float ypar = (float)dy * uy, yb = (float)(dy * dy) * b;   // per-row parts of dpar and |d|^2 b
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+        const int row = base + (r - R) * sw;
+        uint32_t m = 0;
 #pragma unroll
         for (int dx = -R; dx <= R; ++dx) {
-            const int idx = row + dx;
-            const float4 cq = s_col[idx];          // rgb, centre depth bits
-            const bool ok = abs(__float_as_int(cq.w) - ref) <= fp.drej;
-            cnt += ok ? 1 : 0;
-            const float dpar = fmaf((float)dx, ux, ypar);
-            float e = fmaf(dpar * a, dpar, fmaf((float)(dx * dx), b, yb));
-            if (kColor) {
-                const float ex = Cp.x - cq.x, ey = Cp.y - cq.y, ez = Cp.z - cq.z;
-                e = fmaf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)), c, e);
-            }
-            const float w = ok ? ex2_approx(-e) : 0.f;
-            Sx = fmaf(w, cq.x, Sx);
-            Sy = fmaf(w, cq.y, Sy);
-            Sz = fmaf(w, cq.z, Sz);
-            Wt += w;
+            const int dq = __float_as_int(s_col[row + dx].w);     // centre depth bits
+            m |= ((unsigned)(dq + lo) <= span ? 1u : 0u) << (dx + R);
         }
+        mk[r] = m;
+        cnt += __popc(m);
+    }
+    // exponent (log2 units) of contributor (dx, dy)
+    auto expo = [&](int dx, int dy, const float4 &cq) {
+        const float dpar = fmaf((float)dx, ux, (float)dy * uy);
+        float e = fmaf(dpar * a, dpar, fmaf((float)(dx * dx), b, (float)(dy * dy) * b));
+        if (kColor) {
+            const float ex = Cp.x - cq.x, ey = Cp.y - cq.y, ez = Cp.z - cq.z;
+            e = fmaf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)), c, e);
+        }
+        return e;
+    };
+    float Sx = 0.f, Sy = 0.f, Sz = 0.f, Wt = 0.f;
+    auto accumulate = [&](float emin) {
+        Sx = Sy = Sz = Wt = 0.f;
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            uint32_t m = mk[r];
+            while (m) {
+                const int k = __ffs(m) - 1;
+                m &= m - 1;
+                const int dx = k - R;
+                const float4 cq = s_col[base + (r - R) * sw + dx];
+                const float w = ex2_approx(emin - expo(dx, r - R, cq));
+                Sx = fmaf(w, cq.x, Sx);
+                Sy = fmaf(w, cq.y, Sy);
+                Sz = fmaf(w, cq.z, Sz);
+                Wt += w;
+            }
+        }
+    };
+    accumulate(0.0f);
+    float emin = 0.0f;
+    if (!kColor && cnt > 0 && Wt < 1e-20f) {
+        emin = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            uint32_t m = mk[r];
+            while (m) {
+                const int k = __ffs(m) - 1;
+                m &= m - 1;
+                const int dx = k - R;
+                emin = fminf(emin, expo(dx, r - R, s_col[base + (r - R) * sw + dx]));
+            }
+        }
+        accumulate(emin);
     }
     const int2 h = strip_counts(s_col, s_fa, sw, lx, ly, R, tsx, tsy, iso, fp);
     Recon o;
     o.S = make_float3(Sx, Sy, Sz);
     o.W = Wt;
-    o.m = 0.f;
+    o.m = emin * (1.0f / kL2e);   // natural-log units: max weight = exp(-m)
     o.cnt = cnt;
     o.hc = h.x;
     o.ha = h.y;

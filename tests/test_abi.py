@@ -213,14 +213,17 @@ def test_resolve_scratch_and_probe_arguments(L):
     pattern are rejected before anything is launched."""
     L.hm_resolve_scratch_bytes.restype = ctypes.c_size_t
     L.hm_resolve_scratch_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32]
-    assert L.hm_resolve_scratch_bytes(1920, 1080) == 4 * (2 + 2 * 60 * 68)
-    assert L.hm_resolve_scratch_bytes(33, 17) == 4 * (2 + 2 * 2 * 2)
+    # tile list (list, order, key counts of the 32 x 16 tiling), 16-byte
+    # aligned, then two float4 per pixel for the two-pass resolve
+    al = lambda b: (b + 15) // 16 * 16
+    assert L.hm_resolve_scratch_bytes(1920, 1080) == al(4 * (2 + 2 * 60 * 68)) + 32 * 1920 * 1080
+    assert L.hm_resolve_scratch_bytes(33, 17) == al(4 * (2 + 2 * 2 * 2)) + 32 * 33 * 17
     assert L.hm_resolve_scratch_bytes(0, 10) == 0 and L.hm_resolve_scratch_bytes(10, 16385) == 0
     # the adjoint's scratch: colour and screen-tangent gradients per pixel, then the same tile list
     L.hm_backward_scratch_bytes.restype = ctypes.c_size_t
     L.hm_backward_scratch_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32]
     for w, h in ((1920, 1080), (512, 512), (33, 17)):
-        assert L.hm_backward_scratch_bytes(w, h) == 32 * w * h + L.hm_resolve_scratch_bytes(w, h)
+        assert L.hm_backward_scratch_bytes(w, h) == 32 * w * h + 4 * (2 + 2 * ((w + 31) // 32) * ((h + 15) // 16))
     assert L.hm_backward_scratch_bytes(0, 10) == 0
     sc = synth.tiny_scene(0, num_strands=10)
     cam = hm.camera_struct(sc.camera)
@@ -228,8 +231,9 @@ def test_resolve_scratch_and_probe_arguments(L):
     grooms = (ctypes.c_void_p * 1)(1 << 20)
     lights = hm.lights_struct(sc.lights)
     f = hm.filter_struct(synth.FilterParams())
-    assert L.hm_resolve_shade(grooms, 1, ctypes.byref(cam), ctypes.byref(lights), ctypes.byref(f), fake, fake, fake,
-                              ctypes.c_void_p((1 << 20) + 2), None) == INVALID
+    for off in (2, 8):
+        assert L.hm_resolve_shade(grooms, 1, ctypes.byref(cam), ctypes.byref(lights), ctypes.byref(f), fake, fake,
+                                  fake, ctypes.c_void_p((1 << 20) + off), None) == INVALID
     for pattern in (-1, 3):
         assert L.hm_probe_atomic_min(fake, 16, 1, pattern, None) == INVALID
     assert L.hm_probe_atomic_min(fake, 0, 1, 0, None) == INVALID
