@@ -401,13 +401,13 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
     float3 *s_dC = reinterpret_cast<float3 *>(s_col + ns);
     uint16_t *s_list = reinterpret_cast<uint16_t *>(s_dC + ns);
     auto dg_at = [&](int i) { return __float_as_int(s_col[i].w); };
-    const int *s_dg = nullptr;            // the depth rides in s_col.w
     float2 *s_tsG = reinterpret_cast<float2 *>(
         (reinterpret_cast<uintptr_t>(s_list + ((ns + 7) & ~7)) + 15) & ~(uintptr_t)15);
     float2 *s_tsA = s_tsG + kResolveThreads;
     uint8_t *s_isoG = reinterpret_cast<uint8_t *>(s_tsA + kResolveThreads);
     uint8_t *s_isoA = s_isoG + kResolveThreads;
     uint8_t *s_fa = s_isoA + kResolveThreads;
+    int *s_dg = reinterpret_cast<int *>((reinterpret_cast<uintptr_t>(s_fa + ns) + 3) & ~(uintptr_t)3);  // centre depth
     __shared__ int s_count, s_nJA, s_nJG, s_tile;
     __shared__ float4 s_dTs[kResolveThreads];    // per tile pixel: d(screen tangent) of G (xy) and A (zw)
     __shared__ float s_gs[kResolveThreads];      // share of the pixel's gradient the centre reconstruction gets
@@ -452,6 +452,7 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
             fa = !key_empty(ka);
         }
         s_col[i] = make_float4(0.f, 0.f, 0.f, __int_as_float(dg));
+        s_dg[i] = dg;
         s_fa[i] = fa;
         s_dC[i] = f3(0.f, 0.f, 0.f);
     }
@@ -557,7 +558,7 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
         const float2 tsa = s_tsA[t];
         const bool isoA = s_isoA[t] != 0;
         const float3 z = f3(0.f, 0.f, 0.f);
-        Recon ra = reconstruct_fast_r<false>(R, s_fa, s_col, sw, jx, jy, dAq, tsa.x, tsa.y, isoA, z, fp);
+        Recon ra = reconstruct_fast_r<false>(R, s_dg, s_fa, s_col, sw, jx, jy, dAq, tsa.x, tsa.y, isoA, z, fp);
         if (ra.cnt > 0 && ra.W < 1e-20f)
             ra = reconstruct(s_dg, s_fa, s_col, sw, jx, jy, qx, qy, W, H, R, dAq, tsa.x, tsa.y, isoA, false, z, fp);
         if (dg_at(jm) >= 0 && ra.cnt > 0) {            // depth mismatch: split al / (1 - al)
@@ -595,7 +596,7 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
         const int dGq = __float_as_int(c4.w);
         const float2 ts = s_tsG[t];
         const bool isoG = s_isoG[t] != 0;
-        const Recon rg = reconstruct_fast_r<true>(R, s_fa, s_col, sw, jx, jy, dGq, ts.x, ts.y, isoG, Cp, fp);
+        const Recon rg = reconstruct_fast_r<true>(R, s_dg, s_fa, s_col, sw, jx, jy, dGq, ts.x, ts.y, isoG, Cp, fp);
         const float2 d = reconstruct_adjoint(s_dg, s_col, s_dC, sw, jx, jy, qx, qy, W, H, R, dGq, ts.x, ts.y, isoG,
                                              true, Cp, jm, rg, gG, fp);
         s_dTs[t].x = d.x;
@@ -768,7 +769,8 @@ size_t adjoint_smem_bytes(int radius) {
     b += sizeof(uint16_t) * ((ns + 7) & ~7) + 16;
     b += sizeof(float2) * 2 * kResolveThreads;
     b += 2 * kResolveThreads;
-    b += ns;
+    b += ns + 3;                      // s_fa, then the alignment of s_dg
+    b += sizeof(int) * ns;
     return (b + 15) & ~(size_t)15;
 }
 

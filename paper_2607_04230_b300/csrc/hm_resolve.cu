@@ -32,13 +32,13 @@ constexpr int kNoDepth = -(1 << 30);
 // Centre-referenced result of tile pixel (tx, ty): the normalized
 // reconstruction and alpha H_center / H_cons (Sec. 3.3), or the pixel's
 // own colour with alpha 1 when the filter is off.
-__device__ __forceinline__ float4 centre_result(int R, const uint8_t *s_fa, const float4 *s_col, int sw, int tx,
+__device__ __forceinline__ float4 centre_result(int R, const int *s_dg, const uint8_t *s_fa, const float4 *s_col, int sw, int tx,
                                                 int ty, float2 ts, bool iso, const FilterDev &fp) {
     const int mid = (ty + R) * sw + tx + R;
     const float4 c4 = s_col[mid];
     const float3 Cp = make_float3(c4.x, c4.y, c4.z);
     if (!fp.enabled) return make_float4(Cp.x, Cp.y, Cp.z, 1.0f);
-    const Recon rg = reconstruct_fast_r<true>(R, s_fa, s_col, sw, tx, ty, __float_as_int(c4.w), ts.x, ts.y, iso, Cp,
+    const Recon rg = reconstruct_fast_r<true>(R, s_dg, s_fa, s_col, sw, tx, ty, __float_as_int(c4.w), ts.x, ts.y, iso, Cp,
                                               fp);
     const float invW = 1.0f / rg.W;
     return make_float4(rg.S.x * invW, rg.S.y * invW, rg.S.z * invW, __fdiv_rn((float)rg.hc, (float)rg.ha));
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
     const int R = fp.enabled ? fp.radius : 0;
     const int sw = kFwdTileW + 2 * R, sh = kFwdTileH + 2 * R, ns = sw * sh;
     // shared layout: bases | s_col[ns] (rgb + centre depth bits) | s_list[ns] | s_lg[tile] |
-    // s_lb[tile] | s_out[tile] | s_outA[tile] | s_ts[tile] | s_flag[tile] | s_fa[ns]
+    // s_lb[tile] | s_out[tile] | s_outA[tile] | s_ts[tile] | s_flag[tile] | s_fa[ns] | s_dg[ns]
     uint64_t *s_bases = reinterpret_cast<uint64_t *>(smem);
     float4 *s_col = reinterpret_cast<float4 *>(
         (reinterpret_cast<uintptr_t>(s_bases + HM_MAX_GROOMS_PER_CALL + 1) + 15) & ~(uintptr_t)15);  // 16-byte loads
@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
     float2 *s_ts = reinterpret_cast<float2 *>(s_outA + kFwdTilePx);  // G screen tangent
     uint8_t *s_flag = reinterpret_cast<uint8_t *>(s_ts + kFwdTilePx); // bit0 isoG, bit1 isoA, bit2 needs A
     uint8_t *s_fa = s_flag + kFwdTilePx;
+    int *s_dg = reinterpret_cast<int *>((reinterpret_cast<uintptr_t>(s_fa + ns) + 3) & ~(uintptr_t)3);  // centre depth
     __shared__ int s_count, s_ng, s_nb, s_tile;
 
     const int tid = threadIdx.x, lane = tid & 31;
@@ -308,10 +309,12 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
             }
             fa = !key_empty(ka);
             s_fa[i] = fa;
+            s_dg[i] = dg;
             s_col[i] = make_float4(c.x, c.y, c.z, __int_as_float(dg));
             continue;
         }
         s_fa[i] = fa;
+        s_dg[i] = dg;
         s_col[i] = make_float4(0.f, 0.f, 0.f, __int_as_float(dg));
     }
     for (int t = tid; t < kFwdTilePx; t += kFwdThreads) s_flag[t] = 3;
@@ -419,7 +422,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
         if (li < ng) {
             const int t = s_lg[li];
             const int tx = t % kFwdTileW, ty = t / kFwdTileW;
-            s_out[t] = centre_result(R, s_fa, s_col, sw, tx, ty, s_ts[t], (s_flag[t] & 1) != 0, fp);
+            s_out[t] = centre_result(R, s_dg, s_fa, s_col, sw, tx, ty, s_ts[t], (s_flag[t] & 1) != 0, fp);
         } else {
             const int t = s_list[li - ng];
             const int tx = t % kFwdTileW, ty = t / kFwdTileW;
@@ -445,7 +448,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
             }
             const int dA = (int)(ka >> 40);
             const float3 z = make_float3(0.f, 0.f, 0.f);
-            Recon ra = reconstruct_fast_r<false>(R, s_fa, s_col, sw, tx, ty, dA, tsx, tsy, iso, z, fp);
+            Recon ra = reconstruct_fast_r<false>(R, s_dg, s_fa, s_col, sw, tx, ty, dA, tsx, tsy, iso, z, fp);
             if (ra.cnt > 0 && ra.W < 1e-20f)
                 ra = reconstruct(static_cast<const int *>(nullptr), s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA,
                                  tsx, tsy, iso, false, z, fp);
@@ -473,7 +476,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
     for (int li = tid; li < nb; li += kFwdThreads) {
         const int t = s_lb[li];
         const int tx = t % kFwdTileW, ty = t / kFwdTileW;
-        const float4 cg = centre_result(R, s_fa, s_col, sw, tx, ty, s_ts[t], (s_flag[t] & 1) != 0, fp);
+        const float4 cg = centre_result(R, s_dg, s_fa, s_col, sw, tx, ty, s_ts[t], (s_flag[t] & 1) != 0, fp);
         const float4 a = s_outA[t];
         float3 c = make_float3(cg.x, cg.y, cg.z);
         if (a.w >= 0.0f) {
@@ -573,7 +576,8 @@ size_t resolve_smem_bytes(int radius, int tile_h) {
     b += 2 * sizeof(float4) * tile_px;
     b += sizeof(float2) * tile_px;
     b += tile_px;
-    b += ns;
+    b += ns + 3;                      // s_fa, then the alignment of s_dg
+    b += sizeof(int) * ns;
     return (b + 15) & ~(size_t)15;
 }
 

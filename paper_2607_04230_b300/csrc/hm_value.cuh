@@ -182,12 +182,12 @@ __device__ __forceinline__ Recon reconstruct(const int *s_dg, const uint8_t *s_f
 // k slope + hw sqrt(2) + 0.01] are candidates (0.01 px covers the binary32
 // rounding of slope and of the test); each candidate then takes the exact
 // test of in_strip, so the counts equal a full-window scan.
-__device__ __forceinline__ int2 strip_counts(const float4 *s_col, const uint8_t *s_fa, int sw, int lx, int ly, int R,
+__device__ __forceinline__ int2 strip_counts(const int *s_dg, const uint8_t *s_fa, int sw, int lx, int ly, int R,
                                              float tsx, float tsy, bool iso, const FilterDev &fp) {
     int hc = 0, ha = 0;
     if (iso) {
         const int idx = (ly + R) * sw + lx + R;
-        return make_int2(__float_as_int(s_col[idx].w) >= 0 ? 1 : 0, s_fa[idx] ? 1 : 0);
+        return make_int2(s_dg[idx] >= 0 ? 1 : 0, s_fa[idx] ? 1 : 0);
     }
     const bool xmaj = fabsf(tsx) >= fabsf(tsy);
     const float slope = xmaj ? tsy / tsx : tsx / tsy;
@@ -208,7 +208,7 @@ __device__ __forceinline__ int2 strip_counts(const float4 *s_col, const uint8_t 
                 float dpar, perp2;
                 const bool in = cand && in_strip(false, tsx, tsy, dx, dy, fp.hw2, dpar, perp2);
                 const int idx = (ly + dy + R) * sw + lx + dx + R;
-                hc += (in && __float_as_int(s_col[idx].w) >= 0) ? 1 : 0;
+                hc += (in && s_dg[idx] >= 0) ? 1 : 0;
                 ha += (in && s_fa[idx]) ? 1 : 0;
             }
         }
@@ -222,7 +222,7 @@ __device__ __forceinline__ int2 strip_counts(const float4 *s_col, const uint8_t 
             float dpar, perp2;
             if (!in_strip(false, tsx, tsy, dx, dy, fp.hw2, dpar, perp2)) continue;
             const int idx = (ly + dy + R) * sw + lx + dx + R;
-            hc += __float_as_int(s_col[idx].w) >= 0 ? 1 : 0;
+            hc += s_dg[idx] >= 0 ? 1 : 0;
             ha += s_fa[idx] ? 1 : 0;
         }
     }
@@ -240,9 +240,10 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // (perp^2 = |d|^2 - dpar^2), which with the isotropic coefficients
 // (0, 1/s_iso^2) and a zero tangent is the isotropic exponent, so one loop
 // serves both modes; exponents are scaled by log2(e) for ex2.
-// The depth test |d_Q - ref| <= D_rej of Eq. 7's contributors (integer, one
-// shared-memory word per tap; empty centre-layer taps hold a large negative
-// depth, so the test alone rejects them) first builds a bit mask per window
+// The depth test |d_Q - ref| <= D_rej of Eq. 7's contributors (integer, on
+// the staged centre depths s_dg, one 4-byte word per tap so a warp's loads
+// hit distinct banks; empty centre-layer taps hold a large negative depth, so
+// the test alone rejects them) first builds a bit mask per window
 // row, then only the contributing taps are weighted and summed, in (dy, dx)
 // order: most windows hold few contributors (a sparse crowd's
 // centre-referenced windows about 2 of 121, a close-up's 12).
@@ -255,7 +256,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 //    e_min the smallest exponent of a contributor (m = e_min), so the sum is
 //    >= 1 however far off the axis the contributors lie.
 template <int R, bool kColor>
-__device__ __forceinline__ Recon reconstruct_fast(const uint8_t *s_fa, const float4 *s_col, int sw,
+__device__ __forceinline__ Recon reconstruct_fast(const int *s_dg, const uint8_t *s_fa, const float4 *s_col, int sw,
                                                   int lx, int ly, int ref, float tsx, float tsy, bool iso, float3 Cp,
                                                   const FilterDev &fp) {
     constexpr float kL2e = 1.4426950408889634f;
@@ -277,7 +278,7 @@ __device__ __forceinline__ Recon reconstruct_fast(const uint8_t *s_fa, const flo
         uint32_t m = 0;
 #pragma unroll
         for (int dx = -R; dx <= R; ++dx) {
-            const int dq = __float_as_int(s_col[row + dx].w);     // centre depth bits
+            const int dq = s_dg[row + dx];                          // staged centre depth
             m |= ((unsigned)(dq + lo) <= span ? 1u : 0u) << (dx + R);
         }
         mk[r] = m;
@@ -328,7 +329,7 @@ __device__ __forceinline__ Recon reconstruct_fast(const uint8_t *s_fa, const flo
         }
         accumulate(emin);
     }
-    const int2 h = strip_counts(s_col, s_fa, sw, lx, ly, R, tsx, tsy, iso, fp);
+    const int2 h = strip_counts(s_dg, s_fa, sw, lx, ly, R, tsx, tsy, iso, fp);
     Recon o;
     o.S = make_float3(Sx, Sy, Sz);
     o.W = Wt;
@@ -341,15 +342,15 @@ __device__ __forceinline__ Recon reconstruct_fast(const uint8_t *s_fa, const flo
 
 // reconstruct_fast<R, kColor> for a runtime radius 0..HM_MAX_FILTER_RADIUS.
 template <bool kColor>
-__device__ __forceinline__ Recon reconstruct_fast_r(int R, const uint8_t *s_fa, const float4 *s_col,
+__device__ __forceinline__ Recon reconstruct_fast_r(int R, const int *s_dg, const uint8_t *s_fa, const float4 *s_col,
                                                     int sw, int lx, int ly, int ref, float tsx, float tsy, bool iso,
                                                     float3 Cp, const FilterDev &fp) {
     switch (R) {
 #define HM_RF(r) \
-    case r: return reconstruct_fast<r, kColor>(s_fa, s_col, sw, lx, ly, ref, tsx, tsy, iso, Cp, fp);
+    case r: return reconstruct_fast<r, kColor>(s_dg, s_fa, s_col, sw, lx, ly, ref, tsx, tsy, iso, Cp, fp);
         HM_RF(0) HM_RF(1) HM_RF(2) HM_RF(3) HM_RF(4) HM_RF(5) HM_RF(6) HM_RF(7)
 #undef HM_RF
-        default: return reconstruct_fast<8, kColor>(s_fa, s_col, sw, lx, ly, ref, tsx, tsy, iso, Cp, fp);
+        default: return reconstruct_fast<8, kColor>(s_dg, s_fa, s_col, sw, lx, ly, ref, tsx, tsy, iso, Cp, fp);
     }
 }
 
