@@ -51,6 +51,29 @@ __global__ void __launch_bounds__(256) clear_kernel(ulonglong2 *vis_c, ulonglong
     }
 }
 
+// Adds the block's per-thread counters v[0..K) to dst[0..K) with one atomic
+// per counter per block (warp shuffles, then shared memory), so the frame's
+// thousands of warps do not queue on the same few addresses at the end of a
+// pass.  Block-wide (every thread calls it); NT = blockDim.x.
+template <int NT, int K>
+__device__ __forceinline__ void block_add_counters(unsigned long long (&v)[K], unsigned long long *const (&dst)[K]) {
+    __shared__ unsigned long long s_red[NT / 32][K];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(kFull, v[k], o);
+        if (lane == 0) s_red[w][k] = v[k];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < K) {
+        unsigned long long t = 0;
+#pragma unroll
+        for (int i = 0; i < NT / 32; ++i) t += s_red[i][threadIdx.x];
+        if (t) atomicAdd(dst[threadIdx.x], t);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // LOD pre-pass (Sec. 3.2, Eqs. 1-5): one thread per bundle, one CTA per groom
 // ---------------------------------------------------------------------------
@@ -170,17 +193,11 @@ __global__ void __launch_bounds__(kLodSelThreads) lod_select_kernel(CallTable ta
         segs = nseg;
     }
     if (stats) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            strands += __shfl_down_sync(kFull, strands, o);
-            segs += __shfl_down_sync(kFull, segs, o);
-            culled += __shfl_down_sync(kFull, culled, o);
-        }
-        if ((threadIdx.x & 31) == 0 && (strands | segs | culled)) {
-            atomicAdd((unsigned long long *)&stats->strands, strands);
-            atomicAdd((unsigned long long *)&stats->segments, segs);
-            atomicAdd((unsigned long long *)&stats->bundles_culled, culled);
-        }
+        unsigned long long v[3] = {strands, segs, culled};
+        unsigned long long *const dst[3] = {(unsigned long long *)&stats->strands,
+                                            (unsigned long long *)&stats->segments,
+                                            (unsigned long long *)&stats->bundles_culled};
+        block_add_counters<kLodSelThreads, 3>(v, dst);
     }
 }
 
@@ -244,6 +261,24 @@ __global__ void __launch_bounds__(kLodScanThreads) lod_scan_kernel(CallTable tab
     }
 }
 
+// s_goff[0..n] = the exclusive prefix of the call's per-groom batch counts
+// (written by the LOD pass): one thread loads each count (independent
+// global loads, instead of one thread chaining n of them), then one thread
+// sums them in shared memory.  Block-wide; blockDim >= HM_MAX_GROOMS_PER_CALL.
+__device__ __forceinline__ void groom_batch_offsets(const CallTable &tab, uint32_t *s_goff) {
+    if ((int)threadIdx.x < tab.n) s_goff[threadIdx.x + 1] = tab.g[threadIdx.x].counters[kCtrBatches];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        s_goff[0] = 0;
+        for (int i = 1; i <= tab.n; ++i) {
+            acc += s_goff[i];
+            s_goff[i] = acc;
+        }
+    }
+    __syncthreads();
+}
+
 // Segment `seg` (0 <= seg < drawn segments of the groom) of the batch whose
 // first segment lies in bundle f0: its bundle f, strand s and segment j.
 // Groom of work batch b: the last groom whose first batch is <= b (goff
@@ -299,6 +334,7 @@ struct __align__(16) SegRec {
 static_assert(sizeof(SegRec) == 96, "SegRec is read as six 16-byte words");
 
 constexpr int kRasterThreads = 256;
+static_assert(kRasterThreads >= HM_MAX_GROOMS_PER_CALL, "one thread per groom in the prologue");
 constexpr int kRasterWarps = kRasterThreads / 32;
 
 // Candidate pixels of one work item: the minor-axis pixels of major-axis
@@ -384,15 +420,7 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
     constexpr bool kMulti = kMode == 1, kCgb = kMode == 2;
     __shared__ uint32_t s_goff[HM_MAX_GROOMS_PER_CALL + 1];
     __shared__ SegRec s_rec[kRasterWarps][32];
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0;
-        for (int i = 0; i < tab.n; ++i) {
-            s_goff[i] = acc;
-            acc += tab.g[i].counters[kCtrBatches];
-        }
-        s_goff[tab.n] = acc;
-    }
-    __syncthreads();
+    groom_batch_offsets(tab, s_goff);
     const uint32_t total = s_goff[tab.n];
     const int lane = threadIdx.x & 31;
     SegRec *rec = s_rec[threadIdx.x >> 5];
@@ -508,16 +536,10 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
         }   // views
     }
     if (stats) {
-        unsigned long long a = n_cons, c = n_cen;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_down_sync(kFull, a, o);
-            c += __shfl_down_sync(kFull, c, o);
-        }
-        if (lane == 0) {
-            atomicAdd((unsigned long long *)&stats->covered_cons, a);
-            atomicAdd((unsigned long long *)&stats->covered_center, c);
-        }
+        unsigned long long v[2] = {n_cons, n_cen};
+        unsigned long long *const dst[2] = {(unsigned long long *)&stats->covered_cons,
+                                            (unsigned long long *)&stats->covered_center};
+        block_add_counters<kRasterThreads, 2>(v, dst);
     }
 }
 
@@ -598,15 +620,7 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_msaa_kernel(CallTabl
                                                                         hm_frame_stats *stats) {
     __shared__ uint32_t s_goff[HM_MAX_GROOMS_PER_CALL + 1];
     __shared__ SegRec s_rec[kRasterWarps][32];
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0;
-        for (int i = 0; i < tab.n; ++i) {
-            s_goff[i] = acc;
-            acc += tab.g[i].counters[kCtrBatches];
-        }
-        s_goff[tab.n] = acc;
-    }
-    __syncthreads();
+    groom_batch_offsets(tab, s_goff);
     const uint32_t total = s_goff[tab.n];
     const int lane = threadIdx.x & 31;
     SegRec *rec = s_rec[threadIdx.x >> 5];
@@ -697,10 +711,9 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_msaa_kernel(CallTabl
         __syncwarp();
     }
     if (stats) {
-        unsigned long long a = n_hits;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(kFull, a, o);
-        if (lane == 0) atomicAdd((unsigned long long *)&stats->covered_center, a);
+        unsigned long long v[1] = {n_hits};
+        unsigned long long *const dst[1] = {(unsigned long long *)&stats->covered_center};
+        block_add_counters<kRasterThreads, 1>(v, dst);
     }
 }
 
