@@ -9,11 +9,13 @@ from paper_2607_04230_b300 import synth
 RGBA_TOL = 1e-4          # max abs error of linear RGB(A) vs the FP64 oracle
 
 
-def gpu_frame(scene, grooms=None):
+def gpu_frame(scene, grooms=None, tile_list=False):
+    """tile_list: resolve with the tile-list scratch (the two-pass resolve the
+    benchmark times) instead of one CTA per tile."""
     import torch
     from paper_2607_04230_b300 import hm
     grooms = grooms or hm.upload_scene(scene)
-    frame = hm.Frame(scene.camera.width, scene.camera.height)
+    frame = hm.Frame(scene.camera.width, scene.camera.height, tile_list=tile_list)
     hm.render(grooms, scene, frame)
     torch.cuda.synchronize()
     hm.get_device_status()
@@ -55,11 +57,24 @@ def assert_rgba_close(gpu_rgba, ref_rgba, pixels, tol=RGBA_TOL):
     return float(err.max())
 
 
-def check_full(scene, sample=None, rng_seed=0):
+def special_pixels(scene, vc, va):
+    """Every pixel whose output is not a plain centre-referenced
+    reconstruction: promoted pixels (a conservative key, no centre key) and
+    depth mismatches (Sec. 3.3.2), in ascending order."""
+    e = oracle.PAYLOAD_MASK
+    eG, eA = (vc & e) == e, (va & e) == e
+    dG = (vc >> np.uint64(40)).astype(np.int64)
+    dA = (va >> np.uint64(40)).astype(np.int64)
+    _, mis = oracle.depth_thresholds(scene.camera, scene.filt)
+    return np.nonzero(~eA & (eG | (dA + mis <= dG)))[0]
+
+
+def check_full(scene, sample=None, rng_seed=0, all_special=False, tile_list=False):
     """Keys bit-exact over the whole frame, LOD exact, RGBA within tolerance
-    on every covered pixel (or a seeded sample of `sample` covered pixels plus
-    every uncovered pixel check)."""
-    out = gpu_frame(scene)
+    on every covered pixel (or a seeded sample of `sample` covered pixels,
+    plus, with all_special, every promoted and depth-mismatch pixel), and
+    every uncovered pixel exactly zero."""
+    out = gpu_frame(scene, tile_list=tile_list)
     lods, vc, va, counts = oracle_keys(scene)
     for (n, c), (gn, gc) in zip(lods, out["lods"]):
         assert np.array_equal(n, gn), "N_LOD differs"
@@ -73,6 +88,8 @@ def check_full(scene, sample=None, rng_seed=0):
     if sample is not None and covered.size > sample:
         rng = np.random.default_rng(rng_seed)
         pix = np.sort(rng.choice(covered, size=sample, replace=False))
+        if all_special:
+            pix = np.union1d(pix, special_pixels(scene, vc, va))
     ref, pix = oracle_rgba(scene, lods, vc, va, pixels=pix)
     err = assert_rgba_close(out["rgba"], ref, pix)
     # every pixel outside the conservative layer is exactly zero
