@@ -236,11 +236,18 @@ def measured_peaks():
 
 # Sources each profiled kernel is compiled from: a committed ncu figure
 # stays valid while these files are unchanged.
+_RESOLVE_SRC = ["csrc/hm_resolve.cu", "csrc/hm_value.cuh", "csrc/hm_device.cuh", "csrc/hm_kernels.h", "../include/hm.h"]
+_ADJOINT_SRC = ["csrc/hm_backward.cu", "csrc/hm_value.cuh", "csrc/hm_device.cuh", "csrc/hm_kernels.h", "../include/hm.h"]
 KERNEL_SOURCES = {
     "raster_kernel": ["csrc/hm_render.cu", "csrc/hm_device.cuh", "csrc/hm_kernels.h", "../include/hm.h"],
-    "resolve_kernel": ["csrc/hm_resolve.cu", "csrc/hm_value.cuh", "csrc/hm_device.cuh", "csrc/hm_kernels.h",
-                       "../include/hm.h"],
+    "resolve_kernel": _RESOLVE_SRC, "resolve_tiles_kernel": _RESOLVE_SRC, "resolve_order_kernel": _RESOLVE_SRC,
+    "resolve_decode_kernel": _RESOLVE_SRC,
+    "resolve_adjoint_kernel": _ADJOINT_SRC, "geometry_adjoint_kernel": _ADJOINT_SRC,
 }
+# the kernels of the resolve call with the tile list (the benchmark's frames)
+RESOLVE_PHASE_KERNELS = ("resolve_tiles_kernel", "resolve_order_kernel", "resolve_decode_kernel", "resolve_kernel")
+ADJOINT_PHASE_KERNELS = ("resolve_tiles_kernel", "resolve_order_kernel", "resolve_adjoint_kernel",
+                         "geometry_adjoint_kernel")
 
 
 def kernel_src_hash(kernel: str):
@@ -251,18 +258,39 @@ def kernel_src_hash(kernel: str):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, workload: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
-    None when it was taken on other kernel sources or another workload."""
+def ncu_entry(kernel: str, workload: str, key: str | None = None):
+    """The committed ncu counters of one launch of `kernel` on `workload`
+    (profiles/), or None when they were taken on other kernel sources (the
+    counters of a changed kernel are not used)."""
     try:
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
-    e = t.get(workload, {}).get(kernel)
+    e = t.get(workload, {}).get(key or kernel)
     if not e or kernel not in KERNEL_SOURCES or e.get("src_hash") != kernel_src_hash(kernel):
         return None
-    return e.get("dram_bytes_per_launch")
+    return e
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes of `kernel` (ncu), or None."""
+    e = ncu_entry(kernel, workload)
+    return e and e.get("dram_bytes_per_launch")
+
+
+def ncu_phase(kernels, workload: str):
+    """Summed ncu counters of one launch of each of `kernels` (one call's
+    passes), or None when any is missing or stale."""
+    tot = {"dram_bytes_per_launch": 0.0, "warp_inst_per_launch": 0.0, "fp32_flop_per_launch": 0.0,
+           "xu_warp_inst_per_launch": 0.0}
+    for k in kernels:
+        e = ncu_entry(k, workload)
+        if e is None:
+            return None
+        for f in tot:
+            tot[f] += e.get(f, 0.0)
+    return tot
 
 
 # L2 sectors (32 B) one 64-bit atomicMin of each probe pattern touches:
@@ -293,32 +321,26 @@ def probe_atomic_peak(torch, hm, n_elems, rounds=32):
     return best
 
 
-def ncu_warp_inst(kernel: str, workload: str):
-    """Warp instructions one launch of `kernel` issues (ncu, same kernel
-    sources and workload), else None."""
-    try:
-        with open(TRAFFIC_FILE) as f:
-            t = json.load(f)
-    except (OSError, ValueError):
+def alu_views(counters, t_s: float, clk, sms: int):
+    """Issue and FP32 views of a pass from its ncu counters and its
+    event-timed duration t_s: warp instructions against one per cycle per SM
+    sub-partition (sms x 4 x the sampled SM clock), FP32 operations (FFMA
+    counted as 2, the paired FFMA2 as 4) against sms x 128 FP32 lanes x 2 x
+    the clock."""
+    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz")
+    if counters is None or not mhz or t_s <= 0:
         return None
-    e = t.get(workload, {}).get(kernel)
-    if not e or kernel not in KERNEL_SOURCES or e.get("src_hash") != kernel_src_hash(kernel):
-        return None
-    return e.get("warp_inst_per_launch")
-
-
-def ncu_red_sectors_per_atomic(workload: str):
-    """L2 RED sectors per 64-bit atomicMin of the raster kernel from the
-    committed ncu summary (same kernel sources), else None."""
-    try:
-        with open(TRAFFIC_FILE) as f:
-            t = json.load(f)
-    except (OSError, ValueError):
-        return None
-    e = t.get(workload, {}).get("raster_kernel")
-    if not e or e.get("src_hash") != kernel_src_hash("raster_kernel"):
-        return None
-    return e.get("red_sectors_per_atomic")
+    hz = float(mhz) * 1e6
+    issue_peak = sms * 4 * hz
+    fp32_peak = sms * 128 * 2 * hz
+    wi, fl = counters["warp_inst_per_launch"], counters["fp32_flop_per_launch"]
+    return {"issue": {"achieved": wi / t_s / 1e9, "peak": issue_peak / 1e9, "unit": "G warp instructions/s",
+                      "frac": wi / t_s / issue_peak, "warp_inst_per_launch": wi,
+                      "peak_source": f"{sms} SMs x 4 issue slots x {float(mhz):.0f} MHz (sampled)"},
+            "fp32": {"achieved": fl / t_s / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s (FP32, executed)",
+                     "frac": fl / t_s / fp32_peak, "flop_per_launch": fl,
+                     "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {float(mhz):.0f} MHz (sampled)"},
+            "traffic": counters["dram_bytes_per_launch"]}
 
 
 # ---------------------------------------------------------------------------
@@ -641,10 +663,28 @@ def run_grad(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clk = clocks.stop()
     hm.get_device_status()
-    f_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
-    b_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    f_ms = statistics.median(e[0].elapsed_time(e[1]) for e in evs)
+    b_ms = statistics.median(e[1].elapsed_time(e[2]) for e in evs)
     if rank != 0:
         return 0
+    # issue-slot and FP32 views of the adjoint (its kernels' ncu counters over
+    # its event time) and of the forward (raster + one-CTA-per-tile resolve)
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    bwd = alu_views(ncu_phase(ADJOINT_PHASE_KERNELS, "grad_512"), b_ms * 1e-3, clk, sms)
+    fr, fs = ncu_entry("raster_kernel", "grad_512"), ncu_entry("resolve_kernel", "grad_512", "resolve_kernel_per_tile")
+    fwd = None
+    if fr and fs:
+        fwd = alu_views({k: fr.get(k, 0.0) + fs.get(k, 0.0) for k in ("dram_bytes_per_launch", "warp_inst_per_launch",
+                                                                     "fp32_flop_per_launch", "xu_warp_inst_per_launch")},
+                        f_ms * 1e-3, clk, sms)
+    roofline = None
+    if bwd:
+        i = bwd["issue"]
+        roofline = {"bound": "alu", "achieved": i["achieved"], "peak": i["peak"], "unit": i["unit"], "frac": i["frac"],
+                    "traffic": bwd["traffic"], "kernel": "adjoint (" + ", ".join(ADJOINT_PHASE_KERNELS) + ")",
+                    "peak_source": i["peak_source"],
+                    "work_per_launch": f"{i['warp_inst_per_launch']:.0f} warp instructions (ncu) per adjoint",
+                    "fp32": bwd["fp32"]}
     line = {"metric": METRIC, "value": segs / ((f_ms + b_ms) * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": f_ms + b_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
@@ -652,6 +692,7 @@ def run_grad(args, rank, world, local_rank):
                                    "triangles, 6 layers, 20k strands x 12 segments",
                        "l2": "flushed between timed steps (256 MiB write)"},
             "forward_ms": f_ms, "backward_ms": b_ms, "gradient_steps_per_s": 1e3 / (f_ms + b_ms),
+            "roofline": roofline, "forward_views": fwd, "backward_views": bwd,
             "gpu_launches": (LAUNCHES_PER_FRAME + 5) * args.steps, "clocks": clk}   # + zero fill, tile-list count and order, two adjoint passes
     print(json.dumps(line), flush=True)
     return 0
@@ -841,7 +882,8 @@ def frame_roofline(atomics, phase_ms, W, H, peak_rates, workload, clk, sms):
     # operations (a 64-bit atomicMin updates one 32-byte sector; atomics of
     # one instruction that share a sector share the operation)
     sector_peak = max(r * PROBE_SECTORS_PER_ATOMIC[p] for p, r in peak_rates.items())
-    spa = ncu_red_sectors_per_atomic(workload)
+    re = ncu_entry("raster_kernel", workload)
+    spa = re["red_sectors"] / atomics if re and re.get("red_sectors") and atomics else None
     spa_note = "ncu-measured" if spa is not None else "assumed one per atomic (no ncu summary for these sources)"
     spa = spa if spa is not None else 1.0
     t_r = phase_ms["raster"] * 1e-3
@@ -856,18 +898,16 @@ def frame_roofline(atomics, phase_ms, W, H, peak_rates, workload, clk, sms):
         "resolve_kernel": {"bound": "hbm", "achieved": res_bytes / t_s / 1e9, "peak": hbm, "unit": "GB/s",
                            "ms": phase_ms["resolve"], "work": f"{res_bytes} B per launch (32 B/px)"},
     }
-    # instruction-issue view (both kernels issue-heavy): warp instructions
-    # per launch (ncu) / event time, against one warp instruction per cycle
-    # per SM sub-partition (4 per SM) at the sampled SM clock
-    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz")
-    for kname, tk in (("raster_kernel", t_r), ("resolve_kernel", t_s)):
-        wi = ncu_warp_inst(kname, workload)
-        if wi is not None and mhz:
-            peak_issue = sms * 4 * float(mhz) * 1e6
-            kernels[kname]["issue"] = {"achieved": wi / tk / 1e9, "peak": peak_issue / 1e9,
-                                       "unit": "G warp instructions/s", "frac": wi / tk / peak_issue,
-                                       "warp_inst_per_launch": wi,
-                                       "peak_source": f"{sms} SMs x 4 issue slots x {float(mhz):.0f} MHz (sampled)"}
+    # instruction-issue and FP32 views (ncu counters of the same sources and
+    # workload over the event-timed passes): the raster kernel, and the
+    # resolve call's kernels (tile count, order, decode, filter) together
+    rv = alu_views(ncu_phase(("raster_kernel",), workload), t_r, clk, sms)
+    if rv:
+        kernels["raster_kernel"].update(issue=rv["issue"], fp32=rv["fp32"])
+    sv = alu_views(ncu_phase(RESOLVE_PHASE_KERNELS, workload), t_s, clk, sms)
+    if sv:
+        kernels["resolve_kernel"].update(issue=sv["issue"], fp32=sv["fp32"], traffic=sv["traffic"],
+                                         kernels=list(RESOLVE_PHASE_KERNELS))
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     d = kernels[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],

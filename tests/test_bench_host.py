@@ -41,14 +41,24 @@ def test_cpu_baseline_whole_small_workload():
 def test_traffic_record_follows_kernel_sources(tmp_path, monkeypatch):
     import bench
     h = bench.kernel_src_hash("raster_kernel")
-    assert h == bench.kernel_src_hash("raster_kernel") and h != bench.kernel_src_hash("resolve_kernel")
-    rec = {"single_1080p": {"raster_kernel": {"dram_bytes_per_launch": 123.0, "red_sectors_per_atomic": 0.9,
+    hr = bench.kernel_src_hash("resolve_kernel")
+    assert h == bench.kernel_src_hash("raster_kernel") and h != hr
+    rec = {"single_1080p": {"raster_kernel": {"dram_bytes_per_launch": 123.0, "red_sectors": 90.0,
+                                              "warp_inst_per_launch": 10.0, "fp32_flop_per_launch": 4.0,
                                               "src_hash": h},
-                            "resolve_kernel": {"dram_bytes_per_launch": 456.0, "src_hash": "stale"}}}
+                            "resolve_kernel": {"dram_bytes_per_launch": 456.0, "src_hash": "stale"},
+                            "resolve_tiles_kernel": {"dram_bytes_per_launch": 1.0, "warp_inst_per_launch": 2.0,
+                                                     "src_hash": hr}}}
     f = tmp_path / "traffic.json"
     f.write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
     assert bench.ncu_traffic("raster_kernel", "single_1080p") == 123.0
-    assert bench.ncu_red_sectors_per_atomic("single_1080p") == 0.9
+    assert bench.ncu_entry("raster_kernel", "single_1080p")["red_sectors"] == 90.0
     assert bench.ncu_traffic("resolve_kernel", "single_1080p") is None     # taken on other sources
     assert bench.ncu_traffic("raster_kernel", "crowd_4k") is None          # other workload
+    # a pass's counters need every kernel's record on the current sources
+    assert bench.ncu_phase(("raster_kernel",), "single_1080p")["warp_inst_per_launch"] == 10.0
+    assert bench.ncu_phase(("resolve_tiles_kernel", "resolve_kernel"), "single_1080p") is None
+    v = bench.alu_views(bench.ncu_phase(("raster_kernel",), "single_1080p"), 1e-6, {"sm_mhz": 2000.0}, 148)
+    assert abs(v["issue"]["frac"] - 10.0 / 1e-6 / (148 * 4 * 2e9)) < 1e-12
+    assert abs(v["fp32"]["frac"] - 4.0 / 1e-6 / (148 * 128 * 2 * 2e9)) < 1e-12
