@@ -558,9 +558,7 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
         const float2 tsa = s_tsA[t];
         const bool isoA = s_isoA[t] != 0;
         const float3 z = f3(0.f, 0.f, 0.f);
-        Recon ra = reconstruct_fast_r<false>(R, s_dg, s_fa, s_col, sw, jx, jy, dAq, tsa.x, tsa.y, isoA, z, fp);
-        if (ra.cnt > 0 && ra.W < 1e-20f)
-            ra = reconstruct(s_dg, s_fa, s_col, sw, jx, jy, qx, qy, W, H, R, dAq, tsa.x, tsa.y, isoA, false, z, fp);
+        const Recon ra = reconstruct_fast_r<false>(R, s_dg, s_fa, s_col, sw, jx, jy, dAq, tsa.x, tsa.y, isoA, z, fp);
         if (dg_at(jm) >= 0 && ra.cnt > 0) {            // depth mismatch: split al / (1 - al)
             const float al = (float)ra.hc / (float)ra.ha;
             gA = mul3(gA, al);

@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
     uint8_t *s_flag = reinterpret_cast<uint8_t *>(s_ts + kFwdTilePx); // bit0 isoG, bit1 isoA, bit2 needs A
     uint8_t *s_fa = s_flag + kFwdTilePx;
     int *s_dg = reinterpret_cast<int *>((reinterpret_cast<uintptr_t>(s_fa + ns) + 3) & ~(uintptr_t)3);  // centre depth
-    __shared__ int s_count, s_ng, s_nb, s_tile;
+    __shared__ int s_count, s_ng, s_nb, s_tile, s_jobs;
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int W = cam.W, H = cam.H;
@@ -253,6 +253,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
         s_count = 0;
         s_ng = 0;
         s_nb = 0;
+        s_jobs = 0;
     }
     int tile;
     if (list) {
@@ -418,7 +419,14 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
     // all carry a centre key: most mismatches in dense hair) the result is
     // R_A with alpha 1 and the centre reconstruction is not needed; the
     // others go to a second list.
-    for (int li = tid; li < ng + nA; li += kFwdThreads) {
+    // warps claim the jobs 32 at a time from a shared counter, so a warp
+    // whose jobs were short takes more instead of waiting at the barrier
+    for (;;) {
+        int li = 0;
+        if (lane == 0) li = atomicAdd(&s_jobs, 32);
+        li = __shfl_sync(0xFFFFFFFFu, li, 0) + lane;
+        if (li - lane >= ng + nA) break;
+        if (li >= ng + nA) continue;
         if (li < ng) {
             const int t = s_lg[li];
             const int tx = t % kFwdTileW, ty = t / kFwdTileW;
@@ -448,10 +456,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
             }
             const int dA = (int)(ka >> 40);
             const float3 z = make_float3(0.f, 0.f, 0.f);
-            Recon ra = reconstruct_fast_r<false>(R, s_dg, s_fa, s_col, sw, tx, ty, dA, tsx, tsy, iso, z, fp);
-            if (ra.cnt > 0 && ra.W < 1e-20f)
-                ra = reconstruct(static_cast<const int *>(nullptr), s_fa, s_col, sw, tx, ty, gx, gy, W, H, R, dA,
-                                 tsx, tsy, iso, false, z, fp);
+            const Recon ra = reconstruct_fast_r<false>(R, s_dg, s_fa, s_col, sw, tx, ty, dA, tsx, tsy, iso, z, fp);
             float4 oa = make_float4(0.f, 0.f, 0.f, -1.0f);   // no contributor
             if (ra.cnt > 0) {
                 const float iw = 1.0f / ra.W;

@@ -108,70 +108,10 @@ __device__ __forceinline__ float weight_exponent(bool iso, int dx, int dy, float
     return e;
 }
 
-// Normalized bilateral sum around tile pixel (lx, ly) against reference depth
-// `ref`, screen tangent (tsx, tsy) / iso, with or without the colour term
-// (Eqs. 6-7), plus the strip hit counts of Sec. 3.3.3.  The weights are
-// accumulated relative to the largest one seen so far (online rescaling),
-// so tiny weights far off the strand axis never underflow the normalizer.
 // Staged centre-layer depth of tap i: a separate int array, or the depth
 // bits packed into the colour record's w.
 __device__ __forceinline__ int tap_depth(const int *s_dg, const float3 *, int i) { return s_dg[i]; }
 __device__ __forceinline__ int tap_depth(const int *, const float4 *s_col, int i) { return __float_as_int(s_col[i].w); }
-
-template <typename ColT>
-__device__ __forceinline__ Recon reconstruct(const int *s_dg, const uint8_t *s_fa, const ColT *s_col, int sw,
-                                             int lx, int ly, int gx, int gy, int W, int H, int R, int ref, float tsx,
-                                             float tsy, bool iso, bool use_color, float3 Cp, const FilterDev &fp) {
-    Recon o;
-    o.S = make_float3(0.f, 0.f, 0.f);
-    o.W = 0.f;
-    o.m = 0.f;
-    o.cnt = 0;
-    o.hc = 0;
-    o.ha = 0;
-    // Staged pixels outside the screen hold neither layer (s_dg < 0,
-    // s_fa = 0), so skipping empty taps also clips the window to the screen.
-    for (int dy = -R; dy <= R; ++dy) {
-        const int row = (ly + dy + R) * sw + R + lx;
-        for (int dx = -R; dx <= R; ++dx) {
-            const int idx = row + dx;
-            const int dq = tap_depth(s_dg, s_col, idx);
-            const int fa = s_fa[idx];
-            if (dq < 0 && fa == 0) continue;
-            float dpar, perp2;
-            const bool strip = in_strip(iso, tsx, tsy, dx, dy, fp.hw2, dpar, perp2);
-            const bool gq = dq >= 0;
-            if (strip) {
-                o.hc += gq;
-                o.ha += fa;
-            }
-            if (gq && abs(dq - ref) <= fp.drej) {
-                const float3 cq = make_float3(s_col[idx].x, s_col[idx].y, s_col[idx].z);
-                const float e = weight_exponent(iso, dx, dy, dpar, perp2, use_color, Cp, cq, fp);
-                if (o.cnt == 0) {
-                    o.m = e;
-                    o.S = cq;
-                    o.W = 1.0f;
-                } else if (e >= o.m) {
-                    const float w = __expf(o.m - e);
-                    o.S.x += w * cq.x;
-                    o.S.y += w * cq.y;
-                    o.S.z += w * cq.z;
-                    o.W += w;
-                } else {
-                    const float sc = __expf(e - o.m);
-                    o.S.x = o.S.x * sc + cq.x;
-                    o.S.y = o.S.y * sc + cq.y;
-                    o.S.z = o.S.z * sc + cq.z;
-                    o.W = o.W * sc + 1.0f;
-                    o.m = e;
-                }
-                o.cnt += 1;
-            }
-        }
-    }
-    return o;
-}
 
 // Strip hit counts H_center, H_cons of Sec. 3.3.3 over the window: taps
 // within the strip |d - (d.Ts) Ts| <= hw of the screen tangent (the pixel
