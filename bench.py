@@ -1097,15 +1097,19 @@ def run_native(args, rank, world, local_rank):
         h2d = sum(t.numel() * 4 for t in h_lv)
         d2h = h_rgba2[0].numel() * 4
         e2e_steps = max(10, args.steps // 4)
-        comp, copy_s = torch.cuda.current_stream(), torch.cuda.Stream()
+        # the read-back is split over two copy streams (two halves of the image),
+        # which the copy engines serve in parallel
+        comp, copy_ss = torch.cuda.current_stream(), [torch.cuda.Stream(), torch.cuda.Stream()]
+        halves = [slice(0, H // 2), slice(H // 2, H)]
         done = [torch.cuda.Event() for _ in range(e2e_steps + 3)]
-        copied = [torch.cuda.Event() for _ in range(e2e_steps + 3)]
+        copied = [[torch.cuda.Event() for _ in copy_ss] for _ in range(e2e_steps + 3)]
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for k in range(e2e_steps + 3):
             if k == 3:
                 t0.record(comp)
             if k >= 2:
-                comp.wait_event(copied[k - 2])          # rgba2[k % 2] has been read back
+                for ev in copied[k - 2]:                # rgba2[k % 2] has been read back
+                    comp.wait_event(ev)
             flush.fill_(k)
             for hg, h, d in zip(grooms, h_lv, d_lv):
                 d.copy_(h, non_blocking=True)
@@ -1114,17 +1118,37 @@ def run_native(args, rank, world, local_rank):
             hm.resolve_shade(grooms, scene.camera, scene.lights, scene.filt, frame.vis_center, frame.vis_cons,
                              rgba2[k % 2], tile_scratch=frame.tile_scratch)
             done[k].record(comp)
-            copy_s.wait_event(done[k])
-            with torch.cuda.stream(copy_s):
-                h_rgba2[k % 2].copy_(rgba2[k % 2], non_blocking=True)
-            copied[k].record(copy_s)
-        comp.wait_event(copied[e2e_steps + 2])
+            for cs, half, ev in zip(copy_ss, halves, copied[k]):
+                cs.wait_event(done[k])
+                with torch.cuda.stream(cs):
+                    h_rgba2[k % 2][half].copy_(rgba2[k % 2][half], non_blocking=True)
+                ev.record(cs)
+        for ev in copied[e2e_steps + 2]:
+            comp.wait_event(ev)
         t1.record(comp)
         torch.cuda.synchronize()
         te = max_over_ranks(t0.elapsed_time(t1) * 1e-3, world)
+        # the device -> host link alone: the same two-half read-back with
+        # nothing else running (best of 5), the floor of the e2e step
+        link = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(comp)
+            for cs in copy_ss:
+                cs.wait_event(a)
+            for cs, half in zip(copy_ss, halves):
+                with torch.cuda.stream(cs):
+                    h_rgba2[0][half].copy_(rgba2[0][half], non_blocking=True)
+            for cs in copy_ss:
+                comp.wait_stream(cs)
+            b.record(comp)
+            b.synchronize()
+            link.append(a.elapsed_time(b) * 1e-3)
         e2e = {"value": job_throughput(segs, e2e_steps, world, te), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": te / e2e_steps * 1e3,
-               "pipeline": "read-back of frame k on a copy stream overlaps frame k+1; L2 flushes inside the span"}
+               "d2h_alone_ms": min(link) * 1e3, "d2h_link_gbs": d2h / min(link) / 1e9,
+               "pipeline": "read-back of frame k (two halves on two copy streams) overlaps frame k+1; L2 flushes "
+                           "inside the span"}
 
     if rank != 0:
         return 0
