@@ -430,13 +430,36 @@ hm_status hm_get_device_status(void *stream);
  *   raster_ctas_per_sm persistent rasterizer CTAs per SM, 0 = as many as fit
  *   resolve_tile_h     16 or 32: resolve tiles of 32 x tile_h pixels
  *                      (default 32)
+ *   raster_bin_w       0: the direct rasterizer (global atomicMin per
+ *                      covered pixel, default).  16 or 32: the screen-tile
+ *                      binned rasterizer (segments binned to tiles of
+ *                      raster_bin_w x raster_bin_h pixels, shared-memory
+ *                      atomicMin per tile, one coalesced global atomicMin per
+ *                      touched key and chunk) for single-view renders with
+ *                      the ID payload; multiview, compressed, multisample
+ *                      and shadow-map renders keep the direct rasterizer.
+ *                      Its workspace (about 88 B per segment at full detail
+ *                      of the call's grooms, plus 12 B per tile) belongs to
+ *                      the call's first groom, is allocated on first use and
+ *                      grown by later calls, which then synchronize the
+ *                      device; a call that must grow it during CUDA stream
+ *                      capture returns HM_ERR_CAPACITY (render once outside
+ *                      the capture).  A frame whose segment-tile pairs
+ *                      exceed 8 per segment sets device status bit 4
+ *                      (hm_get_device_status) and its keys are incomplete.
+ *   raster_bin_h       16 or 32 when raster_bin_w != 0, else 0
+ *   raster_bin_chunk   256 or 1024 segments per unit of the binned tile
+ *                      pass when raster_bin_w != 0, else 0
  * Not thread-safe against concurrent render calls on other host threads. */
 typedef struct {
     int32_t raster_precheck;
     int32_t raster_min_blocks;
     int32_t raster_ctas_per_sm;
     int32_t resolve_tile_h;
-    int32_t reserved[4];
+    int32_t raster_bin_w;
+    int32_t raster_bin_h;
+    int32_t raster_bin_chunk;
+    int32_t reserved;
 } hm_tuning;
 
 hm_status hm_set_tuning(const hm_tuning *t);

@@ -1,12 +1,13 @@
 """Autotuner for the launch shapes of the rasterizer and the resolve.
 
-Searches the hm_tuning space (read-before-atomic on/off, the rasterizer's
-register budget, persistent rasterizer CTAs per SM, resolve tile height) by
-timing whole frames of the caller's own workload with CUDA events, keeps the
-fastest, and can cache the choice in a JSON file keyed by the workload's
-signature (GPU, resolution, groom count, segments per frame).  The knobs never
-change results: visibility is bit-identical and colours identical under
-every setting.
+Searches the hm_tuning space by timing whole frames of the caller's own
+workload with CUDA events: for the direct rasterizer, read-before-atomic
+on/off, its register budget and persistent CTAs per SM; the screen-tile
+binned rasterizer with its bin (tile) sizes and chunk sizes; and the resolve
+tile height.  It keeps the fastest and can cache the choice in a JSON file
+keyed by the workload's signature (GPU, resolution, groom count, segments per
+frame).  The knobs never change results: visibility is bit-identical and
+colours identical under every setting.
 """
 from __future__ import annotations
 
@@ -18,12 +19,19 @@ import statistics
 from . import hm
 
 
+DIRECT = {"raster_bin_w": 0, "raster_bin_h": 0, "raster_bin_chunk": 0}
+
+
 def candidates():
     out = []
     for pre, mb, th in itertools.product((0, 1), (3, 4), (16, 32)):
         for cps in ((2, 0) if mb == 3 else (2, 3, 0)):
-            out.append({"raster_precheck": pre, "raster_min_blocks": mb, "raster_ctas_per_sm": cps,
-                        "resolve_tile_h": th})
+            out.append(dict({"raster_precheck": pre, "raster_min_blocks": mb, "raster_ctas_per_sm": cps,
+                             "resolve_tile_h": th}, **DIRECT))
+    # the binned rasterizer: bin sizes and chunk sizes (its other knobs fixed)
+    for bw, bh, chunk in itertools.product((16, 32), (16, 32), (256, 1024)):
+        out.append({"raster_precheck": 0, "raster_min_blocks": 4, "raster_ctas_per_sm": 0, "resolve_tile_h": 32,
+                    "raster_bin_w": bw, "raster_bin_h": bh, "raster_bin_chunk": chunk})
     return out
 
 

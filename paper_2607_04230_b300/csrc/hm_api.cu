@@ -42,6 +42,10 @@ struct hm_groom_s {
     // LOD state of the last camera render and the current layer vertices
     float4 *d_segpts;
     bool segpts_valid;
+    // workspace of the binned rasterizer when this groom is the first of a
+    // call (grown on demand), or null
+    void *d_bin_ws;
+    size_t bin_ws_bytes;
 };
 
 namespace {
@@ -190,6 +194,7 @@ void free_groom(hm_groom g) {
     cudaFree(g->d_batch_map_full);
     cudaFree(g->d_counters_full);
     cudaFree(g->d_uv);
+    cudaFree(g->d_bin_ws);
     delete g;
 }
 
@@ -203,12 +208,16 @@ void phase(int i, cudaStream_t s) {
 // Defaults: plain atomics (on B300 the read-before-atomic variant is slower:
 // 1.28 vs 1.07 ms per 1080p frame), the 64-register raster, as many raster
 // CTAs per SM as fit, 32x32 resolve tiles.
-hm_tuning g_tuning = {0, 4, 0, 32, 0, 0, 0, 0};
+hm_tuning g_tuning = {0, 4, 0, 32, 0, 0, 0, 0};   // direct rasterizer
 
 bool valid_tuning(const hm_tuning &t) {
+    const bool direct = t.raster_bin_w == 0 && t.raster_bin_h == 0 && t.raster_bin_chunk == 0;
+    const bool binned = (t.raster_bin_w == 16 || t.raster_bin_w == 32) &&
+                        (t.raster_bin_h == 16 || t.raster_bin_h == 32) &&
+                        (t.raster_bin_chunk == 256 || t.raster_bin_chunk == 1024);
     return (t.raster_precheck == 0 || t.raster_precheck == 1) &&
            (t.raster_min_blocks == 3 || t.raster_min_blocks == 4) && t.raster_ctas_per_sm >= 0 &&
-           t.raster_ctas_per_sm <= 32 && (t.resolve_tile_h == 16 || t.resolve_tile_h == 32);
+           t.raster_ctas_per_sm <= 32 && (t.resolve_tile_h == 16 || t.resolve_tile_h == 32) && (direct || binned);
 }
 
 }  // namespace
@@ -409,6 +418,31 @@ hm_status hm_render_visibility(const hm_groom *grooms, int32_t n, const hm_camer
                                       stream);
 }
 
+// The binned rasterizer's workspace for a call whose first groom is
+// `owner`: kept in the groom and grown when a call needs more (after a device
+// synchronize, since earlier frames may still use it); never grown during
+// stream capture.
+static hm_status bin_workspace(hm_groom owner, size_t need, cudaStream_t s, void **ws) {
+    if (need == 0) return fail(HM_ERR_CAPACITY, "binned rasterizer: too many segments for its 32-bit pair list");
+    if (owner->bin_ws_bytes < need) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        HM_CUDA(cudaStreamIsCapturing(s, &cs), "capture status");
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(HM_ERR_CAPACITY, "binned rasterizer workspace must grow: render once outside stream capture");
+        HM_CUDA(cudaDeviceSynchronize(), "sync before growing the binned workspace");
+        cudaFree(owner->d_bin_ws);
+        owner->d_bin_ws = nullptr;
+        owner->bin_ws_bytes = 0;
+        char *p = nullptr;
+        hm_status st = dev_alloc(&p, need, "binned rasterizer workspace");
+        if (st != HM_OK) return st;
+        owner->d_bin_ws = p;
+        owner->bin_ws_bytes = need;
+    }
+    *ws = owner->d_bin_ws;
+    return HM_OK;
+}
+
 static hm_status render_views(const hm_groom *grooms, int32_t n, int32_t first, int32_t count, const hm_camera *cams,
                                int32_t n_views, uint64_t *const *d_vis_center, uint64_t *const *d_vis_cons,
                                const uint32_t *const *d_scene_d24, int32_t clear, hm_frame_stats *d_stats,
@@ -450,6 +484,20 @@ static hm_status render_views(const hm_groom *grooms, int32_t n, int32_t first, 
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t npx = (int64_t)cams[0].width * cams[0].height;
+    const bool binned = g_tuning.raster_bin_w != 0 && n_views == 1 && !compressed;
+    void *bin_ws = nullptr;
+    uint64_t bin_slots = 0;
+    uint32_t *sw = nullptr;
+    if (binned) {
+        for (int i = 0; i < count; ++i) bin_slots += (uint64_t)tab.g[i].max_batches * hm::kSegBatch;
+        st = bin_workspace(grooms[first],
+                           hm::binned_workspace_bytes(bin_slots, cams[0].width, cams[0].height, g_tuning.raster_bin_w,
+                                                      g_tuning.raster_bin_h),
+                           s, &bin_ws);
+        if (st != HM_OK) return st;
+        sw = status_word();
+        if (!sw) return fail(HM_ERR_CUDA, "device status word unavailable");
+    }
     phase(0, s);
     for (int v = 0; v < n_views; ++v)
         HM_CUDA(hm::launch_clear(d_vis_center[v], d_vis_cons[v], npx, d_scene_d24 ? d_scene_d24[v] : nullptr, clear,
@@ -459,9 +507,15 @@ static hm_status render_views(const hm_groom *grooms, int32_t n, int32_t first, 
     for (int i = 0; i < count; ++i) grooms[first + i]->segpts_valid = false;   // until the raster has rewritten them
     HM_CUDA(hm::launch_lod(tab, views.cam[0], d_stats, s), "lod");
     phase(2, s);
-    HM_CUDA(hm::launch_raster(tab, views, g_tuning.raster_precheck != 0, g_tuning.raster_min_blocks,
-                              g_tuning.raster_ctas_per_sm, d_stats, s, compressed),
-            "raster");
+    if (binned)
+        HM_CUDA(hm::launch_raster_binned(tab, views.cam[0], d_vis_center[0], d_vis_cons[0], bin_ws, bin_slots,
+                                         g_tuning.raster_bin_w, g_tuning.raster_bin_h, g_tuning.raster_bin_chunk, sw,
+                                         d_stats, s),
+                "raster binned");
+    else
+        HM_CUDA(hm::launch_raster(tab, views, g_tuning.raster_precheck != 0, g_tuning.raster_min_blocks,
+                                  g_tuning.raster_ctas_per_sm, d_stats, s, compressed),
+                "raster");
     phase(3, s);
     for (int i = 0; i < count; ++i) grooms[first + i]->segpts_valid = true;
     return HM_OK;

@@ -26,7 +26,7 @@ constexpr int kSegBatch = 32;                      // segments per warp batch
 enum CounterWord : int { kCtrBatches = 0, kCtrTicket = 1, kCtrSegs = 2, kCtrWords = 4 };
 
 // Device status bits (read by hm_get_device_status).
-enum StatusBit : uint32_t { kStatusBadKey = 1u, kStatusBadBatch = 2u };
+enum StatusBit : uint32_t { kStatusBadKey = 1u, kStatusBadBatch = 2u, kStatusBinOverflow = 4u };
 
 // One groom as the kernels see it.  Arrays are device memory owned by the
 // groom handle.

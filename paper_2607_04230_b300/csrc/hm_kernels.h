@@ -83,6 +83,16 @@ cudaError_t launch_clear(uint64_t *vis_c, uint64_t *vis_a, int64_t npx, const ui
 cudaError_t launch_lod(const CallTable &tab, const CamDev &cam, hm_frame_stats *stats, cudaStream_t st);
 cudaError_t launch_raster(const CallTable &tab, const ViewSet &views, bool precheck, int min_blocks, int ctas_per_sm,
                           hm_frame_stats *stats, cudaStream_t st, bool compressed = false);
+// Screen-tile binned rasterizer (the alternative to launch_raster for one
+// view with the ID payload): bytes of its workspace for `slots` segment slots
+// (32 per work batch of the call's grooms at full detail) at W x H with
+// tile_w x tile_h tiles, 0 if out of range; the launch (after the clear and
+// the LOD pass, like launch_raster).  tile_w, tile_h in {16, 32}, chunk in
+// {256, 1024} segments per unit of the tile pass.
+size_t binned_workspace_bytes(uint64_t slots, int W, int H, int tile_w, int tile_h);
+cudaError_t launch_raster_binned(const CallTable &tab, const CamDev &cam, uint64_t *vis_c, uint64_t *vis_a, void *ws,
+                                 uint64_t slots, int tile_w, int tile_h, int chunk, uint32_t *status,
+                                 hm_frame_stats *stats, cudaStream_t st);
 cudaError_t launch_probe_atomic_min(uint64_t *buf, int64_t n, int rounds, int pattern, cudaStream_t st);
 cudaError_t launch_resolve(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                            const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status, int tile_h,

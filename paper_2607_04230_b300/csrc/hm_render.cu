@@ -8,10 +8,9 @@
 
 #include "hm_device.cuh"
 #include "hm_kernels.h"
+#include "hm_raster.cuh"
 
 namespace hm {
-
-constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // ---------------------------------------------------------------------------
 // clear: both layers to EMPTY or to the scene-depth pre-fill; zero the stats
@@ -48,29 +47,6 @@ __global__ void __launch_bounds__(256) clear_kernel(ulonglong2 *vis_c, ulonglong
         }
         vis_c[i] = v;
         if (vis_a != vis_c) vis_a[i] = v;
-    }
-}
-
-// Adds the block's per-thread counters v[0..K) to dst[0..K) with one atomic
-// per counter per block (warp shuffles, then shared memory), so the frame's
-// thousands of warps do not queue on the same few addresses at the end of a
-// pass.  Block-wide (every thread calls it); NT = blockDim.x.
-template <int NT, int K>
-__device__ __forceinline__ void block_add_counters(unsigned long long (&v)[K], unsigned long long *const (&dst)[K]) {
-    __shared__ unsigned long long s_red[NT / 32][K];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(kFull, v[k], o);
-        if (lane == 0) s_red[w][k] = v[k];
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < K) {
-        unsigned long long t = 0;
-#pragma unroll
-        for (int i = 0; i < NT / 32; ++i) t += s_red[i][threadIdx.x];
-        if (t) atomicAdd(dst[threadIdx.x], t);
     }
 }
 
@@ -261,49 +237,6 @@ __global__ void __launch_bounds__(kLodScanThreads) lod_scan_kernel(CallTable tab
     }
 }
 
-// s_goff[0..n] = the exclusive prefix of the call's per-groom batch counts
-// (written by the LOD pass): one thread loads each count (independent
-// global loads, instead of one thread chaining n of them), then one thread
-// sums them in shared memory.  Block-wide; blockDim >= HM_MAX_GROOMS_PER_CALL.
-__device__ __forceinline__ void groom_batch_offsets(const CallTable &tab, uint32_t *s_goff) {
-    if ((int)threadIdx.x < tab.n) s_goff[threadIdx.x + 1] = tab.g[threadIdx.x].counters[kCtrBatches];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0;
-        s_goff[0] = 0;
-        for (int i = 1; i <= tab.n; ++i) {
-            acc += s_goff[i];
-            s_goff[i] = acc;
-        }
-    }
-    __syncthreads();
-}
-
-// Segment `seg` (0 <= seg < drawn segments of the groom) of the batch whose
-// first segment lies in bundle f0: its bundle f, strand s and segment j.
-// Groom of work batch b: the last groom whose first batch is <= b (goff
-// holds the n + 1 prefix batch counts, so grooms without batches are passed
-// over); a binary search, as a crowd call holds up to 64 grooms.
-__device__ __forceinline__ int batch_groom(const uint32_t *goff, int n, uint32_t b) {
-    int lo = 0, hi = n;          // goff[lo] <= b < goff[n]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (goff[mid] <= b) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ void batch_segment(const GroomDev &g, uint32_t f0, uint32_t seg, uint32_t &f, int64_t &s,
-                                              int &j, int &C) {
-    f = f0;
-    while (f + 1 < (uint32_t)g.F && g.lod[f + 1].z <= seg) ++f;
-    const uint4 lo = g.lod[f];
-    C = (int)lo.y;
-    const uint32_t sl = seg - lo.z;
-    s = (int64_t)__ldg(&g.faces[f]).w + sl / (uint32_t)(C - 1);
-    j = (int)(sl % (uint32_t)(C - 1));
-}
-
 // ---------------------------------------------------------------------------
 // rasterizer (Sec. 3.1.1 strand assembly, Sec. 3.1.2 atomicMin visibility,
 // Sec. 3.3 two layers)
@@ -315,103 +248,6 @@ __device__ __forceinline__ void batch_segment(const GroomDev &g, uint32_t f0, ui
 // by a prefix sum, and each item tests its 2-4 minor-axis pixels with the
 // exact predicate and issues the 64-bit atomicMin for each layer.
 // ---------------------------------------------------------------------------
-struct __align__(16) SegRec {
-    int32_t uA, vA;              // start point in the major (u) / minor (v) frame, 1/256 px
-    int32_t du, dv;              // B - A in that frame
-    int32_t umin, umax, vmin, vmax;
-    float zA, dz;                // linear depth at A, zB - zA
-    float fden;                  // float(|B - A|^2), the depth parameter's denominator
-    float slope;                 // dv / du (0 for a point)
-    int32_t hc;                  // centre-sample half-width, 1/256 px
-    int32_t ilo;                 // first major pixel index
-    int32_t start;               // first work item of this segment
-    int32_t flags;               // bit0: u is x; bit1: short (32-bit arithmetic)
-    uint32_t id_lo, id_hi;       // payload strand << 7 | segment; compressed: j, C - 1
-    uint32_t cgb_hi;             // compressed: payload bits 39..12 (tangent, u, v) >> 12
-    float aoA, dao;              // compressed: AO at A, AO(B) - AO(A)
-    uint32_t pad_[3];            // 96 bytes: read back with 16-byte loads
-};
-static_assert(sizeof(SegRec) == 96, "SegRec is read as six 16-byte words");
-
-constexpr int kRasterThreads = 256;
-static_assert(kRasterThreads >= HM_MAX_GROOMS_PER_CALL, "one thread per groom in the prologue");
-constexpr int kRasterWarps = kRasterThreads / 32;
-
-// Candidate pixels of one work item: the minor-axis pixels of major-axis
-// pixel i whose conservative box can meet the segment.  The exact
-// predicate (bounding boxes overlap and the box's corners are not all
-// strictly on one side of the line) is evaluated in incremental form: the
-// corner cross products are e0 + h (sy dU - sx dV) for sx, sy = +-1, with e0 =
-// dU (cv - vA) - dV (cu - uA) the cross product at the box centre (the x/y one
-// up to sign), so "min <= 0 <= max" is |e0| <= h (|dU| + |dV|); e0 and the
-// depth numerator num = (cu - uA) dU + (cv - vA) dV change by constants from
-// one pixel to the next along the minor axis.  For short segments (|dU|,
-// |dV| < 2^14) every quantity fits in 32 bits; long ones use 64 bits.
-// Low 40 bits of a compressed key at projection parameter t.
-__device__ __forceinline__ uint64_t compressed_payload(const SegRec &q, float t) {
-    const float w = fdiv(fadd(__uint2float_rn(q.id_lo), t), __uint2float_rn(q.id_hi));
-    const uint32_t cw = quantize(w, 63.0f, 63u);
-    const uint32_t ca = quantize(fadd(q.aoA, fmul(q.dao, t)), 62.0f, 62u);
-    return ((uint64_t)q.cgb_hi << 12) | (uint64_t)((cw << 6) | ca);
-}
-
-template <typename I, bool kPrecheck, bool kCgb>
-__device__ __forceinline__ void raster_item(const SegRec &q_shared, int i, int W, int H,
-                                            uint64_t *__restrict__ vis_c, uint64_t *__restrict__ vis_a,
-                                            uint32_t &n_cons, uint32_t &n_cen) {
-    const SegRec q = q_shared;
-    const bool xm = q.flags & 1;
-    const int32_t ua = max(256 * i, q.umin), ub = min(256 * i + 256, q.umax);
-    const float va = (float)(ua - q.uA) * q.slope, vb = (float)(ub - q.uA) * q.slope;
-    const float flo = floorf(fminf(va, vb)), fhi = ceilf(fmaxf(va, vb));
-    // float error of the minor range is below |dV| 2^-21 + 1 unit; with
-    // |vA| <= 2^28 (guard band) and |slope| <= 1 every term fits 32 bits
-    const int32_t slack = 8 + (abs(q.dv) >> 20);
-    const int32_t vlo = q.vA + (int32_t)flo - slack;
-    const int32_t vhi = q.vA + (int32_t)fhi + slack;
-    const int dimv = xm ? H : W;
-    // rows whose conservative box can meet the line, and whose box overlaps
-    // the segment's minor extent: vmin <= 256 m + 256 and vmax >= 256 m
-    const int mlo = max(max(((vlo + 255) >> 8) - 1, (q.vmin - 1) >> 8), 0);
-    const int mhi = min(min(vhi >> 8, q.vmax >> 8), dimv - 1);
-    if (mlo > mhi) return;
-    const int32_t cu = 256 * i + 128;
-    const I ru = (I)(cu - q.uA), rv = (I)(256 * mlo + 128 - q.vA);
-    const I du = q.du, dv = q.dv;
-    I e0 = du * rv - dv * ru;
-    I num = ru * du + rv * dv;
-    const I de = du * 256, dn = dv * 256;
-    const I span = (I)abs(q.du) + (I)abs(q.dv);
-    const I k_cons = span * 128, k_cen = span * (I)q.hc;
-    const bool ucen = (q.umin <= cu + q.hc) && (q.umax >= cu - q.hc);
-    const uint64_t id = ((uint64_t)q.id_hi << 32) | q.id_lo;
-    const bool degenerate = (q.du == 0 && q.dv == 0);
-    typedef typename std::make_unsigned<I>::type U;
-    for (int m = mlo; m <= mhi; ++m, e0 += de, num += dn) {
-        const int32_t cv = 256 * m + 128;
-        // conservative line test |e0| <= k_cons (the overlaps hold by the row range)
-        if ((U)(e0 + k_cons) > (U)(2 * k_cons)) continue;
-        const bool cen = ucen && q.vmin <= cv + q.hc && q.vmax >= cv - q.hc && (U)(e0 + k_cen) <= (U)(2 * k_cen);
-        float t = 0.0f;
-        if (!degenerate) {
-            const float fn = sizeof(I) == 4 ? __int2float_rn((int32_t)num) : __ll2float_rn((int64_t)num);
-            t = fclamp(fdiv(fn, q.fden), 0.0f, 1.0f);
-        }
-        const float z = fclamp(fadd(q.zA, fmul(q.dz, t)), 0.0f, 1.0f);
-        uint32_t d24 = (uint32_t)floorf(fmul(z, 16777216.0f));
-        d24 = d24 > 16777215u ? 16777215u : d24;
-        const uint64_t key = ((uint64_t)d24 << 40) | (kCgb ? compressed_payload(q, t) : id);
-        const int px = xm ? i : m, py = xm ? m : i;
-        const uint32_t p = (uint32_t)py * (uint32_t)W + (uint32_t)px;   // < 2^28 pixels
-        n_cons += 1;
-        n_cen += cen;
-        if (!kPrecheck || key < __ldcg(reinterpret_cast<const unsigned long long *>(vis_a + p)))
-            atomicMin(reinterpret_cast<unsigned long long *>(vis_a + p), (unsigned long long)key);
-        if (cen && (!kPrecheck || key < __ldcg(reinterpret_cast<const unsigned long long *>(vis_c + p))))
-            atomicMin(reinterpret_cast<unsigned long long *>(vis_c + p), (unsigned long long)key);
-    }
-}
-
 // kMode: 0 one view, 1 several views (strands assembled once), 2 one view
 // with the compressed payload.
 template <bool kPrecheck, int kMinBlocks, int kMode>
@@ -458,28 +294,13 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
         const int n_views = kMulti ? views.n : 1;
         for (int view = 0; view < n_views; ++view) {
         const CamDev &cam = views.cam[view];
-        uint64_t *__restrict__ vis_c = views.vis_c[view];
-        uint64_t *__restrict__ vis_a = views.vis_a[view];
         SegRec r;
         int nmaj = 0;
         if (active) {
             const Proj A = project(cam, cp[0]);
             const Proj B = project(cam, cp[1]);
             if (A.valid && B.valid) {
-                const bool xm = abs(B.X - A.X) >= abs(B.Y - A.Y);
-                const int32_t uA = xm ? A.X : A.Y, vA = xm ? A.Y : A.X;
-                const int32_t uB = xm ? B.X : B.Y, vB = xm ? B.Y : B.X;
-                r.uA = uA;
-                r.vA = vA;
-                r.du = uB - uA;
-                r.dv = vB - vA;
-                r.umin = min(uA, uB);
-                r.umax = max(uA, uB);
-                r.vmin = min(vA, vB);
-                r.vmax = max(vA, vB);
-                r.zA = A.z;
-                r.dz = fsub(B.z, A.z);
-                r.hc = centre_halfwidth(cam, g.width_m, A.w, B.w);
+                segment_frame(cam, g.width_m, A, B, r);
                 if (kCgb) {
                     r.id_lo = (uint32_t)j;
                     r.id_hi = (uint32_t)(C - 1);
@@ -491,48 +312,19 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
                     r.id_lo = (uint32_t)id;
                     r.id_hi = (uint32_t)(id >> 32);
                 }
-                const int64_t dX = (int64_t)B.X - A.X, dY = (int64_t)B.Y - A.Y;
-                r.fden = __ll2float_rn(dX * dX + dY * dY);
-                r.slope = r.du == 0 ? 0.0f : (float)r.dv / (float)r.du;
-                const bool shrt = abs(r.du) < (1 << 14) && abs(r.dv) < (1 << 14);
-                r.flags = (xm ? 1 : 0) | (shrt ? 2 : 0);
-                const int du = xm ? W : H, dv = xm ? H : W;
-                // pixel m's conservative box spans [256 m, 256 m + 256]
-                int ilo = ((r.umin + 255) >> 8) - 1, ihi = r.umax >> 8;
-                ilo = max(ilo, 0);
-                ihi = min(ihi, du - 1);
-                const bool vin = r.vmax >= 0 && r.vmin <= 256 * dv;
-                r.ilo = ilo;
-                nmaj = (vin && ihi >= ilo) ? ihi - ilo + 1 : 0;
+                const bool xm = r.flags & 1;
+                int ihi, mlo, mhi;
+                if (segment_pixel_box(r, xm ? W : H, xm ? H : W, r.ilo, ihi, mlo, mhi)) nmaj = ihi - r.ilo + 1;
             }
         }
-        int incl = nmaj;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-        }
-        r.start = incl - nmaj;
-        rec[lane] = r;
-        __syncwarp();
-        const int items = __shfl_sync(kFull, incl, 31);
-        for (int base = 0; base < items; base += 32) {
-            const int item = base + lane;
-            int src = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                int v = __shfl_sync(kFull, incl, src + step - 1);
-                if (v <= item) src += step;
-            }
-            if (item >= items) continue;
-            const SegRec &q = rec[src];
-            const int i = q.ilo + (item - q.start);
+        const GlobalKeys<kPrecheck> sink{views.vis_c[view], views.vis_a[view], (uint32_t)W};
+        for_each_item(rec, r, nmaj, [&](const SegRec &q, int i) {
+            const int mmax = (q.flags & 1) ? H - 1 : W - 1;
             if (q.flags & 2)
-                raster_item<int32_t, kPrecheck, kCgb>(q, i, W, H, vis_c, vis_a, n_cons, n_cen);
+                raster_item<int32_t, kCgb>(q, i, 0, mmax, sink, n_cons, n_cen);
             else
-                raster_item<int64_t, kPrecheck, kCgb>(q, i, W, H, vis_c, vis_a, n_cons, n_cen);
-        }
-        __syncwarp();
+                raster_item<int64_t, kCgb>(q, i, 0, mmax, sink, n_cons, n_cen);
+        });
         }   // views
     }
     if (stats) {
@@ -650,26 +442,11 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_msaa_kernel(CallTabl
             const Proj A = project(cam, cp[0]);
             const Proj B = project(cam, cp[1]);
             if (A.valid && B.valid) {
-                const bool xm = abs(B.X - A.X) >= abs(B.Y - A.Y);
-                r.uA = xm ? A.X : A.Y;
-                r.vA = xm ? A.Y : A.X;
-                const int32_t uB = xm ? B.X : B.Y, vB = xm ? B.Y : B.X;
-                r.du = uB - r.uA;
-                r.dv = vB - r.vA;
-                r.umin = min(r.uA, uB);
-                r.umax = max(r.uA, uB);
-                r.vmin = min(r.vA, vB);
-                r.vmax = max(r.vA, vB);
-                r.zA = A.z;
-                r.dz = fsub(B.z, A.z);
-                r.hc = centre_halfwidth(cam, g.width_m, A.w, B.w);
+                segment_frame(cam, g.width_m, A, B, r);
                 const uint64_t id = ((g.base + (uint64_t)s) << 7) | (uint64_t)j;
                 r.id_lo = (uint32_t)id;
                 r.id_hi = (uint32_t)(id >> 32);
-                const int64_t dX = (int64_t)B.X - A.X, dY = (int64_t)B.Y - A.Y;
-                r.fden = __ll2float_rn(dX * dX + dY * dY);
-                r.slope = r.du == 0 ? 0.0f : (float)r.dv / (float)r.du;
-                r.flags = (xm ? 1 : 0) | ((abs(r.du) < (1 << 14) && abs(r.dv) < (1 << 14)) ? 2 : 0);
+                const bool xm = r.flags & 1;
                 const int du = xm ? W : H, dv = xm ? H : W;
                 // columns i whose sample boxes (centre 256 i + 128, sample
                 // offsets up to kOff, half-width hc) can reach [umin, umax]
@@ -683,32 +460,12 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_msaa_kernel(CallTabl
                 nmaj = (vin && ihi >= ilo) ? ihi - ilo + 1 : 0;
             }
         }
-        int incl = nmaj;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-        }
-        r.start = incl - nmaj;
-        rec[lane] = r;
-        __syncwarp();
-        const int items = __shfl_sync(kFull, incl, 31);
-        for (int base = 0; base < items; base += 32) {
-            const int item = base + lane;
-            int src = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                int v = __shfl_sync(kFull, incl, src + step - 1);
-                if (v <= item) src += step;
-            }
-            if (item >= items) continue;
-            const SegRec &q = rec[src];
+        for_each_item(rec, r, nmaj, [&](const SegRec &q, int i) {
             if (q.flags & 2)
-                raster_item_msaa<int32_t, N>(q, q.ilo + (item - q.start), W, H, vis_s, npx, n_hits);
+                raster_item_msaa<int32_t, N>(q, i, W, H, vis_s, npx, n_hits);
             else
-                raster_item_msaa<int64_t, N>(q, q.ilo + (item - q.start), W, H, vis_s, npx, n_hits);
-        }
-        __syncwarp();
+                raster_item_msaa<int64_t, N>(q, i, W, H, vis_s, npx, n_hits);
+        });
     }
     if (stats) {
         unsigned long long v[1] = {n_hits};

@@ -72,10 +72,12 @@ class FilterParams(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("raster_precheck", ctypes.c_int32), ("raster_min_blocks", ctypes.c_int32),
                 ("raster_ctas_per_sm", ctypes.c_int32), ("resolve_tile_h", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("raster_bin_w", ctypes.c_int32), ("raster_bin_h", ctypes.c_int32),
+                ("raster_bin_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
-TUNING_FIELDS = ("raster_precheck", "raster_min_blocks", "raster_ctas_per_sm", "resolve_tile_h")
+TUNING_FIELDS = ("raster_precheck", "raster_min_blocks", "raster_ctas_per_sm", "resolve_tile_h", "raster_bin_w",
+                 "raster_bin_h", "raster_bin_chunk")
 
 STATS_FIELDS = ("strands", "segments", "bundles_culled", "covered_center", "covered_cons")
 

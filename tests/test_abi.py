@@ -127,12 +127,23 @@ def test_tuning_and_range_arguments(L):
     t = hm.Tuning()
     assert L.hm_get_tuning(ctypes.byref(t)) == 0
     assert t.raster_min_blocks in (3, 4) and t.resolve_tile_h in (16, 32)
-    for field, bad in (("raster_precheck", 2), ("raster_min_blocks", 5), ("raster_ctas_per_sm", -1),
-                       ("resolve_tile_h", 24)):
+    assert (t.raster_bin_w, t.raster_bin_h, t.raster_bin_chunk) == (0, 0, 0)     # direct rasterizer
+    for bad in ({"raster_precheck": 2}, {"raster_min_blocks": 5}, {"raster_ctas_per_sm": -1}, {"resolve_tile_h": 24},
+                {"raster_bin_w": 8, "raster_bin_h": 16, "raster_bin_chunk": 256},
+                {"raster_bin_w": 16, "raster_bin_h": 24, "raster_bin_chunk": 256},
+                {"raster_bin_w": 16, "raster_bin_h": 16, "raster_bin_chunk": 512},
+                {"raster_bin_w": 32},                                   # bin height and chunk missing
+                {"raster_bin_h": 16}, {"raster_bin_chunk": 256}):       # set while the direct rasterizer is chosen
         b = hm.Tuning()
         L.hm_get_tuning(ctypes.byref(b))
-        setattr(b, field, bad)
-        assert L.hm_set_tuning(ctypes.byref(b)) == INVALID, field
+        for field, v in bad.items():
+            setattr(b, field, v)
+        assert L.hm_set_tuning(ctypes.byref(b)) == INVALID, bad
+    ok = hm.Tuning()
+    L.hm_get_tuning(ctypes.byref(ok))
+    ok.raster_bin_w, ok.raster_bin_h, ok.raster_bin_chunk = 32, 16, 1024
+    assert L.hm_set_tuning(ctypes.byref(ok)) == 0
+    assert L.hm_set_tuning(ctypes.byref(t)) == 0
     assert L.hm_set_tuning(None) == INVALID
     sc = synth.tiny_scene(0, num_strands=10)
     cam = hm.camera_struct(sc.camera)
