@@ -37,6 +37,7 @@ UNIT = "segments/s"
 L2_FLUSH_BYTES = 256 << 20
 # kernels of one frame: clear, LOD select, LOD scan (work list), raster, resolve
 LAUNCHES_PER_FRAME = 5
+BIN_FIELDS = ("raster_bin_w", "raster_bin_h", "raster_bin_chunk")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 FALLBACK_HBM_GBS = 6400.0
@@ -53,6 +54,9 @@ def parse():
                                            "compressed_1080p", "atomic_probe"],
                     default="single_1080p")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuning", default="",
+                    help="set these hm_tuning fields instead of autotuning (k=v,k=v), e.g. "
+                         "raster_bin_w=32,raster_bin_h=32,raster_bin_chunk=1024 for the binned rasterizer")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -472,6 +476,61 @@ def _timed(torch, step, steps, flush):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def choose_tuning(args, autotune_step, scene, segs, n):
+    """--tuning k=v,...: set those hm_tuning fields and skip the autotuner;
+    otherwise the autotuner's pick for this workload (none with
+    --no-autotune)."""
+    from paper_2607_04230_b300 import autotune, hm
+    if args.tuning:
+        hm.set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(","))})
+        return {"tuning": hm.get_tuning(), "ms": None, "table": [], "forced": True}
+    if args.no_autotune:
+        return None
+    return autotune.autotune(autotune_step, scene, segs, n=n)
+
+
+def launches_per_frame():
+    """Kernels of one resolved frame under the current tuning: the direct
+    rasterizer is one launch, the binned one four (count, scan, fill, tile)."""
+    from paper_2607_04230_b300 import hm
+    return LAUNCHES_PER_FRAME + (3 if hm.get_tuning()["raster_bin_w"] else 0)
+
+
+def raster_modes(torch, hm, step, flush, n=20):
+    """Median raster-phase and frame ms of `step` (L2 flushed before every
+    frame) under the current tuning and under every binned-rasterizer
+    candidate of the autotuner (bin and chunk sizes); restores the tuning."""
+    from paper_2607_04230_b300 import autotune
+    saved = hm.get_tuning()
+    rows = []
+    try:
+        for cand in [None] + [c for c in autotune.candidates() if c["raster_bin_w"]]:
+            if cand is not None:
+                hm.set_tuning(**dict(saved, **{k: cand[k] for k in BIN_FIELDS}))
+            t = hm.get_tuning()
+            for _ in range(3):
+                step()
+            evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(n)]
+            for row in evs:
+                for e in row:
+                    e.record()
+            for k in range(n):
+                flush.fill_(k)
+                hm.set_phase_events(evs[k])
+                step()
+            hm.set_phase_events(None)
+            torch.cuda.synchronize()
+            hm.get_device_status()
+            label = (f"binned {t['raster_bin_w']}x{t['raster_bin_h']} px tiles, {t['raster_bin_chunk']}-segment "
+                     "chunks" if t["raster_bin_w"] else "direct (global atomicMin)")
+            rows.append({"raster": label, "raster_ms": statistics.median(e[2].elapsed_time(e[3]) for e in evs),
+                         "frame_ms": statistics.median(e[0].elapsed_time(e[5]) for e in evs)})
+    finally:
+        hm.set_phase_events(None)
+        hm.set_tuning(**saved)
+    return rows
+
+
 def run_crowd(args, rank, world, local_rank):
     """64 grooms at 4K: the autotuned batched frame (one render + one resolve
     call, captured in a CUDA graph) against one render call per groom."""
@@ -487,9 +546,8 @@ def run_crowd(args, rank, world, local_rank):
     torch.cuda.synchronize()
     st = hm.stats_dict(cr.frame.stats)
     segs = st["segments"]
-    tune = None
-    if not args.no_autotune:
-        tune = autotune.autotune(cr.render_batched, scene, segs, n=3)
+    tune = choose_tuning(args, cr.render_batched, scene, segs, n=3)
+    modes = None if args.tuning else raster_modes(torch, hm, cr.render_batched, flush)
     # per-kernel phase times (same kernels, outside the graph): medians of 20 frames
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(20)]
     for row in ev:
@@ -548,9 +606,11 @@ def run_crowd(args, rank, world, local_rank):
                               "speedup_vs_eager": ms_pc / ms_g, "grooms": n,
                               "per_character_path": "one hm_render_visibility_range call per groom into the shared "
                                                     "key buffers, then one resolve"},
-            "autotune": tune and {"tuning": tune["tuning"], "best_ms": tune["ms"], "candidates": len(tune["table"])},
+            "autotune": tune and {"tuning": tune["tuning"], "best_ms": tune["ms"], "candidates": len(tune["table"]),
+                                  "forced": tune.get("forced", False)},
+            "raster_modes": modes,
             # graph replays: + the tile-list count and order passes and the decode pass per frame
-            "gpu_launches": (LAUNCHES_PER_FRAME + 3) * args.steps, "clocks": clk}
+            "gpu_launches": (launches_per_frame() + 3) * args.steps, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -1046,10 +1106,8 @@ def run_native(args, rank, world, local_rank):
     st = hm.stats_dict(frame.stats)
     segs = st["segments"]
     atomics = st["covered_cons"] + st["covered_center"]
-    tune = None
-    if not args.no_autotune:
-        from paper_2607_04230_b300 import autotune
-        tune = autotune.autotune(step, scene, segs, n=5)
+    tune = choose_tuning(args, step, scene, segs, n=5)
+    modes = None if args.tuning or args.workload != "single_1080p" else raster_modes(torch, hm, step, flush)
 
     peak_rates = probe_atomic_peak(torch, hm, 2 * W * H)
 
@@ -1171,9 +1229,11 @@ def run_native(args, rank, world, local_rank):
             "segments_per_frame": segs, "raster_segments_per_s": segs / (phase_ms["raster"] * 1e-3),
             "lod_raster_segments_per_s": segs / ((phase_ms["lod"] + phase_ms["raster"]) * 1e-3),
             "roofline": roofline, "kernels": kernels,
-            "e2e": e2e, "gpu_launches": (LAUNCHES_PER_FRAME + 3) * args.steps,   # + the tile-list count and order passes and the decode pass
+            "e2e": e2e, "gpu_launches": (launches_per_frame() + 3) * args.steps,   # + the tile-list count and order passes and the decode pass
             "clocks": clk, "wall_s": wall,
-            "autotune": tune and {"tuning": tune["tuning"], "best_ms": tune["ms"], "candidates": len(tune["table"])}}
+            "autotune": tune and {"tuning": tune["tuning"], "best_ms": tune["ms"], "candidates": len(tune["table"]),
+                                  "forced": tune.get("forced", False)},
+            "raster_modes": modes}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(scene)
     print(json.dumps(line), flush=True)
