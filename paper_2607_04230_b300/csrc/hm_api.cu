@@ -295,13 +295,12 @@ hm_status hm_create_groom(const hm_groom_desc *d, void *stream, hm_groom *out) {
         first[f + 1]++;
     }
     for (int32_t f = 0; f < F; ++f) first[f + 1] += first[f];
-    size_t max_batches = 0;
-    for (int32_t f = 0; f < F; ++f) {
-        int64_t nseg = (int64_t)(first[f + 1] - first[f]) * segs;
-        max_batches += (size_t)((nseg + hm::kSegBatch - 1) / hm::kSegBatch);
-    }
-    if (max_batches > 0xFFFFFFF0ull || (uint64_t)S * (uint64_t)segs > 0xFFFFFF00ull)
-        return fail(HM_ERR_CAPACITY, "too many segments in one groom (32-bit segment index)");
+    // work-list batches at full detail: S (segs + 1) control points, a batch
+    // per kBatchStride of them (plus one)
+    const uint64_t max_points = (uint64_t)S * (uint64_t)(segs + 1);
+    if (max_points > 0xFFFFFF00ull)
+        return fail(HM_ERR_CAPACITY, "too many control points in one groom (32-bit index)");
+    const size_t max_batches = (size_t)(max_points / hm::kBatchStride + 2);
 
     // host-side repack to the device layout
     std::vector<float4> lv((size_t)L * V);
@@ -489,7 +488,7 @@ static hm_status render_views(const hm_groom *grooms, int32_t n, int32_t first, 
     uint64_t bin_slots = 0;
     uint32_t *sw = nullptr;
     if (binned) {
-        for (int i = 0; i < count; ++i) bin_slots += (uint64_t)tab.g[i].max_batches * hm::kSegBatch;
+        for (int i = 0; i < count; ++i) bin_slots += (uint64_t)tab.g[i].max_batches * hm::kBatchLanes;
         st = bin_workspace(grooms[first],
                            hm::binned_workspace_bytes(bin_slots, cams[0].width, cams[0].height, g_tuning.raster_bin_w,
                                                       g_tuning.raster_bin_h),

@@ -47,7 +47,7 @@ enum BinCtl : int { kCtlUnitTicket = 0, kCtlPairs = 1, kCtlUnits = 2, kCtlWords 
 
 // Views into the caller's workspace (binned_workspace_bytes).
 struct BinLayout {
-    BinSeg *segs;          // [slots] set-up segment of batch slot b * 32 + lane
+    BinSeg *segs;          // [slots] set-up segment of batch slot b * 32 + lane (lane < 31)
     uint2 *tbox;           // [slots] tile box (tx0 | ty0 << 16, tx1 | ty1 << 16); x = kNoBox: none
     uint32_t *tile_cnt;    // [ntiles] pairs per tile (count), then fill cursors
     uint32_t *tile_off;    // [ntiles + 1] exclusive prefix of the pair counts
@@ -93,8 +93,9 @@ __device__ __forceinline__ int box_tiles(uint2 box, int &tx0, int &ty0, int &tw)
     return tw * ((int)(box.y >> 16) - ty0 + 1);
 }
 
-// 1. count.  Persistent, one warp per 32-segment batch from the work-list
-// ticket (as the direct rasterizer).  Per tile, the lanes of a warp that hit
+// 1. count.  Persistent, one warp per work-list batch from the ticket (as
+// the direct rasterizer: a control point per lane, segments closed by the
+// next lane's point).  Per tile, the lanes of a warp that hit
 // it add their count with one atomic.
 template <int TWL, int THL>
 __global__ void __launch_bounds__(kRasterThreads, 4) bin_count_kernel(CallTable tab, CamDev cam, BinLayout bl) {
@@ -109,49 +110,41 @@ __global__ void __launch_bounds__(kRasterThreads, 4) bin_count_kernel(CallTable 
         if (lane == 0) b = atomicAdd(ticket, 1u);
         b = __shfl_sync(kFull, b, 0);
         // the host sizes the workspace for every batch the grooms can have
-        if (b >= total || b >= bl.slots / kSegBatch) break;
+        if (b >= total || b >= bl.slots / kBatchLanes) break;
         const int gi = batch_groom(s_goff, tab.n, b);
         const GroomDev &g = tab.g[gi];
         const uint32_t lb = b - s_goff[gi];
-        const uint32_t seg = lb * kSegBatch + lane;
-        const uint32_t slot = b * kSegBatch + lane;
+        const uint32_t slot = b * kBatchLanes + lane;
         uint2 box = make_uint2(kNoBox, 0u);
-        if (seg < g.counters[kCtrSegs]) {
-            int64_t s;
-            int j, C;
-            uint32_t f;
-            float3 cp[2];
-            batch_segment(g, __ldg(&g.batch_map[lb]), seg, f, s, j, C);
-            control_pts<2>(g, make_root(g, s, f), C, j, cp);
-            if (g.segpts) store_segment_points(g.segpts, seg, cp);
-            const Proj A = project(cam, cp[0]);
-            const Proj B = project(cam, cp[1]);
-            if (A.valid && B.valid) {
-                SegRec r;
-                segment_frame(cam, g.width_m, A, B, r);
-                const bool xm = r.flags & 1;
-                int ilo, ihi, mlo, mhi;
-                if (segment_pixel_box(r, xm ? W : H, xm ? H : W, ilo, ihi, mlo, mhi)) {
-                    const uint64_t id = ((g.base + (uint64_t)s) << 7) | (uint64_t)j;
-                    BinSeg q;
-                    q.uA = r.uA;
-                    q.vA = r.vA;
-                    q.du = r.du;
-                    q.dv = r.dv;
-                    q.zA = r.zA;
-                    q.dz = r.dz;
-                    q.fden = r.fden;
-                    q.slope = r.slope;
-                    q.hc = r.hc;
-                    q.flags = r.flags;
-                    q.id_lo = (uint32_t)id;
-                    q.id_hi = (uint32_t)(id >> 32);
-                    bl.segs[slot] = q;
-                    const int x0 = xm ? ilo : mlo, x1 = xm ? ihi : mhi;
-                    const int y0 = xm ? mlo : ilo, y1 = xm ? mhi : ihi;
-                    box = make_uint2((uint32_t)(x0 >> TWL) | ((uint32_t)(y0 >> THL) << 16),
-                                     (uint32_t)(x1 >> TWL) | ((uint32_t)(y1 >> THL) << 16));
-                }
+        const BatchPoint bp = batch_lane_point(g, lb, lane);
+        const float3 cp[2] = {bp.p, next_lane(bp.p)};
+        if (bp.seg_ok && g.segpts) store_segment_points(g.segpts, bp.seg, cp);
+        Proj A, B;
+        if (batch_lane_segment(cam, bp, A, B)) {
+            SegRec r;
+            segment_frame(cam, g.width_m, A, B, r);
+            const bool xm = r.flags & 1;
+            int ilo, ihi, mlo, mhi;
+            if (segment_pixel_box(r, xm ? W : H, xm ? H : W, ilo, ihi, mlo, mhi)) {
+                const uint64_t id = ((g.base + (uint64_t)bp.s) << 7) | (uint64_t)bp.j;
+                BinSeg q;
+                q.uA = r.uA;
+                q.vA = r.vA;
+                q.du = r.du;
+                q.dv = r.dv;
+                q.zA = r.zA;
+                q.dz = r.dz;
+                q.fden = r.fden;
+                q.slope = r.slope;
+                q.hc = r.hc;
+                q.flags = r.flags;
+                q.id_lo = (uint32_t)id;
+                q.id_hi = (uint32_t)(id >> 32);
+                bl.segs[slot] = q;
+                const int x0 = xm ? ilo : mlo, x1 = xm ? ihi : mhi;
+                const int y0 = xm ? mlo : ilo, y1 = xm ? mhi : ihi;
+                box = make_uint2((uint32_t)(x0 >> TWL) | ((uint32_t)(y0 >> THL) << 16),
+                                 (uint32_t)(x1 >> TWL) | ((uint32_t)(y1 >> THL) << 16));
             }
         }
         bl.tbox[slot] = box;
@@ -234,7 +227,7 @@ __global__ void __launch_bounds__(1024) bin_scan_kernel(BinLayout bl, uint32_t *
 __global__ void __launch_bounds__(256) bin_fill_kernel(CallTable tab, BinLayout bl) {
     __shared__ uint32_t s_goff[HM_MAX_GROOMS_PER_CALL + 1];
     groom_batch_offsets(tab, s_goff);
-    const uint32_t nslots = min(s_goff[tab.n] * (uint32_t)kSegBatch, bl.slots);
+    const uint32_t nslots = min(s_goff[tab.n] * (uint32_t)kBatchLanes, bl.slots);
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
     // warp-uniform loop: base is the warp's first slot

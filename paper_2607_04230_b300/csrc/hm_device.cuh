@@ -20,10 +20,17 @@ constexpr uint64_t kEmptyKey = ~0ull;
 constexpr uint64_t kPayloadMask = 0xFFFFFFFFFFull;
 constexpr uint64_t kStrandMask = 0x1FFFFFFFFull;   // 33 bits
 constexpr float kGuard = 1048576.0f;               // 2^20 px guard band
-constexpr int kSegBatch = 32;                      // segments per warp batch
+// The rasterizers' work list: batch b of a groom holds its drawn control
+// points kBatchStride b .. kBatchStride b + 31 (bundle order, then strand,
+// then index along the strand), one per lane of a warp; lane l's segment
+// joins its point to lane l + 1's.  Consecutive batches share one point, so
+// every segment lies in exactly one batch.
+constexpr int kBatchLanes = 32;
+constexpr int kBatchStride = kBatchLanes - 1;
 
-// Per-groom device counters (one block of words per groom).
-enum CounterWord : int { kCtrBatches = 0, kCtrTicket = 1, kCtrSegs = 2, kCtrWords = 4 };
+// Per-groom device counters (one block of words per groom): work-list
+// batches, the rasterizer's ticket, drawn segments, drawn control points.
+enum CounterWord : int { kCtrBatches = 0, kCtrTicket = 1, kCtrSegs = 2, kCtrCps = 3, kCtrWords = 4 };
 
 // Device status bits (read by hm_get_device_status).
 enum StatusBit : uint32_t { kStatusBadKey = 1u, kStatusBadBatch = 2u, kStatusBinOverflow = 4u };
@@ -37,8 +44,8 @@ struct GroomDev {
     const float2 *bary;      // [S] (b1, b2)
     const float4 *albedo;    // [S] rgb
     const float *delta;      // [F] LOD offset of Eq. 1
-    uint4 *lod;              // [F] (N_LOD, C, first segment, segments)
-    uint32_t *batch_map;     // [max_batches] bundle holding the first segment of each 32-segment batch
+    uint4 *lod;              // [F] (N_LOD, C, first drawn segment, first drawn control point)
+    uint32_t *batch_map;     // [max_batches] bundle holding the first control point of each batch
     uint32_t *counters;      // [kCtrWords]
     int32_t L, V, F, cmax;
     int64_t S;
@@ -47,9 +54,9 @@ struct GroomDev {
     int32_t lod_enabled;
     int32_t has_ao;          // layer vertices carry baked ambient occlusion in w
     const float2 *uv;        // [V] scalp texture coordinates, or null (compressed payload)
-    uint32_t max_batches;    // 32-segment batches at full detail (batch_map capacity)
+    uint32_t max_batches;    // work-list batches at full detail (batch_map capacity)
     // [drawn segments][2] control points j and j+1 of every drawn segment,
-    // (p_j.xyz, p_j+1.x), (p_j+1.yz, 0, 0), indexed like the batch list
+    // (p_j.xyz, p_j+1.x), (p_j+1.yz, 0, 0), indexed by drawn segment
     // (lod[f].z + strand-in-bundle (C - 1) + j).  The rasterizer writes them
     // when non-null; key decoding reads them instead of regenerating the
     // strand when non-null (the host passes them only while they match the

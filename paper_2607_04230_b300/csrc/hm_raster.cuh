@@ -68,17 +68,85 @@ __device__ __forceinline__ int batch_groom(const uint32_t *goff, int n, uint32_t
     return lo;
 }
 
-// Segment `seg` (0 <= seg < drawn segments of the groom) of the batch whose
-// first segment lies in bundle f0: its bundle f, strand s and segment j.
-__device__ __forceinline__ void batch_segment(const GroomDev &g, uint32_t f0, uint32_t seg, uint32_t &f, int64_t &s,
-                                              int &j, int &C) {
+// Drawn control point q of a groom, found from the bundle f0 that holds
+// its batch's first point: its bundle f, strand s, index j along the strand,
+// the strand's point count C, and the drawn segment it starts (seg, when
+// j < C - 1).  Bundles that draw nothing share their first point with the
+// next bundle and are passed over.
+__device__ __forceinline__ void batch_point(const GroomDev &g, uint32_t f0, uint32_t q, uint32_t &f, int64_t &s,
+                                            int &j, int &C, uint32_t &seg) {
     f = f0;
-    while (f + 1 < (uint32_t)g.F && g.lod[f + 1].z <= seg) ++f;
+    while (f + 1 < (uint32_t)g.F && g.lod[f + 1].w <= q) ++f;
     const uint4 lo = g.lod[f];
     C = (int)lo.y;
-    const uint32_t sl = seg - lo.z;
-    s = (int64_t)__ldg(&g.faces[f]).w + sl / (uint32_t)(C - 1);
-    j = (int)(sl % (uint32_t)(C - 1));
+    const uint32_t local = q - lo.w;
+    const uint32_t sl = local / (uint32_t)C;
+    j = (int)(local - sl * (uint32_t)C);
+    s = (int64_t)__ldg(&g.faces[f]).w + sl;
+    seg = lo.z + sl * (uint32_t)(C - 1) + (uint32_t)j;
+}
+
+// The lane's work-list point: lane l of batch b (local to groom g) holds
+// drawn control point kBatchStride b + l, generated here (bit-identical to
+// generating it within its segment); `seg_ok` when it starts a segment whose
+// other end, the strand's next point, is lane l + 1's.  Warp-uniform call.
+struct BatchPoint {
+    float3 p;
+    int64_t s;
+    int j, C;
+    uint32_t f, seg;
+    bool has, seg_ok;
+};
+
+__device__ __forceinline__ BatchPoint batch_lane_point(const GroomDev &g, uint32_t lb, int lane) {
+    BatchPoint r;
+    const uint32_t q = lb * (uint32_t)kBatchStride + (uint32_t)lane;
+    r.has = q < g.counters[kCtrCps];
+    r.p = make_float3(0.0f, 0.0f, 0.0f);
+    r.s = 0;
+    r.j = 0;
+    r.C = 2;
+    r.f = 0;
+    r.seg = 0;
+    if (r.has) {
+        batch_point(g, __ldg(&g.batch_map[lb]), q, r.f, r.s, r.j, r.C, r.seg);
+        float3 one[1];
+        control_pts<1>(g, make_root(g, r.s, r.f), r.C, r.j, one);
+        r.p = one[0];
+    }
+    r.seg_ok = r.has && lane < kBatchStride && r.j < r.C - 1;
+    return r;
+}
+
+// Lane l + 1's value (lane 31 gets its own back; it never starts a segment).
+__device__ __forceinline__ float3 next_lane(float3 v) {
+    return make_float3(__shfl_down_sync(kFull, v.x, 1), __shfl_down_sync(kFull, v.y, 1),
+                       __shfl_down_sync(kFull, v.z, 1));
+}
+
+// Lane l + 1's projection: the fields the segment set-up reads (X, Y, w, z,
+// valid).
+__device__ __forceinline__ Proj next_lane(const Proj &p) {
+    Proj r;
+    r.X = __shfl_down_sync(kFull, p.X, 1);
+    r.Y = __shfl_down_sync(kFull, p.Y, 1);
+    r.w = __shfl_down_sync(kFull, p.w, 1);
+    r.z = __shfl_down_sync(kFull, p.z, 1);
+    r.xs = r.ys = 0.0f;
+    r.valid = __shfl_down_sync(kFull, (int)p.valid, 1) != 0;
+    return r;
+}
+
+// The lane's segment seen by one camera: each lane projects its own point
+// and takes the far end from lane + 1.  False when the lane starts no
+// segment or an end lies in front of the near plane.  Warp-uniform call.
+__device__ __forceinline__ bool batch_lane_segment(const CamDev &cam, const BatchPoint &bp, Proj &A, Proj &B) {
+    A.X = A.Y = 0;
+    A.w = A.z = A.xs = A.ys = 0.0f;
+    A.valid = false;
+    if (bp.has) A = project(cam, bp.p);
+    B = next_lane(A);
+    return bp.seg_ok && A.valid && B.valid;
 }
 
 // A projected segment in the frame of its major screen axis u (x when
@@ -218,7 +286,7 @@ __device__ __forceinline__ void raster_item(const SegRec &q_shared, int i, int m
     }
 }
 
-// Runs fn(q, i) for every work item of a warp's 32 set-up segments (lane l
+// Runs fn(q, i) for every work item of a warp's set-up segments (lane l
 // holds segment r with nmaj items, major pixels r.ilo ..): the items are
 // dealt to the lanes 32 at a time through a prefix sum over the lanes'
 // counts and a binary search in it, so long and short segments share the

@@ -143,7 +143,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t &total,
 }
 
 // The LOD decision of every bundle, all grooms at once (one thread per
-// bundle): lod[f] = (N_LOD, C, -, segments).
+// bundle): lod[f] = (N_LOD, C, -, -); the scan fills in the offsets.
 constexpr int kLodSelThreads = 256;
 
 __global__ void __launch_bounds__(kLodSelThreads) lod_select_kernel(CallTable tab, CamDev cam,
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kLodSelThreads) lod_select_kernel(CallTable ta
             }
         }
         const uint32_t nseg = (uint32_t)n * (uint32_t)(c - 1);
-        g.lod[f] = make_uint4((uint32_t)n, (uint32_t)c, 0u, nseg);
+        g.lod[f] = make_uint4((uint32_t)n, (uint32_t)c, 0u, 0u);
         strands = (unsigned long long)n;
         segs = nseg;
     }
@@ -177,16 +177,17 @@ __global__ void __launch_bounds__(kLodSelThreads) lod_select_kernel(CallTable ta
     }
 }
 
-// The bundles' first segment (exclusive scan of their drawn segment counts)
-// and the work list the rasterizer pulls from: batches of 32 consecutive
-// segments of the groom in bundle order (one batch may span several
-// bundles, so lanes stay busy when LOD leaves bundles a few segments), each
-// listed with the bundle holding its first segment.  grid.y = groom, grid.x =
+// The bundles' first drawn segment and first drawn control point
+// (exclusive scans of N_LOD (C - 1) and N_LOD C), and the work list the
+// rasterizers pull from: batch b holds the groom's drawn control points
+// kBatchStride b .. kBatchStride b + 31 in bundle order (one batch may span
+// several bundles, so lanes stay busy when LOD leaves bundles a few points),
+// listed with the bundle holding its first point.  grid.y = groom, grid.x =
 // slices of kLodFillPerCta batches: every CTA of a groom repeats the (short)
-// scan over its bundles, the first one publishes it, and each fills its
-// slice one batch per thread by a binary search over the scan (a bundle
-// without segments shares its first segment with the next one, so the
-// search lands on the bundle that holds the segment).
+// scans over its bundles, the first one publishes them, and each fills its
+// slice one batch per thread by a binary search over the point scan (a
+// bundle without points shares its first point with the next one, so the
+// search lands on the bundle that holds the point).
 constexpr int kLodScanThreads = 1024, kLodScanCache = 12000, kLodFillPerCta = 8192;
 
 __global__ void __launch_bounds__(kLodScanThreads) lod_scan_kernel(CallTable tab) {
@@ -197,32 +198,43 @@ __global__ void __launch_bounds__(kLodScanThreads) lod_scan_kernel(CallTable tab
     const bool lead = blockIdx.x == 0;
     if (!cache && !lead) return;                  // large meshes: the first CTA fills serially
     if (!lead && blockIdx.x * (uint32_t)kLodFillPerCta >= g.max_batches) return;   // beyond this groom's list
-    uint32_t running = 0;
+    uint32_t segs = 0, pts = 0;
     for (int base = 0; base < g.F; base += kLodScanThreads) {
         const int f = base + (int)threadIdx.x;
-        const uint32_t ns = f < g.F ? g.lod[f].w : 0u;
-        uint32_t tot;
-        const uint32_t first = running + block_excl_scan<kLodScanThreads>(ns, tot, sm);
+        uint32_t n = 0, c = 0;
         if (f < g.F) {
-            if (lead) g.lod[f].z = first;
+            const uint4 lo = g.lod[f];
+            n = lo.x;
+            c = lo.y;
+        }
+        uint32_t tot_s, tot_p;
+        const uint32_t first_s = segs + block_excl_scan<kLodScanThreads>(n * (c - 1), tot_s, sm);
+        const uint32_t first_p = pts + block_excl_scan<kLodScanThreads>(n * c, tot_p, sm);
+        if (f < g.F) {
+            if (lead) {
+                g.lod[f].z = first_s;
+                g.lod[f].w = first_p;
+            }
             if (cache) {
-                s_first[f] = first;
-            } else if (ns > 0) {
-                for (uint32_t b = (first + kSegBatch - 1) / kSegBatch; b * kSegBatch < first + ns; ++b)
+                s_first[f] = first_p;
+            } else if (n > 0) {
+                for (uint32_t b = (first_p + kBatchStride - 1) / kBatchStride; b * kBatchStride < first_p + n * c; ++b)
                     g.batch_map[b] = (uint32_t)f;
             }
         }
-        running += tot;
+        segs += tot_s;
+        pts += tot_p;
     }
-    const uint32_t nbatch = (running + kSegBatch - 1) / kSegBatch;
+    // every segment (q, q + 1) with q < pts - 1 lies in batch q / kBatchStride
+    const uint32_t nbatch = pts > 1 ? (pts - 2) / kBatchStride + 1 : 0;
     if (cache) {
-        if (threadIdx.x == 0) s_first[g.F] = running;
+        if (threadIdx.x == 0) s_first[g.F] = pts;
         __syncthreads();
         const uint32_t b0 = blockIdx.x * (uint32_t)kLodFillPerCta;
         const uint32_t b1 = min(b0 + (uint32_t)kLodFillPerCta, nbatch);
         for (uint32_t b = b0 + threadIdx.x; b < b1; b += kLodScanThreads) {
-            const uint32_t x = b * kSegBatch;    // first segment of the batch
-            int lo = 0, hi = g.F;                 // s_first[lo] <= x < s_first[hi]
+            const uint32_t x = b * kBatchStride;    // first point of the batch
+            int lo = 0, hi = g.F;                   // s_first[lo] <= x < s_first[hi]
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
                 if (s_first[mid] <= x) lo = mid; else hi = mid;
@@ -232,7 +244,8 @@ __global__ void __launch_bounds__(kLodScanThreads) lod_scan_kernel(CallTable tab
     }
     if (lead && threadIdx.x == 0) {
         g.counters[kCtrBatches] = nbatch;
-        g.counters[kCtrSegs] = running;
+        g.counters[kCtrSegs] = segs;
+        g.counters[kCtrCps] = pts;
         if (blockIdx.y == 0) g.counters[kCtrTicket] = 0;
     }
 }
@@ -241,9 +254,11 @@ __global__ void __launch_bounds__(kLodScanThreads) lod_scan_kernel(CallTable tab
 // rasterizer (Sec. 3.1.1 strand assembly, Sec. 3.1.2 atomicMin visibility,
 // Sec. 3.3 two layers)
 //
-// Persistent grid; each warp pulls 32-segment batches from a ticket.  A lane
-// generates one segment (two control points), projects and snaps it, then the
-// warp enumerates the batch's candidate pixels together: work items are
+// Persistent grid; each warp pulls work-list batches from a ticket.  A lane
+// generates one control point and projects and snaps it; the next lane's
+// point, taken by shuffle, closes the lane's segment (so each point is
+// generated and projected once, not once per segment that ends in it).  The
+// warp then enumerates the batch's candidate pixels together: work items are
 // (segment, pixel step along the major axis), load-balanced across the warp
 // by a prefix sum, and each item tests its 2-4 minor-axis pixels with the
 // exact predicate and issues the 64-bit atomicMin for each layer.
@@ -272,50 +287,45 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
         const int gi = batch_groom(s_goff, tab.n, b);
         const GroomDev &g = tab.g[gi];
         const uint32_t lb = b - s_goff[gi];
-        const uint32_t seg = lb * kSegBatch + lane;
-        const bool active = seg < g.counters[kCtrSegs];
-        int64_t s = 0;
-        int j = 0, C = 2;
-        uint32_t f = 0;
-        float3 cp[2];
+        // this lane's control point, and its segment to lane + 1's point
+        const BatchPoint bp = batch_lane_point(g, lb, lane);
+        const bool active = bp.seg_ok;
+        const float3 cp[2] = {bp.p, next_lane(bp.p)};
+        if (active && g.segpts) store_segment_points(g.segpts, bp.seg, cp);
         uint32_t cgb_hi = 0;
         float aoA = 1.0f, aoB = 1.0f;
-        if (active) {
-            batch_segment(g, __ldg(&g.batch_map[lb]), seg, f, s, j, C);
-            const Root rt = make_root(g, s, f);
-            control_pts<2>(g, rt, C, j, cp);
-            if (g.segpts) store_segment_points(g.segpts, seg, cp);
-            if (kCgb) {
-                cgb_hi = (oct_encode(v3unit(v3sub(cp[1], cp[0]))) << 12) | root_uv_codes(g, rt);
-                aoA = control_ao_exact(g, rt, C, j);
-                aoB = control_ao_exact(g, rt, C, j + 1);
+        if (kCgb) {
+            Root rt;
+            if (bp.has) {
+                rt = make_root(g, bp.s, bp.f);
+                aoA = control_ao_exact(g, rt, bp.C, bp.j);
             }
+            aoB = __shfl_down_sync(kFull, aoA, 1);
+            if (active) cgb_hi = (oct_encode(v3unit(v3sub(cp[1], cp[0]))) << 12) | root_uv_codes(g, rt);
         }
         const int n_views = kMulti ? views.n : 1;
         for (int view = 0; view < n_views; ++view) {
         const CamDev &cam = views.cam[view];
+        Proj A, B;
+        const bool drawn = batch_lane_segment(cam, bp, A, B);
         SegRec r;
         int nmaj = 0;
-        if (active) {
-            const Proj A = project(cam, cp[0]);
-            const Proj B = project(cam, cp[1]);
-            if (A.valid && B.valid) {
-                segment_frame(cam, g.width_m, A, B, r);
-                if (kCgb) {
-                    r.id_lo = (uint32_t)j;
-                    r.id_hi = (uint32_t)(C - 1);
-                    r.cgb_hi = cgb_hi;
-                    r.aoA = aoA;
-                    r.dao = fsub(aoB, aoA);
-                } else {
-                    const uint64_t id = ((g.base + (uint64_t)s) << 7) | (uint64_t)j;
-                    r.id_lo = (uint32_t)id;
-                    r.id_hi = (uint32_t)(id >> 32);
-                }
-                const bool xm = r.flags & 1;
-                int ihi, mlo, mhi;
-                if (segment_pixel_box(r, xm ? W : H, xm ? H : W, r.ilo, ihi, mlo, mhi)) nmaj = ihi - r.ilo + 1;
+        if (drawn) {
+            segment_frame(cam, g.width_m, A, B, r);
+            if (kCgb) {
+                r.id_lo = (uint32_t)bp.j;
+                r.id_hi = (uint32_t)(bp.C - 1);
+                r.cgb_hi = cgb_hi;
+                r.aoA = aoA;
+                r.dao = fsub(aoB, aoA);
+            } else {
+                const uint64_t id = ((g.base + (uint64_t)bp.s) << 7) | (uint64_t)bp.j;
+                r.id_lo = (uint32_t)id;
+                r.id_hi = (uint32_t)(id >> 32);
             }
+            const bool xm = r.flags & 1;
+            int ihi, mlo, mhi;
+            if (segment_pixel_box(r, xm ? W : H, xm ? H : W, r.ilo, ihi, mlo, mhi)) nmaj = ihi - r.ilo + 1;
         }
         const GlobalKeys<kPrecheck> sink{views.vis_c[view], views.vis_a[view], (uint32_t)W};
         for_each_item(rec, r, nmaj, [&](const SegRec &q, int i) {
@@ -428,37 +438,30 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_msaa_kernel(CallTabl
         const int gi = batch_groom(s_goff, tab.n, b);
         const GroomDev &g = tab.g[gi];
         const uint32_t lb = b - s_goff[gi];
-        const uint32_t seg = lb * kSegBatch + lane;
+        const BatchPoint bp = batch_lane_point(g, lb, lane);
+        const float3 cp[2] = {bp.p, next_lane(bp.p)};
+        if (bp.seg_ok && g.segpts) store_segment_points(g.segpts, bp.seg, cp);
+        Proj A, B;
+        const bool drawn = batch_lane_segment(cam, bp, A, B);
         SegRec r;
         int nmaj = 0;
-        if (seg < g.counters[kCtrSegs]) {
-            uint32_t f;
-            int64_t s;
-            int j, C;
-            batch_segment(g, __ldg(&g.batch_map[lb]), seg, f, s, j, C);
-            float3 cp[2];
-            control_pts<2>(g, make_root(g, s, f), C, j, cp);
-            if (g.segpts) store_segment_points(g.segpts, seg, cp);
-            const Proj A = project(cam, cp[0]);
-            const Proj B = project(cam, cp[1]);
-            if (A.valid && B.valid) {
-                segment_frame(cam, g.width_m, A, B, r);
-                const uint64_t id = ((g.base + (uint64_t)s) << 7) | (uint64_t)j;
-                r.id_lo = (uint32_t)id;
-                r.id_hi = (uint32_t)(id >> 32);
-                const bool xm = r.flags & 1;
-                const int du = xm ? W : H, dv = xm ? H : W;
-                // columns i whose sample boxes (centre 256 i + 128, sample
-                // offsets up to kOff, half-width hc) can reach [umin, umax]
-                constexpr int32_t kOff = N == 1 ? 0 : (N == 2 ? 64 : (N == 4 ? 96 : 112));
-                const int32_t reach = kOff + r.hc;
-                int ilo = (r.umin - reach - 128 + 255) >> 8, ihi = (r.umax + reach - 128) >> 8;
-                ilo = max(ilo, 0);
-                ihi = min(ihi, du - 1);
-                const bool vin = r.vmax >= -256 && r.vmin <= 256 * dv + 256;
-                r.ilo = ilo;
-                nmaj = (vin && ihi >= ilo) ? ihi - ilo + 1 : 0;
-            }
+        if (drawn) {
+            segment_frame(cam, g.width_m, A, B, r);
+            const uint64_t id = ((g.base + (uint64_t)bp.s) << 7) | (uint64_t)bp.j;
+            r.id_lo = (uint32_t)id;
+            r.id_hi = (uint32_t)(id >> 32);
+            const bool xm = r.flags & 1;
+            const int du = xm ? W : H, dv = xm ? H : W;
+            // columns i whose sample boxes (centre 256 i + 128, sample
+            // offsets up to kOff, half-width hc) can reach [umin, umax]
+            constexpr int32_t kOff = N == 1 ? 0 : (N == 2 ? 64 : (N == 4 ? 96 : 112));
+            const int32_t reach = kOff + r.hc;
+            int ilo = (r.umin - reach - 128 + 255) >> 8, ihi = (r.umax + reach - 128) >> 8;
+            ilo = max(ilo, 0);
+            ihi = min(ihi, du - 1);
+            const bool vin = r.vmax >= -256 && r.vmin <= 256 * dv + 256;
+            r.ilo = ilo;
+            nmaj = (vin && ihi >= ilo) ? ihi - ilo + 1 : 0;
         }
         for_each_item(rec, r, nmaj, [&](const SegRec &q, int i) {
             if (q.flags & 2)
