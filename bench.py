@@ -243,7 +243,8 @@ def measured_peaks():
 _RESOLVE_SRC = ["csrc/hm_resolve.cu", "csrc/hm_value.cuh", "csrc/hm_device.cuh", "csrc/hm_kernels.h", "../include/hm.h"]
 _ADJOINT_SRC = ["csrc/hm_backward.cu", "csrc/hm_value.cuh", "csrc/hm_device.cuh", "csrc/hm_kernels.h", "../include/hm.h"]
 KERNEL_SOURCES = {
-    "raster_kernel": ["csrc/hm_render.cu", "csrc/hm_device.cuh", "csrc/hm_kernels.h", "../include/hm.h"],
+    "raster_kernel": ["csrc/hm_render.cu", "csrc/hm_raster.cuh", "csrc/hm_device.cuh", "csrc/hm_kernels.h",
+                      "../include/hm.h"],
     "resolve_kernel": _RESOLVE_SRC, "resolve_tiles_kernel": _RESOLVE_SRC, "resolve_order_kernel": _RESOLVE_SRC,
     "resolve_decode_kernel": _RESOLVE_SRC,
     "resolve_adjoint_kernel": _ADJOINT_SRC, "geometry_adjoint_kernel": _ADJOINT_SRC,
