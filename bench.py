@@ -829,8 +829,8 @@ def run_msaa(args, rank, world, local_rank):
 
     for _ in range(args.warmup):
         one_spp()
-    out["1spp_filtered"] = statistics.mean(_timed(torch, one_spp, args.steps, flush))
-    samples = {}
+    out["1spp_filtered"] = statistics.median(_timed(torch, one_spp, args.steps, flush))
+    samples, raster = {}, {}
     for N in (2, 4, 8):
         v = vis[:N]
 
@@ -840,8 +840,20 @@ def run_msaa(args, rank, world, local_rank):
 
         for _ in range(args.warmup):
             step()
-        out[f"msaa{N}"] = statistics.mean(_timed(torch, step, args.steps, flush))
+        out[f"msaa{N}"] = statistics.median(_timed(torch, step, args.steps, flush))
         samples[f"msaa{N}"] = hm.stats_dict(stats)["covered_center"]
+        # the multisample rasterizer alone (phase events around its launch), median
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(max(args.steps, 5))]
+        for row in evs:
+            for e in row:
+                e.record()
+        for k, row in enumerate(evs):
+            flush.fill_(k)
+            hm.set_phase_events(row)
+            step()
+        hm.set_phase_events(None)
+        torch.cuda.synchronize()
+        raster[f"msaa{N}"] = statistics.median(e[2].elapsed_time(e[3]) for e in evs)
     hm.get_device_status()
     if rank != 0:
         return 0
@@ -851,7 +863,8 @@ def run_msaa(args, rank, world, local_rank):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)",
             "data": "synthetic", "config": dict(cfg, workload="single groom, 1920x1080, multisample reference"),
-            "ms_per_frame": out, "covered_samples": samples, "gpu_launches": LAUNCHES_PER_FRAME * args.steps}
+            "ms_per_frame": out, "raster_ms": raster, "covered_samples": samples,
+            "gpu_launches": LAUNCHES_PER_FRAME * args.steps}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -468,8 +468,9 @@ hm_status hm_get_tuning(hm_tuning *t);
 /* Profiling: record CUDA events (cudaEvent_t passed as void*) at phase
  * boundaries of later calls on this host thread, on the call's stream:
  * events[0] before the clear, [1] after the clear, [2] after the LOD
- * pre-pass, [3] after the rasterizer (hm_render_visibility); [4] before and
- * [5] after the resolve kernel (hm_resolve_shade).  count = 0 or events =
+ * pre-pass, [3] after the rasterizer (hm_render_visibility and its
+ * multiview, multisample and shadow-map forms); [4] before and [5] after
+ * the resolve (hm_resolve_shade, hm_resolve_msaa).  count = 0 or events =
  * NULL turns it off; a NULL entry is skipped. */
 hm_status hm_set_phase_events(void *const *events, int32_t count);
 

@@ -549,11 +549,15 @@ hm_status hm_render_shadow_map(const hm_groom *grooms, int32_t n, const hm_camer
     views.vis_a[0] = d_map_cons;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t npx = (int64_t)light_cam->width * light_cam->height;
+    phase(0, s);
     HM_CUDA(hm::launch_clear(d_map_center, d_map_cons, npx, nullptr, 1, d_stats, s), "clear");
+    phase(1, s);
     HM_CUDA(hm::launch_lod(tab, views.cam[0], d_stats, s), "lod");
+    phase(2, s);
     HM_CUDA(hm::launch_raster(tab, views, g_tuning.raster_precheck != 0, g_tuning.raster_min_blocks,
                               g_tuning.raster_ctas_per_sm, d_stats, s),
             "raster");
+    phase(3, s);
     return HM_OK;
 }
 
@@ -573,10 +577,14 @@ hm_status hm_render_visibility_msaa(const hm_groom *grooms, int32_t n, const hm_
     const int64_t npx = (int64_t)cam->width * cam->height;
     // the sample planes are contiguous: cleared as one flat array (one pointer
     // given twice, written once)
+    phase(0, s);
     HM_CUDA(hm::launch_clear(d_vis_samples, d_vis_samples, npx * samples, nullptr, clear, d_stats, s), "clear");
+    phase(1, s);
     for (int i = 0; i < n; ++i) grooms[i]->segpts_valid = false;   // until the raster has rewritten them
     HM_CUDA(hm::launch_lod(tab, cd, d_stats, s), "lod");
+    phase(2, s);
     HM_CUDA(hm::launch_raster_msaa(tab, cd, samples, d_vis_samples, d_stats, s), "raster msaa");
+    phase(3, s);
     for (int i = 0; i < n; ++i) grooms[i]->segpts_valid = true;
     return HM_OK;
 }
@@ -596,9 +604,11 @@ hm_status hm_resolve_msaa(const hm_groom *grooms, int32_t n, const hm_camera *ca
     if ((st = build_table(grooms, n, tab)) != HM_OK) return st;
     uint32_t *sw = status_word();
     if (!sw) return fail(HM_ERR_CUDA, "device status word unavailable");
+    phase(4, static_cast<cudaStream_t>(stream));
     HM_CUDA(hm::launch_resolve_msaa(tab, cam_dev(cam), ld, samples, d_vis_samples, d_rgba, sw,
                                     static_cast<cudaStream_t>(stream)),
             "resolve msaa");
+    phase(5, static_cast<cudaStream_t>(stream));
     return HM_OK;
 }
 
