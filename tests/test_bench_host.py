@@ -62,3 +62,24 @@ def test_traffic_record_follows_kernel_sources(tmp_path, monkeypatch):
     v = bench.alu_views(bench.ncu_phase(("raster_kernel",), "single_1080p"), 1e-6, {"sm_mhz": 2000.0}, 148)
     assert abs(v["issue"]["frac"] - 10.0 / 1e-6 / (148 * 4 * 2e9)) < 1e-12
     assert abs(v["fp32"]["frac"] - 4.0 / 1e-6 / (148 * 128 * 2 * 2e9)) < 1e-12
+
+
+def test_forced_tuning_skips_the_autotuner():
+    """--tuning k=v,... sets those hm_tuning fields (the binned rasterizer
+    here) without timing anything; launches per frame follow the raster mode."""
+    import argparse
+    import bench
+    from paper_2607_04230_b300 import hm
+    saved = hm.get_tuning()
+    try:
+        args = argparse.Namespace(tuning="raster_bin_w=32,raster_bin_h=16,raster_bin_chunk=1024", no_autotune=False)
+        res = bench.choose_tuning(args, None, None, 0, n=1)
+        assert res["forced"] and res["table"] == [] and res["ms"] is None
+        assert (res["tuning"]["raster_bin_w"], res["tuning"]["raster_bin_h"], res["tuning"]["raster_bin_chunk"]) == \
+            (32, 16, 1024)
+        assert bench.launches_per_frame() == bench.LAUNCHES_PER_FRAME + 3
+        hm.set_tuning(raster_bin_w=0, raster_bin_h=0, raster_bin_chunk=0)
+        assert bench.launches_per_frame() == bench.LAUNCHES_PER_FRAME
+        assert bench.choose_tuning(argparse.Namespace(tuning="", no_autotune=True), None, None, 0, n=1) is None
+    finally:
+        hm.set_tuning(**saved)
