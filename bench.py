@@ -1125,10 +1125,13 @@ def run_native(args, rank, world, local_rank):
 
     peak_rates = probe_atomic_peak(torch, hm, 2 * W * H)
 
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
-    for row in ev:              # torch creates the cudaEvent_t on first record
-        for e in row:
-            e.record()
+    # the timed steps record only their own start and end (events between a
+    # frame's kernels would keep the LOD selection from starting beside the
+    # clear); the phases are timed in a separate run below
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev:             # torch creates the cudaEvent_t on first record
+        a.record()
+        b.record()
     torch.cuda.synchronize()
     clocks = ClockSampler(_gpu_uuid(torch, local_rank))
     if world > 1:
@@ -1138,16 +1141,27 @@ def run_native(args, rank, world, local_rank):
     wall0 = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(k)
-        hm.set_phase_events(ev[k])
+        ev[k][0].record()
         step()
-    hm.set_phase_events(None)
+        ev[k][1].record()
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    frame_ms = [e[0].elapsed_time(e[5]) for e in ev]
-    phase_ms = {name: statistics.median(e[a].elapsed_time(e[b]) for e in ev)
+    frame_ms = [a.elapsed_time(b) for a, b in ev]
+    # per-phase medians of 20 more frames with events at the phase boundaries
+    pev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(20)]
+    for row in pev:
+        for e in row:
+            e.record()
+    for k, row in enumerate(pev):
+        flush.fill_(k)
+        hm.set_phase_events(row)
+        step()
+    hm.set_phase_events(None)
+    torch.cuda.synchronize()
+    phase_ms = {name: statistics.median(e[a].elapsed_time(e[b]) for e in pev)
                 for name, a, b in (("clear", 0, 1), ("lod", 1, 2), ("raster", 2, 3), ("resolve", 4, 5))}
     t_total = max_over_ranks(sum(frame_ms) * 1e-3, world)
     value = job_throughput(segs, args.steps, world, t_total)

@@ -32,6 +32,14 @@ constexpr int kBatchStride = kBatchLanes - 1;
 // batches, the rasterizer's ticket, drawn segments, drawn control points.
 enum CounterWord : int { kCtrBatches = 0, kCtrTicket = 1, kCtrSegs = 2, kCtrCps = 3, kCtrWords = 4 };
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization after `pdl_launch_dependents` has run in every CTA of the
+// kernel before it may start while that kernel still runs; `pdl_wait` blocks
+// until the preceding kernel has completed and its memory is visible (at
+// once when there is no programmatic dependency).
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Device status bits (read by hm_get_device_status).
 enum StatusBit : uint32_t { kStatusBadKey = 1u, kStatusBadBatch = 2u, kStatusBinOverflow = 4u };
 

@@ -15,9 +15,14 @@ namespace hm {
 // ---------------------------------------------------------------------------
 // clear: both layers to EMPTY or to the scene-depth pre-fill; zero the stats
 // ---------------------------------------------------------------------------
+constexpr int kClearCtasPerSm = 2;
+
 __global__ void __launch_bounds__(256) clear_kernel(ulonglong2 *vis_c, ulonglong2 *vis_a, int64_t npairs,
                                                     const uint32_t *scene_d24, int64_t npx, int do_clear,
                                                     hm_frame_stats *stats) {
+    // the LOD selection may start beside the clear (it touches neither the
+    // keys nor, until it waits for the clear, the stats)
+    pdl_launch_dependents();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0 && stats) {
         stats->strands = 0;
@@ -168,6 +173,9 @@ __global__ void __launch_bounds__(kLodSelThreads) lod_select_kernel(CallTable ta
         strands = (unsigned long long)n;
         segs = nseg;
     }
+    // launched as a programmatic dependent of the clear: the stats it zeroes
+    // are added to only after it has completed
+    pdl_wait();
     if (stats) {
         unsigned long long v[3] = {strands, segs, culled};
         unsigned long long *const dst[3] = {(unsigned long long *)&stats->strands,
@@ -530,9 +538,11 @@ cudaError_t launch_probe_atomic_min(uint64_t *buf, int64_t n, int rounds, int pa
 cudaError_t launch_clear(uint64_t *vis_c, uint64_t *vis_a, int64_t npx, const uint32_t *scene_d24, int do_clear,
                          hm_frame_stats *stats, cudaStream_t st) {
     int64_t npairs = npx / 2;
-    int sms = num_sms();
+    // a grid-stride store stream on a few CTAs per SM, leaving room for the
+    // LOD selection that runs beside it
+    const int64_t cap = (int64_t)num_sms() * kClearCtasPerSm;
     int64_t want = (npairs + 255) / 256;
-    int grid = (int)(want < (int64_t)sms * 8 ? (want > 0 ? want : 1) : (int64_t)sms * 8);
+    int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
     clear_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<ulonglong2 *>(vis_c), reinterpret_cast<ulonglong2 *>(vis_a),
                                        npairs, scene_d24, npx, do_clear, stats);
     return cudaGetLastError();
@@ -541,8 +551,19 @@ cudaError_t launch_clear(uint64_t *vis_c, uint64_t *vis_a, int64_t npx, const ui
 cudaError_t launch_lod(const CallTable &tab, const CamDev &cam, hm_frame_stats *stats, cudaStream_t st) {
     int fmax = 1;
     for (int i = 0; i < tab.n; ++i) fmax = tab.g[i].F > fmax ? tab.g[i].F : fmax;
-    const dim3 grid((unsigned)((fmax + kLodSelThreads - 1) / kLodSelThreads), (unsigned)tab.n);
-    lod_select_kernel<<<grid, kLodSelThreads, 0, st>>>(tab, cam, stats);
+    // a programmatic dependent of the clear that precedes it on the stream:
+    // it may start while the clear runs and waits for it before the stats
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((fmax + kLodSelThreads - 1) / kLodSelThreads), (unsigned)tab.n);
+    cfg.blockDim = dim3(kLodSelThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, lod_select_kernel, tab, cam, stats);
+    if (e != cudaSuccess) return e;
     uint32_t bmax = 1;
     for (int i = 0; i < tab.n; ++i) bmax = tab.g[i].max_batches > bmax ? tab.g[i].max_batches : bmax;
     const dim3 sgrid((unsigned)((bmax + kLodFillPerCta - 1) / kLodFillPerCta), (unsigned)tab.n);
