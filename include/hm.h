@@ -438,15 +438,16 @@ hm_status hm_get_device_status(void *stream);
  *                      touched key and chunk) for single-view renders with
  *                      the ID payload; multiview, compressed, multisample
  *                      and shadow-map renders keep the direct rasterizer.
- *                      Its workspace (about 88 B per segment at full detail
- *                      of the call's grooms, plus 12 B per tile) belongs to
- *                      the call's first groom, is allocated on first use and
- *                      grown by later calls, which then synchronize the
- *                      device; a call that must grow it during CUDA stream
- *                      capture returns HM_ERR_CAPACITY (render once outside
- *                      the capture).  A frame whose segment-tile pairs
- *                      exceed 8 per segment sets device status bit 4
- *                      (hm_get_device_status) and its keys are incomplete.
+ *                      Its workspace (about 91 B per control point of the
+ *                      call's grooms at full detail, plus 12 B per tile)
+ *                      belongs to the call's first groom, is allocated on
+ *                      first use and grown by later calls, which then
+ *                      synchronize the device; a call that must grow it
+ *                      during CUDA stream capture returns HM_ERR_CAPACITY
+ *                      (render once outside the capture).  A frame whose
+ *                      segment-tile pairs exceed 8 per work-list slot sets
+ *                      device status bit 4 (hm_get_device_status) and its
+ *                      keys are incomplete.
  *   raster_bin_h       16 or 32 when raster_bin_w != 0, else 0
  *   raster_bin_chunk   256 or 1024 segments per unit of the binned tile
  *                      pass when raster_bin_w != 0, else 0
