@@ -255,8 +255,11 @@ template <int TWL>
 struct TileKeys {
     unsigned long long *s_c, *s_a;
     int x0, y0;
-    __device__ __forceinline__ void operator()(int px, int py, uint64_t key, bool cen) const {
-        const int loc = ((py - y0) << TWL) | (px - x0);
+    __device__ __forceinline__ uint32_t index(int px, int py) const {
+        return ((uint32_t)(py - y0) << TWL) | (uint32_t)(px - x0);
+    }
+    __device__ __forceinline__ uint32_t step(bool x_major) const { return x_major ? (1u << TWL) : 1u; }
+    __device__ __forceinline__ void operator()(uint32_t loc, uint64_t key, bool cen) const {
         atomicMin(&s_a[loc], (unsigned long long)key);
         if (cen) atomicMin(&s_c[loc], (unsigned long long)key);
     }

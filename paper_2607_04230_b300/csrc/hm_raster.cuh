@@ -235,7 +235,8 @@ __device__ __forceinline__ uint64_t compressed_payload(const SegRec &q, float t)
 // The minor range is clipped to [mclip_lo, mclip_hi] (the frame, or one
 // screen tile of the binned rasterizer).  The incremental terms are exact
 // integers, so a pixel's key does not depend on where its range starts.
-// Each covered (pixel, layer) goes to sink(px, py, key, centre_covered).
+// Each covered (pixel, layer) goes to sink(index, key, centre_covered),
+// index = sink.index(px, py) advanced by sink.step(x_major) per minor step.
 template <typename I, bool kCgb, typename Sink>
 __device__ __forceinline__ void raster_item(const SegRec &q_shared, int i, int mclip_lo, int mclip_hi,
                                             const Sink &sink, uint32_t &n_cons, uint32_t &n_cen) {
@@ -262,15 +263,23 @@ __device__ __forceinline__ void raster_item(const SegRec &q_shared, int i, int m
     const I de = du * 256, dn = dv * 256;
     const I span = (I)abs(q.du) + (I)abs(q.dv);
     const I k_cons = span * 128, k_cen = span * (I)q.hc;
+    // minor pixels m whose centre box (half-width hc) overlaps the segment's
+    // bounding box: vmin <= 256 m + 128 + hc and vmax >= 256 m + 128 - hc,
+    // i.e. cm_lo <= m <= cm_hi (an empty range when the major extent misses)
     const bool ucen = (q.umin <= cu + q.hc) && (q.umax >= cu - q.hc);
+    const int cm_lo = ucen ? (q.vmin - 128 - q.hc + 255) >> 8 : 1;
+    const int cm_hi = ucen ? (q.vmax - 128 + q.hc) >> 8 : 0;
     const uint64_t id = ((uint64_t)q.id_hi << 32) | q.id_lo;
     const bool degenerate = (q.du == 0 && q.dv == 0);
     typedef typename std::make_unsigned<I>::type U;
-    for (int m = mlo; m <= mhi; ++m, e0 += de, num += dn) {
-        const int32_t cv = 256 * m + 128;
+    // the sink's index of pixel (i, mlo) in the major / minor frame, and its
+    // step along the minor axis
+    uint32_t at = xm ? sink.index(i, mlo) : sink.index(mlo, i);
+    const uint32_t step = sink.step(xm);
+    for (int m = mlo; m <= mhi; ++m, e0 += de, num += dn, at += step) {
         // conservative line test |e0| <= k_cons (the overlaps hold by the row range)
         if ((U)(e0 + k_cons) > (U)(2 * k_cons)) continue;
-        const bool cen = ucen && q.vmin <= cv + q.hc && q.vmax >= cv - q.hc && (U)(e0 + k_cen) <= (U)(2 * k_cen);
+        const bool cen = m >= cm_lo && m <= cm_hi && (U)(e0 + k_cen) <= (U)(2 * k_cen);
         float t = 0.0f;
         if (!degenerate) {
             const float fn = sizeof(I) == 4 ? __int2float_rn((int32_t)num) : __ll2float_rn((int64_t)num);
@@ -282,7 +291,7 @@ __device__ __forceinline__ void raster_item(const SegRec &q_shared, int i, int m
         const uint64_t key = ((uint64_t)d24 << 40) | (kCgb ? compressed_payload(q, t) : id);
         n_cons += 1;
         n_cen += cen;
-        sink(xm ? i : m, xm ? m : i, key, cen);
+        sink(at, key, cen);
     }
 }
 
@@ -328,8 +337,12 @@ struct GlobalKeys {
     uint64_t *vis_c;
     uint64_t *vis_a;
     uint32_t W;
-    __device__ __forceinline__ void operator()(int px, int py, uint64_t key, bool cen) const {
-        const uint32_t p = (uint32_t)py * W + (uint32_t)px;   // < 2^28 pixels
+    __device__ __forceinline__ uint32_t index(int px, int py) const {
+        return (uint32_t)py * W + (uint32_t)px;   // < 2^28 pixels
+    }
+    // x-major items walk a column (a row of W keys per step), y-major ones a row
+    __device__ __forceinline__ uint32_t step(bool x_major) const { return x_major ? W : 1u; }
+    __device__ __forceinline__ void operator()(uint32_t p, uint64_t key, bool cen) const {
         unsigned long long *a = reinterpret_cast<unsigned long long *>(vis_a + p);
         unsigned long long *c = reinterpret_cast<unsigned long long *>(vis_c + p);
         if (!kPrecheck || key < __ldcg(a)) atomicMin(a, (unsigned long long)key);
