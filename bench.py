@@ -92,7 +92,7 @@ def make_scene(name):
 # ---------------------------------------------------------------------------
 class _Nvml:
     """The few read-only NVML queries the clock record needs, through ctypes
-    on the driver's libnvidia-ml (no Python binding is needed on the box)."""
+    on the NVIDIA driver's libnvidia-ml.so.1 (no Python NVML binding needed)."""
     CLOCK_SM = 1
 
     def __init__(self, uuid: str):
