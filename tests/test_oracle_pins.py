@@ -1246,3 +1246,64 @@ def test_depth_mismatch_blend_closed_form():
     assert out[fc.px(near_px), 3] == e[3] == dec["HcG"][fc.px(near_px)] / dec["HaG"][fc.px(near_px)]
     for x in range(x0 - 1, x1 + 2):
         np.testing.assert_allclose(out[fc.px(x)], fc.expected_row_pixel(x, vc, va, cols), rtol=1e-12, atol=1e-15)
+
+
+def test_strand_roots_uniform_over_the_triangle_chi_square():
+    """Roots (Sec. 2: strands placed by barycentric coordinates on the base
+    mesh) are uniform over each triangle: the sqrt(r1) map gives density 2
+    over {b1, b2 >= 0, b1 + b2 <= 1}.  Counts over the 64 congruent
+    sub-triangles of a three-level midpoint subdivision pass a chi-square
+    test, each barycentric coordinate is Beta(1, 2) distributed, and strands
+    are sorted by face (bundle-contiguous) with every coordinate in range."""
+    from scipy import stats
+    g = synth.make_groom(11, 8, 1, 4, 0.05, 200_000, 8)
+    b1 = g.strand_bary[:, 0].astype(np.float64)
+    b2 = g.strand_bary[:, 1].astype(np.float64)
+    b0 = 1.0 - b1 - b2
+    assert np.all(np.diff(g.strand_face.astype(np.int64)) >= 0)
+    assert np.all((b1 >= 0) & (b2 >= 0) & (b0 >= -1e-6))
+    # sub-triangle of a point at level 3: at each level the point lies in the
+    # corner triangle of vertex i when coordinate i exceeds 1/2 (new
+    # coordinates 2c with c_i -> 2 c_i - 1), else in the middle one, whose
+    # vertices are the edge midpoints (new coordinates 1 - 2c)
+    cell = np.zeros(b1.size, np.int64)
+    c = np.stack([b0, b1, b2], 1)
+    for _ in range(3):
+        big = c > 0.5
+        corner = np.where(big.any(1), big.argmax(1), 3)
+        nxt = 1.0 - 2.0 * c
+        rows = np.nonzero(corner < 3)[0]
+        nxt[rows] = 2.0 * c[rows]
+        nxt[rows, corner[rows]] -= 1.0
+        c = nxt
+        cell = cell * 4 + corner
+    counts = np.bincount(cell, minlength=64)
+    assert counts.size == 64
+    chi2, p = stats.chisquare(counts)
+    assert p > 1e-3, (chi2, p)
+    for x in (b0, b1, b2):
+        assert stats.kstest(x, stats.beta(1, 2).cdf).pvalue > 1e-3
+
+
+def test_resolved_frame_alpha_in_unit_interval_and_zero_outside_coverage():
+    """Over a whole oracle frame: alpha in [0, 1], colour finite and
+    non-negative, exactly zero wherever the conservative layer is empty, and
+    positive on every centre pixel (Sec. 3.3.3: alpha is a ratio of strip
+    counts H_center / H_cons with H_cons >= H_center)."""
+    sc = synth.tiny_scene(31, width=96, height=72, num_strands=400)
+    lods = oracle.lods_for(sc)
+    vc, va, _ = oracle.raster(sc.grooms, sc.camera, lods)
+    dec = oracle.resolve_decisions(sc.grooms, sc.camera, lods, sc.filt, vc, va)
+    gts = [v64.GroomT(g, l[1], b) for g, l, b in zip(sc.grooms, lods, oracle.strand_bases(sc.grooms))]
+    rgba, pix = v64.resolve(gts, sc.camera, sc.lights, sc.filt, vc, va, dec)
+    img = v64.full_image(rgba, pix, sc.camera.width, sc.camera.height).numpy().reshape(-1, 4)
+    covered = (va & oracle.PAYLOAD_MASK) != oracle.PAYLOAD_MASK
+    assert covered.sum() > 100
+    assert np.all(np.isfinite(img))
+    assert np.all((img[:, 3] >= 0.0) & (img[:, 3] <= 1.0))
+    assert np.all(img[:, :3] >= 0.0)
+    assert np.all(img[~covered] == 0.0)
+    # a centre pixel counts itself in its strip (H_center >= 1); a promoted
+    # pixel without a contributing neighbour is (0, 0, 0, 0)
+    centre = (vc & oracle.PAYLOAD_MASK) != oracle.PAYLOAD_MASK
+    assert np.all(img[centre, 3] > 0.0)
