@@ -387,6 +387,18 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+def host_cpu_model():
+    """The host CPU's model name (Linux /proc/cpuinfo), or None."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def cpu_baseline(scene, max_segments: int = 2_000_000):
     """The oracle on the workload itself when it has at most max_segments
     strand segments (the 1080p groom: the whole frame, a few seconds on the
@@ -399,7 +411,7 @@ def cpu_baseline(scene, max_segments: int = 2_000_000):
     oracle_frame_sample(scene, 1000)              # warm-up (library load, thread pool)
     segs, dt = oracle_frame_sample(scene, every)
     what = "the whole workload" if every == 1 else f"every {every}th strand of every groom"
-    return {"value": segs / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+    return {"value": segs / dt, "unit": UNIT, "cores": host_cores(), "cpu_model": host_cpu_model(), "kind": "oracle",
             "sample": f"{what} ({segs} segments, one frame) rasterized by the C oracle "
                       f"(OpenMP, all host threads) and resolved by the FP64 torch oracle, {dt:.1f} s"}
 
@@ -440,7 +452,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 decisions + f64 values",
             "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": host_cores(), "cpu_model": host_cpu_model(),
+                             "kind": "oracle",
                              "sample": f"each step: every {every}th strand (rotating offset) of the workload, "
                                        f"C oracle raster + FP64 torch resolve"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -1272,6 +1285,7 @@ def run_native(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
             "config": dict(cfg, parallelism=f"replicas x{world}"),
             "frame_ms": {k: round(v, 5) for k, v in phase_ms.items()},
+            "frame_ms_median": statistics.median(frame_ms),
             "segments_per_frame": segs, "raster_segments_per_s": segs / (phase_ms["raster"] * 1e-3),
             "lod_raster_segments_per_s": segs / ((phase_ms["lod"] + phase_ms["raster"]) * 1e-3),
             "roofline": roofline, "kernels": kernels,
