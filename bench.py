@@ -38,6 +38,8 @@ L2_FLUSH_BYTES = 256 << 20
 # kernels of one frame: clear, LOD select, LOD scan (work list), raster, resolve
 LAUNCHES_PER_FRAME = 5
 BIN_FIELDS = ("raster_bin_w", "raster_bin_h", "raster_bin_chunk")
+KEY_LAYOUTS = {"row": 0, "block": 1}          # the library's HM_KEYS_ROW_MAJOR, HM_KEYS_BLOCK_2X2
+KEY_LAYOUT_NAMES = {0: "row-major [H][W]", 1: "2x2 blocks (one 32-byte sector per block)"}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 FALLBACK_HBM_GBS = 6400.0
@@ -59,6 +61,9 @@ def parse():
                          "raster_bin_w=32,raster_bin_h=32,raster_bin_chunk=1024 for the binned rasterizer")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--key-layout", choices=["block", "row"], default="block",
+                    help="key layer layout of the single_1080p and crowd_4k frames: 2 x 2 blocks (the faster "
+                         "raster, default) or row-major [H][W]; the resolved RGBA is the same either way")
     return ap.parse_args()
 
 
@@ -554,7 +559,8 @@ def run_crowd(args, rank, world, local_rank):
     build.build()
     torch.cuda.set_device(local_rank)
     scene, cfg = make_scene("crowd_4k")
-    cr = crowd.Crowd(scene)
+    layout = KEY_LAYOUTS[args.key_layout]
+    cr = crowd.Crowd(scene, key_layout=layout)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     cr.render_batched()
     torch.cuda.synchronize()
@@ -603,13 +609,16 @@ def run_crowd(args, rank, world, local_rank):
     atomics = st["covered_cons"] + st["covered_center"]
     ms_g = tg / args.steps * 1e3
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    kernels, roofline = frame_roofline(atomics, phase_ms, W, H, peak_rates, args.workload, clk, sms)
+    # the committed ncu counters of this workload in this key layout
+    traffic_key = args.workload + ("_block" if layout == KEY_LAYOUTS["block"] else "")
+    kernels, roofline = frame_roofline(atomics, phase_ms, W, H, peak_rates, traffic_key, clk, sms)
     frame = frame_bound(kernels, phase_ms, W, H, statistics.median(t_graph))
     ms_pc, ms_pcg = statistics.median(t_pc), statistics.median(t_pcg)
     line = {"metric": METRIC, "value": job_throughput(segs, args.steps, world, tg), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_g, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
-            "config": dict(cfg, parallelism=f"replicas x{world}", batching="one render + one resolve call over "
+            "config": dict(cfg, parallelism=f"replicas x{world}", key_layout=KEY_LAYOUT_NAMES[layout],
+                           batching="one render + one resolve call over "
                            "all grooms, replayed as a CUDA graph"),
             "strands_after_lod": st["strands"], "segments_per_frame": segs, "covered_pairs": atomics,
             "frame_ms_phases": phase_ms, "roofline": roofline, "kernels": kernels, "frame_roofline": frame,
@@ -1118,8 +1127,12 @@ def run_native(args, rank, world, local_rank):
     scene, cfg = make_scene(args.workload)
     grooms = hm.upload_scene(scene)
     W, H = scene.camera.width, scene.camera.height
-    # the resolve's tile list: occupied tiles heaviest first on a persistent grid
-    frame = hm.Frame(W, H, tile_list=True)
+    # the resolve's tile list: occupied tiles heaviest first on a persistent grid;
+    # the key layers in the chosen layout (the default workload's frames in
+    # 2 x 2 blocks)
+    layout = KEY_LAYOUTS[args.key_layout] if args.workload in ("single_1080p", "single_1080p_ao") else 0
+    frame = hm.Frame(W, H, tile_list=True, key_layout=layout)
+    fcam = frame.camera(scene.camera)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -1232,8 +1245,8 @@ def run_native(args, rank, world, local_rank):
                 comp.wait_event(uploaded[k])
                 for hg, d in zip(grooms, d_lv2[k % 2]):
                     hg.update_layer_verts(d)                # this step's inputs
-                hm.render_visibility(grooms, scene.camera, frame.vis_center, frame.vis_cons, stats=frame.stats)
-                hm.resolve_shade(grooms, scene.camera, scene.lights, scene.filt, frame.vis_center, frame.vis_cons,
+                hm.render_visibility(grooms, fcam, frame.vis_center, frame.vis_cons, stats=frame.stats)
+                hm.resolve_shade(grooms, fcam, scene.lights, scene.filt, frame.vis_center, frame.vis_cons,
                                  rgba2[k % 2], tile_scratch=frame.tile_scratch)
                 done[k].record(comp)
                 upload(k + 1)                               # the next step's inputs, on the upload stream
@@ -1279,11 +1292,13 @@ def run_native(args, rank, world, local_rank):
     if rank != 0:
         return 0
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    kernels, roofline = frame_roofline(atomics, phase_ms, W, H, peak_rates, args.workload, clk, sms)
+    # the committed ncu counters of this workload in this key layout
+    traffic_key = args.workload + ("_block" if layout == KEY_LAYOUTS["block"] else "")
+    kernels, roofline = frame_roofline(atomics, phase_ms, W, H, peak_rates, traffic_key, clk, sms)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (u64 visibility keys)", "data": "synthetic",
-            "config": dict(cfg, parallelism=f"replicas x{world}"),
+            "config": dict(cfg, parallelism=f"replicas x{world}", key_layout=KEY_LAYOUT_NAMES[layout]),
             "frame_ms": {k: round(v, 5) for k, v in phase_ms.items()},
             "frame_ms_median": statistics.median(frame_ms),
             "segments_per_frame": segs, "raster_segments_per_s": segs / (phase_ms["raster"] * 1e-3),

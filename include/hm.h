@@ -95,14 +95,37 @@ typedef struct {
 } hm_groom_desc;
 
 /* Pinhole camera: clip = view_proj * (x, y, z, 1), row-major; clip.w is the
- * view-axis depth in metres.  Pixels: x right, y down, centres at +0.5. */
+ * view-axis depth in metres.  Pixels: x right, y down, centres at +0.5.
+ *
+ * key_layout: the layout of this camera's two-layer key buffers (the
+ * visibility layers and shadow maps; the RGBA image is always row-major
+ * [height][width] float4):
+ *   HM_KEYS_ROW_MAJOR (0): key of pixel (x, y) at y * width + x;
+ *   HM_KEYS_BLOCK_2X2 (1): 2 x 2 pixel blocks of four keys, one 32-byte
+ *     sector each, the blocks row-major over ceil(width / 2) block columns:
+ *     pixel (x, y) at ((y / 2) * ceil(width / 2) + x / 2) * 4
+ *     + (y % 2) * 2 + x % 2.  The rasterizer's atomics then share sectors
+ *     (neighbouring lanes reach the two rows or columns of a block), which
+ *     the L2 atomic unit serves as one operation.
+ * A key buffer holds hm_vis_buffer_keys(cam) keys; the blocked layout pads
+ * odd sizes, and its padding keys stay EMPTY.  The multisample calls take
+ * row-major sample planes only. */
 typedef struct {
     float view_proj[16];
     float cam_pos[3];
     float near_m, far_m;
     float tan_half_fovy;
     int32_t width, height;
+    int32_t key_layout;
 } hm_camera;
+
+#define HM_KEYS_ROW_MAJOR 0
+#define HM_KEYS_BLOCK_2X2 1
+
+/* Keys in one key layer of a frame of this camera (width * height row-major,
+ * 4 * ceil(width / 2) * ceil(height / 2) in 2 x 2 blocks), 0 for an invalid
+ * size or layout.  No device call. */
+size_t hm_vis_buffer_keys(const hm_camera *cam);
 
 /* LOD of Sec. 3.2: enabled = 0 draws every strand at C_max control points. */
 typedef struct {
@@ -112,9 +135,9 @@ typedef struct {
 
 /* A shadow map of one light (Sec. 3.4 queries shadow/opacity maps with the
  * depth correction of Sec. 3.2 "Depth Comparison Artifact Fix").
- * d_map: [cam.height][cam.width] uint64 keys, the conservative layer of
- * hm_render_shadow_map with the same camera (device memory, caller's, read
- * only).  A shaded point X is projected with cam like a strand control point
+ * d_map: hm_vis_buffer_keys(&cam) uint64 keys in cam's key layout, the
+ * conservative layer of hm_render_shadow_map with the same camera (device
+ * memory, caller's, read only).  A shaded point X is projected with cam like a strand control point
  * (16.8 snap); its texel is (floor(X/256), floor(Y/256)).  With z_map the
  * texel's 24-bit depth / 2^24 and w the point's view depth in the light's
  * camera, the light reaching X is
@@ -219,8 +242,10 @@ hm_status hm_update_albedo(hm_groom g, const float *d_albedo, void *stream);
  * groom, not to the frame: resolve (or differentiate) a frame before the same
  * grooms are rendered for another camera.
  *
- * d_vis_center, d_vis_cons: [height][width] uint64, 8-byte aligned.
- * d_scene_d24: [height][width] uint32 (24-bit depth) or NULL.
+ * d_vis_center, d_vis_cons: hm_vis_buffer_keys(cam) uint64 each, in the
+ * camera's key layout, 16-byte aligned.
+ * d_scene_d24: [height][width] uint32 (24-bit depth, row-major in every
+ * layout) or NULL.
  * d_stats: one hm_frame_stats or NULL.
  * Errors: HM_ERR_INVALID_ARG (n out of 1..HM_MAX_GROOMS_PER_CALL, null or
  * misaligned buffers, resolution out of range, near/far invalid),
@@ -286,7 +311,8 @@ hm_status hm_resolve_compressed(const hm_camera *cam, const hm_lights *lights, c
 /* Shadow map for hm_shadow_map: every groom of grooms[0..n) at full detail
  * (LOD off whatever hm_set_lod holds, no culling: the full geometry set of
  * Sec. 3.2's depth fix), seen from light_cam, into d_map_center /
- * d_map_cons ([H][W] uint64 each, 16-byte aligned, cleared first); the
+ * d_map_cons (hm_vis_buffer_keys(light_cam) uint64 each, in light_cam's
+ * key layout, 16-byte aligned, cleared first); the
  * conservative layer is the map.  Uses per-groom LOD buffers of its own, so
  * the LOD state of the camera's render is left as it was (the two may run
  * on different streams).  Errors as hm_render_visibility. */

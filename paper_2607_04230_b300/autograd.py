@@ -33,6 +33,7 @@ class HairRender(torch.autograd.Function):
         groom.update_albedo(alb)
         hm.render([groom], scene, frame, shadows=shadows)
         ctx.groom, ctx.scene, ctx.shadows = groom, scene, shadows
+        ctx.cam = frame.camera(scene.camera)      # with the frame's key layout
         ctx.vis = (frame.vis_center.clone(), frame.vis_cons.clone())
         ctx.inputs = (lv.clone(), alb.clone())
         ctx.lv_shape, ctx.alb_shape = layer_verts.shape, albedo.shape
@@ -49,7 +50,7 @@ class HairRender(torch.autograd.Function):
             ctx.groom.update_layer_verts(ctx.inputs[0])
             ctx.groom.update_albedo(ctx.inputs[1])
             vc, va = torch.empty_like(ctx.vis[0]), torch.empty_like(ctx.vis[1])
-            hm.render_visibility([ctx.groom], sc.camera, vc, va)
+            hm.render_visibility([ctx.groom], ctx.cam, vc, va)
             ctx.groom.last_forward = ctx.fid
         glv = torch.zeros(ctx.lv_shape, dtype=torch.float32, device=dev)
         galb = torch.zeros(ctx.alb_shape, dtype=torch.float32, device=dev)
@@ -59,7 +60,7 @@ class HairRender(torch.autograd.Function):
         if g.data_ptr() % 16:
             # the adjoint reads float4 rows: a view at an unaligned offset is copied
             g = g.clone(memory_format=torch.contiguous_format)
-        hm.shade_backward([ctx.groom], sc.camera, sc.lights, sc.filt, ctx.vis[0], ctx.vis[1],
+        hm.shade_backward([ctx.groom], ctx.cam, sc.lights, sc.filt, ctx.vis[0], ctx.vis[1],
                           g, [glv], [galb], scratch, shadows=ctx.shadows)
         return glv, galb, None, None, None, None
 

@@ -14,13 +14,13 @@ from . import hm
 
 
 class Crowd:
-    def __init__(self, scene, stream=None):
+    def __init__(self, scene, stream=None, key_layout: int = hm.KEYS_ROW_MAJOR):
         import torch
         self.scene = scene
         self.grooms = hm.upload_scene(scene, stream=stream)
         # a crowd covers a small part of the frame: the resolve lists its
         # occupied tiles first
-        self.frame = hm.Frame(scene.camera.width, scene.camera.height, tile_list=True)
+        self.frame = hm.Frame(scene.camera.width, scene.camera.height, tile_list=True, key_layout=key_layout)
         self.graph = None
         self.graph_pc = None
         self._torch = torch
@@ -63,7 +63,8 @@ class Crowd:
     # -- one call per groom ------------------------------------------------
     def render_per_character(self):
         sc, fr = self.scene, self.frame
+        cam = fr.camera(sc.camera)
         for i in range(len(self.grooms)):
-            hm.render_visibility_range(self.grooms, i, 1, sc.camera, fr.vis_center, fr.vis_cons, clear=(i == 0))
-        hm.resolve_shade(self.grooms, sc.camera, sc.lights, sc.filt, fr.vis_center, fr.vis_cons, fr.rgba,
+            hm.render_visibility_range(self.grooms, i, 1, cam, fr.vis_center, fr.vis_cons, clear=(i == 0))
+        hm.resolve_shade(self.grooms, cam, sc.lights, sc.filt, fr.vis_center, fr.vis_cons, fr.rgba,
                          tile_scratch=fr.tile_scratch)

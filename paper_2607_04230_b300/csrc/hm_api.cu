@@ -95,7 +95,18 @@ hm_status check_camera(const hm_camera *cam) {
         return fail(HM_ERR_INVALID_ARG, "need 0 < near < far");
     if (!(cam->tan_half_fovy > 0.0f) || !std::isfinite(cam->tan_half_fovy))
         return fail(HM_ERR_INVALID_ARG, "tan_half_fovy must be positive");
+    if (cam->key_layout != HM_KEYS_ROW_MAJOR && cam->key_layout != HM_KEYS_BLOCK_2X2)
+        return fail(HM_ERR_INVALID_ARG, "key_layout must be HM_KEYS_ROW_MAJOR or HM_KEYS_BLOCK_2X2");
     return HM_OK;
+}
+
+// Keys in one key layer of the camera's frames (row-major, or 2 x 2 blocks
+// with odd sizes padded); 0 for an invalid size or layout.
+int64_t vis_keys(const hm_camera *c) {
+    if (!c || c->width < 1 || c->height < 1) return 0;
+    if (c->key_layout == HM_KEYS_ROW_MAJOR) return (int64_t)c->width * c->height;
+    if (c->key_layout == HM_KEYS_BLOCK_2X2) return 4 * (int64_t)((c->width + 1) / 2) * ((c->height + 1) / 2);
+    return 0;
 }
 
 hm::CamDev cam_dev(const hm_camera *c) {
@@ -107,6 +118,8 @@ hm::CamDev cam_dev(const hm_camera *c) {
     d.tan_half = c->tan_half_fovy;
     d.W = c->width;
     d.H = c->height;
+    d.layout = c->key_layout;
+    d.Wb = (c->width + 1) / 2;
     return d;
 }
 
@@ -451,8 +464,9 @@ static hm_status render_views(const hm_groom *grooms, int32_t n, int32_t first, 
     hm_status st;
     for (int v = 0; v < n_views; ++v) {
         if ((st = check_camera(&cams[v])) != HM_OK) return st;
-        if (cams[v].width != cams[0].width || cams[v].height != cams[0].height)
-            return fail(HM_ERR_INVALID_ARG, "views must share width and height");
+        if (cams[v].width != cams[0].width || cams[v].height != cams[0].height ||
+            cams[v].key_layout != cams[0].key_layout)
+            return fail(HM_ERR_INVALID_ARG, "views must share width, height and key layout");
         uint64_t *vc = d_vis_center[v], *va = d_vis_cons[v];
         if (!vc || !va) return fail(HM_ERR_INVALID_ARG, "visibility buffer is NULL");
         if ((reinterpret_cast<uintptr_t>(vc) & 15) || (reinterpret_cast<uintptr_t>(va) & 15))
@@ -482,7 +496,7 @@ static hm_status render_views(const hm_groom *grooms, int32_t n, int32_t first, 
         views.vis_a[v] = d_vis_cons[v];
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int64_t npx = (int64_t)cams[0].width * cams[0].height;
+    const int64_t nkeys = vis_keys(&cams[0]);
     const bool binned = g_tuning.raster_bin_w != 0 && n_views == 1 && !compressed;
     void *bin_ws = nullptr;
     uint64_t bin_slots = 0;
@@ -499,8 +513,8 @@ static hm_status render_views(const hm_groom *grooms, int32_t n, int32_t first, 
     }
     phase(0, s);
     for (int v = 0; v < n_views; ++v)
-        HM_CUDA(hm::launch_clear(d_vis_center[v], d_vis_cons[v], npx, d_scene_d24 ? d_scene_d24[v] : nullptr, clear,
-                                 v == 0 ? d_stats : nullptr, s),
+        HM_CUDA(hm::launch_clear(d_vis_center[v], d_vis_cons[v], nkeys, d_scene_d24 ? d_scene_d24[v] : nullptr,
+                                 views.cam[v], clear, v == 0 ? d_stats : nullptr, s),
                 "clear");
     phase(1, s);
     for (int i = 0; i < count; ++i) grooms[first + i]->segpts_valid = false;   // until the raster has rewritten them
@@ -548,9 +562,9 @@ hm_status hm_render_shadow_map(const hm_groom *grooms, int32_t n, const hm_camer
     views.vis_c[0] = d_map_center;
     views.vis_a[0] = d_map_cons;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int64_t npx = (int64_t)light_cam->width * light_cam->height;
     phase(0, s);
-    HM_CUDA(hm::launch_clear(d_map_center, d_map_cons, npx, nullptr, 1, d_stats, s), "clear");
+    HM_CUDA(hm::launch_clear(d_map_center, d_map_cons, vis_keys(light_cam), nullptr, views.cam[0], 1, d_stats, s),
+            "clear");
     phase(1, s);
     HM_CUDA(hm::launch_lod(tab, views.cam[0], d_stats, s), "lod");
     phase(2, s);
@@ -565,6 +579,7 @@ hm_status hm_render_visibility_msaa(const hm_groom *grooms, int32_t n, const hm_
                                     uint64_t *d_vis_samples, int32_t clear, hm_frame_stats *d_stats, void *stream) {
     hm_status st = check_camera(cam);
     if (st != HM_OK) return st;
+    if (cam->key_layout != HM_KEYS_ROW_MAJOR) return fail(HM_ERR_INVALID_ARG, "sample planes are row-major");
     if (samples != 1 && samples != 2 && samples != 4 && samples != 8)
         return fail(HM_ERR_INVALID_ARG, "samples must be 1, 2, 4 or 8");
     if (!d_vis_samples || (reinterpret_cast<uintptr_t>(d_vis_samples) & 15))
@@ -578,7 +593,7 @@ hm_status hm_render_visibility_msaa(const hm_groom *grooms, int32_t n, const hm_
     // the sample planes are contiguous: cleared as one flat array (one pointer
     // given twice, written once)
     phase(0, s);
-    HM_CUDA(hm::launch_clear(d_vis_samples, d_vis_samples, npx * samples, nullptr, clear, d_stats, s), "clear");
+    HM_CUDA(hm::launch_clear(d_vis_samples, d_vis_samples, npx * samples, nullptr, cd, clear, d_stats, s), "clear");
     phase(1, s);
     for (int i = 0; i < n; ++i) grooms[i]->segpts_valid = false;   // until the raster has rewritten them
     HM_CUDA(hm::launch_lod(tab, cd, d_stats, s), "lod");
@@ -593,6 +608,7 @@ hm_status hm_resolve_msaa(const hm_groom *grooms, int32_t n, const hm_camera *ca
                           int32_t samples, const uint64_t *d_vis_samples, float *d_rgba, void *stream) {
     hm_status st = check_camera(cam);
     if (st != HM_OK) return st;
+    if (cam->key_layout != HM_KEYS_ROW_MAJOR) return fail(HM_ERR_INVALID_ARG, "sample planes are row-major");
     if (samples != 1 && samples != 2 && samples != 4 && samples != 8)
         return fail(HM_ERR_INVALID_ARG, "samples must be 1, 2, 4 or 8");
     if (!d_vis_samples || !d_rgba || (reinterpret_cast<uintptr_t>(d_rgba) & 15) ||
@@ -831,6 +847,11 @@ hm_status hm_get_device_status(void *stream) {
 }  // extern "C"
 
 extern "C" {
+
+size_t hm_vis_buffer_keys(const hm_camera *cam) {
+    if (!cam || cam->width > HM_MAX_RESOLUTION || cam->height > HM_MAX_RESOLUTION) return 0;
+    return (size_t)vis_keys(cam);
+}
 
 size_t hm_backward_scratch_bytes(int32_t width, int32_t height) {
     if (width < 1 || height < 1) return 0;

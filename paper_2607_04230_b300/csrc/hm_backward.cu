@@ -442,9 +442,9 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
         int dg = -(1 << 30);                 // far below any d24: the depth test alone rejects it
         uint8_t fa = 0;
         if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-            const int64_t p = (int64_t)gy * W + gx;
-            const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + p));
-            const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + p));
+            const uint32_t kp = key_index(cam, gx, gy);
+            const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + kp));
+            const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + kp));
             if (!key_empty(kg)) {
                 dg = (int)(kg >> 40);
                 s_list[atomicAdd(&s_count, 1)] = (uint16_t)i;
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
         const int i = s_list[li];
         const int lx = i % sw, ly = i / sw;
         const int gx = x0 - R + lx, gy = y0 - R + ly;
-        const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + (int64_t)gy * W + gx));
+        const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + key_index(cam, gx, gy)));
         const Decoded d = decode_key(tab, s_bases, cam, kg, gx, gy, status);
         float3 c = f3(0.f, 0.f, 0.f);
         if (d.ok) {
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
     uint64_t ka = kEmptyKey;
     int dA = -1;
     if (inside) {
-        ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx));
+        ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + key_index(cam, gx, gy)));
         if (fp.enabled && !key_empty(ka)) {
             dA = (int)(ka >> 40);
             const int dgP = dg_at(mid);
@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(kResolveThreads, 2) resolve_adjoint_kernel(
     for (int li = tid; li < nA; li += kResolveThreads) {
         const int t = s_list[li];
         const int px = x0 + t % kTileW, py = y0 + t / kTileW;
-        const uint64_t k = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)py * W + px));
+        const uint64_t k = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + key_index(cam, px, py)));
         const Decoded d = decode_key(tab, s_bases, cam, k, px, py, status);
         s_tsA[t] = make_float2(d.tsx, d.tsy);
         s_isoA[t] = d.iso;
@@ -683,10 +683,11 @@ __global__ void __launch_bounds__(kGeoThreads, kGeoMinBlocks) geometry_adjoint_k
             if (p < npx) {
                 const float4 gc = __ldg(&dC[p]);
                 const float4 gt = __ldg(&dTs[p]);
+                const uint32_t kp = key_index(cam, (int)(p % cam.W), (int)(p / cam.W));
                 jg = (gc.x != 0.f || gc.y != 0.f || gc.z != 0.f || gt.x != 0.f || gt.y != 0.f) &&
-                     !key_empty(__ldg(reinterpret_cast<const unsigned long long *>(vis_c + p)));
+                     !key_empty(__ldg(reinterpret_cast<const unsigned long long *>(vis_c + kp)));
                 ja = (gt.z != 0.f || gt.w != 0.f) &&
-                     !key_empty(__ldg(reinterpret_cast<const unsigned long long *>(vis_a + p)));
+                     !key_empty(__ldg(reinterpret_cast<const unsigned long long *>(vis_a + kp)));
             }
 #pragma unroll
             for (int layer = 0; layer < 2; ++layer) {
@@ -705,7 +706,8 @@ __global__ void __launch_bounds__(kGeoThreads, kGeoMinBlocks) geometry_adjoint_k
             const bool cons = (e & 0x8000) != 0;
             const int64_t p = q0 + (e & 0x7FFF);
             const int px = (int)(p % cam.W), py = (int)(p / cam.W);
-            const uint64_t key = __ldg(reinterpret_cast<const unsigned long long *>((cons ? vis_a : vis_c) + p));
+            const uint64_t key =
+                __ldg(reinterpret_cast<const unsigned long long *>((cons ? vis_a : vis_c) + key_index(cam, px, py)));
             const Decoded d = decode_key(tab, s_bases, cam, key, px, py, status);
             if (!d.ok) continue;
             const GroomDev &g = tab.g[d.gi];
@@ -814,7 +816,7 @@ cudaError_t launch_resolve_adjoint(const CallTable &tab, const CamDev &cam, cons
                                                       adjoint_smem_bytes(HM_MAX_FILTER_RADIUS));
         return (per_sm > 0 ? per_sm : 1) * sms;
     });
-    cudaError_t e = launch_tile_list(vis_a, nullptr, cam.W, cam.H, kTileH, list, st);
+    cudaError_t e = launch_tile_list(vis_a, nullptr, cam, kTileH, list, st);
     if (e != cudaSuccess) return e;
     const int ntiles = ((cam.W + kTileW - 1) / kTileW) * ((cam.H + kTileH - 1) / kTileH);
     resolve_adjoint_kernel<<<resident < ntiles ? resident : ntiles, kResolveThreads, adjoint_smem_bytes(R), st>>>(

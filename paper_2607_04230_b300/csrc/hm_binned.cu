@@ -258,7 +258,7 @@ struct TileKeys {
     __device__ __forceinline__ uint32_t index(int px, int py) const {
         return ((uint32_t)(py - y0) << TWL) | (uint32_t)(px - x0);
     }
-    __device__ __forceinline__ uint32_t step(bool x_major) const { return x_major ? (1u << TWL) : 1u; }
+    __device__ __forceinline__ uint32_t step(bool x_major, bool) const { return x_major ? (1u << TWL) : 1u; }
     __device__ __forceinline__ void operator()(uint32_t loc, uint64_t key, bool cen) const {
         atomicMin(&s_a[loc], (unsigned long long)key);
         if (cen) atomicMin(&s_c[loc], (unsigned long long)key);
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kRasterThreads, 4) bin_tile_kernel(CamDev cam,
         for (int k = threadIdx.x; k < NPX; k += kRasterThreads) {
             const int px = x0 + (k & (TW - 1)), py = y0 + (k >> TWL);
             if (px > x1 || py > y1) continue;
-            const size_t p = (size_t)py * (size_t)W + (size_t)px;
+            const uint32_t p = key_index(cam, px, py);
             const unsigned long long a = s_a[k], c = s_c[k];
             if (a != kEmptyKey) atomicMin(reinterpret_cast<unsigned long long *>(vis_a + p), a);
             if (c != kEmptyKey) atomicMin(reinterpret_cast<unsigned long long *>(vis_c + p), c);

@@ -83,7 +83,18 @@ struct CamDev {
     float cam_pos[3];
     float near_m, far_m, tan_half;
     int32_t W, H;
+    int32_t layout;    // key layout: HM_KEYS_ROW_MAJOR or HM_KEYS_BLOCK_2X2
+    int32_t Wb;        // block columns of the 2 x 2 layout, ceil(W / 2)
 };
+
+// Index of pixel (x, y)'s key in one of the camera's key layers: row-major,
+// or 2 x 2 blocks of four keys (one 32-byte sector) row-major over Wb block
+// columns.  x < W, y < H: below hm_vis_buffer_keys(cam) < 2^30.
+__device__ __forceinline__ uint32_t key_index(const CamDev &c, int x, int y) {
+    if (c.layout == HM_KEYS_ROW_MAJOR) return (uint32_t)y * (uint32_t)c.W + (uint32_t)x;
+    return ((((uint32_t)y >> 1) * (uint32_t)c.Wb + ((uint32_t)x >> 1)) << 2) | (((uint32_t)y & 1u) << 1) |
+           ((uint32_t)x & 1u);
+}
 
 // The views of one rasterizer launch: the strands are assembled once and
 // projected into each view's pair of key layers (all views share W, H).

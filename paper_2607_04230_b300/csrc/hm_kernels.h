@@ -78,8 +78,10 @@ class PerDevice {
 
 int num_sms();
 
-cudaError_t launch_clear(uint64_t *vis_c, uint64_t *vis_a, int64_t npx, const uint32_t *scene_d24, int do_clear,
-                         hm_frame_stats *stats, cudaStream_t st);
+// Both key layers (nkeys keys each, in cam's key layout) to EMPTY or to the
+// scene-depth pre-fill (row-major [H][W] scene_d24, or null); zeroes stats.
+cudaError_t launch_clear(uint64_t *vis_c, uint64_t *vis_a, int64_t nkeys, const uint32_t *scene_d24, const CamDev &cam,
+                         int do_clear, hm_frame_stats *stats, cudaStream_t st);
 cudaError_t launch_lod(const CallTable &tab, const CamDev &cam, hm_frame_stats *stats, cudaStream_t st);
 cudaError_t launch_raster(const CallTable &tab, const ViewSet &views, bool precheck, int min_blocks, int ctas_per_sm,
                           hm_frame_stats *stats, cudaStream_t st, bool compressed = false);
@@ -106,7 +108,8 @@ size_t resolve_scratch_bytes(int W, int H);
 // per-tile conservative key counts (zero-filling keyless tiles of rgba when it
 // is given), then list[0] = occupied tiles, list[1] = 0, list[2 ..] = them,
 // heaviest first.
-cudaError_t launch_tile_list(const uint64_t *vis_a, float4 *rgba, int W, int H, int th, int *list, cudaStream_t st);
+cudaError_t launch_tile_list(const uint64_t *vis_a, float4 *rgba, const CamDev &cam, int th, int *list,
+                             cudaStream_t st);
 cudaError_t launch_resolve_adjoint(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                                    const uint64_t *vis_c, const uint64_t *vis_a, const float *grad_rgba,
                                    float *const *glv, float *const *galb, void *scratch, uint32_t *status,

@@ -236,7 +236,8 @@ __device__ __forceinline__ uint64_t compressed_payload(const SegRec &q, float t)
 // screen tile of the binned rasterizer).  The incremental terms are exact
 // integers, so a pixel's key does not depend on where its range starts.
 // Each covered (pixel, layer) goes to sink(index, key, centre_covered),
-// index = sink.index(px, py) advanced by sink.step(x_major) per minor step.
+// index = sink.index(px, py) advanced per minor step by
+// sink.step(x_major, minor coordinate odd).
 template <typename I, bool kCgb, typename Sink>
 __device__ __forceinline__ void raster_item(const SegRec &q_shared, int i, int mclip_lo, int mclip_hi,
                                             const Sink &sink, uint32_t &n_cons, uint32_t &n_cen) {
@@ -273,10 +274,10 @@ __device__ __forceinline__ void raster_item(const SegRec &q_shared, int i, int m
     const bool degenerate = (q.du == 0 && q.dv == 0);
     typedef typename std::make_unsigned<I>::type U;
     // the sink's index of pixel (i, mlo) in the major / minor frame, and its
-    // step along the minor axis
+    // step to the next minor pixel from an even or an odd minor coordinate
     uint32_t at = xm ? sink.index(i, mlo) : sink.index(mlo, i);
-    const uint32_t step = sink.step(xm);
-    for (int m = mlo; m <= mhi; ++m, e0 += de, num += dn, at += step) {
+    const uint32_t step_even = sink.step(xm, false), step_odd = sink.step(xm, true);
+    for (int m = mlo; m <= mhi; at += (m & 1) ? step_odd : step_even, ++m, e0 += de, num += dn) {
         // conservative line test |e0| <= k_cons (the overlaps hold by the row range)
         if ((U)(e0 + k_cons) > (U)(2 * k_cons)) continue;
         const bool cen = m >= cm_lo && m <= cm_hi && (U)(e0 + k_cen) <= (U)(2 * k_cen);
@@ -329,19 +330,26 @@ __device__ __forceinline__ void for_each_item(SegRec *rec, SegRec &r, int nmaj, 
     __syncwarp();
 }
 
-// Sink of the direct rasterizer: 64-bit atomicMin into the two [H][W] key
-// layers; with kPrecheck the key is read first and atomics that cannot
-// lower it are skipped.
-template <bool kPrecheck>
+// Sink of the direct rasterizer: 64-bit atomicMin into the two key layers,
+// row-major [H][W] or (kBlocked) in 2 x 2 blocks over Wb block columns (the
+// index of key_index); with kPrecheck the key is read first and atomics that
+// cannot lower it are skipped.
+template <bool kPrecheck, bool kBlocked>
 struct GlobalKeys {
     uint64_t *vis_c;
     uint64_t *vis_a;
-    uint32_t W;
+    uint32_t W, Wb;
     __device__ __forceinline__ uint32_t index(int px, int py) const {
-        return (uint32_t)py * W + (uint32_t)px;   // < 2^28 pixels
+        if (!kBlocked) return (uint32_t)py * W + (uint32_t)px;   // < 2^28 pixels
+        return ((((uint32_t)py >> 1) * Wb + ((uint32_t)px >> 1)) << 2) | (((uint32_t)py & 1u) << 1) |
+               ((uint32_t)px & 1u);
     }
-    // x-major items walk a column (a row of W keys per step), y-major ones a row
-    __device__ __forceinline__ uint32_t step(bool x_major) const { return x_major ? W : 1u; }
+    // x-major items walk down a column, y-major ones along a row; in 2 x 2
+    // blocks an even coordinate steps within its block, an odd one to the next
+    __device__ __forceinline__ uint32_t step(bool x_major, bool odd) const {
+        if (!kBlocked) return x_major ? W : 1u;
+        return x_major ? (odd ? 4u * Wb - 2u : 2u) : (odd ? 3u : 1u);
+    }
     __device__ __forceinline__ void operator()(uint32_t p, uint64_t key, bool cen) const {
         unsigned long long *a = reinterpret_cast<unsigned long long *>(vis_a + p);
         unsigned long long *c = reinterpret_cast<unsigned long long *>(vis_c + p);

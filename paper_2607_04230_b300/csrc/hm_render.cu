@@ -17,9 +17,25 @@ namespace hm {
 // ---------------------------------------------------------------------------
 constexpr int kClearCtasPerSm = 2;
 
+// Pre-fill key of key slot k of a key layer in layout (W, H, layout, Wb):
+// the scene depth of its pixel, or EMPTY for the padding of the blocked
+// layout.  scene_d24 is row-major [H][W].
+__device__ __forceinline__ uint64_t prefill_key(const uint32_t *scene_d24, const CamDev &c, int64_t k) {
+    int64_t p = k;
+    if (c.layout != HM_KEYS_ROW_MAJOR) {
+        const int64_t b = k >> 2;
+        const int x = (int)(b % c.Wb) * 2 + (int)(k & 1), y = (int)(b / c.Wb) * 2 + (int)((k >> 1) & 1);
+        if (x >= c.W || y >= c.H) return kEmptyKey;
+        p = (int64_t)y * c.W + x;
+    }
+    return ((uint64_t)(scene_d24[p] & 0xFFFFFFu) << 40) | kPayloadMask;
+}
+
+// nkeys keys per layer (npairs = nkeys / 2 whole 16-byte pairs); cam gives
+// the pre-fill's pixel of each key.
 __global__ void __launch_bounds__(256) clear_kernel(ulonglong2 *vis_c, ulonglong2 *vis_a, int64_t npairs,
-                                                    const uint32_t *scene_d24, int64_t npx, int do_clear,
-                                                    hm_frame_stats *stats) {
+                                                    const uint32_t *scene_d24, int64_t nkeys, CamDev cam,
+                                                    int do_clear, hm_frame_stats *stats) {
     // the LOD selection may start beside the clear (it touches neither the
     // keys nor, until it waits for the clear, the stats)
     pdl_launch_dependents();
@@ -32,20 +48,19 @@ __global__ void __launch_bounds__(256) clear_kernel(ulonglong2 *vis_c, ulonglong
         stats->covered_cons = 0;
     }
     if (!do_clear) return;
-    // npairs = npx / 2 whole 16-byte pairs; an odd last pixel is written alone
-    if (i == 0 && (npx & 1)) {
-        const int64_t p = npx - 1;
-        const uint64_t v = scene_d24 ? (((uint64_t)(scene_d24[p] & 0xFFFFFFu) << 40) | kPayloadMask) : kEmptyKey;
-        reinterpret_cast<uint64_t *>(vis_c)[p] = v;
-        reinterpret_cast<uint64_t *>(vis_a)[p] = v;
+    // an odd last key is written alone
+    if (i == 0 && (nkeys & 1)) {
+        const int64_t k = nkeys - 1;
+        const uint64_t v = scene_d24 ? prefill_key(scene_d24, cam, k) : kEmptyKey;
+        reinterpret_cast<uint64_t *>(vis_c)[k] = v;
+        reinterpret_cast<uint64_t *>(vis_a)[k] = v;
     }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (; i < npairs; i += stride) {
         ulonglong2 v;
         if (scene_d24) {
-            const int64_t p = 2 * i;
-            v.x = ((uint64_t)(scene_d24[p] & 0xFFFFFFu) << 40) | kPayloadMask;
-            v.y = ((uint64_t)(scene_d24[p + 1] & 0xFFFFFFu) << 40) | kPayloadMask;
+            v.x = prefill_key(scene_d24, cam, 2 * i);
+            v.y = prefill_key(scene_d24, cam, 2 * i + 1);
         } else {
             v.x = kEmptyKey;
             v.y = kEmptyKey;
@@ -272,8 +287,9 @@ __global__ void __launch_bounds__(kLodScanThreads) lod_scan_kernel(CallTable tab
 // exact predicate and issues the 64-bit atomicMin for each layer.
 // ---------------------------------------------------------------------------
 // kMode: 0 one view, 1 several views (strands assembled once), 2 one view
-// with the compressed payload.
-template <bool kPrecheck, int kMinBlocks, int kMode>
+// with the compressed payload.  kBlocked: the views' key layers are in 2 x 2
+// blocks (HM_KEYS_BLOCK_2X2), else row-major.
+template <bool kPrecheck, int kMinBlocks, int kMode, bool kBlocked>
 __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(CallTable tab, ViewSet views,
                                                                             hm_frame_stats *stats) {
     constexpr bool kMulti = kMode == 1, kCgb = kMode == 2;
@@ -335,7 +351,8 @@ __global__ void __launch_bounds__(kRasterThreads, kMinBlocks) raster_kernel(Call
             int ihi, mlo, mhi;
             if (segment_pixel_box(r, xm ? W : H, xm ? H : W, r.ilo, ihi, mlo, mhi)) nmaj = ihi - r.ilo + 1;
         }
-        const GlobalKeys<kPrecheck> sink{views.vis_c[view], views.vis_a[view], (uint32_t)W};
+        const GlobalKeys<kPrecheck, kBlocked> sink{views.vis_c[view], views.vis_a[view], (uint32_t)W,
+                                                   (uint32_t)cam.Wb};
         for_each_item(rec, r, nmaj, [&](const SegRec &q, int i) {
             const int mmax = (q.flags & 1) ? H - 1 : W - 1;
             if (q.flags & 2)
@@ -535,16 +552,16 @@ cudaError_t launch_probe_atomic_min(uint64_t *buf, int64_t n, int rounds, int pa
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_clear(uint64_t *vis_c, uint64_t *vis_a, int64_t npx, const uint32_t *scene_d24, int do_clear,
-                         hm_frame_stats *stats, cudaStream_t st) {
-    int64_t npairs = npx / 2;
+cudaError_t launch_clear(uint64_t *vis_c, uint64_t *vis_a, int64_t nkeys, const uint32_t *scene_d24, const CamDev &cam,
+                         int do_clear, hm_frame_stats *stats, cudaStream_t st) {
+    int64_t npairs = nkeys / 2;
     // a grid-stride store stream on a few CTAs per SM, leaving room for the
     // LOD selection that runs beside it
     const int64_t cap = (int64_t)num_sms() * kClearCtasPerSm;
     int64_t want = (npairs + 255) / 256;
     int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
     clear_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<ulonglong2 *>(vis_c), reinterpret_cast<ulonglong2 *>(vis_a),
-                                       npairs, scene_d24, npx, do_clear, stats);
+                                       npairs, scene_d24, nkeys, cam, do_clear, stats);
     return cudaGetLastError();
 }
 
@@ -575,35 +592,44 @@ cudaError_t launch_lod(const CallTable &tab, const CamDev &cam, hm_frame_stats *
 // (min resident CTAs per SM of 256 threads: 3 -> up to 80 registers,
 // 4 -> 64).  The persistent grid is ctas_per_sm CTAs per SM, capped at what
 // fits (0 = as many as fit).
-template <bool P, int M, int V>
+template <bool P, int M, int V, bool B>
 static int raster_fit_per_sm() {
     static PerDevice<int> fit;
     const int v = fit.get([](int) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<P, M, V>, kRasterThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, raster_kernel<P, M, V, B>, kRasterThreads, 0);
         return per_sm;
     });
     return v < 1 ? 1 : v;
 }
 
-template <bool P, int M, int V>
+template <bool P, int M, int V, bool B>
 static cudaError_t launch_raster_v(const CallTable &tab, const ViewSet &views, int ctas_per_sm, hm_frame_stats *stats,
                                    cudaStream_t st) {
-    const int fit = raster_fit_per_sm<P, M, V>();
+    const int fit = raster_fit_per_sm<P, M, V, B>();
     const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < fit) ? ctas_per_sm : fit;
-    raster_kernel<P, M, V><<<per_sm * num_sms(), kRasterThreads, 0, st>>>(tab, views, stats);
+    raster_kernel<P, M, V, B><<<per_sm * num_sms(), kRasterThreads, 0, st>>>(tab, views, stats);
     return cudaGetLastError();
+}
+
+template <int V, bool B>
+static cudaError_t launch_raster_layout(const CallTable &tab, const ViewSet &views, bool precheck, int min_blocks,
+                                        int ctas_per_sm, hm_frame_stats *stats, cudaStream_t st) {
+    const bool m3 = min_blocks == 3;
+    if (precheck)
+        return m3 ? launch_raster_v<true, 3, V, B>(tab, views, ctas_per_sm, stats, st)
+                  : launch_raster_v<true, 4, V, B>(tab, views, ctas_per_sm, stats, st);
+    return m3 ? launch_raster_v<false, 3, V, B>(tab, views, ctas_per_sm, stats, st)
+              : launch_raster_v<false, 4, V, B>(tab, views, ctas_per_sm, stats, st);
 }
 
 template <int V>
 static cudaError_t launch_raster_views(const CallTable &tab, const ViewSet &views, bool precheck, int min_blocks,
                                        int ctas_per_sm, hm_frame_stats *stats, cudaStream_t st) {
-    const bool m3 = min_blocks == 3;
-    if (precheck)
-        return m3 ? launch_raster_v<true, 3, V>(tab, views, ctas_per_sm, stats, st)
-                  : launch_raster_v<true, 4, V>(tab, views, ctas_per_sm, stats, st);
-    return m3 ? launch_raster_v<false, 3, V>(tab, views, ctas_per_sm, stats, st)
-              : launch_raster_v<false, 4, V>(tab, views, ctas_per_sm, stats, st);
+    // every view of a launch shares the key layout (checked by the caller)
+    if (views.cam[0].layout == HM_KEYS_BLOCK_2X2)
+        return launch_raster_layout<V, true>(tab, views, precheck, min_blocks, ctas_per_sm, stats, st);
+    return launch_raster_layout<V, false>(tab, views, precheck, min_blocks, ctas_per_sm, stats, st);
 }
 
 cudaError_t launch_raster(const CallTable &tab, const ViewSet &views, bool precheck, int min_blocks, int ctas_per_sm,

@@ -53,8 +53,9 @@ __device__ __forceinline__ float4 centre_result(int R, const int *s_dg, const ui
 // lane = column, rows walked.
 template <int kFwdTileH>
 __global__ void __launch_bounds__(256) resolve_tiles_kernel(const uint64_t *__restrict__ vis_a,
-                                                            float4 *__restrict__ rgba, int W, int H, int ntx,
+                                                            float4 *__restrict__ rgba, CamDev cam, int ntx,
                                                             int ntiles, int *__restrict__ weights) {
+    const int W = cam.W, H = cam.H;
     const int tile = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (tile >= ntiles) return;
     const int gx = (tile % ntx) * kFwdTileW + lane, y0 = (tile / ntx) * kFwdTileH;
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(256) resolve_tiles_kernel(const uint64_t *__re
     int cnt = 0;
     if (gx < W)
         for (int y = y0; y < y1; ++y)
-            cnt += !key_empty(__ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)y * W + gx)));
+            cnt += !key_empty(__ldg(reinterpret_cast<const unsigned long long *>(vis_a + key_index(cam, gx, y))));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
     if (lane == 0) weights[tile] = cnt;
@@ -153,9 +154,9 @@ __global__ void __launch_bounds__(kDecThreads, 4) resolve_decode_kernel(CallTabl
             const int gx = x0 + t % kFwdTileW, gy = y0 + t / kFwdTileW;
             bool gP = false, needA = false;
             if (gx < W && gy < H) {
-                const int64_t p = (int64_t)gy * W + gx;
-                const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + p));
-                const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + p));
+                const uint32_t kp = key_index(cam, gx, gy);
+                const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + kp));
+                const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + kp));
                 gP = !key_empty(kg);
                 needA = !key_empty(ka) && fp.enabled && (!gP || (int)(ka >> 40) + fp.dmis <= (int)(kg >> 40));
             }
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(kDecThreads, 4) resolve_decode_kernel(CallTabl
             const int gx = x0 + t % kFwdTileW, gy = y0 + t / kFwdTileW;
             const int64_t p = (int64_t)gy * W + gx;
             const uint64_t key =
-                __ldg(reinterpret_cast<const unsigned long long *>((cen ? vis_c : vis_a) + p));
+                __ldg(reinterpret_cast<const unsigned long long *>((cen ? vis_c : vis_a) + key_index(cam, gx, gy)));
             const Decoded d = decode_key(tab, s_bases, cam, key, gx, gy, status);
             if (cen) {
                 float3 c = make_float3(0.f, 0.f, 0.f);
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
             const int gx = x0 + t % kFwdTileW, gy = y0 + t / kFwdTileW;
             if (gx < W && gy < H)
                 any |= !key_empty(
-                    __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx)));
+                    __ldg(reinterpret_cast<const unsigned long long *>(vis_a + key_index(cam, gx, gy))));
         }
         if (!__syncthreads_or(any)) {
             for (int t = tid; t < kFwdTilePx; t += kFwdThreads) {
@@ -291,8 +292,9 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
         uint8_t fa = 0;
         if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
             const int64_t p = (int64_t)gy * W + gx;
-            const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + p));
-            const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + p));
+            const uint32_t kp = key_index(cam, gx, gy);
+            const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + kp));
+            const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + kp));
             float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
             if (!key_empty(kg)) {
                 dg = (int)(kg >> 40);
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
         const int i = s_list[li];
         const int lx = i % sw, ly = i / sw;
         const int gx = x0 - R + lx, gy = y0 - R + ly;
-        const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + (int64_t)gy * W + gx));
+        const uint64_t kg = __ldg(reinterpret_cast<const unsigned long long *>(vis_c + key_index(cam, gx, gy)));
         float3 c = make_float3(0.f, 0.f, 0.f);
         float tsx, tsy;
         bool iso;
@@ -388,7 +390,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
         const bool gP = dgP >= 0, aP = in && s_fa[mid] != 0;
         bool needA = false;
         if (aP && fp.enabled) {
-            const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx));
+            const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + key_index(cam, gx, gy)));
             needA = dgP < 0 || (int)(ka >> 40) + fp.dmis <= dgP;
         }
         const bool gOnly = gP && !needA;
@@ -435,7 +437,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) resolve_kernel(CallTable tab, 
             const int t = s_list[li - ng];
             const int tx = t % kFwdTileW, ty = t / kFwdTileW;
             const int gx = x0 + tx, gy = y0 + ty;
-            const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + (int64_t)gy * W + gx));
+            const uint64_t ka = __ldg(reinterpret_cast<const unsigned long long *>(vis_a + key_index(cam, gx, gy)));
             float tsx, tsy;
             bool iso;
             if (kPre) {
@@ -592,13 +594,15 @@ static int resolve_max_tiles(int W, int H) { return ((W + kFwdTileW - 1) / kFwdT
 // list[0], list[1], the ordered tile list, then one key count per tile.
 size_t resolve_list_bytes(int W, int H) { return sizeof(int) * (2 + 2 * (size_t)resolve_max_tiles(W, H)); }
 
-cudaError_t launch_tile_list(const uint64_t *vis_a, float4 *rgba, int W, int H, int th, int *list, cudaStream_t st) {
+cudaError_t launch_tile_list(const uint64_t *vis_a, float4 *rgba, const CamDev &cam, int th, int *list,
+                             cudaStream_t st) {
+    const int W = cam.W, H = cam.H;
     const int ntx = (W + kFwdTileW - 1) / kFwdTileW, ntiles = ntx * ((H + th - 1) / th);
     int *weights = list + 2 + resolve_max_tiles(W, H);
     if (th == 16)
-        resolve_tiles_kernel<16><<<(ntiles + 7) / 8, 256, 0, st>>>(vis_a, rgba, W, H, ntx, ntiles, weights);
+        resolve_tiles_kernel<16><<<(ntiles + 7) / 8, 256, 0, st>>>(vis_a, rgba, cam, ntx, ntiles, weights);
     else
-        resolve_tiles_kernel<32><<<(ntiles + 7) / 8, 256, 0, st>>>(vis_a, rgba, W, H, ntx, ntiles, weights);
+        resolve_tiles_kernel<32><<<(ntiles + 7) / 8, 256, 0, st>>>(vis_a, rgba, cam, ntx, ntiles, weights);
     resolve_order_kernel<<<1, 1024, 0, st>>>(weights, ntiles, kFwdTileW * th, list);
     return cudaGetLastError();
 }
@@ -641,7 +645,7 @@ static cudaError_t launch_resolve_t(const CallTable &tab, const CamDev &cam, con
         return cudaGetLastError();
     }
     const int ntiles = (int)(grid.x * grid.y);
-    cudaError_t e = launch_tile_list(vis_a, out, cam.W, cam.H, TH, tile_list, st);
+    cudaError_t e = launch_tile_list(vis_a, out, cam, TH, tile_list, st);
     if (e != cudaSuccess) return e;
     if (C) {
         const int resident = resolve_resident<TH, C, false>();

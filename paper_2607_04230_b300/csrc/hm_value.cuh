@@ -49,7 +49,7 @@ __device__ __forceinline__ float shadow_visibility(const ShadowDev &m, float3 X,
     if (!P.valid) return 1.0f;
     const int32_t tx = P.X >> 8, ty = P.Y >> 8;
     if (tx < 0 || ty < 0 || tx >= m.cam.W || ty >= m.cam.H) return 1.0f;
-    const uint64_t key = __ldg(reinterpret_cast<const unsigned long long *>(m.map) + (int64_t)ty * m.cam.W + tx);
+    const uint64_t key = __ldg(reinterpret_cast<const unsigned long long *>(m.map) + key_index(m.cam, tx, ty));
     if (key_empty(key)) return 1.0f;
     const float zmap = (float)(uint32_t)(key >> 40) * (1.0f / 16777216.0f);
     const float d = (P.w - m.cam.near_m) - zmap * (m.cam.far_m - m.cam.near_m) - m.bias;

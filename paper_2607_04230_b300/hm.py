@@ -43,7 +43,10 @@ class GroomDesc(ctypes.Structure):
 class Camera(ctypes.Structure):
     _fields_ = [("view_proj", ctypes.c_float * 16), ("cam_pos", ctypes.c_float * 3), ("near_m", ctypes.c_float),
                 ("far_m", ctypes.c_float), ("tan_half_fovy", ctypes.c_float), ("width", ctypes.c_int32),
-                ("height", ctypes.c_int32)]
+                ("height", ctypes.c_int32), ("key_layout", ctypes.c_int32)]
+
+
+KEYS_ROW_MAJOR, KEYS_BLOCK_2X2 = 0, 1
 
 
 class LodParams(ctypes.Structure):
@@ -135,6 +138,9 @@ def lib():
         L.hm_backward_scratch_bytes.restype = ctypes.c_size_t
         L.hm_resolve_scratch_bytes.argtypes = [i32, i32]
         L.hm_resolve_scratch_bytes.restype = ctypes.c_size_t
+    if hasattr(L, "hm_vis_buffer_keys"):
+        L.hm_vis_buffer_keys.argtypes = [P]
+        L.hm_vis_buffer_keys.restype = ctypes.c_size_t
     L.hm_status_string.argtypes = [ctypes.c_int]
     L.hm_status_string.restype = ctypes.c_char_p
     L.hm_last_error.argtypes = []
@@ -178,7 +184,30 @@ def camera_struct(cam) -> Camera:
         c.cam_pos[i] = float(np.float32(cam.cam_pos[i]))
     c.near_m, c.far_m, c.tan_half_fovy = cam.near, cam.far, cam.tan_half_fovy
     c.width, c.height = cam.width, cam.height
+    c.key_layout = int(getattr(cam, "key_layout", KEYS_ROW_MAJOR))
     return c
+
+
+def vis_buffer_keys(width: int, height: int, key_layout: int = KEYS_ROW_MAJOR) -> int:
+    """Keys in one key layer (hm_vis_buffer_keys)."""
+    c = Camera()
+    c.width, c.height, c.key_layout = width, height, key_layout
+    return int(lib().hm_vis_buffer_keys(ctypes.byref(c)))
+
+
+def key_layout_index(width: int, height: int, key_layout: int) -> np.ndarray:
+    """[height * width] index of each row-major pixel's key in a layer of
+    the given layout (the identity for row-major)."""
+    y, x = np.divmod(np.arange(width * height, dtype=np.int64), width)
+    if key_layout == KEYS_ROW_MAJOR:
+        return y * width + x
+    wb = (width + 1) // 2
+    return (((y >> 1) * wb + (x >> 1)) << 2) | ((y & 1) << 1) | (x & 1)
+
+
+def keys_row_major(keys: np.ndarray, width: int, height: int, key_layout: int) -> np.ndarray:
+    """A key layer of the given layout as row-major [height * width] keys."""
+    return keys[key_layout_index(width, height, key_layout)]
 
 
 def lights_struct(lights, shadows=None) -> Lights:
@@ -459,13 +488,18 @@ def get_device_status(stream=None):
 class Frame:
     """Device buffers of one frame: two key layers, RGBA, counters."""
 
-    def __init__(self, width: int, height: int, device="cuda", tile_list: bool = False):
-        """tile_list: hold the resolve's tile-list scratch (sparse frames)."""
+    def __init__(self, width: int, height: int, device="cuda", tile_list: bool = False,
+                 key_layout: int = KEYS_ROW_MAJOR):
+        """tile_list: hold the resolve's tile-list scratch (sparse frames);
+        key_layout: the layout of the two key layers (render() and the
+        other Frame-level calls give the camera this layout)."""
         import torch
-        npx = width * height
-        self.width, self.height = width, height
-        self.vis_center = torch.empty(npx, dtype=torch.int64, device=device)
-        self.vis_cons = torch.empty(npx, dtype=torch.int64, device=device)
+        nkeys = vis_buffer_keys(width, height, key_layout)
+        if nkeys <= 0:
+            raise ValueError("invalid frame size or key layout")
+        self.width, self.height, self.key_layout = width, height, key_layout
+        self.vis_center = torch.empty(nkeys, dtype=torch.int64, device=device)
+        self.vis_cons = torch.empty(nkeys, dtype=torch.int64, device=device)
         self.rgba = torch.empty((height, width, 4), dtype=torch.float32, device=device)
         self.stats = torch.zeros(8, dtype=torch.int64, device=device)
         self.tile_scratch = None
@@ -474,14 +508,28 @@ class Frame:
                                             device=device)
 
     def keys_numpy(self):
-        return (self.vis_center.cpu().numpy().view(np.uint64), self.vis_cons.cpu().numpy().view(np.uint64))
+        """Both key layers as row-major [height * width] uint64 (whatever the layout)."""
+        out = []
+        for t in (self.vis_center, self.vis_cons):
+            k = t.cpu().numpy().view(np.uint64)
+            out.append(k if self.key_layout == KEYS_ROW_MAJOR else
+                       keys_row_major(k, self.width, self.height, self.key_layout))
+        return tuple(out)
+
+    def camera(self, cam):
+        """cam with this frame's key layout."""
+        if int(getattr(cam, "key_layout", KEYS_ROW_MAJOR)) == self.key_layout:
+            return cam
+        import dataclasses
+        return dataclasses.replace(cam, key_layout=self.key_layout)
 
 
 def render(grooms, scene, frame: Frame, stream=None, shadows=None):
     """Visibility + resolve of one frame (both on the current stream);
-    shadows as for lights_struct."""
-    render_visibility(grooms, scene.camera, frame.vis_center, frame.vis_cons, stats=frame.stats, stream=stream)
-    resolve_shade(grooms, scene.camera, scene.lights, scene.filt, frame.vis_center, frame.vis_cons, frame.rgba,
+    shadows as for lights_struct.  The camera takes the frame's key layout."""
+    cam = frame.camera(scene.camera)
+    render_visibility(grooms, cam, frame.vis_center, frame.vis_cons, stats=frame.stats, stream=stream)
+    resolve_shade(grooms, cam, scene.lights, scene.filt, frame.vis_center, frame.vis_cons, frame.rgba,
                   stream=stream, shadows=shadows, tile_scratch=frame.tile_scratch)
 
 

@@ -83,6 +83,7 @@ class Camera:
     tan_half_fovy: float
     width: int
     height: int
+    key_layout: int = 0          # key buffers: 0 row-major, 1 in 2 x 2 blocks (the library's HM_KEYS_*)
 
 
 @dataclass

@@ -93,6 +93,13 @@ def test_render_and_resolve_reject_bad_arguments(L):
     bad = hm.camera_struct(sc.camera)
     bad.far_m = bad.near_m
     assert L.hm_render_visibility(grooms, 1, ctypes.byref(bad), fake, fake, None, 1, None, None) == INVALID
+    bad = hm.camera_struct(sc.camera)
+    bad.key_layout = 2
+    assert L.hm_render_visibility(grooms, 1, ctypes.byref(bad), fake, fake, None, 1, None, None) == INVALID
+    # multisample sample planes are row-major only
+    blocked = hm.camera_struct(sc.camera)
+    blocked.key_layout = hm.KEYS_BLOCK_2X2
+    assert L.hm_render_visibility_msaa(grooms, 1, ctypes.byref(blocked), 4, fake, 1, None, None) == INVALID
     assert L.hm_render_visibility(grooms, 1, ctypes.byref(cam), None, fake, None, 1, None, None) == INVALID
     assert L.hm_render_visibility(grooms, 1, ctypes.byref(cam), ctypes.c_void_p((1 << 20) + 8), fake, None, 1,
                                   None, None) == INVALID
@@ -249,3 +256,21 @@ def test_resolve_scratch_and_probe_arguments(L):
         assert L.hm_probe_atomic_min(fake, 16, 1, pattern, None) == INVALID
     assert L.hm_probe_atomic_min(fake, 0, 1, 0, None) == INVALID
     assert L.hm_probe_atomic_min(fake, 16, 0, 0, None) == INVALID
+
+
+def test_key_buffer_sizes_per_layout(L):
+    """hm_vis_buffer_keys: width * height row-major; 4 ceil(w/2) ceil(h/2) in
+    2 x 2 blocks (odd sizes padded); 0 for an invalid layout or size.  The
+    host-side index map is a bijection onto the blocked buffer's in-frame slots."""
+    import numpy as np
+    for w, h in ((1920, 1080), (203, 117), (1, 1), (2, 3), (16384, 16384)):
+        assert hm.vis_buffer_keys(w, h, hm.KEYS_ROW_MAJOR) == w * h
+        assert hm.vis_buffer_keys(w, h, hm.KEYS_BLOCK_2X2) == 4 * ((w + 1) // 2) * ((h + 1) // 2)
+    assert hm.vis_buffer_keys(64, 64, 2) == 0 and hm.vis_buffer_keys(0, 64, 0) == 0
+    assert hm.vis_buffer_keys(16385, 8, 0) == 0
+    for w, h in ((7, 5), (8, 6), (33, 2)):
+        idx = hm.key_layout_index(w, h, hm.KEYS_BLOCK_2X2)
+        assert len(np.unique(idx)) == w * h and idx.max() < hm.vis_buffer_keys(w, h, hm.KEYS_BLOCK_2X2)
+        # a 2 x 2 block of pixels fills one 32-byte sector (four consecutive keys)
+        assert sorted(idx[[0, 1, w, w + 1]]) == [0, 1, 2, 3]
+        assert np.array_equal(hm.key_layout_index(w, h, hm.KEYS_ROW_MAJOR), np.arange(w * h))
