@@ -1304,6 +1304,7 @@ def run_native(args, rank, world, local_rank):
             "segments_per_frame": segs, "raster_segments_per_s": segs / (phase_ms["raster"] * 1e-3),
             "lod_raster_segments_per_s": segs / ((phase_ms["lod"] + phase_ms["raster"]) * 1e-3),
             "roofline": roofline, "kernels": kernels,
+            "frame_roofline": frame_bound(kernels, phase_ms, W, H, statistics.median(frame_ms)),
             "e2e": e2e, "gpu_launches": (launches_per_frame() + 3) * args.steps,   # + the tile-list count and order passes and the decode pass
             "clocks": clk, "wall_s": wall,
             "autotune": tune and {"tuning": tune["tuning"], "best_ms": tune["ms"], "candidates": len(tune["table"]),
