@@ -509,6 +509,18 @@ hm_status hm_set_phase_events(void *const *events, int32_t count);
  * are overwritten.  16-byte aligned, n >= 1. */
 hm_status hm_probe_atomic_min(uint64_t *d_buf, int64_t n, int32_t rounds, int32_t pattern, void *stream);
 
+/* Arithmetic probe, not part of rendering: d_out[i] = the binary32 quotient
+ * d_num[i] / d_den[i] exactly as the rasterizers form the depth parameter of
+ * a candidate pixel (Sec. 3.1.2: numerator and |B - A|^2 as floats, one
+ * reciprocal per segment, the correctly rounded quotient from it), so tests
+ * can compare it with IEEE round-to-nearest division bit for bit.  Device
+ * arrays of n floats (n >= 0; n = 0 launches nothing, NULL pointers allowed
+ * then); 1 <= d_den[i] < 2^63 and d_num[i] = 0 or 1 <= |d_num[i]| < 2^63,
+ * the range the rasterizers use (their numerators and denominators are
+ * integers); outside it the values are unspecified (no error).  Errors:
+ * HM_ERR_INVALID_ARG for n < 0 or a NULL array with n > 0. */
+hm_status hm_probe_quotient(const float *d_num, const float *d_den, float *d_out, int64_t n, void *stream);
+
 const char *hm_status_string(hm_status s);
 const char *hm_last_error(void);
 

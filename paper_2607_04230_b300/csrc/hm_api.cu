@@ -805,6 +805,12 @@ hm_status hm_probe_atomic_min(uint64_t *d_buf, int64_t n, int32_t rounds, int32_
     return HM_OK;
 }
 
+hm_status hm_probe_quotient(const float *d_num, const float *d_den, float *d_out, int64_t n, void *stream) {
+    if (n < 0 || (n > 0 && (!d_num || !d_den || !d_out))) return fail(HM_ERR_INVALID_ARG, "bad probe arguments");
+    HM_CUDA(hm::launch_probe_quotient(d_num, d_den, d_out, n, static_cast<cudaStream_t>(stream)), "probe");
+    return HM_OK;
+}
+
 hm_status hm_get_lod(hm_groom g, int32_t *n_lod, int32_t *c, void *stream) {
     if (!g || !n_lod || !c) return fail(HM_ERR_INVALID_ARG, "NULL argument");
     std::vector<uint4> h(g->F);

@@ -325,6 +325,7 @@ __global__ void __launch_bounds__(kRasterThreads, 4) bin_tile_kernel(CamDev cam,
                 r.zA = q.zA;
                 r.dz = q.dz;
                 r.fden = q.fden;
+                r.rden = __frcp_rn(q.fden);
                 r.slope = q.slope;
                 r.hc = q.hc;
                 r.flags = q.flags;

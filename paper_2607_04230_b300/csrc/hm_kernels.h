@@ -96,6 +96,7 @@ cudaError_t launch_raster_binned(const CallTable &tab, const CamDev &cam, uint64
                                  uint64_t slots, int tile_w, int tile_h, int chunk, uint32_t *status,
                                  hm_frame_stats *stats, cudaStream_t st);
 cudaError_t launch_probe_atomic_min(uint64_t *buf, int64_t n, int rounds, int pattern, cudaStream_t st);
+cudaError_t launch_probe_quotient(const float *num, const float *den, float *out, int64_t n, cudaStream_t st);
 cudaError_t launch_resolve(const CallTable &tab, const CamDev &cam, const LightsDev &Ls, const FilterDev &fp,
                            const uint64_t *vis_c, const uint64_t *vis_a, float *rgba, uint32_t *status, int tile_h,
                            cudaStream_t st, const CgbDev *compressed = nullptr, int *tile_list = nullptr);

@@ -155,7 +155,7 @@ struct __align__(16) SegRec {
     int32_t uA, vA;              // start point in the major (u) / minor (v) frame, 1/256 px
     int32_t du, dv;              // B - A in that frame
     int32_t umin, umax, vmin, vmax;
-    float zA, dz;                // linear depth at A, zB - zA
+    float zA, dz;                // linear depth at A and zB - zA, both x 2^24
     float fden;                  // float(|B - A|^2), the depth parameter's denominator
     float slope;                 // dv / du (0 for a point)
     int32_t hc;                  // centre-sample half-width, 1/256 px
@@ -165,7 +165,8 @@ struct __align__(16) SegRec {
     uint32_t id_lo, id_hi;       // payload strand << 7 | segment; compressed: j, C - 1
     uint32_t cgb_hi;             // compressed: payload bits 39..12 (tangent, u, v) >> 12
     float aoA, dao;              // compressed: AO at A, AO(B) - AO(A)
-    uint32_t pad_[3];            // 96 bytes: read back with 16-byte loads
+    float rden;                  // RN(1 / fden), for quotient_rn
+    uint32_t pad_[2];            // 96 bytes: read back with 16-byte loads
 };
 static_assert(sizeof(SegRec) == 96, "SegRec is read as six 16-byte words");
 
@@ -191,11 +192,14 @@ __device__ __forceinline__ void segment_frame(const CamDev &cam, float width_m, 
     r.umax = max(uA, uB);
     r.vmin = min(vA, vB);
     r.vmax = max(vA, vB);
-    r.zA = A.z;
-    r.dz = fsub(B.z, A.z);
+    // depth pre-scaled to d24 units: a power-of-two scale is exact and
+    // commutes with every rounding of depth_d24 (which floors the result)
+    r.zA = fmul(A.z, 16777216.0f);
+    r.dz = fmul(fsub(B.z, A.z), 16777216.0f);
     r.hc = centre_halfwidth(cam, width_m, A.w, B.w);
     const int64_t dX = (int64_t)B.X - A.X, dY = (int64_t)B.Y - A.Y;
     r.fden = __ll2float_rn(dX * dX + dY * dY);
+    r.rden = __frcp_rn(r.fden);
     r.slope = r.du == 0 ? 0.0f : (float)r.dv / (float)r.du;
     const bool shrt = abs(r.du) < (1 << 14) && abs(r.dv) < (1 << 14);
     r.flags = (xm ? 1 : 0) | (shrt ? 2 : 0);
@@ -211,6 +215,31 @@ __device__ __forceinline__ bool segment_pixel_box(const SegRec &r, int dim_u, in
     mlo = max((r.vmin - 1) >> 8, 0);
     mhi = min(r.vmax >> 8, dim_v - 1);
     return ilo <= ihi && r.vmax >= 0 && r.vmin <= 256 * dim_v;
+}
+
+// Correctly rounded binary32 quotient a / b given y = RN(1 / b): Markstein's
+// FMA division (P. Markstein, IBM J. Res. Dev. 34(1), 1990).  q0 = RN(a y)
+// lies within 1.5 ulp of a / b; one correction q1 = RN(q0 + RN(a - b q0) y)
+// brings it within one ulp; Markstein's theorem (y within half an ulp of
+// 1 / b, q1 within one ulp of a / b, radix 2) makes the residual a - b q1
+// exact and q2 = RN(q1 + (a - b q1) y) equal to RN(a / b).  Valid while the
+// quotient and the residuals stay normal or zero: here a is an integer-valued
+// depth numerator (|a| < 2^63) and b = |B - A|^2 >= 1, so they do.
+__device__ __forceinline__ float quotient_rn(float a, float b, float y) {
+    const float q0 = __fmul_rn(a, y);
+    const float q1 = __fmaf_rn(__fmaf_rn(-q0, b, a), y, q0);
+    return __fmaf_rn(__fmaf_rn(-q1, b, a), y, q1);
+}
+
+// 24-bit depth of a candidate at depth parameter t (Sec. 3.1.2): z = clamp(zA
+// + dz t, 0, 1), d24 = min(floor(z 2^24), 2^24 - 1).  zA and dz carry the 2^24
+// scale, so z 2^24 is computed directly and d24 equals the unscaled
+// formula's bit for bit.  t = clamp(fn / |B - A|^2, 0, 1) comes from
+// quotient_rn (0 for a point segment).
+__device__ __forceinline__ uint32_t depth_d24(const SegRec &q, float t) {
+    const float zs = fclamp(fadd(q.zA, fmul(q.dz, t)), 0.0f, 16777216.0f);
+    const uint32_t d24 = (uint32_t)floorf(zs);
+    return d24 > 16777215u ? 16777215u : d24;
 }
 
 // Low 40 bits of a compressed key at projection parameter t.
@@ -284,11 +313,9 @@ __device__ __forceinline__ void raster_item(const SegRec &q_shared, int i, int m
         float t = 0.0f;
         if (!degenerate) {
             const float fn = sizeof(I) == 4 ? __int2float_rn((int32_t)num) : __ll2float_rn((int64_t)num);
-            t = fclamp(fdiv(fn, q.fden), 0.0f, 1.0f);
+            t = fclamp(quotient_rn(fn, q.fden, q.rden), 0.0f, 1.0f);
         }
-        const float z = fclamp(fadd(q.zA, fmul(q.dz, t)), 0.0f, 1.0f);
-        uint32_t d24 = (uint32_t)floorf(fmul(z, 16777216.0f));
-        d24 = d24 > 16777215u ? 16777215u : d24;
+        const uint32_t d24 = depth_d24(q, t);
         const uint64_t key = ((uint64_t)d24 << 40) | (kCgb ? compressed_payload(q, t) : id);
         n_cons += 1;
         n_cen += cen;

@@ -427,11 +427,9 @@ __device__ __forceinline__ void raster_item_msaa(const SegRec &q_shared, int i, 
             if (!degenerate) {
                 const I nk = ru * du + rv * dv;
                 const float fn = sizeof(I) == 4 ? __int2float_rn((int32_t)nk) : __ll2float_rn((int64_t)nk);
-                t = fclamp(fdiv(fn, q.fden), 0.0f, 1.0f);
+                t = fclamp(quotient_rn(fn, q.fden, q.rden), 0.0f, 1.0f);
             }
-            const float z = fclamp(fadd(q.zA, fmul(q.dz, t)), 0.0f, 1.0f);
-            uint32_t d24 = (uint32_t)floorf(fmul(z, 16777216.0f));
-            d24 = d24 > 16777215u ? 16777215u : d24;
+            const uint32_t d24 = depth_d24(q, t);
             const int px = xm ? i : m, py = xm ? m : i;
             const int64_t p = (int64_t)((uint32_t)py * (uint32_t)W + (uint32_t)px);
             atomicMin(reinterpret_cast<unsigned long long *>(vis_s + (int64_t)k * npx + p),
@@ -546,6 +544,24 @@ __global__ void __launch_bounds__(256) probe_atomic_min_kernel(unsigned long lon
 cudaError_t launch_probe_atomic_min(uint64_t *buf, int64_t n, int rounds, int pattern, cudaStream_t st) {
     int grid = num_sms() * 8;
     probe_atomic_min_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<unsigned long long *>(buf), n, rounds, pattern);
+    return cudaGetLastError();
+}
+
+// The rasterizers' depth-parameter quotient over arrays (hm_probe_quotient):
+// the per-segment reciprocal, then quotient_rn.
+__global__ void __launch_bounds__(256) probe_quotient_kernel(const float *__restrict__ num,
+                                                             const float *__restrict__ den,
+                                                             float *__restrict__ out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float b = __ldg(&den[i]);
+        out[i] = quotient_rn(__ldg(&num[i]), b, __frcp_rn(b));
+    }
+}
+
+cudaError_t launch_probe_quotient(const float *num, const float *den, float *out, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t want = (n + 255) / 256, cap = (int64_t)num_sms() * 8;
+    probe_quotient_kernel<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(num, den, out, n);
     return cudaGetLastError();
 }
 

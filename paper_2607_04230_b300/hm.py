@@ -127,6 +127,7 @@ def lib():
         "hm_set_tuning": [P],
         "hm_get_tuning": [P],
         "hm_probe_atomic_min": [P, i64, i32, i32, P],
+        "hm_probe_quotient": [P, P, P, i64, P],
     }
     for name, args in sig.items():
         if hasattr(L, name):
@@ -458,6 +459,14 @@ def set_phase_events(events):
 
 def probe_atomic_min(buf, rounds: int = 1, pattern: int = 0, stream=None):
     check(lib().hm_probe_atomic_min(_dptr(buf), buf.numel(), int(rounds), int(pattern), _stream_ptr(stream)))
+
+
+def probe_quotient(num, den, out, stream=None):
+    """out = the rasterizers' binary32 depth-parameter quotient num / den
+    (float32 device tensors of one size; den >= 1)."""
+    if not (num.numel() == den.numel() == out.numel()):
+        raise ValueError("num, den and out must have the same size")
+    check(lib().hm_probe_quotient(_dptr(num), _dptr(den), _dptr(out), num.numel(), _stream_ptr(stream)))
 
 
 def stats_dict(stats_tensor):

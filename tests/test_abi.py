@@ -256,6 +256,9 @@ def test_resolve_scratch_and_probe_arguments(L):
         assert L.hm_probe_atomic_min(fake, 16, 1, pattern, None) == INVALID
     assert L.hm_probe_atomic_min(fake, 0, 1, 0, None) == INVALID
     assert L.hm_probe_atomic_min(fake, 16, 0, 0, None) == INVALID
+    assert L.hm_probe_quotient(None, None, None, -1, None) == INVALID
+    assert L.hm_probe_quotient(None, fake, fake, 4, None) == INVALID
+    assert L.hm_probe_quotient(None, None, None, 0, None) == 0      # empty: nothing launched
 
 
 def test_key_buffer_sizes_per_layout(L):
