@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256) resolve_tiles_kernel(const uint64_t *__re
 // persistent resolve starts its longest tiles first and ends without a long
 // tail.  Writes list[0] = listed tiles, list[1] = 0 (the resolve's work
 // counter) and list[2 ..] = tile indices.
-constexpr int kOrderBuckets = 64;
+constexpr int kOrderBuckets = 64, kOrderLoads = 8;
 __global__ void __launch_bounds__(1024) resolve_order_kernel(const int *__restrict__ weights, int ntiles,
                                                              int tile_px, int *__restrict__ list) {
     __shared__ int s_hist[kOrderBuckets];
@@ -84,9 +84,18 @@ __global__ void __launch_bounds__(1024) resolve_order_kernel(const int *__restri
     __syncthreads();
     // 1 <= w <= tile_px: class 0 holds the heaviest tiles
     auto bucket = [tile_px](int w) { return kOrderBuckets - 1 - (int)((int64_t)w * kOrderBuckets / (tile_px + 1)); };
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        const int w = weights[t];
-        if (w > 0) atomicAdd(&s_hist[bucket(w)], 1);
+    // kOrderLoads weights per thread are loaded before any is used, so a
+    // pass over a 4K frame's tiles waits for one round of loads, not eight
+    for (int t0 = threadIdx.x; t0 < ntiles; t0 += blockDim.x * kOrderLoads) {
+        int w[kOrderLoads];
+#pragma unroll
+        for (int k = 0; k < kOrderLoads; ++k) {
+            const int t = t0 + k * (int)blockDim.x;
+            w[k] = t < ntiles ? weights[t] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < kOrderLoads; ++k)
+            if (w[k] > 0) atomicAdd(&s_hist[bucket(w[k])], 1);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -100,9 +109,16 @@ __global__ void __launch_bounds__(1024) resolve_order_kernel(const int *__restri
         list[1] = 0;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        const int w = weights[t];
-        if (w > 0) list[2 + atomicAdd(&s_hist[bucket(w)], 1)] = t;
+    for (int t0 = threadIdx.x; t0 < ntiles; t0 += blockDim.x * kOrderLoads) {
+        int w[kOrderLoads];
+#pragma unroll
+        for (int k = 0; k < kOrderLoads; ++k) {
+            const int t = t0 + k * (int)blockDim.x;
+            w[k] = t < ntiles ? weights[t] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < kOrderLoads; ++k)
+            if (w[k] > 0) list[2 + atomicAdd(&s_hist[bucket(w[k])], 1)] = t0 + k * (int)blockDim.x;
     }
 }
 
