@@ -965,6 +965,9 @@ def frame_bound(kernels, phase_ms, W, H, frame_ms):
                            for k, b in (("clear", t_clear), ("raster", t_raster), ("resolve", t_resolve))}}
 
 
+RASTER_TWIN = {"single_1080p_ao": "single_1080p", "single_1080p_ao_block": "single_1080p_block"}
+
+
 def frame_roofline(atomics, phase_ms, W, H, peak_rates, workload, clk, sms):
     """Roofline of one frame's two main kernels: the rasterizer against the
     L2 RED sector rate of the live atomic probe (`peak_rates`, atomics/s per
@@ -978,7 +981,10 @@ def frame_roofline(atomics, phase_ms, W, H, peak_rates, workload, clk, sms):
     # operations (a 64-bit atomicMin updates one 32-byte sector; atomics of
     # one instruction that share a sector share the operation)
     sector_peak = max(r * PROBE_SECTORS_PER_ATOMIC[p] for p, r in peak_rates.items())
-    re = ncu_entry("raster_kernel", workload)
+    # the baked-AO frame rasterizes the same geometry with the same kernel (AO
+    # enters only the shading), so its raster counters are the plain frame's
+    rwl = RASTER_TWIN.get(workload, workload)
+    re = ncu_entry("raster_kernel", rwl)
     spa = re["red_sectors"] / atomics if re and re.get("red_sectors") and atomics else None
     spa_note = "ncu-measured" if spa is not None else "assumed one per atomic (no ncu summary for these sources)"
     spa = spa if spa is not None else 1.0
@@ -997,7 +1003,7 @@ def frame_roofline(atomics, phase_ms, W, H, peak_rates, workload, clk, sms):
     # instruction-issue and FP32 views (ncu counters of the same sources and
     # workload over the event-timed passes): the raster kernel, and the
     # resolve call's kernels (tile count, order, decode, filter) together
-    rv = alu_views(ncu_phase(("raster_kernel",), workload), t_r, clk, sms)
+    rv = alu_views(ncu_phase(("raster_kernel",), rwl), t_r, clk, sms)
     if rv:
         kernels["raster_kernel"].update(issue=rv["issue"], fp32=rv["fp32"])
     sv = alu_views(ncu_phase(RESOLVE_PHASE_KERNELS, workload), t_s, clk, sms)
@@ -1007,7 +1013,8 @@ def frame_roofline(atomics, phase_ms, W, H, peak_rates, workload, clk, sms):
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     d = kernels[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-                "frac": d["achieved"] / d["peak"], "traffic": ncu_traffic(dom, workload), "kernel": dom,
+                "frac": d["achieved"] / d["peak"],
+                "traffic": ncu_traffic(dom, rwl if dom == "raster_kernel" else workload), "kernel": dom,
                 "peak_source": ("live probe hm_probe_atomic_min over a "
                                 f"{2 * W * H}-element buffer: coalesced {peak_rates[0] / 1e9:.1f} Gatom/s "
                                 f"(4 per sector = {peak_rates[0] * 0.25 / 1e9:.1f} G sectors/s), hashed "
