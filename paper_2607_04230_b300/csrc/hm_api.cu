@@ -905,7 +905,7 @@ namespace {
 // sides up to 16384 has fewer than 1,600 tiles of 32 x 16, and the entry
 // point checks the list against this room.
 constexpr int kNoallocMaxTiles = 4096;
-constexpr int kNoallocListFloat4 = (4 * (2 + 2 * kNoallocMaxTiles) + 15) / 16;
+constexpr int kNoallocListFloat4 = (4 * (3 + 2 * kNoallocMaxTiles) + 15) / 16;
 static __device__ __align__(256) float4 g_noalloc_scratch[2 * HM_NOALLOC_MAX_PIXELS + kNoallocListFloat4];
 
 // Device address of g_noalloc_scratch on the current device, looked up once

@@ -75,10 +75,12 @@ __global__ void __launch_bounds__(256) resolve_tiles_kernel(const uint64_t *__re
 // counting sort of their key counts into kOrderBuckets classes, so that the
 // persistent resolve starts its longest tiles first and ends without a long
 // tail.  Writes list[0] = listed tiles, list[1] = 0 (the resolve's work
-// counter) and list[2 ..] = tile indices.
+// counter), list[2 ..] = tile indices and *dec_work = 0 (the decode pass's
+// work counter).
 constexpr int kOrderBuckets = 64, kOrderLoads = 8;
 __global__ void __launch_bounds__(1024) resolve_order_kernel(const int *__restrict__ weights, int ntiles,
-                                                             int tile_px, int *__restrict__ list) {
+                                                             int tile_px, int *__restrict__ list,
+                                                             int *__restrict__ dec_work) {
     __shared__ int s_hist[kOrderBuckets];
     if (threadIdx.x < kOrderBuckets) s_hist[threadIdx.x] = 0;
     __syncthreads();
@@ -107,6 +109,7 @@ __global__ void __launch_bounds__(1024) resolve_order_kernel(const int *__restri
         }
         list[0] = acc;
         list[1] = 0;
+        *dec_work = 0;
     }
     __syncthreads();
     for (int t0 = threadIdx.x; t0 < ntiles; t0 += blockDim.x * kOrderLoads) {
@@ -123,9 +126,10 @@ __global__ void __launch_bounds__(1024) resolve_order_kernel(const int *__restri
 }
 
 // Two-pass resolve with the tile-list scratch, first pass: over strips of 8
-// rows of the listed tiles (the tiles heaviest first, a tile's strips on
-// consecutive CTAs of a persistent grid, round-robin, so a heavy tile is
-// spread over several SMs), every centre key is decoded and shaded once
+// rows of the listed tiles (the tiles heaviest first; the CTAs of a
+// persistent grid take strips one at a time from a work counter, so a heavy
+// tile is spread over several SMs and no CTA idles while strips remain),
+// every centre key is decoded and shaded once
 // (px_col = shaded colour, centre depth bits) and every screen tangent the
 // filter needs is found once: px_ts.xy of the centre key, px_ts.zw of the
 // conservative key of a promoted pixel or a depth mismatch, (0, 0) for a
@@ -142,11 +146,12 @@ __global__ void __launch_bounds__(kDecThreads, 4) resolve_decode_kernel(CallTabl
                                                                        const uint64_t *__restrict__ vis_a,
                                                                        const int *__restrict__ list,
                                                                        float4 *__restrict__ px_col,
-                                                                       float4 *__restrict__ px_ts, uint32_t *status) {
+                                                                       float4 *__restrict__ px_ts, uint32_t *status,
+                                                                       int *__restrict__ work) {
     constexpr int kStrips = kFwdTileH / kDecRows;
     __shared__ uint64_t s_bases[HM_MAX_GROOMS_PER_CALL + 1];
     __shared__ uint16_t s_job[2 * kDecPx];
-    __shared__ int s_ng, s_na;
+    __shared__ int s_ng, s_na, s_wi;
     const int tid = threadIdx.x, lane = tid & 31;
     const int W = cam.W, H = cam.H;
     const int ntx = (W + kFwdTileW - 1) / kFwdTileW;
@@ -156,14 +161,17 @@ __global__ void __launch_bounds__(kDecThreads, 4) resolve_decode_kernel(CallTabl
         s_bases[tid] = b;
     }
     const int nwork = list[0] * kStrips;
-    for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
-        const int tile = list[2 + wi / kStrips];
-        const int x0 = (tile % ntx) * kFwdTileW, y0 = (tile / ntx) * kFwdTileH + (wi % kStrips) * kDecRows;
+    for (;;) {
         if (tid == 0) {
             s_ng = 0;
             s_na = 0;
+            s_wi = atomicAdd(work, 1);      // the next strip, heaviest tiles first
         }
         __syncthreads();
+        const int wi = s_wi;
+        if (wi >= nwork) break;
+        const int tile = list[2 + wi / kStrips];
+        const int x0 = (tile % ntx) * kFwdTileW, y0 = (tile / ntx) * kFwdTileH + (wi % kStrips) * kDecRows;
         // centre decodes go to s_job[0 ..), conservative ones to s_job[kDecPx ..)
         {
             const int t = tid;                   // one strip pixel per thread
@@ -607,8 +615,10 @@ size_t resolve_smem_bytes(int radius, int tile_h) {
 // Tiles of the finest tiling (32 x 16), the most any tile height can have.
 static int resolve_max_tiles(int W, int H) { return ((W + kFwdTileW - 1) / kFwdTileW) * ((H + 15) / 16); }
 
-// list[0], list[1], the ordered tile list, then one key count per tile.
-size_t resolve_list_bytes(int W, int H) { return sizeof(int) * (2 + 2 * (size_t)resolve_max_tiles(W, H)); }
+// list[0], list[1], the ordered tile list, one key count per tile, then the
+// decode pass's work counter.
+size_t resolve_list_bytes(int W, int H) { return sizeof(int) * (3 + 2 * (size_t)resolve_max_tiles(W, H)); }
+static int *decode_work_counter(int *list, int W, int H) { return list + 2 + 2 * (size_t)resolve_max_tiles(W, H); }
 
 cudaError_t launch_tile_list(const uint64_t *vis_a, float4 *rgba, const CamDev &cam, int th, int *list,
                              cudaStream_t st) {
@@ -619,7 +629,7 @@ cudaError_t launch_tile_list(const uint64_t *vis_a, float4 *rgba, const CamDev &
         resolve_tiles_kernel<16><<<(ntiles + 7) / 8, 256, 0, st>>>(vis_a, rgba, cam, ntx, ntiles, weights);
     else
         resolve_tiles_kernel<32><<<(ntiles + 7) / 8, 256, 0, st>>>(vis_a, rgba, cam, ntx, ntiles, weights);
-    resolve_order_kernel<<<1, 1024, 0, st>>>(weights, ntiles, kFwdTileW * th, list);
+    resolve_order_kernel<<<1, 1024, 0, st>>>(weights, ntiles, kFwdTileW * th, list, decode_work_counter(list, W, H));
     return cudaGetLastError();
 }
 
@@ -676,7 +686,8 @@ static cudaError_t launch_resolve_t(const CallTable &tab, const CamDev &cam, con
     float4 *px_ts = px_col + (size_t)cam.W * cam.H;
     const int dec_grid = num_sms() * 4 < ntiles * (TH / kDecRows) ? num_sms() * 4 : ntiles * (TH / kDecRows);
     resolve_decode_kernel<TH><<<dec_grid, kDecThreads, 0, st>>>(tab, cam, Ls, fp, vis_c, vis_a, tile_list, px_col,
-                                                                 px_ts, status);
+                                                                 px_ts, status,
+                                                                 decode_work_counter(tile_list, cam.W, cam.H));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int resident = resolve_resident<TH, false, true>();

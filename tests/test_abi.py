@@ -231,17 +231,18 @@ def test_resolve_scratch_and_probe_arguments(L):
     pattern are rejected before anything is launched."""
     L.hm_resolve_scratch_bytes.restype = ctypes.c_size_t
     L.hm_resolve_scratch_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32]
-    # tile list (list, order, key counts of the 32 x 16 tiling), 16-byte
-    # aligned, then two float4 per pixel for the two-pass resolve
+    # tile list (count and work counter, order, key counts of the 32 x 16
+    # tiling, the decode pass's work counter), 16-byte aligned, then two
+    # float4 per pixel for the two-pass resolve
     al = lambda b: (b + 15) // 16 * 16
-    assert L.hm_resolve_scratch_bytes(1920, 1080) == al(4 * (2 + 2 * 60 * 68)) + 32 * 1920 * 1080
-    assert L.hm_resolve_scratch_bytes(33, 17) == al(4 * (2 + 2 * 2 * 2)) + 32 * 33 * 17
+    assert L.hm_resolve_scratch_bytes(1920, 1080) == al(4 * (3 + 2 * 60 * 68)) + 32 * 1920 * 1080
+    assert L.hm_resolve_scratch_bytes(33, 17) == al(4 * (3 + 2 * 2 * 2)) + 32 * 33 * 17
     assert L.hm_resolve_scratch_bytes(0, 10) == 0 and L.hm_resolve_scratch_bytes(10, 16385) == 0
     # the adjoint's scratch: colour and screen-tangent gradients per pixel, then the same tile list
     L.hm_backward_scratch_bytes.restype = ctypes.c_size_t
     L.hm_backward_scratch_bytes.argtypes = [ctypes.c_int32, ctypes.c_int32]
     for w, h in ((1920, 1080), (512, 512), (33, 17)):
-        assert L.hm_backward_scratch_bytes(w, h) == 32 * w * h + 4 * (2 + 2 * ((w + 31) // 32) * ((h + 15) // 16))
+        assert L.hm_backward_scratch_bytes(w, h) == 32 * w * h + 4 * (3 + 2 * ((w + 31) // 32) * ((h + 15) // 16))
     assert L.hm_backward_scratch_bytes(0, 10) == 0
     sc = synth.tiny_scene(0, num_strands=10)
     cam = hm.camera_struct(sc.camera)
