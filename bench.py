@@ -415,7 +415,7 @@ def cpu_baseline(scene, max_segments: int = 2_000_000):
     every = max(1, int(np.ceil(total / max_segments)))
     oracle_frame_sample(scene, 1000)              # warm-up (library load, thread pool)
     segs, dt = oracle_frame_sample(scene, every)
-    what = "the whole workload" if every == 1 else f"every {every}th strand of every groom"
+    what = "the whole workload" if every == 1 else f"one strand in {every} of every groom"
     return {"value": segs / dt, "unit": UNIT, "cores": host_cores(), "cpu_model": host_cpu_model(), "kind": "oracle",
             "sample": f"{what} ({segs} segments, one frame) rasterized by the C oracle "
                       f"(OpenMP, all host threads) and resolved by the FP64 torch oracle, {dt:.1f} s"}
@@ -459,7 +459,7 @@ def run_reference(args, rank, world):
             "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": host_cores(), "cpu_model": host_cpu_model(),
                              "kind": "oracle",
-                             "sample": f"each step: every {every}th strand (rotating offset) of the workload, "
+                             "sample": f"each step: one strand in {every} (rotating offset) of the workload, "
                                        f"C oracle raster + FP64 torch resolve"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
