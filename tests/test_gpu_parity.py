@@ -220,3 +220,34 @@ def test_tile_list_resolve_bit_identical(tile_h):
     covered = np.nonzero((va & oracle.PAYLOAD_MASK) != oracle.PAYLOAD_MASK)[0]
     ref, pix = oracle_rgba(sc, lods, vc, va, pixels=covered)
     assert_rgba_close(listed.rgba.cpu().numpy().astype(np.float64), ref, pix)
+
+
+def test_tile_list_empty_frame_then_keys():
+    """With the tile-list scratch, a frame without any key lists no tile: the
+    decode pass's CTAs find their work counter past the end at once and every
+    pixel is written RGBA 0; the same scratch then resolves a frame with keys
+    exactly like one CTA per tile (the order pass resets both work counters)."""
+    import torch
+    from paper_2607_04230_b300 import hm
+    sc = synth.tiny_scene(15, width=150, height=90, num_strands=500, dist_m=0.5)
+    grooms = hm.upload_scene(sc)
+    listed = hm.Frame(sc.camera.width, sc.camera.height, tile_list=True)
+    listed.vis_center.fill_(-1)                # EMPTY keys everywhere
+    listed.vis_cons.fill_(-1)
+    listed.rgba.fill_(float("nan"))
+    hm.resolve_shade(grooms, sc.camera, sc.lights, sc.filt, listed.vis_center, listed.vis_cons, listed.rgba,
+                     tile_scratch=listed.tile_scratch)
+    torch.cuda.synchronize()
+    hm.get_device_status()
+    assert torch.count_nonzero(listed.rgba).item() == 0
+    plain = hm.Frame(sc.camera.width, sc.camera.height)
+    hm.render(grooms, sc, plain)
+    listed.vis_center.copy_(plain.vis_center)
+    listed.vis_cons.copy_(plain.vis_cons)
+    listed.rgba.fill_(float("nan"))
+    hm.resolve_shade(grooms, sc.camera, sc.lights, sc.filt, listed.vis_center, listed.vis_cons, listed.rgba,
+                     tile_scratch=listed.tile_scratch)
+    torch.cuda.synchronize()
+    hm.get_device_status()
+    assert torch.count_nonzero(plain.vis_cons != -1).item() > 100
+    assert torch.equal(plain.rgba, listed.rgba)
